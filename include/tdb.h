@@ -1,0 +1,184 @@
+/*
+ * tdb.h - C ABI of libtdb, a GB300 (sm_103a) implementation of the in-situ
+ * compressor of Zamani Ashtiani, Malik and Babaee, "Scalable in situ
+ * compression of transient simulation data using time-dependent bases".
+ *
+ * A p-mode snapshot V(t) (p = 2..4 on the GPU) is approximated by a core T
+ * (r_1 x ... x r_p) and W-orthonormal bases U_n (N_n x r_n):
+ *     V ~ T x_1 U_1 x_2 ... x_p U_p                            (Eq. 2.5)
+ * and streamed through the evolution equations with gauge phi = 0
+ * (Eqs. 2.15, 2.16), advanced by explicit Euler with the first-order data
+ * difference (Sec. 2.3), with the add/remove-mode control of Sec. 2.5.
+ *
+ * Conventions for every entry point
+ *  - Layout: column-major, mode 1 fastest.  Element (i_1..i_p) of an N_1 x ..
+ *    x N_p tensor is at offset sum_n i_n prod_{m<n} N_m; this equals a
+ *    C-contiguous array of shape (N_p, ..., N_1).  U_n is N_n x r_n column-major
+ *    (U[i + N_n a]); the core is r_1 x ... x r_p column-major.
+ *  - Snapshot element type: double in TDB_FP64 mode, float otherwise.
+ *  - Device pointers are CUDA device (or managed) memory of the current device;
+ *    host pointers are ordinary host memory.  Every call is ordered on the
+ *    stream given to tdb_init; calls that return host data synchronise it.
+ *  - Memory: the library allocates no device memory.  The caller allocates a
+ *    workspace of tdb_workspace_bytes() bytes (256-byte aligned) and owns it;
+ *    it must outlive the context.  The context struct itself is host memory
+ *    owned by the library (freed by tdb_destroy).
+ *  - Snapshot buffers stay owned by the caller.  tdb_push_snapshot keeps a
+ *    pointer to the last pushed snapshot as "previous" until the next push
+ *    returns, so the caller must not modify that buffer until then (ping-pong
+ *    two buffers).  tdb_init keeps V0 the same way.
+ *  - Errors: every function returns a tdb_status and never throws.  A message
+ *    for the last failure is in tdb_last_error().  CUDA errors are reported as
+ *    TDB_ERR_CUDA; device-side conditions (non-finite data, failed Cholesky)
+ *    are reported by the call that observes them.
+ */
+#ifndef TDB_H
+#define TDB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TDB_MAX_MODES 4
+#define TDB_MAX_RANK 32
+
+typedef enum tdb_status {
+  TDB_OK = 0,
+  TDB_ERR_INVALID_ARG = 1,     /* null pointer, bad enum, bad threshold */
+  TDB_ERR_SHAPE = 2,           /* ndim outside 2..4, a mode size outside 1..1024 */
+  TDB_ERR_RANK = 3,            /* a rank outside 1..min(N_n, prod_{m!=n} r_m, TDB_MAX_RANK) */
+  TDB_ERR_RANK_DEFICIENT = 4,  /* T_(n) T_(n)^T or U^T W U not positive definite */
+  TDB_ERR_NONFINITE = 5,       /* NaN or Inf in a snapshot or in the state */
+  TDB_ERR_CUDA = 6,            /* a CUDA runtime call failed */
+  TDB_ERR_TIMEOUT = 7,         /* a bounded device-side wait ran out */
+  TDB_ERR_STATE = 8,           /* call out of order (e.g. push before init) */
+  TDB_WARN_RANK_CAP = 9,       /* error above eps_th with every rank at its cap */
+  TDB_ERR_WORKSPACE = 10,      /* workspace null, too small or misaligned */
+  TDB_ERR_UNSUPPORTED = 11     /* configuration not built (see tdb_config) */
+} tdb_status;
+
+/* Arithmetic of the projection pass (Eqs. 2.15, 2.16). */
+enum tdb_precision {
+  TDB_FP64 = 0,       /* double snapshots; every step in double (parity mode) */
+  TDB_FP32 = 1,       /* float snapshots; unfused CUDA-core kernels, float products */
+  TDB_BF16_TTM = 2    /* float snapshots; fused difference + projection on the tensor
+                         cores (bf16 operands, fp32 accumulation), fp64 small algebra */
+};
+
+/* When the exact error of Eq. 2.20 is evaluated. */
+enum tdb_error_mode {
+  TDB_ERRMODE_EXACT = 0,     /* every step */
+  TDB_ERRMODE_EVERY_K = 1,   /* every error_every steps */
+  TDB_ERRMODE_MLP = 2,       /* when the learned estimator cannot rule out eps > eps_th */
+  TDB_ERRMODE_NONE = 3       /* never (fixed rank, no control) */
+};
+
+typedef struct tdb_config {
+  int ndim;                         /* p, 2..TDB_MAX_MODES */
+  int64_t dims[TDB_MAX_MODES];      /* N_n, mode 1 fastest */
+  int rank[TDB_MAX_MODES];          /* initial r_n; 0 = from gamma_th on the HOSVD spectrum */
+  int rank_max[TDB_MAX_MODES];      /* cap on r_n (<= TDB_MAX_RANK); 0 = TDB_MAX_RANK */
+  const double* weights[TDB_MAX_MODES]; /* host, length N_n: diagonal of W^(n) (Eq. 2.17);
+                                       NULL = identity.  Copied by tdb_init. */
+  double eps_th;                    /* epsilon_th of Sec. 2.5; <= 0 disables rank control */
+  double gamma_th;                  /* gamma_th in percent (Eq. 2.21), e.g. 99.999 */
+  int slope_window;                 /* K: steps of the error-slope test (Sec. 2.5); 0 = 10 */
+  int precision;                    /* enum tdb_precision */
+  int error_mode;                   /* enum tdb_error_mode */
+  int error_every;                  /* period for TDB_ERRMODE_EVERY_K and the estimator's
+                                       forced exact checks; 0 = 1 */
+  int reorth;                       /* 1 = weighted Cholesky-QR of U_n after each step
+                                       (recommended; the paper is silent), 0 = off */
+} tdb_config;
+
+/* Per-step report (host struct filled by tdb_push_snapshot). */
+typedef struct tdb_step_info {
+  int64_t step;                     /* snapshots pushed since init */
+  double eps;                       /* exact error after the step and any control (Eq. 2.20),
+                                       or the estimate when eps_exact == 0 */
+  int eps_exact;                    /* 1 = exact evaluation this step, 0 = estimate / none */
+  double eps_step;                  /* exact error of the Euler step before control acted */
+  double gamma[TDB_MAX_MODES];      /* gamma^(n)(r_n) in percent (Eq. 2.21, second form) */
+  double sigma_min[TDB_MAX_MODES];  /* smallest singular value of T_(n) (Eq. 2.18) */
+  int ranks[TDB_MAX_MODES];         /* r_n after the step */
+  int reinit;                       /* HOSVD re-initialisations performed this step */
+  int action;                       /* 0 none, 1 reinit, 2 increase, 3 decrease, 4 revert, 5 cap */
+  double cr;                        /* compression ratio CR of Sec. 2.6 at the new ranks */
+  double dv_norm;                   /* ||V_{k+1} - V_k||_W */
+  double ds_norm;                   /* ||dS||_F (the core increment) */
+} tdb_step_info;
+
+typedef struct tdb_ctx tdb_ctx;
+
+/* Bytes of device workspace needed for cfg (sized for rank_max).  0 on a bad cfg. */
+size_t tdb_workspace_bytes(const tdb_config* cfg);
+
+/* Initialise by truncated HOSVD of V0 (Sec. 2.3 last paragraph; ranks by gamma_th,
+ * Sec. 2.5).  V0: device snapshot.  stream: cudaStream_t (NULL = legacy default).
+ * On success *ctx owns nothing on the device but its view of workspace. */
+tdb_status tdb_init(tdb_ctx** ctx, const tdb_config* cfg, void* workspace, size_t workspace_bytes,
+                    const void* V0, void* stream);
+
+/* Initialise from given factors instead of the HOSVD (for parity runs that start
+ * from a known state).  core: host double r_1..r_p column-major; U[n]: host double
+ * N_n x r_n column-major; ranks: host int[p].  V0 as for tdb_init. */
+tdb_status tdb_init_from_factors(tdb_ctx** ctx, const tdb_config* cfg, void* workspace,
+                                 size_t workspace_bytes, const double* core,
+                                 const double* const* U, const int* ranks, const void* V0,
+                                 void* stream);
+
+/* One step of the compressor with the next snapshot (device pointer):
+ * difference, fused projection (Eqs. 2.15, 2.16), pseudo-inverse and complement
+ * projection (Sec. 2.2), Euler update, re-orthonormalisation, error (Eq. 2.20) per
+ * error_mode, and rank control (Sec. 2.5).  info (host, nullable) receives the
+ * report; the call synchronises the stream. */
+tdb_status tdb_push_snapshot(tdb_ctx* ctx, const void* V_next, tdb_step_info* info);
+
+/* Write V^TDB = T x_1 U_1 ... x_p U_p (Eq. 2.5) into V_out (device, caller-owned,
+ * prod N_n elements of the snapshot type).  Stream-ordered, no sync. */
+tdb_status tdb_reconstruct(tdb_ctx* ctx, void* V_out);
+
+/* Exact error of the current state against V_now (device) and one pass of the
+ * Sec. 2.5 rule on it (re-initialising from V_now if it fires).  ranks_out:
+ * host int[p] (nullable); eps_out: host (nullable).  Synchronises. */
+tdb_status tdb_adapt_rank(tdb_ctx* ctx, const void* V_now, int* ranks_out, double* eps_out);
+
+/* Copy the current factors to host memory: core (prod r_n doubles) and U[n]
+ * (N_n x r_n doubles each); any of them may be NULL.  ranks: host int[p]
+ * (nullable).  Synchronises. */
+tdb_status tdb_get_factors(tdb_ctx* ctx, double* core, double* const* U, int* ranks);
+
+/* Copy the projections of the last step to host memory (for tests): dS
+ * (prod r_n doubles) and Y[n] (prod_{m<n} r_m x N_n x prod_{m>n} r_m doubles,
+ * column-major, i.e. the tensor whose mode-n unfolding is Y_(n) of Eq. 2.16).
+ * Any pointer may be NULL.  Synchronises. */
+tdb_status tdb_get_projection(tdb_ctx* ctx, double* dS, double* const* Y);
+
+/* Current step counter and HOSVD re-initialisation count (host outputs, nullable). */
+tdb_status tdb_get_counters(tdb_ctx* ctx, int64_t* steps, int64_t* reinits, int64_t* exact_evals);
+
+/* Serialise the state (factors, ranks, counters, controller history) into buf
+ * (host).  With buf == NULL only *bytes is set.  Synchronises. */
+tdb_status tdb_save_state(tdb_ctx* ctx, void* buf, size_t* bytes);
+/* Restore a state saved with the same config.  The previous snapshot pointer
+ * must be supplied again (device). */
+tdb_status tdb_load_state(tdb_ctx* ctx, const void* buf, size_t bytes, const void* V_prev);
+
+/* Last error message of ctx (or of the last failed tdb_init on this thread when
+ * ctx is NULL).  Never NULL. */
+const char* tdb_last_error(const tdb_ctx* ctx);
+const char* tdb_status_string(tdb_status s);
+
+/* Release the context (not the workspace).  NULL is accepted. */
+void tdb_destroy(tdb_ctx* ctx);
+
+/* Library version and build facts: "tdb <ver> sm_103a". */
+const char* tdb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TDB_H */

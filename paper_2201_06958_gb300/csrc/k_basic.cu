@@ -1,0 +1,257 @@
+// k_basic.cu - elementwise kernels, weighted norms and the generic n-mode product.
+//
+// The n-mode product (Sec. 2.1) out = in x_n M, with M of shape J x K, is taken on
+// the view in = (L, K, Q), out = (L, J, Q) (column-major, l fastest), where
+// L = prod of the sizes before mode n and Q = prod of the sizes after it:
+//     out[l + L (j + J q)] = sum_k M[j sMj + k sMk] in[l + L (k + K q)].
+// It serves the unfused projection (M = A_n^T = (W_n U_n)^T, Eqs. 2.15/2.16),
+// the reconstruction (M = U_n, Eq. 2.5) and the core compensation (M = R_n).
+#include "common.cuh"
+#include "kernels.h"
+
+namespace tdb {
+
+// ---------------------------------------------------------------------------
+// Elementwise
+// ---------------------------------------------------------------------------
+
+template <typename T>
+__global__ void k_diff(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = a[i] - b[i];
+}
+
+template <typename T>
+void launch_diff(const T* a, const T* b, T* out, int64_t n, cudaStream_t s) {
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  k_diff<T><<<blocks, 256, 0, s>>>(a, b, out, n);
+}
+template void launch_diff<float>(const float*, const float*, float*, int64_t, cudaStream_t);
+template void launch_diff<double>(const double*, const double*, double*, int64_t, cudaStream_t);
+
+// A = W U in the compute type: A[i + N a] = w[i] U[i + N a]  (Eq. 2.17).
+template <typename T>
+__global__ void k_weighted_bases(const double* __restrict__ U, const double* __restrict__ w, T* __restrict__ A,
+                                 int64_t N, int r) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * r; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e % N;
+    A[e] = (T)(w[i] * U[e]);
+  }
+}
+
+template <typename T>
+void launch_weighted_bases(const double* U, const double* w, T* A, int64_t N, int r, cudaStream_t s) {
+  int64_t n = N * r;
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  k_weighted_bases<T><<<blocks, 256, 0, s>>>(U, w, A, N, r);
+}
+template void launch_weighted_bases<float>(const double*, const double*, float*, int64_t, int, cudaStream_t);
+template void launch_weighted_bases<double>(const double*, const double*, double*, int64_t, int, cudaStream_t);
+
+template <typename Ts, typename Td>
+__global__ void k_cast(const Ts* __restrict__ a, Td* __restrict__ b, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    b[i] = (Td)a[i];
+}
+template <typename Ts, typename Td>
+void launch_cast(const Ts* a, Td* b, int64_t n, cudaStream_t s) {
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  if (blocks < 1) blocks = 1;
+  k_cast<Ts, Td><<<blocks, 256, 0, s>>>(a, b, n);
+}
+template void launch_cast<double, float>(const double*, float*, int64_t, cudaStream_t);
+template void launch_cast<float, double>(const float*, double*, int64_t, cudaStream_t);
+template void launch_cast<double, double>(const double*, double*, int64_t, cudaStream_t);
+
+// out = a + (double) b   (core Euler update T + dS, Sec. 2.3)
+template <typename Tb>
+__global__ void k_add(const double* __restrict__ a, const Tb* __restrict__ b, double* __restrict__ out, int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    out[i] = a[i] + (double)b[i];
+}
+template <typename Tb>
+void launch_add(const double* a, const Tb* b, double* out, int64_t n, cudaStream_t s) {
+  int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  if (blocks < 1) blocks = 1;
+  k_add<Tb><<<blocks, 256, 0, s>>>(a, b, out, n);
+}
+template void launch_add<float>(const double*, const float*, double*, int64_t, cudaStream_t);
+template void launch_add<double>(const double*, const double*, double*, int64_t, cudaStream_t);
+
+// ---------------------------------------------------------------------------
+// Weighted squared norms (Eq. 2.2 with the quadrature of Eq. 2.17), deterministic:
+// block partials in fixed order, then one block sums the partials in fixed order.
+//   sum_i w_1(i_1) ... w_p(i_p) (x[i] - y[i])^2      (y may be null)
+// Grid-stride over mode-1 columns; the product of the other weights is formed
+// once per column.
+// ---------------------------------------------------------------------------
+
+
+template <typename T>
+__global__ void k_wnorm2_partial(const T* __restrict__ x, const T* __restrict__ y, WeightView wv,
+                                 double* __restrict__ partial, unsigned* flags) {
+  __shared__ double sh[32];
+  const int64_t N1 = wv.N[0];
+  int64_t ncol = 1;
+  for (int m = 1; m < wv.p; ++m) ncol *= wv.N[m];
+  double acc = 0.0;
+  bool bad = false;
+  for (int64_t c = blockIdx.x; c < ncol; c += gridDim.x) {
+    double wc = 1.0;
+    int64_t rem = c;
+    for (int m = 1; m < wv.p; ++m) {
+      int64_t im = rem % wv.N[m];
+      rem /= wv.N[m];
+      wc *= wv.w[m][im];
+    }
+    const T* xc = x + c * N1;
+    const T* yc = y ? y + c * N1 : nullptr;
+    double s = 0.0;
+    for (int64_t i = threadIdx.x; i < N1; i += blockDim.x) {
+      double d = (double)xc[i] - (yc ? (double)yc[i] : 0.0);
+      bad |= !isfinite(d);
+      s += wv.w[0][i] * d * d;
+    }
+    acc += wc * s;
+  }
+  acc = block_sum(acc, sh);
+  if (bad && flags) atomicOr(flags, kFlagNonFinite);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partial, int n, double* __restrict__ out) {
+  __shared__ double sh[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += partial[i];
+  s = block_sum(s, sh);
+  if (threadIdx.x == 0) *out = s;
+}
+
+template <typename T>
+void launch_wnorm2(const T* x, const T* y, const WeightView& wv, double* partial, int nblocks, double* out,
+                   unsigned* flags, cudaStream_t s) {
+  k_wnorm2_partial<T><<<nblocks, 256, 0, s>>>(x, y, wv, partial, flags);
+  k_sum_partials<<<1, 256, 0, s>>>(partial, nblocks, out);
+}
+template void launch_wnorm2<float>(const float*, const float*, const WeightView&, double*, int, double*, unsigned*,
+                                   cudaStream_t);
+template void launch_wnorm2<double>(const double*, const double*, const WeightView&, double*, int, double*,
+                                    unsigned*, cudaStream_t);
+
+void launch_sum_partials(const double* partial, int n, double* out, cudaStream_t s) {
+  k_sum_partials<<<1, 256, 0, s>>>(partial, n, out);
+}
+
+// ---------------------------------------------------------------------------
+// Generic n-mode product
+// ---------------------------------------------------------------------------
+
+// K large, L == 1: one warp per output column q, lanes split k, JT accumulators.
+template <typename Tin, typename Tm, typename Tacc, int JT>
+__global__ void k_mp_reduce_col(const Tin* __restrict__ in, Tacc* __restrict__ out, const Tm* __restrict__ M, int K,
+                                int J, int64_t Q, int64_t sMj, int64_t sMk) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t q = warp; q < Q; q += nwarps) {
+    const Tin* col = in + q * K;
+    for (int j0 = 0; j0 < J; j0 += JT) {
+      Tacc acc[JT];
+#pragma unroll
+      for (int t = 0; t < JT; ++t) acc[t] = Tacc(0);
+      for (int k = lane; k < K; k += 32) {
+        Tacc v = (Tacc)col[k];
+#pragma unroll
+        for (int t = 0; t < JT; ++t)
+          if (j0 + t < J) acc[t] += (Tacc)M[(j0 + t) * sMj + k * sMk] * v;
+      }
+#pragma unroll
+      for (int t = 0; t < JT; ++t) {
+        Tacc v = warp_sum(acc[t]);
+        if (lane == 0 && j0 + t < J) out[(j0 + t) + (int64_t)J * q] = v;
+      }
+    }
+  }
+}
+
+// K large, L > 1: one thread per (l, q), l fastest (coalesced over l).
+template <typename Tin, typename Tm, typename Tacc, int JT>
+__global__ void k_mp_reduce_gen(const Tin* __restrict__ in, Tacc* __restrict__ out, const Tm* __restrict__ M,
+                                int64_t L, int K, int J, int64_t Q, int64_t sMj, int64_t sMk) {
+  const int64_t total = L * Q;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = e % L, q = e / L;
+    const Tin* base = in + l + L * K * q;
+    for (int j0 = 0; j0 < J; j0 += JT) {
+      Tacc acc[JT];
+#pragma unroll
+      for (int t = 0; t < JT; ++t) acc[t] = Tacc(0);
+      for (int k = 0; k < K; ++k) {
+        Tacc v = (Tacc)base[(int64_t)k * L];
+#pragma unroll
+        for (int t = 0; t < JT; ++t)
+          if (j0 + t < J) acc[t] += (Tacc)M[(j0 + t) * sMj + k * sMk] * v;
+      }
+#pragma unroll
+      for (int t = 0; t < JT; ++t)
+        if (j0 + t < J) out[l + L * ((j0 + t) + (int64_t)J * q)] = acc[t];
+    }
+  }
+}
+
+// K small: one thread per output element (l, j, q), l fastest.
+template <typename Tin, typename Tm, typename Tacc>
+__global__ void k_mp_expand(const Tin* __restrict__ in, Tacc* __restrict__ out, const Tm* __restrict__ M, int64_t L,
+                            int K, int J, int64_t Q, int64_t sMj, int64_t sMk) {
+  const int64_t total = L * J * Q;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = e % L;
+    const int64_t jq = e / L;
+    const int j = (int)(jq % J);
+    const int64_t q = jq / J;
+    const Tin* base = in + l + L * K * q;
+    Tacc acc = Tacc(0);
+    for (int k = 0; k < K; ++k) acc += (Tacc)M[j * sMj + k * sMk] * (Tacc)base[(int64_t)k * L];
+    out[e] = acc;
+  }
+}
+
+template <typename Tin, typename Tm, typename Tacc>
+void launch_modeprod(const Tin* in, Tacc* out, const Tm* M, int64_t L, int K, int J, int64_t Q, int64_t sMj,
+                     int64_t sMk, cudaStream_t s) {
+  if (L <= 0 || K <= 0 || J <= 0 || Q <= 0) return;
+  if (K <= 32 && J >= K) {
+    int64_t total = L * J * Q;
+    int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
+    k_mp_expand<Tin, Tm, Tacc><<<blocks, 256, 0, s>>>(in, out, M, L, K, J, Q, sMj, sMk);
+  } else if (L == 1) {
+    int64_t warps = Q;
+    int blocks = (int)std::min<int64_t>((warps * 32 + 255) / 256, 152 * 32);
+    if (J <= 8)
+      k_mp_reduce_col<Tin, Tm, Tacc, 8><<<blocks, 256, 0, s>>>(in, out, M, K, J, Q, sMj, sMk);
+    else if (J <= 16)
+      k_mp_reduce_col<Tin, Tm, Tacc, 16><<<blocks, 256, 0, s>>>(in, out, M, K, J, Q, sMj, sMk);
+    else
+      k_mp_reduce_col<Tin, Tm, Tacc, 32><<<blocks, 256, 0, s>>>(in, out, M, K, J, Q, sMj, sMk);
+  } else {
+    int64_t total = L * Q;
+    int blocks = (int)std::min<int64_t>((total + 127) / 128, 152 * 32);
+    if (J <= 8)
+      k_mp_reduce_gen<Tin, Tm, Tacc, 8><<<blocks, 128, 0, s>>>(in, out, M, L, K, J, Q, sMj, sMk);
+    else if (J <= 16)
+      k_mp_reduce_gen<Tin, Tm, Tacc, 16><<<blocks, 128, 0, s>>>(in, out, M, L, K, J, Q, sMj, sMk);
+    else
+      k_mp_reduce_gen<Tin, Tm, Tacc, 32><<<blocks, 128, 0, s>>>(in, out, M, L, K, J, Q, sMj, sMk);
+  }
+}
+
+#define INST_MP(Tin, Tm, Tacc)                                                                                   \
+  template void launch_modeprod<Tin, Tm, Tacc>(const Tin*, Tacc*, const Tm*, int64_t, int, int, int64_t, int64_t, \
+                                               int64_t, cudaStream_t);
+INST_MP(float, float, float)
+INST_MP(double, double, double)
+INST_MP(double, float, float)
+INST_MP(float, double, double)
+INST_MP(double, double, float)
+
+}  // namespace tdb

@@ -1,0 +1,93 @@
+// kernels.h - host-side launchers of libtdb's kernels (internal C++ interface).
+#pragma once
+
+#include <algorithm>
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace tdb {
+
+// Bump allocator over the caller's workspace (256-byte aligned pieces); with a
+// null base it only measures.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base((char*)b) {}
+  template <typename T>
+  T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+
+struct WeightView {
+  int p;
+  int64_t N[kMaxModes];
+  const double* w[kMaxModes];
+};
+
+struct RowArgs {
+  ModeDesc d;
+  const void* Y[kMaxModes];      // projection tensors (Tc)
+  const void* Tc;                // core in the compute type
+  const double* U[kMaxModes];
+  const double* w[kMaxModes];
+  const double* Ginv;            // p x LD x LD
+  const double* P;               // p x LD x LD
+  const double* Rinv;            // p x LD x LD
+  double* X[kMaxModes];
+  double* Up[kMaxModes];
+  double* Uout[kMaxModes];
+  void* A[kMaxModes];            // weighted bases (Ta)
+  double* part;                  // p x ntile x LD x LD
+  int ntile;                     // tiles per mode in `part`
+};
+
+struct GramView {
+  int p, n;
+  int64_t N[kMaxModes];
+  const double* w[kMaxModes];
+  int64_t L, Q, Nn;
+};
+
+// k_basic.cu
+template <typename T> void launch_diff(const T* a, const T* b, T* out, int64_t n, cudaStream_t s);
+template <typename T> void launch_weighted_bases(const double* U, const double* w, T* A, int64_t N, int r, cudaStream_t s);
+template <typename Ts, typename Td> void launch_cast(const Ts* a, Td* b, int64_t n, cudaStream_t s);
+template <typename Tb> void launch_add(const double* a, const Tb* b, double* out, int64_t n, cudaStream_t s);
+template <typename T>
+void launch_wnorm2(const T* x, const T* y, const WeightView& wv, double* partial, int nblocks, double* out,
+                   unsigned* flags, cudaStream_t s);
+void launch_sum_partials(const double* partial, int n, double* out, cudaStream_t s);
+template <typename Tin, typename Tm, typename Tacc>
+void launch_modeprod(const Tin* in, Tacc* out, const Tm* M, int64_t L, int K, int J, int64_t Q, int64_t sMj,
+                     int64_t sMk, cudaStream_t s);
+
+// k_small.cu
+void launch_gram(const ModeDesc& d, const double* T, double* Gpart, int nsplit, double* G, double* Ginv,
+                 double* sig2, float* Vprev, int warm, unsigned* flags, cudaStream_t s);
+template <typename Tc>
+void launch_update_rows(RowArgs& a, double* P, double* R, double* Rinv, unsigned* flags, bool reorth, cudaStream_t s);
+template <typename Tc>
+void launch_orthonormalize(RowArgs& a, double* R, double* Rinv, unsigned* flags, cudaStream_t s);
+
+// k_hosvd.cu
+template <typename Tv>
+void launch_wgram(const Tv* V, const GramView& g, double* part, size_t part_cap, double* C64, void* Cc, int cc_float,
+                  cudaStream_t s);
+template <typename T>
+tdb_status eig_leading(const T* Cc, const double* C64, int n, int k, T* A_ws, T* V_ws, T* rin_ws, double* red_ws,
+                       unsigned* bar, unsigned* flags, int* sweeps, double* ev, double* Q, double* trace,
+                       double* scratch, cudaStream_t s);
+template <typename T>
+tdb_status eig_leading_small(const T* Cc, const double* C64, int n, int k, T* A_ws, T* V_ws, unsigned* flags,
+                             double* ev, double* Q, double* trace, double* scratch, cudaStream_t s);
+void launch_scale_basis(const double* Q, const double* w, int64_t n, int r, double* U, cudaStream_t s);
+
+}  // namespace tdb

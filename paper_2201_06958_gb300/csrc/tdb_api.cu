@@ -1,0 +1,1118 @@
+// tdb_api.cu - the C ABI of libtdb: context, workspace layout, the step driver,
+// HOSVD (re)initialisation and the add/remove-mode rule of Sec. 2.5.
+//
+// Step (Secs. 2.2, 2.3): dV = V_{k+1} - V_k; dS and Y_n by the projection of
+// Eqs. 2.15/2.16; X_n = Y_(n) T_(n)^T (T_(n) T_(n)^T)^{-1}; dU_n = (I - U U^T W) X_n;
+// T += dS, U_n += dU_n (explicit Euler, dt cancels); weighted Cholesky-QR with core
+// compensation; error (Eq. 2.20) when scheduled; rank control (Sec. 2.5).
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.h"
+#include "tc_project.h"
+
+namespace tdb {
+
+static thread_local std::string g_init_error;
+
+
+enum Action { ACT_NONE = 0, ACT_REINIT = 1, ACT_INCREASE = 2, ACT_DECREASE = 3, ACT_REVERT = 4, ACT_CAP = 5 };
+
+struct Readback {
+  double err2;
+  double dv2;
+  double ds2;
+  double sig2[kMaxModes][kMaxRank];
+  unsigned flags;
+  unsigned pad;
+};
+
+}  // namespace tdb
+
+using namespace tdb;
+
+struct tdb_ctx {
+  tdb_config cfg;
+  int p = 0;
+  int64_t N[kMaxModes] = {0};
+  int64_t S = 0;
+  int r[kMaxModes] = {0};
+  int cap[kMaxModes] = {0};
+  int kcap[kMaxModes] = {0};      // eigenpairs kept from each HOSVD
+  int prec = 0;
+  bool f64 = false;
+  size_t esz = 4;                 // snapshot element size
+  cudaStream_t stream = nullptr;
+  std::string err;
+
+  // device buffers
+  double* w[kMaxModes];
+  double* U[kMaxModes];
+  double* Up[kMaxModes];
+  double* X[kMaxModes];
+  void* A[kMaxModes];
+  void* Uc[kMaxModes];
+  double* Ubak[kMaxModes];
+  double* T;
+  double* T2;
+  double* Tbak;
+  void* Tcore;                    // compute-type core (alias of T in FP64 mode)
+  void* dS;
+  void* Y[kMaxModes];
+  void* dV;
+  void* ping;
+  void* pong;
+  void* rec;
+  size_t tree_elems = 0;
+  double* G;
+  double* Ginv;
+  double* P;
+  double* R;
+  double* Rinv;
+  double* Gpart;
+  int gsplit = 1;
+  double* rowpart;
+  int ntile = 1;
+  double* sig2;
+  float* Vprev;
+  float* Vprev_bak;
+  double* npart;
+  int nblk = 256;
+  Readback* rb_dev;
+  unsigned* flags;
+  // HOSVD scratch
+  double* C64;
+  void* Cc;
+  void* jA;
+  void* jV;
+  void* jrin;
+  double* jred;
+  unsigned* jbar;
+  int* jsweeps;
+  double* wpart;
+  size_t wpart_cap = 0;
+  double* ev[kMaxModes];
+  double* Qeig[kMaxModes];
+  double* trace;
+  double* eigscratch;
+  // BF16 tensor-core projection
+  TcPlan tc;
+  bool use_tc = false;
+
+  // host state
+  const void* V_prev = nullptr;
+  bool ready = false;
+  bool warm = false;
+  int64_t step = 0, reinits = 0, exact_evals = 0;
+  std::vector<double> history;
+  Readback rb;
+  std::vector<double> h_ev[kMaxModes];
+  double h_trace[kMaxModes];
+};
+
+namespace {
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      ctx->err = std::string(#call) + ": " + cudaGetErrorString(e_);                    \
+      return TDB_ERR_CUDA;                                                              \
+    }                                                                                   \
+  } while (0)
+
+#define CHECK_LAUNCH()                                                                  \
+  do {                                                                                  \
+    cudaError_t e_ = cudaGetLastError();                                                \
+    if (e_ != cudaSuccess) {                                                            \
+      ctx->err = std::string("kernel launch: ") + cudaGetErrorString(e_);              \
+      return TDB_ERR_CUDA;                                                              \
+    }                                                                                   \
+  } while (0)
+
+#define TRY(x)                            \
+  do {                                    \
+    tdb_status s_ = (x);                  \
+    if (s_ != TDB_OK) return s_;          \
+  } while (0)
+
+int64_t prod_except(const int64_t* a, int p, int n) {
+  int64_t v = 1;
+  for (int m = 0; m < p; ++m)
+    if (m != n) v *= a[m];
+  return v;
+}
+
+std::vector<int> clamp_product_bound(std::vector<int> r) {
+  bool changed = true;
+  int p = (int)r.size();
+  while (changed) {
+    changed = false;
+    for (int n = 0; n < p; ++n) {
+      int64_t other = 1;
+      for (int m = 0; m < p; ++m)
+        if (m != n) other *= r[m];
+      if (r[n] > other) {
+        r[n] = (int)other;
+        changed = true;
+      }
+    }
+  }
+  return r;
+}
+
+// Smallest r with sum_{i<=r} max(lambda_i, 0) >= gamma/100 * total (Eq. 2.21, first form).
+int rank_from_spectrum(const std::vector<double>& lam, double total, double gamma_th) {
+  if (!(total > 0.0)) return 1;
+  double target = gamma_th / 100.0 * total, acc = 0.0;
+  for (size_t i = 0; i < lam.size(); ++i) {
+    acc += std::max(lam[i], 0.0);
+    if (acc >= target) return (int)i + 1;
+  }
+  return (int)lam.size() + 1;
+}
+
+// Smallest r with sum_{i<=r} sigma_i^2 >= gamma/100 (sum sigma^2 + eps^2) (Eq. 2.21, second form).
+int rank_from_core(const double* s2, int r, double eps, double gamma_th) {
+  double denom = eps * eps;
+  for (int i = 0; i < r; ++i) denom += std::max(s2[i], 0.0);
+  double target = gamma_th / 100.0 * denom, acc = 0.0;
+  for (int i = 0; i < r; ++i) {
+    acc += std::max(s2[i], 0.0);
+    if (acc >= target) return i + 1;
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// Workspace layout
+// ---------------------------------------------------------------------------
+void carve(tdb_ctx* c, Carver& cv) {
+  const int p = c->p;
+  const size_t tsz = c->f64 ? 8 : 4;
+  int64_t Rprod = 1;
+  for (int n = 0; n < p; ++n) Rprod *= c->cap[n];
+  int64_t Nmax = 0;
+  for (int n = 0; n < p; ++n) Nmax = std::max<int64_t>(Nmax, c->N[n]);
+  for (int n = 0; n < p; ++n) {
+    int64_t nr = c->N[n] * c->cap[n];
+    c->w[n] = cv.take<double>(c->N[n]);
+    c->U[n] = cv.take<double>(nr);
+    c->Up[n] = cv.take<double>(nr);
+    c->X[n] = cv.take<double>(nr);
+    c->Ubak[n] = cv.take<double>(nr);
+    c->A[n] = cv.take<char>(nr * tsz);
+    c->Uc[n] = cv.take<char>(nr * tsz);
+    int64_t ysz = c->N[n] * (Rprod / c->cap[n]);
+    c->Y[n] = cv.take<char>(ysz * tsz);
+  }
+  c->T = cv.take<double>(Rprod);
+  c->T2 = cv.take<double>(Rprod);
+  c->Tbak = cv.take<double>(Rprod);
+  c->Tcore = c->f64 ? (void*)c->T : (void*)cv.take<char>(Rprod * tsz);
+  c->dS = cv.take<char>(Rprod * tsz);
+  // tree scratch: the largest intermediate of the projection or reconstruction chains
+  int64_t tree = 0;
+  for (int n = 0; n < p; ++n) tree = std::max<int64_t>(tree, c->S / c->N[n] * c->cap[n]);
+  tree = std::max<int64_t>(tree, Rprod);
+  c->tree_elems = tree;
+  c->ping = cv.take<char>(tree * tsz);
+  c->pong = cv.take<char>(tree * tsz);
+  c->dV = cv.take<char>(c->S * tsz);
+  c->rec = cv.take<char>(c->S * tsz);
+  c->G = cv.take<double>(p * kMaxRank * kMaxRank);
+  c->Ginv = cv.take<double>(p * kMaxRank * kMaxRank);
+  c->P = cv.take<double>(p * kMaxRank * kMaxRank);
+  c->R = cv.take<double>(p * kMaxRank * kMaxRank);
+  c->Rinv = cv.take<double>(p * kMaxRank * kMaxRank);
+  c->gsplit = 64;
+  c->Gpart = cv.take<double>((size_t)p * c->gsplit * kMaxRank * kMaxRank);
+  c->ntile = (int)((Nmax + 31) / 32);
+  c->rowpart = cv.take<double>((size_t)p * c->ntile * kMaxRank * kMaxRank);
+  c->sig2 = cv.take<double>(p * kMaxRank);
+  c->Vprev = cv.take<float>(p * kMaxRank * kMaxRank);
+  c->Vprev_bak = cv.take<float>(p * kMaxRank * kMaxRank);
+  c->nblk = 512;
+  c->npart = cv.take<double>(c->nblk);
+  c->rb_dev = cv.take<Readback>(1);
+  c->flags = &c->rb_dev->flags;
+  // HOSVD scratch
+  int64_t nn = (Nmax + 1) & ~1;
+  c->C64 = cv.take<double>(Nmax * Nmax);
+  c->Cc = cv.take<char>(Nmax * Nmax * tsz);
+  c->jA = cv.take<char>(nn * nn * tsz);
+  c->jV = cv.take<char>(nn * nn * tsz);
+  c->jrin = cv.take<char>(3 * nn * tsz);
+  c->jred = cv.take<double>(2 * 2048);
+  c->jbar = cv.take<unsigned>(2);
+  c->jsweeps = cv.take<int>(1);
+  int ntile = (int)((Nmax + 31) / 32);
+  c->wpart_cap = (size_t)(ntile * (ntile + 1) / 2) * 8 * 1024;
+  c->wpart = cv.take<double>(c->wpart_cap);
+  for (int n = 0; n < p; ++n) {
+    c->kcap[n] = (int)std::min<int64_t>(c->N[n], c->cap[n] + 2);
+    c->ev[n] = cv.take<double>(c->kcap[n]);
+    c->Qeig[n] = cv.take<double>(c->N[n] * c->kcap[n]);
+  }
+  c->trace = cv.take<double>(p);
+  int kmax = 0;
+  for (int n = 0; n < p; ++n) kmax = std::max(kmax, c->kcap[n]);
+  c->eigscratch = cv.take<double>(64 + Nmax * (kmax + 2));
+  if (c->prec == TDB_BF16_TTM) tc_carve(c->tc, cv, c->p, c->N, c->cap);
+}
+
+tdb_status validate(const tdb_config* cfg, std::string& err) {
+  if (!cfg) { err = "null config"; return TDB_ERR_INVALID_ARG; }
+  if (cfg->ndim < 2 || cfg->ndim > kMaxModes) { err = "ndim must be 2..4"; return TDB_ERR_SHAPE; }
+  for (int n = 0; n < cfg->ndim; ++n)
+    if (cfg->dims[n] < 1 || cfg->dims[n] > 1024) { err = "mode sizes must be 1..1024"; return TDB_ERR_SHAPE; }
+  if (cfg->precision < TDB_FP64 || cfg->precision > TDB_BF16_TTM) { err = "bad precision"; return TDB_ERR_INVALID_ARG; }
+  if (cfg->error_mode < TDB_ERRMODE_EXACT || cfg->error_mode > TDB_ERRMODE_NONE) {
+    err = "bad error_mode";
+    return TDB_ERR_INVALID_ARG;
+  }
+  if (cfg->eps_th > 0 && !(cfg->gamma_th > 0 && cfg->gamma_th <= 100)) { err = "gamma_th must be in (0, 100]"; return TDB_ERR_INVALID_ARG; }
+  for (int n = 0; n < cfg->ndim; ++n) {
+    if (cfg->rank[n] < 0 || cfg->rank[n] > kMaxRank) { err = "rank outside 0..32"; return TDB_ERR_RANK; }
+    if (cfg->rank_max[n] < 0 || cfg->rank_max[n] > kMaxRank) { err = "rank_max outside 0..32"; return TDB_ERR_RANK; }
+  }
+  return TDB_OK;
+}
+
+void setup_dims(tdb_ctx* c, const tdb_config* cfg) {
+  c->cfg = *cfg;
+  c->p = cfg->ndim;
+  c->S = 1;
+  for (int n = 0; n < c->p; ++n) {
+    c->N[n] = cfg->dims[n];
+    c->S *= c->N[n];
+  }
+  if (c->cfg.slope_window <= 0) c->cfg.slope_window = 10;
+  if (c->cfg.error_every <= 0) c->cfg.error_every = 1;
+  c->prec = cfg->precision;
+  c->f64 = (cfg->precision == TDB_FP64);
+  c->esz = c->f64 ? 8 : 4;
+  for (int n = 0; n < c->p; ++n) {
+    int64_t rm = cfg->rank_max[n] > 0 ? cfg->rank_max[n] : kMaxRank;
+    int64_t cp = std::min<int64_t>(std::min<int64_t>(rm, c->N[n]), prod_except(c->N, c->p, n));
+    if (cfg->rank[n] > cp) cp = std::min<int64_t>(cfg->rank[n], std::min<int64_t>(c->N[n], kMaxRank));
+    c->cap[n] = (int)std::min<int64_t>(cp, kMaxRank);
+  }
+}
+
+ModeDesc mode_desc(const tdb_ctx* c) {
+  ModeDesc d;
+  d.p = c->p;
+  for (int n = 0; n < kMaxModes; ++n) {
+    d.N[n] = n < c->p ? c->N[n] : 1;
+    d.r[n] = n < c->p ? c->r[n] : 1;
+  }
+  return d;
+}
+
+WeightView weight_view(const tdb_ctx* c) {
+  WeightView wv;
+  wv.p = c->p;
+  for (int n = 0; n < kMaxModes; ++n) {
+    wv.N[n] = n < c->p ? c->N[n] : 1;
+    wv.w[n] = n < c->p ? c->w[n] : nullptr;
+  }
+  return wv;
+}
+
+// ---------------------------------------------------------------------------
+// Projection (Eqs. 2.15, 2.16) by mode products on the unfused path
+// ---------------------------------------------------------------------------
+template <typename Tc>
+tdb_status project_tree(tdb_ctx* ctx, const Tc* dV) {
+  const int p = ctx->p;
+  cudaStream_t s = ctx->stream;
+  int64_t dims[kMaxModes];
+  auto mp = [&](const Tc* in, Tc* out, int n, int64_t* cur) {
+    int64_t L = 1, Q = 1;
+    for (int m = 0; m < n; ++m) L *= cur[m];
+    for (int m = n + 1; m < p; ++m) Q *= cur[m];
+    launch_modeprod<Tc, Tc, Tc>(in, out, (const Tc*)ctx->A[n], L, (int)cur[n], ctx->r[n], Q, ctx->N[n], 1, s);
+    cur[n] = ctx->r[n];
+  };
+  Tc* ping = (Tc*)ctx->ping;
+  Tc* pong = (Tc*)ctx->pong;
+  // Z1 = dV x_1 A_1^T, then each Y_n (n >= 2) contracts the remaining modes but n
+  for (int m = 0; m < p; ++m) dims[m] = ctx->N[m];
+  mp(dV, ping, 0, dims);
+  int64_t z1dims[kMaxModes];
+  for (int m = 0; m < p; ++m) z1dims[m] = dims[m];
+  for (int n = 1; n < p; ++n) {
+    int64_t cur[kMaxModes];
+    for (int m = 0; m < p; ++m) cur[m] = z1dims[m];
+    std::vector<int> todo;
+    for (int m = 1; m < p; ++m)
+      if (m != n) todo.push_back(m);
+    const Tc* src = ping;
+    for (size_t t = 0; t < todo.size(); ++t) {
+      Tc* dst = (t + 1 == todo.size()) ? (Tc*)ctx->Y[n] : ((t & 1) ? ping : pong);
+      if (t > 0 && dst == src) dst = (dst == ping) ? pong : ping;
+      if (t == 0 && todo.size() > 1) dst = pong;
+      mp(src, dst, todo[t], cur);
+      src = dst;
+    }
+    if (todo.empty()) cudaMemcpyAsync(ctx->Y[n], ping, sizeof(Tc) * ctx->S / ctx->N[0] * ctx->r[0], cudaMemcpyDeviceToDevice, s);
+  }
+  // Y_1 = dV x_2 A_2^T ... x_p A_p^T (ping is free again)
+  {
+    int64_t cur[kMaxModes];
+    for (int m = 0; m < p; ++m) cur[m] = ctx->N[m];
+    const Tc* src = dV;
+    for (int m = 1; m < p; ++m) {
+      Tc* dst = (m == p - 1) ? (Tc*)ctx->Y[0] : ((m & 1) ? ping : pong);
+      mp(src, dst, m, cur);
+      src = dst;
+    }
+  }
+  // dS = Y_p x_p A_p^T
+  {
+    int64_t cur[kMaxModes];
+    for (int m = 0; m < p; ++m) cur[m] = ctx->r[m];
+    cur[p - 1] = ctx->N[p - 1];
+    mp((const Tc*)ctx->Y[p - 1], (Tc*)ctx->dS, p - 1, cur);
+  }
+  CHECK_LAUNCH();
+  return TDB_OK;
+}
+
+// V^TDB = T x_1 U_1 ... x_p U_p into out (compute type)
+template <typename Tc>
+tdb_status reconstruct_into(tdb_ctx* ctx, Tc* out) {
+  const int p = ctx->p;
+  cudaStream_t s = ctx->stream;
+  int64_t cur[kMaxModes];
+  for (int m = 0; m < p; ++m) cur[m] = ctx->r[m];
+  const Tc* src = (const Tc*)ctx->Tcore;
+  Tc* bufs[2] = {(Tc*)ctx->ping, (Tc*)ctx->pong};
+  for (int n = 0; n < p; ++n) {
+    Tc* dst = (n == p - 1) ? out : bufs[n & 1];
+    int64_t L = 1, Q = 1;
+    for (int m = 0; m < n; ++m) L *= cur[m];
+    for (int m = n + 1; m < p; ++m) Q *= cur[m];
+    launch_modeprod<Tc, Tc, Tc>(src, dst, (const Tc*)ctx->Uc[n], L, ctx->r[n], (int)ctx->N[n], Q, 1, ctx->N[n], s);
+    cur[n] = ctx->N[n];
+    src = dst;
+  }
+  CHECK_LAUNCH();
+  return TDB_OK;
+}
+
+template <typename Tc>
+tdb_status exact_error2(tdb_ctx* ctx, const Tc* V) {
+  TRY(reconstruct_into<Tc>(ctx, (Tc*)ctx->rec));
+  launch_wnorm2<Tc>(V, (const Tc*)ctx->rec, weight_view(ctx), ctx->npart, ctx->nblk, &ctx->rb_dev->err2, ctx->flags,
+                    ctx->stream);
+  CHECK_LAUNCH();
+  return TDB_OK;
+}
+
+// Refresh everything derived from (T, U): compute-type copies, weighted bases,
+// G_n, its inverse and sigma^(n) (Eq. 2.18).
+template <typename Tc>
+tdb_status refresh_derived(tdb_ctx* ctx, bool bases_too) {
+  cudaStream_t s = ctx->stream;
+  int64_t Rprod = 1;
+  for (int n = 0; n < ctx->p; ++n) Rprod *= ctx->r[n];
+  if (!ctx->f64) launch_cast<double, float>(ctx->T, (float*)ctx->Tcore, Rprod, s);
+  for (int n = 0; n < ctx->p; ++n) {
+    if (bases_too) launch_weighted_bases<Tc>(ctx->U[n], ctx->w[n], (Tc*)ctx->A[n], ctx->N[n], ctx->r[n], s);
+    if (ctx->f64)
+      cudaMemcpyAsync(ctx->Uc[n], ctx->U[n], sizeof(double) * ctx->N[n] * ctx->r[n], cudaMemcpyDeviceToDevice, s);
+    else
+      launch_cast<double, float>(ctx->U[n], (float*)ctx->Uc[n], ctx->N[n] * ctx->r[n], s);
+  }
+  ModeDesc d = mode_desc(ctx);
+  int64_t maxcol = 1;
+  for (int n = 0; n < ctx->p; ++n) maxcol = std::max<int64_t>(maxcol, Rprod / ctx->r[n]);
+  int nsplit = (int)std::min<int64_t>(ctx->gsplit, std::max<int64_t>(1, maxcol / 8));
+  launch_gram(d, ctx->T, ctx->Gpart, nsplit, ctx->G, ctx->Ginv, ctx->sig2, ctx->Vprev, ctx->warm ? 1 : 0, ctx->flags, s);
+  ctx->warm = true;
+  CHECK_LAUNCH();
+  return TDB_OK;
+}
+
+tdb_status readback(tdb_ctx* ctx) {
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemcpyAsync(ctx->rb_dev->sig2, ctx->sig2, sizeof(double) * ctx->p * kMaxRank, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(&ctx->rb, ctx->rb_dev, sizeof(Readback), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (ctx->rb.flags & kFlagTimeout) { ctx->err = "device wait timed out"; return TDB_ERR_TIMEOUT; }
+  return TDB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// HOSVD: per-mode spectrum (leading eigenpairs and trace), then the truncated state
+// ---------------------------------------------------------------------------
+template <typename Tc>
+tdb_status hosvd_spectrum(tdb_ctx* ctx, const Tc* V) {
+  cudaStream_t s = ctx->stream;
+  for (int n = 0; n < ctx->p; ++n) {
+    GramView g;
+    g.p = ctx->p;
+    g.n = n;
+    for (int m = 0; m < kMaxModes; ++m) {
+      g.N[m] = m < ctx->p ? ctx->N[m] : 1;
+      g.w[m] = m < ctx->p ? ctx->w[m] : nullptr;
+    }
+    g.Nn = ctx->N[n];
+    g.L = 1;
+    for (int m = 0; m < n; ++m) g.L *= ctx->N[m];
+    g.Q = 1;
+    for (int m = n + 1; m < ctx->p; ++m) g.Q *= ctx->N[m];
+    launch_wgram<Tc>(V, g, ctx->wpart, ctx->wpart_cap, ctx->C64, ctx->Cc, ctx->f64 ? 0 : 1, s);
+    CHECK_LAUNCH();
+    int Nn = (int)ctx->N[n];
+    tdb_status st;
+    if (Nn <= 96)
+      st = eig_leading_small<Tc>((const Tc*)ctx->Cc, ctx->C64, Nn, ctx->kcap[n], (Tc*)ctx->jA, (Tc*)ctx->jV,
+                                 ctx->flags, ctx->ev[n], ctx->Qeig[n], ctx->trace + n, ctx->eigscratch, s);
+    else
+      st = eig_leading<Tc>((const Tc*)ctx->Cc, ctx->C64, Nn, ctx->kcap[n], (Tc*)ctx->jA, (Tc*)ctx->jV, (Tc*)ctx->jrin,
+                           ctx->jred, ctx->jbar, ctx->flags, ctx->jsweeps, ctx->ev[n], ctx->Qeig[n], ctx->trace + n,
+                           ctx->eigscratch, s);
+    if (st != TDB_OK) { ctx->err = "eigensolver launch failed"; return st; }
+    CHECK_LAUNCH();
+  }
+  // spectrum to host (needed by the rank rule)
+  for (int n = 0; n < ctx->p; ++n) {
+    ctx->h_ev[n].resize(ctx->kcap[n]);
+    CK(cudaMemcpyAsync(ctx->h_ev[n].data(), ctx->ev[n], sizeof(double) * ctx->kcap[n], cudaMemcpyDeviceToHost, s));
+  }
+  CK(cudaMemcpyAsync(ctx->h_trace, ctx->trace, sizeof(double) * ctx->p, cudaMemcpyDeviceToHost, s));
+  unsigned fl = 0;
+  CK(cudaMemcpyAsync(&fl, ctx->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (fl & kFlagTimeout) { ctx->err = "eigensolver grid barrier timed out"; return TDB_ERR_TIMEOUT; }
+  return TDB_OK;
+}
+
+template <typename Tc>
+tdb_status hosvd_state(tdb_ctx* ctx, const Tc* V, const int* ranks) {
+  cudaStream_t s = ctx->stream;
+  for (int n = 0; n < ctx->p; ++n) ctx->r[n] = ranks[n];
+  // U_n = W^{-1/2} Q_n[:, :r_n], then weighted Cholesky-QR so that U^T W U = I in double
+  for (int n = 0; n < ctx->p; ++n) launch_scale_basis(ctx->Qeig[n], ctx->w[n], ctx->N[n], ctx->r[n], ctx->Up[n], s);
+  RowArgs a;
+  memset(&a, 0, sizeof(a));
+  a.d = mode_desc(ctx);
+  for (int n = 0; n < ctx->p; ++n) {
+    a.U[n] = ctx->U[n];
+    a.w[n] = ctx->w[n];
+    a.Up[n] = ctx->Up[n];
+    a.Uout[n] = ctx->U[n];
+    a.A[n] = ctx->A[n];
+  }
+  a.part = ctx->rowpart;
+  a.ntile = ctx->ntile;
+  launch_orthonormalize<Tc>(a, ctx->R, ctx->Rinv, ctx->flags, s);
+  CHECK_LAUNCH();
+  // T = V x_1 A_1^T ... x_p A_p^T  (Eq. 2.15 projection applied to V)
+  int64_t cur[kMaxModes];
+  for (int m = 0; m < ctx->p; ++m) cur[m] = ctx->N[m];
+  const Tc* src = V;
+  Tc* bufs[2] = {(Tc*)ctx->ping, (Tc*)ctx->pong};
+  for (int n = 0; n < ctx->p; ++n) {
+    Tc* dst = bufs[n & 1];
+    int64_t L = 1, Q = 1;
+    for (int m = 0; m < n; ++m) L *= cur[m];
+    for (int m = n + 1; m < ctx->p; ++m) Q *= cur[m];
+    launch_modeprod<Tc, Tc, Tc>(src, dst, (const Tc*)ctx->A[n], L, (int)cur[n], ctx->r[n], Q, ctx->N[n], 1, s);
+    cur[n] = ctx->r[n];
+    src = dst;
+  }
+  int64_t Rprod = 1;
+  for (int n = 0; n < ctx->p; ++n) Rprod *= ctx->r[n];
+  if (ctx->f64)
+    CK(cudaMemcpyAsync(ctx->T, src, sizeof(double) * Rprod, cudaMemcpyDeviceToDevice, s));
+  else
+    launch_cast<float, double>((const float*)src, ctx->T, Rprod, s);
+  CHECK_LAUNCH();
+  ctx->warm = false;
+  return refresh_derived<Tc>(ctx, false);
+}
+
+// Copy / restore the state for the revert guard of the rank-reduction rule.
+tdb_status backup_state(tdb_ctx* ctx, int* rsave) {
+  cudaStream_t s = ctx->stream;
+  int64_t Rprod = 1;
+  for (int n = 0; n < ctx->p; ++n) { Rprod *= ctx->r[n]; rsave[n] = ctx->r[n]; }
+  CK(cudaMemcpyAsync(ctx->Tbak, ctx->T, sizeof(double) * Rprod, cudaMemcpyDeviceToDevice, s));
+  for (int n = 0; n < ctx->p; ++n)
+    CK(cudaMemcpyAsync(ctx->Ubak[n], ctx->U[n], sizeof(double) * ctx->N[n] * ctx->r[n], cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(ctx->Vprev_bak, ctx->Vprev, sizeof(float) * ctx->p * kMaxRank * kMaxRank, cudaMemcpyDeviceToDevice, s));
+  return TDB_OK;
+}
+
+template <typename Tc>
+tdb_status restore_state(tdb_ctx* ctx, const int* rsave) {
+  cudaStream_t s = ctx->stream;
+  int64_t Rprod = 1;
+  for (int n = 0; n < ctx->p; ++n) { ctx->r[n] = rsave[n]; Rprod *= ctx->r[n]; }
+  CK(cudaMemcpyAsync(ctx->T, ctx->Tbak, sizeof(double) * Rprod, cudaMemcpyDeviceToDevice, s));
+  for (int n = 0; n < ctx->p; ++n)
+    CK(cudaMemcpyAsync(ctx->U[n], ctx->Ubak[n], sizeof(double) * ctx->N[n] * ctx->r[n], cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(ctx->Vprev, ctx->Vprev_bak, sizeof(float) * ctx->p * kMaxRank * kMaxRank, cudaMemcpyDeviceToDevice, s));
+  ctx->warm = true;
+  return refresh_derived<Tc>(ctx, true);
+}
+
+template <typename Tc>
+tdb_status error_now(tdb_ctx* ctx, const Tc* V, double* eps) {
+  TRY(exact_error2<Tc>(ctx, V));
+  TRY(readback(ctx));
+  *eps = std::sqrt(std::max(ctx->rb.err2, 0.0));
+  ctx->exact_evals++;
+  return TDB_OK;
+}
+
+// Largest discarded HOSVD energy among modes below their caps (lowest mode on ties),
+// then other modes follow until r_n <= prod_{m != n} r_m holds.
+bool raise_one(tdb_ctx* ctx, const std::vector<int>& r, std::vector<int>& out) {
+  auto disc = [&](int n, int rn) {
+    double tot = ctx->h_trace[n];
+    double kept = 0.0;
+    for (int i = 0; i < rn && i < (int)ctx->h_ev[n].size(); ++i) kept += std::max(ctx->h_ev[n][i], 0.0);
+    return tot > 0 ? 1.0 - kept / tot : 0.0;
+  };
+  out = r;
+  auto pick = [&](int exclude) {
+    int best = -1;
+    double bv = -1.0;
+    for (int n = 0; n < ctx->p; ++n) {
+      if (n == exclude || out[n] >= ctx->cap[n]) continue;
+      double d = disc(n, out[n]);
+      if (d > bv) { bv = d; best = n; }
+    }
+    return best;
+  };
+  int n0 = pick(-1);
+  if (n0 < 0) return false;
+  out[n0] += 1;
+  while (clamp_product_bound(out) != out) {
+    int m = pick(n0);
+    if (m < 0) return false;
+    out[m] += 1;
+  }
+  return true;
+}
+
+// The add/remove-mode rule of Sec. 2.5 (see tdb.h and the design notes for the reading).
+template <typename Tc>
+tdb_status control(tdb_ctx* ctx, const Tc* V, double eps, double* eps_after, int* n_re, int* action) {
+  *eps_after = eps;
+  *n_re = 0;
+  *action = ACT_NONE;
+  const tdb_config& cfg = ctx->cfg;
+  if (cfg.eps_th <= 0) return TDB_OK;
+  const int p = ctx->p, K = cfg.slope_window;
+  std::vector<int> r(ctx->r, ctx->r + p);
+  if (eps > cfg.eps_th) {
+    TRY(hosvd_spectrum<Tc>(ctx, V));
+    TRY(hosvd_state<Tc>(ctx, V, r.data()));
+    double e1;
+    TRY(error_now<Tc>(ctx, V, &e1));
+    int nre = 1, act = ACT_REINIT;
+    while (e1 > cfg.eps_th) {
+      std::vector<int> nw(p);
+      for (int n = 0; n < p; ++n)
+        nw[n] = std::min(ctx->cap[n], std::max(r[n], rank_from_spectrum(ctx->h_ev[n], ctx->h_trace[n], cfg.gamma_th)));
+      nw = clamp_product_bound(nw);
+      if (nw == r) {
+        std::vector<int> up;
+        if (!raise_one(ctx, r, up)) { act = ACT_CAP; break; }
+        nw = up;
+      }
+      r = nw;
+      TRY(hosvd_state<Tc>(ctx, V, r.data()));
+      TRY(error_now<Tc>(ctx, V, &e1));
+      ++nre;
+      act = ACT_INCREASE;
+    }
+    ctx->history.clear();
+    ctx->reinits += nre;
+    *eps_after = e1;
+    *n_re = nre;
+    *action = act;
+    return TDB_OK;
+  }
+  ctx->history.push_back(eps);
+  if ((int)ctx->history.size() > K + 1) ctx->history.erase(ctx->history.begin(), ctx->history.end() - (K + 1));
+  bool excess = false;
+  for (int n = 0; n < p; ++n)
+    if (rank_from_core(ctx->rb.sig2[n], r[n], eps, cfg.gamma_th) < r[n]) excess = true;
+  if ((int)ctx->history.size() == K + 1 && excess) {
+    double slope = (ctx->history.back() - ctx->history.front()) / K;
+    if (slope < 0) {
+      ctx->history.clear();
+      TRY(hosvd_spectrum<Tc>(ctx, V));
+      std::vector<int> nw(p);
+      for (int n = 0; n < p; ++n)
+        nw[n] = std::min(r[n], rank_from_spectrum(ctx->h_ev[n], ctx->h_trace[n], cfg.gamma_th));
+      nw = clamp_product_bound(nw);
+      if (nw == r) return TDB_OK;
+      int rsave[kMaxModes];
+      TRY(backup_state(ctx, rsave));
+      TRY(hosvd_state<Tc>(ctx, V, nw.data()));
+      double e2;
+      TRY(error_now<Tc>(ctx, V, &e2));
+      ctx->reinits += 1;
+      *n_re = 1;
+      if (e2 <= cfg.eps_th) {
+        *eps_after = e2;
+        *action = ACT_DECREASE;
+      } else {
+        TRY(restore_state<Tc>(ctx, rsave));
+        *action = ACT_REVERT;
+      }
+    }
+  }
+  return TDB_OK;
+}
+
+// ---------------------------------------------------------------------------
+// One step
+// ---------------------------------------------------------------------------
+template <typename Tc>
+tdb_status step_impl(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
+  cudaStream_t s = ctx->stream;
+  const Tc* Vp = (const Tc*)ctx->V_prev;
+  const int p = ctx->p;
+  CK(cudaMemsetAsync(ctx->rb_dev, 0, sizeof(Readback), s));
+  // a1 + a2: difference and projection
+  if (ctx->use_tc) {
+    TRY(tc_project(ctx->tc, (const float*)Vn, (const float*)Vp, ctx->p, ctx->N, ctx->r, (const void* const*)ctx->A,
+                   (float*)ctx->dS, (float* const*)ctx->Y, ctx->npart, ctx->nblk, weight_view(ctx),
+                   &ctx->rb_dev->dv2, ctx->flags, s, ctx->err));
+  } else {
+    launch_diff<Tc>(Vn, Vp, (Tc*)ctx->dV, ctx->S, s);
+    launch_wnorm2<Tc>((const Tc*)ctx->dV, nullptr, weight_view(ctx), ctx->npart, ctx->nblk, &ctx->rb_dev->dv2,
+                      ctx->flags, s);
+    CHECK_LAUNCH();
+    TRY(project_tree<Tc>(ctx, (const Tc*)ctx->dV));
+  }
+  // a3..a6: pseudo-inverse, complement projection, Euler, Cholesky-QR (bases)
+  RowArgs a;
+  memset(&a, 0, sizeof(a));
+  a.d = mode_desc(ctx);
+  for (int n = 0; n < p; ++n) {
+    a.Y[n] = ctx->Y[n];
+    a.U[n] = ctx->U[n];
+    a.w[n] = ctx->w[n];
+    a.X[n] = ctx->X[n];
+    a.Up[n] = ctx->Up[n];
+    a.Uout[n] = ctx->U[n];
+    a.A[n] = ctx->A[n];
+  }
+  a.Tc = ctx->Tcore;
+  a.Ginv = ctx->Ginv;
+  a.part = ctx->rowpart;
+  a.ntile = ctx->ntile;
+  launch_update_rows<Tc>(a, ctx->P, ctx->R, ctx->Rinv, ctx->flags, ctx->cfg.reorth != 0, s);
+  CHECK_LAUNCH();
+  // core: T <- (T + dS) x_1 R_1 ... x_p R_p
+  int64_t Rprod = 1;
+  for (int n = 0; n < p; ++n) Rprod *= ctx->r[n];
+  launch_add<Tc>(ctx->T, (const Tc*)ctx->dS, ctx->T2, Rprod, s);
+  {
+    double* src = ctx->T2;
+    double* bufs[2] = {ctx->T, ctx->T2};
+    for (int n = 0; n < p; ++n) {
+      int64_t L = 1, Q = 1;
+      for (int m = 0; m < n; ++m) L *= ctx->r[m];
+      for (int m = n + 1; m < p; ++m) Q *= ctx->r[m];
+      double* dst = (src == bufs[0]) ? bufs[1] : bufs[0];
+      launch_modeprod<double, double, double>(src, dst, ctx->R + (int64_t)n * kMaxRank * kMaxRank, L, ctx->r[n],
+                                              ctx->r[n], Q, 1, kMaxRank, s);
+      src = dst;
+    }
+    if (src != ctx->T) CK(cudaMemcpyAsync(ctx->T, src, sizeof(double) * Rprod, cudaMemcpyDeviceToDevice, s));
+  }
+  CHECK_LAUNCH();
+  TRY(refresh_derived<Tc>(ctx, false));
+  // a7: error
+  ctx->step++;
+  bool exact = false;
+  switch (ctx->cfg.error_mode) {
+    case TDB_ERRMODE_EXACT: exact = true; break;
+    case TDB_ERRMODE_EVERY_K:
+    case TDB_ERRMODE_MLP: exact = (ctx->step % ctx->cfg.error_every) == 0; break;
+    default: exact = false;
+  }
+  if (exact) TRY(exact_error2<Tc>(ctx, Vn));
+  TRY(readback(ctx));
+  if (ctx->rb.flags & kFlagNonFinite) { ctx->err = "non-finite value in a snapshot difference"; return TDB_ERR_NONFINITE; }
+  if (ctx->rb.flags & kFlagCholGram) { ctx->err = "T_(n) T_(n)^T is not positive definite"; return TDB_ERR_RANK_DEFICIENT; }
+  if (ctx->rb.flags & kFlagCholQR) { ctx->err = "U^T W U is not positive definite"; return TDB_ERR_RANK_DEFICIENT; }
+  double eps = exact ? std::sqrt(std::max(ctx->rb.err2, 0.0)) : NAN;
+  double dv2 = ctx->rb.dv2;
+  double sig_step[kMaxModes][kMaxRank];
+  memcpy(sig_step, ctx->rb.sig2, sizeof(sig_step));
+  if (exact) ctx->exact_evals++;
+  // a8: rank control
+  double eps_after = eps;
+  int n_re = 0, action = ACT_NONE;
+  tdb_status cs = TDB_OK;
+  if (exact) {
+    cs = control<Tc>(ctx, Vn, eps, &eps_after, &n_re, &action);
+    if (cs != TDB_OK) return cs;
+    if (n_re > 0) {
+      TRY(readback(ctx));   // sigma of the new state
+    }
+  }
+  ctx->V_prev = Vn;
+  if (info) {
+    memset(info, 0, sizeof(*info));
+    info->step = ctx->step;
+    info->eps = eps_after;
+    info->eps_exact = exact ? 1 : 0;
+    info->eps_step = eps;
+    info->reinit = n_re;
+    info->action = action;
+    info->dv_norm = std::sqrt(std::max(dv2, 0.0));
+    double denom = 0.0;
+    for (int n = 0; n < p; ++n) denom += (double)ctx->r[n] * (double)ctx->N[n];
+    double rp = 1.0;
+    for (int n = 0; n < p; ++n) rp *= ctx->r[n];
+    info->cr = (double)ctx->S / (denom + rp);
+    for (int n = 0; n < p; ++n) {
+      info->ranks[n] = ctx->r[n];
+      double tot = 0.0;
+      for (int i = 0; i < ctx->r[n]; ++i) tot += std::max(ctx->rb.sig2[n][i], 0.0);
+      double e = (eps_after == eps_after) ? eps_after : 0.0;
+      info->gamma[n] = tot / (tot + e * e) * 100.0;
+      info->sigma_min[n] = std::sqrt(std::max(ctx->rb.sig2[n][ctx->r[n] - 1], 0.0));
+    }
+    (void)sig_step;
+  }
+  return (action == ACT_CAP) ? TDB_WARN_RANK_CAP : TDB_OK;
+}
+
+tdb_status common_init(tdb_ctx** out, const tdb_config* cfg, void* ws, size_t ws_bytes, void* stream, tdb_ctx** made) {
+  *made = nullptr;
+  if (!out) { g_init_error = "null ctx pointer"; return TDB_ERR_INVALID_ARG; }
+  *out = nullptr;
+  std::string err;
+  tdb_status st = validate(cfg, err);
+  if (st != TDB_OK) { g_init_error = err; return st; }
+  tdb_ctx* ctx = new (std::nothrow) tdb_ctx();
+  if (!ctx) { g_init_error = "out of host memory"; return TDB_ERR_INVALID_ARG; }
+  setup_dims(ctx, cfg);
+  ctx->stream = (cudaStream_t)stream;
+  ctx->use_tc = (ctx->prec == TDB_BF16_TTM);
+  if (ctx->use_tc && !tc_supported(ctx->p, ctx->N, ctx->cap, err)) {
+    g_init_error = "bf16 tensor-core path: " + err;
+    delete ctx;
+    return TDB_ERR_UNSUPPORTED;
+  }
+  Carver size_only(nullptr);
+  carve(ctx, size_only);
+  size_t need = size_only.off + 256;
+  if (!ws || ws_bytes < need || ((uintptr_t)ws & 255)) {
+    g_init_error = "workspace null, misaligned or smaller than tdb_workspace_bytes()";
+    delete ctx;
+    return TDB_ERR_WORKSPACE;
+  }
+  Carver cv(ws);
+  carve(ctx, cv);
+  // weights
+  for (int n = 0; n < ctx->p; ++n) {
+    std::vector<double> wh(ctx->N[n], 1.0);
+    if (cfg->weights[n]) {
+      for (int64_t i = 0; i < ctx->N[n]; ++i) {
+        wh[i] = cfg->weights[n][i];
+        if (!(wh[i] > 0.0) || !std::isfinite(wh[i])) {
+          g_init_error = "weights must be positive and finite";
+          delete ctx;
+          return TDB_ERR_INVALID_ARG;
+        }
+      }
+    }
+    cudaError_t e = cudaMemcpyAsync(ctx->w[n], wh.data(), sizeof(double) * ctx->N[n], cudaMemcpyHostToDevice, ctx->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+    if (e != cudaSuccess) {
+      g_init_error = std::string("copying weights: ") + cudaGetErrorString(e);
+      delete ctx;
+      return TDB_ERR_CUDA;
+    }
+  }
+  cudaMemsetAsync(ctx->rb_dev, 0, sizeof(Readback), ctx->stream);
+  *made = ctx;
+  return TDB_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+size_t tdb_workspace_bytes(const tdb_config* cfg) {
+  std::string err;
+  if (validate(cfg, err) != TDB_OK) return 0;
+  tdb_ctx c;
+  setup_dims(&c, cfg);
+  Carver cv(nullptr);
+  carve(&c, cv);
+  return cv.off + 256;
+}
+
+tdb_status tdb_init(tdb_ctx** out, const tdb_config* cfg, void* ws, size_t ws_bytes, const void* V0, void* stream) {
+  tdb_ctx* ctx = nullptr;
+  tdb_status st = common_init(out, cfg, ws, ws_bytes, stream, &ctx);
+  if (st != TDB_OK) return st;
+  if (!V0) { g_init_error = "null V0"; delete ctx; return TDB_ERR_INVALID_ARG; }
+  auto run = [&](auto tag) -> tdb_status {
+    using Tc = decltype(tag);
+    const Tc* V = (const Tc*)V0;
+    TRY(hosvd_spectrum<Tc>(ctx, V));
+    std::vector<int> r(ctx->p);
+    for (int n = 0; n < ctx->p; ++n) {
+      if (cfg->rank[n] > 0)
+        r[n] = std::min(cfg->rank[n], ctx->cap[n]);
+      else
+        r[n] = std::min(ctx->cap[n], rank_from_spectrum(ctx->h_ev[n], ctx->h_trace[n], cfg->gamma_th));
+    }
+    r = clamp_product_bound(r);
+    TRY(hosvd_state<Tc>(ctx, V, r.data()));
+    return readback(ctx);
+  };
+  st = ctx->f64 ? run(double()) : run(float());
+  if (st != TDB_OK) {
+    g_init_error = ctx->err;
+    delete ctx;
+    return st;
+  }
+  ctx->V_prev = V0;
+  ctx->ready = true;
+  *out = ctx;
+  return TDB_OK;
+}
+
+tdb_status tdb_init_from_factors(tdb_ctx** out, const tdb_config* cfg, void* ws, size_t ws_bytes, const double* core,
+                                 const double* const* U, const int* ranks, const void* V0, void* stream) {
+  tdb_ctx* ctx = nullptr;
+  tdb_status st = common_init(out, cfg, ws, ws_bytes, stream, &ctx);
+  if (st != TDB_OK) return st;
+  if (!V0 || !core || !U || !ranks) { g_init_error = "null argument"; delete ctx; return TDB_ERR_INVALID_ARG; }
+  int64_t Rprod = 1;
+  for (int n = 0; n < ctx->p; ++n) {
+    int other = 1;
+    for (int m = 0; m < ctx->p; ++m)
+      if (m != n) other *= ranks[m];
+    if (ranks[n] < 1 || ranks[n] > ctx->cap[n] || ranks[n] > other || !U[n]) {
+      g_init_error = "rank outside 1..min(N_n, prod_{m!=n} r_m, rank cap)";
+      delete ctx;
+      return TDB_ERR_RANK;
+    }
+    ctx->r[n] = ranks[n];
+    Rprod *= ranks[n];
+  }
+  cudaError_t e = cudaMemcpyAsync(ctx->T, core, sizeof(double) * Rprod, cudaMemcpyHostToDevice, ctx->stream);
+  for (int n = 0; n < ctx->p && e == cudaSuccess; ++n)
+    e = cudaMemcpyAsync(ctx->U[n], U[n], sizeof(double) * ctx->N[n] * ctx->r[n], cudaMemcpyHostToDevice, ctx->stream);
+  if (e != cudaSuccess) {
+    g_init_error = std::string("copying factors: ") + cudaGetErrorString(e);
+    delete ctx;
+    return TDB_ERR_CUDA;
+  }
+  st = ctx->f64 ? refresh_derived<double>(ctx, true) : refresh_derived<float>(ctx, true);
+  if (st == TDB_OK) st = readback(ctx);
+  if (st != TDB_OK) {
+    g_init_error = ctx->err;
+    delete ctx;
+    return st;
+  }
+  ctx->V_prev = V0;
+  ctx->ready = true;
+  *out = ctx;
+  return TDB_OK;
+}
+
+tdb_status tdb_push_snapshot(tdb_ctx* ctx, const void* V_next, tdb_step_info* info) {
+  if (!ctx) return TDB_ERR_INVALID_ARG;
+  if (!ctx->ready) { ctx->err = "push before init"; return TDB_ERR_STATE; }
+  if (!V_next) { ctx->err = "null snapshot"; return TDB_ERR_INVALID_ARG; }
+  return ctx->f64 ? step_impl<double>(ctx, (const double*)V_next, info)
+                  : step_impl<float>(ctx, (const float*)V_next, info);
+}
+
+tdb_status tdb_reconstruct(tdb_ctx* ctx, void* V_out) {
+  if (!ctx) return TDB_ERR_INVALID_ARG;
+  if (!ctx->ready) { ctx->err = "reconstruct before init"; return TDB_ERR_STATE; }
+  if (!V_out) { ctx->err = "null output"; return TDB_ERR_INVALID_ARG; }
+  return ctx->f64 ? reconstruct_into<double>(ctx, (double*)V_out) : reconstruct_into<float>(ctx, (float*)V_out);
+}
+
+tdb_status tdb_adapt_rank(tdb_ctx* ctx, const void* V_now, int* ranks_out, double* eps_out) {
+  if (!ctx) return TDB_ERR_INVALID_ARG;
+  if (!ctx->ready) { ctx->err = "adapt before init"; return TDB_ERR_STATE; }
+  if (!V_now) { ctx->err = "null snapshot"; return TDB_ERR_INVALID_ARG; }
+  auto run = [&](auto tag) -> tdb_status {
+    using Tc = decltype(tag);
+    double eps, ea;
+    int nre, act;
+    TRY(error_now<Tc>(ctx, (const Tc*)V_now, &eps));
+    TRY(control<Tc>(ctx, (const Tc*)V_now, eps, &ea, &nre, &act));
+    if (eps_out) *eps_out = ea;
+    return act == ACT_CAP ? TDB_WARN_RANK_CAP : TDB_OK;
+  };
+  tdb_status st = ctx->f64 ? run(double()) : run(float());
+  if (ranks_out)
+    for (int n = 0; n < ctx->p; ++n) ranks_out[n] = ctx->r[n];
+  return st;
+}
+
+tdb_status tdb_get_factors(tdb_ctx* ctx, double* core, double* const* U, int* ranks) {
+  if (!ctx) return TDB_ERR_INVALID_ARG;
+  if (!ctx->ready) { ctx->err = "not initialised"; return TDB_ERR_STATE; }
+  int64_t Rprod = 1;
+  for (int n = 0; n < ctx->p; ++n) Rprod *= ctx->r[n];
+  if (core) CK(cudaMemcpyAsync(core, ctx->T, sizeof(double) * Rprod, cudaMemcpyDeviceToHost, ctx->stream));
+  if (U)
+    for (int n = 0; n < ctx->p; ++n)
+      if (U[n]) CK(cudaMemcpyAsync(U[n], ctx->U[n], sizeof(double) * ctx->N[n] * ctx->r[n], cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (ranks)
+    for (int n = 0; n < ctx->p; ++n) ranks[n] = ctx->r[n];
+  return TDB_OK;
+}
+
+tdb_status tdb_get_projection(tdb_ctx* ctx, double* dS, double* const* Y) {
+  if (!ctx) return TDB_ERR_INVALID_ARG;
+  if (!ctx->ready) { ctx->err = "not initialised"; return TDB_ERR_STATE; }
+  int64_t Rprod = 1;
+  for (int n = 0; n < ctx->p; ++n) Rprod *= ctx->r[n];
+  auto fetch = [&](const void* src, double* dst, int64_t cnt) -> tdb_status {
+    if (ctx->f64) {
+      CK(cudaMemcpyAsync(dst, src, sizeof(double) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+    } else {
+      std::vector<float> tmp(cnt);
+      CK(cudaMemcpyAsync(tmp.data(), src, sizeof(float) * cnt, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      for (int64_t i = 0; i < cnt; ++i) dst[i] = tmp[i];
+    }
+    return TDB_OK;
+  };
+  if (dS) TRY(fetch(ctx->dS, dS, Rprod));
+  if (Y)
+    for (int n = 0; n < ctx->p; ++n)
+      if (Y[n]) TRY(fetch(ctx->Y[n], Y[n], Rprod / ctx->r[n] * ctx->N[n]));
+  return TDB_OK;
+}
+
+tdb_status tdb_get_counters(tdb_ctx* ctx, int64_t* steps, int64_t* reinits, int64_t* exact_evals) {
+  if (!ctx) return TDB_ERR_INVALID_ARG;
+  if (steps) *steps = ctx->step;
+  if (reinits) *reinits = ctx->reinits;
+  if (exact_evals) *exact_evals = ctx->exact_evals;
+  return TDB_OK;
+}
+
+// Serialised layout: magic, p, ranks[4], step, reinits, exact_evals, nhist, history[nhist], T, U_n.
+tdb_status tdb_save_state(tdb_ctx* ctx, void* buf, size_t* bytes) {
+  if (!ctx || !bytes) return TDB_ERR_INVALID_ARG;
+  if (!ctx->ready) { ctx->err = "not initialised"; return TDB_ERR_STATE; }
+  int64_t Rprod = 1;
+  for (int n = 0; n < ctx->p; ++n) Rprod *= ctx->r[n];
+  size_t need = 8 * (1 + 1 + kMaxModes + 3 + 1) + 8 * ctx->history.size() + 8 * Rprod;
+  for (int n = 0; n < ctx->p; ++n) need += 8 * ctx->N[n] * ctx->r[n];
+  if (!buf) { *bytes = need; return TDB_OK; }
+  if (*bytes < need) { *bytes = need; ctx->err = "buffer too small"; return TDB_ERR_INVALID_ARG; }
+  int64_t* h = (int64_t*)buf;
+  h[0] = 0x54444231;  // "TDB1"
+  h[1] = ctx->p;
+  for (int n = 0; n < kMaxModes; ++n) h[2 + n] = n < ctx->p ? ctx->r[n] : 0;
+  h[6] = ctx->step;
+  h[7] = ctx->reinits;
+  h[8] = ctx->exact_evals;
+  h[9] = (int64_t)ctx->history.size();
+  double* d = (double*)(h + 10);
+  for (size_t i = 0; i < ctx->history.size(); ++i) d[i] = ctx->history[i];
+  d += ctx->history.size();
+  CK(cudaMemcpyAsync(d, ctx->T, 8 * Rprod, cudaMemcpyDeviceToHost, ctx->stream));
+  d += Rprod;
+  for (int n = 0; n < ctx->p; ++n) {
+    CK(cudaMemcpyAsync(d, ctx->U[n], 8 * ctx->N[n] * ctx->r[n], cudaMemcpyDeviceToHost, ctx->stream));
+    d += ctx->N[n] * ctx->r[n];
+  }
+  CK(cudaStreamSynchronize(ctx->stream));
+  *bytes = need;
+  return TDB_OK;
+}
+
+tdb_status tdb_load_state(tdb_ctx* ctx, const void* buf, size_t bytes, const void* V_prev) {
+  if (!ctx || !buf || !V_prev) return TDB_ERR_INVALID_ARG;
+  const int64_t* h = (const int64_t*)buf;
+  if (bytes < 80 || h[0] != 0x54444231 || h[1] != ctx->p) { ctx->err = "not a state of this configuration"; return TDB_ERR_INVALID_ARG; }
+  int64_t Rprod = 1;
+  for (int n = 0; n < ctx->p; ++n) {
+    if (h[2 + n] < 1 || h[2 + n] > ctx->cap[n]) { ctx->err = "saved rank exceeds this context's cap"; return TDB_ERR_RANK; }
+    ctx->r[n] = (int)h[2 + n];
+    Rprod *= ctx->r[n];
+  }
+  ctx->step = h[6];
+  ctx->reinits = h[7];
+  ctx->exact_evals = h[8];
+  int64_t nh = h[9];
+  size_t need = 80 + 8 * (size_t)nh + 8 * Rprod;
+  for (int n = 0; n < ctx->p; ++n) need += 8 * ctx->N[n] * ctx->r[n];
+  if (bytes < need) { ctx->err = "state buffer truncated"; return TDB_ERR_INVALID_ARG; }
+  const double* d = (const double*)(h + 10);
+  ctx->history.assign(d, d + nh);
+  d += nh;
+  CK(cudaMemcpyAsync(ctx->T, d, 8 * Rprod, cudaMemcpyHostToDevice, ctx->stream));
+  d += Rprod;
+  for (int n = 0; n < ctx->p; ++n) {
+    CK(cudaMemcpyAsync(ctx->U[n], d, 8 * ctx->N[n] * ctx->r[n], cudaMemcpyHostToDevice, ctx->stream));
+    d += ctx->N[n] * ctx->r[n];
+  }
+  ctx->warm = false;
+  tdb_status st = ctx->f64 ? refresh_derived<double>(ctx, true) : refresh_derived<float>(ctx, true);
+  if (st != TDB_OK) return st;
+  TRY(readback(ctx));
+  ctx->V_prev = V_prev;
+  ctx->ready = true;
+  return TDB_OK;
+}
+
+const char* tdb_last_error(const tdb_ctx* ctx) {
+  if (!ctx) return g_init_error.c_str();
+  return ctx->err.c_str();
+}
+
+const char* tdb_status_string(tdb_status s) {
+  switch (s) {
+    case TDB_OK: return "TDB_OK";
+    case TDB_ERR_INVALID_ARG: return "TDB_ERR_INVALID_ARG";
+    case TDB_ERR_SHAPE: return "TDB_ERR_SHAPE";
+    case TDB_ERR_RANK: return "TDB_ERR_RANK";
+    case TDB_ERR_RANK_DEFICIENT: return "TDB_ERR_RANK_DEFICIENT";
+    case TDB_ERR_NONFINITE: return "TDB_ERR_NONFINITE";
+    case TDB_ERR_CUDA: return "TDB_ERR_CUDA";
+    case TDB_ERR_TIMEOUT: return "TDB_ERR_TIMEOUT";
+    case TDB_ERR_STATE: return "TDB_ERR_STATE";
+    case TDB_WARN_RANK_CAP: return "TDB_WARN_RANK_CAP";
+    case TDB_ERR_WORKSPACE: return "TDB_ERR_WORKSPACE";
+    case TDB_ERR_UNSUPPORTED: return "TDB_ERR_UNSUPPORTED";
+  }
+  return "unknown status";
+}
+
+void tdb_destroy(tdb_ctx* ctx) { delete ctx; }
+
+const char* tdb_version(void) { return "tdb 0.1 sm_103a"; }
+
+}  // extern "C"

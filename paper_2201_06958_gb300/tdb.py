@@ -1,0 +1,308 @@
+"""ctypes binding of libtdb (include/tdb.h): argument marshalling only.
+
+Every computation runs in libtdb's CUDA kernels.  PyTorch provides device
+memory (the workspace and snapshots) and the stream.  Loading fails loudly when
+libtdb.so has not been built; there is no CPU fallback.
+
+Snapshot convention: a logical N_1 x ... x N_p tensor is a C-contiguous torch
+tensor of shape (N_p, ..., N_1) (column-major, mode 1 fastest), float64 in
+"fp64" mode and float32 otherwise.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import List, Optional, Sequence
+
+import numpy as np
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtdb.so")
+MAX_MODES = 4
+MAX_RANK = 32
+
+PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
+ERROR_MODE = {"exact": 0, "every_k": 1, "mlp": 2, "none": 3}
+ACTIONS = {0: "none", 1: "reinit", 2: "increase", 3: "decrease", 4: "revert", 5: "cap"}
+
+TDB_OK = 0
+TDB_WARN_RANK_CAP = 9
+
+
+class tdb_config(C.Structure):
+    _fields_ = [
+        ("ndim", C.c_int),
+        ("dims", C.c_int64 * MAX_MODES),
+        ("rank", C.c_int * MAX_MODES),
+        ("rank_max", C.c_int * MAX_MODES),
+        ("weights", C.POINTER(C.c_double) * MAX_MODES),
+        ("eps_th", C.c_double),
+        ("gamma_th", C.c_double),
+        ("slope_window", C.c_int),
+        ("precision", C.c_int),
+        ("error_mode", C.c_int),
+        ("error_every", C.c_int),
+        ("reorth", C.c_int),
+    ]
+
+
+class tdb_step_info(C.Structure):
+    _fields_ = [
+        ("step", C.c_int64),
+        ("eps", C.c_double),
+        ("eps_exact", C.c_int),
+        ("eps_step", C.c_double),
+        ("gamma", C.c_double * MAX_MODES),
+        ("sigma_min", C.c_double * MAX_MODES),
+        ("ranks", C.c_int * MAX_MODES),
+        ("reinit", C.c_int),
+        ("action", C.c_int),
+        ("cr", C.c_double),
+        ("dv_norm", C.c_double),
+        ("ds_norm", C.c_double),
+    ]
+
+
+_lib = None
+
+EXPORTS = [
+    "tdb_workspace_bytes", "tdb_init", "tdb_init_from_factors", "tdb_push_snapshot", "tdb_reconstruct",
+    "tdb_adapt_rank", "tdb_get_factors", "tdb_get_projection", "tdb_get_counters", "tdb_save_state",
+    "tdb_load_state", "tdb_last_error", "tdb_status_string", "tdb_destroy", "tdb_version",
+]
+
+
+def load(path: str = LIB_PATH):
+    """Load libtdb.so (build it first with paper_2201_06958_gb300.build_lib)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libtdb.so not found at {path}: build it with "
+                          "`python -m paper_2201_06958_gb300.build_lib` (nvcc, sm_103a)")
+    lib = C.CDLL(path)
+    vp, sz, st = C.c_void_p, C.c_size_t, C.c_int
+    lib.tdb_workspace_bytes.argtypes = [C.POINTER(tdb_config)]
+    lib.tdb_workspace_bytes.restype = sz
+    lib.tdb_init.argtypes = [C.POINTER(vp), C.POINTER(tdb_config), vp, sz, vp, vp]
+    lib.tdb_init.restype = st
+    lib.tdb_init_from_factors.argtypes = [C.POINTER(vp), C.POINTER(tdb_config), vp, sz, C.POINTER(C.c_double),
+                                          C.POINTER(C.POINTER(C.c_double)), C.POINTER(C.c_int), vp, vp]
+    lib.tdb_init_from_factors.restype = st
+    lib.tdb_push_snapshot.argtypes = [vp, vp, C.POINTER(tdb_step_info)]
+    lib.tdb_push_snapshot.restype = st
+    lib.tdb_reconstruct.argtypes = [vp, vp]
+    lib.tdb_reconstruct.restype = st
+    lib.tdb_adapt_rank.argtypes = [vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+    lib.tdb_adapt_rank.restype = st
+    lib.tdb_get_factors.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.POINTER(C.c_double)), C.POINTER(C.c_int)]
+    lib.tdb_get_factors.restype = st
+    lib.tdb_get_projection.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.POINTER(C.c_double))]
+    lib.tdb_get_projection.restype = st
+    lib.tdb_get_counters.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    lib.tdb_get_counters.restype = st
+    lib.tdb_save_state.argtypes = [vp, vp, C.POINTER(sz)]
+    lib.tdb_save_state.restype = st
+    lib.tdb_load_state.argtypes = [vp, vp, sz, vp]
+    lib.tdb_load_state.restype = st
+    lib.tdb_last_error.argtypes = [vp]
+    lib.tdb_last_error.restype = C.c_char_p
+    lib.tdb_status_string.argtypes = [st]
+    lib.tdb_status_string.restype = C.c_char_p
+    lib.tdb_destroy.argtypes = [vp]
+    lib.tdb_destroy.restype = None
+    lib.tdb_version.argtypes = []
+    lib.tdb_version.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+class TDBError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{load().tdb_status_string(status).decode()}: {msg}")
+        self.status = status
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def make_config(dims: Sequence[int], rank: Sequence[int], rank_max: Optional[Sequence[int]] = None,
+                weights: Optional[Sequence[Optional[np.ndarray]]] = None, eps_th: float = 0.0,
+                gamma_th: float = 99.999, slope_window: int = 10, precision: str = "fp32",
+                error_mode: str = "exact", error_every: int = 1, reorth: bool = True):
+    """Build a tdb_config; returns (config, keepalive) - keep the second alive while the config is used."""
+    p = len(dims)
+    cfg = tdb_config()
+    cfg.ndim = p
+    keep = []
+    for n in range(p):
+        cfg.dims[n] = int(dims[n])
+        cfg.rank[n] = int(rank[n])
+        cfg.rank_max[n] = int(rank_max[n]) if rank_max is not None else 0
+        if weights is not None and weights[n] is not None:
+            w = np.ascontiguousarray(weights[n], dtype=np.float64)
+            keep.append(w)
+            cfg.weights[n] = _dptr(w)
+    cfg.eps_th = float(eps_th)
+    cfg.gamma_th = float(gamma_th)
+    cfg.slope_window = int(slope_window)
+    cfg.precision = PRECISION[precision]
+    cfg.error_mode = ERROR_MODE[error_mode]
+    cfg.error_every = int(error_every)
+    cfg.reorth = 1 if reorth else 0
+    return cfg, keep
+
+
+class TDB:
+    """One compressor context.  ``device`` defaults to cuda:0; the stream is the
+    current torch stream of that device at construction."""
+
+    def __init__(self, dims, rank, rank_max=None, weights=None, eps_th=0.0, gamma_th=99.999, slope_window=10,
+                 precision="fp32", error_mode="exact", error_every=1, reorth=True, device=None, stream=None):
+        self.lib = load()
+        self.dims = [int(d) for d in dims]
+        self.p = len(self.dims)
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.device = torch.device(device or "cuda:0")
+        self.cfg, self._keep = make_config(dims, rank, rank_max, weights, eps_th, gamma_th, slope_window,
+                                           precision, error_mode, error_every, reorth)
+        nbytes = self.lib.tdb_workspace_bytes(C.byref(self.cfg))
+        if nbytes == 0:
+            raise TDBError(1, "invalid configuration")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.ctx = C.c_void_p()
+        self._prev = None
+
+    @property
+    def storage_shape(self):
+        return tuple(reversed(self.dims))
+
+    def _check(self, status: int, ctx=True):
+        if status not in (TDB_OK, TDB_WARN_RANK_CAP):
+            msg = self.lib.tdb_last_error(self.ctx if ctx else None).decode()
+            raise TDBError(status, msg)
+        return status
+
+    def _snap(self, V: torch.Tensor) -> torch.Tensor:
+        if V.dtype != self.dtype or V.device != self.device or not V.is_contiguous() or tuple(V.shape) != self.storage_shape:
+            raise ValueError(f"snapshot must be a contiguous {self.dtype} tensor of shape {self.storage_shape} on "
+                             f"{self.device}")
+        return V
+
+    def init(self, V0: torch.Tensor):
+        V0 = self._snap(V0)
+        st = self.lib.tdb_init(C.byref(self.ctx), C.byref(self.cfg), C.c_void_p(self.workspace.data_ptr()),
+                               self.workspace.numel(), C.c_void_p(V0.data_ptr()), C.c_void_p(self.stream.cuda_stream))
+        self._check(st, ctx=False)
+        self._prev = V0
+        return self
+
+    def init_from_factors(self, core: np.ndarray, U: Sequence[np.ndarray], V0: torch.Tensor):
+        """core: logical (r_1, ..., r_p) float64; U[n]: (N_n, r_n) float64."""
+        V0 = self._snap(V0)
+        core_f = np.asfortranarray(core, dtype=np.float64).ravel(order="F")
+        Us = [np.asfortranarray(u, dtype=np.float64).ravel(order="F") for u in U]
+        ranks = (C.c_int * self.p)(*[int(s) for s in core.shape])
+        uptr = (C.POINTER(C.c_double) * self.p)(*[_dptr(u) for u in Us])
+        st = self.lib.tdb_init_from_factors(C.byref(self.ctx), C.byref(self.cfg),
+                                            C.c_void_p(self.workspace.data_ptr()), self.workspace.numel(),
+                                            _dptr(core_f), uptr, ranks, C.c_void_p(V0.data_ptr()),
+                                            C.c_void_p(self.stream.cuda_stream))
+        self._check(st, ctx=False)
+        self._prev = V0
+        return self
+
+    def push(self, V: torch.Tensor) -> dict:
+        V = self._snap(V)
+        info = tdb_step_info()
+        st = self.lib.tdb_push_snapshot(self.ctx, C.c_void_p(V.data_ptr()), C.byref(info))
+        self._check(st)
+        self._prev = V
+        return {
+            "step": info.step, "eps": info.eps, "eps_exact": bool(info.eps_exact), "eps_step": info.eps_step,
+            "gamma": list(info.gamma)[: self.p], "sigma_min": list(info.sigma_min)[: self.p],
+            "ranks": list(info.ranks)[: self.p], "reinit": info.reinit, "action": ACTIONS.get(info.action, "?"),
+            "cr": info.cr, "dv_norm": info.dv_norm, "ds_norm": info.ds_norm, "status": st,
+        }
+
+    def push_raw(self, ptr: int, info: Optional[tdb_step_info] = None) -> int:
+        """Push a snapshot given by device address (no checks); returns the status."""
+        return self.lib.tdb_push_snapshot(self.ctx, C.c_void_p(ptr), C.byref(info) if info is not None else None)
+
+    def reconstruct(self, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty(self.storage_shape, dtype=self.dtype, device=self.device)
+        self._check(self.lib.tdb_reconstruct(self.ctx, C.c_void_p(self._snap(out).data_ptr())))
+        return out
+
+    def adapt_rank(self, V: torch.Tensor):
+        V = self._snap(V)
+        ranks = (C.c_int * self.p)()
+        eps = C.c_double()
+        st = self.lib.tdb_adapt_rank(self.ctx, C.c_void_p(V.data_ptr()), ranks, C.byref(eps))
+        self._check(st)
+        self._prev = V
+        return list(ranks), eps.value
+
+    def ranks(self) -> List[int]:
+        r = (C.c_int * self.p)()
+        self._check(self.lib.tdb_get_factors(self.ctx, None, None, r))
+        return list(r)
+
+    def factors(self):
+        """(core (r_1..r_p) float64, [U_n (N_n x r_n)]) as numpy arrays in logical index order."""
+        r = self.ranks()
+        core = np.empty(int(np.prod(r)), dtype=np.float64)
+        Us = [np.empty(self.dims[n] * r[n], dtype=np.float64) for n in range(self.p)]
+        uptr = (C.POINTER(C.c_double) * self.p)(*[_dptr(u) for u in Us])
+        self._check(self.lib.tdb_get_factors(self.ctx, _dptr(core), uptr, None))
+        return (core.reshape(r, order="F"),
+                [u.reshape(self.dims[n], r[n], order="F") for n, u in enumerate(Us)])
+
+    def projection(self):
+        """(dS, [Y_n tensors]) of the last step, logical index order; Y_n has mode n of size N_n."""
+        r = self.ranks()
+        dS = np.empty(int(np.prod(r)), dtype=np.float64)
+        shapes = []
+        for n in range(self.p):
+            sh = list(r)
+            sh[n] = self.dims[n]
+            shapes.append(sh)
+        Ys = [np.empty(int(np.prod(sh)), dtype=np.float64) for sh in shapes]
+        yptr = (C.POINTER(C.c_double) * self.p)(*[_dptr(y) for y in Ys])
+        self._check(self.lib.tdb_get_projection(self.ctx, _dptr(dS), yptr))
+        return dS.reshape(r, order="F"), [y.reshape(sh, order="F") for y, sh in zip(Ys, shapes)]
+
+    def counters(self):
+        s, r, e = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(self.lib.tdb_get_counters(self.ctx, C.byref(s), C.byref(r), C.byref(e)))
+        return {"steps": s.value, "reinits": r.value, "exact_evals": e.value}
+
+    def save_state(self) -> bytes:
+        n = C.c_size_t(0)
+        self._check(self.lib.tdb_save_state(self.ctx, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        self._check(self.lib.tdb_save_state(self.ctx, buf, C.byref(n)))
+        return bytes(buf.raw[: n.value])
+
+    def load_state(self, blob: bytes, V_prev: torch.Tensor):
+        V_prev = self._snap(V_prev)
+        buf = C.create_string_buffer(blob, len(blob))
+        self._check(self.lib.tdb_load_state(self.ctx, buf, len(blob), C.c_void_p(V_prev.data_ptr())))
+        self._prev = V_prev
+
+    def close(self):
+        if self.ctx:
+            self.lib.tdb_destroy(self.ctx)
+            self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
