@@ -1,0 +1,457 @@
+#!/usr/bin/env python
+"""Throughput of the TDB compressor step on GB300.
+
+One step = one tdb_push_snapshot: snapshot difference, fused projection
+(Eqs. 2.15/2.16), pseudo-inverse and complement projection, Euler update,
+re-orthonormalisation, error (Eq. 2.20) and the Sec. 2.5 rank control, on one
+streamed snapshot.  Default workload: the 512 x 256 x 12 reactive-flow-like
+stream (FP32 snapshots, r <= 16, eps_th = 1e-4, gamma_th = 99.999 %, 1000 steps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl tdb|reference]
+
+Prints one JSON line (rank 0).  With N > 1 (torchrun) each rank compresses its own
+independent stream (replicas; the method has no exchange step on one tensor per
+GPU), barrier + max-over-ranks timing, value = all ranks' snapshots / time.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "snapshots/s and HBM GB/s of TDB step vs plain FP32 GPU path at equal error"
+UNIT = "snapshots/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="tdb", choices=["tdb", "reference"])
+    ap.add_argument("--workload", default="reactive", choices=["reactive", "stochastic", "channel", "analytic"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "bf16", "fp32", "fp64"])
+    ap.add_argument("--error-mode", default="auto", choices=["auto", "exact", "mlp", "every_k"])
+    ap.add_argument("--no-compare", action="store_true", help="skip the plain FP32 comparison run")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (torchrun); barrier + max over ranks only
+# ---------------------------------------------------------------------------
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.proc = None
+        self.dev = device_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline inputs
+# ---------------------------------------------------------------------------
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_sha(files):
+    h = hashlib.sha256()
+    for f in files:
+        with open(os.path.join(ROOT, "paper_2201_06958_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel_key: str, sha: str):
+    """DRAM bytes per launch from a committed ncu summary, if the kernel source still matches."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    e = d.get(kernel_key)
+    if not e or e.get("source_sha") != sha:
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands on a bounded sample (spawned process)
+# ---------------------------------------------------------------------------
+CPU_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np, torch
+import oracle as O
+from paper_2201_06958_gb300 import synth as S
+wl = S.make_workload({wl!r})
+w = wl.weights
+budget = {budget}
+ctrl = O.ControllerConfig(wl.eps_th, wl.gamma_th, 10, wl.rank_max) if wl.eps_th > 0 else None
+# only the compressor is timed; snapshot generation is outside the clock
+V_prev = S.to_logical(wl.snapshot(0))
+spec = O.hosvd_spectrum(V_prev, w)
+caps = O.rank_caps(wl.dims, wl.rank_max)
+r = [min(caps[n], O.rank_from_spectrum(spec[n][0], wl.gamma_th)) if wl.rank[n] == 0 else wl.rank[n] for n in range(wl.ndim)]
+r = O.clamp_product_bound(r)
+T, U, _ = O.hosvd(V_prev, w, r, spectrum=spec)
+st = O.TDBState(T, U)
+controller = O.Controller(ctrl, wl.dims, w) if ctrl else None
+elapsed, steps = 0.0, 0
+k = 0
+while elapsed < budget and steps < {max_steps}:
+    k += 1
+    V = S.to_logical(wl.snapshot(k))
+    t0 = time.perf_counter()
+    T1, U1, _, _ = O.step_euler(st.T, st.U, w, V_prev, V)
+    st = O.TDBState(T1, U1)
+    eps = O.error_exact(V, st.T, st.U, w)
+    if controller is not None:
+        st, eps, _, _ = controller.act(V, st, eps)
+    elapsed += time.perf_counter() - t0
+    steps += 1
+    V_prev = V
+print(json.dumps({{"steps": steps, "seconds": elapsed}}))
+"""
+
+
+def cpu_baseline(workload: str, budget_s: float, max_steps: int):
+    cores = os.cpu_count() or 1
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    code = CPU_SNIPPET.format(root=ROOT, wl=workload, budget=budget_s, max_steps=max_steps)
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if p.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "error": p.stderr[-400:]}
+    d = json.loads(p.stdout.strip().splitlines()[-1])
+    return {"value": d["steps"] / d["seconds"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {d['steps']} steps of the same stream (FP64 numpy oracle, exact error and rank "
+                      f"control every step), {d['seconds']:.1f} s of CPU time"}
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the oracle, as it stands, on the host cores
+# ---------------------------------------------------------------------------
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    wl_name = args.workload
+    total = args.warmup + args.steps
+    code = CPU_SNIPPET.format(root=ROOT, wl=wl_name, budget=1e9, max_steps=total)
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=3600)
+    if p.returncode != 0:
+        print(json.dumps({"impl": "reference", "unavailable": "oracle run failed: " + p.stderr[-200:]}))
+        return
+    d = json.loads(p.stdout.strip().splitlines()[-1])
+    per_step = d["seconds"] / max(d["steps"], 1)
+    value = 1.0 / per_step
+    wl = workload_desc(wl_name)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": wl,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{d['steps']} full steps (warm-up included in the mean) of the FP64 numpy oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+
+
+def workload_desc(name):
+    from paper_2201_06958_gb300 import synth as S
+    wl = S.make_workload(name)
+    dims = "x".join(str(d) for d in wl.dims)
+    return {"workload": f"{name} {dims} {wl.dtype}, rank<= {wl.rank_max}, eps_th={wl.eps_th:g}, "
+                        f"gamma_th={wl.gamma_th}%, {wl.steps}-step stream",
+            "dims": wl.dims, "rank_max": wl.rank_max, "eps_th": wl.eps_th, "gamma_th": wl.gamma_th,
+            "seed": 1000 + ["analytic", "reactive", "stochastic", "channel"].index(name) + 1}
+
+
+# ---------------------------------------------------------------------------
+# main arm
+# ---------------------------------------------------------------------------
+def run_tdb(args, world, rank, local):
+    import ctypes as C
+
+    import torch
+
+    from paper_2201_06958_gb300 import build_lib, synth as S, tdb
+
+    build_lib.build()
+    lib = tdb.load()
+    lib.tdb_set_profiling.argtypes = [C.c_void_p, C.c_int]
+    lib.tdb_get_profile.argtypes = [C.c_void_p, C.c_void_p]
+    lib.tdb_kernel_launches.restype = C.c_int64
+
+    class tdb_profile(C.Structure):
+        _fields_ = [("steps", C.c_int64), ("ms_project", C.c_double), ("ms_project_main", C.c_double),
+                    ("ms_update", C.c_double), ("ms_error", C.c_double), ("ms_control", C.c_double),
+                    ("launches_main", C.c_int64)]
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    seed = 1002 + 10 * rank if args.workload == "reactive" else None
+    wl = S.make_workload(args.workload, seed=seed) if seed else S.make_workload(args.workload)
+    precision = args.precision
+    if precision == "auto":
+        precision = "fp64" if wl.dtype == "f64" else "bf16"
+    err_mode = args.error_mode if args.error_mode != "auto" else "exact"
+    K, W = args.steps, args.warmup
+    nsnap = W + K + 1
+    snaps = torch.empty((nsnap,) + tuple(reversed(wl.dims)), dtype=wl.torch_dtype, device=dev)
+    for k in range(nsnap):
+        snaps[k] = wl.snapshot(k, device=dev)
+    torch.cuda.synchronize()
+
+    def make(prec):
+        c = tdb.TDB(wl.dims, wl.rank, rank_max=wl.rank_max, weights=wl.weights, eps_th=wl.eps_th,
+                    gamma_th=wl.gamma_th, precision=prec, error_mode=err_mode, device=dev)
+        return c
+
+    def run(prec, timed_profile=True):
+        c = make(prec)
+        try:
+            c.init(snaps[0])
+        except tdb.TDBError as e:
+            if prec == "bf16" and e.status == 11:
+                return None
+            raise
+        info = tdb.tdb_step_info()
+        for k in range(1, W + 1):
+            st = c.push_raw(snaps[k].data_ptr(), info)
+            assert st in (0, 9), (st, lib.tdb_last_error(c.ctx))
+        eps = []
+        barrier(world)
+        torch.cuda.synchronize()
+        if timed_profile:
+            lib.tdb_set_profiling(c.ctx, 1)
+        l0 = lib.tdb_kernel_launches()
+        sampler = ClockSampler(dev.index)
+        sampler.start()
+        time.sleep(0.3)
+        stream = torch.cuda.current_stream(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t_host0 = time.perf_counter()
+        e0.record(stream)
+        for k in range(W + 1, W + K + 1):
+            st = c.push_raw(snaps[k].data_ptr(), info)
+            if st not in (0, 9):
+                raise tdb.TDBError(st, lib.tdb_last_error(c.ctx).decode())
+            eps.append(info.eps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_host = time.perf_counter() - t_host0
+        clocks = sampler.stop()
+        launches = lib.tdb_kernel_launches() - l0
+        barrier(world)
+        ms = e0.elapsed_time(e1)
+        prof = tdb_profile()
+        lib.tdb_get_profile(c.ctx, C.byref(prof))
+        lib.tdb_set_profiling(c.ctx, 0)
+        counters = c.counters()
+        c.close()
+        return {"ms": ms, "host_s": t_host, "eps": eps, "prof": prof, "clocks": clocks, "launches": launches,
+                "counters": counters}
+
+    res = run(precision)
+    if res is None:
+        precision = "fp32"
+        res = run(precision)
+    ms_total = max_over_ranks(max(res["ms"], res["host_s"] * 1e3), world)
+    value = world * K / (ms_total * 1e-3)
+
+    # roofline of the dominant kernel (the projection pass)
+    prof = res["prof"]
+    S_el = 1
+    for d in wl.dims:
+        S_el *= d
+    esz = 8 if wl.dtype == "f64" else 4
+    alg_bytes = 2 * esz * S_el                      # V_{k+1} and V_k read once
+    kernel_ms = prof.ms_project_main / max(prof.launches_main, 1)
+    if precision == "bf16":
+        kname, kfiles = "tc_project", ["tc_project.cu"]
+    else:
+        kname, kfiles = "mode-1 product", ["k_basic.cu"]
+        alg_bytes = esz * S_el                      # the mode-1 product reads the materialised difference once
+    achieved = alg_bytes / (kernel_ms * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    sha = kernel_source_sha(kfiles)
+    traffic = recorded_traffic(f"{kname}|{args.workload}|{precision}", sha)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": kname, "kernel_ms": kernel_ms,
+                "algorithmic_bytes_per_launch": alg_bytes, "peak_source": peak_kind,
+                "phase_ms_per_step": {"project": prof.ms_project / max(prof.steps, 1),
+                                      "update": prof.ms_update / max(prof.steps, 1),
+                                      "error": prof.ms_error / max(prof.steps, 1),
+                                      "control_host": prof.ms_control / max(prof.steps, 1)}}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"bf16": "bf16", "fp32": "f32", "fp64": "f64"}[precision], "data": "synthetic",
+        "config": dict(workload_desc(args.workload), precision=precision, error_mode=err_mode,
+                       l2=("streamed inputs larger than L2: every step reads a new snapshot "
+                           f"({esz * S_el / 1e6:.1f} MB) from a {nsnap * esz * S_el / 1e9:.2f} GB device-resident "
+                           "stream; the previous snapshot is the one read in the step before"),
+                       parallelism=f"replicas x{world}"),
+        "roofline": roofline, "clocks": res["clocks"], "gpu_launches": int(res["launches"]),
+        "reinits": res["counters"]["reinits"], "exact_evals": res["counters"]["exact_evals"],
+    }
+
+    # the plain FP32 GPU path on the same stream, for the "at equal error" comparison
+    if not args.no_compare and precision != "fp32" and wl.dtype == "f32":
+        ref = run("fp32", timed_profile=True)
+        ms_ref = max_over_ranks(max(ref["ms"], ref["host_s"] * 1e3), world)
+        pairs = [(a, b) for a, b in zip(res["eps"], ref["eps"]) if a == a and b == b]
+        rel = max(abs(a - b) / b for a, b in pairs) if pairs else None
+        line["plain_fp32"] = {"value": world * K / (ms_ref * 1e-3), "unit": UNIT, "ms_per_step": ms_ref / K,
+                              "eps_max_rel_diff": rel, "reinits": ref["counters"]["reinits"]}
+
+    # end to end through the C ABI from pinned host buffers
+    if not args.no_e2e:
+        line["e2e"] = run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb)
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample_seconds, K)
+    if rank == 0:
+        print(json.dumps(line))
+
+
+def run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb):
+    import torch
+    host = torch.empty_like(snaps, device="cpu").pin_memory()
+    host.copy_(snaps)
+    c = tdb.TDB(wl.dims, wl.rank, rank_max=wl.rank_max, weights=wl.weights, eps_th=wl.eps_th,
+                gamma_th=wl.gamma_th, precision=precision, error_mode=err_mode, device=dev)
+    ring = [torch.empty_like(snaps[0]) for _ in range(2)]
+    stream = torch.cuda.current_stream(dev)
+    ring[0].copy_(host[0], non_blocking=True)
+    c.init(ring[0])
+    info = tdb.tdb_step_info()
+    for k in range(1, W + 1):
+        buf = ring[k % 2]
+        buf.copy_(host[k], non_blocking=True)
+        c.push_raw(buf.data_ptr(), info)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k in range(W + 1, W + K + 1):
+        buf = ring[k % 2]
+        buf.copy_(host[k], non_blocking=True)          # H2D of this step's snapshot (pinned)
+        st = c.push_raw(buf.data_ptr(), info)           # the step; it reads the result back to the host
+        if st not in (0, 9):
+            raise tdb.TDBError(st, lib.tdb_last_error(c.ctx).decode())
+    torch.cuda.synchronize()
+    dt = max_over_ranks(time.perf_counter() - t0, world)
+    c.close()
+    h2d = snaps[0].numel() * snaps.element_size()
+    return {"value": world * K / dt, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": 1056}        # the per-step status block read back by the step
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup() if args.impl == "tdb" else (
+        int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+        return
+    run_tdb(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -175,6 +175,28 @@ const char* tdb_status_string(tdb_status s);
 /* Release the context (not the workspace).  NULL is accepted. */
 void tdb_destroy(tdb_ctx* ctx);
 
+/* Accumulated device times of the phases of tdb_push_snapshot, measured with CUDA
+ * events on the context's stream while profiling is enabled (tdb_set_profiling).
+ * No counterpart in the paper: instrumentation for the roofline report. */
+typedef struct tdb_profile {
+  int64_t steps;              /* steps timed */
+  double ms_project;          /* difference + projection (Eqs. 2.15, 2.16) */
+  double ms_project_main;     /* the main projection kernel alone (the fused tensor-core
+                                 kernel in TDB_BF16_TTM, the mode-1 product otherwise) */
+  double ms_update;           /* pseudo-inverse, complement projection, Euler, Cholesky-QR,
+                                 core singular values */
+  double ms_error;            /* exact error (Eq. 2.20) or its estimate */
+  double ms_control;          /* rank control including HOSVD re-initialisations (host clock) */
+  int64_t launches_main;      /* launches of the main projection kernel */
+} tdb_profile;
+
+/* enable != 0 starts (and zeroes) the accumulation; 0 stops it. */
+tdb_status tdb_set_profiling(tdb_ctx* ctx, int enable);
+tdb_status tdb_get_profile(tdb_ctx* ctx, tdb_profile* out);
+
+/* Number of libtdb kernels launched by this process so far (all contexts). */
+int64_t tdb_kernel_launches(void);
+
 /* Library version and build facts: "tdb <ver> sm_103a". */
 const char* tdb_version(void);
 

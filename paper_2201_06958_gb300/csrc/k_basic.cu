@@ -9,7 +9,13 @@
 #include "common.cuh"
 #include "kernels.h"
 
+#include <atomic>
+
 namespace tdb {
+
+static std::atomic<long long> g_launches{0};
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long launches_so_far() { return g_launches.load(std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------------------
 // Elementwise
@@ -24,7 +30,7 @@ __global__ void k_diff(const T* __restrict__ a, const T* __restrict__ b, T* __re
 template <typename T>
 void launch_diff(const T* a, const T* b, T* out, int64_t n, cudaStream_t s) {
   int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
-  k_diff<T><<<blocks, 256, 0, s>>>(a, b, out, n);
+  k_diff<T><<<blocks, 256, 0, s>>>(a, b, out, n); count_launch();
 }
 template void launch_diff<float>(const float*, const float*, float*, int64_t, cudaStream_t);
 template void launch_diff<double>(const double*, const double*, double*, int64_t, cudaStream_t);
@@ -43,7 +49,7 @@ template <typename T>
 void launch_weighted_bases(const double* U, const double* w, T* A, int64_t N, int r, cudaStream_t s) {
   int64_t n = N * r;
   int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
-  k_weighted_bases<T><<<blocks, 256, 0, s>>>(U, w, A, N, r);
+  k_weighted_bases<T><<<blocks, 256, 0, s>>>(U, w, A, N, r); count_launch();
 }
 template void launch_weighted_bases<float>(const double*, const double*, float*, int64_t, int, cudaStream_t);
 template void launch_weighted_bases<double>(const double*, const double*, double*, int64_t, int, cudaStream_t);
@@ -57,7 +63,7 @@ template <typename Ts, typename Td>
 void launch_cast(const Ts* a, Td* b, int64_t n, cudaStream_t s) {
   int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
   if (blocks < 1) blocks = 1;
-  k_cast<Ts, Td><<<blocks, 256, 0, s>>>(a, b, n);
+  k_cast<Ts, Td><<<blocks, 256, 0, s>>>(a, b, n); count_launch();
 }
 template void launch_cast<double, float>(const double*, float*, int64_t, cudaStream_t);
 template void launch_cast<float, double>(const float*, double*, int64_t, cudaStream_t);
@@ -73,7 +79,7 @@ template <typename Tb>
 void launch_add(const double* a, const Tb* b, double* out, int64_t n, cudaStream_t s) {
   int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
   if (blocks < 1) blocks = 1;
-  k_add<Tb><<<blocks, 256, 0, s>>>(a, b, out, n);
+  k_add<Tb><<<blocks, 256, 0, s>>>(a, b, out, n); count_launch();
 }
 template void launch_add<float>(const double*, const float*, double*, int64_t, cudaStream_t);
 template void launch_add<double>(const double*, const double*, double*, int64_t, cudaStream_t);
@@ -130,8 +136,8 @@ __global__ void k_sum_partials(const double* __restrict__ partial, int n, double
 template <typename T>
 void launch_wnorm2(const T* x, const T* y, const WeightView& wv, double* partial, int nblocks, double* out,
                    unsigned* flags, cudaStream_t s) {
-  k_wnorm2_partial<T><<<nblocks, 256, 0, s>>>(x, y, wv, partial, flags);
-  k_sum_partials<<<1, 256, 0, s>>>(partial, nblocks, out);
+  k_wnorm2_partial<T><<<nblocks, 256, 0, s>>>(x, y, wv, partial, flags); count_launch();
+  k_sum_partials<<<1, 256, 0, s>>>(partial, nblocks, out); count_launch();
 }
 template void launch_wnorm2<float>(const float*, const float*, const WeightView&, double*, int, double*, unsigned*,
                                    cudaStream_t);
@@ -139,7 +145,7 @@ template void launch_wnorm2<double>(const double*, const double*, const WeightVi
                                     unsigned*, cudaStream_t);
 
 void launch_sum_partials(const double* partial, int n, double* out, cudaStream_t s) {
-  k_sum_partials<<<1, 256, 0, s>>>(partial, n, out);
+  k_sum_partials<<<1, 256, 0, s>>>(partial, n, out); count_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -220,6 +226,7 @@ template <typename Tin, typename Tm, typename Tacc>
 void launch_modeprod(const Tin* in, Tacc* out, const Tm* M, int64_t L, int K, int J, int64_t Q, int64_t sMj,
                      int64_t sMk, cudaStream_t s) {
   if (L <= 0 || K <= 0 || J <= 0 || Q <= 0) return;
+  count_launch();
   if (K <= 32 && J >= K) {
     int64_t total = L * J * Q;
     int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);

@@ -18,41 +18,6 @@
 namespace tdb {
 
 // ---------------------------------------------------------------------------
-// Bounded grid barrier (all CTAs co-resident: cooperative launch).  On timeout
-// the kernel records kFlagTimeout and every CTA leaves through the flag check.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ bool grid_sync(unsigned* count, unsigned* gen, unsigned nblocks, unsigned* flags) {
-  __shared__ int timed_out;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    timed_out = 0;
-    volatile unsigned* vgen = gen;
-    unsigned g = *vgen;
-    __threadfence();
-    unsigned arrived = atomicAdd(count, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
-      long long spins = 0;
-      while (*vgen == g) {
-        if (++spins > (1ll << 24)) {  // ~1 s at the sleep below
-          atomicOr(flags, kFlagTimeout);
-          timed_out = 1;
-          break;
-        }
-        if (*(volatile unsigned*)flags & kFlagTimeout) { timed_out = 1; break; }
-        __nanosleep(64);
-      }
-    }
-    __threadfence();
-  }
-  __syncthreads();
-  return timed_out == 0;
-}
-
-// ---------------------------------------------------------------------------
 // Weighted mode-n Gram: partial 32x32 tiles over column slices, then finish.
 // Column c of V_(n) is (l, q): V[l + L (i + N q)].
 // ---------------------------------------------------------------------------
@@ -137,156 +102,31 @@ void launch_wgram(const Tv* V, const GramView& g, double* part, size_t part_cap,
   int64_t ncol = g.L * g.Q;
   int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>((152 * 4 + npair - 1) / npair, (ncol + 255) / 256));
   while ((size_t)npair * ksplit * 1024 > part_cap && ksplit > 1) --ksplit;
-  k_wgram_partial<Tv><<<dim3(npair, ksplit), 1024, 0, s>>>(V, g, ntile, ksplit, part);
+  k_wgram_partial<Tv><<<dim3(npair, ksplit), 1024, 0, s>>>(V, g, ntile, ksplit, part); count_launch();
   int blocks = (int)std::min<int64_t>((g.Nn * g.Nn + 255) / 256, 1024);
   if (cc_float)
-    k_wgram_finish<float><<<blocks, 256, 0, s>>>(g, ntile, ksplit, part, C64, (float*)Cc);
+    { k_wgram_finish<float><<<blocks, 256, 0, s>>>(g, ntile, ksplit, part, C64, (float*)Cc); count_launch(); }
   else
-    k_wgram_finish<double><<<blocks, 256, 0, s>>>(g, ntile, ksplit, part, C64, (double*)Cc);
+    { k_wgram_finish<double><<<blocks, 256, 0, s>>>(g, ntile, ksplit, part, C64, (double*)Cc); count_launch(); }
 }
 template void launch_wgram<float>(const float*, const GramView&, double*, size_t, double*, void*, int, cudaStream_t);
 template void launch_wgram<double>(const double*, const GramView&, double*, size_t, double*, void*, int, cudaStream_t);
 
-// ---------------------------------------------------------------------------
-// Multi-CTA Jacobi (cooperative).  A, V: nn x nn (column-major, ld nn), nn even.
-// rin: 2 x (nn/2) x 3 rotation inputs (app, aqq, apq) by round parity.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void pair_of(int rd, int m /* nn-1 */, int i, int* k, int* role) {
-  // round rd pairs: k = 0 -> (rd, m); k >= 1 -> ((rd + k) mod m, (rd - k) mod m)
-  if (i == m) { *k = 0; *role = 1; return; }
-  if (i == rd) { *k = 0; *role = 0; return; }
-  int kk = ((i - rd) % m + m) % m;
-  if (kk <= (m - 1) / 2) { *k = kk; *role = 0; return; }
-  *k = ((rd - i) % m + m) % m;
-  *role = 1;
-}
-
-__device__ __forceinline__ void pair_members(int rd, int m, int k, int* p, int* q) {
-  if (k == 0) { *p = rd; *q = m; }
-  else { *p = (rd + k) % m; *q = ((rd - k) % m + m) % m; }
-}
-
+// Selection of the leading eigenpairs from candidate vectors: the m candidates are
+// the columns of V (n rows, leading dim ldv) with approximate eigenvalues on the
+// diagonal of A (leading dim lda).  Rough order by diag(A), Rayleigh quotients
+// v^T C v / v^T v in double against C64 for the top kk = k + 2, final order by them,
+// sign fix (largest-magnitude entry positive) and the trace of C64.
 template <typename T>
-__global__ void k_jacobi_coop(T* A, T* V, int nn, T* rin, double* redpart, unsigned* bar, unsigned* flags, int max_sweeps, double tol,
-                              int* sweeps_out) {
-  extern __shared__ unsigned char smraw[];
-  T* cs = (T*)smraw;                         // 2 * half
-  int* pq = (int*)(cs + nn);                 // 2 * half
-  __shared__ double red[32];
-  const int half = nn / 2, m = nn - 1;
-  const unsigned nb = gridDim.x;
-  const int64_t gtid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  const int64_t gstride = (int64_t)gridDim.x * blockDim.x;
-  // V = I; rotation inputs of round 0 from A
-  for (int64_t e = gtid; e < (int64_t)nn * nn; e += gstride) {
-    int64_t i = e % nn, j = e / nn;
-    V[e] = (i == j) ? T(1) : T(0);
-  }
-  for (int64_t k = gtid; k < half; k += gstride) {
-    int p, q;
-    pair_members(0, m, (int)k, &p, &q);
-    rin[3 * k + 0] = __ldcg(&A[p + (int64_t)nn * p]);
-    rin[3 * k + 1] = __ldcg(&A[q + (int64_t)nn * q]);
-    rin[3 * k + 2] = __ldcg(&A[p + (int64_t)nn * q]);
-  }
-  if (!grid_sync(bar, bar + 1, nb, flags)) return;
-  int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    // convergence: off-diagonal vs diagonal mass (all CTAs reach the same verdict)
-    double off = 0.0, dia = 0.0;
-    for (int64_t e = gtid; e < (int64_t)nn * nn; e += gstride) {
-      int64_t i = e % nn, j = e / nn;
-      double v = (double)__ldcg(&A[e]);
-      if (i == j) dia += v * v; else off += v * v;
-    }
-    off = block_sum(off, red);
-    dia = block_sum(dia, red);
-    if (threadIdx.x == 0) { redpart[2 * blockIdx.x] = off; redpart[2 * blockIdx.x + 1] = dia; }
-    if (!grid_sync(bar, bar + 1, nb, flags)) return;
-    double to = 0.0, td = 0.0;
-    for (unsigned b = 0; b < nb; ++b) { to += __ldcg(&redpart[2 * b]); td += __ldcg(&redpart[2 * b + 1]); }
-    if (!grid_sync(bar, bar + 1, nb, flags)) return;
-    if (to <= tol * tol * td || td == 0.0) break;
-    for (int rd = 0; rd < m; ++rd) {
-      const int par = (int)(((int64_t)sweep * m + rd) & 1);   // parity runs on across sweeps
-      const T* rcur = rin + (int64_t)par * 3 * half;
-      T* rnext = rin + (int64_t)(par ^ 1) * 3 * half;
-      const int rdn = (rd + 1) % m;
-      for (int k = threadIdx.x; k < half; k += blockDim.x) {
-        int p, q;
-        pair_members(rd, m, k, &p, &q);
-        T app = __ldcg(&rcur[3 * k]), aqq = __ldcg(&rcur[3 * k + 1]), apq = __ldcg(&rcur[3 * k + 2]);
-        T c = 1, s = 0;
-        if (apq != T(0) && fabs((double)apq) > tol * 1e-3 * sqrt(fabs((double)app * (double)aqq))) {
-          T theta = (aqq - app) / (T(2) * apq);
-          T t = (theta >= 0 ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
-          c = T(1) / sqrt(t * t + T(1));
-          s = t * c;
-        }
-        cs[2 * k] = c; cs[2 * k + 1] = s;
-        pq[2 * k] = p; pq[2 * k + 1] = q;
-      }
-      __syncthreads();
-      for (int64_t e = gtid; e < (int64_t)half * half; e += gstride) {
-        int I = (int)(e % half), J = (int)(e / half);
-        int pI = pq[2 * I], qI = pq[2 * I + 1], pJ = pq[2 * J], qJ = pq[2 * J + 1];
-        T cI = cs[2 * I], sI = cs[2 * I + 1], cJ = cs[2 * J], sJ = cs[2 * J + 1];
-        T* a00 = &A[pI + (int64_t)nn * pJ]; T* a01 = &A[pI + (int64_t)nn * qJ];
-        T* a10 = &A[qI + (int64_t)nn * pJ]; T* a11 = &A[qI + (int64_t)nn * qJ];
-        T b00 = __ldcg(a00), b01 = __ldcg(a01), b10 = __ldcg(a10), b11 = __ldcg(a11);
-        T c00 = cJ * b00 - sJ * b01, c01 = sJ * b00 + cJ * b01;
-        T c10 = cJ * b10 - sJ * b11, c11 = sJ * b10 + cJ * b11;
-        T n00 = cI * c00 - sI * c10, n01 = cI * c01 - sI * c11;
-        T n10 = sI * c00 + cI * c10, n11 = sI * c01 + cI * c11;
-        *a00 = n00; *a01 = n01; *a10 = n10; *a11 = n11;
-        // publish the inputs of next round's rotations that live in this block
-        int rows[2] = {pI, qI}, cols[2] = {pJ, qJ};
-        T vals[2][2] = {{n00, n01}, {n10, n11}};
-#pragma unroll
-        for (int x = 0; x < 2; ++x)
-#pragma unroll
-          for (int y = 0; y < 2; ++y) {
-            int i = rows[x], j = cols[y];
-            if (i > j) continue;
-            int ki, ri, kj, rj;
-            pair_of(rdn, m, i, &ki, &ri);
-            pair_of(rdn, m, j, &kj, &rj);
-            if (i == j) rnext[3 * ki + ri] = vals[x][y];
-            else if (ki == kj) rnext[3 * ki + 2] = vals[x][y];
-          }
-      }
-      for (int64_t e = gtid; e < (int64_t)nn * half; e += gstride) {
-        int64_t i = e % nn;
-        int J = (int)(e / nn);
-        int pJ = pq[2 * J], qJ = pq[2 * J + 1];
-        T cJ = cs[2 * J], sJ = cs[2 * J + 1];
-        T vp = __ldcg(&V[i + (int64_t)nn * pJ]), vq = __ldcg(&V[i + (int64_t)nn * qJ]);
-        V[i + (int64_t)nn * pJ] = cJ * vp - sJ * vq;
-        V[i + (int64_t)nn * qJ] = sJ * vp + cJ * vq;
-      }
-      if (!grid_sync(bar, bar + 1, nb, flags)) return;
-    }
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    *sweeps_out = sweep;
-    if (sweep >= max_sweeps) atomicOr(flags, kFlagEigNoConv);
-  }
-}
-
-// Selection of the leading eigenpairs of a Jacobi result (A diagonalised, V its
-// rotations, both nn x nn): rough order by diag(A), Rayleigh quotients
-// v^T C v / v^T v in double against C64 for the top kk = k + 2, final order by
-// them, sign fix (largest-magnitude entry positive) and the trace of C64.
-template <typename T>
-__global__ void k_eig_order(const T* __restrict__ A, int nn, int kk, int* __restrict__ order_out) {
+__global__ void k_eig_order(const T* __restrict__ A, int lda, int m, int kk, int* __restrict__ order_out) {
   __shared__ int order[1024];
   __shared__ float dg[1024];
-  for (int j = threadIdx.x; j < nn; j += blockDim.x) { order[j] = j; dg[j] = (float)A[j + (int64_t)nn * j]; }
+  for (int j = threadIdx.x; j < m; j += blockDim.x) { order[j] = j; dg[j] = (float)A[j + (int64_t)lda * j]; }
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int i = 0; i < kk; ++i) {
       int best = i;
-      for (int j = i + 1; j < nn; ++j)
+      for (int j = i + 1; j < m; ++j)
         if (dg[order[j]] > dg[order[best]]) best = j;
       int t = order[i]; order[i] = order[best]; order[best] = t;
       order_out[i] = order[i];
@@ -295,12 +135,12 @@ __global__ void k_eig_order(const T* __restrict__ A, int nn, int kk, int* __rest
 }
 
 template <typename T>
-__global__ void k_eig_cv(const double* __restrict__ C64, int n, const T* __restrict__ V, int nn,
+__global__ void k_eig_cv(const double* __restrict__ C64, int n, const T* __restrict__ V, int ldv,
                          const int* __restrict__ order, int kk, double* __restrict__ CV) {
   for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * kk; e += (int64_t)gridDim.x * blockDim.x) {
     int64_t i = e % n;
     int j = (int)(e / n);
-    const T* v = V + (int64_t)nn * order[j];
+    const T* v = V + (int64_t)ldv * order[j];
     double s = 0.0;
     for (int l = 0; l < n; ++l) s += C64[i + (int64_t)n * l] * (double)v[l];
     CV[e] = s;
@@ -308,15 +148,15 @@ __global__ void k_eig_cv(const double* __restrict__ C64, int n, const T* __restr
 }
 
 template <typename T>
-__global__ void k_eig_final(const T* __restrict__ V, int nn, int n, const double* __restrict__ C64,
+__global__ void k_eig_final(const T* __restrict__ V, int ldv, int n, const double* __restrict__ C64,
                             const int* __restrict__ order_in, int kk, const double* __restrict__ CV, int k,
                             double* __restrict__ ev_out, double* __restrict__ Q_out, double* __restrict__ trace_out) {
   __shared__ double red[32];
   __shared__ double rq[64];
-  __shared__ int ord[64], pos[64];
+  __shared__ int ord[64];
   __shared__ int imax;
   for (int j = 0; j < kk; ++j) {
-    const T* v = V + (int64_t)nn * order_in[j];
+    const T* v = V + (int64_t)ldv * order_in[j];
     double num = 0.0, den = 0.0;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       double vi = (double)v[i];
@@ -325,7 +165,7 @@ __global__ void k_eig_final(const T* __restrict__ V, int nn, int n, const double
     }
     num = block_sum(num, red);
     den = block_sum(den, red);
-    if (threadIdx.x == 0) { rq[j] = den > 0 ? num / den : 0.0; ord[j] = order_in[j]; pos[j] = j; }
+    if (threadIdx.x == 0) { rq[j] = den > 0 ? num / den : 0.0; ord[j] = order_in[j]; }
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -343,7 +183,10 @@ __global__ void k_eig_final(const T* __restrict__ V, int nn, int n, const double
   tr = block_sum(tr, red);
   if (threadIdx.x == 0) *trace_out = tr;
   for (int j = 0; j < k; ++j) {
-    const T* v = V + (int64_t)nn * ord[j];
+    const T* v = V + (int64_t)ldv * ord[j];
+    double nrm = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) nrm += (double)v[i] * (double)v[i];
+    nrm = block_sum(nrm, red);
     if (threadIdx.x == 0) {
       double best = -1.0;
       int ib = 0;
@@ -355,68 +198,156 @@ __global__ void k_eig_final(const T* __restrict__ V, int nn, int n, const double
       ev_out[j] = rq[j];
     }
     __syncthreads();
-    double sgn = v[imax] < T(0) ? -1.0 : 1.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) Q_out[i + (int64_t)n * j] = sgn * (double)v[i];
+    double sc = (v[imax] < T(0) ? -1.0 : 1.0) / sqrt(nrm > 0 ? nrm : 1.0);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) Q_out[i + (int64_t)n * j] = sc * (double)v[i];
     __syncthreads();
   }
 }
 
 template <typename T>
-static void eig_select(const T* A_ws, const T* V_ws, int nn, int n, const double* C64, int k, double* ev, double* Q,
-                       double* trace, double* scratch, cudaStream_t s) {
-  int kk = k + 2 < n ? k + 2 : n;
+static void eig_select(const T* A, int lda, int m, const T* V, int ldv, int n, const double* C64, int k, double* ev,
+                       double* Q, double* trace, double* scratch, cudaStream_t s) {
+  int kk = k + 2 < m ? k + 2 : m;
+  if (k > kk) k = kk;
   int* order = (int*)scratch;                 // 64 ints
   double* CV = scratch + 64;                  // n x kk
-  k_eig_order<T><<<1, 256, 0, s>>>(A_ws, nn, kk, order);
+  k_eig_order<T><<<1, 256, 0, s>>>(A, lda, m, kk, order); count_launch();
   int blocks = (int)std::min<int64_t>(((int64_t)n * kk + 127) / 128, 1024);
-  k_eig_cv<T><<<blocks, 128, 0, s>>>(C64, n, V_ws, nn, order, kk, CV);
-  k_eig_final<T><<<1, 256, 0, s>>>(V_ws, nn, n, C64, order, kk, CV, k, ev, Q, trace);
+  k_eig_cv<T><<<blocks, 128, 0, s>>>(C64, n, V, ldv, order, kk, CV); count_launch();
+  k_eig_final<T><<<1, 256, 0, s>>>(V, ldv, n, C64, order, kk, CV, k, ev, Q, trace); count_launch();
+}
+
+// ---------------------------------------------------------------------------
+// Block subspace iteration for the leading eigenpairs of an n x n PSD Gram
+// (n > 96): Z = C Q, Q = orth(Z) by Cholesky-QR on the column-normalised Gram
+// (a small diagonal shift is added if the factorisation fails), repeated `iters`
+// times, then Rayleigh-Ritz: H = Q^T C Q, Jacobi on H, Ritz vectors Q S, and
+// the selection above (Rayleigh quotients against C in double).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float hash_unit(uint32_t i, uint32_t j) {
+  uint32_t h = i * 0x9E3779B1u ^ (j + 0x7F4A7C15u) * 0x85EBCA77u;
+  h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
+  return (float)(h & 0xFFFFFF) / 8388608.0f - 1.0f;   // [-1, 1)
 }
 
 template <typename T>
-__global__ void k_pad_copy(const T* __restrict__ C, int n, T* __restrict__ A, int nn) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)nn * nn; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = e % nn, j = e / nn;
-    A[e] = (i < n && j < n) ? C[i + (int64_t)n * j] : T(0);
+__global__ void k_si_start(T* __restrict__ Q, int n, int m) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * m; e += (int64_t)gridDim.x * blockDim.x)
+    Q[e] = (T)hash_unit((uint32_t)(e % n), (uint32_t)(e / n));
+}
+
+// Z = C Q   (C: n x n, Q and Z: n x m, all leading dim n).  Block = 32 rows x 8 cols.
+template <typename T>
+__global__ void k_si_gemm(const T* __restrict__ C, const T* __restrict__ Q, T* __restrict__ Z, int n, int m) {
+  __shared__ T Cs[32][33];
+  __shared__ T Qs[32][9];
+  const int i0 = blockIdx.x * 32, j0 = blockIdx.y * 8;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  T acc = 0;
+  for (int l0 = 0; l0 < n; l0 += 32) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int l = l0 + ty + 8 * q;
+      Cs[tx][ty + 8 * q] = (i0 + tx < n && l < n) ? C[(i0 + tx) + (int64_t)n * l] : T(0);
+    }
+    Qs[tx][ty] = (l0 + tx < n && j0 + ty < m) ? Q[(l0 + tx) + (int64_t)n * (j0 + ty)] : T(0);
+    __syncthreads();
+#pragma unroll 8
+    for (int kk = 0; kk < 32; ++kk) acc += Cs[tx][kk] * Qs[kk][ty];
+    __syncthreads();
+  }
+  if (i0 + tx < n && j0 + ty < m) Z[(i0 + tx) + (int64_t)n * (j0 + ty)] = acc;
+}
+
+// G = X^T Y (m x m, double accumulation of chunks); X, Y: n x m, leading dim n.
+template <typename T>
+__global__ void k_si_inner(const T* __restrict__ X, const T* __restrict__ Y, int n, int m, double* __restrict__ G) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+    int a = e % m, b = e / m;
+    const T* x = X + (int64_t)n * a;
+    const T* y = Y + (int64_t)n * b;
+    double acc = 0.0;
+    for (int i0 = 0; i0 < n; i0 += 32) {
+      T s = 0;
+      int i1 = i0 + 32 < n ? i0 + 32 : n;
+      for (int i = i0; i < i1; ++i) s += x[i] * y[i];
+      acc += (double)s;
+    }
+    G[a + (int64_t)m * b] = acc;
   }
 }
 
-// Eigen-decomposition of the n x n Gram (C64 double; Cc in type T) -> leading k
-// eigenpairs (descending) into ev, Q (n x k double) and the trace.
-template <typename T>
-tdb_status eig_leading(const T* Cc, const double* C64, int n, int k, T* A_ws, T* V_ws, T* rin_ws, double* red_ws,
-                       unsigned* bar, unsigned* flags, int* sweeps, double* ev, double* Q, double* trace,
-                       double* scratch, cudaStream_t s) {
-  int nn = (n + 1) & ~1;
-  int blocks = (int)std::min<int64_t>(((int64_t)nn * nn + 255) / 256, 1024);
-  k_pad_copy<T><<<blocks, 256, 0, s>>>(Cc, n, A_ws, nn);
-  double tol = sizeof(T) == 8 ? 1e-15 : 1e-7;
-  int max_sweeps = 40;
-  int dev = 0;
-  cudaGetDevice(&dev);
-  int nsm = 0;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  int coop = 0;
-  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
-  if (!coop) return TDB_ERR_UNSUPPORTED;
-  size_t sm = (size_t)nn * sizeof(T) + (size_t)nn * sizeof(int);
-  int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_coop<T>, 256, sm);
-  if (per_sm < 1) return TDB_ERR_UNSUPPORTED;
-  int64_t work = (int64_t)(nn / 2) * (nn / 2) + (int64_t)nn * (nn / 2);
-  int grid = (int)std::min<int64_t>((int64_t)nsm * std::min(per_sm, 2), std::max<int64_t>(1, (work + 255) / 256));
-  cudaMemsetAsync(bar, 0, 2 * sizeof(unsigned), s);
-  void* args[] = {(void*)&A_ws, (void*)&V_ws, (void*)&nn, (void*)&rin_ws, (void*)&red_ws, (void*)&bar,
-                  (void*)&flags, (void*)&max_sweeps, (void*)&tol, (void*)&sweeps};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_jacobi_coop<T>, grid, 256, args, sm, s);
-  if (e != cudaSuccess) return TDB_ERR_CUDA;
-  eig_select<T>(A_ws, V_ws, nn, n, C64, k, ev, Q, trace, scratch, s);
-  return TDB_OK;
+// Cholesky-QR factor of the Gram G = Z^T Z: with D = diag(G)^{1/2},
+// D^{-1} G D^{-1} = L L^T (a shift 1e-5 I is added if that fails), and
+// Rinv = D^{-1} L^{-T} so that Q = Z Rinv has (near) orthonormal columns.
+__global__ void k_si_cholinv(const double* __restrict__ G, int m, double* __restrict__ Rinv, unsigned* flags) {
+  extern __shared__ double sm[];
+  double* S = sm;              // m x m (ld 64)
+  double* Li = sm + 64 * 64;   // m x m (ld 64)
+  __shared__ double d[64];
+  __shared__ bool ok;
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    double g = G[j + (int64_t)m * j];
+    d[j] = g > 0 ? sqrt(g) : 1.0;
+  }
+  __syncthreads();
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    double shift = attempt == 0 ? 0.0 : (attempt == 1 ? 1e-5 : 1e-2);
+    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+      int i = e % m, j = e / m;
+      S[i + 64 * j] = G[i + (int64_t)m * j] / (d[i] * d[j]) + (i == j ? shift : 0.0);
+    }
+    __syncthreads();
+    bool good = chol_smem(S, 64, m, &ok);
+    if (good) break;
+    if (attempt == 2 && threadIdx.x == 0) atomicOr(flags, kFlagEigNoConv);
+  }
+  trinv_lower_smem(S, Li, 64, m);
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    int i = e % m, j = e / m;
+    // Rinv = D^{-1} L^{-T}:  Rinv[i][j] = Li[j][i] / d[i]
+    Rinv[i + (int64_t)m * j] = (j >= i) ? Li[j + 64 * i] / d[i] : 0.0;
+  }
 }
-template tdb_status eig_leading<float>(const float*, const double*, int, int, float*, float*, float*, double*,
-                                       unsigned*, unsigned*, int*, double*, double*, double*, double*, cudaStream_t);
-template tdb_status eig_leading<double>(const double*, const double*, int, int, double*, double*, double*, double*,
-                                        unsigned*, unsigned*, int*, double*, double*, double*, double*, cudaStream_t);
+
+// Y = X M (X: n x m ld n, M: m x mc double ld m, Y: n x mc ld n); upper = M upper triangular.
+template <typename T>
+__global__ void k_si_apply(const T* __restrict__ X, const double* __restrict__ M, int n, int m, int mc, int upper,
+                           T* __restrict__ Y) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * mc; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e % n;
+    int j = (int)(e / n);
+    int lmax = upper ? (j < m - 1 ? j : m - 1) : m - 1;
+    double s = 0.0;
+    for (int l = 0; l <= lmax; ++l) s += (double)X[i + (int64_t)n * l] * M[l + (int64_t)m * j];
+    Y[e] = (T)s;
+  }
+}
+
+// X = Q S: Q n x m (ld n), S mm x mm (ld mm; rows >= m are the padding), X n x mm (ld n)
+template <typename T>
+__global__ void k_si_ritz(const T* __restrict__ Q, const T* __restrict__ S, int n, int m, int mm, T* __restrict__ X) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * mm; e += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = e % n;
+    int j = (int)(e / n);
+    double acc = 0.0;
+    for (int l = 0; l < m; ++l) acc += (double)Q[i + (int64_t)n * l] * (double)S[l + (int64_t)mm * j];
+    X[e] = (T)acc;
+  }
+}
+
+template <typename T>
+__global__ void k_to_T(const double* __restrict__ a, T* __restrict__ b, int n) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) b[i] = (T)a[i];
+}
+
+template <typename T>
+__global__ void k_to_double_sym(const double* __restrict__ H, int m, double* __restrict__ out) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
+    int i = e % m, j = e / m;
+    out[e] = 0.5 * (H[i + m * j] + H[j + m * i]);
+  }
+}
 
 // Small n: single-CTA Jacobi then the same selection.
 template <typename T>
@@ -450,16 +381,58 @@ tdb_status eig_leading_small(const T* Cc, const double* C64, int n, int k, T* A_
                              double* ev, double* Q, double* trace, double* scratch, cudaStream_t s) {
   size_t sm = (2 * 97 * 96 + 128 + 32) * sizeof(T) + 128 * sizeof(int);
   cudaFuncSetAttribute(k_jacobi_small_full<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  T tol = sizeof(T) == 8 ? T(1e-15) : T(1e-7);
-  k_jacobi_small_full<T><<<1, 512, sm, s>>>(Cc, n, A_ws, V_ws, 40, tol, flags);
+  T tol = sizeof(T) == 8 ? T(1e-15) : T(1e-6);
+  k_jacobi_small_full<T><<<1, 512, sm, s>>>(Cc, n, A_ws, V_ws, 40, tol, flags); count_launch();
   int nn = (n + 1) & ~1;
-  eig_select<T>(A_ws, V_ws, nn, n, C64, k, ev, Q, trace, scratch, s);
+  eig_select<T>(A_ws, nn, nn, V_ws, nn, n, C64, k, ev, Q, trace, scratch, s);
   return TDB_OK;
 }
 template tdb_status eig_leading_small<float>(const float*, const double*, int, int, float*, float*, unsigned*,
                                              double*, double*, double*, double*, cudaStream_t);
 template tdb_status eig_leading_small<double>(const double*, const double*, int, int, double*, double*, unsigned*,
                                               double*, double*, double*, double*, cudaStream_t);
+
+template <typename T>
+tdb_status eig_subspace(const T* Cc, const double* C64, int n, int k, int iters, const SubspaceWs<T>& ws,
+                        unsigned* flags, double* ev, double* Q, double* trace, double* scratch, cudaStream_t s) {
+  const int m = std::min(n, std::min(64, k + 16));
+  const int mm = (m + 1) & ~1;
+  int blocks_nm = (int)std::min<int64_t>(((int64_t)n * m + 255) / 256, 1024);
+  dim3 ggrid((n + 31) / 32, (m + 7) / 8);
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_si_cholinv, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * (int)sizeof(double));
+    attr = true;
+  }
+  k_si_start<T><<<blocks_nm, 256, 0, s>>>(ws.Q, n, m); count_launch();
+  for (int it = 0; it < iters; ++it) {
+    k_si_gemm<T><<<ggrid, 256, 0, s>>>(Cc, ws.Q, ws.Z, n, m); count_launch();
+    k_si_inner<T><<<(m * m + 255) / 256, 256, 0, s>>>(ws.Z, ws.Z, n, m, ws.G); count_launch();
+    k_si_cholinv<<<1, 256, 2 * 64 * 64 * sizeof(double), s>>>(ws.G, m, ws.R, flags); count_launch();
+    k_si_apply<T><<<blocks_nm, 256, 0, s>>>(ws.Z, ws.R, n, m, m, 1, ws.Q); count_launch();
+  }
+  // Rayleigh-Ritz
+  k_si_gemm<T><<<ggrid, 256, 0, s>>>(Cc, ws.Q, ws.Z, n, m); count_launch();
+  k_si_inner<T><<<(m * m + 255) / 256, 256, 0, s>>>(ws.Q, ws.Z, n, m, ws.G); count_launch();
+  k_to_double_sym<T><<<(m * m + 255) / 256, 256, 0, s>>>(ws.G, m, ws.R); count_launch();
+  k_to_T<T><<<(m * m + 255) / 256, 256, 0, s>>>(ws.R, ws.H, m * m); count_launch();
+  size_t sm = (2 * 97 * 96 + 128 + 32) * sizeof(T) + 128 * sizeof(int);
+  static bool attr2 = false;
+  if (!attr2) {
+    cudaFuncSetAttribute(k_jacobi_small_full<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    attr2 = true;
+  }
+  T tol = sizeof(T) == 8 ? T(1e-15) : T(1e-6);
+  k_jacobi_small_full<T><<<1, 512, sm, s>>>(ws.H, m, ws.JA, ws.JV, 30, tol, flags); count_launch();
+  // Ritz vectors X = Q S  (S = JV, mm x mm with ld mm; use its first m rows)
+  k_si_ritz<T><<<(int)std::min<int64_t>(((int64_t)n * mm + 255) / 256, 1024), 256, 0, s>>>(ws.Q, ws.JV, n, m, mm, ws.X); count_launch();
+  eig_select<T>(ws.JA, mm, mm, ws.X, n, n, C64, k, ev, Q, trace, scratch, s);
+  return TDB_OK;
+}
+template tdb_status eig_subspace<float>(const float*, const double*, int, int, int, const SubspaceWs<float>&, unsigned*,
+                                        double*, double*, double*, double*, cudaStream_t);
+template tdb_status eig_subspace<double>(const double*, const double*, int, int, int, const SubspaceWs<double>&,
+                                         unsigned*, double*, double*, double*, double*, cudaStream_t);
 
 // U = W^{-1/2} Q[:, :r] (before the Cholesky-QR that makes U^T W U = I exact)
 __global__ void k_scale_basis(const double* __restrict__ Q, const double* __restrict__ w, int64_t n, int r,
@@ -472,7 +445,7 @@ __global__ void k_scale_basis(const double* __restrict__ Q, const double* __rest
 void launch_scale_basis(const double* Q, const double* w, int64_t n, int r, double* U, cudaStream_t s) {
   int blocks = (int)std::min<int64_t>((n * r + 255) / 256, 1024);
   if (blocks < 1) blocks = 1;
-  k_scale_basis<<<blocks, 256, 0, s>>>(Q, w, n, r, U);
+  k_scale_basis<<<blocks, 256, 0, s>>>(Q, w, n, r, U); count_launch();
 }
 
 }  // namespace tdb

@@ -110,7 +110,7 @@ __global__ void k_gram_finish(ModeDesc d, const double* __restrict__ Gpart, int 
     Af[a + LD * b] = (float)(s / scale);
   }
   __syncthreads();
-  jacobi_smem<float>(Af, Vf, LD, r, 30, 1e-7f, csf, pq, redf);
+  jacobi_smem<float>(Af, Vf, LD, r, 30, 1e-6f, csf, pq, redf);
   // eigenvectors in the original basis: W = Vp * Vf (or Vf)
   // store W (float) as next warm start; Rayleigh quotients in double
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
@@ -155,9 +155,9 @@ __global__ void k_gram_finish(ModeDesc d, const double* __restrict__ Gpart, int 
 void launch_gram(const ModeDesc& d, const double* T, double* Gpart, int nsplit, double* G, double* Ginv,
                  double* sig2, float* Vprev, int warm, unsigned* flags, cudaStream_t s) {
   dim3 g1(nsplit, d.p);
-  k_gram_partial<<<g1, 256, 0, s>>>(d, T, Gpart, nsplit);
+  k_gram_partial<<<g1, 256, 0, s>>>(d, T, Gpart, nsplit); count_launch();
   size_t sm = 3 * LD * LD * sizeof(double) + 2 * LD * LD * sizeof(float) + (64 + 32) * sizeof(float) + 64 * sizeof(int);
-  k_gram_finish<<<d.p, 256, sm, s>>>(d, Gpart, nsplit, G, Ginv, sig2, Vprev, warm, flags);
+  k_gram_finish<<<d.p, 256, sm, s>>>(d, Gpart, nsplit, G, Ginv, sig2, Vprev, warm, flags); count_launch();
 }
 
 // ---------------------------------------------------------------------------
@@ -325,16 +325,16 @@ void launch_update_rows(RowArgs& a, double* P, double* R, double* Rinv, unsigned
   int64_t Nmax = 0;
   for (int n = 0; n < a.d.p; ++n) Nmax = std::max<int64_t>(Nmax, a.d.N[n]);
   dim3 grid((unsigned)((Nmax + 31) / 32), a.d.p);
-  k_rows_mx<Tc><<<grid, 1024, 0, s>>>(a);
-  k_sum_tiles<<<a.d.p, 256, 0, s>>>(a.d, a.part, a.ntile, P);
+  k_rows_mx<Tc><<<grid, 1024, 0, s>>>(a); count_launch();
+  k_sum_tiles<<<a.d.p, 256, 0, s>>>(a.d, a.part, a.ntile, P); count_launch();
   a.P = P;
-  k_rows_u1<<<grid, 1024, 0, s>>>(a);
+  k_rows_u1<<<grid, 1024, 0, s>>>(a); count_launch();
   if (reorth)
-    k_cholqr_small<<<a.d.p, 256, 0, s>>>(a.d, a.part, a.ntile, R, Rinv, flags);
+    { k_cholqr_small<<<a.d.p, 256, 0, s>>>(a.d, a.part, a.ntile, R, Rinv, flags); count_launch(); }
   else
-    k_set_identity<<<1, 256, 0, s>>>(a.d.p, R, Rinv);
+    { k_set_identity<<<1, 256, 0, s>>>(a.d.p, R, Rinv); count_launch(); }
   a.Rinv = Rinv;
-  k_rows_u2<Tc><<<grid, 1024, 0, s>>>(a);
+  k_rows_u2<Tc><<<grid, 1024, 0, s>>>(a); count_launch();
 }
 template void launch_update_rows<float>(RowArgs&, double*, double*, double*, unsigned*, bool, cudaStream_t);
 template void launch_update_rows<double>(RowArgs&, double*, double*, double*, unsigned*, bool, cudaStream_t);
@@ -370,10 +370,10 @@ void launch_orthonormalize(RowArgs& a, double* R, double* Rinv, unsigned* flags,
   int64_t Nmax = 0;
   for (int n = 0; n < a.d.p; ++n) Nmax = std::max<int64_t>(Nmax, a.d.N[n]);
   dim3 grid((unsigned)((Nmax + 31) / 32), a.d.p);
-  k_rows_cpart<<<grid, 1024, 0, s>>>(a);
-  k_cholqr_small<<<a.d.p, 256, 0, s>>>(a.d, a.part, a.ntile, R, Rinv, flags);
+  k_rows_cpart<<<grid, 1024, 0, s>>>(a); count_launch();
+  k_cholqr_small<<<a.d.p, 256, 0, s>>>(a.d, a.part, a.ntile, R, Rinv, flags); count_launch();
   a.Rinv = Rinv;
-  k_rows_u2<Tc><<<grid, 1024, 0, s>>>(a);
+  k_rows_u2<Tc><<<grid, 1024, 0, s>>>(a); count_launch();
 }
 template void launch_orthonormalize<float>(RowArgs&, double*, double*, unsigned*, cudaStream_t);
 template void launch_orthonormalize<double>(RowArgs&, double*, double*, unsigned*, cudaStream_t);
@@ -434,8 +434,8 @@ void launch_jacobi_eig(const T* A, int n, double* ev, T* V, unsigned* flags, cud
     cudaFuncSetAttribute(k_jacobi_eig<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr = true;
   }
-  T tol = sizeof(T) == 8 ? T(1e-15) : T(1e-7);
-  k_jacobi_eig<T><<<1, 512, sm, s>>>(A, n, ev, V, 40, tol, flags);
+  T tol = sizeof(T) == 8 ? T(1e-15) : T(1e-6);
+  k_jacobi_eig<T><<<1, 512, sm, s>>>(A, n, ev, V, 40, tol, flags); count_launch();
 }
 template void launch_jacobi_eig<float>(const float*, int, double*, float*, unsigned*, cudaStream_t);
 template void launch_jacobi_eig<double>(const double*, int, double*, double*, unsigned*, cudaStream_t);

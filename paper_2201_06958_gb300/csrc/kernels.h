@@ -56,6 +56,10 @@ struct GramView {
   int64_t L, Q, Nn;
 };
 
+// Process-wide count of libtdb kernel launches (tdb_kernel_launches).
+void count_launch(int n = 1);
+long long launches_so_far();
+
 // k_basic.cu
 template <typename T> void launch_diff(const T* a, const T* b, T* out, int64_t n, cudaStream_t s);
 template <typename T> void launch_weighted_bases(const double* U, const double* w, T* A, int64_t N, int r, cudaStream_t s);
@@ -82,12 +86,22 @@ template <typename Tv>
 void launch_wgram(const Tv* V, const GramView& g, double* part, size_t part_cap, double* C64, void* Cc, int cc_float,
                   cudaStream_t s);
 template <typename T>
-tdb_status eig_leading(const T* Cc, const double* C64, int n, int k, T* A_ws, T* V_ws, T* rin_ws, double* red_ws,
-                       unsigned* bar, unsigned* flags, int* sweeps, double* ev, double* Q, double* trace,
-                       double* scratch, cudaStream_t s);
-template <typename T>
 tdb_status eig_leading_small(const T* Cc, const double* C64, int n, int k, T* A_ws, T* V_ws, unsigned* flags,
                              double* ev, double* Q, double* trace, double* scratch, cudaStream_t s);
+template <typename T>
+struct SubspaceWs {
+  T* Q;        // n x 64
+  T* Z;        // n x 64
+  T* X;        // n x 64
+  double* G;   // 64 x 64
+  double* R;   // 64 x 64
+  T* H;        // 64 x 64
+  T* JA;       // 64 x 64
+  T* JV;       // 64 x 64
+};
+template <typename T>
+tdb_status eig_subspace(const T* Cc, const double* C64, int n, int k, int iters, const SubspaceWs<T>& ws,
+                        unsigned* flags, double* ev, double* Q, double* trace, double* scratch, cudaStream_t s);
 void launch_scale_basis(const double* Q, const double* w, int64_t n, int r, double* U, cudaStream_t s);
 
 }  // namespace tdb

@@ -1,18 +1,647 @@
-// tc_project.cu - placeholder until the tensor-core projection lands.
+// tc_project.cu - the projection of Eqs. 2.15/2.16 with the snapshot difference
+// fused in, on the 5th-generation tensor cores (sm_103a).
+//
+// The snapshot is viewed as N1 x N2 x S (S = product of the modes after the
+// second).  One persistent CTA loop walks 128 x 128 (i1 x i2) tiles of one slice s:
+//   * TMA (cp.async.bulk.tensor) streams 64 x 16 FP32 boxes of V_{k+1} and V_k
+//     into eight shared-memory stages, one per converter warp;
+//   * eight converter warps form dV = V_{k+1} - V_k in FP32 (before any rounding),
+//     accumulate ||dV||_W^2, round to BF16 and write one 128-byte-swizzled tile;
+//   * one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32 in TMEM) on
+//     that tile twice: as the K-major A operand of Z1 = dV x_1 A_1^T (M = i2,
+//     K = i1) and as the MN-major A operand of Z2 = dV x_2 A_2^T (M = i1, K = i2);
+//     the weighted bases A_n = W_n U_n are resident in shared memory as BF16;
+//   * four epilogue warps drain the TMEM accumulators (tcgen05.ld) into partial
+//     sums over the i1 tiles (Z1) and i2 tiles (Z2).
+// A small reduction and mode products on the rank-sized remainders then give
+// dS and every Y_n (dimension tree: contract mode 1 first for Y_{n>=2} and dS,
+// mode 2 first for Y_1).
+// Every wait is bounded: on timeout the kernel records a flag, stops issuing,
+// drains its own copies and frees TMEM before returning.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
 #include "tc_project.h"
 
 namespace tdb {
+namespace {
 
-bool tc_supported(int, const int64_t*, const int*, std::string& err) {
-  err = "not built yet";
-  return false;
+constexpr int TILE = 128;
+constexpr int SUB_I1 = 64, SUB_I2 = 16;
+constexpr int NSUB = 16;                                 // sub-tiles per tile: 2 i1 halves x 8 i2 strips
+constexpr int BOX_BYTES = SUB_I1 * SUB_I2 * 4;           // 4 KB
+constexpr int STAGE_BYTES = 2 * BOX_BYTES;               // V_{k+1} and V_k boxes
+constexpr int BF_TILE_BYTES = TILE * TILE * 2;           // 32 KB
+constexpr int HALF_BYTES = BF_TILE_BYTES / 2;            // one 64-wide i1 half: 128 rows x 128 B
+constexpr int NUM_EPI_WARPS = 4;                         // warps 0..3 (TMEM lane quadrants 0..3)
+constexpr int TMA_WARP = 4;
+constexpr int MMA_WARP = 5;
+constexpr int CONV_WARP0 = 6;
+constexpr int NUM_CONV_WARPS = 8;
+constexpr int NUM_WARPS = CONV_WARP0 + NUM_CONV_WARPS;   // 14
+constexpr int NUM_THREADS = NUM_WARPS * 32;              // 448
+constexpr int MAX_STAGES = 8;                            // one stage per converter warp (used twice per tile)
+constexpr uint32_t TMEM_COLS = 128;                      // 2 buffers x (D1 32 cols + D2 32 cols)
+constexpr long long TIMEOUT_CYCLES = 4000000000ll;       // ~2 s at 2 GHz
+constexpr int kSmemLimit = 227 * 1024 - 512;             // dynamic shared memory (static use 256 B)
+
+struct Params {
+  int N1, N2, nslice;
+  int nq1, nq2;
+  int r1, r2, r1pad, r2pad;
+  int nunits, nstages;
+  int b1_bytes, b2_bytes;
+  float* Z1p;                    // [nq1][nslice][N2][r1]
+  float* Z2p;                    // [nq2][nslice][N1][r2]
+  const uint4* B1img;            // BF16 operand images (global)
+  const uint4* B2img;
+  const double* w1;
+  const double* w2;
+  const double* wsl;             // slice weights (product over modes >= 3)
+  double* npart;                 // per-CTA ||dV||_W^2
+  unsigned* flags;
+};
+
+// ---------------------------------------------------------------------------
+// PTX wrappers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
 }
-void tc_carve(TcPlan&, Carver&, int, const int64_t*, const int*) {}
-tdb_status tc_project(TcPlan&, const float*, const float*, int, const int64_t*, const int*, const void* const*, float*,
-                      float* const*, double*, int, const WeightView&, double*, unsigned*, cudaStream_t,
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on a phase parity.  Returns false (and raises the abort flag) on
+// timeout or when another role already aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* flags) {
+  long long t0 = clock64();
+  for (int it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255) == 255) {
+      if (*abort_flag) return false;
+      if (clock64() - t0 > TIMEOUT_CYCLES) {
+        *abort_flag = 1;
+        atomicOr(flags, kFlagTimeout);
+        return false;
+      }
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int x, int y, int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: start, leading / stride byte offsets, version 1,
+// 128-byte swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, B K-major, A K- or MN-major.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N, int a_mn_major) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)a_mn_major << 15) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(
+          d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, "
+      "[%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&h);
+}
+
+// ---------------------------------------------------------------------------
+// The fused kernel
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NUM_THREADS, 1)
+    k_tc_project(const __grid_constant__ CUtensorMap tmVn, const __grid_constant__ CUtensorMap tmVp, Params P) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* bf_tiles = smem;                                          // 2 x 32 KB
+  unsigned char* b1_smem = bf_tiles + 2 * BF_TILE_BYTES;                   // resident A_1 image
+  unsigned char* b2_smem = b1_smem + ((P.b1_bytes + 1023) & ~1023);        // resident A_2 image
+  unsigned char* stages = b2_smem + ((P.b2_bytes + 1023) & ~1023);         // nstages x 16 KB
+  uint64_t* bars = (uint64_t*)(stages + P.nstages * STAGE_BYTES);
+  uint64_t* full = bars;                    // [MAX_STAGES]
+  uint64_t* empty = bars + MAX_STAGES;      // [MAX_STAGES]
+  uint64_t* bf_full = bars + 2 * MAX_STAGES;
+  uint64_t* mma_done = bf_full + 2;
+  uint64_t* epi_done = mma_done + 2;
+  uint32_t* tmem_slot = (uint32_t*)(epi_done + 2);
+  volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
+  __shared__ double red[32];
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  if (tid == 0) {
+    for (int s = 0; s < MAX_STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&bf_full[b]), NUM_CONV_WARPS);
+      mbar_init(smem_u32(&mma_done[b]), 1);
+      mbar_init(smem_u32(&epi_done[b]), NUM_EPI_WARPS);
+    }
+    *abort_flag = 0;
+    fence_mbar_init();
+  }
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  // resident BF16 images of the weighted bases
+  {
+    uint4* d1 = (uint4*)b1_smem;
+    for (int i = tid; i < P.b1_bytes / 16; i += NUM_THREADS) d1[i] = P.B1img[i];
+    uint4* d2 = (uint4*)b2_smem;
+    for (int i = tid; i < P.b2_bytes / 16; i += NUM_THREADS) d2[i] = P.B2img[i];
+  }
+  fence_proxy_async();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+  const uint32_t bf_base = smem_u32(bf_tiles);
+  double acc_norm = 0.0;
+
+  if (warp == TMA_WARP) {
+    if (lane == 0) {
+      // sub-tile j = h*8 + q (i1 half h, i2 strip q) goes to stage q, owned by converter
+      // warp q, which uses it twice per tile (h = 0 then h = 1)
+      int last_t = -1;
+      bool ok = true;
+      int t = 0;
+      for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x, ++t) {
+        const int q1 = u % P.nq1, q2 = (u / P.nq1) % P.nq2, sl = u / (P.nq1 * P.nq2);
+        for (int j = 0; j < NSUB; ++j) {
+          const int st = j & 7, use = 2 * t + (j >> 3);
+          if (!mbar_wait(smem_u32(&empty[st]), (use & 1) ^ 1, abort_flag, P.flags)) { ok = false; break; }
+          const uint32_t fb = smem_u32(&full[st]);
+          mbar_arrive_expect_tx(fb, STAGE_BYTES);
+          const int x = q1 * TILE + (j >> 3) * SUB_I1;
+          const int y = q2 * TILE + (j & 7) * SUB_I2;
+          const uint32_t dst = smem_u32(stages + st * STAGE_BYTES);
+          tma_load_3d(dst, &tmVn, x, y, sl, fb);
+          tma_load_3d(dst + BOX_BYTES, &tmVp, x, y, sl, fb);
+        }
+        if (ok) last_t = t;
+      }
+      // drain: the copies of the last armed tile have landed before the CTA may leave
+      if (last_t >= 0)
+        for (int j = 0; j < 8; ++j) {
+          long long t0 = clock64();
+          while (!mbar_try_wait(smem_u32(&full[j]), (2 * last_t + 1) & 1) && clock64() - t0 < TIMEOUT_CYCLES) {
+          }
+        }
+    }
+  } else if (warp == MMA_WARP) {
+    if (lane == 0) {
+      const uint32_t idesc1 = instr_desc(128, P.r1pad, 0);
+      const uint32_t idesc2 = instr_desc(128, P.r2pad, 1);
+      const uint32_t b1 = smem_u32(b1_smem), b2 = smem_u32(b2_smem);
+      const uint32_t blk1 = (uint32_t)P.r1pad * 128u, blk2 = (uint32_t)P.r2pad * 128u;
+      int t = 0;
+      bool ok = true;
+      for (int u = blockIdx.x; u < P.nunits; u += gridDim.x, ++t) {
+        const int q1 = u % P.nq1, q2 = (u / P.nq1) % P.nq2;
+        const int buf = t & 1;
+        if (!mbar_wait(smem_u32(&bf_full[buf]), (t >> 1) & 1, abort_flag, P.flags)) { ok = false; break; }
+        if (t >= 2 && !mbar_wait(smem_u32(&epi_done[buf]), ((t >> 1) - 1) & 1, abort_flag, P.flags)) {
+          ok = false;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t tile = bf_base + buf * BF_TILE_BYTES;
+        const uint32_t d1 = tmem_base + buf * 64;
+        const uint32_t d2 = tmem_base + buf * 64 + 32;
+        // Z1 tile: D1[i2, a] = sum_{i1} dV[i1, i2] A1[i1, a]  (A: K-major view, K = i1)
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          uint64_t ad = smem_desc(tile + (kk >> 2) * HALF_BYTES + (kk & 3) * 32, 16, 1024);
+          uint64_t bd = smem_desc(b1 + (q1 * 2 + (kk >> 2)) * blk1 + (kk & 3) * 32, 16, 1024);
+          mma_bf16(d1, ad, bd, idesc1, kk > 0 ? 1u : 0u);
+        }
+        // Z2 tile: D2[i1, b] = sum_{i2} dV[i1, i2] A2[i2, b]  (A: MN-major view, M = i1, K = i2)
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+          uint64_t ad = smem_desc(tile + kk * 2048, HALF_BYTES, 1024);
+          uint64_t bd = smem_desc(b2 + (q2 * 2 + (kk >> 2)) * blk2 + (kk & 3) * 32, 16, 1024);
+          mma_bf16(d2, ad, bd, idesc2, kk > 0 ? 1u : 0u);
+        }
+        mma_commit(smem_u32(&mma_done[buf]));
+      }
+      // make sure the last committed MMAs have finished before TMEM is released
+      if (t > 0) {
+        const int tl = t - 1;
+        long long t0 = clock64();
+        while (!mbar_try_wait(smem_u32(&mma_done[tl & 1]), (tl >> 1) & 1) && clock64() - t0 < TIMEOUT_CYCLES) {
+        }
+      }
+      (void)ok;
+    }
+  } else if (warp < NUM_EPI_WARPS) {
+    // epilogue: TMEM lanes 32*warp .. 32*warp+31
+    int t = 0;
+    for (int u = blockIdx.x; u < P.nunits; u += gridDim.x, ++t) {
+      const int q1 = u % P.nq1, q2 = (u / P.nq1) % P.nq2, sl = u / (P.nq1 * P.nq2);
+      const int buf = t & 1;
+      if (!mbar_wait(smem_u32(&mma_done[buf]), (t >> 1) & 1, abort_flag, P.flags)) break;
+      tc_fence_after();
+      const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+      float v[32];
+      // Z1 partial: row i2
+      tmem_ld16(tmem_base + lane_base + buf * 64, v);
+      if (P.r1pad > 16) tmem_ld16(tmem_base + lane_base + buf * 64 + 16, v + 16);
+      const int i2 = q2 * TILE + 32 * warp + lane;
+      if (i2 < P.N2) {
+        float* dst = P.Z1p + (((size_t)q1 * P.nslice + sl) * P.N2 + i2) * P.r1;
+        for (int a = 0; a < P.r1; ++a) dst[a] = v[a];
+      }
+      // Z2 partial: row i1
+      tmem_ld16(tmem_base + lane_base + buf * 64 + 32, v);
+      if (P.r2pad > 16) tmem_ld16(tmem_base + lane_base + buf * 64 + 48, v + 16);
+      const int i1 = q1 * TILE + 32 * warp + lane;
+      if (i1 < P.N1) {
+        float* dst = P.Z2p + (((size_t)q2 * P.nslice + sl) * P.N1 + i1) * P.r2;
+        for (int b = 0; b < P.r2; ++b) dst[b] = v[b];
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&epi_done[buf]));
+    }
+  } else if (warp >= CONV_WARP0) {
+    // converter warp c owns stage c: sub-tiles (h = 0, strip c) and (h = 1, strip c) of every tile
+    const int c = warp - CONV_WARP0;
+    const int cx = lane & 15, ry = lane >> 4;
+    const int chunk = cx >> 1, hoff = (cx & 1) * 8;
+    int t = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x, ++t) {
+      const int q1 = u % P.nq1, q2 = (u / P.nq1) % P.nq2, sl = u / (P.nq1 * P.nq2);
+      const int buf = t & 1;
+      if (t >= 2 && !mbar_wait(smem_u32(&mma_done[buf]), ((t >> 1) - 1) & 1, abort_flag, P.flags)) break;
+      float acc = 0.f;
+      for (int h = 0; h < 2; ++h) {
+        const int use = 2 * t + h;
+        if (!mbar_wait(smem_u32(&full[c]), use & 1, abort_flag, P.flags)) { ok = false; break; }
+        const float4* vn = (const float4*)(stages + c * STAGE_BYTES);
+        const float4* vp = (const float4*)(stages + c * STAGE_BYTES + BOX_BYTES);
+        const int i1b = q1 * TILE + h * SUB_I1 + 4 * cx;
+        float w1v[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) w1v[e] = (i1b + e < P.N1) ? (float)P.w1[i1b + e] : 0.f;
+        unsigned char* half = bf_tiles + buf * BF_TILE_BYTES + h * HALF_BYTES;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+          const int row = ry + 2 * k;                 // 0..15 within the box
+          const float4 a = vn[row * 16 + cx];
+          const float4 b = vp[row * 16 + cx];
+          const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+          const int r = c * SUB_I2 + row;             // tile row (i2 within the tile)
+          const int i2 = q2 * TILE + r;
+          const float w2v = (i2 < P.N2) ? (float)P.w2[i2] : 0.f;
+          acc += w2v * (w1v[0] * d0 * d0 + w1v[1] * d1 * d1 + w1v[2] * d2 * d2 + w1v[3] * d3 * d3);
+          uint2 pk = make_uint2(pack_bf16x2(d0, d1), pack_bf16x2(d2, d3));
+          *(uint2*)(half + r * 128 + ((chunk ^ (r & 7)) << 4) + hoff) = pk;
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&empty[c]));
+      }
+      if (!ok) break;
+      acc_norm += (double)acc * P.wsl[sl];
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&bf_full[buf]));
+    }
+  }
+
+  // ||dV||_W^2 partial of this CTA (converter threads contribute, others add 0)
+  tc_fence_before();
+  __syncthreads();
+  {
+    double s = acc_norm;
+    s = warp_sum(s);
+    if (lane == 0) red[warp] = s;
+    __syncthreads();
+    if (tid == 0) {
+      double tot = 0.0;
+      for (int w = 0; w < NUM_WARPS; ++w) tot += red[w];
+      P.npart[blockIdx.x] = tot;
+    }
+  }
+  if (warp == MMA_WARP) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// ---------------------------------------------------------------------------
+// BF16 operand images of the weighted bases (K-major, 128-byte swizzle):
+// 64-row K blocks of rpad rows x 128 B; element (k, a) of block g at
+//   g*rpad*128 + a*128 + (((k/8) ^ (a%8)) * 16) + (k%8)*2.
+// ---------------------------------------------------------------------------
+__global__ void k_pack_bimg(const float* __restrict__ A, int N, int r, int rpad, int nblk,
+                            __nv_bfloat16* __restrict__ img) {
+  const int total = nblk * rpad * 64;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const int k = e % 64, a = (e / 64) % rpad, g = e / (64 * rpad);
+    const int i = g * 64 + k;
+    float v = (a < r && i < N) ? A[i + (int64_t)N * a] : 0.f;
+    const int off = g * rpad * 64 + a * 64 + (((k >> 3) ^ (a & 7)) << 3) + (k & 7);
+    img[off] = __float2bfloat16_rn(v);
+  }
+}
+
+// Z1 (r1 x N2 x S, column-major) and Z2 (N1 x r2 x S) from the tile partials.
+__global__ void k_tc_reduce(const float* __restrict__ Z1p, const float* __restrict__ Z2p, int N1, int N2, int nslice,
+                            int nq1, int nq2, int r1, int r2, float* __restrict__ Z1, float* __restrict__ Z2) {
+  const int64_t n1 = (int64_t)r1 * N2 * nslice, n2 = (int64_t)N1 * r2 * nslice;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n1 + n2; e += (int64_t)gridDim.x * blockDim.x) {
+    if (e < n1) {
+      // e = a + r1 (i2 + N2 s); partial index [q][s][i2][a] is the same offset within each q
+      float s = 0.f;
+      for (int q = 0; q < nq1; ++q) s += Z1p[q * n1 + e];
+      Z1[e] = s;
+    } else {
+      const int64_t f = e - n1;                  // f = i1 + N1 (b + r2 s)
+      const int64_t i1 = f % N1;
+      const int64_t bs = f / N1;
+      const int64_t b = bs % r2, sl = bs / r2;
+      float s = 0.f;
+      for (int q = 0; q < nq2; ++q) s += Z2p[((q * nslice + sl) * (int64_t)N1 + i1) * r2 + b];
+      Z2[f] = s;
+    }
+  }
+}
+
+__global__ void k_slice_weights(int p, const double* w3, int N3, const double* w4, int N4, double* out) {
+  int n = (p >= 3 ? N3 : 1) * (p >= 4 ? N4 : 1);
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
+    double v = 1.0;
+    if (p >= 3) v *= w3[s % N3];
+    if (p >= 4) v *= w4[s / N3];
+    out[s] = v;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+
+bool get_encoder(std::string& err) {
+  if (g_encode) return true;
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+    err = "cuTensorMapEncodeTiled unavailable";
+    return false;
+  }
+  g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  return true;
+}
+
+bool encode_map(CUtensorMap* tm, const float* base, int N1, int N2, int nslice, std::string& err) {
+  cuuint64_t dims[3] = {(cuuint64_t)N1, (cuuint64_t)N2, (cuuint64_t)nslice};
+  cuuint64_t strides[2] = {(cuuint64_t)N1 * 4, (cuuint64_t)N1 * N2 * 4};
+  cuuint32_t box[3] = {SUB_I1, SUB_I2, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    err = "cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")";
+    return false;
+  }
+  return true;
+}
+
+int rpad_of(int r) { return r <= 16 ? 16 : 32; }
+
+}  // namespace
+
+bool tc_supported(int p, const int64_t* N, const int* cap, std::string& err) {
+  if (p < 2 || p > 4) { err = "needs 2..4 modes"; return false; }
+  if (N[0] % 4 != 0) { err = "N_1 must be a multiple of 4 (16-byte TMA row stride)"; return false; }
+  if (cap[0] > 32 || cap[1] > 32) { err = "ranks of modes 1, 2 must be <= 32"; return false; }
+  int dev = 0, major = 0, minor = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+  cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+  if (major != 10) { err = "needs a compute capability 10.x GPU (tcgen05)"; return false; }
+  int nq1 = (int)((N[0] + TILE - 1) / TILE), nq2 = (int)((N[1] + TILE - 1) / TILE);
+  int b1 = nq1 * 2 * rpad_of(cap[0]) * 128, b2 = nq2 * 2 * rpad_of(cap[1]) * 128;
+  int fixed = 1024 + 2 * BF_TILE_BYTES + ((b1 + 1023) & ~1023) + ((b2 + 1023) & ~1023) + 512;
+  if (fixed + MAX_STAGES * STAGE_BYTES > kSmemLimit) { err = "basis images too large for shared memory"; return false; }
+  return get_encoder(err);
+}
+
+void tc_carve(TcPlan& plan, Carver& cv, int p, const int64_t* N, const int* cap) {
+  plan.p = p;
+  int64_t nslice = 1;
+  for (int n = 2; n < p; ++n) nslice *= N[n];
+  int nq1 = (int)((N[0] + TILE - 1) / TILE), nq2 = (int)((N[1] + TILE - 1) / TILE);
+  plan.Abf[0] = cv.take<char>((size_t)nq1 * 2 * rpad_of(cap[0]) * 128);
+  plan.Abf[1] = cv.take<char>((size_t)nq2 * 2 * rpad_of(cap[1]) * 128);
+  plan.z1p = cv.take<float>((size_t)nq1 * nslice * N[1] * cap[0]);
+  plan.z2p = cv.take<float>((size_t)nq2 * nslice * N[0] * cap[1]);
+  plan.wsl = cv.take<double>((size_t)nslice);
+  plan.npart = cv.take<double>(1024);
+}
+
+tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, const int64_t* N, const int* r,
+                      const void* const* A, const double* const* w, float* Z1, float* Z2, float* scratch,
+                      float* dS, float* const* Y, double* dv2, unsigned* flags, cudaStream_t s, cudaEvent_t* evm,
                       std::string& err) {
-  err = "not built yet";
-  return TDB_ERR_UNSUPPORTED;
+  if (!get_encoder(err)) return TDB_ERR_UNSUPPORTED;
+  const int N1 = (int)N[0], N2 = (int)N[1];
+  int nslice = 1;
+  for (int n = 2; n < p; ++n) nslice *= (int)N[n];
+  const int nq1 = (N1 + TILE - 1) / TILE, nq2 = (N2 + TILE - 1) / TILE;
+  const int r1pad = rpad_of(r[0]), r2pad = rpad_of(r[1]);
+  // operand images of A_1 = W_1 U_1 and A_2 = W_2 U_2 (refreshed every step)
+  {
+    int tot1 = nq1 * 2 * r1pad * 64, tot2 = nq2 * 2 * r2pad * 64;
+    k_pack_bimg<<<(tot1 + 255) / 256, 256, 0, s>>>((const float*)A[0], N1, r[0], r1pad, nq1 * 2,
+                                                   (__nv_bfloat16*)plan.Abf[0]);
+    count_launch();
+    k_pack_bimg<<<(tot2 + 255) / 256, 256, 0, s>>>((const float*)A[1], N2, r[1], r2pad, nq2 * 2,
+                                                   (__nv_bfloat16*)plan.Abf[1]);
+    count_launch();
+  }
+  if (!plan.wsl_ready) {
+    k_slice_weights<<<(nslice + 255) / 256, 256, 0, s>>>(p, p >= 3 ? w[2] : nullptr, p >= 3 ? (int)N[2] : 1,
+                                                         p >= 4 ? w[3] : nullptr, p >= 4 ? (int)N[3] : 1, plan.wsl);
+    count_launch();
+    plan.wsl_ready = true;
+  }
+  CUtensorMap tmn, tmp;
+  if (!encode_map(&tmn, Vn, N1, N2, nslice, err) || !encode_map(&tmp, Vp, N1, N2, nslice, err))
+    return TDB_ERR_UNSUPPORTED;
+  Params P;
+  memset(&P, 0, sizeof(P));
+  P.N1 = N1;
+  P.N2 = N2;
+  P.nslice = nslice;
+  P.nq1 = nq1;
+  P.nq2 = nq2;
+  P.r1 = r[0];
+  P.r2 = r[1];
+  P.r1pad = r1pad;
+  P.r2pad = r2pad;
+  P.nunits = nq1 * nq2 * nslice;
+  P.b1_bytes = nq1 * 2 * r1pad * 128;
+  P.b2_bytes = nq2 * 2 * r2pad * 128;
+  // 1 KB alignment slack for the 1024-byte swizzle atoms, then one stage per converter warp
+  int fixed = 1024 + 2 * BF_TILE_BYTES + ((P.b1_bytes + 1023) & ~1023) + ((P.b2_bytes + 1023) & ~1023) + 512;
+  P.nstages = MAX_STAGES;
+  if ((size_t)fixed + (size_t)P.nstages * STAGE_BYTES > (size_t)kSmemLimit) {
+    err = "shared memory budget exceeded";
+    return TDB_ERR_UNSUPPORTED;
+  }
+  size_t smem = (size_t)fixed + (size_t)P.nstages * STAGE_BYTES;
+  P.Z1p = plan.z1p;
+  P.Z2p = plan.z2p;
+  P.B1img = (const uint4*)plan.Abf[0];
+  P.B2img = (const uint4*)plan.Abf[1];
+  P.w1 = w[0];
+  P.w2 = w[1];
+  P.wsl = plan.wsl;
+  P.npart = plan.npart;
+  P.flags = flags;
+  if (!plan.attr_set) {
+    cudaFuncSetAttribute(k_tc_project, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    plan.attr_set = true;
+  }
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::min(P.nunits, std::min(nsm, 1024));
+  if (evm) cudaEventRecord(evm[0], s);
+  k_tc_project<<<grid, NUM_THREADS, smem, s>>>(tmn, tmp, P);
+  count_launch();
+  if (evm) cudaEventRecord(evm[1], s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    err = std::string("k_tc_project launch: ") + cudaGetErrorString(e);
+    return TDB_ERR_CUDA;
+  }
+  launch_sum_partials(plan.npart, grid, dv2, s);
+  // Z1 (r1 x N2 x S) and Z2 (N1 x r2 x S)
+  {
+    int64_t tot = (int64_t)r[0] * N2 * nslice + (int64_t)N1 * r[1] * nslice;
+    int blocks = (int)std::min<int64_t>((tot + 255) / 256, 152 * 8);
+    k_tc_reduce<<<blocks, 256, 0, s>>>(plan.z1p, plan.z2p, N1, N2, nslice, nq1, nq2, r[0], r[1], Z1, Z2);
+    count_launch();
+  }
+  // remaining contractions on rank-sized tensors (mode products, FP32)
+  auto mp = [&](const float* in, float* out, int n, int64_t* cur) {
+    int64_t L = 1, Q = 1;
+    for (int m = 0; m < n; ++m) L *= cur[m];
+    for (int m = n + 1; m < p; ++m) Q *= cur[m];
+    launch_modeprod<float, float, float>(in, out, (const float*)A[n], L, (int)cur[n], r[n], Q, N[n], 1, s);
+    cur[n] = r[n];
+  };
+  if (p == 2) {
+    cudaMemcpyAsync(Y[1], Z1, sizeof(float) * r[0] * N2, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(Y[0], Z2, sizeof(float) * N1 * r[1], cudaMemcpyDeviceToDevice, s);
+    int64_t cur[kMaxModes] = {r[0], N2, 1, 1};
+    mp(Y[1], dS, 1, cur);
+  } else if (p == 3) {
+    int64_t c1[kMaxModes] = {r[0], N2, N[2], 1};
+    mp(Z1, Y[1], 2, c1);                               // Y_2 = Z1 x_3 A_3^T
+    int64_t c2[kMaxModes] = {r[0], N2, N[2], 1};
+    mp(Z1, Y[2], 1, c2);                               // Y_3 = Z1 x_2 A_2^T
+    int64_t c3[kMaxModes] = {N1, r[1], N[2], 1};
+    mp(Z2, Y[0], 2, c3);                               // Y_1 = Z2 x_3 A_3^T
+    int64_t c4[kMaxModes] = {r[0], r[1], N[2], 1};
+    mp(Y[2], dS, 2, c4);                               // dS = Y_3 x_3 A_3^T
+  } else {
+    int64_t a[kMaxModes] = {r[0], N2, N[2], N[3]};
+    mp(Z1, scratch, 3, a);                             // Z1 x_4
+    mp(scratch, Y[1], 2, a);                           // Y_2 = (Z1 x_4) x_3
+    int64_t b[kMaxModes] = {r[0], N2, N[2], N[3]};
+    mp(Z1, scratch, 3, b);
+    mp(scratch, Y[2], 1, b);                           // Y_3 = (Z1 x_4) x_2
+    int64_t c[kMaxModes] = {r[0], N2, N[2], N[3]};
+    mp(Z1, scratch, 2, c);
+    mp(scratch, Y[3], 1, c);                           // Y_4 = (Z1 x_3) x_2
+    int64_t d[kMaxModes] = {N1, r[1], N[2], N[3]};
+    mp(Z2, scratch, 3, d);
+    mp(scratch, Y[0], 2, d);                           // Y_1 = (Z2 x_4) x_3
+    int64_t f[kMaxModes] = {r[0], r[1], r[2], N[3]};
+    mp(Y[3], dS, 3, f);                                // dS = Y_4 x_4 A_4^T
+  }
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    err = std::string("projection finish: ") + cudaGetErrorString(e);
+    return TDB_ERR_CUDA;
+  }
+  return TDB_OK;
 }
 
 }  // namespace tdb

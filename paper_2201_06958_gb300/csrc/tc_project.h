@@ -9,15 +9,23 @@ namespace tdb {
 
 struct TcPlan {
   int p = 0;
-  void* Abf[kMaxModes] = {nullptr};   // bf16 weighted bases, swizzled operand images
-  float* zpart = nullptr;             // partial first-level contractions
-  size_t zpart_elems = 0;
+  void* Abf[2] = {nullptr, nullptr};  // BF16 operand images of A_1, A_2 (128-byte swizzled, K-major)
+  float* z1p = nullptr;               // [tiles along i1][slices][N2][r1] partial dV x_1 A_1^T
+  float* z2p = nullptr;               // [tiles along i2][slices][N1][r2] partial dV x_2 A_2^T
+  double* wsl = nullptr;              // product of the weights of modes >= 3, per slice
+  double* npart = nullptr;            // per-CTA ||dV||_W^2
+  bool wsl_ready = false;
+  bool attr_set = false;
 };
 
 bool tc_supported(int p, const int64_t* N, const int* cap, std::string& err);
 void tc_carve(TcPlan& plan, Carver& cv, int p, const int64_t* N, const int* cap);
+// dS and Y_n of dV = Vn - Vp (Eqs. 2.15, 2.16) and ||dV||_W^2 into *dv2.  A: FP32
+// weighted bases (N_n x r_n); w: mode weights; Z1 (r1 x N2 x S), Z2 (N1 x r2 x S)
+// and scratch (>= the largest intermediate) are device buffers of the caller.
 tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, const int64_t* N, const int* r,
-                      const void* const* A, float* dS, float* const* Y, double* npart, int nblk,
-                      const WeightView& wv, double* dv2, unsigned* flags, cudaStream_t s, std::string& err);
+                      const void* const* A, const double* const* w, float* Z1, float* Z2, float* scratch,
+                      float* dS, float* const* Y, double* dv2, unsigned* flags, cudaStream_t s, cudaEvent_t* evm,
+                      std::string& err);
 
 }  // namespace tdb

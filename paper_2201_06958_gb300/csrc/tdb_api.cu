@@ -5,6 +5,7 @@
 // Eqs. 2.15/2.16; X_n = Y_(n) T_(n)^T (T_(n) T_(n)^T)^{-1}; dU_n = (I - U U^T W) X_n;
 // T += dS, U_n += dU_n (explicit Euler, dt cancels); weighted Cholesky-QR with core
 // compensation; error (Eq. 2.20) when scheduled; rank control (Sec. 2.5).
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -91,10 +92,14 @@ struct tdb_ctx {
   void* Cc;
   void* jA;
   void* jV;
-  void* jrin;
-  double* jred;
-  unsigned* jbar;
-  int* jsweeps;
+  void* siQ;
+  void* siZ;
+  void* siX;
+  double* siG;
+  double* siR;
+  void* siH;
+  void* siJA;
+  void* siJV;
   double* wpart;
   size_t wpart_cap = 0;
   double* ev[kMaxModes];
@@ -104,6 +109,10 @@ struct tdb_ctx {
   // BF16 tensor-core projection
   TcPlan tc;
   bool use_tc = false;
+  // profiling (CUDA events on the stream)
+  bool prof = false;
+  cudaEvent_t pev[6] = {nullptr};
+  tdb_profile pacc;
 
   // host state
   const void* V_prev = nullptr;
@@ -246,12 +255,17 @@ void carve(tdb_ctx* c, Carver& cv) {
   int64_t nn = (Nmax + 1) & ~1;
   c->C64 = cv.take<double>(Nmax * Nmax);
   c->Cc = cv.take<char>(Nmax * Nmax * tsz);
-  c->jA = cv.take<char>(nn * nn * tsz);
-  c->jV = cv.take<char>(nn * nn * tsz);
-  c->jrin = cv.take<char>(3 * nn * tsz);
-  c->jred = cv.take<double>(2 * 2048);
-  c->jbar = cv.take<unsigned>(2);
-  c->jsweeps = cv.take<int>(1);
+  int64_t nsmall = std::min<int64_t>(nn, 96);
+  c->jA = cv.take<char>(nsmall * nsmall * tsz);
+  c->jV = cv.take<char>(nsmall * nsmall * tsz);
+  c->siQ = cv.take<char>(Nmax * 64 * tsz);
+  c->siZ = cv.take<char>(Nmax * 64 * tsz);
+  c->siX = cv.take<char>(Nmax * 64 * tsz);
+  c->siG = cv.take<double>(64 * 64);
+  c->siR = cv.take<double>(64 * 64);
+  c->siH = cv.take<char>(64 * 64 * tsz);
+  c->siJA = cv.take<char>(64 * 64 * tsz);
+  c->siJV = cv.take<char>(64 * 64 * tsz);
   int ntile = (int)((Nmax + 31) / 32);
   c->wpart_cap = (size_t)(ntile * (ntile + 1) / 2) * 8 * 1024;
   c->wpart = cv.take<double>(c->wpart_cap);
@@ -330,7 +344,7 @@ WeightView weight_view(const tdb_ctx* c) {
 // Projection (Eqs. 2.15, 2.16) by mode products on the unfused path
 // ---------------------------------------------------------------------------
 template <typename Tc>
-tdb_status project_tree(tdb_ctx* ctx, const Tc* dV) {
+tdb_status project_tree(tdb_ctx* ctx, const Tc* dV, cudaEvent_t* evm) {
   const int p = ctx->p;
   cudaStream_t s = ctx->stream;
   int64_t dims[kMaxModes];
@@ -345,7 +359,9 @@ tdb_status project_tree(tdb_ctx* ctx, const Tc* dV) {
   Tc* pong = (Tc*)ctx->pong;
   // Z1 = dV x_1 A_1^T, then each Y_n (n >= 2) contracts the remaining modes but n
   for (int m = 0; m < p; ++m) dims[m] = ctx->N[m];
+  if (evm) cudaEventRecord(evm[0], s);
   mp(dV, ping, 0, dims);
+  if (evm) cudaEventRecord(evm[1], s);
   int64_t z1dims[kMaxModes];
   for (int m = 0; m < p; ++m) z1dims[m] = dims[m];
   for (int n = 1; n < p; ++n) {
@@ -477,10 +493,12 @@ tdb_status hosvd_spectrum(tdb_ctx* ctx, const Tc* V) {
     if (Nn <= 96)
       st = eig_leading_small<Tc>((const Tc*)ctx->Cc, ctx->C64, Nn, ctx->kcap[n], (Tc*)ctx->jA, (Tc*)ctx->jV,
                                  ctx->flags, ctx->ev[n], ctx->Qeig[n], ctx->trace + n, ctx->eigscratch, s);
-    else
-      st = eig_leading<Tc>((const Tc*)ctx->Cc, ctx->C64, Nn, ctx->kcap[n], (Tc*)ctx->jA, (Tc*)ctx->jV, (Tc*)ctx->jrin,
-                           ctx->jred, ctx->jbar, ctx->flags, ctx->jsweeps, ctx->ev[n], ctx->Qeig[n], ctx->trace + n,
-                           ctx->eigscratch, s);
+    else {
+      SubspaceWs<Tc> ws{(Tc*)ctx->siQ, (Tc*)ctx->siZ, (Tc*)ctx->siX, ctx->siG, ctx->siR,
+                        (Tc*)ctx->siH, (Tc*)ctx->siJA, (Tc*)ctx->siJV};
+      st = eig_subspace<Tc>((const Tc*)ctx->Cc, ctx->C64, Nn, ctx->kcap[n], 24, ws, ctx->flags, ctx->ev[n],
+                            ctx->Qeig[n], ctx->trace + n, ctx->eigscratch, s);
+    }
     if (st != TDB_OK) { ctx->err = "eigensolver launch failed"; return st; }
     CHECK_LAUNCH();
   }
@@ -493,7 +511,7 @@ tdb_status hosvd_spectrum(tdb_ctx* ctx, const Tc* V) {
   unsigned fl = 0;
   CK(cudaMemcpyAsync(&fl, ctx->flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
   CK(cudaStreamSynchronize(s));
-  if (fl & kFlagTimeout) { ctx->err = "eigensolver grid barrier timed out"; return TDB_ERR_TIMEOUT; }
+  if (fl & kFlagTimeout) { ctx->err = "eigensolver wait timed out"; return TDB_ERR_TIMEOUT; }
   return TDB_OK;
 }
 
@@ -689,18 +707,22 @@ tdb_status step_impl(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
   const Tc* Vp = (const Tc*)ctx->V_prev;
   const int p = ctx->p;
   CK(cudaMemsetAsync(ctx->rb_dev, 0, sizeof(Readback), s));
+  cudaEvent_t* ev = ctx->prof ? ctx->pev : nullptr;
+  if (ev) CK(cudaEventRecord(ev[0], s));
   // a1 + a2: difference and projection
   if (ctx->use_tc) {
     TRY(tc_project(ctx->tc, (const float*)Vn, (const float*)Vp, ctx->p, ctx->N, ctx->r, (const void* const*)ctx->A,
-                   (float*)ctx->dS, (float* const*)ctx->Y, ctx->npart, ctx->nblk, weight_view(ctx),
-                   &ctx->rb_dev->dv2, ctx->flags, s, ctx->err));
+                   (const double* const*)ctx->w, (float*)ctx->ping, (float*)ctx->pong, (float*)ctx->dV,
+                   (float*)ctx->dS, (float* const*)ctx->Y, &ctx->rb_dev->dv2, ctx->flags, s, ev ? ev + 4 : nullptr,
+                   ctx->err));
   } else {
     launch_diff<Tc>(Vn, Vp, (Tc*)ctx->dV, ctx->S, s);
     launch_wnorm2<Tc>((const Tc*)ctx->dV, nullptr, weight_view(ctx), ctx->npart, ctx->nblk, &ctx->rb_dev->dv2,
                       ctx->flags, s);
     CHECK_LAUNCH();
-    TRY(project_tree<Tc>(ctx, (const Tc*)ctx->dV));
+    TRY(project_tree<Tc>(ctx, (const Tc*)ctx->dV, ev ? ev + 4 : nullptr));
   }
+  if (ev) CK(cudaEventRecord(ev[1], s));
   // a3..a6: pseudo-inverse, complement projection, Euler, Cholesky-QR (bases)
   RowArgs a;
   memset(&a, 0, sizeof(a));
@@ -740,6 +762,7 @@ tdb_status step_impl(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
   }
   CHECK_LAUNCH();
   TRY(refresh_derived<Tc>(ctx, false));
+  if (ev) CK(cudaEventRecord(ev[2], s));
   // a7: error
   ctx->step++;
   bool exact = false;
@@ -750,7 +773,21 @@ tdb_status step_impl(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
     default: exact = false;
   }
   if (exact) TRY(exact_error2<Tc>(ctx, Vn));
+  if (ev) CK(cudaEventRecord(ev[3], s));
   TRY(readback(ctx));
+  if (ev) {
+    float m01 = 0, m12 = 0, m23 = 0, m45 = 0;
+    CK(cudaEventElapsedTime(&m01, ev[0], ev[1]));
+    CK(cudaEventElapsedTime(&m12, ev[1], ev[2]));
+    CK(cudaEventElapsedTime(&m23, ev[2], ev[3]));
+    CK(cudaEventElapsedTime(&m45, ev[4], ev[5]));
+    ctx->pacc.steps++;
+    ctx->pacc.ms_project += m01;
+    ctx->pacc.ms_update += m12;
+    ctx->pacc.ms_error += m23;
+    ctx->pacc.ms_project_main += m45;
+    ctx->pacc.launches_main++;
+  }
   if (ctx->rb.flags & kFlagNonFinite) { ctx->err = "non-finite value in a snapshot difference"; return TDB_ERR_NONFINITE; }
   if (ctx->rb.flags & kFlagCholGram) { ctx->err = "T_(n) T_(n)^T is not positive definite"; return TDB_ERR_RANK_DEFICIENT; }
   if (ctx->rb.flags & kFlagCholQR) { ctx->err = "U^T W U is not positive definite"; return TDB_ERR_RANK_DEFICIENT; }
@@ -764,7 +801,10 @@ tdb_status step_impl(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
   int n_re = 0, action = ACT_NONE;
   tdb_status cs = TDB_OK;
   if (exact) {
+    auto t0 = std::chrono::steady_clock::now();
     cs = control<Tc>(ctx, Vn, eps, &eps_after, &n_re, &action);
+    if (ctx->prof)
+      ctx->pacc.ms_control += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (cs != TDB_OK) return cs;
     if (n_re > 0) {
       TRY(readback(ctx));   // sigma of the new state
@@ -1111,7 +1151,31 @@ const char* tdb_status_string(tdb_status s) {
   return "unknown status";
 }
 
-void tdb_destroy(tdb_ctx* ctx) { delete ctx; }
+tdb_status tdb_set_profiling(tdb_ctx* ctx, int enable) {
+  if (!ctx) return TDB_ERR_INVALID_ARG;
+  if (enable) {
+    for (int i = 0; i < 6; ++i)
+      if (!ctx->pev[i]) CK(cudaEventCreate(&ctx->pev[i]));
+    memset(&ctx->pacc, 0, sizeof(ctx->pacc));
+  }
+  ctx->prof = enable != 0;
+  return TDB_OK;
+}
+
+tdb_status tdb_get_profile(tdb_ctx* ctx, tdb_profile* out) {
+  if (!ctx || !out) return TDB_ERR_INVALID_ARG;
+  *out = ctx->pacc;
+  return TDB_OK;
+}
+
+int64_t tdb_kernel_launches(void) { return (int64_t)tdb::launches_so_far(); }
+
+void tdb_destroy(tdb_ctx* ctx) {
+  if (!ctx) return;
+  for (int i = 0; i < 6; ++i)
+    if (ctx->pev[i]) cudaEventDestroy(ctx->pev[i]);
+  delete ctx;
+}
 
 const char* tdb_version(void) { return "tdb 0.1 sm_103a"; }
 
