@@ -112,13 +112,13 @@ __global__ void k_wnorm2_partial(const T* __restrict__ x, const T* __restrict__ 
     }
     const T* xc = x + c * N1;
     const T* yc = y ? y + c * N1 : nullptr;
-    double s = 0.0;
+    T s = 0;                 // per-thread partial over <= N1 / blockDim terms in the data type
     for (int64_t i = threadIdx.x; i < N1; i += blockDim.x) {
-      double d = (double)xc[i] - (yc ? (double)yc[i] : 0.0);
-      bad |= !isfinite(d);
-      s += wv.w[0][i] * d * d;
+      T d = xc[i] - (yc ? yc[i] : T(0));
+      bad |= !isfinite((double)d);
+      s += (T)wv.w[0][i] * d * d;
     }
-    acc += wc * s;
+    acc += wc * (double)s;
   }
   acc = block_sum(acc, sh);
   if (bad && flags) atomicOr(flags, kFlagNonFinite);
@@ -205,6 +205,35 @@ __global__ void k_mp_reduce_gen(const Tin* __restrict__ in, Tacc* __restrict__ o
   }
 }
 
+// K large, L * Q small: one warp per (l, q), lanes split k, JT accumulators.
+template <typename Tin, typename Tm, typename Tacc, int JT>
+__global__ void k_mp_reduce_warp(const Tin* __restrict__ in, Tacc* __restrict__ out, const Tm* __restrict__ M,
+                                 int64_t L, int K, int J, int64_t Q, int64_t sMj, int64_t sMk) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t w = warp; w < L * Q; w += nwarps) {
+    const int64_t l = w % L, q = w / L;
+    const Tin* base = in + l + L * K * q;
+    for (int j0 = 0; j0 < J; j0 += JT) {
+      Tacc acc[JT];
+#pragma unroll
+      for (int t = 0; t < JT; ++t) acc[t] = Tacc(0);
+      for (int k = lane; k < K; k += 32) {
+        Tacc v = (Tacc)base[(int64_t)k * L];
+#pragma unroll
+        for (int t = 0; t < JT; ++t)
+          if (j0 + t < J) acc[t] += (Tacc)M[(j0 + t) * sMj + k * sMk] * v;
+      }
+#pragma unroll
+      for (int t = 0; t < JT; ++t) {
+        Tacc v = warp_sum(acc[t]);
+        if (lane == 0 && j0 + t < J) out[l + L * ((j0 + t) + (int64_t)J * q)] = v;
+      }
+    }
+  }
+}
+
 // K small: one thread per output element (l, j, q), l fastest.
 template <typename Tin, typename Tm, typename Tacc>
 __global__ void k_mp_expand(const Tin* __restrict__ in, Tacc* __restrict__ out, const Tm* __restrict__ M, int64_t L,
@@ -227,10 +256,19 @@ void launch_modeprod(const Tin* in, Tacc* out, const Tm* M, int64_t L, int K, in
                      int64_t sMk, cudaStream_t s) {
   if (L <= 0 || K <= 0 || J <= 0 || Q <= 0) return;
   count_launch();
-  if (K <= 32 && J >= K) {
+  if (K <= 64) {
     int64_t total = L * J * Q;
     int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
     k_mp_expand<Tin, Tm, Tacc><<<blocks, 256, 0, s>>>(in, out, M, L, K, J, Q, sMj, sMk);
+  } else if (L > 1 && L * Q <= 32768) {
+    int64_t warps = L * Q;
+    int blocks = (int)std::min<int64_t>((warps * 32 + 255) / 256, 152 * 32);
+    if (J <= 8)
+      k_mp_reduce_warp<Tin, Tm, Tacc, 8><<<blocks, 256, 0, s>>>(in, out, M, L, K, J, Q, sMj, sMk);
+    else if (J <= 16)
+      k_mp_reduce_warp<Tin, Tm, Tacc, 16><<<blocks, 256, 0, s>>>(in, out, M, L, K, J, Q, sMj, sMk);
+    else
+      k_mp_reduce_warp<Tin, Tm, Tacc, 32><<<blocks, 256, 0, s>>>(in, out, M, L, K, J, Q, sMj, sMk);
   } else if (L == 1) {
     int64_t warps = Q;
     int blocks = (int)std::min<int64_t>((warps * 32 + 255) / 256, 152 * 32);

@@ -182,19 +182,35 @@ __global__ void k_eig_final(const T* __restrict__ V, int ldv, int n, const doubl
   for (int i = threadIdx.x; i < n; i += blockDim.x) tr += C64[i + (int64_t)n * i];
   tr = block_sum(tr, red);
   if (threadIdx.x == 0) *trace_out = tr;
+  __shared__ double bv[32];
+  __shared__ int bi[32];
   for (int j = 0; j < k; ++j) {
     const T* v = V + (int64_t)ldv * ord[j];
     double nrm = 0.0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) nrm += (double)v[i] * (double)v[i];
+    double best = -1.0;
+    int ib = 0x7fffffff;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      double a = (double)v[i];
+      nrm += a * a;
+      a = fabs(a);
+      if (a > best || (a == best && i < ib)) { best = a; ib = i; }
+    }
     nrm = block_sum(nrm, red);
+    // block argmax of |v_i| (first index on ties)
+    for (int o = 16; o > 0; o >>= 1) {
+      double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      int oi = __shfl_xor_sync(0xffffffffu, ib, o);
+      if (ob > best || (ob == best && oi < ib)) { best = ob; ib = oi; }
+    }
+    if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = ib; }
+    __syncthreads();
     if (threadIdx.x == 0) {
-      double best = -1.0;
-      int ib = 0;
-      for (int i = 0; i < n; ++i) {
-        double a = fabs((double)v[i]);
-        if (a > best) { best = a; ib = i; }
-      }
-      imax = ib;
+      int nw = (blockDim.x + 31) >> 5;
+      double b0 = bv[0];
+      int i0 = bi[0];
+      for (int w = 1; w < nw; ++w)
+        if (bv[w] > b0 || (bv[w] == b0 && bi[w] < i0)) { b0 = bv[w]; i0 = bi[w]; }
+      imax = i0;
       ev_out[j] = rq[j];
     }
     __syncthreads();
@@ -259,31 +275,33 @@ __global__ void k_si_gemm(const T* __restrict__ C, const T* __restrict__ Q, T* _
   if (i0 + tx < n && j0 + ty < m) Z[(i0 + tx) + (int64_t)n * (j0 + ty)] = acc;
 }
 
-// G = X^T Y (m x m, double accumulation of chunks); X, Y: n x m, leading dim n.
+// G = X^T Y (m x m); X, Y: n x m, leading dim n.  One warp per entry, lanes over
+// rows (coalesced), partial sums in T, the warp total in double.
 template <typename T>
 __global__ void k_si_inner(const T* __restrict__ X, const T* __restrict__ Y, int n, int m, double* __restrict__ G) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < m * m; e += gridDim.x * blockDim.x) {
-    int a = e % m, b = e / m;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int e = warp; e < m * m; e += nw) {
+    const int a = e % m, b = e / m;
     const T* x = X + (int64_t)n * a;
     const T* y = Y + (int64_t)n * b;
-    double acc = 0.0;
-    for (int i0 = 0; i0 < n; i0 += 32) {
-      T s = 0;
-      int i1 = i0 + 32 < n ? i0 + 32 : n;
-      for (int i = i0; i < i1; ++i) s += x[i] * y[i];
-      acc += (double)s;
-    }
-    G[a + (int64_t)m * b] = acc;
+    T s = 0;
+    for (int i = lane; i < n; i += 32) s += x[i] * y[i];
+    double d = warp_sum((double)s);
+    if (lane == 0) G[a + (int64_t)m * b] = d;
   }
 }
 
-// Cholesky-QR factor of the Gram G = Z^T Z: with D = diag(G)^{1/2},
-// D^{-1} G D^{-1} = L L^T (a shift 1e-5 I is added if that fails), and
-// Rinv = D^{-1} L^{-T} so that Q = Z Rinv has (near) orthonormal columns.
+// Cholesky-QR factor of the Gram G = Z^T Z, in the working precision T: with
+// D = diag(G)^{1/2}, D^{-1} G D^{-1} = L L^T (a shift of 1e-5 or 1e-2 on the unit
+// diagonal is added if that fails), and Rinv = D^{-1} L^{-T} so that Q = Z Rinv
+// has (near) orthonormal columns.
+template <typename T>
 __global__ void k_si_cholinv(const double* __restrict__ G, int m, double* __restrict__ Rinv, unsigned* flags) {
-  extern __shared__ double sm[];
-  double* S = sm;              // m x m (ld 64)
-  double* Li = sm + 64 * 64;   // m x m (ld 64)
+  extern __shared__ unsigned char smraw_ci[];
+  T* S = (T*)smraw_ci;         // m x m (ld 64)
+  T* Li = S + 64 * 64;         // m x m (ld 64)
   __shared__ double d[64];
   __shared__ bool ok;
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
@@ -295,18 +313,18 @@ __global__ void k_si_cholinv(const double* __restrict__ G, int m, double* __rest
     double shift = attempt == 0 ? 0.0 : (attempt == 1 ? 1e-5 : 1e-2);
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
       int i = e % m, j = e / m;
-      S[i + 64 * j] = G[i + (int64_t)m * j] / (d[i] * d[j]) + (i == j ? shift : 0.0);
+      S[i + 64 * j] = (T)(G[i + (int64_t)m * j] / (d[i] * d[j]) + (i == j ? shift : 0.0));
     }
     __syncthreads();
-    bool good = chol_smem(S, 64, m, &ok);
+    bool good = chol_smem_t<T>(S, 64, m, &ok);
     if (good) break;
     if (attempt == 2 && threadIdx.x == 0) atomicOr(flags, kFlagEigNoConv);
   }
-  trinv_lower_smem(S, Li, 64, m);
+  trinv_lower_smem_t<T>(S, Li, 64, m);
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     int i = e % m, j = e / m;
     // Rinv = D^{-1} L^{-T}:  Rinv[i][j] = Li[j][i] / d[i]
-    Rinv[i + (int64_t)m * j] = (j >= i) ? Li[j + 64 * i] / d[i] : 0.0;
+    Rinv[i + (int64_t)m * j] = (j >= i) ? (double)Li[j + 64 * i] / d[i] : 0.0;
   }
 }
 
@@ -401,19 +419,19 @@ tdb_status eig_subspace(const T* Cc, const double* C64, int n, int k, int iters,
   dim3 ggrid((n + 31) / 32, (m + 7) / 8);
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(k_si_cholinv, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * (int)sizeof(double));
+    cudaFuncSetAttribute(k_si_cholinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * (int)sizeof(T));
     attr = true;
   }
   k_si_start<T><<<blocks_nm, 256, 0, s>>>(ws.Q, n, m); count_launch();
   for (int it = 0; it < iters; ++it) {
     k_si_gemm<T><<<ggrid, 256, 0, s>>>(Cc, ws.Q, ws.Z, n, m); count_launch();
-    k_si_inner<T><<<(m * m + 255) / 256, 256, 0, s>>>(ws.Z, ws.Z, n, m, ws.G); count_launch();
-    k_si_cholinv<<<1, 256, 2 * 64 * 64 * sizeof(double), s>>>(ws.G, m, ws.R, flags); count_launch();
+    k_si_inner<T><<<(m * m * 32 + 255) / 256, 256, 0, s>>>(ws.Z, ws.Z, n, m, ws.G); count_launch();
+    k_si_cholinv<T><<<1, 256, 2 * 64 * 64 * sizeof(T), s>>>(ws.G, m, ws.R, flags); count_launch();
     k_si_apply<T><<<blocks_nm, 256, 0, s>>>(ws.Z, ws.R, n, m, m, 1, ws.Q); count_launch();
   }
   // Rayleigh-Ritz
   k_si_gemm<T><<<ggrid, 256, 0, s>>>(Cc, ws.Q, ws.Z, n, m); count_launch();
-  k_si_inner<T><<<(m * m + 255) / 256, 256, 0, s>>>(ws.Q, ws.Z, n, m, ws.G); count_launch();
+  k_si_inner<T><<<(m * m * 32 + 255) / 256, 256, 0, s>>>(ws.Q, ws.Z, n, m, ws.G); count_launch();
   k_to_double_sym<T><<<(m * m + 255) / 256, 256, 0, s>>>(ws.G, m, ws.R); count_launch();
   k_to_T<T><<<(m * m + 255) / 256, 256, 0, s>>>(ws.R, ws.H, m * m); count_launch();
   size_t sm = (2 * 97 * 96 + 128 + 32) * sizeof(T) + 128 * sizeof(int);

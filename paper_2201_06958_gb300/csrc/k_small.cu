@@ -94,20 +94,26 @@ __global__ void k_gram_finish(ModeDesc d, const double* __restrict__ Gpart, int 
   for (int a = 0; a < r; ++a) scale = fmax(scale, G[a + LD * a]);
   if (scale <= 0.0) scale = 1.0;
   float* Vp = Vprev + (int64_t)n * LD * LD;
-  // A = Vp^T G Vp / scale (float) when warm, else G / scale
-  for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
-    int a = e % r, b = e / r;
-    double s = 0.0;
-    if (warm) {
-      for (int i = 0; i < r; ++i) {
-        double gi = 0.0;
-        for (int j = 0; j < r; ++j) gi += G[i + LD * j] * (double)Vp[j + LD * b];
-        s += (double)Vp[i + LD * a] * gi;
-      }
-    } else {
-      s = G[a + LD * b];
+  // A = Vp^T (G / scale) Vp in float when warm (two r^3 products through Vf as scratch), else G / scale
+  if (warm) {
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      int i = e % r, b = e / r;
+      float s = 0.f;
+      for (int j = 0; j < r; ++j) s += (float)(G[i + LD * j] / scale) * Vp[j + LD * b];
+      Vf[i + LD * b] = s;                        // G Vp
     }
-    Af[a + LD * b] = (float)(s / scale);
+    __syncthreads();
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      int a = e % r, b = e / r;
+      float s = 0.f;
+      for (int i = 0; i < r; ++i) s += Vp[i + LD * a] * Vf[i + LD * b];
+      Af[a + LD * b] = s;
+    }
+  } else {
+    for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
+      int a = e % r, b = e / r;
+      Af[a + LD * b] = (float)(G[a + LD * b] / scale);
+    }
   }
   __syncthreads();
   jacobi_smem<float>(Af, Vf, LD, r, 30, 1e-6f, csf, pq, redf);
@@ -181,17 +187,34 @@ __global__ void k_rows_mx(RowArgs a) {
   const int64_t L = prod_r_below(a.d, n), Q = prod_r_above(a.d, n);
   const Tc* Y = (const Tc*)a.Y[n];
   const Tc* T = (const Tc*)a.Tc;
-  if (ca < r) {
-    Tc s = Tc(0);
-    if (i < N) {
-      for (int64_t q = 0; q < Q; ++q) {
-        const Tc* yq = Y + L * (i + N * q);
-        const Tc* tq = T + L * (ca + (int64_t)r * q);
-        for (int64_t l = 0; l < L; ++l) s += yq[l] * tq[l];
+  // M[i, ca] = sum_c Y_(n)[i, c] T_(n)[ca, c] over column chunks of 32 staged in shared memory;
+  // column c = l + L q addresses Y[l + L (i + N q)] and T[l + L (ca + r q)]
+  __shared__ Tc Ysh[32][33];
+  __shared__ Tc Tsh[LD][33];
+  const int64_t ncol = L * Q;
+  Tc s = Tc(0);
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (int64_t c0 = 0; c0 < ncol; c0 += 32) {
+    {
+      const int64_t c = c0 + tx;
+      const int64_t ii = i0 + ty;
+      Tc vy = Tc(0), vt = Tc(0);
+      if (c < ncol) {
+        const int64_t l = c % L, q = c / L;
+        if (ii < N) vy = Y[l + L * (ii + N * q)];
+        if (ty < r) vt = T[l + L * (ty + (int64_t)r * q)];
       }
+      Ysh[ty][tx] = vy;
+      Tsh[ty][tx] = vt;
     }
-    Msh[li][ca] = (double)s;
+    __syncthreads();
+    if (ca < r) {
+#pragma unroll 8
+      for (int x = 0; x < 32; ++x) s += Ysh[li][x] * Tsh[ca][x];
+    }
+    __syncthreads();
   }
+  if (ca < r) Msh[li][ca] = (double)s;
   __syncthreads();
   if (ca < r) {
     double x = 0.0;

@@ -83,17 +83,18 @@ __device__ __noinline__ int jacobi_smem(T* A, T* V, int lda, int n, int max_swee
 
 // Cholesky of the SPD matrix S (r x r, shared, leading dim lda) in place: lower
 // factor L with S = L L^T.  Returns false if a pivot is not positive.
-__device__ __forceinline__ bool chol_smem(double* S, int lda, int r, bool* ok_sh) {
+template <typename T>
+__device__ __forceinline__ bool chol_smem_t(T* S, int lda, int r, bool* ok_sh) {
   if (threadIdx.x == 0) *ok_sh = true;
   __syncthreads();
   for (int k = 0; k < r; ++k) {
     if (threadIdx.x == 0) {
-      double d = S[k + lda * k];
-      if (!(d > 0.0)) { *ok_sh = false; d = 1.0; }
+      T d = S[k + lda * k];
+      if (!(d > T(0))) { *ok_sh = false; d = T(1); }
       S[k + lda * k] = sqrt(d);
     }
     __syncthreads();
-    double dk = S[k + lda * k];
+    T dk = S[k + lda * k];
     for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) S[i + lda * k] /= dk;
     __syncthreads();
     for (int e = threadIdx.x; e < (r - k - 1) * (r - k - 1); e += blockDim.x) {
@@ -104,23 +105,28 @@ __device__ __forceinline__ bool chol_smem(double* S, int lda, int r, bool* ok_sh
   }
   for (int e = threadIdx.x; e < r * r; e += blockDim.x) {
     int i = e % r, j = e / r;
-    if (j > i) S[i + lda * j] = 0.0;
+    if (j > i) S[i + lda * j] = T(0);
   }
   __syncthreads();
   return *ok_sh;
 }
+__device__ __forceinline__ bool chol_smem(double* S, int lda, int r, bool* ok_sh) { return chol_smem_t<double>(S, lda, r, ok_sh); }
 
 // Inverse of the lower-triangular L (shared) into Li (shared): column j solves L x = e_j.
-__device__ __forceinline__ void trinv_lower_smem(const double* L, double* Li, int lda, int r) {
+template <typename T>
+__device__ __forceinline__ void trinv_lower_smem_t(const T* L, T* Li, int lda, int r) {
   for (int j = threadIdx.x; j < r; j += blockDim.x) {
     for (int i = 0; i < r; ++i) {
-      if (i < j) { Li[i + lda * j] = 0.0; continue; }
-      double s = (i == j) ? 1.0 : 0.0;
+      if (i < j) { Li[i + lda * j] = T(0); continue; }
+      T s = (i == j) ? T(1) : T(0);
       for (int k = j; k < i; ++k) s -= L[i + lda * k] * Li[k + lda * j];
       Li[i + lda * j] = s / L[i + lda * i];
     }
   }
   __syncthreads();
+}
+__device__ __forceinline__ void trinv_lower_smem(const double* L, double* Li, int lda, int r) {
+  trinv_lower_smem_t<double>(L, Li, lda, r);
 }
 
 }  // namespace tdb
