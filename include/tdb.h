@@ -48,7 +48,7 @@ extern "C" {
 typedef enum tdb_status {
   TDB_OK = 0,
   TDB_ERR_INVALID_ARG = 1,     /* null pointer, bad enum, bad threshold */
-  TDB_ERR_SHAPE = 2,           /* ndim outside 2..4, a mode size outside 1..1024 */
+  TDB_ERR_SHAPE = 2,           /* ndim outside 2..4, a mode size outside 1..1024, >= 2^31 elements */
   TDB_ERR_RANK = 3,            /* a rank outside 1..min(N_n, prod_{m!=n} r_m, TDB_MAX_RANK) */
   TDB_ERR_RANK_DEFICIENT = 4,  /* T_(n) T_(n)^T or U^T W U not positive definite */
   TDB_ERR_NONFINITE = 5,       /* NaN or Inf in a snapshot or in the state */

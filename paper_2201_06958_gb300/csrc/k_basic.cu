@@ -39,10 +39,9 @@ template void launch_diff<double>(const double*, const double*, double*, int64_t
 template <typename T>
 __global__ void k_weighted_bases(const double* __restrict__ U, const double* __restrict__ w, T* __restrict__ A,
                                  int64_t N, int r) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < N * r; e += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = e % N;
-    A[e] = (T)(w[i] * U[e]);
-  }
+  const unsigned n = (unsigned)N, tot = (unsigned)(N * r);
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += gridDim.x * blockDim.x)
+    A[e] = (T)(w[e % n] * U[e]);
 }
 
 template <typename T>
@@ -104,11 +103,11 @@ __global__ void k_wnorm2_partial(const T* __restrict__ x, const T* __restrict__ 
   bool bad = false;
   for (int64_t c = blockIdx.x; c < ncol; c += gridDim.x) {
     double wc = 1.0;
-    int64_t rem = c;
+    unsigned rem = (unsigned)c;
     for (int m = 1; m < wv.p; ++m) {
-      int64_t im = rem % wv.N[m];
-      rem /= wv.N[m];
-      wc *= wv.w[m][im];
+      const unsigned nm = (unsigned)wv.N[m];
+      wc *= wv.w[m][rem % nm];
+      rem /= nm;
     }
     const T* xc = x + c * N1;
     const T* yc = y ? y + c * N1 : nullptr;
@@ -143,6 +142,64 @@ template void launch_wnorm2<float>(const float*, const float*, const WeightView&
                                    cudaStream_t);
 template void launch_wnorm2<double>(const double*, const double*, const WeightView&, double*, int, double*,
                                     unsigned*, cudaStream_t);
+
+// Exact error of Eq. 2.20 without materialising V^TDB: with H = T x_2 U_2 ... x_p U_p
+// (r_1 x N_2 x ... x N_p), every mode-1 column of the reconstruction is U_1 H[:, c];
+// each block takes whole columns, forms V - U_1 H[:, c] in the data type and
+// accumulates w_1(i_1) w_c (V - V^TDB)^2 (float partials per column, double across).
+template <typename T>
+__global__ void k_recon_err(const T* __restrict__ V, const T* __restrict__ U1, const T* __restrict__ H, int r1,
+                            WeightView wv, double* __restrict__ partial, unsigned* flags) {
+  __shared__ T hcol[32];
+  __shared__ double sh[32];
+  __shared__ double wcs;
+  const unsigned N1 = (unsigned)wv.N[0];
+  unsigned ncol = 1;
+  for (int m = 1; m < wv.p; ++m) ncol *= (unsigned)wv.N[m];
+  double acc = 0.0;
+  bool bad = false;
+  for (unsigned c = blockIdx.x; c < ncol; c += gridDim.x) {
+    if (threadIdx.x < (unsigned)r1) hcol[threadIdx.x] = H[threadIdx.x + (size_t)r1 * c];
+    if (threadIdx.x == 32) {
+      double wc = 1.0;
+      unsigned rem = c;
+      for (int m = 1; m < wv.p; ++m) {
+        const unsigned nm = (unsigned)wv.N[m];
+        wc *= wv.w[m][rem % nm];
+        rem /= nm;
+      }
+      wcs = wc;
+    }
+    __syncthreads();
+    const T* vc = V + (size_t)N1 * c;
+    T s = 0;
+    for (unsigned i = threadIdx.x; i < N1; i += blockDim.x) {
+      T rec = 0;
+      for (int a = 0; a < r1; ++a) rec += U1[i + (size_t)N1 * a] * hcol[a];
+      T d = vc[i] - rec;
+      bad |= !isfinite((double)d);
+      s += (T)wv.w[0][i] * d * d;
+    }
+    acc += wcs * (double)s;
+    __syncthreads();
+  }
+  acc = block_sum(acc, sh);
+  if (bad && flags) atomicOr(flags, kFlagNonFinite);
+  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
+}
+
+template <typename T>
+void launch_recon_err(const T* V, const T* U1, const T* H, int r1, const WeightView& wv, double* partial, int nblocks,
+                      double* out, unsigned* flags, cudaStream_t s) {
+  k_recon_err<T><<<nblocks, 256, 0, s>>>(V, U1, H, r1, wv, partial, flags);
+  count_launch();
+  k_sum_partials<<<1, 256, 0, s>>>(partial, nblocks, out);
+  count_launch();
+}
+template void launch_recon_err<float>(const float*, const float*, const float*, int, const WeightView&, double*, int,
+                                      double*, unsigned*, cudaStream_t);
+template void launch_recon_err<double>(const double*, const double*, const double*, int, const WeightView&, double*,
+                                       int, double*, unsigned*, cudaStream_t);
 
 void launch_sum_partials(const double* partial, int n, double* out, cudaStream_t s) {
   k_sum_partials<<<1, 256, 0, s>>>(partial, n, out); count_launch();
@@ -184,10 +241,10 @@ __global__ void k_mp_reduce_col(const Tin* __restrict__ in, Tacc* __restrict__ o
 template <typename Tin, typename Tm, typename Tacc, int JT>
 __global__ void k_mp_reduce_gen(const Tin* __restrict__ in, Tacc* __restrict__ out, const Tm* __restrict__ M,
                                 int64_t L, int K, int J, int64_t Q, int64_t sMj, int64_t sMk) {
-  const int64_t total = L * Q;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t l = e % L, q = e / L;
-    const Tin* base = in + l + L * K * q;
+  const unsigned total = (unsigned)(L * Q), uL = (unsigned)L;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const unsigned l = e % uL, q = e / uL;
+    const Tin* base = in + l + (size_t)uL * K * q;
     for (int j0 = 0; j0 < J; j0 += JT) {
       Tacc acc[JT];
 #pragma unroll
@@ -212,9 +269,10 @@ __global__ void k_mp_reduce_warp(const Tin* __restrict__ in, Tacc* __restrict__ 
   const int lane = threadIdx.x & 31;
   const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const unsigned uL = (unsigned)L;
   for (int64_t w = warp; w < L * Q; w += nwarps) {
-    const int64_t l = w % L, q = w / L;
-    const Tin* base = in + l + L * K * q;
+    const unsigned l = (unsigned)w % uL, q = (unsigned)w / uL;
+    const Tin* base = in + l + (size_t)uL * K * q;
     for (int j0 = 0; j0 < J; j0 += JT) {
       Tacc acc[JT];
 #pragma unroll
@@ -234,19 +292,56 @@ __global__ void k_mp_reduce_warp(const Tin* __restrict__ in, Tacc* __restrict__ 
   }
 }
 
+// K large, very few (l, q): one block per (l, q), threads split k, block reduction.
+template <typename Tin, typename Tm, typename Tacc, int JT>
+__global__ void k_mp_reduce_block(const Tin* __restrict__ in, Tacc* __restrict__ out, const Tm* __restrict__ M,
+                                  int64_t L, int K, int J, int64_t Q, int64_t sMj, int64_t sMk) {
+  __shared__ Tacc sh[JT][33];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const unsigned uL = (unsigned)L;
+  for (unsigned w = blockIdx.x; w < (unsigned)(L * Q); w += gridDim.x) {
+    const unsigned l = w % uL, q = w / uL;
+    const Tin* base = in + l + (size_t)uL * K * q;
+    for (int j0 = 0; j0 < J; j0 += JT) {
+      Tacc acc[JT];
+#pragma unroll
+      for (int t = 0; t < JT; ++t) acc[t] = Tacc(0);
+      for (int k = threadIdx.x; k < K; k += blockDim.x) {
+        Tacc v = (Tacc)base[(size_t)k * uL];
+#pragma unroll
+        for (int t = 0; t < JT; ++t)
+          if (j0 + t < J) acc[t] += (Tacc)M[(j0 + t) * sMj + k * sMk] * v;
+      }
+#pragma unroll
+      for (int t = 0; t < JT; ++t) {
+        Tacc v = warp_sum(acc[t]);
+        if (lane == 0) sh[t][wid] = v;
+      }
+      __syncthreads();
+      if (threadIdx.x < JT && j0 + (int)threadIdx.x < J) {
+        Tacc v = Tacc(0);
+        for (int x = 0; x < nw; ++x) v += sh[threadIdx.x][x];
+        out[l + uL * ((j0 + threadIdx.x) + (size_t)J * q)] = v;
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // K small: one thread per output element (l, j, q), l fastest.
 template <typename Tin, typename Tm, typename Tacc>
 __global__ void k_mp_expand(const Tin* __restrict__ in, Tacc* __restrict__ out, const Tm* __restrict__ M, int64_t L,
                             int K, int J, int64_t Q, int64_t sMj, int64_t sMk) {
-  const int64_t total = L * J * Q;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t l = e % L;
-    const int64_t jq = e / L;
-    const int j = (int)(jq % J);
-    const int64_t q = jq / J;
-    const Tin* base = in + l + L * K * q;
+  const unsigned total = (unsigned)(L * J * Q), uL = (unsigned)L, uJ = (unsigned)J;
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
+    const unsigned l = e % uL;
+    const unsigned jq = e / uL;
+    const unsigned j = jq % uJ;
+    const unsigned q = jq / uJ;
+    const Tin* base = in + l + (size_t)uL * K * q;
+    const Tm* mrow = M + j * sMj;
     Tacc acc = Tacc(0);
-    for (int k = 0; k < K; ++k) acc += (Tacc)M[j * sMj + k * sMk] * (Tacc)base[(int64_t)k * L];
+    for (int k = 0; k < K; ++k) acc += (Tacc)mrow[k * sMk] * (Tacc)base[(size_t)k * uL];
     out[e] = acc;
   }
 }
@@ -260,6 +355,14 @@ void launch_modeprod(const Tin* in, Tacc* out, const Tm* M, int64_t L, int K, in
     int64_t total = L * J * Q;
     int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
     k_mp_expand<Tin, Tm, Tacc><<<blocks, 256, 0, s>>>(in, out, M, L, K, J, Q, sMj, sMk);
+  } else if (L > 1 && L * Q <= 1024) {
+    int blocks = (int)std::min<int64_t>(L * Q, 152 * 8);
+    if (J <= 8)
+      k_mp_reduce_block<Tin, Tm, Tacc, 8><<<blocks, 256, 0, s>>>(in, out, M, L, K, J, Q, sMj, sMk);
+    else if (J <= 16)
+      k_mp_reduce_block<Tin, Tm, Tacc, 16><<<blocks, 256, 0, s>>>(in, out, M, L, K, J, Q, sMj, sMk);
+    else
+      k_mp_reduce_block<Tin, Tm, Tacc, 32><<<blocks, 256, 0, s>>>(in, out, M, L, K, J, Q, sMj, sMk);
   } else if (L > 1 && L * Q <= 32768) {
     int64_t warps = L * Q;
     int blocks = (int)std::min<int64_t>((warps * 32 + 255) / 256, 152 * 32);

@@ -22,6 +22,20 @@ namespace tdb {
 
 constexpr int LD = kMaxRank;  // leading dimension of r x r matrices
 
+// sum_{k < n} p[k * stride] with four independent accumulators (fixed order, loads in flight)
+__device__ __forceinline__ double sum_strided(const double* __restrict__ p, int n, int64_t stride) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int k = 0;
+  for (; k + 4 <= n; k += 4) {
+    s0 += p[(int64_t)k * stride];
+    s1 += p[(int64_t)(k + 1) * stride];
+    s2 += p[(int64_t)(k + 2) * stride];
+    s3 += p[(int64_t)(k + 3) * stride];
+  }
+  for (; k < n; ++k) s0 += p[(int64_t)k * stride];
+  return (s0 + s1) + (s2 + s3);
+}
+
 // ---------------------------------------------------------------------------
 // G_n = T_(n) T_(n)^T : partial sums over slices of the column range (p modes at once)
 // ---------------------------------------------------------------------------
@@ -71,7 +85,7 @@ __global__ void k_gram_finish(ModeDesc d, const double* __restrict__ Gpart, int 
     double s = 0.0;
     if (a < r && b < r) {
       int aa = a <= b ? a : b, bb = a <= b ? b : a;
-      for (int k = 0; k < nsplit; ++k) s += Gpart[((int64_t)n * nsplit + k) * LD * LD + aa + LD * bb];
+      s = sum_strided(Gpart + (int64_t)n * nsplit * LD * LD + aa + LD * bb, nsplit, LD * LD);
     }
     G[e] = s;
     Lc[e] = s;
@@ -243,8 +257,7 @@ __global__ void k_sum_tiles(ModeDesc d, const double* __restrict__ part, int nti
   for (int e = threadIdx.x; e < LD * LD; e += blockDim.x) {
     int a = e % LD, b = e / LD;
     double s = 0.0;
-    if (a < r && b < r)
-      for (int t = 0; t < nt; ++t) s += part[(((int64_t)n * ntile) + t) * LD * LD + e];
+    if (a < r && b < r) s = sum_strided(part + (int64_t)n * ntile * LD * LD + e, nt, LD * LD);
     out[(int64_t)n * LD * LD + e] = s;
   }
 }
@@ -296,8 +309,7 @@ __global__ void k_cholqr_small(ModeDesc d, const double* __restrict__ part, int 
   for (int e = threadIdx.x; e < LD * LD; e += blockDim.x) {
     int a = e % LD, b = e / LD;
     double s = 0.0;
-    if (a < r && b < r)
-      for (int t = 0; t < nt; ++t) s += part[(((int64_t)n * ntile) + t) * LD * LD + e];
+    if (a < r && b < r) s = sum_strided(part + (int64_t)n * ntile * LD * LD + e, nt, LD * LD);
     C[e] = s;
   }
   __syncthreads();

@@ -247,7 +247,7 @@ void carve(tdb_ctx* c, Carver& cv) {
   c->sig2 = cv.take<double>(p * kMaxRank);
   c->Vprev = cv.take<float>(p * kMaxRank * kMaxRank);
   c->Vprev_bak = cv.take<float>(p * kMaxRank * kMaxRank);
-  c->nblk = 512;
+  c->nblk = 608;
   c->npart = cv.take<double>(c->nblk);
   c->rb_dev = cv.take<Readback>(1);
   c->flags = &c->rb_dev->flags;
@@ -286,6 +286,11 @@ tdb_status validate(const tdb_config* cfg, std::string& err) {
   if (cfg->ndim < 2 || cfg->ndim > kMaxModes) { err = "ndim must be 2..4"; return TDB_ERR_SHAPE; }
   for (int n = 0; n < cfg->ndim; ++n)
     if (cfg->dims[n] < 1 || cfg->dims[n] > 1024) { err = "mode sizes must be 1..1024"; return TDB_ERR_SHAPE; }
+  {
+    int64_t S = 1;
+    for (int n = 0; n < cfg->ndim; ++n) S *= cfg->dims[n];
+    if (S >= ((int64_t)1 << 31)) { err = "a snapshot must have fewer than 2^31 elements"; return TDB_ERR_SHAPE; }
+  }
   if (cfg->precision < TDB_FP64 || cfg->precision > TDB_BF16_TTM) { err = "bad precision"; return TDB_ERR_INVALID_ARG; }
   if (cfg->error_mode < TDB_ERRMODE_EXACT || cfg->error_mode > TDB_ERRMODE_NONE) {
     err = "bad error_mode";
@@ -424,11 +429,27 @@ tdb_status reconstruct_into(tdb_ctx* ctx, Tc* out) {
   return TDB_OK;
 }
 
+// err2 = ||V - T x U||_W^2 (Eq. 2.20): H = T x_2 U_2 ... x_p U_p, then the fused pass
+// over V that forms each mode-1 column U_1 H[:, c] on the fly.
 template <typename Tc>
 tdb_status exact_error2(tdb_ctx* ctx, const Tc* V) {
-  TRY(reconstruct_into<Tc>(ctx, (Tc*)ctx->rec));
-  launch_wnorm2<Tc>(V, (const Tc*)ctx->rec, weight_view(ctx), ctx->npart, ctx->nblk, &ctx->rb_dev->err2, ctx->flags,
-                    ctx->stream);
+  const int p = ctx->p;
+  cudaStream_t s = ctx->stream;
+  int64_t cur[kMaxModes];
+  for (int m = 0; m < p; ++m) cur[m] = ctx->r[m];
+  const Tc* src = (const Tc*)ctx->Tcore;
+  Tc* bufs[2] = {(Tc*)ctx->ping, (Tc*)ctx->pong};
+  for (int n = 1; n < p; ++n) {
+    Tc* dst = bufs[n & 1];
+    int64_t L = 1, Q = 1;
+    for (int m = 0; m < n; ++m) L *= cur[m];
+    for (int m = n + 1; m < p; ++m) Q *= cur[m];
+    launch_modeprod<Tc, Tc, Tc>(src, dst, (const Tc*)ctx->Uc[n], L, ctx->r[n], (int)ctx->N[n], Q, 1, ctx->N[n], s);
+    cur[n] = ctx->N[n];
+    src = dst;
+  }
+  launch_recon_err<Tc>(V, (const Tc*)ctx->Uc[0], src, ctx->r[0], weight_view(ctx), ctx->npart, ctx->nblk,
+                       &ctx->rb_dev->err2, ctx->flags, s);
   CHECK_LAUNCH();
   return TDB_OK;
 }
