@@ -197,6 +197,29 @@ tdb_status tdb_get_profile(tdb_ctx* ctx, tdb_profile* out);
 /* Number of libtdb kernels launched by this process so far (all contexts). */
 int64_t tdb_kernel_launches(void);
 
+/* Allocation-free form of the fused snapshot difference + projection (the kernels
+ * of the TDB_BF16_TTM step), for callers that cannot allocate device memory -
+ * e.g. a simulation code that hands every byte of the GPU to its own pool
+ * allocator, or runs where cudaMalloc is not allowed after start-up.  The paper
+ * has no counterpart: this is a packaging of the existing computation.
+ *   dims, ranks : host, ndim entries (2..4 modes; N_1 a multiple of 4; r_1, r_2 <= 32)
+ *   V_next, V_prev : device float snapshots (layout as above)
+ *   A[n] : device float N_n x r_n, the weighted bases W_n U_n; w[n] : device double, N_n
+ *   dS (prod r_n), Y[n] (the tensor with mode n of size N_n, other modes r_m) and
+ *   dv2 (||V_next - V_prev||_W^2, one double): device outputs owned by the caller.
+ * Scratch comes from a static device array of 16 MiB compiled into the library
+ * (held by every GPU that loads it until process exit); sizes needing more are
+ * refused with TDB_ERR_WORKSPACE before anything is launched.  The call allocates
+ * nothing (no cudaMalloc or allocating library routine).  The first call on a
+ * device looks up the array's device address once for that device; make that first
+ * call before any stream capture.  All calls share the array and it keeps the last
+ * call's contents (every value read is written earlier in the same call), so calls
+ * that overlap on the GPU - on different streams or host threads - race.  The call
+ * synchronises `stream` and returns TDB_ERR_TIMEOUT if a bounded device wait ran out. */
+tdb_status tdb_project_noalloc(int ndim, const int64_t* dims, const int* ranks, const float* V_next,
+                               const float* V_prev, const float* const* A, const double* const* w, float* dS,
+                               float* const* Y, double* dv2, void* stream);
+
 /* Library version and build facts: "tdb <ver> sm_103a". */
 const char* tdb_version(void);
 

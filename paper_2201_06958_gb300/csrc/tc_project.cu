@@ -23,6 +23,7 @@
 #include <cudaTypedefs.h>
 
 #include <cstring>
+#include <mutex>
 
 #include "tc_project.h"
 
@@ -644,4 +645,87 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   return TDB_OK;
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the fused projection (see tdb_project_noalloc in
+// include/tdb.h).  Its scratch lives in this file-scope device array; host code
+// may not use the array's name as a device address, so the address is fetched
+// once per device with cudaGetSymbolAddress.
+// ---------------------------------------------------------------------------
+constexpr size_t kNoAllocScratchBytes = (size_t)16 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[64] = {nullptr};
+
+// Bytes of scratch the projection needs for these sizes, laid out by `lay`.
+size_t noalloc_layout(Carver& cv, TcPlan& plan, int p, const int64_t* N, const int* r, float** Z1, float** Z2,
+                      float** scratch, unsigned** status) {
+  *status = cv.take<unsigned>(64);
+  int cap[kMaxModes] = {r[0], r[1], p > 2 ? r[2] : 1, p > 3 ? r[3] : 1};
+  tc_carve(plan, cv, p, N, cap);
+  int64_t S = 1;
+  for (int n = 0; n < p; ++n) S *= N[n];
+  *Z1 = cv.take<float>((size_t)(S / N[0]) * r[0]);
+  *Z2 = cv.take<float>((size_t)(S / N[1]) * r[1]);
+  int64_t sc = 1;
+  for (int n = 0; n < p; ++n) sc = std::max<int64_t>(sc, S / N[n] * r[n]);
+  *scratch = cv.take<float>((size_t)sc);
+  return cv.off;
+}
+}  // namespace
+
 }  // namespace tdb
+
+extern "C" tdb_status tdb_project_noalloc(int ndim, const int64_t* dims, const int* ranks, const float* V_next,
+                                          const float* V_prev, const float* const* A, const double* const* w,
+                                          float* dS, float* const* Y, double* dv2, void* stream) {
+  using namespace tdb;
+  std::string err;
+  if (ndim < 2 || ndim > kMaxModes || !dims || !ranks || !V_next || !V_prev || !A || !w || !dS || !Y || !dv2)
+    return TDB_ERR_INVALID_ARG;
+  int64_t N[kMaxModes] = {1, 1, 1, 1};
+  int r[kMaxModes] = {1, 1, 1, 1};
+  for (int n = 0; n < ndim; ++n) {
+    N[n] = dims[n];
+    r[n] = ranks[n];
+    if (N[n] < 1 || N[n] > 1024) return TDB_ERR_SHAPE;
+    if (r[n] < 1 || r[n] > kMaxRank || r[n] > N[n] || !A[n] || !w[n] || !Y[n]) return TDB_ERR_RANK;
+  }
+  if (!tc_supported(ndim, N, r, err)) return TDB_ERR_UNSUPPORTED;
+  // sizes beyond the static scratch are refused before anything is launched
+  TcPlan plan;
+  float *Z1 = nullptr, *Z2 = nullptr, *scr = nullptr;
+  unsigned* status = nullptr;
+  {
+    Carver measure(nullptr);
+    if (noalloc_layout(measure, plan, ndim, N, r, &Z1, &Z2, &scr, &status) > kNoAllocScratchBytes)
+      return TDB_ERR_WORKSPACE;
+  }
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return TDB_ERR_CUDA;
+  void* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return TDB_ERR_CUDA;
+      g_noalloc_addr[dev] = ptr;
+    }
+    base = g_noalloc_addr[dev];
+  }
+  plan = TcPlan();
+  Carver cv(base);
+  noalloc_layout(cv, plan, ndim, N, r, &Z1, &Z2, &scr, &status);
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(status, 0, sizeof(unsigned), s) != cudaSuccess) return TDB_ERR_CUDA;
+  tdb_status st = tc_project(plan, V_next, V_prev, ndim, N, r, (const void* const*)A, w, Z1, Z2, scr, dS, Y, dv2,
+                             status, s, nullptr, err);
+  if (st != TDB_OK) return st;
+  unsigned h_status = 0;
+  if (cudaMemcpyAsync(&h_status, status, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return TDB_ERR_CUDA;
+  return (h_status & kFlagTimeout) ? TDB_ERR_TIMEOUT : TDB_OK;
+}

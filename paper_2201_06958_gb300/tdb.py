@@ -71,6 +71,7 @@ EXPORTS = [
     "tdb_workspace_bytes", "tdb_init", "tdb_init_from_factors", "tdb_push_snapshot", "tdb_reconstruct",
     "tdb_adapt_rank", "tdb_get_factors", "tdb_get_projection", "tdb_get_counters", "tdb_save_state",
     "tdb_load_state", "tdb_last_error", "tdb_status_string", "tdb_destroy", "tdb_version",
+    "tdb_set_profiling", "tdb_get_profile", "tdb_kernel_launches", "tdb_project_noalloc",
 ]
 
 
@@ -115,6 +116,15 @@ def load(path: str = LIB_PATH):
     lib.tdb_destroy.restype = None
     lib.tdb_version.argtypes = []
     lib.tdb_version.restype = C.c_char_p
+    lib.tdb_set_profiling.argtypes = [vp, C.c_int]
+    lib.tdb_set_profiling.restype = st
+    lib.tdb_get_profile.argtypes = [vp, vp]
+    lib.tdb_get_profile.restype = st
+    lib.tdb_kernel_launches.argtypes = []
+    lib.tdb_kernel_launches.restype = C.c_int64
+    lib.tdb_project_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int), vp, vp,
+                                        C.POINTER(vp), C.POINTER(vp), vp, C.POINTER(vp), vp, vp]
+    lib.tdb_project_noalloc.restype = st
     _lib = lib
     return lib
 
@@ -306,3 +316,23 @@ class TDB:
             self.close()
         except Exception:
             pass
+
+
+def project_noalloc(dims, ranks, V_next: torch.Tensor, V_prev: torch.Tensor, A, w, dS: torch.Tensor,
+                    Y, dv2: torch.Tensor, stream=None) -> int:
+    """tdb_project_noalloc (include/tdb.h): the fused difference + projection into
+    caller-owned device outputs, with no device allocation inside the library.
+    A[n]: float32 (N_n, r_n) device tensors of W_n U_n in column-major order;
+    w[n]: float64 device tensors; dS, Y[n], dv2: float32 / float64 device outputs.
+    Returns the tdb_status code."""
+    lib = load()
+    p = len(dims)
+    cdims = (C.c_int64 * p)(*[int(d) for d in dims])
+    cr = (C.c_int * p)(*[int(r) for r in ranks])
+    aptr = (C.c_void_p * p)(*[a.data_ptr() for a in A])
+    wptr = (C.c_void_p * p)(*[x.data_ptr() for x in w])
+    yptr = (C.c_void_p * p)(*[y.data_ptr() for y in Y])
+    s = stream if stream is not None else torch.cuda.current_stream(V_next.device)
+    return lib.tdb_project_noalloc(p, cdims, cr, C.c_void_p(V_next.data_ptr()), C.c_void_p(V_prev.data_ptr()),
+                                   aptr, wptr, C.c_void_p(dS.data_ptr()), yptr, C.c_void_p(dv2.data_ptr()),
+                                   C.c_void_p(s.cuda_stream))
