@@ -109,6 +109,10 @@ typedef struct tdb_step_info {
   double cr;                        /* compression ratio CR of Sec. 2.6 at the new ranks */
   double dv_norm;                   /* ||V_{k+1} - V_k||_W */
   double ds_norm;                   /* ||dS||_F (the core increment) */
+  double eps_est;                   /* the learned estimate of eps (NaN when no estimator is fitted) */
+  int gate;                         /* why the exact error ran under TDB_ERRMODE_MLP: bit 0 estimate above
+                                       the gate, bit 1 error_every steps without one, bit 2 a feature
+                                       outside the training range; 0 = skipped */
 } tdb_step_info;
 
 typedef struct tdb_ctx tdb_ctx;
@@ -174,6 +178,41 @@ const char* tdb_status_string(tdb_status s);
 
 /* Release the context (not the workspace).  NULL is accepted. */
 void tdb_destroy(tdb_ctx* ctx);
+
+/* ---- Learned error estimator --------------------------------------------------
+ * Not in the paper, which evaluates the error of Eq. 2.20 by a full reconstruction.
+ * A two-hidden-layer perceptron (8 -> 64 -> 64 -> 1, tanh) predicts the change of
+ * log10 of that error over each step from reduced quantities: the previous step's error
+ * (exact, or the estimate when skipped), ||dV||_W, the residual sqrt(||dV||_W^2 - ||dS||^2)
+ * of the step and of the previous step, ||dS||, the smallest sigma_min / sigma_max of the
+ * core unfoldings (Eq. 2.18), ||T|| and steps since the last re-initialisation.  Parameter vector (float,
+ * tdb_mlp_param_count() entries): W1 (64 x 8, row-major), b1, W2 (64 x 64,
+ * row-major), b2, w3, b3.  Training and inference run in libtdb's kernels. */
+int tdb_mlp_param_count(void);
+/* y[i] = MLP(X[i, :]) for n rows of 8 features (all device float). */
+tdb_status tdb_mlp_forward(const float* params, const float* X, int n, float* y, void* stream);
+/* Mean-squared-error loss over n rows and its gradient (device float, one per
+ * parameter).  scratch: device float, >= 1024 * (tdb_mlp_param_count() + 1) entries
+ * for the widest split (fewer entries use fewer partial sums).  loss may be NULL. */
+tdb_status tdb_mlp_loss_grad(const float* params, const float* X, const float* t, int n, float* scratch,
+                             size_t scratch_floats, float* loss, float* grad, void* stream);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8); step counts from 1; m, v device state. */
+tdb_status tdb_mlp_adam_step(float* params, const float* grad, float* m, float* v, int step, float lr, void* stream);
+/* Fit the context's estimator on the (features, log10 exact error) rows it has recorded
+ * (every exact evaluation of an FP32/BF16 context records one): standardisation, Glorot
+ * initialisation from `seed`, `iters` full-batch Adam steps at rate lr.  Afterwards, in
+ * TDB_ERRMODE_MLP the exact error is evaluated only when the estimate exceeds
+ * gate * eps_th, when error_every steps passed without one, or when a feature leaves
+ * the training range; decisions of Sec. 2.5 are taken on exact evaluations only.
+ * loss_out (host, nullable): final training loss (standardised units).  Synchronises. */
+tdb_status tdb_estimator_fit(tdb_ctx* ctx, int iters, float lr, uint64_t seed, double gate, double* loss_out);
+/* Copy the fitted estimator out (get_out, host, param_count + 18 floats: parameters then
+ * feature means, feature scales, target mean, target scale) and / or install one
+ * (set_in, same layout; gate > 0 replaces the gate factor).  Either may be NULL. */
+tdb_status tdb_estimator_params(tdb_ctx* ctx, float* get_out, const float* set_in, double gate);
+/* Recorded training rows: on input *n is the capacity of X (n x 8) and t (n); on
+ * output the number recorded (X, t may be NULL to query). */
+tdb_status tdb_estimator_trace(tdb_ctx* ctx, float* X, float* t, int* n);
 
 /* Accumulated device times of the phases of tdb_push_snapshot, measured with CUDA
  * events on the context's stream while profiling is enabled (tdb_set_profiling).

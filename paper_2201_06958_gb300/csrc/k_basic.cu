@@ -149,7 +149,11 @@ template void launch_wnorm2<double>(const double*, const double*, const WeightVi
 // accumulates w_1(i_1) w_c (V - V^TDB)^2 (float partials per column, double across).
 template <typename T>
 __global__ void k_recon_err(const T* __restrict__ V, const T* __restrict__ U1, const T* __restrict__ H, int r1,
-                            WeightView wv, double* __restrict__ partial, unsigned* flags) {
+                            WeightView wv, double* __restrict__ partial, unsigned* flags, const int* __restrict__ gate) {
+  if (gate && *gate == 0) {            // the estimator ruled this evaluation out
+    if (threadIdx.x == 0) partial[blockIdx.x] = 0.0;
+    return;
+  }
   __shared__ T hcol[32];
   __shared__ double sh[32];
   __shared__ double wcs;
@@ -190,16 +194,16 @@ __global__ void k_recon_err(const T* __restrict__ V, const T* __restrict__ U1, c
 
 template <typename T>
 void launch_recon_err(const T* V, const T* U1, const T* H, int r1, const WeightView& wv, double* partial, int nblocks,
-                      double* out, unsigned* flags, cudaStream_t s) {
-  k_recon_err<T><<<nblocks, 256, 0, s>>>(V, U1, H, r1, wv, partial, flags);
+                      double* out, unsigned* flags, cudaStream_t s, const int* gate) {
+  k_recon_err<T><<<nblocks, 256, 0, s>>>(V, U1, H, r1, wv, partial, flags, gate);
   count_launch();
   k_sum_partials<<<1, 256, 0, s>>>(partial, nblocks, out);
   count_launch();
 }
 template void launch_recon_err<float>(const float*, const float*, const float*, int, const WeightView&, double*, int,
-                                      double*, unsigned*, cudaStream_t);
+                                      double*, unsigned*, cudaStream_t, const int*);
 template void launch_recon_err<double>(const double*, const double*, const double*, int, const WeightView&, double*,
-                                       int, double*, unsigned*, cudaStream_t);
+                                       int, double*, unsigned*, cudaStream_t, const int*);
 
 void launch_sum_partials(const double* partial, int n, double* out, cudaStream_t s) {
   k_sum_partials<<<1, 256, 0, s>>>(partial, n, out); count_launch();
@@ -331,7 +335,8 @@ __global__ void k_mp_reduce_block(const Tin* __restrict__ in, Tacc* __restrict__
 // K small: one thread per output element (l, j, q), l fastest.
 template <typename Tin, typename Tm, typename Tacc>
 __global__ void k_mp_expand(const Tin* __restrict__ in, Tacc* __restrict__ out, const Tm* __restrict__ M, int64_t L,
-                            int K, int J, int64_t Q, int64_t sMj, int64_t sMk) {
+                            int K, int J, int64_t Q, int64_t sMj, int64_t sMk, const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;
   const unsigned total = (unsigned)(L * J * Q), uL = (unsigned)L, uJ = (unsigned)J;
   for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
     const unsigned l = e % uL;
@@ -348,13 +353,13 @@ __global__ void k_mp_expand(const Tin* __restrict__ in, Tacc* __restrict__ out, 
 
 template <typename Tin, typename Tm, typename Tacc>
 void launch_modeprod(const Tin* in, Tacc* out, const Tm* M, int64_t L, int K, int J, int64_t Q, int64_t sMj,
-                     int64_t sMk, cudaStream_t s) {
+                     int64_t sMk, cudaStream_t s, const int* gate) {
   if (L <= 0 || K <= 0 || J <= 0 || Q <= 0) return;
   count_launch();
   if (K <= 64) {
     int64_t total = L * J * Q;
     int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
-    k_mp_expand<Tin, Tm, Tacc><<<blocks, 256, 0, s>>>(in, out, M, L, K, J, Q, sMj, sMk);
+    k_mp_expand<Tin, Tm, Tacc><<<blocks, 256, 0, s>>>(in, out, M, L, K, J, Q, sMj, sMk, gate);
   } else if (L > 1 && L * Q <= 1024) {
     int blocks = (int)std::min<int64_t>(L * Q, 152 * 8);
     if (J <= 8)
@@ -395,7 +400,7 @@ void launch_modeprod(const Tin* in, Tacc* out, const Tm* M, int64_t L, int K, in
 
 #define INST_MP(Tin, Tm, Tacc)                                                                                   \
   template void launch_modeprod<Tin, Tm, Tacc>(const Tin*, Tacc*, const Tm*, int64_t, int, int, int64_t, int64_t, \
-                                               int64_t, cudaStream_t);
+                                               int64_t, cudaStream_t, const int*);
 INST_MP(float, float, float)
 INST_MP(double, double, double)
 INST_MP(double, float, float)

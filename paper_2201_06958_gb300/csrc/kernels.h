@@ -71,10 +71,10 @@ void launch_wnorm2(const T* x, const T* y, const WeightView& wv, double* partial
 void launch_sum_partials(const double* partial, int n, double* out, cudaStream_t s);
 template <typename T>
 void launch_recon_err(const T* V, const T* U1, const T* H, int r1, const WeightView& wv, double* partial, int nblocks,
-                      double* out, unsigned* flags, cudaStream_t s);
+                      double* out, unsigned* flags, cudaStream_t s, const int* gate = nullptr);
 template <typename Tin, typename Tm, typename Tacc>
 void launch_modeprod(const Tin* in, Tacc* out, const Tm* M, int64_t L, int K, int J, int64_t Q, int64_t sMj,
-                     int64_t sMk, cudaStream_t s);
+                     int64_t sMk, cudaStream_t s, const int* gate = nullptr);
 
 // k_small.cu
 void launch_gram(const ModeDesc& d, const double* T, double* Gpart, int nsplit, double* G, double* Ginv,

@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "mlp.h"
 #include "tc_project.h"
 
 namespace tdb {
@@ -29,9 +30,11 @@ struct Readback {
   double err2;
   double dv2;
   double ds2;
+  double est;                      // estimator output (error, not log)
   double sig2[kMaxModes][kMaxRank];
+  float feat[MLP_F];               // estimator features of this step
+  int need;                        // 1: the exact error was evaluated this step
   unsigned flags;
-  unsigned pad;
 };
 
 }  // namespace tdb
@@ -109,6 +112,21 @@ struct tdb_ctx {
   // BF16 tensor-core projection
   TcPlan tc;
   bool use_tc = false;
+  // learned error estimator
+  EstState est;
+  float* mlpP = nullptr;
+  float* mlpNorm = nullptr;
+  float* mlpM = nullptr;
+  float* mlpV = nullptr;
+  float* mlpG = nullptr;
+  float* mlpGpart = nullptr;
+  float* mlpLpart = nullptr;
+  float* mlpLoss = nullptr;
+  float* trX = nullptr;
+  float* trT = nullptr;
+  int mlp_parts = 128;
+  int tr_cap = 8192;
+  std::vector<float> hX, hT;
   // profiling (CUDA events on the stream)
   bool prof = false;
   cudaEvent_t pev[6] = {nullptr};
@@ -278,6 +296,16 @@ void carve(tdb_ctx* c, Carver& cv) {
   int kmax = 0;
   for (int n = 0; n < p; ++n) kmax = std::max(kmax, c->kcap[n]);
   c->eigscratch = cv.take<double>(64 + Nmax * (kmax + 2));
+  c->mlpP = cv.take<float>(MLP_NPARAM);
+  c->mlpNorm = cv.take<float>(2 * MLP_F + 2);
+  c->mlpM = cv.take<float>(MLP_NPARAM);
+  c->mlpV = cv.take<float>(MLP_NPARAM);
+  c->mlpG = cv.take<float>(MLP_NPARAM);
+  c->mlpGpart = cv.take<float>((size_t)c->mlp_parts * MLP_NPARAM);
+  c->mlpLpart = cv.take<float>(c->mlp_parts);
+  c->mlpLoss = cv.take<float>(1);
+  c->trX = cv.take<float>((size_t)c->tr_cap * MLP_F);
+  c->trT = cv.take<float>(c->tr_cap);
   if (c->prec == TDB_BF16_TTM) tc_carve(c->tc, cv, c->p, c->N, c->cap);
 }
 
@@ -432,7 +460,7 @@ tdb_status reconstruct_into(tdb_ctx* ctx, Tc* out) {
 // err2 = ||V - T x U||_W^2 (Eq. 2.20): H = T x_2 U_2 ... x_p U_p, then the fused pass
 // over V that forms each mode-1 column U_1 H[:, c] on the fly.
 template <typename Tc>
-tdb_status exact_error2(tdb_ctx* ctx, const Tc* V) {
+tdb_status exact_error2(tdb_ctx* ctx, const Tc* V, const int* gate = nullptr) {
   const int p = ctx->p;
   cudaStream_t s = ctx->stream;
   int64_t cur[kMaxModes];
@@ -444,12 +472,13 @@ tdb_status exact_error2(tdb_ctx* ctx, const Tc* V) {
     int64_t L = 1, Q = 1;
     for (int m = 0; m < n; ++m) L *= cur[m];
     for (int m = n + 1; m < p; ++m) Q *= cur[m];
-    launch_modeprod<Tc, Tc, Tc>(src, dst, (const Tc*)ctx->Uc[n], L, ctx->r[n], (int)ctx->N[n], Q, 1, ctx->N[n], s);
+    launch_modeprod<Tc, Tc, Tc>(src, dst, (const Tc*)ctx->Uc[n], L, ctx->r[n], (int)ctx->N[n], Q, 1, ctx->N[n], s,
+                                gate);
     cur[n] = ctx->N[n];
     src = dst;
   }
   launch_recon_err<Tc>(V, (const Tc*)ctx->Uc[0], src, ctx->r[0], weight_view(ctx), ctx->npart, ctx->nblk,
-                       &ctx->rb_dev->err2, ctx->flags, s);
+                       &ctx->rb_dev->err2, ctx->flags, s, gate);
   CHECK_LAUNCH();
   return TDB_OK;
 }
@@ -612,6 +641,16 @@ tdb_status error_now(tdb_ctx* ctx, const Tc* V, double* eps) {
   TRY(readback(ctx));
   *eps = std::sqrt(std::max(ctx->rb.err2, 0.0));
   ctx->exact_evals++;
+  return TDB_OK;
+}
+
+// Exact error of a freshly initialised state: seeds the estimator's last error.
+template <typename Tc>
+tdb_status seed_estimator(tdb_ctx* ctx, const Tc* V) {
+  double e;
+  TRY(error_now<Tc>(ctx, V, &e));
+  ctx->exact_evals--;               // not a step's evaluation
+  ctx->est.last_log_eps = std::log10(std::max(e, 1e-300));
   return TDB_OK;
 }
 
@@ -784,16 +823,27 @@ tdb_status step_impl(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
   CHECK_LAUNCH();
   TRY(refresh_derived<Tc>(ctx, false));
   if (ev) CK(cudaEventRecord(ev[2], s));
-  // a7: error
+  // a7: error, exact or estimated
   ctx->step++;
+  ctx->est.steps_since_exact += 1;
+  ctx->est.steps_since_reinit += 1;
+  const bool feats = !ctx->f64;
+  if (feats) {
+    int64_t nds = 1;
+    for (int n = 0; n < p; ++n) nds *= ctx->r[n];
+    est_features(&ctx->est, (const float*)ctx->dS, (int)nds, &ctx->rb_dev->dv2, ctx->sig2, ctx->r, p, ctx->mlpP,
+                 ctx->mlpNorm, ctx->rb_dev->feat, &ctx->rb_dev->est, &ctx->rb_dev->need, &ctx->rb_dev->ds2, s);
+    CHECK_LAUNCH();
+  }
   bool exact = false;
+  const bool gated = ctx->cfg.error_mode == TDB_ERRMODE_MLP && ctx->est.ready;
   switch (ctx->cfg.error_mode) {
     case TDB_ERRMODE_EXACT: exact = true; break;
-    case TDB_ERRMODE_EVERY_K:
-    case TDB_ERRMODE_MLP: exact = (ctx->step % ctx->cfg.error_every) == 0; break;
+    case TDB_ERRMODE_EVERY_K: exact = (ctx->step % ctx->cfg.error_every) == 0; break;
+    case TDB_ERRMODE_MLP: exact = true; break;      // decided on the device when the estimator is ready
     default: exact = false;
   }
-  if (exact) TRY(exact_error2<Tc>(ctx, Vn));
+  if (exact) TRY(exact_error2<Tc>(ctx, Vn, gated ? &ctx->rb_dev->need : nullptr));
   if (ev) CK(cudaEventRecord(ev[3], s));
   TRY(readback(ctx));
   if (ev) {
@@ -812,7 +862,8 @@ tdb_status step_impl(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
   if (ctx->rb.flags & kFlagNonFinite) { ctx->err = "non-finite value in a snapshot difference"; return TDB_ERR_NONFINITE; }
   if (ctx->rb.flags & kFlagCholGram) { ctx->err = "T_(n) T_(n)^T is not positive definite"; return TDB_ERR_RANK_DEFICIENT; }
   if (ctx->rb.flags & kFlagCholQR) { ctx->err = "U^T W U is not positive definite"; return TDB_ERR_RANK_DEFICIENT; }
-  double eps = exact ? std::sqrt(std::max(ctx->rb.err2, 0.0)) : NAN;
+  if (gated) exact = ctx->rb.need != 0;
+  double eps = exact ? std::sqrt(std::max(ctx->rb.err2, 0.0)) : (gated ? ctx->rb.est : NAN);
   double dv2 = ctx->rb.dv2;
   double sig_step[kMaxModes][kMaxRank];
   memcpy(sig_step, ctx->rb.sig2, sizeof(sig_step));
@@ -831,9 +882,29 @@ tdb_status step_impl(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
       TRY(readback(ctx));   // sigma of the new state
     }
   }
+  // estimator bookkeeping: the trace (features, log10 exact error of the step) and counters
+  if (feats) {
+    // training row: features and the change of log10 error over this step (target of the network)
+    if (exact && eps > 0 && std::isfinite(eps)) {
+      if ((int)ctx->hT.size() >= ctx->tr_cap) {
+        ctx->hX.erase(ctx->hX.begin(), ctx->hX.begin() + MLP_F);
+        ctx->hT.erase(ctx->hT.begin());
+      }
+      ctx->hX.insert(ctx->hX.end(), ctx->rb.feat, ctx->rb.feat + MLP_F);
+      ctx->hT.push_back((float)(std::log10(eps) - ctx->est.last_log_eps));
+    }
+    const double e_now = exact ? eps_after : eps;
+    if (e_now > 0 && std::isfinite(e_now)) ctx->est.last_log_eps = std::log10(e_now);
+    ctx->est.prev_res_log = ctx->rb.feat[2];
+    if (exact) ctx->est.steps_since_exact = 0;
+    if (n_re > 0) ctx->est.steps_since_reinit = 0;
+  }
   ctx->V_prev = Vn;
   if (info) {
     memset(info, 0, sizeof(*info));
+    info->ds_norm = std::sqrt(std::max(ctx->rb.ds2, 0.0));
+    info->eps_est = ctx->est.ready ? ctx->rb.est : NAN;
+    info->gate = gated ? ctx->rb.need : 0;
     info->step = ctx->step;
     info->eps = eps_after;
     info->eps_exact = exact ? 1 : 0;
@@ -908,6 +979,18 @@ tdb_status common_init(tdb_ctx** out, const tdb_config* cfg, void* ws, size_t ws
     }
   }
   cudaMemsetAsync(ctx->rb_dev, 0, sizeof(Readback), ctx->stream);
+  memset(&ctx->est, 0, sizeof(ctx->est));
+  ctx->est.last_log_eps = -30.0;
+  ctx->est.max_skip = std::max(1, ctx->cfg.error_every);
+  ctx->est.gate = 0.5;
+  ctx->est.eps_th = ctx->cfg.eps_th;
+  ctx->est.novelty_z = 8.0;
+  ctx->est.prev_res_log = -30.0;
+  if (ctx->cfg.error_mode == TDB_ERRMODE_MLP && ctx->f64) {
+    g_init_error = "the learned estimator runs in the FP32 and BF16 modes";
+    delete ctx;
+    return TDB_ERR_UNSUPPORTED;
+  }
   *made = ctx;
   return TDB_OK;
 }
@@ -947,7 +1030,9 @@ tdb_status tdb_init(tdb_ctx** out, const tdb_config* cfg, void* ws, size_t ws_by
     }
     r = clamp_product_bound(r);
     TRY(hosvd_state<Tc>(ctx, V, r.data()));
-    return readback(ctx);
+    TRY(readback(ctx));
+    if (!ctx->f64) TRY(seed_estimator<Tc>(ctx, V));
+    return TDB_OK;
   };
   st = ctx->f64 ? run(double()) : run(float());
   if (st != TDB_OK) {
@@ -990,6 +1075,7 @@ tdb_status tdb_init_from_factors(tdb_ctx** out, const tdb_config* cfg, void* ws,
   }
   st = ctx->f64 ? refresh_derived<double>(ctx, true) : refresh_derived<float>(ctx, true);
   if (st == TDB_OK) st = readback(ctx);
+  if (st == TDB_OK && !ctx->f64) st = seed_estimator<float>(ctx, (const float*)V0);
   if (st != TDB_OK) {
     g_init_error = ctx->err;
     delete ctx;
@@ -1170,6 +1256,64 @@ const char* tdb_status_string(tdb_status s) {
     case TDB_ERR_UNSUPPORTED: return "TDB_ERR_UNSUPPORTED";
   }
   return "unknown status";
+}
+
+tdb_status tdb_estimator_fit(tdb_ctx* ctx, int iters, float lr, uint64_t seed, double gate, double* loss_out) {
+  if (!ctx || iters < 1 || !(lr > 0) || !(gate > 0)) return TDB_ERR_INVALID_ARG;
+  if (!ctx->ready || ctx->f64) { ctx->err = "estimator needs an initialised FP32/BF16 context"; return TDB_ERR_STATE; }
+  const int n = (int)ctx->hT.size();
+  if (n < 16) { ctx->err = "fewer than 16 exact evaluations recorded"; return TDB_ERR_STATE; }
+  cudaStream_t s = ctx->stream;
+  CK(cudaMemcpyAsync(ctx->trX, ctx->hX.data(), sizeof(float) * n * MLP_F, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ctx->trT, ctx->hT.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s));
+  est_normalize(ctx->trX, ctx->trT, n, ctx->mlpNorm, s);
+  est_init_params(ctx->mlpP, (unsigned long long)seed, s);
+  CK(cudaMemsetAsync(ctx->mlpM, 0, sizeof(float) * MLP_NPARAM, s));
+  CK(cudaMemsetAsync(ctx->mlpV, 0, sizeof(float) * MLP_NPARAM, s));
+  for (int it = 1; it <= iters; ++it) {
+    mlp_loss_grad(ctx->mlpP, ctx->trX, ctx->trT, n, ctx->mlpGpart, ctx->mlpLpart, ctx->mlp_parts, ctx->mlpG,
+                  ctx->mlpLoss, s);
+    mlp_adam(ctx->mlpP, ctx->mlpG, ctx->mlpM, ctx->mlpV, it, lr, s);
+  }
+  CHECK_LAUNCH();
+  float loss = 0.f;
+  CK(cudaMemcpyAsync(&loss, ctx->mlpLoss, sizeof(float), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  if (loss_out) *loss_out = loss;
+  ctx->est.ready = 1;
+  ctx->est.gate = gate;
+  return TDB_OK;
+}
+
+tdb_status tdb_estimator_params(tdb_ctx* ctx, float* get_out, const float* set_in, double gate) {
+  if (!ctx) return TDB_ERR_INVALID_ARG;
+  if (!ctx->ready || ctx->f64) { ctx->err = "estimator needs an initialised FP32/BF16 context"; return TDB_ERR_STATE; }
+  cudaStream_t s = ctx->stream;
+  if (get_out) {
+    CK(cudaMemcpyAsync(get_out, ctx->mlpP, sizeof(float) * MLP_NPARAM, cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(get_out + MLP_NPARAM, ctx->mlpNorm, sizeof(float) * (2 * MLP_F + 2), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+  }
+  if (set_in) {
+    CK(cudaMemcpyAsync(ctx->mlpP, set_in, sizeof(float) * MLP_NPARAM, cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->mlpNorm, set_in + MLP_NPARAM, sizeof(float) * (2 * MLP_F + 2), cudaMemcpyHostToDevice, s));
+    CK(cudaStreamSynchronize(s));
+    ctx->est.ready = 1;
+    if (gate > 0) ctx->est.gate = gate;
+  }
+  return TDB_OK;
+}
+
+tdb_status tdb_estimator_trace(tdb_ctx* ctx, float* X, float* t, int* n) {
+  if (!ctx || !n) return TDB_ERR_INVALID_ARG;
+  const int have = (int)ctx->hT.size();
+  if (X && t) {
+    const int m = std::min(*n, have);
+    memcpy(X, ctx->hX.data(), sizeof(float) * m * MLP_F);
+    memcpy(t, ctx->hT.data(), sizeof(float) * m);
+  }
+  *n = have;
+  return TDB_OK;
 }
 
 tdb_status tdb_set_profiling(tdb_ctx* ctx, int enable) {

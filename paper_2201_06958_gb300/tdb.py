@@ -62,6 +62,8 @@ class tdb_step_info(C.Structure):
         ("cr", C.c_double),
         ("dv_norm", C.c_double),
         ("ds_norm", C.c_double),
+        ("eps_est", C.c_double),
+        ("gate", C.c_int),
     ]
 
 
@@ -72,6 +74,8 @@ EXPORTS = [
     "tdb_adapt_rank", "tdb_get_factors", "tdb_get_projection", "tdb_get_counters", "tdb_save_state",
     "tdb_load_state", "tdb_last_error", "tdb_status_string", "tdb_destroy", "tdb_version",
     "tdb_set_profiling", "tdb_get_profile", "tdb_kernel_launches", "tdb_project_noalloc",
+    "tdb_mlp_param_count", "tdb_mlp_forward", "tdb_mlp_loss_grad", "tdb_mlp_adam_step", "tdb_estimator_fit",
+    "tdb_estimator_params", "tdb_estimator_trace",
 ]
 
 
@@ -125,6 +129,20 @@ def load(path: str = LIB_PATH):
     lib.tdb_project_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int), vp, vp,
                                         C.POINTER(vp), C.POINTER(vp), vp, C.POINTER(vp), vp, vp]
     lib.tdb_project_noalloc.restype = st
+    lib.tdb_mlp_param_count.argtypes = []
+    lib.tdb_mlp_param_count.restype = C.c_int
+    lib.tdb_mlp_forward.argtypes = [vp, vp, C.c_int, vp, vp]
+    lib.tdb_mlp_forward.restype = st
+    lib.tdb_mlp_loss_grad.argtypes = [vp, vp, vp, C.c_int, vp, sz, vp, vp, vp]
+    lib.tdb_mlp_loss_grad.restype = st
+    lib.tdb_mlp_adam_step.argtypes = [vp, vp, vp, vp, C.c_int, C.c_float, vp]
+    lib.tdb_mlp_adam_step.restype = st
+    lib.tdb_estimator_fit.argtypes = [vp, C.c_int, C.c_float, C.c_uint64, C.c_double, C.POINTER(C.c_double)]
+    lib.tdb_estimator_fit.restype = st
+    lib.tdb_estimator_params.argtypes = [vp, vp, vp, C.c_double]
+    lib.tdb_estimator_params.restype = st
+    lib.tdb_estimator_trace.argtypes = [vp, vp, vp, C.POINTER(C.c_int)]
+    lib.tdb_estimator_trace.restype = st
     _lib = lib
     return lib
 
@@ -237,7 +255,8 @@ class TDB:
             "step": info.step, "eps": info.eps, "eps_exact": bool(info.eps_exact), "eps_step": info.eps_step,
             "gamma": list(info.gamma)[: self.p], "sigma_min": list(info.sigma_min)[: self.p],
             "ranks": list(info.ranks)[: self.p], "reinit": info.reinit, "action": ACTIONS.get(info.action, "?"),
-            "cr": info.cr, "dv_norm": info.dv_norm, "ds_norm": info.ds_norm, "status": st,
+            "cr": info.cr, "dv_norm": info.dv_norm, "ds_norm": info.ds_norm, "eps_est": info.eps_est,
+            "gate": info.gate, "status": st,
         }
 
     def push_raw(self, ptr: int, info: Optional[tdb_step_info] = None) -> int:
@@ -306,6 +325,28 @@ class TDB:
         self._check(self.lib.tdb_load_state(self.ctx, buf, len(blob), C.c_void_p(V_prev.data_ptr())))
         self._prev = V_prev
 
+    def estimator_fit(self, iters: int = 2000, lr: float = 3e-3, seed: int = 1, gate: float = 0.5) -> float:
+        loss = C.c_double()
+        self._check(self.lib.tdb_estimator_fit(self.ctx, iters, lr, seed, gate, C.byref(loss)))
+        return loss.value
+
+    def estimator_params(self, set_params: Optional[np.ndarray] = None, gate: float = 0.0) -> np.ndarray:
+        n = self.lib.tdb_mlp_param_count() + 18
+        out = np.empty(n, dtype=np.float32)
+        inp = None if set_params is None else np.ascontiguousarray(set_params, dtype=np.float32)
+        self._check(self.lib.tdb_estimator_params(
+            self.ctx, out.ctypes.data_as(C.c_void_p), None if inp is None else inp.ctypes.data_as(C.c_void_p), gate))
+        return out
+
+    def estimator_trace(self):
+        n = C.c_int(0)
+        self._check(self.lib.tdb_estimator_trace(self.ctx, None, None, C.byref(n)))
+        X = np.empty((n.value, 8), dtype=np.float32)
+        t = np.empty(n.value, dtype=np.float32)
+        self._check(self.lib.tdb_estimator_trace(self.ctx, X.ctypes.data_as(C.c_void_p), t.ctypes.data_as(C.c_void_p),
+                                                 C.byref(n)))
+        return X, t
+
     def close(self):
         if self.ctx:
             self.lib.tdb_destroy(self.ctx)
@@ -336,3 +377,39 @@ def project_noalloc(dims, ranks, V_next: torch.Tensor, V_prev: torch.Tensor, A, 
     return lib.tdb_project_noalloc(p, cdims, cr, C.c_void_p(V_next.data_ptr()), C.c_void_p(V_prev.data_ptr()),
                                    aptr, wptr, C.c_void_p(dS.data_ptr()), yptr, C.c_void_p(dv2.data_ptr()),
                                    C.c_void_p(s.cuda_stream))
+
+
+def mlp_forward(params: torch.Tensor, X: torch.Tensor) -> torch.Tensor:
+    """tdb_mlp_forward on device tensors (float32)."""
+    lib = load()
+    y = torch.empty(X.shape[0], dtype=torch.float32, device=X.device)
+    st = lib.tdb_mlp_forward(C.c_void_p(params.data_ptr()), C.c_void_p(X.data_ptr()), X.shape[0],
+                             C.c_void_p(y.data_ptr()), C.c_void_p(torch.cuda.current_stream(X.device).cuda_stream))
+    if st != 0:
+        raise TDBError(st, "tdb_mlp_forward")
+    return y
+
+
+def mlp_loss_grad(params: torch.Tensor, X: torch.Tensor, t: torch.Tensor):
+    """tdb_mlp_loss_grad on device tensors (float32); returns (loss tensor, grad tensor)."""
+    lib = load()
+    npar = lib.tdb_mlp_param_count()
+    scratch = torch.empty(1024 * (npar + 1), dtype=torch.float32, device=X.device)
+    loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    grad = torch.empty(npar, dtype=torch.float32, device=X.device)
+    st = lib.tdb_mlp_loss_grad(C.c_void_p(params.data_ptr()), C.c_void_p(X.data_ptr()), C.c_void_p(t.data_ptr()),
+                               X.shape[0], C.c_void_p(scratch.data_ptr()), scratch.numel(),
+                               C.c_void_p(loss.data_ptr()), C.c_void_p(grad.data_ptr()),
+                               C.c_void_p(torch.cuda.current_stream(X.device).cuda_stream))
+    if st != 0:
+        raise TDBError(st, "tdb_mlp_loss_grad")
+    return loss, grad
+
+
+def mlp_adam_step(params: torch.Tensor, grad: torch.Tensor, m: torch.Tensor, v: torch.Tensor, step: int, lr: float):
+    lib = load()
+    st = lib.tdb_mlp_adam_step(C.c_void_p(params.data_ptr()), C.c_void_p(grad.data_ptr()), C.c_void_p(m.data_ptr()),
+                               C.c_void_p(v.data_ptr()), step, lr,
+                               C.c_void_p(torch.cuda.current_stream(params.device).cuda_stream))
+    if st != 0:
+        raise TDBError(st, "tdb_mlp_adam_step")

@@ -64,5 +64,5 @@ def test_struct_layout_matches_header():
     assert C.sizeof(tdb.tdb_config) == 144
     assert tdb.tdb_config.eps_th.offset == 104
     assert tdb.tdb_config.reorth.offset == 136
-    assert C.sizeof(tdb.tdb_step_info) == 144
+    assert C.sizeof(tdb.tdb_step_info) == 160
     assert tdb.tdb_step_info.cr.offset == 120
