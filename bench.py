@@ -41,6 +41,8 @@ def parse_args():
     ap.add_argument("--workload", default="reactive", choices=["reactive", "stochastic", "channel", "analytic"])
     ap.add_argument("--precision", default="auto", choices=["auto", "bf16", "fp32", "fp64"])
     ap.add_argument("--error-mode", default="auto", choices=["auto", "exact", "mlp", "every_k"])
+    ap.add_argument("--train-steps", type=int, default=300,
+                    help="steps of the separate training stream for the error estimator")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -286,32 +288,40 @@ def run_tdb(args, world, rank, local):
     precision = args.precision
     if precision == "auto":
         precision = "fp64" if wl.dtype == "f64" else "bf16"
-    err_mode = args.error_mode if args.error_mode != "auto" else "exact"
+    err_mode = args.error_mode
+    if err_mode == "auto":
+        err_mode = "mlp" if (precision == "bf16" and wl.eps_th > 0) else "exact"
     K, W = args.steps, args.warmup
+    est_params, est_info = None, None
+    if err_mode == "mlp":
+        est_params, est_info = train_estimator(args, wl, precision, dev, tdb, S)
     nsnap = W + K + 1
     snaps = torch.empty((nsnap,) + tuple(reversed(wl.dims)), dtype=wl.torch_dtype, device=dev)
     for k in range(nsnap):
         snaps[k] = wl.snapshot(k, device=dev)
     torch.cuda.synchronize()
 
-    def make(prec):
+    def make(prec, mode):
         c = tdb.TDB(wl.dims, wl.rank, rank_max=wl.rank_max, weights=wl.weights, eps_th=wl.eps_th,
-                    gamma_th=wl.gamma_th, precision=prec, error_mode=err_mode, device=dev)
+                    gamma_th=wl.gamma_th, precision=prec, error_mode=mode, error_every=50, device=dev)
         return c
 
-    def run(prec, timed_profile=True):
-        c = make(prec)
+    def run(prec, timed_profile=True, mode=None):
+        mode = mode or err_mode
+        c = make(prec, mode)
         try:
             c.init(snaps[0])
         except tdb.TDBError as e:
             if prec == "bf16" and e.status == 11:
                 return None
             raise
+        if mode == "mlp":
+            c.estimator_params(est_params, gate=0.9)
         info = tdb.tdb_step_info()
         for k in range(1, W + 1):
             st = c.push_raw(snaps[k].data_ptr(), info)
             assert st in (0, 9), (st, lib.tdb_last_error(c.ctx))
-        eps = []
+        eps, acts = [], []
         barrier(world)
         torch.cuda.synchronize()
         if timed_profile:
@@ -328,7 +338,8 @@ def run_tdb(args, world, rank, local):
             st = c.push_raw(snaps[k].data_ptr(), info)
             if st not in (0, 9):
                 raise tdb.TDBError(st, lib.tdb_last_error(c.ctx).decode())
-            eps.append(info.eps)
+            eps.append(info.eps if info.eps_exact else float("nan"))
+            acts.append((info.action, tuple(info.ranks[: wl.ndim])))
         e1.record(stream)
         torch.cuda.synchronize()
         t_host = time.perf_counter() - t_host0
@@ -342,7 +353,7 @@ def run_tdb(args, world, rank, local):
         counters = c.counters()
         c.close()
         return {"ms": ms, "host_s": t_host, "eps": eps, "prof": prof, "clocks": clocks, "launches": launches,
-                "counters": counters}
+                "counters": counters, "acts": acts}
 
     res = run(precision)
     if res is None:
@@ -388,19 +399,23 @@ def run_tdb(args, world, rank, local):
         "roofline": roofline, "clocks": res["clocks"], "gpu_launches": int(res["launches"]),
         "reinits": res["counters"]["reinits"], "exact_evals": res["counters"]["exact_evals"],
     }
+    if est_info is not None:
+        line["estimator"] = dict(est_info, exact_eval_fraction=res["counters"]["exact_evals"] / max(K + W, 1))
 
     # the plain FP32 GPU path on the same stream, for the "at equal error" comparison
     if not args.no_compare and precision != "fp32" and wl.dtype == "f32":
-        ref = run("fp32", timed_profile=True)
+        ref = run("fp32", timed_profile=True, mode="exact")
         ms_ref = max_over_ranks(max(ref["ms"], ref["host_s"] * 1e3), world)
         pairs = [(a, b) for a, b in zip(res["eps"], ref["eps"]) if a == a and b == b]
         rel = max(abs(a - b) / b for a, b in pairs) if pairs else None
         line["plain_fp32"] = {"value": world * K / (ms_ref * 1e-3), "unit": UNIT, "ms_per_step": ms_ref / K,
-                              "eps_max_rel_diff": rel, "reinits": ref["counters"]["reinits"]}
+                              "eps_max_rel_diff_at_exact_steps": rel, "reinits": ref["counters"]["reinits"],
+                              "same_decisions": res["acts"] == ref["acts"],
+                              "exact_evals": ref["counters"]["exact_evals"]}
 
     # end to end through the C ABI from pinned host buffers
     if not args.no_e2e:
-        line["e2e"] = run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb)
+        line["e2e"] = run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_params)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample_seconds, K)
@@ -408,16 +423,42 @@ def run_tdb(args, world, rank, local):
         print(json.dumps(line))
 
 
-def run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb):
+def train_estimator(args, wl, precision, dev, tdb, S):
+    """Fit the error estimator on a separate stream of the same workload (another seed),
+    evaluated exactly every step; returns (parameters, report).  Not timed."""
+    import torch
+    tseed = 8001 + ["analytic", "reactive", "stochastic", "channel"].index(args.workload)
+    wt = S.make_workload(args.workload, seed=tseed)
+    c = tdb.TDB(wt.dims, wt.rank, rank_max=wt.rank_max, weights=wt.weights, eps_th=wt.eps_th,
+                gamma_th=wt.gamma_th, precision=precision, error_mode="exact", device=dev)
+    bufs = [wt.snapshot(0, device=dev), None]
+    c.init(bufs[0])
+    for k in range(1, args.train_steps + 1):
+        bufs[k % 2] = wt.snapshot(k, device=dev)
+        c.push(bufs[k % 2])
+    t0 = time.perf_counter()
+    loss = c.estimator_fit(iters=2000, lr=3e-3, seed=11, gate=0.9)
+    torch.cuda.synchronize()
+    fit_s = time.perf_counter() - t0
+    params = c.estimator_params()
+    c.close()
+    return params, {"train_stream": f"{args.workload} stream with seed {tseed}, {args.train_steps} exact steps",
+                    "fit_seconds": fit_s, "fit_loss": loss,
+                    "gate": 0.9, "max_skip": 50}
+
+
+def run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_params=None):
     import torch
     host = torch.empty_like(snaps, device="cpu").pin_memory()
     host.copy_(snaps)
     c = tdb.TDB(wl.dims, wl.rank, rank_max=wl.rank_max, weights=wl.weights, eps_th=wl.eps_th,
-                gamma_th=wl.gamma_th, precision=precision, error_mode=err_mode, device=dev)
+                gamma_th=wl.gamma_th, precision=precision, error_mode=err_mode, error_every=50, device=dev)
     ring = [torch.empty_like(snaps[0]) for _ in range(2)]
     stream = torch.cuda.current_stream(dev)
     ring[0].copy_(host[0], non_blocking=True)
     c.init(ring[0])
+    if err_mode == "mlp":
+        c.estimator_params(est_params, gate=0.9)
     info = tdb.tdb_step_info()
     for k in range(1, W + 1):
         buf = ring[k % 2]
