@@ -279,7 +279,8 @@ def run_tdb(args, world, rank, local):
     class tdb_profile(C.Structure):
         _fields_ = [("steps", C.c_int64), ("ms_project", C.c_double), ("ms_project_main", C.c_double),
                     ("ms_update", C.c_double), ("ms_error", C.c_double), ("ms_control", C.c_double),
-                    ("launches_main", C.c_int64)]
+                    ("launches_main", C.c_int64), ("update_phases", C.c_int64),
+                    ("us_update_phase", C.c_double * 12)]
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
@@ -385,7 +386,9 @@ def run_tdb(args, world, rank, local):
                 "phase_ms_per_step": {"project": prof.ms_project / max(prof.steps, 1),
                                       "update": prof.ms_update / max(prof.steps, 1),
                                       "error": prof.ms_error / max(prof.steps, 1),
-                                      "control_host": prof.ms_control / max(prof.steps, 1)}}
+                                      "control_host": prof.ms_control / max(prof.steps, 1)},
+                "update_phase_us_per_step": [round(prof.us_update_phase[k] / max(prof.steps, 1), 2)
+                                             for k in range(prof.update_phases)]}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,

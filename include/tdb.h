@@ -227,6 +227,12 @@ typedef struct tdb_profile {
   double ms_error;            /* exact error (Eq. 2.20) or its estimate */
   double ms_control;          /* rank control including HOSVD re-initialisations (host clock) */
   int64_t launches_main;      /* launches of the main projection kernel */
+  int64_t update_phases;      /* entries of us_update_phase in use (6 + number of modes) */
+  double us_update_phase[12]; /* microseconds summed over the timed steps, per phase of the
+                                 fused update kernel (device global timer at its grid barriers):
+                                 rows M/X/P, P reduce, rows U'/C, Cholesky-QR factors,
+                                 rows U'' with the core product of mode 1, core products of
+                                 modes 2..p, Gram partials, Gram finish */
 } tdb_profile;
 
 /* enable != 0 starts (and zeroes) the accumulation; 0 stops it. */

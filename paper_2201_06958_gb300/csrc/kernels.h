@@ -49,6 +49,37 @@ struct RowArgs {
   int ntile;                     // tiles per mode in `part`
 };
 
+// Arguments of the fused per-step update (k_update.cu).  Tc is the compute type;
+// r x r matrices are column-major with leading dimension kMaxRank.
+struct UpdArgs {
+  ModeDesc d;
+  const void* Y[kMaxModes];      // projections Y_n (Tc)
+  const void* dS;                // core increment (Tc)
+  double* T;                     // core (in: step k, out: step k+1)
+  double* T2;                    // scratch core
+  void* Tcore;                   // Tc copy of the core (in and out; aliases T in FP64)
+  double* U[kMaxModes];          // bases (in and out)
+  double* Up[kMaxModes];         // U' (scratch)
+  void* X[kMaxModes];            // M G^{-1} (Tc scratch, N_n x r_n)
+  const double* w[kMaxModes];    // quadrature weights
+  void* A[kMaxModes];            // W U (Tc; in: step k, out: step k+1)
+  void* Uc[kMaxModes];           // U (Tc; in and out)
+  double* G;                     // p x LD x LD (out)
+  double* Ginv;                  // p x LD x LD (out)
+  float* Ginvf;                  // float copy of Ginv (in: of the core of step k; out), null in FP64
+  double* R;                     // p x LD x LD (out)
+  double* Rinv;                  // p x LD x LD (out)
+  double* sig2;                  // p x LD, descending (out)
+  float* Vprev;                  // p x LD x LD, eigenvectors of G_n (Jacobi warm start; in and out)
+  void* part;                    // 2 x p x ntile x LD x LD partial sums (Tc scratch)
+  double* gpart;                 // p x gsplit x LD x LD Gram partials (scratch)
+  int ntile, gsplit;
+  int warm, reorth;
+  unsigned* bar;                 // [count, generation]
+  unsigned long long* stamps;    // per-phase timer stamps (profiling), or null
+  unsigned* flags;
+};
+
 struct GramView {
   int p, n;
   int64_t N[kMaxModes];
@@ -76,13 +107,27 @@ template <typename Tin, typename Tm, typename Tacc>
 void launch_modeprod(const Tin* in, Tacc* out, const Tm* M, int64_t L, int K, int J, int64_t Q, int64_t sMj,
                      int64_t sMk, cudaStream_t s, const int* gate = nullptr);
 
-// k_small.cu
+// Column slices of the Gram partials G_n = T_(n) T_(n)^T: one per 32 columns of the
+// widest unfolding, at most `cap`.  The fused update and the standalone refresh use
+// the same split, so both sum in the same order.
+inline int gram_split(const int* r, int p, int cap) {
+  int64_t Rprod = 1, maxcol = 1;
+  for (int n = 0; n < p; ++n) Rprod *= r[n];
+  for (int n = 0; n < p; ++n) maxcol = std::max<int64_t>(maxcol, Rprod / r[n]);
+  return (int)std::min<int64_t>(cap, std::max<int64_t>(1, maxcol / 32));
+}
+
+// k_update.cu (standalone Gram refresh)
 void launch_gram(const ModeDesc& d, const double* T, double* Gpart, int nsplit, double* G, double* Ginv,
-                 double* sig2, float* Vprev, int warm, unsigned* flags, cudaStream_t s);
-template <typename Tc>
-void launch_update_rows(RowArgs& a, double* P, double* R, double* Rinv, unsigned* flags, bool reorth, cudaStream_t s);
+                 float* Ginvf, double* sig2, float* Vprev, int warm, unsigned* flags, cudaStream_t s);
+
+// k_small.cu
 template <typename Tc>
 void launch_orthonormalize(RowArgs& a, double* R, double* Rinv, unsigned* flags, cudaStream_t s);
+
+// k_update.cu
+template <typename Tc>
+tdb_status launch_update(UpdArgs& a, int grid_hint, cudaStream_t s);
 
 // k_hosvd.cu
 template <typename Tv>

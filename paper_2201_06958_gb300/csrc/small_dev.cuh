@@ -43,7 +43,8 @@ __device__ __noinline__ int jacobi_smem(T* A, T* V, int lda, int n, int max_swee
         else { p = (rd + k) % (nn - 1); q = (rd - k + (nn - 1)) % (nn - 1); }
         T app = A[p + lda * p], aqq = A[q + lda * q], apq = A[p + lda * q];
         T c = 1, s = 0;
-        if (apq != T(0) && fabs((double)apq) > (double)tol * 1e-3 * sqrt(fabs((double)app * (double)aqq))) {
+        const T thr = tol * T(1e-3);   // skip rotations of negligible pairs (no square root, compute type)
+        if (apq != T(0) && apq * apq > thr * thr * fabs(app * aqq)) {
           T theta = (aqq - app) / (T(2) * apq);
           T t = (theta >= 0 ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
           c = T(1) / sqrt(t * t + T(1));

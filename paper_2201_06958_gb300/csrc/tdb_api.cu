@@ -76,12 +76,15 @@ struct tdb_ctx {
   size_t tree_elems = 0;
   double* G;
   double* Ginv;
+  float* Ginvf;                   // float copy of Ginv (float compute types)
   double* P;
   double* R;
   double* Rinv;
   double* Gpart;
   int gsplit = 1;
   double* rowpart;
+  unsigned* bar;                  // grid-barrier words of the fused update
+  unsigned long long* stamps;     // phase timer stamps of the fused update (profiling)
   int ntile = 1;
   double* sig2;
   float* Vprev;
@@ -255,13 +258,16 @@ void carve(tdb_ctx* c, Carver& cv) {
   c->rec = cv.take<char>(c->S * tsz);
   c->G = cv.take<double>(p * kMaxRank * kMaxRank);
   c->Ginv = cv.take<double>(p * kMaxRank * kMaxRank);
+  c->Ginvf = c->f64 ? nullptr : cv.take<float>(p * kMaxRank * kMaxRank);
   c->P = cv.take<double>(p * kMaxRank * kMaxRank);
   c->R = cv.take<double>(p * kMaxRank * kMaxRank);
   c->Rinv = cv.take<double>(p * kMaxRank * kMaxRank);
   c->gsplit = 64;
   c->Gpart = cv.take<double>((size_t)p * c->gsplit * kMaxRank * kMaxRank);
   c->ntile = (int)((Nmax + 31) / 32);
-  c->rowpart = cv.take<double>((size_t)p * c->ntile * kMaxRank * kMaxRank);
+  c->rowpart = cv.take<double>((size_t)2 * p * c->ntile * kMaxRank * kMaxRank);
+  c->bar = cv.take<unsigned>(2);
+  c->stamps = cv.take<unsigned long long>(32);
   c->sig2 = cv.take<double>(p * kMaxRank);
   c->Vprev = cv.take<float>(p * kMaxRank * kMaxRank);
   c->Vprev_bak = cv.take<float>(p * kMaxRank * kMaxRank);
@@ -499,10 +505,8 @@ tdb_status refresh_derived(tdb_ctx* ctx, bool bases_too) {
       launch_cast<double, float>(ctx->U[n], (float*)ctx->Uc[n], ctx->N[n] * ctx->r[n], s);
   }
   ModeDesc d = mode_desc(ctx);
-  int64_t maxcol = 1;
-  for (int n = 0; n < ctx->p; ++n) maxcol = std::max<int64_t>(maxcol, Rprod / ctx->r[n]);
-  int nsplit = (int)std::min<int64_t>(ctx->gsplit, std::max<int64_t>(1, maxcol / 8));
-  launch_gram(d, ctx->T, ctx->Gpart, nsplit, ctx->G, ctx->Ginv, ctx->sig2, ctx->Vprev, ctx->warm ? 1 : 0, ctx->flags, s);
+  const int nsplit = gram_split(ctx->r, ctx->p, ctx->gsplit);
+  launch_gram(d, ctx->T, ctx->Gpart, nsplit, ctx->G, ctx->Ginv, ctx->Ginvf, ctx->sig2, ctx->Vprev, ctx->warm ? 1 : 0, ctx->flags, s);
   ctx->warm = true;
   CHECK_LAUNCH();
   return TDB_OK;
@@ -783,45 +787,52 @@ tdb_status step_impl(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
     TRY(project_tree<Tc>(ctx, (const Tc*)ctx->dV, ev ? ev + 4 : nullptr));
   }
   if (ev) CK(cudaEventRecord(ev[1], s));
-  // a3..a6: pseudo-inverse, complement projection, Euler, Cholesky-QR (bases)
-  RowArgs a;
-  memset(&a, 0, sizeof(a));
-  a.d = mode_desc(ctx);
-  for (int n = 0; n < p; ++n) {
-    a.Y[n] = ctx->Y[n];
-    a.U[n] = ctx->U[n];
-    a.w[n] = ctx->w[n];
-    a.X[n] = ctx->X[n];
-    a.Up[n] = ctx->Up[n];
-    a.Uout[n] = ctx->U[n];
-    a.A[n] = ctx->A[n];
-  }
-  a.Tc = ctx->Tcore;
-  a.Ginv = ctx->Ginv;
-  a.part = ctx->rowpart;
-  a.ntile = ctx->ntile;
-  launch_update_rows<Tc>(a, ctx->P, ctx->R, ctx->Rinv, ctx->flags, ctx->cfg.reorth != 0, s);
-  CHECK_LAUNCH();
-  // core: T <- (T + dS) x_1 R_1 ... x_p R_p
-  int64_t Rprod = 1;
-  for (int n = 0; n < p; ++n) Rprod *= ctx->r[n];
-  launch_add<Tc>(ctx->T, (const Tc*)ctx->dS, ctx->T2, Rprod, s);
+  // a3..a6 and the refresh of G_n, G_n^{-1}, sigma^(n): one cooperative launch
   {
-    double* src = ctx->T2;
-    double* bufs[2] = {ctx->T, ctx->T2};
+    UpdArgs a;
+    memset(&a, 0, sizeof(a));
+    a.d = mode_desc(ctx);
+    int64_t Rprod = 1, ntiles = 0;
+    for (int n = 0; n < p; ++n) Rprod *= ctx->r[n];
     for (int n = 0; n < p; ++n) {
-      int64_t L = 1, Q = 1;
-      for (int m = 0; m < n; ++m) L *= ctx->r[m];
-      for (int m = n + 1; m < p; ++m) Q *= ctx->r[m];
-      double* dst = (src == bufs[0]) ? bufs[1] : bufs[0];
-      launch_modeprod<double, double, double>(src, dst, ctx->R + (int64_t)n * kMaxRank * kMaxRank, L, ctx->r[n],
-                                              ctx->r[n], Q, 1, kMaxRank, s);
-      src = dst;
+      a.Y[n] = ctx->Y[n];
+      a.U[n] = ctx->U[n];
+      a.Up[n] = ctx->Up[n];
+      a.X[n] = ctx->X[n];
+      a.w[n] = ctx->w[n];
+      a.A[n] = ctx->A[n];
+      a.Uc[n] = ctx->Uc[n];
+      ntiles += (ctx->N[n] + 31) / 32;
     }
-    if (src != ctx->T) CK(cudaMemcpyAsync(ctx->T, src, sizeof(double) * Rprod, cudaMemcpyDeviceToDevice, s));
+    a.dS = ctx->dS;
+    a.T = ctx->T;
+    a.T2 = ctx->T2;
+    a.Tcore = ctx->Tcore;
+    a.G = ctx->G;
+    a.Ginv = ctx->Ginv;
+    a.Ginvf = ctx->Ginvf;
+    a.R = ctx->R;
+    a.Rinv = ctx->Rinv;
+    a.sig2 = ctx->sig2;
+    a.Vprev = ctx->Vprev;
+    a.part = ctx->rowpart;
+    a.ntile = ctx->ntile;
+    a.gpart = ctx->Gpart;
+    a.gsplit = gram_split(ctx->r, p, ctx->gsplit);
+    a.warm = ctx->warm ? 1 : 0;
+    a.reorth = ctx->cfg.reorth != 0;
+    a.bar = ctx->bar;
+    a.stamps = ctx->prof ? ctx->stamps : nullptr;
+    a.flags = ctx->flags;
+    const int64_t hint = std::max<int64_t>({ntiles, (int64_t)p * a.gsplit, Rprod / 2048});
+    const tdb_status us = launch_update<Tc>(a, (int)std::min<int64_t>(hint, 1 << 20), s);
+    if (us != TDB_OK) {
+      ctx->err = us == TDB_ERR_UNSUPPORTED ? "cooperative launch unsupported" : "fused update launch failed";
+      return us;
+    }
+    ctx->warm = true;
+    CHECK_LAUNCH();
   }
-  CHECK_LAUNCH();
-  TRY(refresh_derived<Tc>(ctx, false));
   if (ev) CK(cudaEventRecord(ev[2], s));
   // a7: error, exact or estimated
   ctx->step++;
@@ -1322,6 +1333,7 @@ tdb_status tdb_set_profiling(tdb_ctx* ctx, int enable) {
     for (int i = 0; i < 6; ++i)
       if (!ctx->pev[i]) CK(cudaEventCreate(&ctx->pev[i]));
     memset(&ctx->pacc, 0, sizeof(ctx->pacc));
+    CK(cudaMemsetAsync(ctx->stamps, 0, 32 * sizeof(unsigned long long), ctx->stream));
   }
   ctx->prof = enable != 0;
   return TDB_OK;
@@ -1329,6 +1341,11 @@ tdb_status tdb_set_profiling(tdb_ctx* ctx, int enable) {
 
 tdb_status tdb_get_profile(tdb_ctx* ctx, tdb_profile* out) {
   if (!ctx || !out) return TDB_ERR_INVALID_ARG;
+  unsigned long long st[32];
+  CK(cudaMemcpyAsync(st, ctx->stamps, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->pacc.update_phases = std::min(6 + ctx->p, 12);
+  for (int k = 0; k < 12; ++k) ctx->pacc.us_update_phase[k] = k < ctx->pacc.update_phases ? 1e-3 * (double)st[16 + k] : 0.0;
   *out = ctx->pacc;
   return TDB_OK;
 }
