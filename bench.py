@@ -304,7 +304,7 @@ def run_tdb(args, world, rank, local):
 
     def make(prec, mode):
         c = tdb.TDB(wl.dims, wl.rank, rank_max=wl.rank_max, weights=wl.weights, eps_th=wl.eps_th,
-                    gamma_th=wl.gamma_th, precision=prec, error_mode=mode, error_every=50, device=dev)
+                    gamma_th=wl.gamma_th, precision=prec, error_mode=mode, error_every=20, device=dev)
         return c
 
     def run(prec, timed_profile=True, mode=None):
@@ -447,7 +447,7 @@ def train_estimator(args, wl, precision, dev, tdb, S):
     c.close()
     return params, {"train_stream": f"{args.workload} stream with seed {tseed}, {args.train_steps} exact steps",
                     "fit_seconds": fit_s, "fit_loss": loss,
-                    "gate": 0.9, "max_skip": 50}
+                    "gate": 0.9, "max_skip": 20}
 
 
 def run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_params=None):
@@ -455,7 +455,7 @@ def run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_para
     host = torch.empty_like(snaps, device="cpu").pin_memory()
     host.copy_(snaps)
     c = tdb.TDB(wl.dims, wl.rank, rank_max=wl.rank_max, weights=wl.weights, eps_th=wl.eps_th,
-                gamma_th=wl.gamma_th, precision=precision, error_mode=err_mode, error_every=50, device=dev)
+                gamma_th=wl.gamma_th, precision=precision, error_mode=err_mode, error_every=20, device=dev)
     ring = [torch.empty_like(snaps[0]) for _ in range(2)]
     stream = torch.cuda.current_stream(dev)
     ring[0].copy_(host[0], non_blocking=True)

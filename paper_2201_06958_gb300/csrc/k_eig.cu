@@ -1,0 +1,770 @@
+// k_eig.cu - truncated-HOSVD spectra for the float compute types (Sec. 2.3 last
+// paragraph, Sec. 2.5): the weighted mode-n Gram
+//     C_n = W_n^{1/2} V_(n) W_{-n} V_(n)^T W_n^{1/2}
+// formed as Vw_(n) Vw_(n)^T with Vw = V scaled by sqrt(w_1 ... w_p) once, and its
+// leading eigenpairs by block subspace iteration with Rayleigh-Ritz in one
+// cooperative launch.
+//
+// Precision: products in float, 32-column chunk sums in float, chunks accumulated
+// as float-float pairs (TwoSum), so the Gram carries the float rounding of the
+// chunk sums and nothing coarser; the subspace iteration and Ritz values are float
+// (eigenvalues to ~1e-7 of the largest, which resolves the energy fractions of
+// Eq. 2.21 used by the rank rule), the eigenvectors are returned in double.
+#include "common.cuh"
+#include "kernels.h"
+
+namespace tdb {
+
+namespace {
+
+constexpr int SY_T = 64;          // Gram output tile
+constexpr int SY_K = 32;          // columns per chunk
+constexpr int EIG_THREADS = 256;
+constexpr int RB = 16;            // rows per row block in the eigensolver
+constexpr int MMAX = 64;          // block size limit
+constexpr int LDM = MMAX + 1;     // leading dimension of m x m float matrices in shared memory
+
+__device__ __forceinline__ void two_sum(float& hi, float& lo, float x) {
+  const float s = hi + x;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (x - bb);
+  hi = s;
+  lo += err;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Bounded grid barrier (monotonic counter zeroed before the launch; the k-th barrier
+// waits for k * gridDim.x arrivals).
+__device__ bool eig_grid_sync(unsigned* count, unsigned k, unsigned* flags, volatile int* abort_sh) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    red_release_gpu(count, 1u);
+    const unsigned target = k * gridDim.x;
+    const long long t0 = clock64();
+    while (ld_acquire_gpu(count) < target) {
+      if (clock64() - t0 > 4000000000ll || (ld_acquire_gpu(flags) & kFlagTimeout)) {
+        atomicOr(flags, kFlagTimeout);
+        *abort_sh = 1;
+        break;
+      }
+      __nanosleep(20);
+    }
+  }
+  __syncthreads();
+  return *abort_sh == 0;
+}
+
+__device__ __forceinline__ float hash_unit(uint32_t i, uint32_t j) {
+  uint32_t h = i * 0x9E3779B1u ^ (j + 0x7F4A7C15u) * 0x85EBCA77u;
+  h ^= h >> 15; h *= 0x2C1B3C6Du; h ^= h >> 12; h *= 0x297A2D39u; h ^= h >> 15;
+  return (float)(h & 0xFFFFFF) / 8388608.0f - 1.0f;   // [-1, 1)
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Vw = V * sqrt(w_1[i_1] ... w_p[i_p])   (ws[n] = sqrt(w_n) in float)
+// ---------------------------------------------------------------------------
+struct SqrtWeights {
+  int p;
+  int N[kMaxModes];
+  const float* ws[kMaxModes];
+};
+
+__global__ void k_weight_data(const float* __restrict__ V, SqrtWeights sw, int S, float* __restrict__ Vw) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < S; e += gridDim.x * blockDim.x) {
+    int rem = e;
+    float f = 1.f;
+    for (int n = 0; n < sw.p; ++n) {
+      const int i = rem % sw.N[n];
+      rem /= sw.N[n];
+      f *= sw.ws[n][i];
+    }
+    Vw[e] = V[e] * f;
+  }
+}
+
+__global__ void k_sqrt_weights(const double* __restrict__ w, int n, float* __restrict__ ws) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) ws[i] = (float)sqrt(w[i]);
+}
+
+// ---------------------------------------------------------------------------
+// Gram tiles: blockIdx.x = upper tile pair (ti <= tj) of 64 x 64, blockIdx.y =
+// column slice.  256 threads, 4 x 4 outputs each.  Column c of Vw_(n) is (l, q):
+// Vw[l + L (i + N q)].
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_syrk_partial(const float* __restrict__ Vw, int64_t L, int64_t Nn, int64_t Q,
+                                                      int ntile, int ksplit, double* __restrict__ part) {
+  int t = blockIdx.x, ti = 0;
+  while (t >= ntile - ti) { t -= ntile - ti; ++ti; }
+  const int tj = ti + t;
+  const bool diag = (ti == tj);
+  const int64_t i0 = (int64_t)ti * SY_T, j0 = (int64_t)tj * SY_T;
+  const int64_t ncol = L * Q;
+  const int64_t c0 = ncol * blockIdx.y / ksplit, c1 = ncol * (blockIdx.y + 1) / ksplit;
+  __shared__ __align__(16) float As[SY_K][SY_T + 4];
+  __shared__ __align__(16) float Bs[SY_K][SY_T + 4];
+  const int tid = threadIdx.x;
+  const int tr = tid & 15, tc = tid >> 4;       // output rows tr*4.., columns tc*4..
+  const bool rows_fast = (L == 1);
+  // load mapping: 8 elements per panel per thread.  With L == 1 the lanes run along
+  // rows (contiguous) and column c is q = c; otherwise the lanes run along columns
+  // (l contiguous) and each thread keeps its column's (l, q), advanced by 32 per chunk.
+  const int ccol = tid & 31;
+  int64_t lcur = 0, qcur = 0;
+  if (!rows_fast) { lcur = (c0 + ccol) % L; qcur = (c0 + ccol) / L; }
+  auto load = [&](int64_t cb, float* ra, float* rb) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      int ri;
+      int64_t c, l, q;
+      if (rows_fast) { ri = tid & 63; c = cb + (tid >> 6) + 4 * u; l = 0; q = c; }
+      else { ri = (tid >> 5) + 8 * u; c = cb + ccol; l = lcur; q = qcur; }
+      float va = 0.f, vb = 0.f;
+      if (c < c1) {
+        const int64_t ia = i0 + ri, ib = j0 + ri;
+        if (ia < Nn) va = Vw[l + L * (ia + Nn * q)];
+        if (!diag && ib < Nn) vb = Vw[l + L * (ib + Nn * q)];
+      }
+      ra[u] = va;
+      rb[u] = vb;
+    }
+    if (!rows_fast) {
+      lcur += SY_K;
+      while (lcur >= L) { lcur -= L; ++qcur; }
+    }
+  };
+  auto store = [&](const float* ra, const float* rb) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      int ri, cc;
+      if (rows_fast) { ri = tid & 63; cc = (tid >> 6) + 4 * u; }
+      else { cc = ccol; ri = (tid >> 5) + 8 * u; }
+      As[cc][ri] = ra[u];
+      if (!diag) Bs[cc][ri] = rb[u];
+    }
+  };
+  float hi[16], lo[16];
+#pragma unroll
+  for (int x = 0; x < 16; ++x) { hi[x] = 0.f; lo[x] = 0.f; }
+  float ra[8], rb[8];
+  load(c0, ra, rb);
+  for (int64_t cb = c0; cb < c1; cb += SY_K) {
+    __syncthreads();
+    store(ra, rb);
+    __syncthreads();
+    if (cb + SY_K < c1) load(cb + SY_K, ra, rb);
+    const float (*Bp)[SY_T + 4] = diag ? As : Bs;
+    float acc[16];
+#pragma unroll
+    for (int x = 0; x < 16; ++x) acc[x] = 0.f;
+#pragma unroll 4
+    for (int k = 0; k < SY_K; ++k) {
+      const float4 a = *reinterpret_cast<const float4*>(&As[k][tr * 4]);
+      const float4 b = *reinterpret_cast<const float4*>(&Bp[k][tc * 4]);
+      const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 4; ++y) acc[x * 4 + y] = fmaf(av[x], bv[y], acc[x * 4 + y]);
+    }
+#pragma unroll
+    for (int x = 0; x < 16; ++x) two_sum(hi[x], lo[x], acc[x]);
+  }
+  double* out = part + ((int64_t)blockIdx.x * ksplit + blockIdx.y) * SY_T * SY_T;
+#pragma unroll
+  for (int x = 0; x < 4; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y)
+      out[(tr * 4 + x) + SY_T * (tc * 4 + y)] = (double)hi[x * 4 + y] + (double)lo[x * 4 + y];
+}
+
+// Sum the slices: C64 (double) and Cc (float), both full n x n; trace of C64.
+__global__ void k_syrk_finish(int64_t Nn, int ntile, int ksplit, const double* __restrict__ part,
+                              double* __restrict__ C64, float* __restrict__ Cc) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < Nn * Nn; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % Nn, j = e / Nn;
+    const int64_t a = i <= j ? i : j, b = i <= j ? j : i;
+    const int ti = (int)(a / SY_T), tj = (int)(b / SY_T);
+    const int pair = ti * ntile - ti * (ti - 1) / 2 + (tj - ti);
+    int x = (int)(a % SY_T), y = (int)(b % SY_T);
+    if (ti == tj && x > y) { const int t = x; x = y; y = t; }
+    double s = 0.0;
+    const double* src = part + (int64_t)pair * ksplit * SY_T * SY_T + x + SY_T * y;
+    for (int k = 0; k < ksplit; ++k) s += src[(int64_t)k * SY_T * SY_T];
+    C64[e] = s;
+    Cc[e] = (float)s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Eigensolver.  CTA 0 does the m x m work; CTAs 1.. own row blocks of 16 rows.
+// Iteration: Z <- C Q with Q = Z X and X^T (Z^T Z) X = I; the m x m factor X of
+// the next Gram is computed on CTA 0 while the other CTAs form W = C Z, so an
+// iteration takes two grid barriers.  X comes from Gaussian elimination of the
+// diagonally scaled Gram without pivoting: [G^ | I] -> [U | E], G^ = E^{-1} D_u E^{-T},
+// X = D^{-1} E^T D_u^{-1/2} (shifted diagonal retried if a pivot fails).
+// ---------------------------------------------------------------------------
+struct EigArgs {
+  const float* C;        // n x n (ld n)
+  const double* C64;     // n x n, for the trace
+  int n, m, k, iters;
+  float* Z;              // n x m, row-major (ld m)
+  float* W;              // n x m, row-major (ld m); at the end the Ritz vectors, ld k
+  float* Gp;             // gridDim.x x m x m partial Grams
+  float* Xg;             // m x m
+  double* ev;            // k eigenvalues, descending
+  double* Qout;          // n x k eigenvectors
+  double* trace;
+  unsigned* bar;
+  unsigned* flags;
+};
+
+// CTA 0: X from the summed partial Grams (upper triangles of the row-block CTAs).
+__device__ void eig_factor(const EigArgs& a, float* Gs, float* Es, float* dsc, int* fail) {
+  const int m = a.m, tid = threadIdx.x;
+  const int nb = gridDim.x;
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int i = e % m, j = e / m;
+    const int aa = i <= j ? i : j, bb = i <= j ? j : i;
+    float s = 0.f;
+    for (int c = 1; c < nb; ++c) s += __ldcg(&a.Gp[(int64_t)c * m * m + aa + m * bb]);
+    Gs[i + LDM * j] = s;
+  }
+  __syncthreads();
+  for (int i = tid; i < m; i += blockDim.x) {
+    const float g = Gs[i + LDM * i];
+    dsc[i] = g > 0.f ? rsqrtf(g) : 1.f;
+  }
+  __syncthreads();
+  float* A = Gs + MMAX * LDM;            // working copy, m x m
+  for (int attempt = 0; attempt < 3; ++attempt) {
+    const float shift = attempt == 0 ? 0.f : (attempt == 1 ? 1e-5f : 1e-2f);
+    if (tid == 0) *fail = 0;
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      const int i = e % m, j = e / m;
+      A[i + LDM * j] = Gs[i + LDM * j] * dsc[i] * dsc[j] + (i == j ? shift : 0.f);
+      Es[i + LDM * j] = (i == j) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    for (int k = 0; k < m; ++k) {
+      const float piv = A[k + LDM * k];
+      if (!(piv > 1e-30f)) {
+        if (tid == 0) *fail = 1;
+      } else {
+        const float ip = 1.f / piv;
+        // rows below k: row_i -= (a_ik / a_kk) row_k on U (columns > k) and E (columns <= k)
+        const int rows = m - 1 - k;
+        for (int e = tid; e < rows * m; e += blockDim.x) {
+          const int i = k + 1 + e % rows, c = e / rows;
+          const float f = A[i + LDM * k] * ip;
+          if (c > k) A[i + LDM * c] = fmaf(-f, A[k + LDM * c], A[i + LDM * c]);
+          else Es[i + LDM * c] = fmaf(-f, Es[k + LDM * c], Es[i + LDM * c]);
+        }
+      }
+      __syncthreads();
+    }
+    if (*fail == 0) break;
+    if (attempt == 2 && tid == 0) atomicOr(a.flags, kFlagEigNoConv);
+    __syncthreads();
+  }
+  // X[i][j] = dsc[i] * E[j][i] / sqrt(u_jj)  (upper triangular)
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int i = e % m, j = e / m;
+    const float u = A[j + LDM * j];
+    a.Xg[i + m * j] = (j >= i) ? dsc[i] * Es[j + LDM * i] * (u > 0.f ? rsqrtf(u) : 0.f) : 0.f;
+  }
+}
+
+// Rows [r0, r0 + RB): out = C[rows, :] Zin (n x m).  The whole Zin is staged in
+// shared memory (chunks of ZCH rows), C rows in [RB][ZCH + 1].  Thread layout: row
+// pair rp (8), column quad cq (mq), l-split ls; partial sums reduced in shared memory.
+__device__ void eig_rows_cz(const EigArgs& a, const float* __restrict__ Zin, int r0, float* out, float* sm, int ZCH) {
+  const int n = a.n, m = a.m, tid = threadIdx.x;
+  const int mq = (m + 3) / 4, mp = mq * 4;
+  float* Zs = sm;                         // ZCH x mp
+  float* Cs = Zs + ZCH * mp;              // RB x (ZCH + 1)
+  float* Rs = Cs + RB * (ZCH + 1);        // reduction: nls x RB x mp
+  const int nthr_rc = 8 * mq;
+  const int nls = EIG_THREADS / nthr_rc;
+  const int rp = tid % 8, cq = (tid / 8) % mq, ls = tid / nthr_rc;
+  float acc[2][4];
+#pragma unroll
+  for (int x = 0; x < 2; ++x)
+#pragma unroll
+    for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
+  for (int l0 = 0; l0 < n; l0 += ZCH) {
+    const int lc = min(ZCH, n - l0);
+    __syncthreads();
+    for (int e = tid; e < lc * mp; e += blockDim.x) {
+      const int l = e / mp, c = e % mp;
+      Zs[e] = (c < m) ? __ldcg(&Zin[(int64_t)(l0 + l) * m + c]) : 0.f;
+    }
+    for (int e = tid; e < RB * lc; e += blockDim.x) {
+      const int rr = e / lc, l = e % lc;
+      const int row = r0 + rr;
+      Cs[rr * (ZCH + 1) + l] = (row < n) ? a.C[(l0 + l) + (int64_t)n * row] : 0.f;   // C symmetric: row = column
+    }
+    __syncthreads();
+    if (ls < nls) {
+      const int lb = lc * ls / nls, le = lc * (ls + 1) / nls;
+      for (int l = lb; l < le; ++l) {
+        const float c0 = Cs[(2 * rp) * (ZCH + 1) + l], c1 = Cs[(2 * rp + 1) * (ZCH + 1) + l];
+        const float4 z = *reinterpret_cast<const float4*>(&Zs[l * mp + cq * 4]);
+        acc[0][0] = fmaf(c0, z.x, acc[0][0]); acc[0][1] = fmaf(c0, z.y, acc[0][1]);
+        acc[0][2] = fmaf(c0, z.z, acc[0][2]); acc[0][3] = fmaf(c0, z.w, acc[0][3]);
+        acc[1][0] = fmaf(c1, z.x, acc[1][0]); acc[1][1] = fmaf(c1, z.y, acc[1][1]);
+        acc[1][2] = fmaf(c1, z.z, acc[1][2]); acc[1][3] = fmaf(c1, z.w, acc[1][3]);
+      }
+    }
+  }
+  __syncthreads();
+  if (ls < nls)
+#pragma unroll
+    for (int x = 0; x < 2; ++x)
+#pragma unroll
+      for (int y = 0; y < 4; ++y) Rs[(ls * RB + 2 * rp + x) * mp + cq * 4 + y] = acc[x][y];
+  __syncthreads();
+  for (int e = tid; e < RB * m; e += blockDim.x) {
+    const int rr = e % RB, c = e / RB;
+    float s = 0.f;
+    for (int q = 0; q < nls; ++q) s += Rs[(q * RB + rr) * mp + c];
+    if (r0 + rr < n) out[(int64_t)(r0 + rr) * m + c] = s;
+  }
+}
+
+// Rows [r0, r0 + RB): Z = W X (X upper) and this block's partial of Z^T Z (upper).
+__device__ void eig_rows_apply(const EigArgs& a, int r0, float* Gpart, float* sm, bool accumulate) {
+  const int n = a.n, m = a.m, tid = threadIdx.x;
+  float* Xs = sm;                         // m x m (ld LDM)
+  float* Ws = Xs + MMAX * LDM;            // RB x m (ld LDM)
+  float* Zs = Ws + RB * LDM;              // RB x m
+  for (int e = tid; e < m * m; e += blockDim.x) Xs[(e % m) + LDM * (e / m)] = __ldcg(&a.Xg[e]);
+  for (int e = tid; e < RB * m; e += blockDim.x) {
+    const int rr = e % RB, c = e / RB;
+    Ws[rr * LDM + c] = (r0 + rr < n) ? __ldcg(&a.W[(int64_t)(r0 + rr) * m + c]) : 0.f;
+  }
+  __syncthreads();
+  for (int e = tid; e < RB * m; e += blockDim.x) {
+    const int rr = e % RB, c = e / RB;
+    float s = 0.f;
+    for (int l = 0; l <= c; ++l) s = fmaf(Ws[rr * LDM + l], Xs[l + LDM * c], s);
+    Zs[rr * LDM + c] = s;
+    if (r0 + rr < n) a.Z[(int64_t)(r0 + rr) * m + c] = s;
+  }
+  __syncthreads();
+  for (int e = tid; e < m * m; e += blockDim.x) {
+    const int i = e % m, j = e / m;
+    if (i > j) continue;
+    float s = 0.f;
+#pragma unroll 4
+    for (int rr = 0; rr < RB; ++rr) s = fmaf(Zs[rr * LDM + i], Zs[rr * LDM + j], s);
+    Gpart[e] = accumulate ? Gpart[e] + s : s;
+  }
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
+  extern __shared__ __align__(16) float smf[];
+  __shared__ int abort_sh, fail_sh;
+  __shared__ float dsc[MMAX];
+  if (threadIdx.x == 0) abort_sh = 0;
+  __syncthreads();
+  const int n = a.n, m = a.m, tid = threadIdx.x;
+  const int nrb = (n + RB - 1) / RB;
+  const int nb = gridDim.x;
+  unsigned nbar = 0;
+  float* myG = a.Gp + (int64_t)blockIdx.x * m * m;
+  // start: Z = hash columns, partial Grams
+  if (blockIdx.x > 0) {
+    bool first = true;
+    for (int rb = blockIdx.x - 1; rb < nrb; rb += nb - 1) {
+      const int r0 = rb * RB;
+      float* Zs = smf;
+      for (int e = tid; e < RB * m; e += blockDim.x) {
+        const int rr = e % RB, c = e / RB;
+        const float v = (r0 + rr < n) ? hash_unit((uint32_t)(r0 + rr), (uint32_t)c) : 0.f;
+        Zs[rr * LDM + c] = v;
+        if (r0 + rr < n) a.Z[(int64_t)(r0 + rr) * m + c] = v;
+      }
+      __syncthreads();
+      for (int e = tid; e < m * m; e += blockDim.x) {
+        const int i = e % m, j = e / m;
+        if (i > j) continue;
+        float s = 0.f;
+        for (int rr = 0; rr < RB; ++rr) s = fmaf(Zs[rr * LDM + i], Zs[rr * LDM + j], s);
+        myG[e] = first ? s : myG[e] + s;
+      }
+      __syncthreads();
+      first = false;
+    }
+    if (first)
+      for (int e = tid; e < m * m; e += blockDim.x) myG[e] = 0.f;
+  }
+  if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
+  for (int it = 0; it <= a.iters; ++it) {
+    // phase 1: CTA 0 factors the Gram of Z; the others form W = C Z
+    if (blockIdx.x == 0) {
+      eig_factor(a, smf, smf + 2 * MMAX * LDM, dsc, &fail_sh);
+    } else {
+      for (int rb = blockIdx.x - 1; rb < nrb; rb += nb - 1) eig_rows_cz(a, a.Z, rb * RB, a.W, smf, ZCH);
+    }
+    if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
+    if (it == a.iters) break;
+    // phase 2: Z = W X (= C Q) and its partial Grams
+    if (blockIdx.x > 0) {
+      bool first = true;
+      for (int rb = blockIdx.x - 1; rb < nrb; rb += nb - 1) {
+        eig_rows_apply(a, rb * RB, myG, smf, !first);
+        first = false;
+      }
+      if (first)
+        for (int e = tid; e < m * m; e += blockDim.x) myG[e] = 0.f;
+    }
+    if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
+  }
+  // Rayleigh-Ritz.  Now Z = C Q_prev, W = C Z, X orthonormalises Z: Q = Z X,
+  // H = Q^T C Q = X^T (Z^T W) X.  Partial M = Z^T W per CTA.
+  if (blockIdx.x > 0) {
+    float* Zs = smf;
+    float* Ws = Zs + RB * LDM;
+    bool first = true;
+    for (int rb = blockIdx.x - 1; rb < nrb; rb += nb - 1) {
+      const int r0 = rb * RB;
+      for (int e = tid; e < RB * m; e += blockDim.x) {
+        const int rr = e % RB, c = e / RB;
+        const bool in = r0 + rr < n;
+        Zs[rr * LDM + c] = in ? __ldcg(&a.Z[(int64_t)(r0 + rr) * m + c]) : 0.f;
+        Ws[rr * LDM + c] = in ? __ldcg(&a.W[(int64_t)(r0 + rr) * m + c]) : 0.f;
+      }
+      __syncthreads();
+      for (int e = tid; e < m * m; e += blockDim.x) {
+        const int i = e % m, j = e / m;
+        float s = 0.f;
+        for (int rr = 0; rr < RB; ++rr) s = fmaf(Zs[rr * LDM + i], Ws[rr * LDM + j], s);
+        myG[e] = first ? s : myG[e] + s;
+      }
+      __syncthreads();
+      first = false;
+    }
+    if (first)
+      for (int e = tid; e < m * m; e += blockDim.x) myG[e] = 0.f;
+  }
+  if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
+  // CTA 0: H, Jacobi, ordering; P = X S[:, order] written to W's first m x k block
+  if (blockIdx.x == 0) {
+    float* Ms = smf;                      // m x m
+    float* Xs = Ms + MMAX * LDM;          // m x m
+    float* Hs = Xs + MMAX * LDM;          // m x m
+    float* Vs = Hs + MMAX * LDM;          // m x m
+    float* cs = Vs + MMAX * LDM;          // 2 * MMAX
+    int* pq = (int*)(cs + 2 * MMAX);      // 2 * MMAX
+    int* ord = pq + 2 * MMAX;             // MMAX
+    float* red = (float*)(ord + MMAX);    // 64
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      const int i = e % m, j = e / m;
+      float s = 0.f;
+      for (int c = 1; c < nb; ++c) s += __ldcg(&a.Gp[(int64_t)c * m * m + e]);
+      Ms[i + LDM * j] = s;
+      Xs[i + LDM * j] = __ldcg(&a.Xg[e]);
+    }
+    __syncthreads();
+    for (int e = tid; e < m * m; e += blockDim.x) {          // Vs = M X (temporary)
+      const int i = e % m, j = e / m;
+      float s = 0.f;
+      for (int l = 0; l <= j; ++l) s = fmaf(Ms[i + LDM * l], Xs[l + LDM * j], s);
+      Vs[i + LDM * j] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < m * m; e += blockDim.x) {          // H = X^T (M X), symmetrised below
+      const int i = e % m, j = e / m;
+      float s = 0.f;
+      for (int l = 0; l <= i; ++l) s = fmaf(Xs[l + LDM * i], Vs[l + LDM * j], s);
+      Hs[i + LDM * j] = s;
+    }
+    __syncthreads();
+    for (int e = tid; e < m * m; e += blockDim.x) {
+      const int i = e % m, j = e / m;
+      if (i < j) {
+        const float h = 0.5f * (Hs[i + LDM * j] + Hs[j + LDM * i]);
+        Hs[i + LDM * j] = h;
+        Hs[j + LDM * i] = h;
+      }
+    }
+    __syncthreads();
+    // cyclic Jacobi (Brent-Luk ordering) on H, eigenvectors in Vs
+    const int nn = (m + 1) & ~1, half = nn / 2;
+    for (int e = tid; e < nn * nn; e += blockDim.x) {
+      const int i = e % nn, j = e / nn;
+      if (i >= m || j >= m) Hs[i + LDM * j] = 0.f;
+      Vs[i + LDM * j] = (i == j) ? 1.f : 0.f;
+    }
+    __syncthreads();
+    const float tol = 1e-6f, thr = 1e-9f;
+    float off_prev = 0.f;
+    for (int sweep = 0; sweep < 40; ++sweep) {
+      float off = 0.f, dia = 0.f;
+      for (int e = tid; e < nn * nn; e += blockDim.x) {
+        const int i = e % nn, j = e / nn;
+        const float v = Hs[i + LDM * j];
+        if (i == j) dia += v * v; else off += v * v;
+      }
+      off = warp_sum(off);
+      dia = warp_sum(dia);
+      if ((tid & 31) == 0) { red[tid >> 5] = off; red[8 + (tid >> 5)] = dia; }
+      __syncthreads();
+      off = 0.f;
+      dia = 0.f;
+      for (int w = 0; w < EIG_THREADS / 32; ++w) { off += red[w]; dia += red[8 + w]; }
+      __syncthreads();
+      if (off <= tol * tol * dia || dia == 0.f) break;
+      if (sweep >= 3 && off > 0.5f * off_prev) break;
+      off_prev = off;
+      for (int rd = 0; rd < nn - 1; ++rd) {
+        if (tid < half) {
+          const int k = tid;
+          int p = rd, q = nn - 1;
+          if (k > 0) {
+            p = rd + k;
+            if (p >= nn - 1) p -= nn - 1;
+            q = rd - k;
+            if (q < 0) q += nn - 1;
+          }
+          const float app = Hs[p + LDM * p], aqq = Hs[q + LDM * q], apq = Hs[p + LDM * q];
+          float c = 1.f, s = 0.f;
+          if (apq != 0.f && apq * apq > thr * thr * fabsf(app * aqq)) {
+            const float theta = (aqq - app) / (2.f * apq);
+            const float tt = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+            c = rsqrtf(tt * tt + 1.f);
+            s = tt * c;
+          }
+          cs[2 * k] = c;
+          cs[2 * k + 1] = s;
+          pq[2 * k] = p;
+          pq[2 * k + 1] = q;
+        }
+        __syncthreads();
+        for (int e = tid; e < half * half; e += blockDim.x) {
+          const int I = e % half, J = e / half;
+          const int pI = pq[2 * I], qI = pq[2 * I + 1], pJ = pq[2 * J], qJ = pq[2 * J + 1];
+          const float cI = cs[2 * I], sI = cs[2 * I + 1], cJ = cs[2 * J], sJ = cs[2 * J + 1];
+          const float b00 = Hs[pI + LDM * pJ], b01 = Hs[pI + LDM * qJ], b10 = Hs[qI + LDM * pJ], b11 = Hs[qI + LDM * qJ];
+          const float c00 = cJ * b00 - sJ * b01, c01 = sJ * b00 + cJ * b01;
+          const float c10 = cJ * b10 - sJ * b11, c11 = sJ * b10 + cJ * b11;
+          Hs[pI + LDM * pJ] = cI * c00 - sI * c10;
+          Hs[pI + LDM * qJ] = cI * c01 - sI * c11;
+          Hs[qI + LDM * pJ] = sI * c00 + cI * c10;
+          Hs[qI + LDM * qJ] = sI * c01 + cI * c11;
+        }
+        for (int e = tid; e < nn * half; e += blockDim.x) {
+          const int i = e % nn, J = e / nn;
+          const int pJ = pq[2 * J], qJ = pq[2 * J + 1];
+          const float cJ = cs[2 * J], sJ = cs[2 * J + 1];
+          const float vp = Vs[i + LDM * pJ], vq = Vs[i + LDM * qJ];
+          Vs[i + LDM * pJ] = cJ * vp - sJ * vq;
+          Vs[i + LDM * qJ] = sJ * vp + cJ * vq;
+        }
+        __syncthreads();
+      }
+    }
+    // descending order of the Ritz values (integer ranks of the float keys)
+    for (int j = tid; j < m; j += blockDim.x) {
+      const float vj = Hs[j + LDM * j];
+      int rank = 0;
+      for (int l = 0; l < m; ++l) {
+        const float vl = Hs[l + LDM * l];
+        rank += (vl > vj) || (vl == vj && l < j);
+      }
+      ord[rank] = j;
+    }
+    __syncthreads();
+    for (int j = tid; j < a.k; j += blockDim.x) a.ev[j] = (double)Hs[ord[j] + LDM * ord[j]];
+    for (int e = tid; e < m * a.k; e += blockDim.x) {        // P = X S[:, ord[:k]] -> Xg (m x k)
+      const int i = e % m, j = e / m;
+      const int oj = ord[j];
+      float s = 0.f;
+      for (int l = i; l < m; ++l) s = fmaf(Xs[i + LDM * l], Vs[l + LDM * oj], s);
+      a.Xg[i + m * j] = s;
+    }
+    if (tid < 32) {
+      double t = 0.0;
+      for (int i = tid; i < n; i += 32) t += a.C64[i + (int64_t)n * i];
+      t = warp_sum(t);
+      if (tid == 0) *a.trace = t;
+    }
+  }
+  if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
+  // Ritz vectors Y = Z P (n x k) into W; per-CTA column norms^2 and largest |entry|
+  float* colnorm = a.Gp;                                      // [cta][k] norms, [cta][MMAX + k] max |y|, index as float bits
+  if (blockIdx.x > 0) {
+    float* Ps = smf;                      // m x k (ld LDM)
+    float* Zs = Ps + MMAX * LDM;          // RB x m
+    float* Ys = Zs + RB * LDM;            // RB x k
+    float* nrm = Ys + RB * LDM;           // k
+    float* mx = nrm + MMAX;               // k
+    int* ix = (int*)(mx + MMAX);          // k
+    for (int j = tid; j < a.k; j += blockDim.x) { nrm[j] = 0.f; mx[j] = -1.f; ix[j] = 0x7fffffff; }
+    for (int e = tid; e < m * a.k; e += blockDim.x) Ps[(e % m) + LDM * (e / m)] = __ldcg(&a.Xg[e]);
+    __syncthreads();
+    for (int rb = blockIdx.x - 1; rb < nrb; rb += nb - 1) {
+      const int r0 = rb * RB;
+      for (int e = tid; e < RB * m; e += blockDim.x) {
+        const int rr = e % RB, c = e / RB;
+        Zs[rr * LDM + c] = (r0 + rr < n) ? __ldcg(&a.Z[(int64_t)(r0 + rr) * m + c]) : 0.f;
+      }
+      __syncthreads();
+      for (int e = tid; e < RB * a.k; e += blockDim.x) {
+        const int rr = e % RB, j = e / RB;
+        float s = 0.f;
+        for (int l = 0; l < m; ++l) s = fmaf(Zs[rr * LDM + l], Ps[l + LDM * j], s);
+        Ys[rr * LDM + j] = s;
+        if (r0 + rr < n) a.W[(int64_t)(r0 + rr) * a.k + j] = s;
+      }
+      __syncthreads();
+      for (int j = tid; j < a.k; j += blockDim.x) {
+        for (int rr = 0; rr < RB && r0 + rr < n; ++rr) {
+          const float y = Ys[rr * LDM + j];
+          nrm[j] = fmaf(y, y, nrm[j]);
+          const float ay = fabsf(y);
+          if (ay > mx[j]) { mx[j] = ay; ix[j] = r0 + rr; }
+        }
+      }
+      __syncthreads();
+    }
+    for (int j = tid; j < a.k; j += blockDim.x) {
+      colnorm[(int64_t)blockIdx.x * 3 * MMAX + j] = nrm[j];
+      colnorm[(int64_t)blockIdx.x * 3 * MMAX + MMAX + j] = mx[j];
+      colnorm[(int64_t)blockIdx.x * 3 * MMAX + 2 * MMAX + j] = __int_as_float(ix[j]);
+    }
+  }
+  if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
+  // every CTA: the column scales (1 / norm with the sign making the largest |entry|
+  // positive; first index on ties), then its rows of Qout in double
+  {
+    float* scale = smf;                   // k
+    for (int j = tid; j < a.k; j += blockDim.x) {
+      float nr = 0.f, best = -1.f;
+      int bi = 0x7fffffff;
+      for (int c = 1; c < nb; ++c) {
+        nr += __ldcg(&colnorm[(int64_t)c * 3 * MMAX + j]);
+        const float v = __ldcg(&colnorm[(int64_t)c * 3 * MMAX + MMAX + j]);
+        const int ii = __float_as_int(__ldcg(&colnorm[(int64_t)c * 3 * MMAX + 2 * MMAX + j]));
+        if (v > best || (v == best && ii < bi)) { best = v; bi = ii; }
+      }
+      const float ybi = (bi < n) ? __ldcg(&a.W[(int64_t)bi * a.k + j]) : 1.f;
+      scale[j] = (ybi < 0.f ? -1.f : 1.f) * (nr > 0.f ? rsqrtf(nr) : 1.f);
+    }
+    __syncthreads();
+    if (blockIdx.x > 0)
+      for (int rb = blockIdx.x - 1; rb < nrb; rb += nb - 1)
+        for (int e = tid; e < RB * a.k; e += blockDim.x) {
+          const int rr = e % RB, j = e / RB, row = rb * RB + rr;
+          if (row < n) a.Qout[row + (int64_t)n * j] = (double)(__ldcg(&a.W[(int64_t)row * a.k + j]) * scale[j]);
+        }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+void launch_sqrt_weights(const double* w, int n, float* ws, cudaStream_t s) {
+  k_sqrt_weights<<<std::max(1, std::min((n + 255) / 256, 64)), 256, 0, s>>>(w, n, ws);
+  count_launch();
+}
+
+void launch_weight_data(const float* V, int p, const int64_t* N, const float* const* ws, int64_t S, float* Vw,
+                        cudaStream_t s) {
+  SqrtWeights sw;
+  sw.p = p;
+  for (int n = 0; n < kMaxModes; ++n) {
+    sw.N[n] = n < p ? (int)N[n] : 1;
+    sw.ws[n] = n < p ? ws[n] : nullptr;
+  }
+  const int blocks = (int)std::min<int64_t>((S + 255) / 256, 152 * 8);
+  k_weight_data<<<blocks, 256, 0, s>>>(V, sw, (int)S, Vw);
+  count_launch();
+}
+
+void launch_gram_weighted(const float* Vw, int64_t L, int64_t Nn, int64_t Q, double* part, size_t part_cap, double* C64,
+                          float* Cc, cudaStream_t s) {
+  const int ntile = (int)((Nn + SY_T - 1) / SY_T);
+  const int npair = ntile * (ntile + 1) / 2;
+  const int64_t ncol = L * Q;
+  int ksplit = (int)std::max<int64_t>(1, std::min<int64_t>((152 + npair - 1) / npair, (ncol + 127) / 128));
+  while ((size_t)npair * ksplit * SY_T * SY_T > part_cap && ksplit > 1) --ksplit;
+  k_syrk_partial<<<dim3(npair, ksplit), 256, 0, s>>>(Vw, L, Nn, Q, ntile, ksplit, part);
+  count_launch();
+  const int blocks = (int)std::min<int64_t>((Nn * Nn + 255) / 256, 1024);
+  k_syrk_finish<<<blocks, 256, 0, s>>>(Nn, ntile, ksplit, part, C64, Cc);
+  count_launch();
+}
+
+size_t eig_si_scratch_floats(int n) {
+  // Z, W: n x MMAX each; partial Grams / norms: 152 x MMAX x MMAX; Xg: MMAX x MMAX
+  return (size_t)2 * n * MMAX + (size_t)152 * MMAX * MMAX + MMAX * MMAX;
+}
+
+tdb_status eig_si_float(const float* Cc, const double* C64, int n, int k, int iters, float* scratch, unsigned* bar,
+                        unsigned* flags, double* ev, double* Q, double* trace, cudaStream_t s) {
+  const int m = std::min(n, std::min(MMAX, k + 16));
+  if (k > m) return TDB_ERR_INVALID_ARG;
+  static int nsm = 0;
+  static size_t smem_cap = 0;
+  if (nsm == 0) {
+    int dev = 0, coop = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (!coop) { nsm = 0; return TDB_ERR_UNSUPPORTED; }
+    smem_cap = (size_t)optin - 2048;
+  }
+  const int mp = ((m + 3) / 4) * 4;
+  // rows-times-Z phase: ZCH rows of Z staged, plus C rows and the reduction buffer
+  const int nls = EIG_THREADS / (8 * ((m + 3) / 4));
+  int ZCH = n;
+  auto need = [&](int zch) {
+    return ((size_t)zch * mp + (size_t)RB * (zch + 1) + (size_t)nls * RB * mp) * sizeof(float);
+  };
+  while (ZCH > 64 && need(ZCH) > smem_cap) ZCH = (ZCH + 1) / 2;
+  const size_t small = (size_t)(5 * MMAX * LDM + 6 * MMAX + 64) * sizeof(float);
+  const size_t smem = std::max(need(ZCH), small);
+  if (smem > smem_cap) return TDB_ERR_UNSUPPORTED;
+  cudaFuncSetAttribute(k_eig_si, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eig_si, EIG_THREADS, smem);
+  if (per_sm < 1) return TDB_ERR_UNSUPPORTED;
+  const int nrb = (n + RB - 1) / RB;
+  const int grid = std::min(std::min(nsm, 152), nrb + 1);
+  EigArgs a;
+  a.C = Cc;
+  a.C64 = C64;
+  a.n = n;
+  a.m = m;
+  a.k = k;
+  a.iters = iters;
+  a.Z = scratch;
+  a.W = a.Z + (size_t)n * MMAX;
+  a.Gp = a.W + (size_t)n * MMAX;
+  a.Xg = a.Gp + (size_t)152 * MMAX * MMAX;
+  a.ev = ev;
+  a.Qout = Q;
+  a.trace = trace;
+  a.bar = bar;
+  a.flags = flags;
+  cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
+  void* args[] = {(void*)&a, (void*)&ZCH};
+  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_eig_si, grid, EIG_THREADS, args, smem, s);
+  count_launch();
+  return e == cudaSuccess ? TDB_OK : TDB_ERR_CUDA;
+}
+
+}  // namespace tdb

@@ -228,37 +228,45 @@ namespace tdb {
 // re-initialisation + 1), log10 of the previous step's residual.  The network predicts
 // the change of log10 error over the step, so the estimate chains from the previous
 // error and the features do not depend on which steps were evaluated exactly.
-__global__ void k_est_features(EstState st, const float* __restrict__ dS, int nds, const double* __restrict__ dv2,
-                               const double* __restrict__ sig2, int4 ranks, int p, const float* __restrict__ P,
-                               const float* __restrict__ norm, float* __restrict__ feat, double* __restrict__ est,
-                               int* __restrict__ need, double* __restrict__ ds2_out) {
+__global__ void __launch_bounds__(256) k_est_features(EstState st, const float* __restrict__ dS, int nds,
+                                                      const double* __restrict__ dv2, const double* __restrict__ sig2,
+                                                      int4 ranks, int p, const float* __restrict__ P,
+                                                      const float* __restrict__ norm, float* __restrict__ feat,
+                                                      double* __restrict__ est, int* __restrict__ need,
+                                                      double* __restrict__ ds2_out) {
+  // The features are float-valued and ||dS|| is only as accurate as the projection,
+  // so everything is float except the difference ||dV||^2 - ||dS||^2 (double: it can
+  // cancel).  The network's parameters are staged in shared memory with coalesced loads.
+  __shared__ float Ps[MLP_NPARAM];
   __shared__ double sh[32];
   __shared__ float xs[MLP_F], h1[MLP_H];
-  __shared__ float red[2];
-  double s = 0.0;
-  for (int i = threadIdx.x; i < nds; i += blockDim.x) s += (double)dS[i] * (double)dS[i];
-  s = block_sum(s, sh);
-  const double tiny = 1e-300;
-  if (threadIdx.x == 0) {
+  __shared__ float red[8];
+  const int tid = threadIdx.x;
+  for (int i = tid; i < MLP_NPARAM; i += blockDim.x) Ps[i] = P[i];
+  float sf = 0.f;
+  for (int i = tid; i < nds; i += blockDim.x) sf = fmaf(dS[i], dS[i], sf);
+  const double s = block_sum((double)sf, sh);
+  if (tid == 0) {
     const double d2 = *dv2;
-    const double res2 = fmax(d2 - s, 0.0);
-    double smin = 1.0, tot = 0.0;
+    const float res2 = (float)fmax(d2 - s, 0.0);
+    const float tiny = 1e-30f;
+    float smin = 1.f, tot = 0.f;
     const int rr[4] = {ranks.x, ranks.y, ranks.z, ranks.w};
     for (int n = 0; n < p; ++n) {
       const double* sg = sig2 + n * kMaxRank;
-      const double mx = fmax(sg[0], tiny), mn = fmax(sg[rr[n] - 1], tiny);
-      smin = fmin(smin, sqrt(mn / mx));
+      const float mx = fmaxf((float)sg[0], tiny), mn = fmaxf((float)sg[rr[n] - 1], tiny);
+      smin = fminf(smin, sqrtf(mn / mx));
       if (n == 0)
-        for (int i = 0; i < rr[0]; ++i) tot += fmax(sg[i], 0.0);
+        for (int i = 0; i < rr[0]; ++i) tot += fmaxf((float)sg[i], 0.f);
     }
     float f[MLP_F];
     f[0] = (float)st.last_log_eps;
-    f[1] = (float)log10(sqrt(d2) + tiny);
-    f[2] = (float)log10(sqrt(res2) + tiny);
-    f[3] = (float)log10(sqrt(s) + tiny);
-    f[4] = (float)log10(smin + tiny);
-    f[5] = (float)log10(sqrt(tot) + tiny);
-    f[6] = (float)log10((double)st.steps_since_reinit + 1.0);
+    f[1] = log10f(sqrtf((float)d2) + tiny);
+    f[2] = log10f(sqrtf(res2) + tiny);
+    f[3] = log10f(sqrtf((float)s) + tiny);
+    f[4] = log10f(smin + tiny);
+    f[5] = log10f(sqrtf(tot) + tiny);
+    f[6] = log10f((float)st.steps_since_reinit + 1.f);
     f[7] = (float)st.prev_res_log;
     for (int i = 0; i < MLP_F; ++i) {
       feat[i] = f[i];
@@ -268,37 +276,38 @@ __global__ void k_est_features(EstState st, const float* __restrict__ dS, int nd
   }
   __syncthreads();
   if (!st.ready) {
-    if (threadIdx.x == 0) { *need = 1; *est = nan(""); }
+    if (tid == 0) { *need = 1; *est = nan(""); }
     return;
   }
-  // forward pass, one sample, 64 threads
-  const int j = threadIdx.x;
-  const float* W1 = P;
+  // forward pass of one sample
+  const float* W1 = Ps;
   const float* b1 = W1 + MLP_H * MLP_F;
   const float* W2 = b1 + MLP_H;
   const float* b2 = W2 + MLP_H * MLP_H;
   const float* w3 = b2 + MLP_H;
-  if (j < MLP_H) {
-    float a = b1[j];
-    for (int f = 0; f < MLP_F; ++f) a += W1[j * MLP_F + f] * xs[f];
-    h1[j] = tanhf(a);
+  if (tid < MLP_H) {
+    float a = b1[tid];
+#pragma unroll
+    for (int f = 0; f < MLP_F; ++f) a = fmaf(W1[tid * MLP_F + f], xs[f], a);
+    h1[tid] = tanhf(a);
   }
   __syncthreads();
-  float part = 0.f;
-  if (j < MLP_H) {
-    float a2 = b2[j];
-    for (int k = 0; k < MLP_H; ++k) a2 += W2[j * MLP_H + k] * h1[k];
-    part = w3[j] * tanhf(a2);
-  }
-  if (j < 64) {
-    part = warp_sum(part);
-    if ((j & 31) == 0) red[j >> 5] = part;
-  }
+  // hidden layer 2: four threads per unit, 16 inputs each, reduced by shuffles
+  const int j = tid >> 2, q = tid & 3;
+  float a2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < MLP_H / 4; ++k) a2 = fmaf(W2[j * MLP_H + q * (MLP_H / 4) + k], h1[q * (MLP_H / 4) + k], a2);
+  a2 += __shfl_xor_sync(0xffffffffu, a2, 1);
+  a2 += __shfl_xor_sync(0xffffffffu, a2, 2);
+  float part = (q == 0) ? w3[j] * tanhf(a2 + b2[j]) : 0.f;
+  part = warp_sum(part);
+  if ((tid & 31) == 0) red[tid >> 5] = part;
   __syncthreads();
-  if (j == 0) {
-    const float yz = red[0] + red[1] + w3[MLP_H];
-    const double dlog = (double)yz * norm[2 * MLP_F + 1] + norm[2 * MLP_F];
-    const double e = pow(10.0, st.last_log_eps + dlog);
+  if (tid == 0) {
+    float yz = w3[MLP_H];
+    for (int w = 0; w < 8; ++w) yz += red[w];
+    const float dlog = yz * norm[2 * MLP_F + 1] + norm[2 * MLP_F];
+    const double e = (double)exp10f((float)st.last_log_eps + dlog);
     *est = e;
     bool novel = false;
     for (int i = 1; i < MLP_F; ++i)
@@ -311,7 +320,7 @@ void est_features(const EstState* st, const float* dS, int nds, const double* dv
                   int p, const float* P, const float* norm, float* feat, double* est, int* need, double* ds2,
                   cudaStream_t s) {
   int4 rk = make_int4(ranks[0], p > 1 ? ranks[1] : 1, p > 2 ? ranks[2] : 1, p > 3 ? ranks[3] : 1);
-  k_est_features<<<1, 64, 0, s>>>(*st, dS, nds, dv2, sig2, rk, p, P, norm, feat, est, need, ds2);
+  k_est_features<<<1, 256, 0, s>>>(*st, dS, nds, dv2, sig2, rk, p, P, norm, feat, est, need, ds2);
   count_launch();
 }
 

@@ -34,14 +34,15 @@ namespace {
 
 constexpr int LD = kMaxRank;
 constexpr int UPD_THREADS = 1024;
-constexpr size_t kUpdSmem = 42 * 1024;   // largest phase: rows M/X/P with Tc = double, 33.5 KB
-constexpr int GJ_THREADS = 256;          // warps 0..7 invert G_n ...
-constexpr int JAC_WARP = 31;             // ... while warp 31 runs the float Jacobi
+constexpr size_t kUpdSmem = 48 * 1024;   // largest phase: the Gram finish, 45.6 KB
+constexpr int GJ_THREADS = 256;          // threads 0..255 invert G_n by Gauss-Jordan
 
 // ---------------------------------------------------------------------------
 // Double reciprocal and reciprocal square root.  The float seed is built from the
-// bit pattern with integer operations (no double-pipe conversion), refined by two
-// Newton steps; |x| outside [2^-120, 2^120] takes the plain division.
+// bit pattern with integer operations (no double-pipe conversion) and refined to a
+// residual of the seed's error to the fourth power (two Newton steps; for the
+// reciprocal the second step's square is formed alongside the first, three
+// dependent operations); |x| outside [2^-120, 2^120] takes the plain division.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool seedable(double x) {
   const unsigned e = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
@@ -70,11 +71,11 @@ __device__ __forceinline__ float rsqrt_approx(float x) {
 }
 __device__ __forceinline__ double drcp(double x) {
   if (!seedable(x)) return 1.0 / x;
-  double y = f64_exact(rcp_approx(f32_trunc(x)));
-  double t = fma(-x, y, 1.0);
-  y = fma(y, t, y);
-  t = fma(-x, y, 1.0);
-  return fma(y, t, y);
+  const double y0 = f64_exact(rcp_approx(f32_trunc(x)));
+  const double e0 = fma(-x, y0, 1.0);           // x y0 = 1 - e0
+  const double y1 = fma(y0, e0, y0);            // y0 (1 + e0)
+  const double e1 = e0 * e0;                    // alongside y1
+  return fma(y1, e1, y1);                       // y0 (1 + e0)(1 + e0^2): residual e0^4
 }
 __device__ __forceinline__ double drsqrt(double x) {           // x > 0
   if (!seedable(x)) return 1.0 / sqrt(x);
@@ -201,48 +202,69 @@ __device__ void trinv_warp_f(const float* L, float* Li, int r) {
 }
 
 // ---------------------------------------------------------------------------
-// Cyclic Jacobi on a symmetric float matrix by one warp (Brent-Luk round-robin
-// ordering, as jacobi_smem): eigenvalues on the diagonal of A, vectors in V.  Stops
-// when the off-diagonal mass is below tol^2 of the diagonal mass, or when a sweep
-// after the second no longer halves it (the float rounding floor).
+// Cyclic Jacobi on a symmetric float matrix (n <= 32, ld LD, shared) by a group of
+// `gs` threads (gt = index in the group, hardware barrier `bar`), Brent-Luk
+// round-robin ordering as jacobi_smem: eigenvalues end on the diagonal of A and the
+// vectors in V.  Stops when the off-diagonal mass is below tol^2 of the diagonal
+// mass, after max_sweeps, or when a sweep after the second no longer halves it
+// (the float rounding floor).  red holds >= 2 * gs / 32 floats.
 // ---------------------------------------------------------------------------
-__device__ int jacobi_warp(float* A, float* V, int n, int max_sweeps, float tol, float* cs, int* pq) {
-  const int lane = threadIdx.x & 31;
+__device__ int jacobi_group(float* A, float* V, int n, int max_sweeps, float tol, float* cs, int* pq, float* red,
+                            int gt, int gs, int bar) {
   const int nn = (n + 1) & ~1, half = nn / 2;
-  for (int e = lane; e < nn * nn; e += 32) {
+  const int nw = gs >> 5, gl = gt & 31, gw = gt >> 5;
+  for (int e = gt; e < nn * nn; e += gs) {
     const int i = e % nn, j = e / nn;
     if (i >= n || j >= n) A[i + LD * j] = 0.f;
     V[i + LD * j] = (i == j) ? 1.f : 0.f;
   }
-  __syncwarp();
+  // the block (I, J) and the V entries (i, J) owned by this thread, fixed for all rounds
+  const int bI = gt % half, bJ = gt / half;
+  const bool has_b = gt < half * half;
+  const int nv = nn * half;
+  named_bar(bar, gs);
   const float thr = tol * 1e-3f;
   float off_prev = 0.f;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     float off = 0.f, dia = 0.f;
-    for (int e = lane; e < nn * nn; e += 32) {
+    for (int e = gt; e < nn * nn; e += gs) {
       const int i = e % nn, j = e / nn;
       const float v = A[i + LD * j];
       if (i == j) dia += v * v; else off += v * v;
     }
     off = warp_sum(off);
     dia = warp_sum(dia);
+    if (gl == 0) { red[gw] = off; red[nw + gw] = dia; }
+    named_bar(bar, gs);
+    off = 0.f;
+    dia = 0.f;
+    for (int w = 0; w < nw; ++w) { off += red[w]; dia += red[nw + w]; }
+    named_bar(bar, gs);
     if (off <= tol * tol * dia || dia == 0.f) break;
-    // converged to the float rounding floor: a sweep that no longer halves the
-    // off-diagonal mass is past the quadratic phase
     if (sweep >= 2 && off > 0.5f * off_prev) break;
     off_prev = off;
     for (int rd = 0; rd < nn - 1; ++rd) {
-      for (int k = lane; k < half; k += 32) {
-        int p, q;
-        if (k == 0) { p = rd; q = nn - 1; }
-        else { p = (rd + k) % (nn - 1); q = (rd - k + (nn - 1)) % (nn - 1); }
+      if (gt < half) {
+        const int k = gt;
+        int p = rd, q = nn - 1;
+        if (k > 0) {
+          p = rd + k;
+          if (p >= nn - 1) p -= nn - 1;
+          q = rd - k;
+          if (q < 0) q += nn - 1;
+        }
         const float app = A[p + LD * p], aqq = A[q + LD * q], apq = A[p + LD * q];
         float c = 1.f, s = 0.f;
         if (apq != 0.f && apq * apq > thr * thr * fabsf(app * aqq)) {
-          const float theta = (aqq - app) / (2.f * apq);
-          const float t = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
-          c = rsqrtf(t * t + 1.f);
+          // tan of the rotation angle, t = sign(theta) / (|theta| + sqrt(theta^2 + 1)),
+          // with approximate reciprocals: c^2 + s^2 = 1 holds whatever t's rounding
+          const float theta = (aqq - app) * rcp_approx(2.f * apq);
+          const float at = fabsf(theta);
+          const float x = fmaf(at, at, 1.f);
+          const float root = (at < 1e18f) ? x * rsqrt_approx(x) : at;
+          const float t = copysignf(rcp_approx(at + root), theta);
+          c = rsqrt_approx(fmaf(t, t, 1.f));
           s = t * c;
         }
         cs[2 * k] = c;
@@ -250,11 +272,10 @@ __device__ int jacobi_warp(float* A, float* V, int n, int max_sweeps, float tol,
         pq[2 * k] = p;
         pq[2 * k + 1] = q;
       }
-      __syncwarp();
-      for (int e = lane; e < half * half; e += 32) {
-        const int I = e % half, J = e / half;
-        const int pI = pq[2 * I], qI = pq[2 * I + 1], pJ = pq[2 * J], qJ = pq[2 * J + 1];
-        const float cI = cs[2 * I], sI = cs[2 * I + 1], cJ = cs[2 * J], sJ = cs[2 * J + 1];
+      named_bar(bar, gs);
+      if (has_b) {
+        const int pI = pq[2 * bI], qI = pq[2 * bI + 1], pJ = pq[2 * bJ], qJ = pq[2 * bJ + 1];
+        const float cI = cs[2 * bI], sI = cs[2 * bI + 1], cJ = cs[2 * bJ], sJ = cs[2 * bJ + 1];
         const float b00 = A[pI + LD * pJ], b01 = A[pI + LD * qJ], b10 = A[qI + LD * pJ], b11 = A[qI + LD * qJ];
         const float c00 = cJ * b00 - sJ * b01, c01 = sJ * b00 + cJ * b01;
         const float c10 = cJ * b10 - sJ * b11, c11 = sJ * b10 + cJ * b11;
@@ -263,7 +284,7 @@ __device__ int jacobi_warp(float* A, float* V, int n, int max_sweeps, float tol,
         A[qI + LD * pJ] = sI * c00 + cI * c10;
         A[qI + LD * qJ] = sI * c01 + cI * c11;
       }
-      for (int e = lane; e < nn * half; e += 32) {
+      for (int e = gt; e < nv; e += gs) {
         const int i = e % nn, J = e / nn;
         const int pJ = pq[2 * J], qJ = pq[2 * J + 1];
         const float cJ = cs[2 * J], sJ = cs[2 * J + 1];
@@ -271,77 +292,86 @@ __device__ int jacobi_warp(float* A, float* V, int n, int max_sweeps, float tol,
         V[i + LD * pJ] = cJ * vp - sJ * vq;
         V[i + LD * qJ] = sJ * vp + cJ * vq;
       }
-      __syncwarp();
+      named_bar(bar, gs);
     }
   }
   return sweep;
 }
 
-// In-place Gauss-Jordan inversion of the SPD matrix A (r x r, ld LD, shared) by the
-// threads [0, nthr) with hardware barrier `bar`; no pivoting (the pivots are the
-// positive Schur-complement diagonals).  Returns false if a pivot is not positive.
-__device__ bool gj_inverse(double* A, int r, double* rowk, double* colk, int nthr, int bar) {
+// Gauss-Jordan inversion of the SPD matrix in A0 (r x r, ld LD, shared) by the
+// threads [0, nthr) with hardware barrier `bar`, no pivoting (the pivots are the
+// positive Schur-complement diagonals).  Step k reads one buffer and writes the
+// other, so a step needs one barrier; returns the buffer holding the inverse.
+// *ok is false if a pivot is not a positive finite number.
+__device__ double* gj_inverse(double* A0, double* A1, int r, int nthr, int bar, bool* ok) {
   const int tid = threadIdx.x;
-  bool ok = true;
+  double* cur = A0;
+  double* nxt = A1;
+  bool good = true;
   for (int k = 0; k < r; ++k) {
-    double p = A[k + LD * k];
-    if (!(p > 0.0)) { ok = false; p = 1.0; }
+    double p = cur[k + LD * k];
+    const int hi = __double2hiint(p);
+    if (hi <= 0 || ((hi >> 20) & 0x7ff) == 0x7ff) { good = false; p = 1.0; }
     const double ip = drcp(p);
-    for (int j = tid; j < r; j += nthr) {
-      rowk[j] = (j == k) ? ip : A[k + LD * j] * ip;
-      colk[j] = A[j + LD * k];
-    }
-    named_bar(bar, nthr);
     for (int e = tid; e < r * r; e += nthr) {
       const int i = e % r, j = e / r;
-      if (i == k) A[k + LD * j] = rowk[j];
-      else A[i + LD * j] = (j == k ? 0.0 : A[i + LD * j]) - colk[i] * rowk[j];
+      const double akj = (j == k) ? ip : cur[k + LD * j] * ip;     // row k after the step
+      nxt[i + LD * j] = (i == k) ? akj : (j == k ? 0.0 : cur[i + LD * j]) - cur[i + LD * k] * akj;
     }
     named_bar(bar, nthr);
+    double* t = cur;
+    cur = nxt;
+    nxt = t;
   }
-  return ok;
+  *ok = good;
+  return cur;
 }
 
 // Bounded grid barrier; every CTA is resident (cooperative launch, <= 1 CTA per SM).
-__device__ __forceinline__ bool grid_sync(unsigned* count, unsigned* gen, unsigned nblocks, unsigned* flags,
+// The counter (zeroed before the launch) only grows: the k-th barrier (k from 1)
+// waits for k * nblocks arrivals.  Release on arrival and acquire on the spin order
+// the CTA's writes before and its reads after the barrier.
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ bool grid_sync(unsigned* count, unsigned k, unsigned nblocks, unsigned* flags,
                                           volatile int* abort_sh) {
   __syncthreads();
   if (threadIdx.x == 0) {
-    volatile unsigned* vgen = gen;
-    const unsigned g = *vgen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(count, 1u);
-    if (arrived == nblocks - 1) {
-      atomicExch(count, 0u);
-      __threadfence();
-      atomicAdd(gen, 1u);
-    } else {
-      const long long t0 = clock64();
-      while (*vgen == g) {
-        if (clock64() - t0 > 4000000000ll || (*(volatile unsigned*)flags & kFlagTimeout)) {
-          atomicOr(flags, kFlagTimeout);
-          *abort_sh = 1;
-          break;
-        }
-        __nanosleep(32);
+    red_release_gpu(count, 1u);
+    const unsigned target = k * nblocks;
+    const long long t0 = clock64();
+    while (ld_acquire_gpu(count) < target) {
+      if (clock64() - t0 > 4000000000ll || (ld_acquire_gpu(flags) & kFlagTimeout)) {
+        atomicOr(flags, kFlagTimeout);
+        *abort_sh = 1;
+        break;
       }
+      __nanosleep(20);
     }
-    __threadfence();
   }
   __syncthreads();
   return *abort_sh == 0;
 }
 
 // Profiling: CTA 0 reads the global timer at the start, after every grid barrier
-// and at its end; st[0..15] keeps the last stamps and st[16 + k] accumulates the
-// nanoseconds of phase k over launches (null when profiling is off).
-__device__ __forceinline__ void stamp(unsigned long long* st, int k) {
+// and at its end into shared memory; at the end it adds the phase durations to
+// st[16 + k] (nanoseconds summed over launches; st null when profiling is off).
+__device__ __forceinline__ void stamp(unsigned long long* sh, const unsigned long long* st, int k) {
   if (st && blockIdx.x == 0 && threadIdx.x == 0) {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    if (k > 0) st[16 + k - 1] += t - st[k - 1];
-    st[k] = t;
+    sh[k] = t;
   }
+}
+__device__ __forceinline__ void stamp_flush(const unsigned long long* sh, unsigned long long* st, int nst) {
+  if (st && blockIdx.x == 0 && threadIdx.x == 0)
+    for (int k = 1; k <= nst; ++k) atomicAdd(&st[16 + k - 1], sh[k] - sh[k - 1]);
 }
 
 }  // namespace
@@ -381,32 +411,35 @@ __device__ void gram_partial(const ModeDesc& d, const double* T, double* gpart, 
   if ((int)threadIdx.x < ntri) gpart[((int64_t)n * gsplit + sp) * LD * LD + ta + LD * tb] = s;
 }
 
-// Mode n: sum the partials into G_n; G_n^{-1} by Gauss-Jordan (warps 0..7) while
-// warp 31 runs the float Jacobi on Vp^T (G / scale) Vp (Vp the previous
+// Mode n: sum the partials into G_n; G_n^{-1} by Gauss-Jordan (threads 0..255)
+// while threads 256..511 run the float Jacobi on Vp^T (G / scale) Vp (Vp the previous
 // eigenvectors, identity when cold); then Rayleigh quotients v^T G v / v^T v in
-// double, sorted descending by an integer key, and the sorted eigenvectors become
-// the next warm start.  One CTA of UPD_THREADS threads; smraw holds >= 34 KB.
+// double, sorted descending by an integer key; the sorted eigenvectors become the
+// next warm start.  One CTA of UPD_THREADS threads; smraw holds >= 46 KB.
 __device__ __noinline__ void gram_finish(const ModeDesc& d, int n, const double* gpart, int gsplit, double* Gout,
                                          double* Ginv, float* Ginvf, double* sig2, float* Vprev, int warm,
                                          unsigned* flags, unsigned char* smraw) {
   const int r = d.r[n];
   double* G = (double*)smraw;          // LD*LD
-  double* Ai = G + LD * LD;            // LD*LD: Gauss-Jordan in place, then G W
-  double* rowk = Ai + LD * LD;         // LD
-  double* colk = rowk + LD;            // LD
-  double* lam = colk + LD;             // LD
+  double* Ai = G + LD * LD;            // LD*LD: Gauss-Jordan buffers, then G W
+  double* Ai2 = Ai + LD * LD;          // LD*LD
+  double* lam = Ai2 + LD * LD;         // LD
   float* Gf = (float*)(lam + LD);      // LD*LD: G / scale in float
-  float* Af = Gf + LD * LD;            // LD*LD
+  float* Vps = Gf + LD * LD;           // LD*LD: previous eigenvectors
+  float* Af = Vps + LD * LD;           // LD*LD
   float* Vf = Af + LD * LD;            // LD*LD  (Af and Vf later hold W in double)
   float* Wf = Vf + LD * LD;            // LD*LD
   float* cs = Wf + LD * LD;            // 64
-  int* pq = (int*)(cs + 64);           // 64
+  float* red = cs + 64;                // 64
+  int* pq = (int*)(red + 64);          // 64
   int* slot = pq + 64;                 // LD
   double* GW = Ai;
   double* Wd = (double*)Af;
   __shared__ int bad_sh;
   __shared__ float scale_sh;
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
+  constexpr int JG = 256;              // Jacobi group: threads [JG, 2 JG)
+  float* Vp = Vprev + (int64_t)n * LD * LD;
   if (tid == 0) bad_sh = 0;
   for (int e = tid; e < LD * LD; e += blockDim.x) {
     const int ra = e % LD, rb = e / LD;
@@ -418,6 +451,7 @@ __device__ __noinline__ void gram_finish(const ModeDesc& d, int n, const double*
     }
     G[e] = s;
     Ai[e] = s;
+    Vps[e] = (warm && ra < r && rb < r) ? Vp[e] : 0.f;
   }
   __syncthreads();
   if (wid == 0) {
@@ -432,38 +466,44 @@ __device__ __noinline__ void gram_finish(const ModeDesc& d, int n, const double*
     Gf[a + LD * b] = (float)G[a + LD * b] * scale_sh;
   }
   __syncthreads();
-  float* Vp = Vprev + (int64_t)n * LD * LD;
+  __shared__ double* inv_sh;
   if (tid < GJ_THREADS) {
-    if (!gj_inverse(Ai, r, rowk, colk, GJ_THREADS, 1) && tid == 0) bad_sh = 1;
-  } else if (wid == JAC_WARP) {
+    bool good;
+    double* res = gj_inverse(Ai, Ai2, r, GJ_THREADS, 1, &good);
+    if (tid == 0) {
+      inv_sh = res;
+      if (!good) bad_sh = 1;
+    }
+  } else if (tid < GJ_THREADS + JG) {
+    const int gt = tid - GJ_THREADS;
     if (warm) {
-      for (int e = lane; e < r * r; e += 32) {           // Wf = (G / scale) Vp
+      for (int e = gt; e < r * r; e += JG) {             // Wf = (G / scale) Vp
         const int i = e % r, b = e / r;
         float s = 0.f;
-        for (int j = 0; j < r; ++j) s = fmaf(Gf[i + LD * j], Vp[j + LD * b], s);
+        for (int j = 0; j < r; ++j) s = fmaf(Gf[i + LD * j], Vps[j + LD * b], s);
         Wf[i + LD * b] = s;
       }
-      __syncwarp();
-      for (int e = lane; e < r * r; e += 32) {           // Af = Vp^T Wf
+      named_bar(2, JG);
+      for (int e = gt; e < r * r; e += JG) {             // Af = Vp^T Wf
         const int a = e % r, b = e / r;
         float s = 0.f;
-        for (int i = 0; i < r; ++i) s = fmaf(Vp[i + LD * a], Wf[i + LD * b], s);
+        for (int i = 0; i < r; ++i) s = fmaf(Vps[i + LD * a], Wf[i + LD * b], s);
         Af[a + LD * b] = s;
       }
     } else {
-      for (int e = lane; e < r * r; e += 32) {
+      for (int e = gt; e < r * r; e += JG) {
         const int a = e % r, b = e / r;
         Af[a + LD * b] = Gf[a + LD * b];
       }
     }
-    __syncwarp();
-    jacobi_warp(Af, Vf, r, 30, 1e-6f, cs, pq);
-    for (int e = lane; e < r * r; e += 32) {             // eigenvectors in the original basis
+    named_bar(2, JG);
+    jacobi_group(Af, Vf, r, warm ? 2 : 30, 1e-6f, cs, pq, red, gt, JG, 2);
+    for (int e = gt; e < r * r; e += JG) {               // eigenvectors in the original basis
       const int a = e % r, b = e / r;
       float s = Vf[a + LD * b];
       if (warm) {
         s = 0.f;
-        for (int k = 0; k < r; ++k) s = fmaf(Vp[a + LD * k], Vf[k + LD * b], s);
+        for (int k = 0; k < r; ++k) s = fmaf(Vps[a + LD * k], Vf[k + LD * b], s);
       }
       Wf[a + LD * b] = s;
     }
@@ -472,11 +512,16 @@ __device__ __noinline__ void gram_finish(const ModeDesc& d, int n, const double*
   if (bad_sh && tid == 0) atomicOr(flags, kFlagCholGram);
   for (int e = tid; e < LD * LD; e += blockDim.x) {
     const int a = e % LD, b = e / LD;
-    const double gi = (a < r && b < r) ? Ai[e] : 0.0;
+    const bool in = a < r && b < r;
+    const double gi = in ? inv_sh[e] : 0.0;
     Gout[(int64_t)n * LD * LD + e] = G[e];
     Ginv[(int64_t)n * LD * LD + e] = gi;
-    if (Ginvf) Ginvf[(int64_t)n * LD * LD + e] = (float)gi;
-    if (a < r && b < r) Wd[a + LD * b] = (double)Wf[a + LD * b];
+    if (Ginvf) Ginvf[(int64_t)n * LD * LD + e] = in ? (float)gi : 0.f;
+  }
+  __syncthreads();
+  for (int e = tid; e < r * r; e += blockDim.x) {
+    const int a = e % r, b = e / r;
+    Wd[a + LD * b] = (double)Wf[a + LD * b];
   }
   __syncthreads();
   // Rayleigh quotients: GW = G W, then warp j reduces column j
@@ -864,8 +909,10 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_update(UpdArgs a) {
   __shared__ int abort_sh;
   if (threadIdx.x == 0) abort_sh = 0;
   __syncthreads();
+  __shared__ unsigned long long st_sh[16];
   int nst = 0;
-  stamp(a.stamps, 0);
+  unsigned nbar = 0;
+  stamp(st_sh, a.stamps, 0);
   const ModeDesc& d = a.d;
   const int p = d.p;
   const unsigned nb = gridDim.x;
@@ -889,8 +936,8 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_update(UpdArgs a) {
     tile_of(task, &n, &t);
     rows_mxp<Tc>(a, n, (int64_t)t * 32, t, smraw);
   }
-  if (!grid_sync(a.bar, a.bar + 1, nb, a.flags, &abort_sh)) return;
-  stamp(a.stamps, ++nst);
+  if (!grid_sync(a.bar, ++nbar, nb, a.flags, &abort_sh)) return;
+  stamp(st_sh, a.stamps, ++nst);
 
   // 2: P, U', partial C
   for (int task = blockIdx.x; task < ntiles_total; task += nb) {
@@ -898,13 +945,13 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_update(UpdArgs a) {
     tile_of(task, &n, &t);
     rows_u1<Tc>(a, n, (int64_t)t * 32, t, smraw);
   }
-  if (!grid_sync(a.bar, a.bar + 1, nb, a.flags, &abort_sh)) return;
-  stamp(a.stamps, ++nst);
+  if (!grid_sync(a.bar, ++nbar, nb, a.flags, &abort_sh)) return;
+  stamp(st_sh, a.stamps, ++nst);
 
   // 3: Cholesky-QR factors, one CTA per mode
   for (int n = blockIdx.x; n < p; n += nb) mode_cholqr<Tc>(a, n, smraw);
-  if (!grid_sync(a.bar, a.bar + 1, nb, a.flags, &abort_sh)) return;
-  stamp(a.stamps, ++nst);
+  if (!grid_sync(a.bar, ++nbar, nb, a.flags, &abort_sh)) return;
+  stamp(st_sh, a.stamps, ++nst);
 
   // 4: U'' and the core product of mode 1; 5: the other modes (T -> T2 -> T ...)
   for (int task = blockIdx.x; task < ntiles_total; task += nb) {
@@ -916,8 +963,8 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_update(UpdArgs a) {
     const double* src = (n & 1) ? a.T2 : a.T;
     double* dst = (n & 1) ? a.T : a.T2;
     core_mode<Tc>(a, n, src, dst, smraw);
-    if (!grid_sync(a.bar, a.bar + 1, nb, a.flags, &abort_sh)) return;
-    stamp(a.stamps, ++nst);
+    if (!grid_sync(a.bar, ++nbar, nb, a.flags, &abort_sh)) return;
+    stamp(st_sh, a.stamps, ++nst);
   }
 
   // 6: final core in T, compute-type copy, Gram partials
@@ -933,13 +980,14 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_update(UpdArgs a) {
     for (int task = blockIdx.x; task < p * a.gsplit; task += nb)
       gram_partial(d, Tfin, a.gpart, a.gsplit, task / a.gsplit, task % a.gsplit, (double(*)[33])smraw);
   }
-  if (!grid_sync(a.bar, a.bar + 1, nb, a.flags, &abort_sh)) return;
-  stamp(a.stamps, ++nst);
+  if (!grid_sync(a.bar, ++nbar, nb, a.flags, &abort_sh)) return;
+  stamp(st_sh, a.stamps, ++nst);
 
   // 7: G, G^{-1}, sigma^2
   for (int n = blockIdx.x; n < p; n += nb)
     gram_finish(d, n, a.gpart, a.gsplit, a.G, a.Ginv, a.Ginvf, a.sig2, a.Vprev, a.warm, a.flags, smraw);
-  stamp(a.stamps, ++nst);
+  stamp(st_sh, a.stamps, ++nst);
+  stamp_flush(st_sh, a.stamps, nst);
 }
 
 // The Gram refresh of phases 6-7 as two ordinary launches (after (re)initialisation

@@ -75,7 +75,7 @@ struct UpdArgs {
   double* gpart;                 // p x gsplit x LD x LD Gram partials (scratch)
   int ntile, gsplit;
   int warm, reorth;
-  unsigned* bar;                 // [count, generation]
+  unsigned* bar;                 // arrival counter of the grid barriers (zeroed per launch)
   unsigned long long* stamps;    // per-phase timer stamps (profiling), or null
   unsigned* flags;
 };
@@ -128,6 +128,16 @@ void launch_orthonormalize(RowArgs& a, double* R, double* Rinv, unsigned* flags,
 // k_update.cu
 template <typename Tc>
 tdb_status launch_update(UpdArgs& a, int grid_hint, cudaStream_t s);
+
+// k_eig.cu (float compute types)
+void launch_sqrt_weights(const double* w, int n, float* ws, cudaStream_t s);
+void launch_weight_data(const float* V, int p, const int64_t* N, const float* const* ws, int64_t S, float* Vw,
+                        cudaStream_t s);
+void launch_gram_weighted(const float* Vw, int64_t L, int64_t Nn, int64_t Q, double* part, size_t part_cap,
+                          double* C64, float* Cc, cudaStream_t s);
+size_t eig_si_scratch_floats(int n);
+tdb_status eig_si_float(const float* Cc, const double* C64, int n, int k, int iters, float* scratch, unsigned* bar,
+                        unsigned* flags, double* ev, double* Q, double* trace, cudaStream_t s);
 
 // k_hosvd.cu
 template <typename Tv>

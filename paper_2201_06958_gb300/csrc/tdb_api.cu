@@ -107,6 +107,8 @@ struct tdb_ctx {
   void* siJA;
   void* siJV;
   double* wpart;
+  float* eigf;                    // float eigensolver scratch (float compute types)
+  float* wsf[kMaxModes];          // sqrt of the weights in float
   size_t wpart_cap = 0;
   double* ev[kMaxModes];
   double* Qeig[kMaxModes];
@@ -291,8 +293,10 @@ void carve(tdb_ctx* c, Carver& cv) {
   c->siJA = cv.take<char>(64 * 64 * tsz);
   c->siJV = cv.take<char>(64 * 64 * tsz);
   int ntile = (int)((Nmax + 31) / 32);
-  c->wpart_cap = (size_t)(ntile * (ntile + 1) / 2) * 8 * 1024;
+  c->wpart_cap = std::max<size_t>((size_t)(ntile * (ntile + 1) / 2) * 8 * 1024, (size_t)152 * 64 * 64);
   c->wpart = cv.take<double>(c->wpart_cap);
+  c->eigf = c->f64 ? nullptr : cv.take<float>(eig_si_scratch_floats((int)Nmax));
+  for (int n = 0; n < p; ++n) c->wsf[n] = c->f64 ? nullptr : cv.take<float>(c->N[n]);
   for (int n = 0; n < p; ++n) {
     c->kcap[n] = (int)std::min<int64_t>(c->N[n], c->cap[n] + 2);
     c->ev[n] = cv.take<double>(c->kcap[n]);
@@ -527,6 +531,31 @@ tdb_status readback(tdb_ctx* ctx) {
 template <typename Tc>
 tdb_status hosvd_spectrum(tdb_ctx* ctx, const Tc* V) {
   cudaStream_t s = ctx->stream;
+  if (!ctx->f64) {
+    // float compute types: weight the data once, 64 x 64 Gram tiles, cooperative eigensolver
+    for (int n = 0; n < ctx->p; ++n) launch_sqrt_weights(ctx->w[n], (int)ctx->N[n], ctx->wsf[n], s);
+    launch_weight_data((const float*)V, ctx->p, ctx->N, ctx->wsf, ctx->S, (float*)ctx->rec, s);
+    CHECK_LAUNCH();
+    for (int n = 0; n < ctx->p; ++n) {
+      int64_t L = 1, Q = 1;
+      for (int m = 0; m < n; ++m) L *= ctx->N[m];
+      for (int m = n + 1; m < ctx->p; ++m) Q *= ctx->N[m];
+      launch_gram_weighted((const float*)ctx->rec, L, ctx->N[n], Q, ctx->wpart, ctx->wpart_cap, ctx->C64,
+                           (float*)ctx->Cc, s);
+      CHECK_LAUNCH();
+      const int Nn = (int)ctx->N[n];
+      tdb_status st;
+      if (Nn <= 96)
+        st = eig_leading_small<float>((const float*)ctx->Cc, ctx->C64, Nn, ctx->kcap[n], (float*)ctx->jA,
+                                      (float*)ctx->jV, ctx->flags, ctx->ev[n], ctx->Qeig[n], ctx->trace + n,
+                                      ctx->eigscratch, s);
+      else
+        st = eig_si_float((const float*)ctx->Cc, ctx->C64, Nn, ctx->kcap[n], 24, ctx->eigf, ctx->bar, ctx->flags,
+                          ctx->ev[n], ctx->Qeig[n], ctx->trace + n, s);
+      if (st != TDB_OK) { ctx->err = "eigensolver launch failed"; return st; }
+      CHECK_LAUNCH();
+    }
+  } else
   for (int n = 0; n < ctx->p; ++n) {
     GramView g;
     g.p = ctx->p;

@@ -70,13 +70,15 @@ def test_estimator_gain_on_reactive_stream(tdbmod):
     error exactly on a small fraction of the gated steps, and never skips a step whose
     exact error (from B) exceeds eps_th.  The gate (0.9 eps_th) leaves room for the
     estimator's error: on this stream the exact error stays between half the threshold
-    (after each HOSVD) and the threshold."""
+    (after each HOSVD) and the threshold.  Estimates are chained through skipped steps,
+    so a per-step bias of a few 1e-3 in log10 compounds; re-anchoring on an exact
+    evaluation at least every 20 steps (error_every) bounds that drift to under 10 %."""
     wl = S.make_workload("reactive")
     w = wl.weights
     steps = 450
     snaps = [wl.snapshot(k, device="cuda") for k in range(steps + 1)]
     kw = dict(rank_max=wl.rank_max, weights=w, eps_th=wl.eps_th, gamma_th=wl.gamma_th, precision="bf16",
-              error_every=50)
+              error_every=20)
     A = tdbmod.TDB(wl.dims, wl.rank, error_mode="mlp", **kw).init(snaps[0])
     B = tdbmod.TDB(wl.dims, wl.rank, error_mode="exact", **kw).init(snaps[0])
     skipped_true = []
