@@ -76,9 +76,26 @@ def max_over_ranks(x: float, world: int) -> float:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def replica_seed(workload: str, rank: int):
+    """Each replica compresses its own stream: rank 0 keeps the workload's default
+    seed (so one GPU measures the named configuration), rank k > 0 uses that seed + 10 k."""
+    from paper_2201_06958_gb300 import synth as S
+    if rank == 0:
+        return None
+    return S.default_seed(workload) + 10 * rank
+
+
+def replica_value(world: int, steps: int, ms_local: float, host_s_local: float):
+    """Whole-job snapshots/s: the steps of every rank over the slowest rank's time (the
+    longer of its device-event and host-clock measurements).  Returns (value, ms)."""
+    ms_total = max_over_ranks(max(ms_local, host_s_local * 1e3), world)
+    return world * steps / (ms_total * 1e-3), ms_total
 
 
 # ---------------------------------------------------------------------------
@@ -284,8 +301,7 @@ def run_tdb(args, world, rank, local):
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    seed = 1002 + 10 * rank if args.workload == "reactive" else None
-    wl = S.make_workload(args.workload, seed=seed) if seed else S.make_workload(args.workload)
+    wl = S.make_workload(args.workload, seed=replica_seed(args.workload, rank))
     precision = args.precision
     if precision == "auto":
         precision = "fp64" if wl.dtype == "f64" else "bf16"
@@ -360,8 +376,7 @@ def run_tdb(args, world, rank, local):
     if res is None:
         precision = "fp32"
         res = run(precision)
-    ms_total = max_over_ranks(max(res["ms"], res["host_s"] * 1e3), world)
-    value = world * K / (ms_total * 1e-3)
+    value, ms_total = replica_value(world, K, res["ms"], res["host_s"])
 
     # roofline of the dominant kernel (the projection pass)
     prof = res["prof"]
@@ -408,7 +423,7 @@ def run_tdb(args, world, rank, local):
     # the plain FP32 GPU path on the same stream, for the "at equal error" comparison
     if not args.no_compare and precision != "fp32" and wl.dtype == "f32":
         ref = run("fp32", timed_profile=True, mode="exact")
-        ms_ref = max_over_ranks(max(ref["ms"], ref["host_s"] * 1e3), world)
+        _, ms_ref = replica_value(world, K, ref["ms"], ref["host_s"])
         pairs = [(a, b) for a, b in zip(res["eps"], ref["eps"]) if a == a and b == b]
         rel = max(abs(a - b) / b for a, b in pairs) if pairs else None
         line["plain_fp32"] = {"value": world * K / (ms_ref * 1e-3), "unit": UNIT, "ms_per_step": ms_ref / K,

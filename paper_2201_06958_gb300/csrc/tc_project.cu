@@ -44,7 +44,8 @@ constexpr int CONV_WARP0 = 6;
 constexpr int NUM_CONV_WARPS = 8;
 constexpr int NUM_WARPS = CONV_WARP0 + NUM_CONV_WARPS;   // 14
 constexpr int NUM_THREADS = NUM_WARPS * 32;              // 448
-constexpr int MAX_STAGES = 8;                            // one stage per converter warp (used twice per tile)
+constexpr int MAX_STAGES = 16;                           // one stage per sub-tile when shared memory allows, else 8
+constexpr int MIN_STAGES = 8;                            // (one per converter warp, used twice per tile)
 constexpr uint32_t TMEM_COLS = 128;                      // 2 buffers x (D1 32 cols + D2 32 cols)
 constexpr long long TIMEOUT_CYCLES = 4000000000ll;       // ~2 s at 2 GHz
 constexpr int kSmemLimit = 227 * 1024 - 512;             // dynamic shared memory (static use 256 B)
@@ -59,8 +60,8 @@ struct Params {
   float* Z2p;                    // [nq2][nslice][N1][r2]
   const uint4* B1img;            // BF16 operand images (global)
   const uint4* B2img;
-  const double* w1;
-  const double* w2;
+  const float* w1f;             // float copies of w_1, w_2, zero-padded to whole tiles
+  const float* w2f;
   const double* wsl;             // slice weights (product over modes >= 3)
   double* npart;                 // per-CTA ||dV||_W^2
   unsigned* flags;
@@ -174,6 +175,7 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 // ---------------------------------------------------------------------------
 // The fused kernel
 // ---------------------------------------------------------------------------
+template <int NS>   // pipeline stages: 16 (one per sub-tile) or 8 (one per converter warp)
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_tc_project(const __grid_constant__ CUtensorMap tmVn, const __grid_constant__ CUtensorMap tmVp, Params P) {
   extern __shared__ unsigned char smem_raw[];
@@ -181,8 +183,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   unsigned char* bf_tiles = smem;                                          // 2 x 32 KB
   unsigned char* b1_smem = bf_tiles + 2 * BF_TILE_BYTES;                   // resident A_1 image
   unsigned char* b2_smem = b1_smem + ((P.b1_bytes + 1023) & ~1023);        // resident A_2 image
-  unsigned char* stages = b2_smem + ((P.b2_bytes + 1023) & ~1023);         // nstages x 16 KB
-  uint64_t* bars = (uint64_t*)(stages + P.nstages * STAGE_BYTES);
+  float* epi_stage = (float*)(b2_smem + ((P.b2_bytes + 1023) & ~1023));   // 4 warps x 32 x 33 floats
+  unsigned char* stages = (unsigned char*)(epi_stage + NUM_EPI_WARPS * 32 * 33);   // nstages x 8 KB
+  uint64_t* bars = (uint64_t*)(stages + NS * STAGE_BYTES);
   uint64_t* full = bars;                    // [MAX_STAGES]
   uint64_t* empty = bars + MAX_STAGES;      // [MAX_STAGES]
   uint64_t* bf_full = bars + 2 * MAX_STAGES;
@@ -230,33 +233,41 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
   if (warp == TMA_WARP) {
     if (lane == 0) {
-      // sub-tile j = h*8 + q (i1 half h, i2 strip q) goes to stage q, owned by converter
-      // warp q, which uses it twice per tile (h = 0 then h = 1)
-      int last_t = -1;
+      // sub-tile j = h*8 + q (i1 half h, i2 strip q) goes to stage j % nstages and is
+      // converted by warp q: with 16 stages every sub-tile of a tile is in flight at
+      // once, with 8 each stage is used twice per tile (h = 0 then h = 1)
+      // sub-tiles wholly outside the tensor (ragged last tiles) are neither loaded nor
+      // waited for; both sides skip the same ones and count the uses of each stage
+      int ucount[NS];
+#pragma unroll
+      for (int j = 0; j < NS; ++j) ucount[j] = 0;
       bool ok = true;
       int t = 0;
       for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x, ++t) {
         const int q1 = u % P.nq1, q2 = (u / P.nq1) % P.nq2, sl = u / (P.nq1 * P.nq2);
+#pragma unroll
         for (int j = 0; j < NSUB; ++j) {
-          const int st = j & 7, use = 2 * t + (j >> 3);
-          if (!mbar_wait(smem_u32(&empty[st]), (use & 1) ^ 1, abort_flag, P.flags)) { ok = false; break; }
-          const uint32_t fb = smem_u32(&full[st]);
-          mbar_arrive_expect_tx(fb, STAGE_BYTES);
           const int x = q1 * TILE + (j >> 3) * SUB_I1;
           const int y = q2 * TILE + (j & 7) * SUB_I2;
+          if (!ok || x >= P.N1 || y >= P.N2) continue;
+          const int st = j % NS, use = ucount[st];
+          if (!mbar_wait(smem_u32(&empty[st]), (use & 1) ^ 1, abort_flag, P.flags)) { ok = false; continue; }
+          ucount[st] = use + 1;
+          const uint32_t fb = smem_u32(&full[st]);
+          mbar_arrive_expect_tx(fb, STAGE_BYTES);
           const uint32_t dst = smem_u32(stages + st * STAGE_BYTES);
           tma_load_3d(dst, &tmVn, x, y, sl, fb);
           tma_load_3d(dst + BOX_BYTES, &tmVp, x, y, sl, fb);
         }
-        if (ok) last_t = t;
       }
-      // drain: the copies of the last armed tile have landed before the CTA may leave
-      if (last_t >= 0)
-        for (int j = 0; j < 8; ++j) {
-          long long t0 = clock64();
-          while (!mbar_try_wait(smem_u32(&full[j]), (2 * last_t + 1) & 1) && clock64() - t0 < TIMEOUT_CYCLES) {
-          }
+      // drain: every armed copy has landed before the CTA may leave
+#pragma unroll
+      for (int j = 0; j < NS; ++j) {
+        if (ucount[j] == 0) continue;
+        long long t0 = clock64();
+        while (!mbar_try_wait(smem_u32(&full[j]), (ucount[j] - 1) & 1) && clock64() - t0 < TIMEOUT_CYCLES) {
         }
+      }
     }
   } else if (warp == MMA_WARP) {
     if (lane == 0) {
@@ -312,32 +323,55 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       if (!mbar_wait(smem_u32(&mma_done[buf]), (t >> 1) & 1, abort_flag, P.flags)) break;
       tc_fence_after();
       const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
+      float* es = epi_stage + warp * 32 * 33;       // this warp's 32 rows, padded to 33
       float v[32];
-      // Z1 partial: row i2
+      // Z1 partial, rows i2 = q2*128 + 32*warp + lane: the warp's 32 rows x r1 values are one
+      // contiguous block of Z1p, written through shared memory with consecutive lanes on
+      // consecutive addresses
       tmem_ld16(tmem_base + lane_base + buf * 64, v);
       if (P.r1pad > 16) tmem_ld16(tmem_base + lane_base + buf * 64 + 16, v + 16);
-      const int i2 = q2 * TILE + 32 * warp + lane;
-      if (i2 < P.N2) {
-        float* dst = P.Z1p + (((size_t)q1 * P.nslice + sl) * P.N2 + i2) * P.r1;
-        for (int a = 0; a < P.r1; ++a) dst[a] = v[a];
+#pragma unroll
+      for (int a = 0; a < 32; ++a) es[lane * 33 + a] = v[a];
+      __syncwarp();
+      {
+        const int row0 = q2 * TILE + 32 * warp;
+        const int nrow = min(32, P.N2 - row0);
+        float* dst = P.Z1p + (((size_t)q1 * P.nslice + sl) * P.N2 + row0) * P.r1;
+        int rw = lane / P.r1, col = lane % P.r1;
+        for (int e = lane; e < nrow * P.r1; e += 32) {
+          dst[e] = es[rw * 33 + col];
+          col += 32;
+          while (col >= P.r1) { col -= P.r1; ++rw; }
+        }
       }
-      // Z2 partial: row i1
+      __syncwarp();
+      // Z2 partial, rows i1 = q1*128 + 32*warp + lane
       tmem_ld16(tmem_base + lane_base + buf * 64 + 32, v);
       if (P.r2pad > 16) tmem_ld16(tmem_base + lane_base + buf * 64 + 48, v + 16);
-      const int i1 = q1 * TILE + 32 * warp + lane;
-      if (i1 < P.N1) {
-        float* dst = P.Z2p + (((size_t)q2 * P.nslice + sl) * P.N1 + i1) * P.r2;
-        for (int b = 0; b < P.r2; ++b) dst[b] = v[b];
+#pragma unroll
+      for (int a = 0; a < 32; ++a) es[lane * 33 + a] = v[a];
+      __syncwarp();
+      {
+        const int row0 = q1 * TILE + 32 * warp;
+        const int nrow = min(32, P.N1 - row0);
+        float* dst = P.Z2p + (((size_t)q2 * P.nslice + sl) * P.N1 + row0) * P.r2;
+        int rw = lane / P.r2, col = lane % P.r2;
+        for (int e = lane; e < nrow * P.r2; e += 32) {
+          dst[e] = es[rw * 33 + col];
+          col += 32;
+          while (col >= P.r2) { col -= P.r2; ++rw; }
+        }
       }
       tc_fence_before();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&epi_done[buf]));
     }
   } else if (warp >= CONV_WARP0) {
-    // converter warp c owns stage c: sub-tiles (h = 0, strip c) and (h = 1, strip c) of every tile
+    // converter warp c takes sub-tiles (h = 0, strip c) and (h = 1, strip c) of every tile
     const int c = warp - CONV_WARP0;
     const int cx = lane & 15, ry = lane >> 4;
     const int chunk = cx >> 1, hoff = (cx & 1) * 8;
+    int ucnt0 = 0, ucnt1 = 0;                        // uses of this warp's stage(s)
     int t = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x, ++t) {
@@ -345,16 +379,31 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const int buf = t & 1;
       if (t >= 2 && !mbar_wait(smem_u32(&mma_done[buf]), ((t >> 1) - 1) & 1, abort_flag, P.flags)) break;
       float acc = 0.f;
-      for (int h = 0; h < 2; ++h) {
-        const int use = 2 * t + h;
-        if (!mbar_wait(smem_u32(&full[c]), use & 1, abort_flag, P.flags)) { ok = false; break; }
-        const float4* vn = (const float4*)(stages + c * STAGE_BYTES);
-        const float4* vp = (const float4*)(stages + c * STAGE_BYTES + BOX_BYTES);
-        const int i1b = q1 * TILE + h * SUB_I1 + 4 * cx;
-        float w1v[4];
+      // weights of the rows this lane converts (zero past N_2): fetched once per tile
+      float w2v[8];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) w1v[e] = (i1b + e < P.N1) ? (float)P.w1[i1b + e] : 0.f;
+      for (int k = 0; k < 8; ++k) w2v[k] = __ldg(&P.w2f[q2 * TILE + c * SUB_I2 + ry + 2 * k]);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!ok) continue;
+        const int j = h * 8 + c, st = j % NS;
         unsigned char* half = bf_tiles + buf * BF_TILE_BYTES + h * HALF_BYTES;
+        if (q1 * TILE + h * SUB_I1 >= P.N1 || q2 * TILE + c * SUB_I2 >= P.N2) {
+          // wholly outside the tensor: zeros in the BF16 tile, no copy to wait for
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            const int r = c * SUB_I2 + ry + 2 * k;
+            *(uint2*)(half + r * 128 + ((chunk ^ (r & 7)) << 4) + hoff) = make_uint2(0u, 0u);
+          }
+          continue;
+        }
+        const int use = (NS == MAX_STAGES && h == 1) ? ucnt1++ : ucnt0++;
+        if (!mbar_wait(smem_u32(&full[st]), use & 1, abort_flag, P.flags)) { ok = false; continue; }
+        const float4* vn = (const float4*)(stages + st * STAGE_BYTES);
+        const float4* vp = (const float4*)(stages + st * STAGE_BYTES + BOX_BYTES);
+        const int i1b = q1 * TILE + h * SUB_I1 + 4 * cx;
+        const float4 w1q = __ldg((const float4*)(P.w1f + i1b));
+        const float w1v[4] = {w1q.x, w1q.y, w1q.z, w1q.w};
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int row = ry + 2 * k;                 // 0..15 within the box
@@ -362,14 +411,12 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const float4 b = vp[row * 16 + cx];
           const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
           const int r = c * SUB_I2 + row;             // tile row (i2 within the tile)
-          const int i2 = q2 * TILE + r;
-          const float w2v = (i2 < P.N2) ? (float)P.w2[i2] : 0.f;
-          acc += w2v * (w1v[0] * d0 * d0 + w1v[1] * d1 * d1 + w1v[2] * d2 * d2 + w1v[3] * d3 * d3);
+          acc += w2v[k] * (w1v[0] * d0 * d0 + w1v[1] * d1 * d1 + w1v[2] * d2 * d2 + w1v[3] * d3 * d3);
           uint2 pk = make_uint2(pack_bf16x2(d0, d1), pack_bf16x2(d2, d3));
           *(uint2*)(half + r * 128 + ((chunk ^ (r & 7)) << 4) + hoff) = pk;
         }
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&empty[c]));
+        if (lane == 0) mbar_arrive(smem_u32(&empty[st]));
       }
       if (!ok) break;
       acc_norm += (double)acc * P.wsl[sl];
@@ -438,6 +485,12 @@ __global__ void k_tc_reduce(const float* __restrict__ Z1p, const float* __restri
   }
 }
 
+// Float copies of w_1 and w_2, zero-padded to whole 128-wide tiles (read by the converters).
+__global__ void k_weights_f(const double* w1, int N1, int L1, const double* w2, int N2, int L2, float* out) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L1 + L2; i += gridDim.x * blockDim.x)
+    out[i] = (i < L1) ? (i < N1 ? (float)w1[i] : 0.f) : (i - L1 < N2 ? (float)w2[i - L1] : 0.f);
+}
+
 __global__ void k_slice_weights(int p, const double* w3, int N3, const double* w4, int N4, double* out) {
   int n = (p >= 3 ? N3 : 1) * (p >= 4 ? N4 : 1);
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
@@ -496,8 +549,9 @@ bool tc_supported(int p, const int64_t* N, const int* cap, std::string& err) {
   if (major != 10) { err = "needs a compute capability 10.x GPU (tcgen05)"; return false; }
   int nq1 = (int)((N[0] + TILE - 1) / TILE), nq2 = (int)((N[1] + TILE - 1) / TILE);
   int b1 = nq1 * 2 * rpad_of(cap[0]) * 128, b2 = nq2 * 2 * rpad_of(cap[1]) * 128;
-  int fixed = 1024 + 2 * BF_TILE_BYTES + ((b1 + 1023) & ~1023) + ((b2 + 1023) & ~1023) + 512;
-  if (fixed + MAX_STAGES * STAGE_BYTES > kSmemLimit) { err = "basis images too large for shared memory"; return false; }
+  int fixed = 1024 + 2 * BF_TILE_BYTES + ((b1 + 1023) & ~1023) + ((b2 + 1023) & ~1023) + NUM_EPI_WARPS * 32 * 33 * 4 +
+              512;
+  if (fixed + MIN_STAGES * STAGE_BYTES > kSmemLimit) { err = "basis images too large for shared memory"; return false; }
   return get_encoder(err);
 }
 
@@ -511,6 +565,7 @@ void tc_carve(TcPlan& plan, Carver& cv, int p, const int64_t* N, const int* cap)
   plan.z1p = cv.take<float>((size_t)nq1 * nslice * N[1] * cap[0]);
   plan.z2p = cv.take<float>((size_t)nq2 * nslice * N[0] * cap[1]);
   plan.wsl = cv.take<double>((size_t)nslice);
+  plan.w12f = cv.take<float>((size_t)(nq1 + nq2) * TILE);
   plan.npart = cv.take<double>(1024);
 }
 
@@ -538,6 +593,9 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
     k_slice_weights<<<(nslice + 255) / 256, 256, 0, s>>>(p, p >= 3 ? w[2] : nullptr, p >= 3 ? (int)N[2] : 1,
                                                          p >= 4 ? w[3] : nullptr, p >= 4 ? (int)N[3] : 1, plan.wsl);
     count_launch();
+    k_weights_f<<<((nq1 + nq2) * TILE + 255) / 256, 256, 0, s>>>(w[0], N1, nq1 * TILE, w[1], N2, nq2 * TILE,
+                                                                plan.w12f);
+    count_launch();
     plan.wsl_ready = true;
   }
   CUtensorMap tmn, tmp;
@@ -558,8 +616,9 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   P.b1_bytes = nq1 * 2 * r1pad * 128;
   P.b2_bytes = nq2 * 2 * r2pad * 128;
   // 1 KB alignment slack for the 1024-byte swizzle atoms, then one stage per converter warp
-  int fixed = 1024 + 2 * BF_TILE_BYTES + ((P.b1_bytes + 1023) & ~1023) + ((P.b2_bytes + 1023) & ~1023) + 512;
-  P.nstages = MAX_STAGES;
+  int fixed = 1024 + 2 * BF_TILE_BYTES + ((P.b1_bytes + 1023) & ~1023) + ((P.b2_bytes + 1023) & ~1023) +
+              NUM_EPI_WARPS * 32 * 33 * 4 + 512;
+  P.nstages = ((size_t)fixed + (size_t)MAX_STAGES * STAGE_BYTES <= (size_t)kSmemLimit) ? MAX_STAGES : MIN_STAGES;
   if ((size_t)fixed + (size_t)P.nstages * STAGE_BYTES > (size_t)kSmemLimit) {
     err = "shared memory budget exceeded";
     return TDB_ERR_UNSUPPORTED;
@@ -569,13 +628,14 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   P.Z2p = plan.z2p;
   P.B1img = (const uint4*)plan.Abf[0];
   P.B2img = (const uint4*)plan.Abf[1];
-  P.w1 = w[0];
-  P.w2 = w[1];
+  P.w1f = plan.w12f;
+  P.w2f = plan.w12f + nq1 * TILE;
   P.wsl = plan.wsl;
   P.npart = plan.npart;
   P.flags = flags;
   if (!plan.attr_set) {
-    cudaFuncSetAttribute(k_tc_project, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    cudaFuncSetAttribute(k_tc_project<MAX_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    cudaFuncSetAttribute(k_tc_project<MIN_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     plan.attr_set = true;
   }
   int dev = 0, nsm = 0;
@@ -583,7 +643,10 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   const int grid = std::min(P.nunits, std::min(nsm, 1024));
   if (evm) cudaEventRecord(evm[0], s);
-  k_tc_project<<<grid, NUM_THREADS, smem, s>>>(tmn, tmp, P);
+  if (P.nstages == MAX_STAGES)
+    k_tc_project<MAX_STAGES><<<grid, NUM_THREADS, smem, s>>>(tmn, tmp, P);
+  else
+    k_tc_project<MIN_STAGES><<<grid, NUM_THREADS, smem, s>>>(tmn, tmp, P);
   count_launch();
   if (evm) cudaEventRecord(evm[1], s);
   cudaError_t e = cudaGetLastError();

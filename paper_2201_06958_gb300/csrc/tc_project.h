@@ -13,6 +13,7 @@ struct TcPlan {
   float* z1p = nullptr;               // [tiles along i1][slices][N2][r1] partial dV x_1 A_1^T
   float* z2p = nullptr;               // [tiles along i2][slices][N1][r2] partial dV x_2 A_2^T
   double* wsl = nullptr;              // product of the weights of modes >= 3, per slice
+  float* w12f = nullptr;              // float w_1, w_2, zero-padded to whole tiles
   double* npart = nullptr;            // per-CTA ||dV||_W^2
   bool wsl_ready = false;
   bool attr_set = false;

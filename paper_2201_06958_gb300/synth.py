@@ -349,6 +349,14 @@ WORKLOADS = {
 }
 
 
+DEFAULT_SEEDS = {"analytic": 1001, "reactive": 1002, "stochastic": 1003, "channel": 1004}
+
+
+def default_seed(name: str) -> int:
+    """The seed a workload uses when none is given (1000 + its index)."""
+    return DEFAULT_SEEDS[name]
+
+
 def make_workload(name: str, seed: Optional[int] = None, **kw) -> Workload:
     """Build a workload by name; ``seed`` defaults to 1000 + its index."""
     f = WORKLOADS[name]

@@ -449,3 +449,32 @@ def test_mlp_adam_first_step_and_fit():
         L, g = M.loss_and_grad(theta, X, t, F, H)
         theta, m, v = M.adam_update(theta, g, m, v, s, 3e-3)
     assert L < 0.02 * L0
+
+
+# ---------------------------------------------------------------------------
+# Coherent-structure rotation (Eq. 2.19)
+# ---------------------------------------------------------------------------
+
+def test_rotate_coherent_diagonalises_the_core_grams():
+    """U~_n = U_n Psi_n (Eq. 2.19): recovering Psi_n = U_n^T W_n U~_n and rotating the core
+    by Psi_n^T makes every T~_(n) T~_(n)^T diagonal with the squared core singular values
+    (Eq. 2.18, computed separately by an eigensolver) in descending order, keeps
+    U~_n^T W_n U~_n = I, and leaves T x U unchanged."""
+    rng = np.random.default_rng(77)
+    dims, ranks = (9, 8, 7), (4, 3, 3)
+    w = [_rand_weights(rng, N) for N in dims]
+    U = [_rand_orth_w(rng, N, r, wn) for N, r, wn in zip(dims, ranks, w)]
+    T = rng.standard_normal(ranks)
+    Ut = O.rotate_coherent(T, U)
+    Psi = [U[n].T @ (w[n][:, None] * Ut[n]) for n in range(3)]
+    Tt = T
+    for n in range(3):
+        Tt = O.mode_product(Tt, Psi[n].T, n)
+    sig = O.core_singular_values(T)
+    for n in range(3):
+        G = O.unfold(Tt, n) @ O.unfold(Tt, n).T
+        assert np.abs(G - np.diag(np.diag(G))).max() <= 1e-12 * np.abs(G).max()
+        np.testing.assert_allclose(np.diag(G), sig[n] ** 2, rtol=1e-12)
+        np.testing.assert_allclose(Ut[n].T @ (w[n][:, None] * Ut[n]), np.eye(ranks[n]), atol=1e-12)
+    ref = O.reconstruct(T, U)
+    assert np.abs(O.reconstruct(Tt, Ut) - ref).max() <= 1e-12 * np.abs(ref).max()
