@@ -38,11 +38,14 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="tdb", choices=["tdb", "reference"])
-    ap.add_argument("--workload", default="reactive", choices=["reactive", "stochastic", "channel", "analytic"])
+    ap.add_argument("--workload", default="reactive",
+                    choices=["reactive", "stochastic", "channel", "analytic", "batch"])
     ap.add_argument("--precision", default="auto", choices=["auto", "bf16", "fp32", "fp64"])
     ap.add_argument("--error-mode", default="auto", choices=["auto", "exact", "mlp", "every_k"])
     ap.add_argument("--train-steps", type=int, default=300,
                     help="steps of the separate training stream for the error estimator")
+    ap.add_argument("--api", default="slots", choices=["slots", "pointer"],
+                    help="slots: input slots + recorded step graphs (default); pointer: tdb_push_snapshot")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -323,20 +326,38 @@ def run_tdb(args, world, rank, local):
                     gamma_th=wl.gamma_th, precision=prec, error_mode=mode, error_every=20, device=dev)
         return c
 
-    def run(prec, timed_profile=True, mode=None):
+    def run(prec, timed_profile=True, mode=None, api=None):
+        """api 'slots': each snapshot is copied from the resident stream into the context's
+        input slot inside the timed region and the recorded step replayed (one graph launch
+        per step); 'pointer': tdb_push_snapshot on the resident snapshot."""
         mode = mode or err_mode
+        api = api or args.api
         c = make(prec, mode)
+        slots = None
+        if api == "slots":
+            slots = [torch.empty_like(snaps[0]), torch.empty_like(snaps[0])]
+            slots[1].copy_(snaps[0])
         try:
-            c.init(snaps[0])
+            c.init(slots[1] if slots else snaps[0])
         except tdb.TDBError as e:
             if prec == "bf16" and e.status == 11:
                 return None
             raise
+        if slots:
+            c.set_input_slots(slots[0], slots[1])
         if mode == "mlp":
             c.estimator_params(est_params, gate=0.9)
         info = tdb.tdb_step_info()
+
+        def step(k):
+            if slots is None:
+                return c.push_raw(snaps[k].data_ptr(), info)
+            par = (k - 1) % 2
+            slots[par].copy_(snaps[k])
+            return lib.tdb_push_slot(c.ctx, par, C.byref(info))
+
         for k in range(1, W + 1):
-            st = c.push_raw(snaps[k].data_ptr(), info)
+            st = step(k)
             assert st in (0, 9), (st, lib.tdb_last_error(c.ctx))
         eps, acts = [], []
         barrier(world)
@@ -352,7 +373,7 @@ def run_tdb(args, world, rank, local):
         t_host0 = time.perf_counter()
         e0.record(stream)
         for k in range(W + 1, W + K + 1):
-            st = c.push_raw(snaps[k].data_ptr(), info)
+            st = step(k)
             if st not in (0, 9):
                 raise tdb.TDBError(st, lib.tdb_last_error(c.ctx).decode())
             eps.append(info.eps if info.eps_exact else float("nan"))
@@ -372,14 +393,18 @@ def run_tdb(args, world, rank, local):
         return {"ms": ms, "host_s": t_host, "eps": eps, "prof": prof, "clocks": clocks, "launches": launches,
                 "counters": counters, "acts": acts}
 
-    res = run(precision)
+    # timed run: recorded steps, no instrumentation; then a shorter profiled run of the same
+    # stream (steps not recorded, CUDA events around each phase and the projection kernel)
+    res = run(precision, timed_profile=False)
+    resp = run(precision, timed_profile=True) if res is not None else None
     if res is None:
         precision = "fp32"
-        res = run(precision)
+        res = run(precision, timed_profile=False)
+        resp = run(precision, timed_profile=True)
     value, ms_total = replica_value(world, K, res["ms"], res["host_s"])
 
     # roofline of the dominant kernel (the projection pass)
-    prof = res["prof"]
+    prof = resp["prof"]
     S_el = 1
     for d in wl.dims:
         S_el *= d
@@ -409,7 +434,7 @@ def run_tdb(args, world, rank, local):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"bf16": "bf16", "fp32": "f32", "fp64": "f64"}[precision], "data": "synthetic",
-        "config": dict(workload_desc(args.workload), precision=precision, error_mode=err_mode,
+        "config": dict(workload_desc(args.workload), precision=precision, error_mode=err_mode, api=args.api,
                        l2=("streamed inputs larger than L2: every step reads a new snapshot "
                            f"({esz * S_el / 1e6:.1f} MB) from a {nsnap * esz * S_el / 1e9:.2f} GB device-resident "
                            "stream; the previous snapshot is the one read in the step before"),
@@ -422,7 +447,7 @@ def run_tdb(args, world, rank, local):
 
     # the plain FP32 GPU path on the same stream, for the "at equal error" comparison
     if not args.no_compare and precision != "fp32" and wl.dtype == "f32":
-        ref = run("fp32", timed_profile=True, mode="exact")
+        ref = run("fp32", timed_profile=False, mode="exact")
         _, ms_ref = replica_value(world, K, ref["ms"], ref["host_s"])
         pairs = [(a, b) for a, b in zip(res["eps"], ref["eps"]) if a == a and b == b]
         rel = max(abs(a - b) / b for a, b in pairs) if pairs else None
@@ -433,7 +458,7 @@ def run_tdb(args, world, rank, local):
 
     # end to end through the C ABI from pinned host buffers
     if not args.no_e2e:
-        line["e2e"] = run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_params)
+        line["e2e"] = run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_params, args.api)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample_seconds, K)
@@ -465,7 +490,8 @@ def train_estimator(args, wl, precision, dev, tdb, S):
                     "gate": 0.9, "max_skip": 20}
 
 
-def run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_params=None):
+def run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_params=None, api="slots"):
+    import ctypes as C
     import torch
     host = torch.empty_like(snaps, device="cpu").pin_memory()
     host.copy_(snaps)
@@ -475,20 +501,27 @@ def run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_para
     stream = torch.cuda.current_stream(dev)
     ring[0].copy_(host[0], non_blocking=True)
     c.init(ring[0])
+    slots = api == "slots"
+    if slots:
+        c.set_input_slots(ring[1], ring[0])       # step k reads V_{k+1} from ring[k % 2]
     if err_mode == "mlp":
         c.estimator_params(est_params, gate=0.9)
     info = tdb.tdb_step_info()
-    for k in range(1, W + 1):
+
+    def step(k):
         buf = ring[k % 2]
-        buf.copy_(host[k], non_blocking=True)
-        c.push_raw(buf.data_ptr(), info)
+        buf.copy_(host[k], non_blocking=True)          # H2D of this step's snapshot (pinned)
+        if slots:                                      # the step; it reads the result back to the host
+            return lib.tdb_push_slot(c.ctx, 1 - k % 2, C.byref(info))
+        return c.push_raw(buf.data_ptr(), info)
+
+    for k in range(1, W + 1):
+        step(k)
     barrier(world)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in range(W + 1, W + K + 1):
-        buf = ring[k % 2]
-        buf.copy_(host[k], non_blocking=True)          # H2D of this step's snapshot (pinned)
-        st = c.push_raw(buf.data_ptr(), info)           # the step; it reads the result back to the host
+        st = step(k)
         if st not in (0, 9):
             raise tdb.TDBError(st, lib.tdb_last_error(c.ctx).decode())
     torch.cuda.synchronize()
@@ -499,6 +532,99 @@ def run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_para
             "d2h_bytes_per_step": 1056}        # the per-step status block read back by the step
 
 
+def run_batch(args, world, rank, local):
+    """The batched configuration: 64 independent 3-mode tensors (N_n ~ U{32..128}, ranks
+    U{4..24}), one context each (BF16 tensor cores where N_1 is a multiple of 4, FP32
+    otherwise), every member's step recorded into one graph over 8 streams.  value =
+    member snapshots per second.  Each batch step first moves the 64 resident snapshots
+    into the members' input slots (torch._foreach_copy_, inside the timed region)."""
+    import ctypes as C
+    import torch
+    from paper_2201_06958_gb300 import build_lib, tdb, synth as S
+    build_lib.build()
+    lib = tdb.load()
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    members = S.make_batch(seed=1005 + 10 * rank, count=64)
+    K, W = min(args.steps, 200), args.warmup
+    nsnap = W + K + 1
+    streams, ctxs, slots = [], [], []
+    total = 0
+    for wl in members:
+        n = 1
+        for d in wl.dims:
+            n *= d
+        total += n
+        st = torch.empty((nsnap,) + tuple(reversed(wl.dims)), dtype=torch.float32, device=dev)
+        for k in range(nsnap):
+            st[k] = wl.snapshot(k, device=dev)
+        streams.append(st)
+        prec = "bf16" if wl.dims[0] % 4 == 0 else "fp32"
+        c = tdb.TDB(wl.dims, wl.rank, rank_max=wl.rank_max, weights=wl.weights, precision=prec,
+                    error_mode="every_k", error_every=20, device=dev)
+        sl = [torch.empty_like(st[0]), torch.empty_like(st[0])]
+        sl[1].copy_(st[0])
+        c.init(sl[1]).set_input_slots(sl[0], sl[1])
+        ctxs.append(c)
+        slots.append(sl)
+    batch = tdb.Batch(ctxs, nstreams=8)
+    infos = (tdb.tdb_step_info * len(ctxs))()
+
+    def step(k):
+        par = (k - 1) % 2
+        torch._foreach_copy_([sl[par] for sl in slots], [st[k] for st in streams])
+        return lib.tdb_batch_push(batch.b, par, C.cast(infos, C.c_void_p))
+
+    for k in range(1, W + 1):
+        assert step(k) in (0, 9), lib.tdb_batch_last_error(batch.b)
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = lib.tdb_kernel_launches()
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    time.sleep(0.3)
+    stream = torch.cuda.current_stream(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    e0.record(stream)
+    for k in range(W + 1, W + K + 1):
+        st = step(k)
+        if st not in (0, 9):
+            raise tdb.TDBError(st, lib.tdb_batch_last_error(batch.b).decode())
+    e1.record(stream)
+    torch.cuda.synchronize()
+    host_s = time.perf_counter() - t0
+    clocks = sampler.stop()
+    launches = lib.tdb_kernel_launches() - l0
+    ms = e0.elapsed_time(e1)
+    value, ms_total = replica_value(world, K * len(ctxs), ms, host_s)
+    counters = batch.counters()
+    nbf16 = sum(1 for c in ctxs if c.precision == "bf16")
+    alg = 2 * 4 * total
+    gbs = alg / (ms_total / K * 1e-3) / 1e9
+    peak, peak_kind = measured_peaks()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16+f32", "data": "synthetic",
+        "config": {"workload": f"batch of {len(ctxs)} 3-mode tensors, N_n ~ U{{32..128}}, r ~ U{{4..24}}, "
+                               f"{total / 1e6:.1f}M elements per batch step, fixed ranks, exact error every 20 steps",
+                   "members": len(ctxs), "members_bf16": nbf16, "elements_per_step": total, "api": "batch graph",
+                   "ingest": "torch._foreach_copy_ of the resident snapshots into the slots, timed",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                     "traffic": None, "kernel": "whole batch step (graph)", "algorithmic_bytes_per_launch": alg,
+                     "peak_source": peak_kind},
+        "clocks": clocks, "gpu_launches": int(launches), "batch_steps_per_s": K / (ms_total * 1e-3),
+        "graph": counters,
+    }
+    batch.close()
+    for c in ctxs:
+        c.close()
+    if rank == 0:
+        print(json.dumps(line))
+
+
 def main():
     args = parse_args()
     world, rank, local = dist_setup() if args.impl == "tdb" else (
@@ -506,7 +632,10 @@ def main():
     if args.impl == "reference":
         run_reference(args, world, rank)
         return
-    run_tdb(args, world, rank, local)
+    if args.workload == "batch":
+        run_batch(args, world, rank, local)
+    else:
+        run_tdb(args, world, rank, local)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()

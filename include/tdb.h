@@ -266,6 +266,50 @@ tdb_status tdb_project_noalloc(int ndim, const int64_t* dims, const int* ranks, 
                                float* const* Y, double* dv2, void* stream);
 
 /* Library version and build facts: "tdb <ver> sm_103a". */
+/* ---------------------------------------------------------------------------
+ * Input slots and recorded steps.  The paper streams one snapshot per step (Sec. 2.3);
+ * these calls change only how the same step is issued, not what it computes.
+ *
+ * tdb_set_input_slots: two distinct device buffers, each holding one snapshot in the
+ *   layout of tdb_push_snapshot, owned by the caller (who writes each new snapshot
+ *   into them, e.g. straight from a simulation or a host copy).  NULL, NULL removes them.
+ * tdb_push_slot: one step with V_{k+1} in slot[parity] and V_k in slot[1 - parity];
+ *   the previous step (or the init) must have consumed slot[1 - parity], otherwise
+ *   TDB_ERR_STATE.  The device work of the step is recorded once per slot parity and
+ *   rank configuration as a CUDA graph and replayed afterwards, so a step costs one
+ *   launch; the results are those of tdb_push_snapshot on the same snapshots.  Steps
+ *   run as tdb_push_snapshot does (not recorded) while profiling is enabled, on the
+ *   first step of a tensor-core context, or if the configuration cannot be recorded.
+ * ------------------------------------------------------------------------- */
+tdb_status tdb_set_input_slots(tdb_ctx* ctx, const void* slot0, const void* slot1);
+tdb_status tdb_push_slot(tdb_ctx* ctx, int parity, tdb_step_info* info /* nullable, host */);
+
+/* ---------------------------------------------------------------------------
+ * Batches: many independent tensors (fields, species or samples of uneven sizes and
+ * ranks) stepped together.  The paper compresses one tensor at a time; a batch runs
+ * each member's own step, unchanged, with every member's device work recorded into one
+ * CUDA graph over `nstreams` streams (member i on stream i mod nstreams) and one
+ * synchronisation per batch step; the host then finishes each member in turn (error
+ * control and rank adaptation, which may re-initialise a member by HOSVD on its own
+ * stream and causes the graph to be recorded again at the next step).
+ *
+ * tdb_batch_create: members are initialised contexts with input slots set; the batch
+ *   keeps pointers to them (the caller still owns and destroys them, after the batch).
+ *   stream: the caller's stream on which each batch step is launched and synchronised.
+ * tdb_batch_push: one step of every member, V_{k+1} in each member's slot[parity];
+ *   infos (nullable) receives one record per member in member order.  Returns the most
+ *   severe member status (an error over TDB_WARN_RANK_CAP); tdb_batch_last_error names
+ *   the member.
+ * ------------------------------------------------------------------------- */
+typedef struct tdb_batch tdb_batch;
+tdb_status tdb_batch_create(tdb_batch** out, tdb_ctx* const* members, int n, int nstreams, void* cuda_stream);
+tdb_status tdb_batch_push(tdb_batch* batch, int parity, tdb_step_info* infos /* nullable, n records */);
+const char* tdb_batch_last_error(const tdb_batch* batch);
+/* How many steps of ctx (or batch steps of batch; exactly one of the two non-NULL) were
+ * replayed from a recorded graph, and how many recordings were made (host, nullable). */
+tdb_status tdb_get_graph_counters(const tdb_ctx* ctx, const tdb_batch* batch, int64_t* replays, int64_t* records);
+void tdb_batch_destroy(tdb_batch* batch);
+
 const char* tdb_version(void);
 
 #ifdef __cplusplus

@@ -144,66 +144,123 @@ template void launch_wnorm2<double>(const double*, const double*, const WeightVi
                                     unsigned*, cudaStream_t);
 
 // Exact error of Eq. 2.20 without materialising V^TDB: with H = T x_2 U_2 ... x_p U_p
-// (r_1 x N_2 x ... x N_p), every mode-1 column of the reconstruction is U_1 H[:, c];
-// each block takes whole columns, forms V - U_1 H[:, c] in the data type and
-// accumulates w_1(i_1) w_c (V - V^TDB)^2 (float partials per column, double across).
+// (r_1 x N_2 x ... x N_p), every mode-1 column of the reconstruction is U_1 H[:, c].
+// One warp per column (lanes over rows, coalesced), U_1 staged in shared memory when
+// it fits, the column's H values held in registers; w_1 and the column weights
+// w_c = prod_{m>1} w_m(i_m) in the compute type; per-column sums in the compute type,
+// double across columns.  The last CTA to finish adds the per-CTA partials in a fixed
+// order and writes *out (no second launch); `counter` is zero before and after.
 template <typename T>
-__global__ void k_recon_err(const T* __restrict__ V, const T* __restrict__ U1, const T* __restrict__ H, int r1,
-                            WeightView wv, double* __restrict__ partial, unsigned* flags, const int* __restrict__ gate) {
-  if (gate && *gate == 0) {            // the estimator ruled this evaluation out
-    if (threadIdx.x == 0) partial[blockIdx.x] = 0.0;
-    return;
-  }
-  __shared__ T hcol[32];
+__global__ void __launch_bounds__(256) k_recon_err(const T* __restrict__ V, const T* __restrict__ U1,
+                                                   const T* __restrict__ H, int r1, int N1, unsigned ncol,
+                                                   const T* __restrict__ w1, const T* __restrict__ wcol,
+                                                   int stage_u1, double* __restrict__ partial,
+                                                   unsigned* __restrict__ counter, double* __restrict__ out,
+                                                   unsigned* flags, const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;          // the estimator ruled this evaluation out
+  extern __shared__ __align__(16) unsigned char sm_re[];
+  T* U1s = (T*)sm_re;
   __shared__ double sh[32];
-  __shared__ double wcs;
+  __shared__ bool last;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  const T* Usrc = U1;
+  if (stage_u1) {
+    for (int e = tid; e < N1 * r1; e += blockDim.x) U1s[e] = U1[e];
+    __syncthreads();
+    Usrc = U1s;
+  }
+  double acc = 0.0;
+  bool bad = false;
+  for (unsigned c = blockIdx.x * nw + warp; c < ncol; c += gridDim.x * nw) {
+    const T hl = lane < r1 ? H[lane + (size_t)r1 * c] : T(0);
+    T h[32];
+#pragma unroll
+    for (int a = 0; a < 32; ++a) h[a] = __shfl_sync(0xffffffffu, hl, a);
+    const T* vc = V + (size_t)N1 * c;
+    T s = T(0);
+    for (int i = lane; i < N1; i += 32) {
+      T rec = T(0);
+#pragma unroll
+      for (int a = 0; a < 32; ++a)
+        if (a < r1) rec += Usrc[i + N1 * a] * h[a];
+      const T d = vc[i] - rec;
+      bad |= !isfinite(d);
+      s += w1[i] * d * d;
+    }
+    acc += (double)(wcol[c] * s);
+  }
+  acc = block_sum(acc, sh);
+  if (bad && flags) atomicOr(flags, kFlagNonFinite);
+  if (tid == 0) {
+    partial[blockIdx.x] = acc;
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t = 0.0;
+  for (int k = tid; k < (int)gridDim.x; k += blockDim.x) t += __ldcg(&partial[k]);
+  t = block_sum(t, sh);
+  if (tid == 0) {
+    *out = t;
+    atomicExch(counter, 0u);
+  }
+}
+
+template <typename T>
+void launch_recon_err(const T* V, const T* U1, const T* H, int r1, int N1, int64_t ncol, const T* w1, const T* wcol,
+                      double* partial, unsigned* counter, int nblocks, double* out, unsigned* flags, cudaStream_t s,
+                      const int* gate) {
+  const size_t u1_bytes = (size_t)N1 * r1 * sizeof(T);
+  const int stage = u1_bytes <= 96 * 1024 ? 1 : 0;
+  static bool attr[2] = {false, false};
+  if (stage && !attr[sizeof(T) == 8]) {
+    cudaFuncSetAttribute(k_recon_err<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
+    attr[sizeof(T) == 8] = true;
+  }
+  const int blocks = (int)std::min<int64_t>(nblocks, (ncol + 7) / 8);
+  k_recon_err<T><<<blocks, 256, stage ? u1_bytes : 0, s>>>(V, U1, H, r1, N1, (unsigned)ncol, w1, wcol, stage,
+                                                           partial, counter, out, flags, gate);
+  count_launch();
+}
+template void launch_recon_err<float>(const float*, const float*, const float*, int, int, int64_t, const float*,
+                                      const float*, double*, unsigned*, int, double*, unsigned*, cudaStream_t,
+                                      const int*);
+template void launch_recon_err<double>(const double*, const double*, const double*, int, int, int64_t, const double*,
+                                       const double*, double*, unsigned*, int, double*, unsigned*, cudaStream_t,
+                                       const int*);
+
+// Weights in the compute type: w_1 (N_1) and the column weights of the mode-1 unfolding,
+// w_c = prod_{m>1} w_m(i_m) for c = i_2 + N_2 (i_3 + ...).
+template <typename T>
+__global__ void k_weights_T(WeightView wv, T* __restrict__ w1, T* __restrict__ wcol) {
   const unsigned N1 = (unsigned)wv.N[0];
   unsigned ncol = 1;
   for (int m = 1; m < wv.p; ++m) ncol *= (unsigned)wv.N[m];
-  double acc = 0.0;
-  bool bad = false;
-  for (unsigned c = blockIdx.x; c < ncol; c += gridDim.x) {
-    if (threadIdx.x < (unsigned)r1) hcol[threadIdx.x] = H[threadIdx.x + (size_t)r1 * c];
-    if (threadIdx.x == 32) {
+  for (unsigned e = blockIdx.x * blockDim.x + threadIdx.x; e < N1 + ncol; e += gridDim.x * blockDim.x) {
+    if (e < N1) {
+      w1[e] = (T)wv.w[0][e];
+    } else {
+      unsigned rem = e - N1;
       double wc = 1.0;
-      unsigned rem = c;
       for (int m = 1; m < wv.p; ++m) {
         const unsigned nm = (unsigned)wv.N[m];
         wc *= wv.w[m][rem % nm];
         rem /= nm;
       }
-      wcs = wc;
+      wcol[e - N1] = (T)wc;
     }
-    __syncthreads();
-    const T* vc = V + (size_t)N1 * c;
-    T s = 0;
-    for (unsigned i = threadIdx.x; i < N1; i += blockDim.x) {
-      T rec = 0;
-      for (int a = 0; a < r1; ++a) rec += U1[i + (size_t)N1 * a] * hcol[a];
-      T d = vc[i] - rec;
-      bad |= !isfinite((double)d);
-      s += (T)wv.w[0][i] * d * d;
-    }
-    acc += wcs * (double)s;
-    __syncthreads();
   }
-  acc = block_sum(acc, sh);
-  if (bad && flags) atomicOr(flags, kFlagNonFinite);
-  if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
 template <typename T>
-void launch_recon_err(const T* V, const T* U1, const T* H, int r1, const WeightView& wv, double* partial, int nblocks,
-                      double* out, unsigned* flags, cudaStream_t s, const int* gate) {
-  k_recon_err<T><<<nblocks, 256, 0, s>>>(V, U1, H, r1, wv, partial, flags, gate);
-  count_launch();
-  k_sum_partials<<<1, 256, 0, s>>>(partial, nblocks, out);
+void launch_weights_T(const WeightView& wv, T* w1, T* wcol, cudaStream_t s) {
+  k_weights_T<T><<<152, 256, 0, s>>>(wv, w1, wcol);
   count_launch();
 }
-template void launch_recon_err<float>(const float*, const float*, const float*, int, const WeightView&, double*, int,
-                                      double*, unsigned*, cudaStream_t, const int*);
-template void launch_recon_err<double>(const double*, const double*, const double*, int, const WeightView&, double*,
-                                       int, double*, unsigned*, cudaStream_t, const int*);
+template void launch_weights_T<float>(const WeightView&, float*, float*, cudaStream_t);
+template void launch_weights_T<double>(const WeightView&, double*, double*, cudaStream_t);
 
 void launch_sum_partials(const double* partial, int n, double* out, cudaStream_t s) {
   k_sum_partials<<<1, 256, 0, s>>>(partial, n, out); count_launch();

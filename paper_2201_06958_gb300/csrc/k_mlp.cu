@@ -228,7 +228,7 @@ namespace tdb {
 // re-initialisation + 1), log10 of the previous step's residual.  The network predicts
 // the change of log10 error over the step, so the estimate chains from the previous
 // error and the features do not depend on which steps were evaluated exactly.
-__global__ void __launch_bounds__(256) k_est_features(EstState st, const float* __restrict__ dS, int nds,
+__global__ void __launch_bounds__(256) k_est_features(const EstState* __restrict__ stp, const float* __restrict__ dS, int nds,
                                                       const double* __restrict__ dv2, const double* __restrict__ sig2,
                                                       int4 ranks, int p, const float* __restrict__ P,
                                                       const float* __restrict__ norm, float* __restrict__ feat,
@@ -239,6 +239,7 @@ __global__ void __launch_bounds__(256) k_est_features(EstState st, const float* 
   // cancel).  The network's parameters are staged in shared memory with coalesced loads.
   __shared__ float Ps[MLP_NPARAM];
   __shared__ double sh[32];
+  const EstState st = *stp;     // the host's estimator state of this step (device copy)
   __shared__ float xs[MLP_F], h1[MLP_H];
   __shared__ float red[8];
   const int tid = threadIdx.x;
@@ -316,11 +317,11 @@ __global__ void __launch_bounds__(256) k_est_features(EstState st, const float* 
   }
 }
 
-void est_features(const EstState* st, const float* dS, int nds, const double* dv2, const double* sig2, const int* ranks,
-                  int p, const float* P, const float* norm, float* feat, double* est, int* need, double* ds2,
-                  cudaStream_t s) {
+void est_features(const EstState* st_dev, const float* dS, int nds, const double* dv2, const double* sig2,
+                  const int* ranks, int p, const float* P, const float* norm, float* feat, double* est, int* need,
+                  double* ds2, cudaStream_t s) {
   int4 rk = make_int4(ranks[0], p > 1 ? ranks[1] : 1, p > 2 ? ranks[2] : 1, p > 3 ? ranks[3] : 1);
-  k_est_features<<<1, 256, 0, s>>>(*st, dS, nds, dv2, sig2, rk, p, P, norm, feat, est, need, ds2);
+  k_est_features<<<1, 256, 0, s>>>(st_dev, dS, nds, dv2, sig2, rk, p, P, norm, feat, est, need, ds2);
   count_launch();
 }
 

@@ -1035,8 +1035,19 @@ tdb_status launch_update(UpdArgs& a, int grid_hint, cudaStream_t s) {
   // every CTA is resident (one per SM at most), so the grid barriers cannot deadlock
   const int grid = std::max(a.d.p, std::min(nsm, grid_hint));
   cudaMemsetAsync(a.bar, 0, 2 * sizeof(unsigned), s);
-  void* args[] = {(void*)&a};
-  cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_update<Tc>, grid, UPD_THREADS, args, kUpdSmem, s);
+  // cooperative launch through the extensible API, which stream capture records as a
+  // cooperative kernel node
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(UPD_THREADS);
+  cfg.dynamicSmemBytes = kUpdSmem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_update<Tc>, a);
   count_launch();
   return e == cudaSuccess ? TDB_OK : TDB_ERR_CUDA;
 }

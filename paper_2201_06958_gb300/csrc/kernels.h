@@ -101,8 +101,11 @@ void launch_wnorm2(const T* x, const T* y, const WeightView& wv, double* partial
                    unsigned* flags, cudaStream_t s);
 void launch_sum_partials(const double* partial, int n, double* out, cudaStream_t s);
 template <typename T>
-void launch_recon_err(const T* V, const T* U1, const T* H, int r1, const WeightView& wv, double* partial, int nblocks,
-                      double* out, unsigned* flags, cudaStream_t s, const int* gate = nullptr);
+void launch_recon_err(const T* V, const T* U1, const T* H, int r1, int N1, int64_t ncol, const T* w1, const T* wcol,
+                      double* partial, unsigned* counter, int nblocks, double* out, unsigned* flags, cudaStream_t s,
+                      const int* gate = nullptr);
+template <typename T>
+void launch_weights_T(const WeightView& wv, T* w1, T* wcol, cudaStream_t s);
 template <typename Tin, typename Tm, typename Tacc>
 void launch_modeprod(const Tin* in, Tacc* out, const Tm* M, int64_t L, int K, int J, int64_t Q, int64_t sMj,
                      int64_t sMk, cudaStream_t s, const int* gate = nullptr);

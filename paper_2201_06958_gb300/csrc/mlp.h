@@ -27,9 +27,10 @@ struct EstState {
 };
 
 // Features of the current step, the estimate and the gate (one CTA).
-void est_features(const EstState* st, const float* dS, int nds, const double* dv2, const double* sig2, const int* ranks,
-                  int p, const float* P, const float* norm, float* feat, double* est, int* need, double* ds2,
-                  cudaStream_t s);
+// st_dev: device copy of the estimator state for this step.
+void est_features(const EstState* st_dev, const float* dS, int nds, const double* dv2, const double* sig2,
+                  const int* ranks, int p, const float* P, const float* norm, float* feat, double* est, int* need,
+                  double* ds2, cudaStream_t s);
 void est_normalize(float* X, float* t, int n, float* norm, cudaStream_t s);
 void est_init_params(float* P, unsigned long long seed, cudaStream_t s);
 

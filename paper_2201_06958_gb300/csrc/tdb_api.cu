@@ -84,6 +84,9 @@ struct tdb_ctx {
   int gsplit = 1;
   double* rowpart;
   unsigned* bar;                  // grid-barrier words of the fused update
+  unsigned* redcnt;               // last-CTA reduction counters (zero between launches)
+  void* w1T;                      // w_1 in the compute type
+  void* wcolT;                    // mode-1 column weights prod_{m>1} w_m in the compute type
   unsigned long long* stamps;     // phase timer stamps of the fused update (profiling)
   int ntile = 1;
   double* sig2;
@@ -137,6 +140,23 @@ struct tdb_ctx {
   cudaEvent_t pev[6] = {nullptr};
   tdb_profile pacc;
 
+  // pinned host staging: the step record read back each step and the estimator state /
+  // error gate sent down each step (copies that stream capture can record)
+  Readback* rb_pin = nullptr;
+  EstState* est_pin = nullptr;
+  int* need_pin = nullptr;
+  EstState* est_dev = nullptr;
+  bool need_host = false;          // this step's host gate (evaluate the exact error)
+  bool gated_step = false;         // the estimator decides on the device this step
+  // input slots and the captured step graphs (one per slot parity)
+  const void* slot[2] = {nullptr, nullptr};
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  uint64_t gkey[2] = {0, 0};
+  long long gcount[2] = {0, 0};     // library kernels recorded in each graph (launch counter)
+  cudaStream_t cap_stream = nullptr; // steps are recorded here (any stream can replay them)
+  bool graph_broken = false;
+  int64_t graph_replays = 0, graph_records = 0;
+
   // host state
   const void* V_prev = nullptr;
   bool ready = false;
@@ -146,6 +166,37 @@ struct tdb_ctx {
   Readback rb;
   std::vector<double> h_ev[kMaxModes];
   double h_trace[kMaxModes];
+
+  ~tdb_ctx() {
+    for (int i = 0; i < 2; ++i)
+      if (gexec[i]) cudaGraphExecDestroy(gexec[i]);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (rb_pin) cudaFreeHost(rb_pin);
+  }
+};
+
+struct tdb_batch {
+  std::vector<tdb_ctx*> m;
+  cudaStream_t main = nullptr;       // the caller's stream: graphs are launched here
+  cudaStream_t cap = nullptr;        // private origin stream of the recording
+  std::vector<cudaStream_t> st;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> join;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  std::vector<uint64_t> keys[2];
+  long long gcount[2] = {0, 0};
+  bool broken = false;
+  int64_t replays = 0, records = 0;
+  std::string err;
+
+  ~tdb_batch() {
+    for (int i = 0; i < 2; ++i)
+      if (gexec[i]) cudaGraphExecDestroy(gexec[i]);
+    for (auto e : join) cudaEventDestroy(e);
+    if (fork) cudaEventDestroy(fork);
+    for (auto q : st) cudaStreamDestroy(q);
+    if (cap) cudaStreamDestroy(cap);
+  }
 };
 
 namespace {
@@ -269,6 +320,9 @@ void carve(tdb_ctx* c, Carver& cv) {
   c->ntile = (int)((Nmax + 31) / 32);
   c->rowpart = cv.take<double>((size_t)2 * p * c->ntile * kMaxRank * kMaxRank);
   c->bar = cv.take<unsigned>(2);
+  c->redcnt = cv.take<unsigned>(8);
+  c->w1T = cv.take<char>((size_t)c->N[0] * tsz);
+  c->wcolT = cv.take<char>((size_t)(c->S / c->N[0]) * tsz);
   c->stamps = cv.take<unsigned long long>(32);
   c->sig2 = cv.take<double>(p * kMaxRank);
   c->Vprev = cv.take<float>(p * kMaxRank * kMaxRank);
@@ -276,6 +330,7 @@ void carve(tdb_ctx* c, Carver& cv) {
   c->nblk = 608;
   c->npart = cv.take<double>(c->nblk);
   c->rb_dev = cv.take<Readback>(1);
+  c->est_dev = cv.take<EstState>(1);
   c->flags = &c->rb_dev->flags;
   // HOSVD scratch
   int64_t nn = (Nmax + 1) & ~1;
@@ -487,7 +542,8 @@ tdb_status exact_error2(tdb_ctx* ctx, const Tc* V, const int* gate = nullptr) {
     cur[n] = ctx->N[n];
     src = dst;
   }
-  launch_recon_err<Tc>(V, (const Tc*)ctx->Uc[0], src, ctx->r[0], weight_view(ctx), ctx->npart, ctx->nblk,
+  launch_recon_err<Tc>(V, (const Tc*)ctx->Uc[0], src, ctx->r[0], (int)ctx->N[0], ctx->S / ctx->N[0],
+                       (const Tc*)ctx->w1T, (const Tc*)ctx->wcolT, ctx->npart, ctx->redcnt, ctx->nblk,
                        &ctx->rb_dev->err2, ctx->flags, s, gate);
   CHECK_LAUNCH();
   return TDB_OK;
@@ -516,13 +572,25 @@ tdb_status refresh_derived(tdb_ctx* ctx, bool bases_too) {
   return TDB_OK;
 }
 
-tdb_status readback(tdb_ctx* ctx) {
+// The step record: sigma^2 into the record, then the record to pinned host memory.
+tdb_status readback_enqueue(tdb_ctx* ctx) {
   cudaStream_t s = ctx->stream;
   CK(cudaMemcpyAsync(ctx->rb_dev->sig2, ctx->sig2, sizeof(double) * ctx->p * kMaxRank, cudaMemcpyDeviceToDevice, s));
-  CK(cudaMemcpyAsync(&ctx->rb, ctx->rb_dev, sizeof(Readback), cudaMemcpyDeviceToHost, s));
-  CK(cudaStreamSynchronize(s));
+  CK(cudaMemcpyAsync(ctx->rb_pin, ctx->rb_dev, sizeof(Readback), cudaMemcpyDeviceToHost, s));
+  return TDB_OK;
+}
+
+// After the stream (or a graph holding readback_enqueue) has completed.
+tdb_status readback_done(tdb_ctx* ctx) {
+  ctx->rb = *ctx->rb_pin;
   if (ctx->rb.flags & kFlagTimeout) { ctx->err = "device wait timed out"; return TDB_ERR_TIMEOUT; }
   return TDB_OK;
+}
+
+tdb_status readback(tdb_ctx* ctx) {
+  TRY(readback_enqueue(ctx));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return readback_done(ctx);
 }
 
 // ---------------------------------------------------------------------------
@@ -792,14 +860,37 @@ tdb_status control(tdb_ctx* ctx, const Tc* V, double eps, double* eps_after, int
 }
 
 // ---------------------------------------------------------------------------
-// One step
+// One step: prepare (host), enqueue (device work, no host synchronisation, so that
+// stream capture can record it), finish (host, after the step record is back).
 // ---------------------------------------------------------------------------
+
+// Host bookkeeping before the device work: counters, the error gate, and the staged
+// estimator state.
+void prepare_step(tdb_ctx* ctx) {
+  ctx->step++;
+  ctx->est.steps_since_exact += 1;
+  ctx->est.steps_since_reinit += 1;
+  ctx->gated_step = ctx->cfg.error_mode == TDB_ERRMODE_MLP && ctx->est.ready;
+  switch (ctx->cfg.error_mode) {
+    case TDB_ERRMODE_EXACT: ctx->need_host = true; break;
+    case TDB_ERRMODE_EVERY_K: ctx->need_host = (ctx->step % ctx->cfg.error_every) == 0; break;
+    case TDB_ERRMODE_MLP: ctx->need_host = true; break;      // the device decides when the estimator is ready
+    default: ctx->need_host = false;
+  }
+  *ctx->est_pin = ctx->est;
+  *ctx->need_pin = ctx->need_host ? 1 : 0;
+}
+
+// a1..a7 and the step record, on ctx->stream.  `all_paths` (graph capture) enqueues the
+// exact-error kernels on every step, gated by the device word, so that the recorded
+// work does not depend on host decisions.
 template <typename Tc>
-tdb_status step_impl(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
+tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths) {
   cudaStream_t s = ctx->stream;
-  const Tc* Vp = (const Tc*)ctx->V_prev;
   const int p = ctx->p;
   CK(cudaMemsetAsync(ctx->rb_dev, 0, sizeof(Readback), s));
+  CK(cudaMemcpyAsync(&ctx->rb_dev->need, ctx->need_pin, sizeof(int), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ctx->est_dev, ctx->est_pin, sizeof(EstState), cudaMemcpyHostToDevice, s));
   cudaEvent_t* ev = ctx->prof ? ctx->pev : nullptr;
   if (ev) CK(cudaEventRecord(ev[0], s));
   // a1 + a2: difference and projection
@@ -859,33 +950,32 @@ tdb_status step_impl(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
       ctx->err = us == TDB_ERR_UNSUPPORTED ? "cooperative launch unsupported" : "fused update launch failed";
       return us;
     }
-    ctx->warm = true;
     CHECK_LAUNCH();
   }
   if (ev) CK(cudaEventRecord(ev[2], s));
   // a7: error, exact or estimated
-  ctx->step++;
-  ctx->est.steps_since_exact += 1;
-  ctx->est.steps_since_reinit += 1;
-  const bool feats = !ctx->f64;
-  if (feats) {
+  if (!ctx->f64) {
     int64_t nds = 1;
     for (int n = 0; n < p; ++n) nds *= ctx->r[n];
-    est_features(&ctx->est, (const float*)ctx->dS, (int)nds, &ctx->rb_dev->dv2, ctx->sig2, ctx->r, p, ctx->mlpP,
+    est_features(ctx->est_dev, (const float*)ctx->dS, (int)nds, &ctx->rb_dev->dv2, ctx->sig2, ctx->r, p, ctx->mlpP,
                  ctx->mlpNorm, ctx->rb_dev->feat, &ctx->rb_dev->est, &ctx->rb_dev->need, &ctx->rb_dev->ds2, s);
     CHECK_LAUNCH();
   }
-  bool exact = false;
-  const bool gated = ctx->cfg.error_mode == TDB_ERRMODE_MLP && ctx->est.ready;
-  switch (ctx->cfg.error_mode) {
-    case TDB_ERRMODE_EXACT: exact = true; break;
-    case TDB_ERRMODE_EVERY_K: exact = (ctx->step % ctx->cfg.error_every) == 0; break;
-    case TDB_ERRMODE_MLP: exact = true; break;      // decided on the device when the estimator is ready
-    default: exact = false;
-  }
-  if (exact) TRY(exact_error2<Tc>(ctx, Vn, gated ? &ctx->rb_dev->need : nullptr));
+  if (all_paths)
+    TRY(exact_error2<Tc>(ctx, Vn, &ctx->rb_dev->need));
+  else if (ctx->need_host)
+    TRY(exact_error2<Tc>(ctx, Vn, ctx->gated_step ? &ctx->rb_dev->need : nullptr));
   if (ev) CK(cudaEventRecord(ev[3], s));
-  TRY(readback(ctx));
+  return readback_enqueue(ctx);
+}
+
+// After the step record is back: errors, rank control (Sec. 2.5), estimator bookkeeping,
+// the step info.
+template <typename Tc>
+tdb_status finish_step(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
+  const int p = ctx->p;
+  ctx->warm = true;
+  cudaEvent_t* ev = ctx->prof ? ctx->pev : nullptr;
   if (ev) {
     float m01 = 0, m12 = 0, m23 = 0, m45 = 0;
     CK(cudaEventElapsedTime(&m01, ev[0], ev[1]));
@@ -902,11 +992,11 @@ tdb_status step_impl(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
   if (ctx->rb.flags & kFlagNonFinite) { ctx->err = "non-finite value in a snapshot difference"; return TDB_ERR_NONFINITE; }
   if (ctx->rb.flags & kFlagCholGram) { ctx->err = "T_(n) T_(n)^T is not positive definite"; return TDB_ERR_RANK_DEFICIENT; }
   if (ctx->rb.flags & kFlagCholQR) { ctx->err = "U^T W U is not positive definite"; return TDB_ERR_RANK_DEFICIENT; }
-  if (gated) exact = ctx->rb.need != 0;
+  const bool gated = ctx->gated_step;
+  const bool exact = gated ? ctx->rb.need != 0 : ctx->need_host;
+  const bool feats = !ctx->f64;
   double eps = exact ? std::sqrt(std::max(ctx->rb.err2, 0.0)) : (gated ? ctx->rb.est : NAN);
   double dv2 = ctx->rb.dv2;
-  double sig_step[kMaxModes][kMaxRank];
-  memcpy(sig_step, ctx->rb.sig2, sizeof(sig_step));
   if (exact) ctx->exact_evals++;
   // a8: rank control
   double eps_after = eps;
@@ -965,9 +1055,132 @@ tdb_status step_impl(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
       info->gamma[n] = tot / (tot + e * e) * 100.0;
       info->sigma_min[n] = std::sqrt(std::max(ctx->rb.sig2[n][ctx->r[n] - 1], 0.0));
     }
-    (void)sig_step;
   }
   return (action == ACT_CAP) ? TDB_WARN_RANK_CAP : TDB_OK;
+}
+
+template <typename Tc>
+tdb_status step_impl(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
+  prepare_step(ctx);
+  TRY(enqueue_step<Tc>(ctx, Vn, (const Tc*)ctx->V_prev, false));
+  CK(cudaStreamSynchronize(ctx->stream));
+  TRY(readback_done(ctx));
+  return finish_step<Tc>(ctx, Vn, info);
+}
+
+// What the recorded step depends on besides data: the ranks and the modes of work.
+uint64_t graph_key(const tdb_ctx* ctx) {
+  uint64_t k = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) { k = (k ^ v) * 1099511628211ull; };
+  for (int n = 0; n < ctx->p; ++n) mix((uint64_t)ctx->r[n]);
+  mix(ctx->prof ? 1 : 0);
+  mix(ctx->warm ? 1 : 0);
+  mix((uint64_t)ctx->cfg.error_mode);
+  mix(ctx->use_tc ? 1 : 0);
+  return k | 1ull;
+}
+
+void drop_graphs(tdb_ctx* ctx) {
+  for (int i = 0; i < 2; ++i) {
+    if (ctx->gexec[i]) cudaGraphExecDestroy(ctx->gexec[i]);
+    ctx->gexec[i] = nullptr;
+    ctx->gkey[i] = 0;
+  }
+}
+
+// Record the step on the context's stream into an executable graph (parity = slot of V_{k+1}).
+// (The caller's stream may be the legacy default stream, which cannot be captured: the
+// work is recorded on a private stream and the graph launched on the caller's.)
+template <typename Tc>
+tdb_status capture_step(tdb_ctx* ctx, int parity, cudaGraphExec_t* out) {
+  if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->err = "capture stream unavailable";
+    return TDB_ERR_CUDA;
+  }
+  cudaStream_t s = ctx->cap_stream;
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->err = "stream capture could not begin";
+    return TDB_ERR_CUDA;
+  }
+  cudaStream_t own = ctx->stream;
+  ctx->stream = s;
+  const long long l0 = launches_so_far();
+  tdb_status st = enqueue_step<Tc>(ctx, (const Tc*)ctx->slot[parity], (const Tc*)ctx->slot[1 - parity], true);
+  ctx->gcount[parity] = launches_so_far() - l0;
+  count_launch(-(int)ctx->gcount[parity]);     // recorded, not launched; counted per replay
+  ctx->stream = own;
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (st != TDB_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (st == TDB_OK) { ctx->err = std::string("step capture: ") + cudaGetErrorString(e); st = TDB_ERR_CUDA; }
+    return st;
+  }
+  e = cudaGraphInstantiate(out, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { ctx->err = std::string("graph instantiate: ") + cudaGetErrorString(e); return TDB_ERR_CUDA; }
+  return TDB_OK;
+}
+
+template <typename Tc>
+tdb_status step_slot(tdb_ctx* ctx, int parity, tdb_step_info* info) {
+  const Tc* Vn = (const Tc*)ctx->slot[parity];
+  // the tensor-core plan prepares its constant weights on its first (eager) call;
+  // profiled steps run eagerly (events inside a graph cannot be timed)
+  const bool can_graph = !ctx->graph_broken && !ctx->prof && (!ctx->use_tc || ctx->tc.wsl_ready);
+  if (!can_graph) return step_impl<Tc>(ctx, Vn, info);
+  prepare_step(ctx);
+  const uint64_t key = graph_key(ctx);
+  if (!ctx->gexec[parity] || ctx->gkey[parity] != key) {
+    if (ctx->gexec[parity]) cudaGraphExecDestroy(ctx->gexec[parity]);
+    ctx->gexec[parity] = nullptr;
+    if (capture_step<Tc>(ctx, parity, &ctx->gexec[parity]) != TDB_OK) {
+      // stream capture unavailable for this configuration: run this and later steps eagerly
+      ctx->graph_broken = true;
+      ctx->gexec[parity] = nullptr;
+      TRY(enqueue_step<Tc>(ctx, Vn, (const Tc*)ctx->V_prev, false));
+      CK(cudaStreamSynchronize(ctx->stream));
+      TRY(readback_done(ctx));
+      return finish_step<Tc>(ctx, Vn, info);
+    }
+    ctx->gkey[parity] = key;
+    ctx->graph_records++;
+  }
+  CK(cudaGraphLaunch(ctx->gexec[parity], ctx->stream));
+  ctx->graph_replays++;
+  count_launch((int)ctx->gcount[parity]);
+  CK(cudaStreamSynchronize(ctx->stream));
+  TRY(readback_done(ctx));
+  return finish_step<Tc>(ctx, Vn, info);
+}
+
+tdb_status enqueue_any(tdb_ctx* ctx, int parity) {
+  return ctx->f64 ? enqueue_step<double>(ctx, (const double*)ctx->slot[parity], (const double*)ctx->slot[1 - parity], true)
+                  : enqueue_step<float>(ctx, (const float*)ctx->slot[parity], (const float*)ctx->slot[1 - parity], true);
+}
+
+tdb_status finish_any(tdb_ctx* ctx, int parity, tdb_step_info* info) {
+  return ctx->f64 ? finish_step<double>(ctx, (const double*)ctx->slot[parity], info)
+                  : finish_step<float>(ctx, (const float*)ctx->slot[parity], info);
+}
+
+tdb_status step_any(tdb_ctx* ctx, int parity, tdb_step_info* info) {
+  return ctx->f64 ? step_impl<double>(ctx, (const double*)ctx->slot[parity], info)
+                  : step_impl<float>(ctx, (const float*)ctx->slot[parity], info);
+}
+
+tdb_status slot_check(tdb_ctx* ctx, int parity) {
+  if (!ctx->ready) { ctx->err = "push before init"; return TDB_ERR_STATE; }
+  if (parity != 0 && parity != 1) { ctx->err = "slot parity must be 0 or 1"; return TDB_ERR_INVALID_ARG; }
+  if (!ctx->slot[0] || !ctx->slot[1]) { ctx->err = "input slots not set (tdb_set_input_slots)"; return TDB_ERR_STATE; }
+  if (ctx->V_prev != ctx->slot[1 - parity]) {
+    ctx->err = "the previous snapshot is not in the other slot";
+    return TDB_ERR_STATE;
+  }
+  return TDB_OK;
 }
 
 tdb_status common_init(tdb_ctx** out, const tdb_config* cfg, void* ws, size_t ws_bytes, void* stream, tdb_ctx** made) {
@@ -1018,7 +1231,20 @@ tdb_status common_init(tdb_ctx** out, const tdb_config* cfg, void* ws, size_t ws
       return TDB_ERR_CUDA;
     }
   }
+  if (cudaHostAlloc((void**)&ctx->rb_pin, sizeof(Readback) + sizeof(EstState) + 64, cudaHostAllocDefault) !=
+      cudaSuccess) {
+    g_init_error = "pinned host memory for the step record unavailable";
+    delete ctx;
+    return TDB_ERR_CUDA;
+  }
+  ctx->est_pin = (EstState*)((char*)ctx->rb_pin + ((sizeof(Readback) + 15) & ~(size_t)15));
+  ctx->need_pin = (int*)((char*)ctx->est_pin + ((sizeof(EstState) + 15) & ~(size_t)15));
   cudaMemsetAsync(ctx->rb_dev, 0, sizeof(Readback), ctx->stream);
+  cudaMemsetAsync(ctx->redcnt, 0, 8 * sizeof(unsigned), ctx->stream);
+  if (ctx->f64)
+    launch_weights_T<double>(weight_view(ctx), (double*)ctx->w1T, (double*)ctx->wcolT, ctx->stream);
+  else
+    launch_weights_T<float>(weight_view(ctx), (float*)ctx->w1T, (float*)ctx->wcolT, ctx->stream);
   memset(&ctx->est, 0, sizeof(ctx->est));
   ctx->est.last_log_eps = -30.0;
   ctx->est.max_skip = std::max(1, ctx->cfg.error_every);
@@ -1388,6 +1614,166 @@ void tdb_destroy(tdb_ctx* ctx) {
   delete ctx;
 }
 
-const char* tdb_version(void) { return "tdb 0.1 sm_103a"; }
+tdb_status tdb_set_input_slots(tdb_ctx* ctx, const void* slot0, const void* slot1) {
+  if (!ctx) return TDB_ERR_INVALID_ARG;
+  if ((slot0 == nullptr) != (slot1 == nullptr) || (slot0 && slot0 == slot1)) {
+    ctx->err = "two distinct slots, or none";
+    return TDB_ERR_INVALID_ARG;
+  }
+  ctx->slot[0] = slot0;
+  ctx->slot[1] = slot1;
+  drop_graphs(ctx);
+  return TDB_OK;
+}
+
+tdb_status tdb_push_slot(tdb_ctx* ctx, int parity, tdb_step_info* info) {
+  if (!ctx) return TDB_ERR_INVALID_ARG;
+  TRY(slot_check(ctx, parity));
+  return ctx->f64 ? step_slot<double>(ctx, parity, info) : step_slot<float>(ctx, parity, info);
+}
+
+tdb_status tdb_batch_create(tdb_batch** out, tdb_ctx* const* members, int n, int nstreams, void* stream) {
+  if (!out || !members || n < 1 || nstreams < 1) return TDB_ERR_INVALID_ARG;
+  *out = nullptr;
+  for (int i = 0; i < n; ++i)
+    if (!members[i] || !members[i]->ready) return TDB_ERR_STATE;
+  tdb_batch* b = new (std::nothrow) tdb_batch();
+  if (!b) return TDB_ERR_INVALID_ARG;
+  b->m.assign(members, members + n);
+  b->main = (cudaStream_t)stream;
+  const int ns = std::min(nstreams, n);
+  for (int k = 0; k < ns; ++k) {
+    cudaStream_t q = nullptr;
+    cudaEvent_t e = nullptr;
+    if (cudaStreamCreateWithFlags(&q, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+      if (q) cudaStreamDestroy(q);
+      delete b;
+      return TDB_ERR_CUDA;
+    }
+    b->st.push_back(q);
+    b->join.push_back(e);
+  }
+  if (cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    delete b;
+    return TDB_ERR_CUDA;
+  }
+  *out = b;
+  return TDB_OK;
+}
+
+// Record every member's step, member i on stream i mod nstreams, into one graph.
+static tdb_status batch_capture(tdb_batch* b, int parity) {
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+    cudaGetLastError();
+    b->err = "batch capture could not begin";
+    return TDB_ERR_CUDA;
+  }
+  tdb_status st = TDB_OK;
+  const long long l0 = launches_so_far();
+  cudaEventRecord(b->fork, b->cap);
+  for (size_t k = 0; k < b->st.size(); ++k) cudaStreamWaitEvent(b->st[k], b->fork, 0);
+  for (size_t i = 0; i < b->m.size() && st == TDB_OK; ++i) {
+    tdb_ctx* c = b->m[i];
+    cudaStream_t own = c->stream;
+    c->stream = b->st[i % b->st.size()];
+    st = enqueue_any(c, parity);
+    c->stream = own;
+    if (st != TDB_OK) b->err = "member " + std::to_string(i) + ": " + c->err;
+  }
+  for (size_t k = 0; k < b->st.size(); ++k) {
+    cudaEventRecord(b->join[k], b->st[k]);
+    cudaStreamWaitEvent(b->cap, b->join[k], 0);
+  }
+  b->gcount[parity] = launches_so_far() - l0;
+  count_launch(-(int)b->gcount[parity]);
+  cudaError_t e = cudaStreamEndCapture(b->cap, &g);
+  if (st != TDB_OK || e != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    if (st == TDB_OK) { b->err = std::string("batch capture: ") + cudaGetErrorString(e); st = TDB_ERR_CUDA; }
+    return st;
+  }
+  e = cudaGraphInstantiate(&b->gexec[parity], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) { b->err = std::string("batch instantiate: ") + cudaGetErrorString(e); return TDB_ERR_CUDA; }
+  return TDB_OK;
+}
+
+tdb_status tdb_batch_push(tdb_batch* b, int parity, tdb_step_info* infos) {
+  if (!b) return TDB_ERR_INVALID_ARG;
+  const size_t n = b->m.size();
+  bool eager = b->broken;
+  for (size_t i = 0; i < n; ++i) {
+    tdb_ctx* c = b->m[i];
+    tdb_status st = slot_check(c, parity);
+    if (st != TDB_OK) { b->err = "member " + std::to_string(i) + ": " + c->err; return st; }
+    if ((c->use_tc && !c->tc.wsl_ready) || c->prof) eager = true;
+  }
+  tdb_status worst = TDB_OK;
+  auto note = [&](tdb_status st, size_t i) {
+    if (st == TDB_OK) return;
+    if (worst == TDB_OK || (worst == TDB_WARN_RANK_CAP && st != TDB_WARN_RANK_CAP)) {
+      worst = st;
+      b->err = "member " + std::to_string(i) + ": " + b->m[i]->err;
+    }
+  };
+  if (eager) {
+    for (size_t i = 0; i < n; ++i) note(step_any(b->m[i], parity, infos ? infos + i : nullptr), i);
+    return worst;
+  }
+  for (size_t i = 0; i < n; ++i) prepare_step(b->m[i]);
+  bool fresh = b->gexec[parity] != nullptr && b->keys[parity].size() == n;
+  for (size_t i = 0; i < n && fresh; ++i) fresh = b->keys[parity][i] == graph_key(b->m[i]);
+  if (!fresh) {
+    if (b->gexec[parity]) cudaGraphExecDestroy(b->gexec[parity]);
+    b->gexec[parity] = nullptr;
+    if (batch_capture(b, parity) != TDB_OK) {
+      // capture unavailable: this and later steps run member by member
+      b->broken = true;
+      b->gexec[parity] = nullptr;
+      for (size_t i = 0; i < n; ++i) {
+        tdb_ctx* c = b->m[i];
+        tdb_status st = enqueue_any(c, parity);
+        if (st == TDB_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = TDB_ERR_CUDA;
+        if (st == TDB_OK) st = readback_done(c);
+        if (st == TDB_OK) st = finish_any(c, parity, infos ? infos + i : nullptr);
+        note(st, i);
+      }
+      return worst;
+    }
+    b->keys[parity].resize(n);
+    for (size_t i = 0; i < n; ++i) b->keys[parity][i] = graph_key(b->m[i]);
+    b->records++;
+  }
+  b->replays++;
+  if (cudaGraphLaunch(b->gexec[parity], b->main) != cudaSuccess || cudaStreamSynchronize(b->main) != cudaSuccess) {
+    b->err = std::string("batch graph: ") + cudaGetErrorString(cudaGetLastError());
+    return TDB_ERR_CUDA;
+  }
+  count_launch((int)b->gcount[parity]);
+  for (size_t i = 0; i < n; ++i) {
+    tdb_ctx* c = b->m[i];
+    tdb_status st = readback_done(c);
+    if (st == TDB_OK) st = finish_any(c, parity, infos ? infos + i : nullptr);
+    note(st, i);
+  }
+  return worst;
+}
+
+const char* tdb_batch_last_error(const tdb_batch* b) { return b ? b->err.c_str() : "null batch"; }
+
+tdb_status tdb_get_graph_counters(const tdb_ctx* ctx, const tdb_batch* b, int64_t* replays, int64_t* records) {
+  if ((ctx == nullptr) == (b == nullptr)) return TDB_ERR_INVALID_ARG;
+  if (replays) *replays = ctx ? ctx->graph_replays : b->replays;
+  if (records) *records = ctx ? ctx->graph_records : b->records;
+  return TDB_OK;
+}
+
+void tdb_batch_destroy(tdb_batch* b) { delete b; }
+
+const char* tdb_version(void) { return "tdb 0.2 sm_103a"; }
 
 }  // extern "C"

@@ -75,7 +75,8 @@ EXPORTS = [
     "tdb_load_state", "tdb_last_error", "tdb_status_string", "tdb_destroy", "tdb_version",
     "tdb_set_profiling", "tdb_get_profile", "tdb_kernel_launches", "tdb_project_noalloc",
     "tdb_mlp_param_count", "tdb_mlp_forward", "tdb_mlp_loss_grad", "tdb_mlp_adam_step", "tdb_estimator_fit",
-    "tdb_estimator_params", "tdb_estimator_trace",
+    "tdb_estimator_params", "tdb_estimator_trace", "tdb_set_input_slots", "tdb_push_slot",
+    "tdb_batch_create", "tdb_batch_push", "tdb_batch_last_error", "tdb_batch_destroy", "tdb_get_graph_counters",
 ]
 
 
@@ -120,6 +121,20 @@ def load(path: str = LIB_PATH):
     lib.tdb_destroy.restype = None
     lib.tdb_version.argtypes = []
     lib.tdb_version.restype = C.c_char_p
+    lib.tdb_set_input_slots.argtypes = [vp, vp, vp]
+    lib.tdb_set_input_slots.restype = st
+    lib.tdb_push_slot.argtypes = [vp, C.c_int, C.POINTER(tdb_step_info)]
+    lib.tdb_push_slot.restype = st
+    lib.tdb_batch_create.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int, C.c_int, vp]
+    lib.tdb_batch_create.restype = st
+    lib.tdb_batch_push.argtypes = [vp, C.c_int, vp]
+    lib.tdb_batch_push.restype = st
+    lib.tdb_batch_last_error.argtypes = [vp]
+    lib.tdb_batch_last_error.restype = C.c_char_p
+    lib.tdb_batch_destroy.argtypes = [vp]
+    lib.tdb_batch_destroy.restype = None
+    lib.tdb_get_graph_counters.argtypes = [vp, vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+    lib.tdb_get_graph_counters.restype = st
     lib.tdb_set_profiling.argtypes = [vp, C.c_int]
     lib.tdb_set_profiling.restype = st
     lib.tdb_get_profile.argtypes = [vp, vp]
@@ -263,6 +278,35 @@ class TDB:
         """Push a snapshot given by device address (no checks); returns the status."""
         return self.lib.tdb_push_snapshot(self.ctx, C.c_void_p(ptr), C.byref(info) if info is not None else None)
 
+    def set_input_slots(self, slot0: Optional[torch.Tensor], slot1: Optional[torch.Tensor]):
+        """Two snapshot buffers owned by the caller; steps then read V_{k+1} from one and
+        V_k from the other (``push_slot``).  None, None removes them."""
+        if slot0 is None and slot1 is None:
+            self._check(self.lib.tdb_set_input_slots(self.ctx, None, None))
+            self._slots = None
+            return self
+        a, b = self._snap(slot0), self._snap(slot1)
+        self._check(self.lib.tdb_set_input_slots(self.ctx, C.c_void_p(a.data_ptr()), C.c_void_p(b.data_ptr())))
+        self._slots = (a, b)
+        return self
+
+    def push_slot(self, parity: int) -> dict:
+        """One step with V_{k+1} in slot ``parity`` (recorded once, then replayed as a graph)."""
+        info = tdb_step_info()
+        st = self.lib.tdb_push_slot(self.ctx, int(parity), C.byref(info))
+        self._check(st)
+        self._prev = self._slots[parity]
+        return self._info_dict(info, st)
+
+    def _info_dict(self, info, st):
+        return {
+            "step": info.step, "eps": info.eps, "eps_exact": bool(info.eps_exact), "eps_step": info.eps_step,
+            "gamma": list(info.gamma)[: self.p], "sigma_min": list(info.sigma_min)[: self.p],
+            "ranks": list(info.ranks)[: self.p], "reinit": info.reinit, "action": ACTIONS.get(info.action, "?"),
+            "cr": info.cr, "dv_norm": info.dv_norm, "ds_norm": info.ds_norm, "eps_est": info.eps_est,
+            "gate": info.gate, "status": st,
+        }
+
     def reconstruct(self, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         if out is None:
             out = torch.empty(self.storage_shape, dtype=self.dtype, device=self.device)
@@ -310,7 +354,10 @@ class TDB:
     def counters(self):
         s, r, e = C.c_int64(), C.c_int64(), C.c_int64()
         self._check(self.lib.tdb_get_counters(self.ctx, C.byref(s), C.byref(r), C.byref(e)))
-        return {"steps": s.value, "reinits": r.value, "exact_evals": e.value}
+        g, gr = C.c_int64(), C.c_int64()
+        self._check(self.lib.tdb_get_graph_counters(self.ctx, None, C.byref(g), C.byref(gr)))
+        return {"steps": s.value, "reinits": r.value, "exact_evals": e.value, "graph_replays": g.value,
+                "graph_records": gr.value}
 
     def save_state(self) -> bytes:
         n = C.c_size_t(0)
@@ -351,6 +398,52 @@ class TDB:
         if self.ctx:
             self.lib.tdb_destroy(self.ctx)
             self.ctx = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Independent contexts stepped together: every member's step recorded into one
+    graph over ``nstreams`` streams, one synchronisation per batch step.  Members must
+    be initialised and have input slots; they stay owned by the caller."""
+
+    def __init__(self, members: Sequence[TDB], nstreams: int = 8, stream=None):
+        self.lib = load()
+        self.members = list(members)
+        arr = (C.c_void_p * len(self.members))(*[m.ctx.value for m in self.members])
+        self.stream = stream or torch.cuda.current_stream(self.members[0].device)
+        self.b = C.c_void_p()
+        st = self.lib.tdb_batch_create(C.byref(self.b), arr, len(self.members), int(nstreams),
+                                       C.c_void_p(self.stream.cuda_stream))
+        if st != TDB_OK:
+            raise TDBError(st, "batch create")
+        self._infos = (tdb_step_info * len(self.members))()
+
+    def push(self, parity: int) -> List[dict]:
+        st = self.lib.tdb_batch_push(self.b, int(parity), C.cast(self._infos, C.c_void_p))
+        if st not in (TDB_OK, TDB_WARN_RANK_CAP):
+            raise TDBError(st, self.lib.tdb_batch_last_error(self.b).decode())
+        out = []
+        for m, info in zip(self.members, self._infos):
+            m._prev = m._slots[parity]
+            out.append(m._info_dict(info, st))
+        return out
+
+    def counters(self):
+        g, gr = C.c_int64(), C.c_int64()
+        st = self.lib.tdb_get_graph_counters(None, self.b, C.byref(g), C.byref(gr))
+        if st != TDB_OK:
+            raise TDBError(st, "graph counters")
+        return {"graph_replays": g.value, "graph_records": gr.value}
+
+    def close(self):
+        if self.b:
+            self.lib.tdb_batch_destroy(self.b)
+            self.b = C.c_void_p()
 
     def __del__(self):
         try:

@@ -1,0 +1,99 @@
+"""Recorded steps and batches give the results of plain pushes, bit for bit.
+
+tdb_push_slot records a step's device work as a CUDA graph (once per slot parity and
+rank configuration) and replays it; a batch records every member's step into one
+graph over several streams.  Neither changes what a step computes, so the step records
+and the final factors must equal those of tdb_push_snapshot on the same snapshots,
+including across control actions (re-initialisations and rank changes re-record)."""
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2201_06958_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+cuda = pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")
+
+KEYS = ("eps", "eps_exact", "eps_step", "ranks", "reinit", "action", "dv_norm", "gamma", "sigma_min")
+
+
+@pytest.fixture(scope="module")
+def tdbmod():
+    from paper_2201_06958_gb300 import build_lib, tdb
+    build_lib.build()
+    return tdb
+
+
+def same_info(a, b):
+    for k in KEYS:
+        va, vb = a[k], b[k]
+        if isinstance(va, float) and np.isnan(va):
+            assert np.isnan(vb), k
+        else:
+            assert va == vb, (k, va, vb)
+
+
+def same_factors(A, B):
+    Ta, Ua = A.factors()
+    Tb, Ub = B.factors()
+    assert np.array_equal(Ta, Tb)
+    assert all(np.array_equal(x, y) for x, y in zip(Ua, Ub))
+
+
+@cuda
+@pytest.mark.parametrize("precision", ["bf16", "fp32"])
+def test_slot_graph_steps_equal_pointer_pushes(tdbmod, precision):
+    wl = S.make_workload("reactive")
+    steps = 80
+    snaps = [wl.snapshot(k, device="cuda") for k in range(steps + 1)]
+    kw = dict(rank_max=wl.rank_max, weights=wl.weights, eps_th=8e-5, gamma_th=99.9, slope_window=5,
+              precision=precision, error_mode="exact")
+    A = tdbmod.TDB(wl.dims, wl.rank, **kw).init(snaps[0])
+    B = tdbmod.TDB(wl.dims, wl.rank, **kw)
+    slots = [torch.empty_like(snaps[0]), torch.empty_like(snaps[0])]
+    slots[1].copy_(snaps[0])
+    B.init(slots[1]).set_input_slots(slots[0], slots[1])
+    actions = set()
+    for k in range(1, steps + 1):
+        parity = (k - 1) % 2
+        slots[parity].copy_(snaps[k])
+        ib = B.push_slot(parity)
+        ia = A.push(snaps[k])
+        same_info(ia, ib)
+        actions.add(ia["action"])
+    same_factors(A, B)
+    assert actions - {"none"}, "the run should include a control action (re-recording the step)"
+    c = B.counters()
+    # every step after the first (which prepares the tensor-core weights) is a replay
+    assert c["graph_replays"] >= steps - 1 and 2 <= c["graph_records"] < steps // 2, c
+
+
+@cuda
+def test_batch_equals_members_stepped_alone(tdbmod):
+    members = S.make_batch(count=6)
+    steps = 24
+    A, B, snaps, slots = [], [], [], []
+    for wl in members:
+        prec = "bf16" if wl.dims[0] % 4 == 0 else "fp32"
+        kw = dict(rank_max=wl.rank_max, weights=wl.weights, precision=prec, error_mode="every_k", error_every=5)
+        sn = [wl.snapshot(k, device="cuda").to(torch.float32).contiguous() for k in range(steps + 1)]
+        sl = [torch.empty_like(sn[0]), torch.empty_like(sn[0])]
+        sl[1].copy_(sn[0])
+        A.append(tdbmod.TDB(wl.dims, wl.rank, **kw).init(sn[0]))
+        B.append(tdbmod.TDB(wl.dims, wl.rank, **kw).init(sl[1]).set_input_slots(sl[0], sl[1]))
+        snaps.append(sn)
+        slots.append(sl)
+    batch = tdbmod.Batch(B, nstreams=3)
+    for k in range(1, steps + 1):
+        parity = (k - 1) % 2
+        for i in range(len(members)):
+            slots[i][parity].copy_(snaps[i][k])
+        infos = batch.push(parity)
+        for i in range(len(members)):
+            same_info(A[i].push(snaps[i][k]), infos[i])
+    for a, b in zip(A, B):
+        same_factors(a, b)
+    c = batch.counters()
+    assert c["graph_replays"] >= steps - 1 and c["graph_records"] <= 3, c
+    batch.close()
