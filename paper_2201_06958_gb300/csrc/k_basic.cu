@@ -145,11 +145,14 @@ template void launch_wnorm2<double>(const double*, const double*, const WeightVi
 
 // Exact error of Eq. 2.20 without materialising V^TDB: with H = T x_2 U_2 ... x_p U_p
 // (r_1 x N_2 x ... x N_p), every mode-1 column of the reconstruction is U_1 H[:, c].
-// One warp per column (lanes over rows, coalesced), U_1 staged in shared memory when
-// it fits, the column's H values held in registers; w_1 and the column weights
+// One warp per column, U_1 and w_1 staged in shared memory when they fit, the
+// column's H values broadcast by shuffles; w_1 and the column weights
 // w_c = prod_{m>1} w_m(i_m) in the compute type; per-column sums in the compute type,
-// double across columns.  The last CTA to finish adds the per-CTA partials in a fixed
-// order and writes *out (no second launch); `counter` is zero before and after.
+// double across columns.  Float with N_1 % 4 == 0: lanes own float4 row groups and a
+// warp works on two columns at once with all their loads issued before the
+// arithmetic (the pass is bound by how many bytes of V are in flight).  The last CTA
+// to finish adds the per-CTA partials in a fixed order and writes *out (no second
+// launch); `counter` is zero before and after.
 template <typename T>
 __global__ void __launch_bounds__(256) k_recon_err(const T* __restrict__ V, const T* __restrict__ U1,
                                                    const T* __restrict__ H, int r1, int N1, unsigned ncol,
@@ -160,34 +163,118 @@ __global__ void __launch_bounds__(256) k_recon_err(const T* __restrict__ V, cons
   if (gate && *gate == 0) return;          // the estimator ruled this evaluation out
   extern __shared__ __align__(16) unsigned char sm_re[];
   T* U1s = (T*)sm_re;
+  T* w1s = U1s + (size_t)N1 * r1;
   __shared__ double sh[32];
   __shared__ bool last;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
   const T* Usrc = U1;
+  const T* wsrc = w1;
   if (stage_u1) {
-    for (int e = tid; e < N1 * r1; e += blockDim.x) U1s[e] = U1[e];
+    // every load of the staging issued before the first store (eight per thread in flight)
+    bool vec = false;
+    if constexpr (sizeof(T) == 4) vec = (N1 & 3) == 0;
+    if (vec) {
+      const float4* su = reinterpret_cast<const float4*>(U1);
+      float4* du = reinterpret_cast<float4*>(U1s);
+      const int nu4 = N1 * r1 / 4, nw4 = N1 / 4;
+#pragma unroll 8
+      for (int e = tid; e < nu4; e += blockDim.x) du[e] = __ldg(&su[e]);
+#pragma unroll 4
+      for (int e = tid; e < nw4; e += blockDim.x)
+        reinterpret_cast<float4*>(w1s)[e] = __ldg(&reinterpret_cast<const float4*>(w1)[e]);
+    } else {
+#pragma unroll 8
+      for (int e = tid; e < N1 * r1; e += blockDim.x) U1s[e] = U1[e];
+#pragma unroll 4
+      for (int e = tid; e < N1; e += blockDim.x) w1s[e] = w1[e];
+    }
     __syncthreads();
     Usrc = U1s;
+    wsrc = w1s;
   }
   double acc = 0.0;
   bool bad = false;
-  for (unsigned c = blockIdx.x * nw + warp; c < ncol; c += gridDim.x * nw) {
-    const T hl = lane < r1 ? H[lane + (size_t)r1 * c] : T(0);
-    T h[32];
+  const unsigned gw = blockIdx.x * nw + warp, tw = gridDim.x * nw;
+  bool done = false;
+  if constexpr (sizeof(T) == 4) {
+    if (stage_u1 && (N1 & 3) == 0) {
+      const int n4 = N1 >> 2;
+      const float4* U4 = reinterpret_cast<const float4*>(Usrc);
+      const float4* w4 = reinterpret_cast<const float4*>(wsrc);
+      const float4* V4 = reinterpret_cast<const float4*>(V);
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (unsigned c0 = gw; c0 < ncol; c0 += 2 * tw) {
+        const unsigned c1 = c0 + tw;
+        const bool has1 = c1 < ncol;
+        const float hl0 = lane < r1 ? H[lane + (size_t)r1 * c0] : 0.f;
+        const float hl1 = (has1 && lane < r1) ? H[lane + (size_t)r1 * c1] : 0.f;
+        float s0 = 0.f, s1 = 0.f;
+        for (int g0 = 0; g0 < n4; g0 += 128) {
+          float4 v0[4], v1[4], q0[4], q1[4];
 #pragma unroll
-    for (int a = 0; a < 32; ++a) h[a] = __shfl_sync(0xffffffffu, hl, a);
-    const T* vc = V + (size_t)N1 * c;
-    T s = T(0);
-    for (int i = lane; i < N1; i += 32) {
-      T rec = T(0);
+          for (int t = 0; t < 4; ++t) {
+            const int g = g0 + lane + 32 * t;
+            v0[t] = g < n4 ? V4[(size_t)n4 * c0 + g] : z4;
+            v1[t] = (has1 && g < n4) ? V4[(size_t)n4 * c1 + g] : z4;
+            q0[t] = z4;
+            q1[t] = z4;
+          }
+          for (int a = 0; a < r1; ++a) {
+            const float h0 = __shfl_sync(0xffffffffu, hl0, a), h1 = __shfl_sync(0xffffffffu, hl1, a);
 #pragma unroll
-      for (int a = 0; a < 32; ++a)
-        if (a < r1) rec += Usrc[i + N1 * a] * h[a];
-      const T d = vc[i] - rec;
-      bad |= !isfinite(d);
-      s += w1[i] * d * d;
+            for (int t = 0; t < 4; ++t) {
+              const int g = g0 + lane + 32 * t;
+              if (g < n4) {
+                const float4 u = U4[(size_t)n4 * a + g];
+                q0[t].x = fmaf(u.x, h0, q0[t].x); q0[t].y = fmaf(u.y, h0, q0[t].y);
+                q0[t].z = fmaf(u.z, h0, q0[t].z); q0[t].w = fmaf(u.w, h0, q0[t].w);
+                q1[t].x = fmaf(u.x, h1, q1[t].x); q1[t].y = fmaf(u.y, h1, q1[t].y);
+                q1[t].z = fmaf(u.z, h1, q1[t].z); q1[t].w = fmaf(u.w, h1, q1[t].w);
+              }
+            }
+          }
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            const int g = g0 + lane + 32 * t;
+            if (g < n4) {
+              const float4 w = w4[g];
+              const float d0[4] = {v0[t].x - q0[t].x, v0[t].y - q0[t].y, v0[t].z - q0[t].z, v0[t].w - q0[t].w};
+              const float d1[4] = {v1[t].x - q1[t].x, v1[t].y - q1[t].y, v1[t].z - q1[t].z, v1[t].w - q1[t].w};
+              const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+              for (int u = 0; u < 4; ++u) {
+                bad |= !isfinite(d0[u]) || !isfinite(d1[u]);
+                s0 += wv[u] * d0[u] * d0[u];
+                s1 += wv[u] * d1[u] * d1[u];
+              }
+            }
+          }
+        }
+        acc += (double)(wcol[c0] * s0);
+        if (has1) acc += (double)(wcol[c1] * s1);
+      }
+      done = true;
     }
-    acc += (double)(wcol[c] * s);
+  }
+  if (!done) {
+    for (unsigned c = gw; c < ncol; c += tw) {
+      const T hl = lane < r1 ? H[lane + (size_t)r1 * c] : T(0);
+      T h[32];
+#pragma unroll
+      for (int a = 0; a < 32; ++a) h[a] = __shfl_sync(0xffffffffu, hl, a);
+      const T* vc = V + (size_t)N1 * c;
+      T s = T(0);
+      for (int i = lane; i < N1; i += 32) {
+        T rec = T(0);
+#pragma unroll
+        for (int a = 0; a < 32; ++a)
+          if (a < r1) rec += Usrc[i + N1 * a] * h[a];
+        const T d = vc[i] - rec;
+        bad |= !isfinite(d);
+        s += wsrc[i] * d * d;
+      }
+      acc += (double)(wcol[c] * s);
+    }
   }
   acc = block_sum(acc, sh);
   if (bad && flags) atomicOr(flags, kFlagNonFinite);
@@ -212,15 +299,17 @@ template <typename T>
 void launch_recon_err(const T* V, const T* U1, const T* H, int r1, int N1, int64_t ncol, const T* w1, const T* wcol,
                       double* partial, unsigned* counter, int nblocks, double* out, unsigned* flags, cudaStream_t s,
                       const int* gate) {
-  const size_t u1_bytes = (size_t)N1 * r1 * sizeof(T);
-  const int stage = u1_bytes <= 96 * 1024 ? 1 : 0;
+  const size_t st_bytes = (size_t)N1 * (r1 + 1) * sizeof(T);
+  const int stage = st_bytes <= 96 * 1024 ? 1 : 0;
   static bool attr[2] = {false, false};
   if (stage && !attr[sizeof(T) == 8]) {
     cudaFuncSetAttribute(k_recon_err<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 96 * 1024);
     attr[sizeof(T) == 8] = true;
   }
-  const int blocks = (int)std::min<int64_t>(nblocks, (ncol + 7) / 8);
-  k_recon_err<T><<<blocks, 256, stage ? u1_bytes : 0, s>>>(V, U1, H, r1, N1, (unsigned)ncol, w1, wcol, stage,
+  // float4 path: two columns per warp and iteration
+  const int per_block = (sizeof(T) == 4 && stage && N1 % 4 == 0) ? 16 : 8;
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(nblocks, (ncol + per_block - 1) / per_block));
+  k_recon_err<T><<<blocks, 256, stage ? st_bytes : 0, s>>>(V, U1, H, r1, N1, (unsigned)ncol, w1, wcol, stage,
                                                            partial, counter, out, flags, gate);
   count_launch();
 }

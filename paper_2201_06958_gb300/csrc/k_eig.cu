@@ -206,96 +206,171 @@ __global__ void k_syrk_finish(int64_t Nn, int ntile, int ksplit, const double* _
 }
 
 // ---------------------------------------------------------------------------
-// Eigensolver.  CTA 0 does the m x m work; CTAs 1.. own row blocks of 16 rows.
-// Iteration: Z <- C Q with Q = Z X and X^T (Z^T Z) X = I; the m x m factor X of
-// the next Gram is computed on CTA 0 while the other CTAs form W = C Z, so an
-// iteration takes two grid barriers.  X comes from Gaussian elimination of the
+// Eigensolver.  Every CTA owns row blocks of 16 rows (CTA b: blocks b, b + nb, ...).
+// Iteration: Z <- C Q with Q = Z X and X^T (Z^T Z) X = I.  Each CTA sums the
+// per-CTA partial Grams of Z itself and factors the m x m Gram (one or two warps)
+// while its other warps form W = C Z for its rows; then Z' = W X and the partial
+// Gram of Z' for its rows.  Z and the partials are double-buffered, so an
+// iteration takes one grid barrier.  X comes from Gaussian elimination of the
 // diagonally scaled Gram without pivoting: [G^ | I] -> [U | E], G^ = E^{-1} D_u E^{-T},
-// X = D^{-1} E^T D_u^{-1/2} (shifted diagonal retried if a pivot fails).
+// X = D^{-1} E^T D_u^{-1/2} (shifted diagonal retried if a pivot fails).  Every CTA
+// runs the same instructions on the same data, so all hold the same X.
 // ---------------------------------------------------------------------------
 struct EigArgs {
-  const float* C;        // n x n (ld n)
+  const float* C;        // n x n (ld n), symmetric
   const double* C64;     // n x n, for the trace
   int n, m, k, iters;
-  float* Z;              // n x m, row-major (ld m)
-  float* W;              // n x m, row-major (ld m); at the end the Ritz vectors, ld k
-  float* Gp;             // gridDim.x x m x m partial Grams
-  float* Xg;             // m x m
+  float* Z[2];           // n x m, row-major (ld ldz, the padding columns zero), ping-pong
+  float* W;              // the Ritz vectors at the end, n x k row-major
+  int ldz;               // m rounded up to a multiple of 4 (16-byte rows)
+  float* Gp[2];          // nb x gstride partial Grams (m x m, column-major), ping-pong
+  int gstride;           // m * m rounded up to a multiple of 4
+  float* Xg;             // m x k: X S of the Rayleigh-Ritz step
   double* ev;            // k eigenvalues, descending
   double* Qout;          // n x k eigenvectors
   double* trace;
   unsigned* bar;
   unsigned* flags;
+  int fw;                // warps that factor the Gram (the others form C Z)
+  int c_resident;        // one row block per CTA and all of Z staged at once: C rows loaded once
 };
 
-// CTA 0: X from the summed partial Grams (upper triangles of the row-block CTAs).
-__device__ void eig_factor(const EigArgs& a, float* Gs, float* Es, float* dsc, int* fail) {
-  const int m = a.m, tid = threadIdx.x;
-  const int nb = gridDim.x;
-  for (int e = tid; e < m * m; e += blockDim.x) {
-    const int i = e % m, j = e / m;
-    const int aa = i <= j ? i : j, bb = i <= j ? j : i;
-    float s = 0.f;
-    for (int c = 1; c < nb; ++c) s += __ldcg(&a.Gp[(int64_t)c * m * m + aa + m * bb]);
-    Gs[i + LDM * j] = s;
-  }
-  __syncthreads();
-  for (int i = tid; i < m; i += blockDim.x) {
-    const float g = Gs[i + LDM * i];
-    dsc[i] = g > 0.f ? rsqrtf(g) : 1.f;
-  }
-  __syncthreads();
-  float* A = Gs + MMAX * LDM;            // working copy, m x m
-  for (int attempt = 0; attempt < 3; ++attempt) {
-    const float shift = attempt == 0 ? 0.f : (attempt == 1 ? 1e-5f : 1e-2f);
-    if (tid == 0) *fail = 0;
-    for (int e = tid; e < m * m; e += blockDim.x) {
-      const int i = e % m, j = e / m;
-      A[i + LDM * j] = Gs[i + LDM * j] * dsc[i] * dsc[j] + (i == j ? shift : 0.f);
-      Es[i + LDM * j] = (i == j) ? 1.f : 0.f;
-    }
-    __syncthreads();
-    for (int k = 0; k < m; ++k) {
-      const float piv = A[k + LDM * k];
-      if (!(piv > 1e-30f)) {
-        if (tid == 0) *fail = 1;
-      } else {
-        const float ip = 1.f / piv;
-        // rows below k: row_i -= (a_ik / a_kk) row_k on U (columns > k) and E (columns <= k)
-        const int rows = m - 1 - k;
-        for (int e = tid; e < rows * m; e += blockDim.x) {
-          const int i = k + 1 + e % rows, c = e / rows;
-          const float f = A[i + LDM * k] * ip;
-          if (c > k) A[i + LDM * c] = fmaf(-f, A[k + LDM * c], A[i + LDM * c]);
-          else Es[i + LDM * c] = fmaf(-f, Es[k + LDM * c], Es[i + LDM * c]);
-        }
+__device__ __forceinline__ void named_bar(int id, int nthr) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthr) : "memory");
+}
+
+// out[e] = sum over CTAs c = 0 .. nb-1 of Gp[c * gstride + e] for the m x m entries,
+// stored to Gs[i + LDM j]; float4 loads, eight partials in flight, fixed order.
+__device__ void sum_gram(const float* __restrict__ Gp, int nb, int gstride, int m, float* Gs) {
+  const int q4 = gstride / 4;
+  const float4* p = reinterpret_cast<const float4*>(Gp);
+  for (int q = threadIdx.x; q < q4; q += blockDim.x) {
+    float4 acc[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int c = 0;
+    for (; c + 7 < nb; c += 8) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const float4 v = __ldcg(&p[(int64_t)(c + u) * q4 + q]);
+        acc[u].x += v.x; acc[u].y += v.y; acc[u].z += v.z; acc[u].w += v.w;
       }
-      __syncthreads();
     }
-    if (*fail == 0) break;
-    if (attempt == 2 && tid == 0) atomicOr(a.flags, kFlagEigNoConv);
-    __syncthreads();
-  }
-  // X[i][j] = dsc[i] * E[j][i] / sqrt(u_jj)  (upper triangular)
-  for (int e = tid; e < m * m; e += blockDim.x) {
-    const int i = e % m, j = e / m;
-    const float u = A[j + LDM * j];
-    a.Xg[i + m * j] = (j >= i) ? dsc[i] * Es[j + LDM * i] * (u > 0.f ? rsqrtf(u) : 0.f) : 0.f;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (c + u < nb) {
+        const float4 v = __ldcg(&p[(int64_t)(c + u) * q4 + q]);
+        acc[u].x += v.x; acc[u].y += v.y; acc[u].z += v.z; acc[u].w += v.w;
+      }
+#pragma unroll
+    for (int u = 1; u < 8; u += 2) {
+      acc[u - 1].x += acc[u].x; acc[u - 1].y += acc[u].y; acc[u - 1].z += acc[u].z; acc[u - 1].w += acc[u].w;
+    }
+    const float r[4] = {(acc[0].x + acc[2].x) + (acc[4].x + acc[6].x), (acc[0].y + acc[2].y) + (acc[4].y + acc[6].y),
+                        (acc[0].z + acc[2].z) + (acc[4].z + acc[6].z), (acc[0].w + acc[2].w) + (acc[4].w + acc[6].w)};
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = 4 * q + u;
+      if (e < m * m) Gs[(e % m) + LDM * (e / m)] = r[u];
+    }
   }
 }
 
-// Rows [r0, r0 + RB): out = C[rows, :] Zin (n x m).  The whole Zin is staged in
-// shared memory (chunks of ZCH rows), C rows in [RB][ZCH + 1].  Thread layout: row
-// pair rp (8), column quad cq (mq), l-split ls; partial sums reduced in shared memory.
-__device__ void eig_rows_cz(const EigArgs& a, const float* __restrict__ Zin, int r0, float* out, float* sm, int ZCH) {
-  const int n = a.n, m = a.m, tid = threadIdx.x;
+// X (upper triangular, Xs[i + LDM j]) from the Gram Gs on the FW = 4 warps [0, 128):
+// lane l owns rows l and l + 32, warp w the columns c = w + 4 j (j < 16).  A step
+// loads the pivot row's and then the own row's entries into registers (no stores in
+// between) before it updates them.  A pivot that is not positive restarts the
+// elimination with a shifted diagonal (1e-5, then 1e-2: the columns of the block
+// beyond the float resolution of the spectrum are nearly dependent); on the last
+// attempt such a column is skipped and its column of X is zero.  Every thread reads
+// the same pivots after a barrier, so the decisions are uniform.
+constexpr int FW = 4;
+__device__ void eig_factor(int m, const float* Gs, float* A, float* E, float* Xs, float* dsc, unsigned* flags) {
+  constexpr int nthr = FW * 32, CPT = MMAX / FW;
+  const int t = threadIdx.x, lane = t & 31, w = t >> 5;
+  for (int i = t; i < m; i += nthr) {
+    const float g = Gs[i + LDM * i];
+    dsc[i] = g > 0.f ? rsqrtf(g) : 1.f;
+  }
+  bool ok = false;
+  for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
+    const float shift = attempt == 0 ? 0.f : (attempt == 1 ? 1e-5f : 1e-2f);
+    named_bar(2, nthr);
+    for (int i = lane; i < m; i += 32)
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        const int c = w + FW * j;
+        if (c < m) {
+          A[i + LDM * c] = Gs[i + LDM * c] * dsc[i] * dsc[c] + (i == c ? shift : 0.f);
+          E[i + LDM * c] = (i == c) ? 1.f : 0.f;
+        }
+      }
+    named_bar(2, nthr);
+    ok = true;
+    for (int k = 0; k < m; ++k) {
+      const float piv = A[k + LDM * k];
+      if (!(piv > 1e-30f)) {
+        ok = false;
+        if (attempt < 2) break;
+        continue;
+      }
+      const float ip = 1.f / piv;
+      // the pivot row: A (columns > k) and E (columns <= k)
+      float prow[CPT];
+#pragma unroll
+      for (int j = 0; j < CPT; ++j) {
+        const int c = w + FW * j;
+        prow[j] = c < m ? (c > k ? A[k + LDM * c] : E[k + LDM * c]) : 0.f;
+      }
+      // rows below k: row_i -= (a_ik / a_kk) row_k
+      for (int i = k + 1 + lane; i < m; i += 32) {
+        const float f = A[i + LDM * k] * ip;
+        float rv[CPT];
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+          const int c = w + FW * j;
+          rv[j] = c < m ? (c > k ? A[i + LDM * c] : E[i + LDM * c]) : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+          const int c = w + FW * j;
+          if (c < m) {
+            const float v = fmaf(-f, prow[j], rv[j]);
+            if (c > k) A[i + LDM * c] = v;
+            else E[i + LDM * c] = v;
+          }
+        }
+      }
+      named_bar(2, nthr);
+    }
+  }
+  if (!ok && t == 0) atomicOr(flags, kFlagEigNoConv);
+  // X[i][j] = dsc[i] * E[j][i] / sqrt(u_jj)  (upper triangular; zero for a skipped pivot)
+  for (int i = lane; i < m; i += 32)
+#pragma unroll
+    for (int jj = 0; jj < CPT; ++jj) {
+      const int j = w + FW * jj;
+      if (j < m) {
+        const float u = A[j + LDM * j];
+        Xs[i + LDM * j] = (j >= i) ? dsc[i] * E[j + LDM * i] * (u > 0.f ? rsqrtf(u) : 0.f) : 0.f;
+      }
+    }
+}
+
+// Rows [r0, r0 + RB): Wr = C[rows, :] Zin (RB x m, ld LDM) on threads [t0, t0 + ng).
+// Zin is staged in shared memory (chunks of ZCH rows), C rows in [RB][ZCH + 1]
+// (kept across calls when load_c is false).  Thread layout: row pair rp (8), column
+// quad cq (mq), l-split ls; partial sums reduced in shared memory.
+__device__ void eig_rows_cz(const EigArgs& a, const float* __restrict__ Zin, int r0, float* Wr, float* sm, int ZCH,
+                            int t0, int ng, bool load_c) {
+  const int n = a.n, m = a.m, lt = threadIdx.x - t0;
   const int mq = (m + 3) / 4, mp = mq * 4;
   float* Zs = sm;                         // ZCH x mp
   float* Cs = Zs + ZCH * mp;              // RB x (ZCH + 1)
   float* Rs = Cs + RB * (ZCH + 1);        // reduction: nls x RB x mp
   const int nthr_rc = 8 * mq;
-  const int nls = EIG_THREADS / nthr_rc;
-  const int rp = tid % 8, cq = (tid / 8) % mq, ls = tid / nthr_rc;
+  const int nls = ng / nthr_rc;
+  const int rp = lt % 8, cq = (lt / 8) % mq, ls = lt / nthr_rc;
   float acc[2][4];
 #pragma unroll
   for (int x = 0; x < 2; ++x)
@@ -303,19 +378,40 @@ __device__ void eig_rows_cz(const EigArgs& a, const float* __restrict__ Zin, int
     for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
   for (int l0 = 0; l0 < n; l0 += ZCH) {
     const int lc = min(ZCH, n - l0);
-    __syncthreads();
-    for (int e = tid; e < lc * mp; e += blockDim.x) {
-      const int l = e / mp, c = e % mp;
-      Zs[e] = (c < m) ? __ldcg(&Zin[(int64_t)(l0 + l) * m + c]) : 0.f;
+    if (l0 > 0) named_bar(1, ng);
+    {
+      // Z rows l0 .. l0+lc-1 are one contiguous block of lc * ldz floats (ldz == mp)
+      const float4* src = (const float4*)(Zin + (int64_t)l0 * a.ldz);
+      float4* dst = (float4*)Zs;
+      const int nf4 = lc * mp / 4;
+#pragma unroll 4
+      for (int e = lt; e < nf4; e += ng) dst[e] = __ldcg(&src[e]);
     }
-    for (int e = tid; e < RB * lc; e += blockDim.x) {
-      const int rr = e / lc, l = e % lc;
-      const int row = r0 + rr;
-      Cs[rr * (ZCH + 1) + l] = (row < n) ? a.C[(l0 + l) + (int64_t)n * row] : 0.f;   // C symmetric: row = column
+    if (load_c || ZCH < n) {
+      if ((n & 3) == 0) {            // rows of C (= columns, C symmetric) as float4 runs
+        const int q4 = lc / 4;
+#pragma unroll 4
+        for (int e = lt; e < RB * q4; e += ng) {
+          const int rr = e / q4, l4 = e % q4;
+          const int row = r0 + rr;
+          float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (row < n) v = __ldcg((const float4*)(a.C + (int64_t)row * n + l0) + l4);
+          float* d = Cs + rr * (ZCH + 1) + 4 * l4;
+          d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+        }
+      } else {
+#pragma unroll 4
+        for (int e = lt; e < RB * lc; e += ng) {
+          const int rr = e / lc, l = e % lc;
+          const int row = r0 + rr;
+          Cs[rr * (ZCH + 1) + l] = (row < n) ? __ldcg(&a.C[(int64_t)row * n + l0 + l]) : 0.f;
+        }
+      }
     }
-    __syncthreads();
+    named_bar(1, ng);
     if (ls < nls) {
       const int lb = lc * ls / nls, le = lc * (ls + 1) / nls;
+#pragma unroll 4
       for (int l = lb; l < le; ++l) {
         const float c0 = Cs[(2 * rp) * (ZCH + 1) + l], c1 = Cs[(2 * rp + 1) * (ZCH + 1) + l];
         const float4 z = *reinterpret_cast<const float4*>(&Zs[l * mp + cq * 4]);
@@ -326,156 +422,131 @@ __device__ void eig_rows_cz(const EigArgs& a, const float* __restrict__ Zin, int
       }
     }
   }
-  __syncthreads();
   if (ls < nls)
 #pragma unroll
     for (int x = 0; x < 2; ++x)
 #pragma unroll
       for (int y = 0; y < 4; ++y) Rs[(ls * RB + 2 * rp + x) * mp + cq * 4 + y] = acc[x][y];
-  __syncthreads();
-  for (int e = tid; e < RB * m; e += blockDim.x) {
+  named_bar(1, ng);
+  for (int e = lt; e < RB * m; e += ng) {
     const int rr = e % RB, c = e / RB;
     float s = 0.f;
     for (int q = 0; q < nls; ++q) s += Rs[(q * RB + rr) * mp + c];
-    if (r0 + rr < n) out[(int64_t)(r0 + rr) * m + c] = s;
+    Wr[rr * LDM + c] = s;
   }
 }
 
-// Rows [r0, r0 + RB): Z = W X (X upper) and this block's partial of Z^T Z (upper).
-__device__ void eig_rows_apply(const EigArgs& a, int r0, float* Gpart, float* sm, bool accumulate) {
-  const int n = a.n, m = a.m, tid = threadIdx.x;
-  float* Xs = sm;                         // m x m (ld LDM)
-  float* Ws = Xs + MMAX * LDM;            // RB x m (ld LDM)
-  float* Zs = Ws + RB * LDM;              // RB x m
-  for (int e = tid; e < m * m; e += blockDim.x) Xs[(e % m) + LDM * (e / m)] = __ldcg(&a.Xg[e]);
-  for (int e = tid; e < RB * m; e += blockDim.x) {
-    const int rr = e % RB, c = e / RB;
-    Ws[rr * LDM + c] = (r0 + rr < n) ? __ldcg(&a.W[(int64_t)(r0 + rr) * m + c]) : 0.f;
-  }
-  __syncthreads();
-  for (int e = tid; e < RB * m; e += blockDim.x) {
-    const int rr = e % RB, c = e / RB;
-    float s = 0.f;
-    for (int l = 0; l <= c; ++l) s = fmaf(Ws[rr * LDM + l], Xs[l + LDM * c], s);
-    Zs[rr * LDM + c] = s;
-    if (r0 + rr < n) a.Z[(int64_t)(r0 + rr) * m + c] = s;
-  }
-  __syncthreads();
-  for (int e = tid; e < m * m; e += blockDim.x) {
+// Ga (+)= Ar^T Br over the RB staged rows (m x m, column-major, all entries).
+__device__ void rows_gram(int m, const float* Ar, const float* Br, float* Ga, bool accumulate) {
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     const int i = e % m, j = e / m;
-    if (i > j) continue;
     float s = 0.f;
 #pragma unroll 4
-    for (int rr = 0; rr < RB; ++rr) s = fmaf(Zs[rr * LDM + i], Zs[rr * LDM + j], s);
-    Gpart[e] = accumulate ? Gpart[e] + s : s;
+    for (int rr = 0; rr < RB; ++rr) s = fmaf(Ar[rr * LDM + i], Br[rr * LDM + j], s);
+    Ga[e] = accumulate ? Ga[e] + s : s;
   }
-  __syncthreads();
 }
+
+__device__ void store_gram(int m, int gstride, const float* Ga, bool any, float* dst) {
+  for (int e = threadIdx.x; e < gstride; e += blockDim.x) dst[e] = (any && e < m * m) ? Ga[e] : 0.f;
+}
+
+// Shared-memory layout of the kernel (floats): the m x m work area, then the C Z area.
+constexpr int EIG_WORK_FLOATS = 5 * MMAX * LDM + 2 * RB * LDM;
 
 __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
   extern __shared__ __align__(16) float smf[];
-  __shared__ int abort_sh, fail_sh;
+  __shared__ int abort_sh;
   __shared__ float dsc[MMAX];
   if (threadIdx.x == 0) abort_sh = 0;
   __syncthreads();
   const int n = a.n, m = a.m, tid = threadIdx.x;
   const int nrb = (n + RB - 1) / RB;
-  const int nb = gridDim.x;
+  const int nb = gridDim.x, b = blockIdx.x;
+  float* Gs = smf;                        // summed Gram (Rayleigh-Ritz: M)
+  float* As = Gs + MMAX * LDM;            // elimination work (H)
+  float* Es = As + MMAX * LDM;            // elimination E (Jacobi vectors)
+  float* Xs = Es + MMAX * LDM;            // X, kept to the Rayleigh-Ritz step
+  float* Ga = Xs + MMAX * LDM;            // this CTA's partial Gram (small scratch)
+  float* Wr = Ga + MMAX * LDM;            // RB x m rows of C Z
+  float* Zr = Wr + RB * LDM;              // RB x m rows of Z
+  float* czs = smf + EIG_WORK_FLOATS;     // C Z staging
+  const int t0 = 32 * a.fw, ng = EIG_THREADS - t0;
   unsigned nbar = 0;
-  float* myG = a.Gp + (int64_t)blockIdx.x * m * m;
-  // start: Z = hash columns, partial Grams
-  if (blockIdx.x > 0) {
-    bool first = true;
-    for (int rb = blockIdx.x - 1; rb < nrb; rb += nb - 1) {
-      const int r0 = rb * RB;
-      float* Zs = smf;
-      for (int e = tid; e < RB * m; e += blockDim.x) {
-        const int rr = e % RB, c = e / RB;
-        const float v = (r0 + rr < n) ? hash_unit((uint32_t)(r0 + rr), (uint32_t)c) : 0.f;
-        Zs[rr * LDM + c] = v;
-        if (r0 + rr < n) a.Z[(int64_t)(r0 + rr) * m + c] = v;
-      }
-      __syncthreads();
-      for (int e = tid; e < m * m; e += blockDim.x) {
-        const int i = e % m, j = e / m;
-        if (i > j) continue;
-        float s = 0.f;
-        for (int rr = 0; rr < RB; ++rr) s = fmaf(Zs[rr * LDM + i], Zs[rr * LDM + j], s);
-        myG[e] = first ? s : myG[e] + s;
-      }
-      __syncthreads();
-      first = false;
+  // start: Z = hash columns (a function of the indices only, so the result depends on
+  // C alone), partial Grams into Gp[0]
+  bool any = false;
+  for (int rb = b; rb < nrb; rb += nb) {
+    const int r0 = rb * RB;
+    for (int e = tid; e < RB * a.ldz; e += blockDim.x) {
+      const int rr = e % RB, c = e / RB;
+      const int row = r0 + rr;
+      const float v = (row < n && c < m) ? hash_unit((uint32_t)row, (uint32_t)c) : 0.f;
+      if (c < m) Zr[rr * LDM + c] = v;
+      if (row < n) a.Z[0][(int64_t)row * a.ldz + c] = v;
     }
-    if (first)
-      for (int e = tid; e < m * m; e += blockDim.x) myG[e] = 0.f;
+    __syncthreads();
+    rows_gram(m, Zr, Zr, Ga, any);
+    __syncthreads();
+    any = true;
   }
+  store_gram(m, a.gstride, Ga, any, a.Gp[0] + (int64_t)b * a.gstride);
   if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
   for (int it = 0; it <= a.iters; ++it) {
-    // phase 1: CTA 0 factors the Gram of Z; the others form W = C Z
-    if (blockIdx.x == 0) {
-      eig_factor(a, smf, smf + 2 * MMAX * LDM, dsc, &fail_sh);
-    } else {
-      for (int rb = blockIdx.x - 1; rb < nrb; rb += nb - 1) eig_rows_cz(a, a.Z, rb * RB, a.W, smf, ZCH);
-    }
-    if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
-    if (it == a.iters) break;
-    // phase 2: Z = W X (= C Q) and its partial Grams
-    if (blockIdx.x > 0) {
-      bool first = true;
-      for (int rb = blockIdx.x - 1; rb < nrb; rb += nb - 1) {
-        eig_rows_apply(a, rb * RB, myG, smf, !first);
-        first = false;
-      }
-      if (first)
-        for (int e = tid; e < m * m; e += blockDim.x) myG[e] = 0.f;
-    }
-    if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
-  }
-  // Rayleigh-Ritz.  Now Z = C Q_prev, W = C Z, X orthonormalises Z: Q = Z X,
-  // H = Q^T C Q = X^T (Z^T W) X.  Partial M = Z^T W per CTA.
-  if (blockIdx.x > 0) {
-    float* Zs = smf;
-    float* Ws = Zs + RB * LDM;
-    bool first = true;
-    for (int rb = blockIdx.x - 1; rb < nrb; rb += nb - 1) {
+    const int cur = it & 1;
+    const float* Zc = a.Z[cur];
+    sum_gram(a.Gp[cur], nb, a.gstride, m, Gs);
+    __syncthreads();
+    any = false;
+    for (int rb = b; rb < nrb; rb += nb) {
       const int r0 = rb * RB;
-      for (int e = tid; e < RB * m; e += blockDim.x) {
-        const int rr = e % RB, c = e / RB;
-        const bool in = r0 + rr < n;
-        Zs[rr * LDM + c] = in ? __ldcg(&a.Z[(int64_t)(r0 + rr) * m + c]) : 0.f;
-        Ws[rr * LDM + c] = in ? __ldcg(&a.W[(int64_t)(r0 + rr) * m + c]) : 0.f;
+      if (tid < t0) {
+        if (!any) eig_factor(m, Gs, As, Es, Xs, dsc, a.flags);
+      } else {
+        eig_rows_cz(a, Zc, r0, Wr, czs, ZCH, t0, ng, !(a.c_resident && it > 0));
       }
       __syncthreads();
-      for (int e = tid; e < m * m; e += blockDim.x) {
-        const int i = e % m, j = e / m;
-        float s = 0.f;
-        for (int rr = 0; rr < RB; ++rr) s = fmaf(Zs[rr * LDM + i], Ws[rr * LDM + j], s);
-        myG[e] = first ? s : myG[e] + s;
+      if (it < a.iters) {
+        // Z' = W X for these rows (X upper), and their partial Gram
+        float* Zn = a.Z[cur ^ 1];
+        for (int e = tid; e < RB * a.ldz; e += blockDim.x) {
+          const int rr = e % RB, c = e / RB;
+          float s = 0.f;
+          if (c < m) {
+            for (int l = 0; l <= c; ++l) s = fmaf(Wr[rr * LDM + l], Xs[l + LDM * c], s);
+            Zr[rr * LDM + c] = s;
+          }
+          if (r0 + rr < n) Zn[(int64_t)(r0 + rr) * a.ldz + c] = s;
+        }
+        __syncthreads();
+        rows_gram(m, Zr, Zr, Ga, any);
+      } else {
+        // Rayleigh-Ritz: partial M = Z^T W = Z^T C Z
+        for (int e = tid; e < RB * m; e += blockDim.x) {
+          const int rr = e % RB, c = e / RB;
+          Zr[rr * LDM + c] = (r0 + rr < n) ? __ldcg(&Zc[(int64_t)(r0 + rr) * a.ldz + c]) : 0.f;
+        }
+        __syncthreads();
+        rows_gram(m, Zr, Wr, Ga, any);
       }
       __syncthreads();
-      first = false;
+      any = true;
     }
-    if (first)
-      for (int e = tid; e < m * m; e += blockDim.x) myG[e] = 0.f;
+    if (!any && tid < t0) eig_factor(m, Gs, As, Es, Xs, dsc, a.flags);   // (no rows: keeps X defined)
+    store_gram(m, a.gstride, Ga, any, a.Gp[cur ^ 1] + (int64_t)b * a.gstride);
+    if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
   }
-  if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
-  // CTA 0: H, Jacobi, ordering; P = X S[:, order] written to W's first m x k block
-  if (blockIdx.x == 0) {
-    float* Ms = smf;                      // m x m
-    float* Xs = Ms + MMAX * LDM;          // m x m
-    float* Hs = Xs + MMAX * LDM;          // m x m
-    float* Vs = Hs + MMAX * LDM;          // m x m
-    float* cs = Vs + MMAX * LDM;          // 2 * MMAX
+  const int fin = a.iters & 1;            // Z[fin] is the final block; Gp[fin ^ 1] holds M
+  // CTA 0: H = X^T M X, Jacobi, ordering; P = X S[:, order] into Xg
+  if (b == 0) {
+    float* Ms = Gs;
+    float* Hs = As;
+    float* Vs = Es;
+    float* cs = Ga;                       // 2 * MMAX
     int* pq = (int*)(cs + 2 * MMAX);      // 2 * MMAX
     int* ord = pq + 2 * MMAX;             // MMAX
     float* red = (float*)(ord + MMAX);    // 64
-    for (int e = tid; e < m * m; e += blockDim.x) {
-      const int i = e % m, j = e / m;
-      float s = 0.f;
-      for (int c = 1; c < nb; ++c) s += __ldcg(&a.Gp[(int64_t)c * m * m + e]);
-      Ms[i + LDM * j] = s;
-      Xs[i + LDM * j] = __ldcg(&a.Xg[e]);
-    }
+    sum_gram(a.Gp[fin ^ 1], nb, a.gstride, m, Ms);
     __syncthreads();
     for (int e = tid; e < m * m; e += blockDim.x) {          // Vs = M X (temporary)
       const int i = e % m, j = e / m;
@@ -575,13 +646,19 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
         __syncthreads();
       }
     }
-    // descending order of the Ritz values (integer ranks of the float keys)
+    // descending order of the Ritz values: ranks of order-preserving integer keys of the
+    // float bits, ties by index, so the ranks are a permutation whatever the values
+    // (a NaN included) and every ord[] entry is written
+    auto fkey = [](float v) {
+      const int b = __float_as_int(v);
+      return b >= 0 ? b : (b ^ 0x7fffffff);
+    };
     for (int j = tid; j < m; j += blockDim.x) {
-      const float vj = Hs[j + LDM * j];
+      const int kj = fkey(Hs[j + LDM * j]);
       int rank = 0;
       for (int l = 0; l < m; ++l) {
-        const float vl = Hs[l + LDM * l];
-        rank += (vl > vj) || (vl == vj && l < j);
+        const int kl = fkey(Hs[l + LDM * l]);
+        rank += (kl > kj) || (kl == kj && l < j);
       }
       ord[rank] = j;
     }
@@ -603,22 +680,23 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
   }
   if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
   // Ritz vectors Y = Z P (n x k) into W; per-CTA column norms^2 and largest |entry|
-  float* colnorm = a.Gp;                                      // [cta][k] norms, [cta][MMAX + k] max |y|, index as float bits
-  if (blockIdx.x > 0) {
-    float* Ps = smf;                      // m x k (ld LDM)
-    float* Zs = Ps + MMAX * LDM;          // RB x m
-    float* Ys = Zs + RB * LDM;            // RB x k
-    float* nrm = Ys + RB * LDM;           // k
+  float* colnorm = a.Gp[fin];                                 // [cta][k] norms, [cta][MMAX + k] max |y|, index as float bits
+  {
+    const float* Zf = a.Z[fin];
+    float* Ps = Gs;                       // m x k (ld LDM)
+    float* Zs = Zr;                       // RB x m
+    float* Ys = Wr;                       // RB x k
+    float* nrm = Ga;                      // k
     float* mx = nrm + MMAX;               // k
     int* ix = (int*)(mx + MMAX);          // k
     for (int j = tid; j < a.k; j += blockDim.x) { nrm[j] = 0.f; mx[j] = -1.f; ix[j] = 0x7fffffff; }
     for (int e = tid; e < m * a.k; e += blockDim.x) Ps[(e % m) + LDM * (e / m)] = __ldcg(&a.Xg[e]);
     __syncthreads();
-    for (int rb = blockIdx.x - 1; rb < nrb; rb += nb - 1) {
+    for (int rb = b; rb < nrb; rb += nb) {
       const int r0 = rb * RB;
       for (int e = tid; e < RB * m; e += blockDim.x) {
         const int rr = e % RB, c = e / RB;
-        Zs[rr * LDM + c] = (r0 + rr < n) ? __ldcg(&a.Z[(int64_t)(r0 + rr) * m + c]) : 0.f;
+        Zs[rr * LDM + c] = (r0 + rr < n) ? __ldcg(&Zf[(int64_t)(r0 + rr) * a.ldz + c]) : 0.f;
       }
       __syncthreads();
       for (int e = tid; e < RB * a.k; e += blockDim.x) {
@@ -640,20 +718,20 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
       __syncthreads();
     }
     for (int j = tid; j < a.k; j += blockDim.x) {
-      colnorm[(int64_t)blockIdx.x * 3 * MMAX + j] = nrm[j];
-      colnorm[(int64_t)blockIdx.x * 3 * MMAX + MMAX + j] = mx[j];
-      colnorm[(int64_t)blockIdx.x * 3 * MMAX + 2 * MMAX + j] = __int_as_float(ix[j]);
+      colnorm[(int64_t)b * 3 * MMAX + j] = nrm[j];
+      colnorm[(int64_t)b * 3 * MMAX + MMAX + j] = mx[j];
+      colnorm[(int64_t)b * 3 * MMAX + 2 * MMAX + j] = __int_as_float(ix[j]);
     }
   }
   if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
   // every CTA: the column scales (1 / norm with the sign making the largest |entry|
   // positive; first index on ties), then its rows of Qout in double
   {
-    float* scale = smf;                   // k
+    float* scale = Ga;                    // k
     for (int j = tid; j < a.k; j += blockDim.x) {
       float nr = 0.f, best = -1.f;
       int bi = 0x7fffffff;
-      for (int c = 1; c < nb; ++c) {
+      for (int c = 0; c < nb; ++c) {
         nr += __ldcg(&colnorm[(int64_t)c * 3 * MMAX + j]);
         const float v = __ldcg(&colnorm[(int64_t)c * 3 * MMAX + MMAX + j]);
         const int ii = __float_as_int(__ldcg(&colnorm[(int64_t)c * 3 * MMAX + 2 * MMAX + j]));
@@ -663,12 +741,11 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
       scale[j] = (ybi < 0.f ? -1.f : 1.f) * (nr > 0.f ? rsqrtf(nr) : 1.f);
     }
     __syncthreads();
-    if (blockIdx.x > 0)
-      for (int rb = blockIdx.x - 1; rb < nrb; rb += nb - 1)
-        for (int e = tid; e < RB * a.k; e += blockDim.x) {
-          const int rr = e % RB, j = e / RB, row = rb * RB + rr;
-          if (row < n) a.Qout[row + (int64_t)n * j] = (double)(__ldcg(&a.W[(int64_t)row * a.k + j]) * scale[j]);
-        }
+    for (int rb = b; rb < nrb; rb += nb)
+      for (int e = tid; e < RB * a.k; e += blockDim.x) {
+        const int rr = e % RB, j = e / RB, row = rb * RB + rr;
+        if (row < n) a.Qout[row + (int64_t)n * j] = (double)(__ldcg(&a.W[(int64_t)row * a.k + j]) * scale[j]);
+      }
   }
 }
 
@@ -708,14 +785,14 @@ void launch_gram_weighted(const float* Vw, int64_t L, int64_t Nn, int64_t Q, dou
 }
 
 size_t eig_si_scratch_floats(int n) {
-  // Z, W: n x MMAX each; partial Grams / norms: 152 x MMAX x MMAX; Xg: MMAX x MMAX
-  return (size_t)2 * n * MMAX + (size_t)152 * MMAX * MMAX + MMAX * MMAX;
+  // Z (two buffers), Ritz vectors: n x MMAX each; partial Grams (two): 152 x MMAX^2; Xg: MMAX^2
+  return (size_t)3 * n * MMAX + (size_t)2 * 152 * MMAX * MMAX + MMAX * MMAX;
 }
 
 tdb_status eig_si_float(const float* Cc, const double* C64, int n, int k, int iters, float* scratch, unsigned* bar,
                         unsigned* flags, double* ev, double* Q, double* trace, cudaStream_t s) {
   const int m = std::min(n, std::min(MMAX, k + 16));
-  if (k > m) return TDB_ERR_INVALID_ARG;
+  if (k > m || iters < 0) return TDB_ERR_INVALID_ARG;
   static int nsm = 0;
   static size_t smem_cap = 0;
   if (nsm == 0) {
@@ -727,23 +804,28 @@ tdb_status eig_si_float(const float* Cc, const double* C64, int n, int k, int it
     if (!coop) { nsm = 0; return TDB_ERR_UNSUPPORTED; }
     smem_cap = (size_t)optin - 2048;
   }
-  const int mp = ((m + 3) / 4) * 4;
-  // rows-times-Z phase: ZCH rows of Z staged, plus C rows and the reduction buffer
-  const int nls = EIG_THREADS / (8 * ((m + 3) / 4));
-  int ZCH = n;
+  const int mq = (m + 3) / 4, mp = mq * 4;
+  const int fw = FW;                                 // factor warps
+  const int nls = (EIG_THREADS - 32 * fw) / (8 * mq);
+  // C Z staging: ZCH rows of Z (a multiple of 16 when chunked, so float4 runs of C
+  // rows stay aligned), C rows and the reduction buffer, after the m x m work area
   auto need = [&](int zch) {
-    return ((size_t)zch * mp + (size_t)RB * (zch + 1) + (size_t)nls * RB * mp) * sizeof(float);
+    return ((size_t)EIG_WORK_FLOATS + (size_t)zch * mp + (size_t)RB * (zch + 1) + (size_t)nls * RB * mp) *
+           sizeof(float);
   };
-  while (ZCH > 64 && need(ZCH) > smem_cap) ZCH = (ZCH + 1) / 2;
-  const size_t small = (size_t)(5 * MMAX * LDM + 6 * MMAX + 64) * sizeof(float);
-  const size_t smem = std::max(need(ZCH), small);
+  int ZCH = n;
+  while (ZCH > 64 && need(ZCH) > smem_cap) ZCH = ((ZCH / 2) + 15) & ~15;
+  const size_t smem = need(ZCH);
   if (smem > smem_cap) return TDB_ERR_UNSUPPORTED;
   cudaFuncSetAttribute(k_eig_si, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int per_sm = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_eig_si, EIG_THREADS, smem);
   if (per_sm < 1) return TDB_ERR_UNSUPPORTED;
   const int nrb = (n + RB - 1) / RB;
-  const int grid = std::min(std::min(nsm, 152), nrb + 1);
+  const int gstride = ((m * m + 3) / 4) * 4;
+  // every CTA sums all partial Grams each iteration: bound their count
+  const int cap = std::max(8, 131072 / gstride);
+  const int grid = std::min(std::min(nsm, 152), std::min(nrb, cap));
   EigArgs a;
   a.C = Cc;
   a.C64 = C64;
@@ -751,15 +833,21 @@ tdb_status eig_si_float(const float* Cc, const double* C64, int n, int k, int it
   a.m = m;
   a.k = k;
   a.iters = iters;
-  a.Z = scratch;
-  a.W = a.Z + (size_t)n * MMAX;
-  a.Gp = a.W + (size_t)n * MMAX;
-  a.Xg = a.Gp + (size_t)152 * MMAX * MMAX;
+  a.Z[0] = scratch;
+  a.Z[1] = a.Z[0] + (size_t)n * MMAX;
+  a.W = a.Z[1] + (size_t)n * MMAX;
+  a.ldz = mp;
+  a.Gp[0] = a.W + (size_t)n * MMAX;
+  a.Gp[1] = a.Gp[0] + (size_t)152 * MMAX * MMAX;
+  a.gstride = gstride;
+  a.Xg = a.Gp[1] + (size_t)152 * MMAX * MMAX;
   a.ev = ev;
   a.Qout = Q;
   a.trace = trace;
   a.bar = bar;
   a.flags = flags;
+  a.fw = fw;
+  a.c_resident = (ZCH >= n && grid == nrb) ? 1 : 0;
   cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
   void* args[] = {(void*)&a, (void*)&ZCH};
   cudaError_t e = cudaLaunchCooperativeKernel((const void*)k_eig_si, grid, EIG_THREADS, args, smem, s);

@@ -22,7 +22,7 @@ __global__ void __launch_bounds__(MLP_H) k_mlp_grad(const float* __restrict__ P,
                                                      float* __restrict__ gpart, float* __restrict__ lpart) {
   constexpr int F = MLP_F, H = MLP_H;
   __shared__ float W2[H][H + 1];
-  __shared__ float h1[H], h2[H], da2[H], xs[F];
+  __shared__ float h1[H], da2[H], xs[F];
   __shared__ float red[2];
   const int j = threadIdx.x;
   const float* W1 = P;
@@ -57,7 +57,6 @@ __global__ void __launch_bounds__(MLP_H) k_mlp_grad(const float* __restrict__ P,
 #pragma unroll 16
     for (int k = 0; k < H; ++k) a2 += W2[j][k] * h1[k];
     const float h2j = tanhf(a2);
-    h2[j] = h2j;
     float part = w3j * h2j;
     part = warp_sum(part);
     if ((j & 31) == 0) red[j >> 5] = part;
@@ -236,42 +235,69 @@ __global__ void __launch_bounds__(256) k_est_features(const EstState* __restrict
                                                       double* __restrict__ ds2_out) {
   // The features are float-valued and ||dS|| is only as accurate as the projection,
   // so everything is float except the difference ||dV||^2 - ||dS||^2 (double: it can
-  // cancel).  The network's parameters are staged in shared memory with coalesced loads.
-  __shared__ float Ps[MLP_NPARAM];
+  // cancel).  One CTA; the launch is latency-bound, so every global load is issued up
+  // front by the thread that uses it: the network's weights go straight to registers
+  // (layer 1: thread j < H owns unit j; layer 2: four threads per unit, 16 inputs each),
+  // warps 1 and 2 reduce the sigma^2 features while all threads sum ||dS||^2.
+  constexpr int F = MLP_F, H = MLP_H;
   __shared__ double sh[32];
-  const EstState st = *stp;     // the host's estimator state of this step (device copy)
-  __shared__ float xs[MLP_F], h1[MLP_H];
-  __shared__ float red[8];
-  const int tid = threadIdx.x;
-  for (int i = tid; i < MLP_NPARAM; i += blockDim.x) Ps[i] = P[i];
+  __shared__ float xs[F], h1[H], red[8], nrm_s[2 * F + 2];
+  __shared__ float tot_sh, smin_sh;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const float* W1 = P;
+  const float* b1 = W1 + H * F;
+  const float* W2 = b1 + H;
+  const float* b2 = W2 + H * H;
+  const float* w3 = b2 + H;
+  const int j = tid >> 2, q = tid & 3;
+  float w1r[F], w2r[H / 4];
+  float b1v = 0.f;
+  if (tid < H) {
+#pragma unroll
+    for (int f = 0; f < F; ++f) w1r[f] = W1[tid * F + f];
+    b1v = b1[tid];
+  }
+#pragma unroll
+  for (int k = 0; k < H / 4; ++k) w2r[k] = W2[j * H + q * (H / 4) + k];
+  const float b2v = b2[j], w3v = w3[j];
+  const float tiny = 1e-30f;
+  const int rr[4] = {ranks.x, ranks.y, ranks.z, ranks.w};
+  if (wid == 1) {                       // sum of the mode-1 sigma^2 (kept part)
+    float v = lane < rr[0] ? fmaxf((float)sig2[lane], 0.f) : 0.f;
+    v = warp_sum(v);
+    if (lane == 0) tot_sh = v;
+  } else if (wid == 2) {                // smallest sigma_min / sigma_max over the modes
+    float v = 1.f;
+    if (lane < p) {
+      const double* sg = sig2 + lane * kMaxRank;
+      const float mx = fmaxf((float)sg[0], tiny), mn = fmaxf((float)sg[rr[lane] - 1], tiny);
+      v = sqrtf(mn / mx);
+    }
+    for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) smin_sh = v;
+  } else if (wid == 3 && lane < 2 * F + 2) {
+    nrm_s[lane] = norm[lane];
+  }
   float sf = 0.f;
   for (int i = tid; i < nds; i += blockDim.x) sf = fmaf(dS[i], dS[i], sf);
-  const double s = block_sum((double)sf, sh);
+  const double s = block_sum((double)sf, sh);     // (its barriers also publish the values above)
+  const EstState st = *stp;     // the host's estimator state of this step (device copy)
   if (tid == 0) {
     const double d2 = *dv2;
     const float res2 = (float)fmax(d2 - s, 0.0);
-    const float tiny = 1e-30f;
-    float smin = 1.f, tot = 0.f;
-    const int rr[4] = {ranks.x, ranks.y, ranks.z, ranks.w};
-    for (int n = 0; n < p; ++n) {
-      const double* sg = sig2 + n * kMaxRank;
-      const float mx = fmaxf((float)sg[0], tiny), mn = fmaxf((float)sg[rr[n] - 1], tiny);
-      smin = fminf(smin, sqrtf(mn / mx));
-      if (n == 0)
-        for (int i = 0; i < rr[0]; ++i) tot += fmaxf((float)sg[i], 0.f);
-    }
-    float f[MLP_F];
+    float f[F];
     f[0] = (float)st.last_log_eps;
     f[1] = log10f(sqrtf((float)d2) + tiny);
     f[2] = log10f(sqrtf(res2) + tiny);
     f[3] = log10f(sqrtf((float)s) + tiny);
-    f[4] = log10f(smin + tiny);
-    f[5] = log10f(sqrtf(tot) + tiny);
+    f[4] = log10f(smin_sh + tiny);
+    f[5] = log10f(sqrtf(tot_sh) + tiny);
     f[6] = log10f((float)st.steps_since_reinit + 1.f);
     f[7] = (float)st.prev_res_log;
-    for (int i = 0; i < MLP_F; ++i) {
+#pragma unroll
+    for (int i = 0; i < F; ++i) {
       feat[i] = f[i];
-      xs[i] = st.ready ? (f[i] - norm[i]) / norm[MLP_F + i] : 0.f;
+      xs[i] = st.ready ? (f[i] - nrm_s[i]) / nrm_s[F + i] : 0.f;
     }
     *ds2_out = s;
   }
@@ -281,37 +307,30 @@ __global__ void __launch_bounds__(256) k_est_features(const EstState* __restrict
     return;
   }
   // forward pass of one sample
-  const float* W1 = Ps;
-  const float* b1 = W1 + MLP_H * MLP_F;
-  const float* W2 = b1 + MLP_H;
-  const float* b2 = W2 + MLP_H * MLP_H;
-  const float* w3 = b2 + MLP_H;
-  if (tid < MLP_H) {
-    float a = b1[tid];
+  if (tid < H) {
+    float a = b1v;
 #pragma unroll
-    for (int f = 0; f < MLP_F; ++f) a = fmaf(W1[tid * MLP_F + f], xs[f], a);
+    for (int f = 0; f < F; ++f) a = fmaf(w1r[f], xs[f], a);
     h1[tid] = tanhf(a);
   }
   __syncthreads();
-  // hidden layer 2: four threads per unit, 16 inputs each, reduced by shuffles
-  const int j = tid >> 2, q = tid & 3;
   float a2 = 0.f;
 #pragma unroll
-  for (int k = 0; k < MLP_H / 4; ++k) a2 = fmaf(W2[j * MLP_H + q * (MLP_H / 4) + k], h1[q * (MLP_H / 4) + k], a2);
+  for (int k = 0; k < H / 4; ++k) a2 = fmaf(w2r[k], h1[q * (H / 4) + k], a2);
   a2 += __shfl_xor_sync(0xffffffffu, a2, 1);
   a2 += __shfl_xor_sync(0xffffffffu, a2, 2);
-  float part = (q == 0) ? w3[j] * tanhf(a2 + b2[j]) : 0.f;
+  float part = (q == 0) ? w3v * tanhf(a2 + b2v) : 0.f;
   part = warp_sum(part);
-  if ((tid & 31) == 0) red[tid >> 5] = part;
+  if (lane == 0) red[wid] = part;
   __syncthreads();
   if (tid == 0) {
-    float yz = w3[MLP_H];
+    float yz = w3[H];
     for (int w = 0; w < 8; ++w) yz += red[w];
-    const float dlog = yz * norm[2 * MLP_F + 1] + norm[2 * MLP_F];
+    const float dlog = yz * nrm_s[2 * F + 1] + nrm_s[2 * F];
     const double e = (double)exp10f((float)st.last_log_eps + dlog);
     *est = e;
     bool novel = false;
-    for (int i = 1; i < MLP_F; ++i)
+    for (int i = 1; i < F; ++i)
       if (i != 6) novel |= fabsf(xs[i]) > (float)st.novelty_z;
     *need = (e > st.gate * st.eps_th ? 1 : 0) | (st.steps_since_exact >= st.max_skip ? 2 : 0) | (novel ? 4 : 0);
   }

@@ -930,11 +930,24 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_update(UpdArgs a) {
     *t_out = task - tile_base[n];
   };
 
-  // 1: M, X, partial P
+  // 1: M, X, partial P; the last CTA also forms dS = Y_3 x_3 A_3^T when the projection
+  // left it (read from phase 4 on)
   for (int task = blockIdx.x; task < ntiles_total; task += nb) {
     int n, t;
     tile_of(task, &n, &t);
     rows_mxp<Tc>(a, n, (int64_t)t * 32, t, smraw);
+  }
+  if (a.y3 && blockIdx.x == nb - 1) {
+    const Tc* Y3 = (const Tc*)a.y3;
+    const Tc* A3 = (const Tc*)a.A[2];
+    const int r12 = d.r[0] * d.r[1], r3 = d.r[2];
+    const int N3 = (int)d.N[2];
+    for (int e = threadIdx.x; e < r12 * r3; e += blockDim.x) {
+      const int a12 = e % r12, c = e / r12;
+      Tc s = Tc(0);
+      for (int sl = 0; sl < N3; ++sl) s += Y3[a12 + (int64_t)r12 * sl] * A3[sl + (int64_t)N3 * c];
+      ((Tc*)a.dS_out)[e] = s;
+    }
   }
   if (!grid_sync(a.bar, ++nbar, nb, a.flags, &abort_sh)) return;
   stamp(st_sh, a.stamps, ++nst);

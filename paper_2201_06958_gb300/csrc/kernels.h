@@ -55,6 +55,8 @@ struct UpdArgs {
   ModeDesc d;
   const void* Y[kMaxModes];      // projections Y_n (Tc)
   const void* dS;                // core increment (Tc)
+  const void* y3;                // Y_3 (Tc, three modes): when set, phase 1 forms dS = Y_3 x_3 A_3^T
+  void* dS_out;                  // ... into this buffer (the one dS points to)
   double* T;                     // core (in: step k, out: step k+1)
   double* T2;                    // scratch core
   void* Tcore;                   // Tc copy of the core (in and out; aliases T in FP64)
@@ -139,6 +141,8 @@ void launch_weight_data(const float* V, int p, const int64_t* N, const float* co
 void launch_gram_weighted(const float* Vw, int64_t L, int64_t Nn, int64_t Q, double* part, size_t part_cap,
                           double* C64, float* Cc, cudaStream_t s);
 size_t eig_si_scratch_floats(int n);
+// Leading k eigenpairs of the float Gram Cc (n x n) by block subspace iteration from
+// hash columns (the result depends on Cc only).
 tdb_status eig_si_float(const float* Cc, const double* C64, int n, int k, int iters, float* scratch, unsigned* bar,
                         unsigned* flags, double* ev, double* Q, double* trace, cudaStream_t s);
 

@@ -55,7 +55,8 @@ struct Params {
   int nq1, nq2;
   int r1, r2, r1pad, r2pad;
   int nunits, nstages;
-  int b1_bytes, b2_bytes;
+  int b1_bytes, b2_bytes;        // resident image bytes in shared memory
+  int bsub;                      // 1: one unit per CTA, only its two K blocks of each image resident
   float* Z1p;                    // [nq1][nslice][N2][r1]
   float* Z2p;                    // [nq2][nslice][N1][r2]
   const uint4* B1img;            // BF16 operand images (global)
@@ -116,6 +117,13 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm,
       "[%5];" ::"r"(dst),
       "l"((uint64_t)tm), "r"(x), "r"(y), "r"(z), "r"(bar)
       : "memory");
+}
+
+// Untiled bulk copy global -> shared (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"((uint64_t)src), "r"(bytes), "r"(bar)
+               : "memory");
 }
 
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
@@ -191,7 +199,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   uint64_t* bf_full = bars + 2 * MAX_STAGES;
   uint64_t* mma_done = bf_full + 2;
   uint64_t* epi_done = mma_done + 2;
-  uint32_t* tmem_slot = (uint32_t*)(epi_done + 2);
+  uint64_t* bimg_full = epi_done + 2;       // the operand images have landed
+  uint32_t* tmem_slot = (uint32_t*)(bimg_full + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   __shared__ double red[32];
 
@@ -207,6 +216,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       mbar_init(smem_u32(&mma_done[b]), 1);
       mbar_init(smem_u32(&epi_done[b]), NUM_EPI_WARPS);
     }
+    mbar_init(smem_u32(bimg_full), 1);
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -216,14 +226,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
-  // resident BF16 images of the weighted bases
-  {
-    uint4* d1 = (uint4*)b1_smem;
-    for (int i = tid; i < P.b1_bytes / 16; i += NUM_THREADS) d1[i] = P.B1img[i];
-    uint4* d2 = (uint4*)b2_smem;
-    for (int i = tid; i < P.b2_bytes / 16; i += NUM_THREADS) d2[i] = P.B2img[i];
-  }
-  fence_proxy_async();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -241,6 +243,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       int ucount[NS];
 #pragma unroll
       for (int j = 0; j < NS; ++j) ucount[j] = 0;
+      // the BF16 images of the weighted bases (A_1, A_2), resident for the CTA's units
+      // (only the unit's two K blocks of each when it has one unit) by one bulk copy
+      // each; with 16 stages they follow the first tile's copies, with 8 they lead
+      bool b_issued = false;
+      auto issue_b = [&]() {
+        const uint32_t bb = smem_u32(bimg_full);
+        mbar_arrive_expect_tx(bb, (uint32_t)(P.b1_bytes + P.b2_bytes));
+        const int u0 = blockIdx.x;
+        const char* s1 = (const char*)P.B1img + (P.bsub ? (size_t)(u0 % P.nq1) * P.b1_bytes : 0);
+        const char* s2 = (const char*)P.B2img + (P.bsub ? (size_t)((u0 / P.nq1) % P.nq2) * P.b2_bytes : 0);
+        bulk_load(smem_u32(b1_smem), s1, (uint32_t)P.b1_bytes, bb);
+        bulk_load(smem_u32(b2_smem), s2, (uint32_t)P.b2_bytes, bb);
+        b_issued = true;
+      };
+      if (NS < NSUB && blockIdx.x < P.nunits) issue_b();
       bool ok = true;
       int t = 0;
       for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x, ++t) {
@@ -259,8 +276,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           tma_load_3d(dst, &tmVn, x, y, sl, fb);
           tma_load_3d(dst + BOX_BYTES, &tmVp, x, y, sl, fb);
         }
+        if (!b_issued && ok) issue_b();
       }
       // drain: every armed copy has landed before the CTA may leave
+      if (b_issued) {
+        long long t0 = clock64();
+        while (!mbar_try_wait(smem_u32(bimg_full), 0) && clock64() - t0 < TIMEOUT_CYCLES) {
+        }
+      }
 #pragma unroll
       for (int j = 0; j < NS; ++j) {
         if (ucount[j] == 0) continue;
@@ -279,7 +302,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       bool ok = true;
       for (int u = blockIdx.x; u < P.nunits; u += gridDim.x, ++t) {
         const int q1 = u % P.nq1, q2 = (u / P.nq1) % P.nq2;
+        const int kb1 = P.bsub ? 0 : q1 * 2, kb2 = P.bsub ? 0 : q2 * 2;   // first K block of the unit
         const int buf = t & 1;
+        if (t == 0 && !mbar_wait(smem_u32(bimg_full), 0, abort_flag, P.flags)) { ok = false; break; }
         if (!mbar_wait(smem_u32(&bf_full[buf]), (t >> 1) & 1, abort_flag, P.flags)) { ok = false; break; }
         if (t >= 2 && !mbar_wait(smem_u32(&epi_done[buf]), ((t >> 1) - 1) & 1, abort_flag, P.flags)) {
           ok = false;
@@ -293,14 +318,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
           uint64_t ad = smem_desc(tile + (kk >> 2) * HALF_BYTES + (kk & 3) * 32, 16, 1024);
-          uint64_t bd = smem_desc(b1 + (q1 * 2 + (kk >> 2)) * blk1 + (kk & 3) * 32, 16, 1024);
+          uint64_t bd = smem_desc(b1 + (kb1 + (kk >> 2)) * blk1 + (kk & 3) * 32, 16, 1024);
           mma_bf16(d1, ad, bd, idesc1, kk > 0 ? 1u : 0u);
         }
         // Z2 tile: D2[i1, b] = sum_{i2} dV[i1, i2] A2[i2, b]  (A: MN-major view, M = i1, K = i2)
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
           uint64_t ad = smem_desc(tile + kk * 2048, HALF_BYTES, 1024);
-          uint64_t bd = smem_desc(b2 + (q2 * 2 + (kk >> 2)) * blk2 + (kk & 3) * 32, 16, 1024);
+          uint64_t bd = smem_desc(b2 + (kb2 + (kk >> 2)) * blk2 + (kk & 3) * 32, 16, 1024);
           mma_bf16(d2, ad, bd, idesc2, kk > 0 ? 1u : 0u);
         }
         mma_commit(smem_u32(&mma_done[buf]));
@@ -451,15 +476,23 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 // 64-row K blocks of rpad rows x 128 B; element (k, a) of block g at
 //   g*rpad*128 + a*128 + (((k/8) ^ (a%8)) * 16) + (k%8)*2.
 // ---------------------------------------------------------------------------
-__global__ void k_pack_bimg(const float* __restrict__ A, int N, int r, int rpad, int nblk,
-                            __nv_bfloat16* __restrict__ img) {
-  const int total = nblk * rpad * 64;
+__device__ __forceinline__ void pack_bimg_elem(const float* __restrict__ A, int N, int r, int rpad, int e,
+                                               __nv_bfloat16* __restrict__ img) {
+  const int k = e % 64, a = (e / 64) % rpad, g = e / (64 * rpad);
+  const int i = g * 64 + k;
+  float v = (a < r && i < N) ? A[i + (int64_t)N * a] : 0.f;
+  const int off = g * rpad * 64 + a * 64 + (((k >> 3) ^ (a & 7)) << 3) + (k & 7);
+  img[off] = __float2bfloat16_rn(v);
+}
+
+// Both images in one launch: elements [0, nblk1 rpad1 64) of A_1, then those of A_2.
+__global__ void k_pack_bimg(const float* __restrict__ A1, int N1, int r1, int rpad1, int nblk1,
+                            __nv_bfloat16* __restrict__ img1, const float* __restrict__ A2, int N2, int r2, int rpad2,
+                            int nblk2, __nv_bfloat16* __restrict__ img2) {
+  const int tot1 = nblk1 * rpad1 * 64, total = tot1 + nblk2 * rpad2 * 64;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    const int k = e % 64, a = (e / 64) % rpad, g = e / (64 * rpad);
-    const int i = g * 64 + k;
-    float v = (a < r && i < N) ? A[i + (int64_t)N * a] : 0.f;
-    const int off = g * rpad * 64 + a * 64 + (((k >> 3) ^ (a & 7)) << 3) + (k & 7);
-    img[off] = __float2bfloat16_rn(v);
+    if (e < tot1) pack_bimg_elem(A1, N1, r1, rpad1, e, img1);
+    else pack_bimg_elem(A2, N2, r2, rpad2, e - tot1, img2);
   }
 }
 
@@ -481,6 +514,134 @@ __global__ void k_tc_reduce(const float* __restrict__ Z1p, const float* __restri
       float s = 0.f;
       for (int q = 0; q < nq2; ++q) s += Z2p[((q * nslice + sl) * (int64_t)N1 + i1) * r2 + b];
       Z2[f] = s;
+    }
+  }
+}
+
+// Three-mode finish, first launch.  A CTA owns a tile of 64 elements: of Z1 (r1 x N2,
+// element e = a + r1 i2) or of Z2 (element f = b + r2 i1).  For slices in chunks of
+// 16 it stages z[s][e] = sum_q of the partials (one coalesced pass, all loads of a
+// chunk in flight), writes Z1, and accumulates Y_2 = Z1 x_3 A_3^T or
+// Y_1 = Z2 x_3 A_3^T from shared memory (thread per (element, c), c < r3 <= 32).
+// Both partial layouts put (element, slice, tile q) at e + n (q S + s).  CTA 0 also
+// adds the per-CTA ||dV||_W^2 partials.
+constexpr int FA_TE = 64, FA_SC = 16;
+__global__ void __launch_bounds__(256) k_tc_finish_a(const float* __restrict__ Z1p, const float* __restrict__ Z2p,
+                                                     int N1, int N2, int S, int nq1, int nq2, int r1, int r2, int r3,
+                                                     const float* __restrict__ A3, float* __restrict__ Z1,
+                                                     float* __restrict__ Y2, float* __restrict__ Y1,
+                                                     const double* __restrict__ npart, int nnp,
+                                                     double* __restrict__ dv2) {
+  __shared__ float zs[FA_SC][FA_TE + 1];
+  __shared__ float as[FA_SC][33];
+  const int tid = threadIdx.x;
+  if (blockIdx.x == 0) {
+    __shared__ double sh[32];
+    double t = 0.0;
+    for (int i = tid; i < nnp; i += blockDim.x) t += npart[i];
+    t = block_sum(t, sh);
+    if (tid == 0) *dv2 = t;
+  }
+  const int64_t n1 = (int64_t)r1 * N2, n2 = (int64_t)N1 * r2;
+  const int nt1 = (int)((n1 + FA_TE - 1) / FA_TE), nt2 = (int)((n2 + FA_TE - 1) / FA_TE);
+  for (int tile = blockIdx.x; tile < nt1 + nt2; tile += gridDim.x) {
+    const bool first = tile < nt1;
+    const int64_t e0 = (int64_t)(first ? tile : tile - nt1) * FA_TE;
+    const int64_t ne = first ? n1 : n2;
+    const int nq = first ? nq1 : nq2;
+    const float* Pp = first ? Z1p : Z2p;
+    float acc[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) acc[j] = 0.f;
+    for (int s0 = 0; s0 < S; s0 += FA_SC) {
+      const int sc = min(FA_SC, S - s0);
+#pragma unroll
+      for (int u = 0; u < FA_SC * FA_TE / 256; ++u) {
+        const int idx = tid + 256 * u;
+        const int el = idx % FA_TE, sl = idx / FA_TE;
+        const int64_t e = e0 + el;
+        const bool in = sl < sc && e < ne;
+        const float* pe = Pp + e + ne * (int64_t)(s0 + sl);
+        float v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = (in && q < nq) ? __ldcg(&pe[ne * (int64_t)q * S]) : 0.f;
+        float z = ((v[0] + v[1]) + v[2]) + v[3];
+        if (in) {
+          for (int q = 4; q < nq; ++q) z += __ldcg(&pe[ne * (int64_t)q * S]);
+          if (first) Z1[e + n1 * (s0 + sl)] = z;
+        }
+        zs[sl][el] = z;
+      }
+      for (int idx = tid; idx < FA_SC * 32; idx += 256) {
+        const int sl = idx / 32, c = idx % 32;
+        as[sl][c] = (sl < sc && c < r3) ? __ldg(&A3[s0 + sl + (int64_t)S * c]) : 0.f;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        const int pidx = tid + 256 * j;
+        const int el = pidx % FA_TE, c = pidx / FA_TE;
+        if (c < r3)
+          for (int sl = 0; sl < sc; ++sl) acc[j] = fmaf(as[sl][c], zs[sl][el], acc[j]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int pidx = tid + 256 * j;
+      const int el = pidx % FA_TE, c = pidx / FA_TE;
+      const int64_t e = e0 + el;
+      if (c < r3 && e < ne) {
+        if (first) {
+          Y2[e + n1 * c] = acc[j];
+        } else {
+          const int64_t b = e % r2, i1 = e / r2;
+          Y1[i1 + (int64_t)N1 * (b + (int64_t)r2 * c)] = acc[j];
+        }
+      }
+    }
+  }
+}
+
+// Three-mode finish, second launch: Y_3 = Z1 x_2 A_2^T (r1 x r2 x S), a CTA per
+// slice, i2 in chunks of FB_CH staged in shared memory (thread per output (a1, a2)).
+// dS = Y_3 x_3 A_3^T follows in the update kernel.
+constexpr int FB_CH = 128;
+constexpr size_t kFinishBSmem = (size_t)(32 * FB_CH + 32 * (FB_CH + 1)) * sizeof(float);
+__global__ void __launch_bounds__(256) k_tc_finish_b(const float* __restrict__ Z1, int N2, int S, int r1, int r2,
+                                                     const float* __restrict__ A2, float* __restrict__ Y3) {
+  extern __shared__ float fb_sm[];
+  float* zs = fb_sm;                   // r1 x FB_CH (element a + r1 il)
+  float* as = zs + 32 * FB_CH;         // FB_CH x r2 (ld FB_CH + 1)
+  const int tid = threadIdx.x;
+  const int64_t n1 = (int64_t)r1 * N2;
+  for (int sl = blockIdx.x; sl < S; sl += gridDim.x) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int i0 = 0; i0 < N2; i0 += FB_CH) {
+      const int ch = min(FB_CH, N2 - i0);
+      const float* src = Z1 + (int64_t)r1 * i0 + n1 * sl;
+#pragma unroll 4
+      for (int e = tid; e < r1 * ch; e += 256) zs[e] = __ldcg(&src[e]);
+#pragma unroll 4
+      for (int e = tid; e < ch * r2; e += 256) {
+        const int il = e % ch, b = e / ch;
+        as[il + (FB_CH + 1) * b] = __ldg(&A2[i0 + il + (int64_t)N2 * b]);
+      }
+      __syncthreads();
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int o = tid + 256 * j;
+        const int a1 = o % r1, a2 = o / r1;
+        if (a2 < r2)
+          for (int il = 0; il < ch; ++il) acc[j] = fmaf(as[il + (FB_CH + 1) * a2], zs[a1 + r1 * il], acc[j]);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int o = tid + 256 * j;
+      const int a1 = o % r1, a2 = o / r1;
+      if (a2 < r2) Y3[a1 + (int64_t)r1 * (a2 + (int64_t)r2 * sl)] = acc[j];
     }
   }
 }
@@ -572,7 +733,7 @@ void tc_carve(TcPlan& plan, Carver& cv, int p, const int64_t* N, const int* cap)
 tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, const int64_t* N, const int* r,
                       const void* const* A, const double* const* w, float* Z1, float* Z2, float* scratch,
                       float* dS, float* const* Y, double* dv2, unsigned* flags, cudaStream_t s, cudaEvent_t* evm,
-                      std::string& err) {
+                      std::string& err, bool defer_ds) {
   if (!get_encoder(err)) return TDB_ERR_UNSUPPORTED;
   const int N1 = (int)N[0], N2 = (int)N[1];
   int nslice = 1;
@@ -581,12 +742,10 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   const int r1pad = rpad_of(r[0]), r2pad = rpad_of(r[1]);
   // operand images of A_1 = W_1 U_1 and A_2 = W_2 U_2 (refreshed every step)
   {
-    int tot1 = nq1 * 2 * r1pad * 64, tot2 = nq2 * 2 * r2pad * 64;
-    k_pack_bimg<<<(tot1 + 255) / 256, 256, 0, s>>>((const float*)A[0], N1, r[0], r1pad, nq1 * 2,
-                                                   (__nv_bfloat16*)plan.Abf[0]);
-    count_launch();
-    k_pack_bimg<<<(tot2 + 255) / 256, 256, 0, s>>>((const float*)A[1], N2, r[1], r2pad, nq2 * 2,
-                                                   (__nv_bfloat16*)plan.Abf[1]);
+    const int tot = nq1 * 2 * r1pad * 64 + nq2 * 2 * r2pad * 64;
+    k_pack_bimg<<<(tot + 255) / 256, 256, 0, s>>>((const float*)A[0], N1, r[0], r1pad, nq1 * 2,
+                                                  (__nv_bfloat16*)plan.Abf[0], (const float*)A[1], N2, r[1], r2pad,
+                                                  nq2 * 2, (__nv_bfloat16*)plan.Abf[1]);
     count_launch();
   }
   if (!plan.wsl_ready) {
@@ -613,8 +772,14 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   P.r1pad = r1pad;
   P.r2pad = r2pad;
   P.nunits = nq1 * nq2 * nslice;
-  P.b1_bytes = nq1 * 2 * r1pad * 128;
-  P.b2_bytes = nq2 * 2 * r2pad * 128;
+  int dev = 0, nsm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::min(P.nunits, std::min(nsm, 1024));
+  // one unit per CTA: only that unit's two K blocks of each image are resident
+  P.bsub = grid >= P.nunits ? 1 : 0;
+  P.b1_bytes = (P.bsub ? 2 : nq1 * 2) * r1pad * 128;
+  P.b2_bytes = (P.bsub ? 2 : nq2 * 2) * r2pad * 128;
   // 1 KB alignment slack for the 1024-byte swizzle atoms, then one stage per converter warp
   int fixed = 1024 + 2 * BF_TILE_BYTES + ((P.b1_bytes + 1023) & ~1023) + ((P.b2_bytes + 1023) & ~1023) +
               NUM_EPI_WARPS * 32 * 33 * 4 + 512;
@@ -638,10 +803,6 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
     cudaFuncSetAttribute(k_tc_project<MIN_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     plan.attr_set = true;
   }
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::min(P.nunits, std::min(nsm, 1024));
   if (evm) cudaEventRecord(evm[0], s);
   if (P.nstages == MAX_STAGES)
     k_tc_project<MAX_STAGES><<<grid, NUM_THREADS, smem, s>>>(tmn, tmp, P);
@@ -653,6 +814,28 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   if (e != cudaSuccess) {
     err = std::string("k_tc_project launch: ") + cudaGetErrorString(e);
     return TDB_ERR_CUDA;
+  }
+  if (tc_defers_ds(p, r)) {
+    // two launches: the partial sums with Y_2, Y_1 and ||dV||^2, then Y_3; dS follows in
+    // the update kernel (defer_ds) or as one mode product here
+    const int64_t ntile = ((int64_t)r[0] * N2 + FA_TE - 1) / FA_TE + ((int64_t)N1 * r[1] + FA_TE - 1) / FA_TE;
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ntile, 152 * 8));
+    k_tc_finish_a<<<blocks, 256, 0, s>>>(plan.z1p, plan.z2p, N1, N2, nslice, nq1, nq2, r[0], r[1], r[2],
+                                         (const float*)A[2], Z1, Y[1], Y[0], plan.npart, grid, dv2);
+    count_launch();
+    k_tc_finish_b<<<std::min(nslice, 152 * 8), 256, kFinishBSmem, s>>>(Z1, N2, nslice, r[0], r[1],
+                                                                       (const float*)A[1], Y[2]);
+    count_launch();
+    if (!defer_ds) {
+      const int64_t L = (int64_t)r[0] * r[1];
+      launch_modeprod<float, float, float>(Y[2], dS, (const float*)A[2], L, nslice, r[2], 1, nslice, 1, s);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) {
+      err = std::string("projection finish: ") + cudaGetErrorString(e);
+      return TDB_ERR_CUDA;
+    }
+    return TDB_OK;
   }
   launch_sum_partials(plan.npart, grid, dv2, s);
   // Z1 (r1 x N2 x S) and Z2 (N1 x r2 x S)

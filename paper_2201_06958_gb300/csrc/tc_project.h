@@ -20,13 +20,15 @@ struct TcPlan {
 };
 
 bool tc_supported(int p, const int64_t* N, const int* cap, std::string& err);
+// Three modes (r_3 <= 32): tc_project leaves dS = Y_3 x_3 A_3^T to the update kernel.
+inline bool tc_defers_ds(int p, const int* r) { return p == 3 && r[2] <= 32; }
 void tc_carve(TcPlan& plan, Carver& cv, int p, const int64_t* N, const int* cap);
-// dS and Y_n of dV = Vn - Vp (Eqs. 2.15, 2.16) and ||dV||_W^2 into *dv2.  A: FP32
+// dS (unless tc_defers_ds) and Y_n of dV = Vn - Vp (Eqs. 2.15, 2.16) and ||dV||_W^2 into *dv2.  A: FP32
 // weighted bases (N_n x r_n); w: mode weights; Z1 (r1 x N2 x S), Z2 (N1 x r2 x S)
 // and scratch (>= the largest intermediate) are device buffers of the caller.
 tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, const int64_t* N, const int* r,
                       const void* const* A, const double* const* w, float* Z1, float* Z2, float* scratch,
                       float* dS, float* const* Y, double* dv2, unsigned* flags, cudaStream_t s, cudaEvent_t* evm,
-                      std::string& err);
+                      std::string& err, bool defer_ds = false);
 
 }  // namespace tdb

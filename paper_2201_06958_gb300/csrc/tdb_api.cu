@@ -898,7 +898,7 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
     TRY(tc_project(ctx->tc, (const float*)Vn, (const float*)Vp, ctx->p, ctx->N, ctx->r, (const void* const*)ctx->A,
                    (const double* const*)ctx->w, (float*)ctx->ping, (float*)ctx->pong, (float*)ctx->dV,
                    (float*)ctx->dS, (float* const*)ctx->Y, &ctx->rb_dev->dv2, ctx->flags, s, ev ? ev + 4 : nullptr,
-                   ctx->err));
+                   ctx->err, true));
   } else {
     launch_diff<Tc>(Vn, Vp, (Tc*)ctx->dV, ctx->S, s);
     launch_wnorm2<Tc>((const Tc*)ctx->dV, nullptr, weight_view(ctx), ctx->npart, ctx->nblk, &ctx->rb_dev->dv2,
@@ -925,6 +925,8 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
       ntiles += (ctx->N[n] + 31) / 32;
     }
     a.dS = ctx->dS;
+    a.y3 = (ctx->use_tc && tc_defers_ds(p, ctx->r)) ? ctx->Y[2] : nullptr;
+    a.dS_out = ctx->dS;
     a.T = ctx->T;
     a.T2 = ctx->T2;
     a.Tcore = ctx->Tcore;

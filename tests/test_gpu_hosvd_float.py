@@ -70,3 +70,45 @@ def test_float_hosvd_init_matches_oracle(tdbmod, dims, ranks):
     assert rel(O.reconstruct(Tg, Ug), O.reconstruct(To, Uo)) <= 1e-5
     for a, b in zip(O.core_singular_values(Tg), O.core_singular_values(To)):
         assert rel(a, b) <= 1e-4
+
+
+@cuda
+def test_float_reinit_matches_oracle(tdbmod):
+    """A re-initialisation (Sec. 2.5) in the float path, in the middle of a stream.
+    The state it leaves is the truncated HOSVD of that snapshot at the new ranks:
+    projectors within
+    max(1e-4, 20 u lambda_1 / gap) of the oracle's (u = 2^-24; the float Gram moves
+    the r-dimensional eigenspace by its rounding over the gap lambda_r - lambda_{r+1}),
+    the reconstruction within max(1e-5, sum_n b_n sqrt(2 lambda_r / sum lambda)): a
+    rotation of the kept subspace by an angle b_n near the cut moves the energy of the
+    directions r and r + 1, about 2 lambda_r of the total."""
+    wl = S.make_workload("reactive")
+    w = wl.weights
+    c = tdbmod.TDB(wl.dims, wl.rank, rank_max=wl.rank_max, weights=w, eps_th=8e-5, gamma_th=99.9,
+                   slope_window=5, precision="fp32", error_mode="exact")
+    c.init(wl.snapshot(0, device="cuda"))
+    snap, info = None, None
+    for k in range(1, 81):
+        snap = wl.snapshot(k, device="cuda")
+        info = c.push(snap)
+        if info["reinit"] > 0 and info["action"] in ("reinit", "increase"):
+            break
+    else:
+        pytest.fail("no re-initialisation within 80 steps")
+    V = S.to_logical(snap)
+    ranks = info["ranks"]
+    spec = O.hosvd_spectrum(V, w)
+    To, Uo, _ = O.hosvd(V, w, ranks, spectrum=spec)
+    Tg, Ug = c.factors()
+    rec_bound = 0.0
+    for n in range(3):
+        lam = spec[n][0]
+        r = ranks[n]
+        gap = lam[r - 1] - (lam[r] if r < len(lam) else 0.0)
+        bound = max(1e-4, 20 * 2.0 ** -24 * lam[0] / max(gap, 1e-300))
+        rec_bound += bound * np.sqrt(2 * lam[r - 1] / lam.sum())
+        Pg = Ug[n] @ (Ug[n].T * w[n][None, :])
+        Po = Uo[n] @ (Uo[n].T * w[n][None, :])
+        assert np.abs(Pg - Po).max() <= bound, (n, r, np.abs(Pg - Po).max(), bound)
+    d = rel(O.reconstruct(Tg, Ug), O.reconstruct(To, Uo))
+    assert d <= max(1e-5, rec_bound), (d, rec_bound)
