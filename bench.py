@@ -455,6 +455,13 @@ def run_tdb(args, world, rank, local):
                               "eps_max_rel_diff_at_exact_steps": rel, "reinits": ref["counters"]["reinits"],
                               "same_decisions": res["acts"] == ref["acts"],
                               "exact_evals": ref["counters"]["exact_evals"]}
+        div = next((i for i, (a, b) in enumerate(zip(res["acts"], ref["acts"])) if a != b), None)
+        if div is not None:
+            # the first timed step whose action or ranks differ (actions: 0 none, 1 re-init,
+            # 2 increase, 3 decrease, 4 revert, 5 cap); whether this path evaluated it exactly
+            line["plain_fp32"]["first_divergence"] = {
+                "step": W + 1 + div, "this": list(res["acts"][div]), "plain": list(ref["acts"][div]),
+                "this_exact": res["eps"][div] == res["eps"][div]}
 
     # end to end through the C ABI from pinned host buffers
     if not args.no_e2e:

@@ -276,16 +276,18 @@ __device__ void sum_gram(const float* __restrict__ Gp, int nb, int gstride, int 
   }
 }
 
-// X (upper triangular, Xs[i + LDM j]) from the Gram Gs on the FW = 4 warps [0, 128):
-// lane l owns rows l and l + 32, warp w the columns c = w + 4 j (j < 16).  A step
-// loads the pivot row's and then the own row's entries into registers (no stores in
-// between) before it updates them.  A pivot that is not positive restarts the
-// elimination with a shifted diagonal (1e-5, then 1e-2: the columns of the block
-// beyond the float resolution of the spectrum are nearly dependent); on the last
-// attempt such a column is skipped and its column of X is zero.  Every thread reads
-// the same pivots after a barrier, so the decisions are uniform.
+// X (upper triangular, Xs[i + LDM j]) from the Gram Gs on the FW = 4 warps [0, 128).
+// R is the augmented matrix [G^ | I] (m x 2m, element (i, cc) at R[i + LDM cc], the
+// identity block from column m on), so step k updates the contiguous window of columns
+// k+1 .. k+m (U right of the pivot, then E up to column k) with no per-column select:
+// lane l owns rows l and l + 32, warp w the window columns w, w + 4, ...; the pivot
+// row's and the own row's entries are loaded into registers before the stores.  A
+// pivot that is not positive restarts the elimination with a shifted diagonal (1e-5,
+// then 1e-2: the block's tail columns sit below the float resolution of the
+// spectrum); on the last attempt such a column is skipped and its column of X is zero.
+// Every thread reads the same pivots after a barrier, so the decisions are uniform.
 constexpr int FW = 4;
-__device__ void eig_factor(int m, const float* Gs, float* A, float* E, float* Xs, float* dsc, unsigned* flags) {
+__device__ void eig_factor(int m, const float* Gs, float* R, float* Xs, float* dsc, unsigned* flags) {
   constexpr int nthr = FW * 32, CPT = MMAX / FW;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   for (int i = t; i < m; i += nthr) {
@@ -298,63 +300,73 @@ __device__ void eig_factor(int m, const float* Gs, float* A, float* E, float* Xs
     named_bar(2, nthr);
     for (int i = lane; i < m; i += 32)
 #pragma unroll
-      for (int j = 0; j < CPT; ++j) {
-        const int c = w + FW * j;
-        if (c < m) {
-          A[i + LDM * c] = Gs[i + LDM * c] * dsc[i] * dsc[c] + (i == c ? shift : 0.f);
-          E[i + LDM * c] = (i == c) ? 1.f : 0.f;
-        }
+      for (int j = 0; j < 2 * CPT; ++j) {
+        const int cc = w + FW * j;
+        if (cc < 2 * m)
+          R[i + LDM * cc] = cc < m ? Gs[i + LDM * cc] * dsc[i] * dsc[cc] + (i == cc ? shift : 0.f)
+                                   : (cc - m == i ? 1.f : 0.f);
       }
     named_bar(2, nthr);
     ok = true;
     for (int k = 0; k < m; ++k) {
-      const float piv = A[k + LDM * k];
+      const float piv = R[k + LDM * k];
       if (!(piv > 1e-30f)) {
         ok = false;
         if (attempt < 2) break;
         continue;
       }
       const float ip = 1.f / piv;
-      // the pivot row: A (columns > k) and E (columns <= k)
       float prow[CPT];
 #pragma unroll
       for (int j = 0; j < CPT; ++j) {
-        const int c = w + FW * j;
-        prow[j] = c < m ? (c > k ? A[k + LDM * c] : E[k + LDM * c]) : 0.f;
+        const int off = w + FW * j;                    // window column k + 1 + off
+        prow[j] = off < m ? R[k + LDM * (k + 1 + off)] : 0.f;
       }
-      // rows below k: row_i -= (a_ik / a_kk) row_k
+      // rows below k: row_i -= (a_ik / a_kk) row_k over the window
       for (int i = k + 1 + lane; i < m; i += 32) {
-        const float f = A[i + LDM * k] * ip;
+        const float f = R[i + LDM * k] * ip;
         float rv[CPT];
 #pragma unroll
         for (int j = 0; j < CPT; ++j) {
-          const int c = w + FW * j;
-          rv[j] = c < m ? (c > k ? A[i + LDM * c] : E[i + LDM * c]) : 0.f;
+          const int off = w + FW * j;
+          rv[j] = off < m ? R[i + LDM * (k + 1 + off)] : 0.f;
         }
 #pragma unroll
         for (int j = 0; j < CPT; ++j) {
-          const int c = w + FW * j;
-          if (c < m) {
-            const float v = fmaf(-f, prow[j], rv[j]);
-            if (c > k) A[i + LDM * c] = v;
-            else E[i + LDM * c] = v;
-          }
+          const int off = w + FW * j;
+          if (off < m) R[i + LDM * (k + 1 + off)] = fmaf(-f, prow[j], rv[j]);
         }
       }
       named_bar(2, nthr);
     }
   }
   if (!ok && t == 0) atomicOr(flags, kFlagEigNoConv);
-  // X[i][j] = dsc[i] * E[j][i] / sqrt(u_jj)  (upper triangular; zero for a skipped pivot)
-  for (int i = lane; i < m; i += 32)
+  // X[i][j] = dsc[i] * E[j][i] / sqrt(u_jj) with E[j][i] = R(j, m + i) (upper triangular;
+  // zero for a skipped pivot); every load before the first store
+  float xv[2][CPT];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int i = lane + 32 * h;
 #pragma unroll
     for (int jj = 0; jj < CPT; ++jj) {
       const int j = w + FW * jj;
-      if (j < m) {
-        const float u = A[j + LDM * j];
-        Xs[i + LDM * j] = (j >= i) ? dsc[i] * E[j + LDM * i] * (u > 0.f ? rsqrtf(u) : 0.f) : 0.f;
+      float x = 0.f;
+      if (i < m && j < m && j >= i) {
+        const float u = R[j + LDM * j];
+        x = dsc[i] * R[j + LDM * (m + i)] * (u > 0.f ? rsqrtf(u) : 0.f);
       }
+      xv[h][jj] = x;
     }
+  }
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int i = lane + 32 * h;
+#pragma unroll
+    for (int jj = 0; jj < CPT; ++jj) {
+      const int j = w + FW * jj;
+      if (i < m && j < m) Xs[i + LDM * j] = xv[h][jj];
+    }
+  }
 }
 
 // Rows [r0, r0 + RB): Wr = C[rows, :] Zin (RB x m, ld LDM) on threads [t0, t0 + ng).
@@ -464,8 +476,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
   const int nrb = (n + RB - 1) / RB;
   const int nb = gridDim.x, b = blockIdx.x;
   float* Gs = smf;                        // summed Gram (Rayleigh-Ritz: M)
-  float* As = Gs + MMAX * LDM;            // elimination work (H)
-  float* Es = As + MMAX * LDM;            // elimination E (Jacobi vectors)
+  float* As = Gs + MMAX * LDM;            // elimination [G^ | I]: 2 MMAX columns (H)
+  float* Es = As + MMAX * LDM;            // (second half of the above; Jacobi vectors)
   float* Xs = Es + MMAX * LDM;            // X, kept to the Rayleigh-Ritz step
   float* Ga = Xs + MMAX * LDM;            // this CTA's partial Gram (small scratch)
   float* Wr = Ga + MMAX * LDM;            // RB x m rows of C Z
@@ -501,7 +513,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
     for (int rb = b; rb < nrb; rb += nb) {
       const int r0 = rb * RB;
       if (tid < t0) {
-        if (!any) eig_factor(m, Gs, As, Es, Xs, dsc, a.flags);
+        if (!any) eig_factor(m, Gs, As, Xs, dsc, a.flags);
       } else {
         eig_rows_cz(a, Zc, r0, Wr, czs, ZCH, t0, ng, !(a.c_resident && it > 0));
       }
@@ -532,7 +544,7 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
       __syncthreads();
       any = true;
     }
-    if (!any && tid < t0) eig_factor(m, Gs, As, Es, Xs, dsc, a.flags);   // (no rows: keeps X defined)
+    if (!any && tid < t0) eig_factor(m, Gs, As, Xs, dsc, a.flags);   // (no rows: keeps X defined)
     store_gram(m, a.gstride, Ga, any, a.Gp[cur ^ 1] + (int64_t)b * a.gstride);
     if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
   }
