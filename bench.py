@@ -310,7 +310,9 @@ def run_tdb(args, world, rank, local):
         precision = "fp64" if wl.dtype == "f64" else "bf16"
     err_mode = args.error_mode
     if err_mode == "auto":
-        err_mode = "mlp" if (precision == "bf16" and wl.eps_th > 0) else "exact"
+        # the exact error of every step runs beside the G_n refresh on a second stream and
+        # costs less than gating it with the learned estimator (which serialises them)
+        err_mode = "exact"
     K, W = args.steps, args.warmup
     est_params, est_info = None, None
     if err_mode == "mlp":

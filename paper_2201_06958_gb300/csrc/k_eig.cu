@@ -278,16 +278,20 @@ __device__ void sum_gram(const float* __restrict__ Gp, int nb, int gstride, int 
 
 // X (upper triangular, Xs[i + LDM j]) from the Gram Gs on the FW = 4 warps [0, 128).
 // R is the augmented matrix [G^ | I] (m x 2m, element (i, cc) at R[i + LDM cc], the
-// identity block from column m on), so step k updates the contiguous window of columns
-// k+1 .. k+m (U right of the pivot, then E up to column k) with no per-column select:
-// lane l owns rows l and l + 32, warp w the window columns w, w + 4, ...; the pivot
-// row's and the own row's entries are loaded into registers before the stores.  A
-// pivot that is not positive restarts the elimination with a shifted diagonal (1e-5,
-// then 1e-2: the block's tail columns sit below the float resolution of the
-// spectrum); on the last attempt such a column is skipped and its column of X is zero.
-// Every thread reads the same pivots after a barrier, so the decisions are uniform.
-constexpr int FW = 4;
-__device__ void eig_factor(int m, const float* Gs, float* R, float* Xs, float* dsc, unsigned* flags) {
+// identity block from column m on); Gaussian elimination below the diagonal turns it
+// into [U | E] with E = L^{-1}.  Blocked by FB = 8 pivots (right-looking): warp 0
+// factors the m x FB panel in registers (lane l owns rows l and l + 32, pivot rows by
+// shuffles, multipliers stored below the diagonal); then every thread of the group
+// solves the block rows against L11 (a thread per trailing column) and applies the
+// rank-FB update L21 U12 to the rows below (lane per row, warp per column group).
+// Trailing columns are A's right of the block and E's left of its end: m in all.
+// A pivot that is not positive restarts the elimination with a shifted diagonal
+// (1e-5, then 1e-2: the block's tail columns sit below the float resolution of the
+// spectrum); on the last attempt such a pivot is skipped (multipliers zero) and its
+// column of X is zero.  The panel's verdict reaches the group through shared memory
+// behind a barrier, so the decisions are uniform.
+constexpr int FW = 4, FB = 8;
+__device__ void eig_factor(int m, const float* Gs, float* R, float* Xs, float* dsc, unsigned* flags, int* fail_sh) {
   constexpr int nthr = FW * 32, CPT = MMAX / FW;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
   for (int i = t; i < m; i += nthr) {
@@ -308,33 +312,94 @@ __device__ void eig_factor(int m, const float* Gs, float* R, float* Xs, float* d
       }
     named_bar(2, nthr);
     ok = true;
-    for (int k = 0; k < m; ++k) {
-      const float piv = R[k + LDM * k];
-      if (!(piv > 1e-30f)) {
-        ok = false;
-        if (attempt < 2) break;
-        continue;
-      }
-      const float ip = 1.f / piv;
-      float prow[CPT];
+    for (int kb = 0; kb < m; kb += FB) {
+      const int ke = min(kb + FB, m), nbk = ke - kb;
+      // (1) panel: rows kb.., columns kb .. ke-1, on warp 0
+      if (w == 0) {
+        float pr[2][FB];
 #pragma unroll
-      for (int j = 0; j < CPT; ++j) {
-        const int off = w + FW * j;                    // window column k + 1 + off
-        prow[j] = off < m ? R[k + LDM * (k + 1 + off)] : 0.f;
-      }
-      // rows below k: row_i -= (a_ik / a_kk) row_k over the window
-      for (int i = k + 1 + lane; i < m; i += 32) {
-        const float f = R[i + LDM * k] * ip;
-        float rv[CPT];
+        for (int h = 0; h < 2; ++h) {
+          const int i = lane + 32 * h;
 #pragma unroll
-        for (int j = 0; j < CPT; ++j) {
-          const int off = w + FW * j;
-          rv[j] = off < m ? R[i + LDM * (k + 1 + off)] : 0.f;
+          for (int c = 0; c < FB; ++c) pr[h][c] = (i >= kb && i < m && c < nbk) ? R[i + LDM * (kb + c)] : 0.f;
+        }
+        bool fail = false;
+#pragma unroll
+        for (int kr = 0; kr < FB; ++kr) {
+          if (kr < nbk) {
+            const int k = kb + kr, src = k & 31, hk = k >> 5;
+            const float pk = __shfl_sync(0xffffffffu, hk ? pr[1][kr] : pr[0][kr], src);
+            float prow[FB];
+#pragma unroll
+            for (int c = kr + 1; c < FB; ++c) prow[c] = __shfl_sync(0xffffffffu, hk ? pr[1][c] : pr[0][c], src);
+            const bool good = pk > 1e-30f;
+            fail |= !good;
+            const float ip = good ? 1.f / pk : 0.f;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              const int i = lane + 32 * h;
+              if (i > k && i < m) {
+                const float f = pr[h][kr] * ip;
+                pr[h][kr] = f;
+#pragma unroll
+                for (int c = kr + 1; c < FB; ++c) pr[h][c] = fmaf(-f, prow[c], pr[h][c]);
+              }
+            }
+          }
         }
 #pragma unroll
-        for (int j = 0; j < CPT; ++j) {
-          const int off = w + FW * j;
-          if (off < m) R[i + LDM * (k + 1 + off)] = fmaf(-f, prow[j], rv[j]);
+        for (int h = 0; h < 2; ++h) {
+          const int i = lane + 32 * h;
+          if (i >= kb && i < m)
+#pragma unroll
+            for (int c = 0; c < FB; ++c)
+              if (c < nbk) R[i + LDM * (kb + c)] = pr[h][c];
+        }
+        if (lane == 0) *fail_sh = fail ? 1 : 0;
+      }
+      named_bar(2, nthr);
+      if (*fail_sh) {
+        ok = false;
+        if (attempt < 2) break;               // uniform: every thread read the same flag
+      }
+      // (2) block rows kb .. ke-1: U12 = L11^{-1} R[kb:ke, T], a thread per trailing column
+      const int nA = m - ke;                   // trailing A columns ke .. m-1, then E columns m .. m+ke-1
+      for (int tt = t; tt < m; tt += nthr) {
+        const int col = tt < nA ? ke + tt : m + (tt - nA);
+        float v[FB];
+#pragma unroll
+        for (int q = 0; q < FB; ++q) v[q] = q < nbk ? R[kb + q + LDM * col] : 0.f;
+#pragma unroll
+        for (int q = 1; q < FB; ++q)
+#pragma unroll
+          for (int r = 0; r < q; ++r)
+            if (q < nbk) v[q] = fmaf(-R[kb + q + LDM * (kb + r)], v[r], v[q]);
+#pragma unroll
+        for (int q = 1; q < FB; ++q)
+          if (q < nbk) R[kb + q + LDM * col] = v[q];
+      }
+      named_bar(2, nthr);
+      // (3) rows ke..m-1: R[i, T] -= L21[i, :] U12, lane per row, warp per column group;
+      // four columns' operands loaded before their stores
+      for (int i = ke + lane; i < m; i += 32) {
+        float L[FB];
+#pragma unroll
+        for (int q = 0; q < FB; ++q) L[q] = q < nbk ? R[i + LDM * (kb + q)] : 0.f;
+        for (int t0 = w; t0 < m; t0 += 4 * FW) {
+          float acc[4];
+          int cols[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int tt = t0 + u * FW;
+            cols[u] = tt < nA ? ke + tt : m + (tt - nA);
+            acc[u] = tt < m ? R[i + LDM * cols[u]] : 0.f;
+#pragma unroll
+            for (int q = 0; q < FB; ++q)
+              if (tt < m && q < nbk) acc[u] = fmaf(-L[q], R[kb + q + LDM * cols[u]], acc[u]);
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (t0 + u * FW < m) R[i + LDM * cols[u]] = acc[u];
         }
       }
       named_bar(2, nthr);
@@ -371,8 +436,9 @@ __device__ void eig_factor(int m, const float* Gs, float* R, float* Xs, float* d
 
 // Rows [r0, r0 + RB): Wr = C[rows, :] Zin (RB x m, ld LDM) on threads [t0, t0 + ng).
 // Zin is staged in shared memory (chunks of ZCH rows), C rows in [RB][ZCH + 1]
-// (kept across calls when load_c is false).  Thread layout: row pair rp (8), column
-// quad cq (mq), l-split ls; partial sums reduced in shared memory.
+// (kept across calls when load_c is false).  Thread layout: row quad rq (4), column
+// quad cq (mq), l-split ls (4 x 4 outputs, 16 FMAs per 5 shared loads); partial sums
+// reduced in shared memory.
 __device__ void eig_rows_cz(const EigArgs& a, const float* __restrict__ Zin, int r0, float* Wr, float* sm, int ZCH,
                             int t0, int ng, bool load_c) {
   const int n = a.n, m = a.m, lt = threadIdx.x - t0;
@@ -380,12 +446,12 @@ __device__ void eig_rows_cz(const EigArgs& a, const float* __restrict__ Zin, int
   float* Zs = sm;                         // ZCH x mp
   float* Cs = Zs + ZCH * mp;              // RB x (ZCH + 1)
   float* Rs = Cs + RB * (ZCH + 1);        // reduction: nls x RB x mp
-  const int nthr_rc = 8 * mq;
+  const int nthr_rc = 4 * mq;
   const int nls = ng / nthr_rc;
-  const int rp = lt % 8, cq = (lt / 8) % mq, ls = lt / nthr_rc;
-  float acc[2][4];
+  const int rq = lt % 4, cq = (lt / 4) % mq, ls = lt / nthr_rc;
+  float acc[4][4];
 #pragma unroll
-  for (int x = 0; x < 2; ++x)
+  for (int x = 0; x < 4; ++x)
 #pragma unroll
     for (int y = 0; y < 4; ++y) acc[x][y] = 0.f;
   for (int l0 = 0; l0 < n; l0 += ZCH) {
@@ -425,20 +491,21 @@ __device__ void eig_rows_cz(const EigArgs& a, const float* __restrict__ Zin, int
       const int lb = lc * ls / nls, le = lc * (ls + 1) / nls;
 #pragma unroll 4
       for (int l = lb; l < le; ++l) {
-        const float c0 = Cs[(2 * rp) * (ZCH + 1) + l], c1 = Cs[(2 * rp + 1) * (ZCH + 1) + l];
         const float4 z = *reinterpret_cast<const float4*>(&Zs[l * mp + cq * 4]);
-        acc[0][0] = fmaf(c0, z.x, acc[0][0]); acc[0][1] = fmaf(c0, z.y, acc[0][1]);
-        acc[0][2] = fmaf(c0, z.z, acc[0][2]); acc[0][3] = fmaf(c0, z.w, acc[0][3]);
-        acc[1][0] = fmaf(c1, z.x, acc[1][0]); acc[1][1] = fmaf(c1, z.y, acc[1][1]);
-        acc[1][2] = fmaf(c1, z.z, acc[1][2]); acc[1][3] = fmaf(c1, z.w, acc[1][3]);
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          const float cx = Cs[(4 * rq + x) * (ZCH + 1) + l];
+          acc[x][0] = fmaf(cx, z.x, acc[x][0]); acc[x][1] = fmaf(cx, z.y, acc[x][1]);
+          acc[x][2] = fmaf(cx, z.z, acc[x][2]); acc[x][3] = fmaf(cx, z.w, acc[x][3]);
+        }
       }
     }
   }
   if (ls < nls)
 #pragma unroll
-    for (int x = 0; x < 2; ++x)
+    for (int x = 0; x < 4; ++x)
 #pragma unroll
-      for (int y = 0; y < 4; ++y) Rs[(ls * RB + 2 * rp + x) * mp + cq * 4 + y] = acc[x][y];
+      for (int y = 0; y < 4; ++y) Rs[(ls * RB + 4 * rq + x) * mp + cq * 4 + y] = acc[x][y];
   named_bar(1, ng);
   for (int e = lt; e < RB * m; e += ng) {
     const int rr = e % RB, c = e / RB;
@@ -463,12 +530,38 @@ __device__ void store_gram(int m, int gstride, const float* Ga, bool any, float*
   for (int e = threadIdx.x; e < gstride; e += blockDim.x) dst[e] = (any && e < m * m) ? Ga[e] : 0.f;
 }
 
+// Convergence of the block (one warp): with Z = C Q and Q orthonormal, the diagonally
+// scaled Gram of Z is the identity once the leading columns of Q are eigenvectors
+// (C q_i . C q_j = 0), and its off-diagonal entry (i, j) is of the order of the mixing
+// of q_i and q_j otherwise.  Converged when every pair among the first k columns is
+// below 2e-6 (the rounding of the float Gram) plus 3e-6 sqrt(G_00 / min(G_ii, G_jj)):
+// C q_j carries float rounding of ~1e-6 of the largest eigenvalue, so a column of
+// eigenvalue lambda_j is resolved to ~1e-6 lambda_1 / lambda_j at best.
+constexpr int kMinIters = 4;
+__device__ bool gram_converged(int m, int k, const float* Gs) {
+  const int lane = threadIdx.x & 31;
+  const float g00 = Gs[0];
+  const int kk = min(k, m);
+  bool ok = g00 > 0.f;
+  for (int e = lane; e < kk * kk; e += 32) {
+    const int i = e % kk, j = e / kk;
+    if (i >= j) continue;
+    const float gi = Gs[i + LDM * i], gj = Gs[j + LDM * j];
+    const float gmin = fminf(gi, gj);
+    if (!(gmin > 0.f)) { ok = false; continue; }
+    const float aij = fabsf(Gs[i + LDM * j]) * rsqrtf(gi) * rsqrtf(gj);
+    const float tol = 2e-6f + 3e-6f * sqrtf(g00 / gmin);
+    if (!(aij <= tol)) ok = false;
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
 // Shared-memory layout of the kernel (floats): the m x m work area, then the C Z area.
 constexpr int EIG_WORK_FLOATS = 5 * MMAX * LDM + 2 * RB * LDM;
 
 __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
   extern __shared__ __align__(16) float smf[];
-  __shared__ int abort_sh;
+  __shared__ int abort_sh, fail_sh, conv_sh;
   __shared__ float dsc[MMAX];
   if (threadIdx.x == 0) abort_sh = 0;
   __syncthreads();
@@ -504,21 +597,34 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
   }
   store_gram(m, a.gstride, Ga, any, a.Gp[0] + (int64_t)b * a.gstride);
   if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
-  for (int it = 0; it <= a.iters; ++it) {
+  int it_last = a.iters;                  // the iteration that prepares the Rayleigh-Ritz step
+  bool conv_prev = false;
+  for (int it = 0; it <= it_last; ++it) {
     const int cur = it & 1;
     const float* Zc = a.Z[cur];
     sum_gram(a.Gp[cur], nb, a.gstride, m, Gs);
     __syncthreads();
+    if (it >= kMinIters && it < it_last) {
+      // convergence (every CTA holds the same Gram, so all take the same decision)
+      if (tid < 32) {
+        const bool c = gram_converged(m, a.k, Gs);
+        if (tid == 0) conv_sh = c ? 1 : 0;
+      }
+      __syncthreads();
+      const bool conv = conv_sh != 0;
+      if (conv && conv_prev) it_last = it;
+      conv_prev = conv;
+    }
     any = false;
     for (int rb = b; rb < nrb; rb += nb) {
       const int r0 = rb * RB;
       if (tid < t0) {
-        if (!any) eig_factor(m, Gs, As, Xs, dsc, a.flags);
+        if (!any) eig_factor(m, Gs, As, Xs, dsc, a.flags, &fail_sh);
       } else {
         eig_rows_cz(a, Zc, r0, Wr, czs, ZCH, t0, ng, !(a.c_resident && it > 0));
       }
       __syncthreads();
-      if (it < a.iters) {
+      if (it < it_last) {
         // Z' = W X for these rows (X upper), and their partial Gram
         float* Zn = a.Z[cur ^ 1];
         for (int e = tid; e < RB * a.ldz; e += blockDim.x) {
@@ -544,11 +650,11 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
       __syncthreads();
       any = true;
     }
-    if (!any && tid < t0) eig_factor(m, Gs, As, Xs, dsc, a.flags);   // (no rows: keeps X defined)
+    if (!any && tid < t0) eig_factor(m, Gs, As, Xs, dsc, a.flags, &fail_sh);   // (no rows: keeps X defined)
     store_gram(m, a.gstride, Ga, any, a.Gp[cur ^ 1] + (int64_t)b * a.gstride);
     if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
   }
-  const int fin = a.iters & 1;            // Z[fin] is the final block; Gp[fin ^ 1] holds M
+  const int fin = it_last & 1;            // Z[fin] is the final block; Gp[fin ^ 1] holds M
   // CTA 0: H = X^T M X, Jacobi, ordering; P = X S[:, order] into Xg
   if (b == 0) {
     float* Ms = Gs;
@@ -598,7 +704,8 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
       for (int e = tid; e < nn * nn; e += blockDim.x) {
         const int i = e % nn, j = e / nn;
         const float v = Hs[i + LDM * j];
-        if (i == j) dia += v * v; else off += v * v;
+        if (i == j) { if (i < a.k) dia += v * v; }
+        else if (i < a.k || j < a.k) off += v * v;
       }
       off = warp_sum(off);
       dia = warp_sum(dia);
@@ -623,7 +730,9 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
           }
           const float app = Hs[p + LDM * p], aqq = Hs[q + LDM * q], apq = Hs[p + LDM * q];
           float c = 1.f, s = 0.f;
-          if (apq != 0.f && apq * apq > thr * thr * fabsf(app * aqq)) {
+          // pairs within the block's tail (columns k.. of Q, below the wanted eigenpairs)
+          // are left alone: only the leading k rows and columns must be diagonalised
+          if ((p < a.k || q < a.k) && apq != 0.f && apq * apq > thr * thr * fabsf(app * aqq)) {
             const float theta = (aqq - app) / (2.f * apq);
             const float tt = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
             c = rsqrtf(tt * tt + 1.f);
@@ -818,7 +927,7 @@ tdb_status eig_si_float(const float* Cc, const double* C64, int n, int k, int it
   }
   const int mq = (m + 3) / 4, mp = mq * 4;
   const int fw = FW;                                 // factor warps
-  const int nls = (EIG_THREADS - 32 * fw) / (8 * mq);
+  const int nls = (EIG_THREADS - 32 * fw) / (4 * mq);
   // C Z staging: ZCH rows of Z (a multiple of 16 when chunked, so float4 runs of C
   // rows stay aligned), C rows and the reduction buffer, after the m x m work area
   auto need = [&](int zch) {

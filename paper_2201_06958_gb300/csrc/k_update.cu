@@ -996,9 +996,10 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_update(UpdArgs a) {
   if (!grid_sync(a.bar, ++nbar, nb, a.flags, &abort_sh)) return;
   stamp(st_sh, a.stamps, ++nst);
 
-  // 7: G, G^{-1}, sigma^2
-  for (int n = blockIdx.x; n < p; n += nb)
-    gram_finish(d, n, a.gpart, a.gsplit, a.G, a.Ginv, a.Ginvf, a.sig2, a.Vprev, a.warm, a.flags, smraw);
+  // 7: G, G^{-1}, sigma^2 (or a separate launch beside the exact error)
+  if (!a.skip_finish)
+    for (int n = blockIdx.x; n < p; n += nb)
+      gram_finish(d, n, a.gpart, a.gsplit, a.G, a.Ginv, a.Ginvf, a.sig2, a.Vprev, a.warm, a.flags, smraw);
   stamp(st_sh, a.stamps, ++nst);
   stamp_flush(st_sh, a.stamps, nst);
 }
@@ -1018,16 +1019,21 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_gram_finish(ModeDesc d, cons
   gram_finish(d, blockIdx.x, gpart, gsplit, G, Ginv, Ginvf, sig2, Vprev, warm, flags, smraw);
 }
 
-void launch_gram(const ModeDesc& d, const double* T, double* Gpart, int nsplit, double* G, double* Ginv,
-                 float* Ginvf, double* sig2, float* Vprev, int warm, unsigned* flags, cudaStream_t s) {
+void launch_gram_finish(const ModeDesc& d, const double* Gpart, int nsplit, double* G, double* Ginv, float* Ginvf,
+                        double* sig2, float* Vprev, int warm, unsigned* flags, cudaStream_t s) {
   static bool attr = false;
   if (!attr) {
     cudaFuncSetAttribute(k_gram_finish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kUpdSmem);
     attr = true;
   }
-  k_gram_partial<<<d.p * nsplit, UPD_THREADS, 0, s>>>(d, T, Gpart, nsplit); count_launch();
   k_gram_finish<<<d.p, UPD_THREADS, kUpdSmem, s>>>(d, Gpart, nsplit, G, Ginv, Ginvf, sig2, Vprev, warm, flags);
   count_launch();
+}
+
+void launch_gram(const ModeDesc& d, const double* T, double* Gpart, int nsplit, double* G, double* Ginv,
+                 float* Ginvf, double* sig2, float* Vprev, int warm, unsigned* flags, cudaStream_t s) {
+  k_gram_partial<<<d.p * nsplit, UPD_THREADS, 0, s>>>(d, T, Gpart, nsplit); count_launch();
+  launch_gram_finish(d, Gpart, nsplit, G, Ginv, Ginvf, sig2, Vprev, warm, flags, s);
 }
 
 template <typename Tc>

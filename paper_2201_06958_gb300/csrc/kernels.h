@@ -77,6 +77,7 @@ struct UpdArgs {
   double* gpart;                 // p x gsplit x LD x LD Gram partials (scratch)
   int ntile, gsplit;
   int warm, reorth;
+  int skip_finish;               // phase 7 (G, G^{-1}, sigma^2) left to launch_gram_finish
   unsigned* bar;                 // arrival counter of the grid barriers (zeroed per launch)
   unsigned long long* stamps;    // per-phase timer stamps (profiling), or null
   unsigned* flags;
@@ -123,6 +124,9 @@ inline int gram_split(const int* r, int p, int cap) {
 }
 
 // k_update.cu (standalone Gram refresh)
+// Phase 7 of the update alone (p CTAs): G_n, G_n^{-1}, sigma^(n) from the Gram partials.
+void launch_gram_finish(const ModeDesc& d, const double* Gpart, int nsplit, double* G, double* Ginv, float* Ginvf,
+                        double* sig2, float* Vprev, int warm, unsigned* flags, cudaStream_t s);
 void launch_gram(const ModeDesc& d, const double* T, double* Gpart, int nsplit, double* G, double* Ginv,
                  float* Ginvf, double* sig2, float* Vprev, int warm, unsigned* flags, cudaStream_t s);
 

@@ -154,6 +154,8 @@ struct tdb_ctx {
   uint64_t gkey[2] = {0, 0};
   long long gcount[2] = {0, 0};     // library kernels recorded in each graph (launch counter)
   cudaStream_t cap_stream = nullptr; // steps are recorded here (any stream can replay them)
+  cudaStream_t aux = nullptr;        // second branch of a step (G_n refresh beside the exact error)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool graph_broken = false;
   int64_t graph_replays = 0, graph_records = 0;
 
@@ -171,6 +173,9 @@ struct tdb_ctx {
     for (int i = 0; i < 2; ++i)
       if (gexec[i]) cudaGraphExecDestroy(gexec[i]);
     if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (aux) cudaStreamDestroy(aux);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (ev_join) cudaEventDestroy(ev_join);
     if (rb_pin) cudaFreeHost(rb_pin);
   }
 };
@@ -888,6 +893,8 @@ template <typename Tc>
 tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths) {
   cudaStream_t s = ctx->stream;
   const int p = ctx->p;
+  // exact error on every step: the G_n refresh runs beside it on the context's second stream
+  const bool split = ctx->cfg.error_mode == TDB_ERRMODE_EXACT && ctx->aux && ctx->ev_fork && ctx->ev_join;
   CK(cudaMemsetAsync(ctx->rb_dev, 0, sizeof(Readback), s));
   CK(cudaMemcpyAsync(&ctx->rb_dev->need, ctx->need_pin, sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(ctx->est_dev, ctx->est_pin, sizeof(EstState), cudaMemcpyHostToDevice, s));
@@ -943,6 +950,7 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
     a.gsplit = gram_split(ctx->r, p, ctx->gsplit);
     a.warm = ctx->warm ? 1 : 0;
     a.reorth = ctx->cfg.reorth != 0;
+    a.skip_finish = split ? 1 : 0;
     a.bar = ctx->bar;
     a.stamps = ctx->prof ? ctx->stamps : nullptr;
     a.flags = ctx->flags;
@@ -955,6 +963,26 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
     CHECK_LAUNCH();
   }
   if (ev) CK(cudaEventRecord(ev[2], s));
+  if (split) {
+    // exact error every step: G_n, G_n^{-1}, sigma^(n) and the estimator's features on a
+    // second branch while this one evaluates Eq. 2.20 (neither reads what the other writes)
+    CK(cudaEventRecord(ctx->ev_fork, s));
+    CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+    launch_gram_finish(mode_desc(ctx), ctx->Gpart, gram_split(ctx->r, p, ctx->gsplit), ctx->G, ctx->Ginv, ctx->Ginvf,
+                       ctx->sig2, ctx->Vprev, ctx->warm ? 1 : 0, ctx->flags, ctx->aux);
+    if (!ctx->f64) {
+      int64_t nds = 1;
+      for (int n = 0; n < p; ++n) nds *= ctx->r[n];
+      est_features(ctx->est_dev, (const float*)ctx->dS, (int)nds, &ctx->rb_dev->dv2, ctx->sig2, ctx->r, p, ctx->mlpP,
+                   ctx->mlpNorm, ctx->rb_dev->feat, &ctx->rb_dev->est, &ctx->rb_dev->need, &ctx->rb_dev->ds2, ctx->aux);
+    }
+    CHECK_LAUNCH();
+    TRY(exact_error2<Tc>(ctx, Vn, nullptr));
+    CK(cudaEventRecord(ctx->ev_join, ctx->aux));
+    CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
+    if (ev) CK(cudaEventRecord(ev[3], s));
+    return readback_enqueue(ctx);
+  }
   // a7: error, exact or estimated
   if (!ctx->f64) {
     int64_t nds = 1;
@@ -1238,6 +1266,17 @@ tdb_status common_init(tdb_ctx** out, const tdb_config* cfg, void* ws, size_t ws
     g_init_error = "pinned host memory for the step record unavailable";
     delete ctx;
     return TDB_ERR_CUDA;
+  }
+  // the second branch of exact-error steps (without it those steps run on one stream)
+  if (cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->aux) cudaStreamDestroy(ctx->aux);
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+    ctx->aux = nullptr;
+    ctx->ev_fork = ctx->ev_join = nullptr;
   }
   ctx->est_pin = (EstState*)((char*)ctx->rb_pin + ((sizeof(Readback) + 15) & ~(size_t)15));
   ctx->need_pin = (int*)((char*)ctx->est_pin + ((sizeof(EstState) + 15) & ~(size_t)15));
