@@ -231,7 +231,6 @@ struct EigArgs {
   double* trace;
   unsigned* bar;
   unsigned* flags;
-  int fw;                // warps that factor the Gram (the others form C Z)
   int c_resident;        // one row block per CTA and all of Z staged at once: C rows loaded once
 };
 
@@ -276,32 +275,31 @@ __device__ void sum_gram(const float* __restrict__ Gp, int nb, int gstride, int 
   }
 }
 
-// X (upper triangular, Xs[i + LDM j]) from the Gram Gs on the FW = 4 warps [0, 128).
+// X (upper triangular, Xs[i + LDM j]) from the Gram Gs, on all EIG_THREADS threads.
 // R is the augmented matrix [G^ | I] (m x 2m, element (i, cc) at R[i + LDM cc], the
 // identity block from column m on); Gaussian elimination below the diagonal turns it
-// into [U | E] with E = L^{-1}.  Blocked by FB = 8 pivots (right-looking): warp 0
-// factors the m x FB panel in registers (lane l owns rows l and l + 32, pivot rows by
-// shuffles, multipliers stored below the diagonal); then every thread of the group
-// solves the block rows against L11 (a thread per trailing column) and applies the
-// rank-FB update L21 U12 to the rows below (lane per row, warp per column group).
-// Trailing columns are A's right of the block and E's left of its end: m in all.
-// A pivot that is not positive restarts the elimination with a shifted diagonal
-// (1e-5, then 1e-2: the block's tail columns sit below the float resolution of the
-// spectrum); on the last attempt such a pivot is skipped (multipliers zero) and its
-// column of X is zero.  The panel's verdict reaches the group through shared memory
-// behind a barrier, so the decisions are uniform.
-constexpr int FW = 4, FB = 8;
-__device__ void eig_factor(int m, const float* Gs, float* R, float* Xs, float* dsc, unsigned* flags, int* fail_sh) {
-  constexpr int nthr = FW * 32, CPT = MMAX / FW;
+// into [U | E] with E = L^{-1}.  Step k updates the contiguous window of columns
+// k+1 .. k+m (U right of the pivot, then E up to column k): lane l owns rows l and
+// l + 32, warp w the window columns w, w + 8, ...; the pivot row's and the own row's
+// entries are loaded into registers before the stores.  (The elimination is a chain of
+// m dependent steps; with one warp per SM sub-partition its instruction latency, not
+// its arithmetic, sets the time, so it runs on every warp of the CTA.)  A pivot that
+// is not positive restarts the elimination with a shifted diagonal (1e-5, then 1e-2:
+// the block's tail columns sit below the float resolution of the spectrum); on the
+// last attempt such a column is skipped and its column of X is zero.  Every thread
+// reads the same pivots after a barrier, so the decisions are uniform.
+constexpr int FW = EIG_THREADS / 32;
+__device__ void eig_factor(int m, const float* Gs, float* R, float* Xs, float* dsc, unsigned* flags) {
+  constexpr int CPT = MMAX / FW;
   const int t = threadIdx.x, lane = t & 31, w = t >> 5;
-  for (int i = t; i < m; i += nthr) {
+  for (int i = t; i < m; i += EIG_THREADS) {
     const float g = Gs[i + LDM * i];
     dsc[i] = g > 0.f ? rsqrtf(g) : 1.f;
   }
   bool ok = false;
   for (int attempt = 0; attempt < 3 && !ok; ++attempt) {
     const float shift = attempt == 0 ? 0.f : (attempt == 1 ? 1e-5f : 1e-2f);
-    named_bar(2, nthr);
+    __syncthreads();
     for (int i = lane; i < m; i += 32)
 #pragma unroll
       for (int j = 0; j < 2 * CPT; ++j) {
@@ -310,99 +308,38 @@ __device__ void eig_factor(int m, const float* Gs, float* R, float* Xs, float* d
           R[i + LDM * cc] = cc < m ? Gs[i + LDM * cc] * dsc[i] * dsc[cc] + (i == cc ? shift : 0.f)
                                    : (cc - m == i ? 1.f : 0.f);
       }
-    named_bar(2, nthr);
+    __syncthreads();
     ok = true;
-    for (int kb = 0; kb < m; kb += FB) {
-      const int ke = min(kb + FB, m), nbk = ke - kb;
-      // (1) panel: rows kb.., columns kb .. ke-1, on warp 0
-      if (w == 0) {
-        float pr[2][FB];
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int i = lane + 32 * h;
-#pragma unroll
-          for (int c = 0; c < FB; ++c) pr[h][c] = (i >= kb && i < m && c < nbk) ? R[i + LDM * (kb + c)] : 0.f;
-        }
-        bool fail = false;
-#pragma unroll
-        for (int kr = 0; kr < FB; ++kr) {
-          if (kr < nbk) {
-            const int k = kb + kr, src = k & 31, hk = k >> 5;
-            const float pk = __shfl_sync(0xffffffffu, hk ? pr[1][kr] : pr[0][kr], src);
-            float prow[FB];
-#pragma unroll
-            for (int c = kr + 1; c < FB; ++c) prow[c] = __shfl_sync(0xffffffffu, hk ? pr[1][c] : pr[0][c], src);
-            const bool good = pk > 1e-30f;
-            fail |= !good;
-            const float ip = good ? 1.f / pk : 0.f;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-              const int i = lane + 32 * h;
-              if (i > k && i < m) {
-                const float f = pr[h][kr] * ip;
-                pr[h][kr] = f;
-#pragma unroll
-                for (int c = kr + 1; c < FB; ++c) pr[h][c] = fmaf(-f, prow[c], pr[h][c]);
-              }
-            }
-          }
-        }
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int i = lane + 32 * h;
-          if (i >= kb && i < m)
-#pragma unroll
-            for (int c = 0; c < FB; ++c)
-              if (c < nbk) R[i + LDM * (kb + c)] = pr[h][c];
-        }
-        if (lane == 0) *fail_sh = fail ? 1 : 0;
-      }
-      named_bar(2, nthr);
-      if (*fail_sh) {
+    for (int k = 0; k < m; ++k) {
+      const float piv = R[k + LDM * k];
+      if (!(piv > 1e-30f)) {
         ok = false;
-        if (attempt < 2) break;               // uniform: every thread read the same flag
+        if (attempt < 2) break;
+        continue;
       }
-      // (2) block rows kb .. ke-1: U12 = L11^{-1} R[kb:ke, T], a thread per trailing column
-      const int nA = m - ke;                   // trailing A columns ke .. m-1, then E columns m .. m+ke-1
-      for (int tt = t; tt < m; tt += nthr) {
-        const int col = tt < nA ? ke + tt : m + (tt - nA);
-        float v[FB];
+      const float ip = 1.f / piv;
+      float prow[CPT];
 #pragma unroll
-        for (int q = 0; q < FB; ++q) v[q] = q < nbk ? R[kb + q + LDM * col] : 0.f;
-#pragma unroll
-        for (int q = 1; q < FB; ++q)
-#pragma unroll
-          for (int r = 0; r < q; ++r)
-            if (q < nbk) v[q] = fmaf(-R[kb + q + LDM * (kb + r)], v[r], v[q]);
-#pragma unroll
-        for (int q = 1; q < FB; ++q)
-          if (q < nbk) R[kb + q + LDM * col] = v[q];
+      for (int j = 0; j < CPT; ++j) {
+        const int off = w + FW * j;                    // window column k + 1 + off
+        prow[j] = off < m ? R[k + LDM * (k + 1 + off)] : 0.f;
       }
-      named_bar(2, nthr);
-      // (3) rows ke..m-1: R[i, T] -= L21[i, :] U12, lane per row, warp per column group;
-      // four columns' operands loaded before their stores
-      for (int i = ke + lane; i < m; i += 32) {
-        float L[FB];
+      // rows below k: row_i -= (a_ik / a_kk) row_k over the window
+      for (int i = k + 1 + lane; i < m; i += 32) {
+        const float f = R[i + LDM * k] * ip;
+        float rv[CPT];
 #pragma unroll
-        for (int q = 0; q < FB; ++q) L[q] = q < nbk ? R[i + LDM * (kb + q)] : 0.f;
-        for (int t0 = w; t0 < m; t0 += 4 * FW) {
-          float acc[4];
-          int cols[4];
+        for (int j = 0; j < CPT; ++j) {
+          const int off = w + FW * j;
+          rv[j] = off < m ? R[i + LDM * (k + 1 + off)] : 0.f;
+        }
 #pragma unroll
-          for (int u = 0; u < 4; ++u) {
-            const int tt = t0 + u * FW;
-            cols[u] = tt < nA ? ke + tt : m + (tt - nA);
-            acc[u] = tt < m ? R[i + LDM * cols[u]] : 0.f;
-#pragma unroll
-            for (int q = 0; q < FB; ++q)
-              if (tt < m && q < nbk) acc[u] = fmaf(-L[q], R[kb + q + LDM * cols[u]], acc[u]);
-          }
-#pragma unroll
-          for (int u = 0; u < 4; ++u)
-            if (t0 + u * FW < m) R[i + LDM * cols[u]] = acc[u];
+        for (int j = 0; j < CPT; ++j) {
+          const int off = w + FW * j;
+          if (off < m) R[i + LDM * (k + 1 + off)] = fmaf(-f, prow[j], rv[j]);
         }
       }
-      named_bar(2, nthr);
+      __syncthreads();
     }
   }
   if (!ok && t == 0) atomicOr(flags, kFlagEigNoConv);
@@ -561,7 +498,7 @@ constexpr int EIG_WORK_FLOATS = 5 * MMAX * LDM + 2 * RB * LDM;
 
 __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
   extern __shared__ __align__(16) float smf[];
-  __shared__ int abort_sh, fail_sh, conv_sh;
+  __shared__ int abort_sh, conv_sh;
   __shared__ float dsc[MMAX];
   if (threadIdx.x == 0) abort_sh = 0;
   __syncthreads();
@@ -576,7 +513,6 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
   float* Wr = Ga + MMAX * LDM;            // RB x m rows of C Z
   float* Zr = Wr + RB * LDM;              // RB x m rows of Z
   float* czs = smf + EIG_WORK_FLOATS;     // C Z staging
-  const int t0 = 32 * a.fw, ng = EIG_THREADS - t0;
   unsigned nbar = 0;
   // start: Z = hash columns (a function of the indices only, so the result depends on
   // C alone), partial Grams into Gp[0]
@@ -618,11 +554,11 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
     any = false;
     for (int rb = b; rb < nrb; rb += nb) {
       const int r0 = rb * RB;
-      if (tid < t0) {
-        if (!any) eig_factor(m, Gs, As, Xs, dsc, a.flags, &fail_sh);
-      } else {
-        eig_rows_cz(a, Zc, r0, Wr, czs, ZCH, t0, ng, !(a.c_resident && it > 0));
+      if (!any) {
+        eig_factor(m, Gs, As, Xs, dsc, a.flags);
+        __syncthreads();
       }
+      eig_rows_cz(a, Zc, r0, Wr, czs, ZCH, 0, EIG_THREADS, !(a.c_resident && it > 0));
       __syncthreads();
       if (it < it_last) {
         // Z' = W X for these rows (X upper), and their partial Gram
@@ -650,11 +586,19 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
       __syncthreads();
       any = true;
     }
-    if (!any && tid < t0) eig_factor(m, Gs, As, Xs, dsc, a.flags, &fail_sh);   // (no rows: keeps X defined)
+    if (!any) eig_factor(m, Gs, As, Xs, dsc, a.flags);   // (no rows: keeps X defined)
     store_gram(m, a.gstride, Ga, any, a.Gp[cur ^ 1] + (int64_t)b * a.gstride);
     if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
   }
   const int fin = it_last & 1;            // Z[fin] is the final block; Gp[fin ^ 1] holds M
+  // trace of C (double), on another CTA while CTA 0 runs the Rayleigh-Ritz step
+  if (b == (nb > 1 ? 1 : 0) && tid < 32) {
+    double t = 0.0;
+#pragma unroll 8
+    for (int i = tid; i < n; i += 32) t += __ldcg(&a.C64[i + (int64_t)n * i]);
+    t = warp_sum(t);
+    if (tid == 0) *a.trace = t;
+  }
   // CTA 0: H = X^T M X, Jacobi, ordering; P = X S[:, order] into Xg
   if (b == 0) {
     float* Ms = Gs;
@@ -792,12 +736,6 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
       for (int l = i; l < m; ++l) s = fmaf(Xs[i + LDM * l], Vs[l + LDM * oj], s);
       a.Xg[i + m * j] = s;
     }
-    if (tid < 32) {
-      double t = 0.0;
-      for (int i = tid; i < n; i += 32) t += a.C64[i + (int64_t)n * i];
-      t = warp_sum(t);
-      if (tid == 0) *a.trace = t;
-    }
   }
   if (!eig_grid_sync(a.bar, ++nbar, a.flags, &abort_sh)) return;
   // Ritz vectors Y = Z P (n x k) into W; per-CTA column norms^2 and largest |entry|
@@ -926,8 +864,7 @@ tdb_status eig_si_float(const float* Cc, const double* C64, int n, int k, int it
     smem_cap = (size_t)optin - 2048;
   }
   const int mq = (m + 3) / 4, mp = mq * 4;
-  const int fw = FW;                                 // factor warps
-  const int nls = (EIG_THREADS - 32 * fw) / (4 * mq);
+  const int nls = EIG_THREADS / (4 * mq);
   // C Z staging: ZCH rows of Z (a multiple of 16 when chunked, so float4 runs of C
   // rows stay aligned), C rows and the reduction buffer, after the m x m work area
   auto need = [&](int zch) {
@@ -967,7 +904,6 @@ tdb_status eig_si_float(const float* Cc, const double* C64, int n, int k, int it
   a.trace = trace;
   a.bar = bar;
   a.flags = flags;
-  a.fw = fw;
   a.c_resident = (ZCH >= n && grid == nrb) ? 1 : 0;
   cudaMemsetAsync(bar, 0, sizeof(unsigned), s);
   void* args[] = {(void*)&a, (void*)&ZCH};
