@@ -234,6 +234,17 @@ struct EigArgs {
   int c_resident;        // one row block per CTA and all of Z staged at once: C rows loaded once
 };
 
+__device__ __forceinline__ float frcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float frsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ void named_bar(int id, int nthr) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthr) : "memory");
 }
@@ -643,6 +654,20 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
     __syncthreads();
     const float tol = 1e-6f, thr = 1e-9f;
     float off_prev = 0.f;
+    // the 2 x 2 blocks (I, J) and the V entries (i, J) of this thread, the same in every
+    // round (packed I | J << 8; -1 for none): no index arithmetic inside the rounds
+    const int nb2 = half * half, nv = nn * half;
+    int blk[4], vent[8];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int e = tid + EIG_THREADS * u;
+      blk[u] = e < nb2 ? ((e % half) | ((e / half) << 8)) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = tid + EIG_THREADS * u;
+      vent[u] = e < nv ? ((e % nn) | ((e / nn) << 8)) : -1;
+    }
     for (int sweep = 0; sweep < 40; ++sweep) {
       float off = 0.f, dia = 0.f;
       for (int e = tid; e < nn * nn; e += blockDim.x) {
@@ -677,9 +702,14 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
           // pairs within the block's tail (columns k.. of Q, below the wanted eigenpairs)
           // are left alone: only the leading k rows and columns must be diagonalised
           if ((p < a.k || q < a.k) && apq != 0.f && apq * apq > thr * thr * fabsf(app * aqq)) {
-            const float theta = (aqq - app) / (2.f * apq);
-            const float tt = (theta >= 0.f ? 1.f : -1.f) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
-            c = rsqrtf(tt * tt + 1.f);
+            // t = sign(theta) / (|theta| + sqrt(theta^2 + 1)) with approximate reciprocals:
+            // c = 1 / sqrt(1 + t^2), s = t c keep c^2 + s^2 = 1 whatever t's rounding
+            const float theta = (aqq - app) * frcp_approx(2.f * apq);
+            const float at = fabsf(theta);
+            const float x = fmaf(at, at, 1.f);
+            const float root = (at < 1e18f) ? x * frsqrt_approx(x) : at;
+            const float tt = copysignf(frcp_approx(at + root), theta);
+            c = frsqrt_approx(fmaf(tt, tt, 1.f));
             s = tt * c;
           }
           cs[2 * k] = c;
@@ -688,8 +718,10 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
           pq[2 * k + 1] = q;
         }
         __syncthreads();
-        for (int e = tid; e < half * half; e += blockDim.x) {
-          const int I = e % half, J = e / half;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (blk[u] < 0) continue;
+          const int I = blk[u] & 255, J = blk[u] >> 8;
           const int pI = pq[2 * I], qI = pq[2 * I + 1], pJ = pq[2 * J], qJ = pq[2 * J + 1];
           const float cI = cs[2 * I], sI = cs[2 * I + 1], cJ = cs[2 * J], sJ = cs[2 * J + 1];
           const float b00 = Hs[pI + LDM * pJ], b01 = Hs[pI + LDM * qJ], b10 = Hs[qI + LDM * pJ], b11 = Hs[qI + LDM * qJ];
@@ -700,8 +732,10 @@ __global__ void __launch_bounds__(EIG_THREADS, 1) k_eig_si(EigArgs a, int ZCH) {
           Hs[qI + LDM * pJ] = sI * c00 + cI * c10;
           Hs[qI + LDM * qJ] = sI * c01 + cI * c11;
         }
-        for (int e = tid; e < nn * half; e += blockDim.x) {
-          const int i = e % nn, J = e / nn;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (vent[u] < 0) continue;
+          const int i = vent[u] & 255, J = vent[u] >> 8;
           const int pJ = pq[2 * J], qJ = pq[2 * J + 1];
           const float cJ = cs[2 * J], sJ = cs[2 * J + 1];
           const float vp = Vs[i + LDM * pJ], vq = Vs[i + LDM * qJ];

@@ -301,29 +301,50 @@ __device__ int jacobi_group(float* A, float* V, int n, int max_sweeps, float tol
 // Gauss-Jordan inversion of the SPD matrix in A0 (r x r, ld LD, shared) by the
 // threads [0, nthr) with hardware barrier `bar`, no pivoting (the pivots are the
 // positive Schur-complement diagonals).  Step k reads one buffer and writes the
-// other, so a step needs one barrier; returns the buffer holding the inverse.
-// *ok is false if a pivot is not a positive finite number.
-__device__ double* gj_inverse(double* A0, double* A1, int r, int nthr, int bar, bool* ok) {
+// other, so a step needs one barrier; returns the buffer holding the inverse.  The
+// reciprocal of the next pivot is formed once, by the thread that updates that
+// diagonal entry, into ipk[(k+1) & 1] (FP64 issues one warp-instruction per 64 cycles
+// per SM sub-partition, so every thread forming it would cost the step more than the
+// update itself).  *ok is false if a pivot is not a positive finite number.
+__device__ double* gj_inverse(double* A0, double* A1, int r, int nthr, int bar, bool* ok, double* ipk, int* bad) {
   const int tid = threadIdx.x;
   double* cur = A0;
   double* nxt = A1;
-  bool good = true;
-  for (int k = 0; k < r; ++k) {
-    double p = cur[k + LD * k];
+  auto pivot_rcp = [&](double p, int slot) {
     const int hi = __double2hiint(p);
-    if (hi <= 0 || ((hi >> 20) & 0x7ff) == 0x7ff) { good = false; p = 1.0; }
-    const double ip = drcp(p);
-    for (int e = tid; e < r * r; e += nthr) {
-      const int i = e % r, j = e / r;
+    if (hi <= 0 || ((hi >> 20) & 0x7ff) == 0x7ff) { *bad = 1; p = 1.0; }
+    ipk[slot] = drcp(p);
+  };
+  if (tid == 0) {
+    *bad = 0;
+    pivot_rcp(cur[0], 0);
+  }
+  // this thread's entries (i, j), the same in every step (packed i | j << 8, -1 none)
+  constexpr int EPT = LD * LD / GJ_THREADS;
+  int ent[EPT];
+#pragma unroll
+  for (int u = 0; u < EPT; ++u) {
+    const int e = tid + nthr * u;
+    ent[u] = e < r * r ? ((e % r) | ((e / r) << 8)) : -1;
+  }
+  named_bar(bar, nthr);
+  for (int k = 0; k < r; ++k) {
+    const double ip = ipk[k & 1];
+#pragma unroll
+    for (int u = 0; u < EPT; ++u) {
+      if (ent[u] < 0) continue;
+      const int i = ent[u] & 255, j = ent[u] >> 8;
       const double akj = (j == k) ? ip : cur[k + LD * j] * ip;     // row k after the step
-      nxt[i + LD * j] = (i == k) ? akj : (j == k ? 0.0 : cur[i + LD * j]) - cur[i + LD * k] * akj;
+      const double v = (i == k) ? akj : (j == k ? 0.0 : cur[i + LD * j]) - cur[i + LD * k] * akj;
+      nxt[i + LD * j] = v;
+      if (i == k + 1 && j == k + 1) pivot_rcp(v, (k + 1) & 1);
     }
     named_bar(bar, nthr);
     double* t = cur;
     cur = nxt;
     nxt = t;
   }
-  *ok = good;
+  *ok = *bad == 0;
   return cur;
 }
 
@@ -435,8 +456,9 @@ __device__ __noinline__ void gram_finish(const ModeDesc& d, int n, const double*
   int* slot = pq + 64;                 // LD
   double* GW = Ai;
   double* Wd = (double*)Af;
-  __shared__ int bad_sh;
+  __shared__ int bad_sh, gjbad_sh;
   __shared__ float scale_sh;
+  __shared__ double ipk_sh[2];
   const int tid = threadIdx.x, wid = tid >> 5, lane = tid & 31;
   constexpr int JG = 256;              // Jacobi group: threads [JG, 2 JG)
   float* Vp = Vprev + (int64_t)n * LD * LD;
@@ -469,7 +491,7 @@ __device__ __noinline__ void gram_finish(const ModeDesc& d, int n, const double*
   __shared__ double* inv_sh;
   if (tid < GJ_THREADS) {
     bool good;
-    double* res = gj_inverse(Ai, Ai2, r, GJ_THREADS, 1, &good);
+    double* res = gj_inverse(Ai, Ai2, r, GJ_THREADS, 1, &good, ipk_sh, &gjbad_sh);
     if (tid == 0) {
       inv_sh = res;
       if (!good) bad_sh = 1;

@@ -815,7 +815,7 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
     err = std::string("k_tc_project launch: ") + cudaGetErrorString(e);
     return TDB_ERR_CUDA;
   }
-  if (tc_defers_ds(p, r)) {
+  if (tc_defers_ds(p, N, r)) {
     // two launches: the partial sums with Y_2, Y_1 and ||dV||^2, then Y_3; dS follows in
     // the update kernel (defer_ds) or as one mode product here
     const int64_t ntile = ((int64_t)r[0] * N2 + FA_TE - 1) / FA_TE + ((int64_t)N1 * r[1] + FA_TE - 1) / FA_TE;

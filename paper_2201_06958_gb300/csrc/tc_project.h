@@ -20,8 +20,10 @@ struct TcPlan {
 };
 
 bool tc_supported(int p, const int64_t* N, const int* cap, std::string& err);
-// Three modes (r_3 <= 32): tc_project leaves dS = Y_3 x_3 A_3^T to the update kernel.
-inline bool tc_defers_ds(int p, const int* r) { return p == 3 && r[2] <= 32; }
+// Three modes with few slices (N_3 <= 64, r_3 <= 32): tc_project finishes with the two
+// fused launches (each CTA walks all slices, so many slices would serialise them) and
+// leaves dS = Y_3 x_3 A_3^T to the update kernel.
+inline bool tc_defers_ds(int p, const int64_t* N, const int* r) { return p == 3 && N[2] <= 64 && r[2] <= 32; }
 void tc_carve(TcPlan& plan, Carver& cv, int p, const int64_t* N, const int* cap);
 // dS (unless tc_defers_ds) and Y_n of dV = Vn - Vp (Eqs. 2.15, 2.16) and ||dV||_W^2 into *dv2.  A: FP32
 // weighted bases (N_n x r_n); w: mode weights; Z1 (r1 x N2 x S), Z2 (N1 x r2 x S)

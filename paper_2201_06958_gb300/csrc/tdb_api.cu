@@ -932,7 +932,7 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
       ntiles += (ctx->N[n] + 31) / 32;
     }
     a.dS = ctx->dS;
-    a.y3 = (ctx->use_tc && tc_defers_ds(p, ctx->r)) ? ctx->Y[2] : nullptr;
+    a.y3 = (ctx->use_tc && tc_defers_ds(p, ctx->N, ctx->r)) ? ctx->Y[2] : nullptr;
     a.dS_out = ctx->dS;
     a.T = ctx->T;
     a.T2 = ctx->T2;
