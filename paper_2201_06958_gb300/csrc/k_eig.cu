@@ -199,6 +199,7 @@ __global__ void k_syrk_finish(int64_t Nn, int ntile, int ksplit, const double* _
     if (ti == tj && x > y) { const int t = x; x = y; y = t; }
     double s = 0.0;
     const double* src = part + (int64_t)pair * ksplit * SY_T * SY_T + x + SY_T * y;
+#pragma unroll 8
     for (int k = 0; k < ksplit; ++k) s += src[(int64_t)k * SY_T * SY_T];
     C64[e] = s;
     Cc[e] = (float)s;

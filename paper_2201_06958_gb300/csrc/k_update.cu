@@ -469,6 +469,7 @@ __device__ __noinline__ void gram_finish(const ModeDesc& d, int n, const double*
     if (ra < r && rb < r) {
       const int aa = ra <= rb ? ra : rb, bb = ra <= rb ? rb : ra;
       const double* src = gpart + (int64_t)n * gsplit * LD * LD + aa + LD * bb;
+#pragma unroll 8
       for (int k = 0; k < gsplit; ++k) s += __ldcg(&src[(int64_t)k * LD * LD]);
     }
     G[e] = s;
@@ -682,6 +683,7 @@ __device__ void rows_u1(const UpdArgs& a, int n, int64_t i0, int tile, unsigned 
     Tc s = Tc(0);
     if (ra < r && rb < r) {
       const Tc* src = part + (int64_t)n * a.ntile * LD * LD + e;
+#pragma unroll 8
       for (int t = 0; t < nt; ++t) s += __ldcg(&src[(int64_t)t * LD * LD]);
     }
     Psh[e] = s;
@@ -733,6 +735,7 @@ __device__ void mode_cholqr(const UpdArgs& a, int n, unsigned char* sm) {
       const int ra = e % LD, rb = e / LD;
       double s = 0.0;
       if (ra < r && rb < r)
+#pragma unroll 8
         for (int t = 0; t < nt; ++t) s += (double)__ldcg(&part[(int64_t)t * LD * LD + e]);
       C[e] = s;
     }
@@ -755,6 +758,7 @@ __device__ void mode_cholqr(const UpdArgs& a, int n, unsigned char* sm) {
       const int ra = e % LD, rb = e / LD;
       float s = 0.f;
       if (ra < r && rb < r)
+#pragma unroll 8
         for (int t = 0; t < nt; ++t) s += (float)__ldcg(&part[(int64_t)t * LD * LD + e]);
       Cf[e] = s;
     }
