@@ -39,7 +39,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="tdb", choices=["tdb", "reference"])
     ap.add_argument("--workload", default="reactive",
-                    choices=["reactive", "stochastic", "channel", "analytic", "batch"])
+                    choices=["reactive", "stochastic", "channel", "analytic", "runge", "batch"])
     ap.add_argument("--precision", default="auto", choices=["auto", "bf16", "fp32", "fp64"])
     ap.add_argument("--error-mode", default="auto", choices=["auto", "exact", "mlp", "every_k"])
     ap.add_argument("--train-steps", type=int, default=300,
@@ -277,7 +277,7 @@ def workload_desc(name):
     return {"workload": f"{name} {dims} {wl.dtype}, rank<= {wl.rank_max}, eps_th={wl.eps_th:g}, "
                         f"gamma_th={wl.gamma_th}%, {wl.steps}-step stream",
             "dims": wl.dims, "rank_max": wl.rank_max, "eps_th": wl.eps_th, "gamma_th": wl.gamma_th,
-            "seed": 1000 + ["analytic", "reactive", "stochastic", "channel"].index(name) + 1}
+            "seed": S.default_seed(name)}
 
 
 # ---------------------------------------------------------------------------
@@ -479,7 +479,7 @@ def train_estimator(args, wl, precision, dev, tdb, S):
     """Fit the error estimator on a separate stream of the same workload (another seed),
     evaluated exactly every step; returns (parameters, report).  Not timed."""
     import torch
-    tseed = 8001 + ["analytic", "reactive", "stochastic", "channel"].index(args.workload)
+    tseed = 7000 + S.default_seed(args.workload)
     wt = S.make_workload(args.workload, seed=tseed)
     c = tdb.TDB(wt.dims, wt.rank, rank_max=wt.rank_max, weights=wt.weights, eps_th=wt.eps_th,
                 gamma_th=wt.gamma_th, precision=precision, error_mode="exact", device=dev)

@@ -180,6 +180,31 @@ def test_rank_control_decisions_match_oracle(tdbmod):
 
 
 @cuda
+def test_runge_adaptive_ranks_match_oracle(tdbmod):
+    """The Runge function of Sec. 3.1 (48^3, t in [0, 2]) through the FP64 path with rank
+    adaptivity: every step's action and ranks equal the oracle controller's, ε within
+    1e-8 relative, and the ranks rise before t = 1 and fall after."""
+    wl = S.make_workload("runge", n=48)
+    w = wl.weights
+    snaps = [wl.snapshot(k, device="cuda") for k in range(0, wl.steps + 1)]
+    logical = [S.to_logical(x) for x in snaps]
+    ctrl = O.ControllerConfig(wl.eps_th, wl.gamma_th, 10, wl.rank_max)
+    _, recs = O.compress_stream(logical, w, [0, 0, 0], ctrl)
+    c = tdbmod.TDB(wl.dims, [0, 0, 0], rank_max=wl.rank_max, weights=w, eps_th=wl.eps_th, gamma_th=wl.gamma_th,
+                   slope_window=10, precision="fp64", error_mode="exact")
+    c.init(snaps[0])
+    totals = []
+    for k in range(1, wl.steps + 1):
+        info = c.push(snaps[k])
+        rec = recs[k - 1]
+        assert info["action"] == rec.action, (k, info["action"], rec.action)
+        assert info["ranks"] == rec.ranks, (k, info["ranks"], rec.ranks)
+        assert abs(info["eps"] - rec.eps) <= 1e-8 * rec.eps, (k, info["eps"], rec.eps)
+        totals.append(sum(info["ranks"]))
+    assert max(totals) > totals[0] and totals[-1] < max(totals)
+
+
+@cuda
 def test_save_load_resume_is_bit_identical(tdbmod):
     wl = S.make_workload("reactive", nx=64, ny=48, ns=6)
     snaps = [wl.snapshot(k, device="cuda") for k in range(0, 13)]

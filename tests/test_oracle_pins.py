@@ -408,6 +408,42 @@ def test_controller_decrease_and_revert():
     assert eps0 < 1e-3
 
 
+def test_runge_field_and_derivative_closed_form():
+    """The Runge workload is Eq. 3.1's function itself: values at grid points and the
+    analytic time derivative against a central difference."""
+    wl = S.make_workload("runge", n=9)
+    x = np.linspace(-math.pi, math.pi, 9)
+    t = 0.37
+    a = 1.0 - 0.5 * math.exp(-0.5 * (t - 1.0) ** 2)
+    V = S.to_logical(wl._field(t, torch.device("cpu")))
+    for (i, j, k) in [(0, 0, 0), (4, 4, 4), (1, 7, 3), (8, 2, 5)]:
+        assert V[i, j, k] == pytest.approx(1.0 / (a * a + x[i] ** 2 + x[j] ** 2 + x[k] ** 2), rel=1e-14)
+    h = 1e-5
+    fd = (S.to_logical(wl._field(t + h, torch.device("cpu"))) - S.to_logical(wl._field(t - h, torch.device("cpu")))) / (2 * h)
+    dV = S.to_logical(wl.snapshot_dot(t))
+    assert np.abs(fd - dV).max() <= 1e-8 * np.abs(dV).max()
+
+
+def test_runge_ranks_rise_towards_t1_and_fall_after():
+    """Sec. 3.1: with a(t) = 1 - 0.5 exp(-0.5 (t-1)^2) the rank that keeps the error
+    below the threshold must grow from t = 0 to t = 1 and shrink after.  The oracle's
+    controller on the function over t in [0, 2] (48^3 grid; the spectrum does not
+    depend on the grid at this resolution) adds modes before t = 1, removes them after,
+    and keeps every step's error at or below eps_th."""
+    wl = S.make_workload("runge", n=48)
+    snaps = [S.to_logical(wl.snapshot(k)) for k in range(0, wl.steps + 1)]
+    ctrl = O.ControllerConfig(wl.eps_th, wl.gamma_th, 10, wl.rank_max)
+    _, recs = O.compress_stream(snaps, wl.weights, [0, 0, 0], ctrl)
+    total = [sum(r.ranks) for r in recs]
+    t_of = lambda i: (i + 1) * wl.dt
+    up = [i for i in range(1, len(recs)) if total[i] > total[i - 1]]
+    down = [i for i in range(1, len(recs)) if total[i] < total[i - 1]]
+    assert up and down, (up, down)
+    assert all(t_of(i) <= 1.0 for i in up) and all(t_of(i) > 1.0 for i in down), (up, down)
+    assert max(total) > total[0] and total[-1] < max(total)
+    assert all(r.eps <= wl.eps_th for r in recs)
+
+
 # ---------------------------------------------------------------------------
 # The estimator network's reference (textbook back-propagation and Adam)
 # ---------------------------------------------------------------------------
