@@ -19,6 +19,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -50,6 +51,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    ap.add_argument("--scaling-sweep", action="store_true",
+                    help="TDB step vs on-GPU HOSVD over N^3 grids of the Runge function (one JSON line)")
     return ap.parse_args()
 
 
@@ -634,8 +637,59 @@ def run_batch(args, world, rank, local):
         print(json.dumps(line))
 
 
+def run_scaling_sweep(args):
+    """Cost of one TDB step against one HOSVD re-initialisation over N^3 grids (the paper's
+    Sec. 2.6 claim: the step grows like S = N^3, the HOSVD like N^4 = S^(4/3) through its
+    mode Grams).  Runge function of Sec. 3.1 at t = 1, FP32 snapshots, BF16 projection,
+    fixed ranks (6, 6, 6); CUDA-event times averaged over `steps` pushes and 5 HOSVDs."""
+    import torch
+
+    from paper_2201_06958_gb300 import build_lib, synth as S, tdb
+    build_lib.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    rows = []
+    K = max(10, min(args.steps, 100))
+    for n in (32, 48, 64, 96, 128, 192, 256):
+        wl = S.make_workload("runge", n=n)
+        snaps = [wl.snapshot(200 + k, device=dev, dtype=torch.float32) for k in range(K + 2)]
+        c = tdb.TDB(wl.dims, [6, 6, 6], rank_max=[8, 8, 8], weights=wl.weights, eps_th=0.0, precision="bf16",
+                    error_mode="exact", device=dev).init(snaps[0])
+        for k in range(1, 3):
+            c.push(snaps[k])
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for k in range(2, K + 2):
+            c.push(snaps[k])
+        e1.record()
+        torch.cuda.synchronize()
+        step_ms = e0.elapsed_time(e1) / K
+        e0.record()
+        for _ in range(5):
+            c.reinit(snaps[K + 1])
+        e1.record()
+        torch.cuda.synchronize()
+        hosvd_ms = e0.elapsed_time(e1) / 5
+        c.close()
+        rows.append({"N": n, "S": n ** 3, "step_ms": step_ms, "hosvd_ms": hosvd_ms})
+    lg = lambda v: [math.log(x) for x in v]
+    big = [r for r in rows if r["N"] >= 96]
+    def slope(key):
+        xs, ys = lg([r["S"] for r in big]), lg([r[key] for r in big])
+        mx, my = sum(xs) / len(xs), sum(ys) / len(ys)
+        return sum((x - mx) * (y - my) for x, y in zip(xs, ys)) / sum((x - mx) ** 2 for x in xs)
+    print(json.dumps({"metric": "TDB step vs HOSVD re-initialisation time over N^3 (Runge function, BF16 projection)",
+                      "unit": "ms", "rows": rows,
+                      "exponent_in_S_for_N_ge_96": {"step": slope("step_ms"), "hosvd": slope("hosvd_ms")},
+                      "data": "synthetic", "config": {"workload": "runge N^3, t = 1, ranks (6, 6, 6) fixed"}}))
+
+
 def main():
     args = parse_args()
+    if args.scaling_sweep:
+        run_scaling_sweep(args)
+        return
     world, rank, local = dist_setup() if args.impl == "tdb" else (
         int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")), 0)
     if args.impl == "reference":

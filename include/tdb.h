@@ -150,6 +150,15 @@ tdb_status tdb_reconstruct(tdb_ctx* ctx, void* V_out);
  * host int[p] (nullable); eps_out: host (nullable).  Synchronises. */
 tdb_status tdb_adapt_rank(tdb_ctx* ctx, const void* V_now, int* ranks_out, double* eps_out);
 
+/* Re-initialise the state from V_now (device snapshot, same layout and type as the
+ * pushes) by the truncated HOSVD at the current ranks (Sec. 2.3 end, Sec. 2.5): U_n =
+ * W_n^{-1/2} times the leading eigenvectors of the weighted mode-n Gram, T the Eq. 2.15
+ * projection of V_now.  V_now becomes the previous snapshot of the next push (it must
+ * stay unmodified until then, as for tdb_push_snapshot).  Clears the slope window of the
+ * rank rule.  Synchronises the stream.  Errors: TDB_ERR_INVALID_ARG (null ctx or
+ * snapshot), TDB_ERR_STATE (before init), TDB_ERR_TIMEOUT / TDB_ERR_CUDA (device). */
+tdb_status tdb_reinit(tdb_ctx* ctx, const void* V_now);
+
 /* Copy the current factors to host memory: core (prod r_n doubles) and U[n]
  * (N_n x r_n doubles each); any of them may be NULL.  ranks: host int[p]
  * (nullable).  Synchronises. */

@@ -1428,6 +1428,27 @@ tdb_status tdb_adapt_rank(tdb_ctx* ctx, const void* V_now, int* ranks_out, doubl
   return st;
 }
 
+tdb_status tdb_reinit(tdb_ctx* ctx, const void* V_now) {
+  if (!ctx) return TDB_ERR_INVALID_ARG;
+  if (!ctx->ready) { ctx->err = "reinit before init"; return TDB_ERR_STATE; }
+  if (!V_now) { ctx->err = "null snapshot"; return TDB_ERR_INVALID_ARG; }
+  auto run = [&](auto tag) -> tdb_status {
+    using Tc = decltype(tag);
+    const Tc* V = (const Tc*)V_now;
+    std::vector<int> r(ctx->r, ctx->r + ctx->p);
+    TRY(hosvd_spectrum<Tc>(ctx, V));
+    TRY(hosvd_state<Tc>(ctx, V, r.data()));
+    return readback(ctx);
+  };
+  const tdb_status st = ctx->f64 ? run(double()) : run(float());
+  if (st == TDB_OK) {
+    ctx->history.clear();
+    ctx->reinits += 1;
+    ctx->V_prev = V_now;
+  }
+  return st;
+}
+
 tdb_status tdb_get_factors(tdb_ctx* ctx, double* core, double* const* U, int* ranks) {
   if (!ctx) return TDB_ERR_INVALID_ARG;
   if (!ctx->ready) { ctx->err = "not initialised"; return TDB_ERR_STATE; }

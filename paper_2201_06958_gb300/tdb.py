@@ -71,7 +71,7 @@ _lib = None
 
 EXPORTS = [
     "tdb_workspace_bytes", "tdb_init", "tdb_init_from_factors", "tdb_push_snapshot", "tdb_reconstruct",
-    "tdb_adapt_rank", "tdb_get_factors", "tdb_get_projection", "tdb_get_counters", "tdb_save_state",
+    "tdb_adapt_rank", "tdb_reinit", "tdb_get_factors", "tdb_get_projection", "tdb_get_counters", "tdb_save_state",
     "tdb_load_state", "tdb_last_error", "tdb_status_string", "tdb_destroy", "tdb_version",
     "tdb_set_profiling", "tdb_get_profile", "tdb_kernel_launches", "tdb_project_noalloc",
     "tdb_mlp_param_count", "tdb_mlp_forward", "tdb_mlp_loss_grad", "tdb_mlp_adam_step", "tdb_estimator_fit",
@@ -103,6 +103,8 @@ def load(path: str = LIB_PATH):
     lib.tdb_reconstruct.restype = st
     lib.tdb_adapt_rank.argtypes = [vp, vp, C.POINTER(C.c_int), C.POINTER(C.c_double)]
     lib.tdb_adapt_rank.restype = st
+    lib.tdb_reinit.argtypes = [vp, vp]
+    lib.tdb_reinit.restype = st
     lib.tdb_get_factors.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.POINTER(C.c_double)), C.POINTER(C.c_int)]
     lib.tdb_get_factors.restype = st
     lib.tdb_get_projection.argtypes = [vp, C.POINTER(C.c_double), C.POINTER(C.POINTER(C.c_double))]
@@ -312,6 +314,13 @@ class TDB:
             out = torch.empty(self.storage_shape, dtype=self.dtype, device=self.device)
         self._check(self.lib.tdb_reconstruct(self.ctx, C.c_void_p(self._snap(out).data_ptr())))
         return out
+
+    def reinit(self, V: torch.Tensor):
+        """Truncated HOSVD of V at the current ranks (tdb_reinit); V becomes the previous snapshot."""
+        V = self._snap(V)
+        self._check(self.lib.tdb_reinit(self.ctx, C.c_void_p(V.data_ptr())))
+        self._prev = V
+        return self
 
     def adapt_rank(self, V: torch.Tensor):
         V = self._snap(V)

@@ -205,6 +205,29 @@ def test_runge_adaptive_ranks_match_oracle(tdbmod):
 
 
 @cuda
+def test_reinit_is_the_oracle_hosvd(tdbmod):
+    """tdb_reinit re-initialises from a snapshot by the truncated HOSVD at the current
+    ranks (Sec. 2.3 end): after two steps, the state equals the oracle's HOSVD of that
+    snapshot to 1e-10 (FP64), with W-orthonormal bases, and a following push runs."""
+    rng = np.random.default_rng(41)
+    dims, ranks = (37, 29, 23), (3, 4, 2)
+    w, U, T = rand_case(rng, dims, ranks)
+    Vs = [O.reconstruct(T, U) + 1e-3 * k * rng.standard_normal(dims) for k in range(4)]
+    dev = [S.from_logical(v, dtype=torch.float64, device="cuda") for v in Vs]
+    c = tdbmod.TDB(dims, ranks, weights=w, precision="fp64", error_mode="exact").init(dev[0])
+    c.push(dev[1])
+    c.push(dev[2])
+    c.reinit(dev[3])
+    Tg, Ug = c.factors()
+    To, Uo, _ = O.hosvd(Vs[3], w, list(ranks))
+    assert rel(O.reconstruct(Tg, Ug), O.reconstruct(To, Uo)) <= 1e-10
+    for n in range(3):
+        assert np.abs(Ug[n].T @ (w[n][:, None] * Ug[n]) - np.eye(ranks[n])).max() <= 1e-12
+    info = c.push(dev[2])
+    assert info["ranks"] == list(ranks)
+
+
+@cuda
 def test_save_load_resume_is_bit_identical(tdbmod):
     wl = S.make_workload("reactive", nx=64, ny=48, ns=6)
     snaps = [wl.snapshot(k, device="cuda") for k in range(0, 13)]
