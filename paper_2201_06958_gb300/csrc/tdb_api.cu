@@ -618,7 +618,7 @@ tdb_status hosvd_spectrum(tdb_ctx* ctx, const Tc* V) {
       CHECK_LAUNCH();
       const int Nn = (int)ctx->N[n];
       tdb_status st;
-      if (Nn <= 96)
+      if (Nn <= 48)   // (the single-CTA Jacobi is slower than the subspace iteration above ~48)
         st = eig_leading_small<float>((const float*)ctx->Cc, ctx->C64, Nn, ctx->kcap[n], (float*)ctx->jA,
                                       (float*)ctx->jV, ctx->flags, ctx->ev[n], ctx->Qeig[n], ctx->trace + n,
                                       ctx->eigscratch, s);

@@ -49,7 +49,8 @@ def case(rng, dims, inner):
 @cuda
 @pytest.mark.parametrize("dims,ranks", [
     ((200, 130, 12), (6, 5, 4)),     # modes 1 and 2 through the subspace iteration, ragged row blocks
-    ((512, 64, 12), (12, 10, 6)),    # the reactive mode-1 size; mode 2 through the single-CTA Jacobi
+    ((512, 64, 12), (12, 10, 6)),    # the reactive mode-1 size; mode 2 (N = 64) also through the subspace iteration
+    ((40, 36, 12), (5, 5, 4)),       # every mode through the single-CTA Jacobi (N <= 48)
 ])
 def test_float_hosvd_init_matches_oracle(tdbmod, dims, ranks):
     rng = np.random.default_rng(301)
