@@ -387,6 +387,81 @@ __global__ void k_mp_reduce_col(const Tin* __restrict__ in, Tacc* __restrict__ o
   }
 }
 
+// K large, Q == 1, J <= 32: out (L x J) = in (L x K) M^T as a tiled product.  A CTA
+// owns 64 consecutive l and all j; K in chunks of 32 staged in shared memory (in along
+// l: coalesced; M once per chunk), the next chunk loaded into registers while the
+// current one is multiplied; thread (tl, tj) accumulates l = 4 tl .. 4 tl + 3 and
+// j = 2 tj, 2 tj + 1.  Fixed summation order over k.
+template <typename Tin, typename Tm, typename Tacc>
+__global__ void __launch_bounds__(256) k_mp_gemm(const Tin* __restrict__ in, Tacc* __restrict__ out,
+                                                 const Tm* __restrict__ M, int64_t L, int K, int J, int64_t sMj,
+                                                 int64_t sMk) {
+  constexpr int BM = 64, BK = 32;
+  __shared__ Tacc As[BK][BM + 1];
+  __shared__ Tacc Bs[BK][33];
+  const int tid = threadIdx.x;
+  const int tl = tid & 15, tj = tid >> 4;
+  for (int64_t l0 = blockIdx.x * (int64_t)BM; l0 < L; l0 += (int64_t)gridDim.x * BM) {
+    Tacc acc[4][2];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) acc[x][0] = acc[x][1] = Tacc(0);
+    // register staging of one chunk: 8 entries of in, 4 of M per thread
+    Tacc ra[8], rb[4];
+    auto fetch = [&](int k0) {
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = tid + 256 * u, i = e % BM, kk = e / BM;
+        const int64_t l = l0 + i;
+        const int k = k0 + kk;
+        ra[u] = (l < L && k < K) ? (Tacc)in[l + L * (int64_t)k] : Tacc(0);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = tid + 256 * u, j = e % 32, kk = e / 32;
+        const int k = k0 + kk;
+        rb[u] = (j < J && k < K) ? (Tacc)M[j * sMj + (int64_t)k * sMk] : Tacc(0);
+      }
+    };
+    fetch(0);
+    for (int k0 = 0; k0 < K; k0 += BK) {
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int e = tid + 256 * u;
+        As[e / BM][e % BM] = ra[u];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int e = tid + 256 * u;
+        Bs[e / 32][e % 32] = rb[u];
+      }
+      __syncthreads();
+      if (k0 + BK < K) fetch(k0 + BK);
+#pragma unroll 8
+      for (int kk = 0; kk < BK; ++kk) {
+        Tacc a[4], b[2];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) a[x] = As[kk][4 * tl + x];
+        b[0] = Bs[kk][2 * tj];
+        b[1] = Bs[kk][2 * tj + 1];
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+          acc[x][0] = fma(a[x], b[0], acc[x][0]);
+          acc[x][1] = fma(a[x], b[1], acc[x][1]);
+        }
+      }
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 2; ++y) {
+        const int64_t l = l0 + 4 * tl + x;
+        const int j = 2 * tj + y;
+        if (l < L && j < J) out[l + L * (int64_t)j] = acc[x][y];
+      }
+  }
+}
+
 // K large, L > 1: one thread per (l, q), l fastest (coalesced over l).
 template <typename Tin, typename Tm, typename Tacc, int JT>
 __global__ void k_mp_reduce_gen(const Tin* __restrict__ in, Tacc* __restrict__ out, const Tm* __restrict__ M,
@@ -506,6 +581,9 @@ void launch_modeprod(const Tin* in, Tacc* out, const Tm* M, int64_t L, int K, in
     int64_t total = L * J * Q;
     int blocks = (int)std::min<int64_t>((total + 255) / 256, 152 * 32);
     k_mp_expand<Tin, Tm, Tacc><<<blocks, 256, 0, s>>>(in, out, M, L, K, J, Q, sMj, sMk, gate);
+  } else if (Q == 1 && L >= 64 && J <= 32) {
+    const int blocks = (int)std::min<int64_t>((L + 63) / 64, 152 * 8);
+    k_mp_gemm<Tin, Tm, Tacc><<<blocks, 256, 0, s>>>(in, out, M, L, K, J, sMj, sMk);
   } else if (L > 1 && L * Q <= 1024) {
     int blocks = (int)std::min<int64_t>(L * Q, 152 * 8);
     if (J <= 8)
