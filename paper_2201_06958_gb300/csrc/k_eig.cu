@@ -209,10 +209,9 @@ __global__ void k_syrk_finish(int64_t Nn, int ntile, int ksplit, const double* _
 // ---------------------------------------------------------------------------
 // Eigensolver.  Every CTA owns row blocks of 16 rows (CTA b: blocks b, b + nb, ...).
 // Iteration: Z <- C Q with Q = Z X and X^T (Z^T Z) X = I.  Each CTA sums the
-// per-CTA partial Grams of Z itself and factors the m x m Gram (one or two warps)
-// while its other warps form W = C Z for its rows; then Z' = W X and the partial
-// Gram of Z' for its rows.  Z and the partials are double-buffered, so an
-// iteration takes one grid barrier.  X comes from Gaussian elimination of the
+// per-CTA partial Grams of Z itself, factors the m x m Gram, forms W = C Z for its
+// rows, then Z' = W X and the partial Gram of Z' for its rows.  Z and the partials
+// are double-buffered, so an iteration takes one grid barrier.  X comes from Gaussian elimination of the
 // diagonally scaled Gram without pivoting: [G^ | I] -> [U | E], G^ = E^{-1} D_u E^{-T},
 // X = D^{-1} E^T D_u^{-1/2} (shifted diagonal retried if a pivot fails).  Every CTA
 // runs the same instructions on the same data, so all hold the same X.
