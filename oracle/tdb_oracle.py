@@ -33,7 +33,7 @@ import numpy as np
 
 __all__ = [
     "unfold", "fold", "mode_product", "multi_mode_product", "weighted_bases",
-    "project", "core_gram", "basis_rhs", "tdb_rhs", "step_euler", "step_rk4",
+    "project", "core_gram", "basis_rhs", "tdb_rhs", "step_euler", "step_heun", "step_rk4",
     "cholqr", "reconstruct", "weighted_norm2", "error_exact",
     "hosvd_spectrum", "hosvd", "rank_from_spectrum", "rank_from_core",
     "core_singular_values", "gamma_percent", "rotate_coherent",
@@ -160,6 +160,26 @@ def step_euler(T, U, w, V_k, V_k1, reorth: bool = True):
     if reorth:
         T1, U1 = cholqr(T1, U1, w)
     return T1, U1, dS, Y
+
+
+def step_heun(T, U, w, V_k, V_k1, reorth: bool = True):
+    """One step of Heun's second-order Runge-Kutta scheme on the same equations, with the
+    data forcing taken from the piecewise-linear interpolant of the snapshots (both stages
+    use the step's difference V_k1 - V_k; the paper's Sec. 3.1 compares this family of
+    schemes with Euler).  Stage 1 is the Euler increment at the state of step k, stage 2
+    the increment at the predicted state; the step takes their mean, then re-orthonormalises
+    (reading C4; the predicted state is an intermediate of the scheme and is not).
+    Returns (T', U')."""
+    dV = V_k1 - V_k
+    k1T, k1U = tdb_rhs(T, U, w, dV)
+    Tp = T + k1T
+    Up = [U[n] + k1U[n] for n in range(T.ndim)]
+    k2T, k2U = tdb_rhs(Tp, Up, w, dV)
+    T1 = T + 0.5 * (k1T + k2T)
+    U1 = [U[n] + 0.5 * (k1U[n] + k2U[n]) for n in range(T.ndim)]
+    if reorth:
+        T1, U1 = cholqr(T1, U1, w)
+    return T1, U1
 
 
 def step_rk4(T, U, w, t: float, dt: float, vdot, reorth: bool = True):
