@@ -43,6 +43,8 @@ def parse_args():
                     choices=["reactive", "stochastic", "channel", "analytic", "runge", "batch"])
     ap.add_argument("--precision", default="auto", choices=["auto", "bf16", "fp32", "fp64"])
     ap.add_argument("--error-mode", default="auto", choices=["auto", "exact", "mlp", "every_k"])
+    ap.add_argument("--integrator", default="euler", choices=["euler", "heun"],
+                    help="heun: two projection passes per snapshot (second-order scheme)")
     ap.add_argument("--train-steps", type=int, default=300,
                     help="steps of the separate training stream for the error estimator")
     ap.add_argument("--api", default="slots", choices=["slots", "pointer"],
@@ -328,7 +330,8 @@ def run_tdb(args, world, rank, local):
 
     def make(prec, mode):
         c = tdb.TDB(wl.dims, wl.rank, rank_max=wl.rank_max, weights=wl.weights, eps_th=wl.eps_th,
-                    gamma_th=wl.gamma_th, precision=prec, error_mode=mode, error_every=20, device=dev)
+                    gamma_th=wl.gamma_th, precision=prec, error_mode=mode, error_every=20,
+                    integrator=args.integrator, device=dev)
         return c
 
     def run(prec, timed_profile=True, mode=None, api=None):
@@ -440,6 +443,7 @@ def run_tdb(args, world, rank, local):
         "ms_per_step": ms_total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"bf16": "bf16", "fp32": "f32", "fp64": "f64"}[precision], "data": "synthetic",
         "config": dict(workload_desc(args.workload), precision=precision, error_mode=err_mode, api=args.api,
+                       integrator=args.integrator,
                        l2=("streamed inputs larger than L2: every step reads a new snapshot "
                            f"({esz * S_el / 1e6:.1f} MB) from a {nsnap * esz * S_el / 1e9:.2f} GB device-resident "
                            "stream; the previous snapshot is the one read in the step before"),
@@ -470,9 +474,10 @@ def run_tdb(args, world, rank, local):
 
     # end to end through the C ABI from pinned host buffers
     if not args.no_e2e:
-        line["e2e"] = run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_params, args.api)
+        line["e2e"] = run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_params, args.api,
+                              args.integrator)
 
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.integrator == "euler":
         line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample_seconds, K)
     if rank == 0:
         print(json.dumps(line))
@@ -502,13 +507,15 @@ def train_estimator(args, wl, precision, dev, tdb, S):
                     "gate": 0.9, "max_skip": 20}
 
 
-def run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_params=None, api="slots"):
+def run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_params=None, api="slots",
+            integrator="euler"):
     import ctypes as C
     import torch
     host = torch.empty_like(snaps, device="cpu").pin_memory()
     host.copy_(snaps)
     c = tdb.TDB(wl.dims, wl.rank, rank_max=wl.rank_max, weights=wl.weights, eps_th=wl.eps_th,
-                gamma_th=wl.gamma_th, precision=precision, error_mode=err_mode, error_every=20, device=dev)
+                gamma_th=wl.gamma_th, precision=precision, error_mode=err_mode, error_every=20,
+                integrator=integrator, device=dev)
     ring = [torch.empty_like(snaps[0]) for _ in range(2)]
     stream = torch.cuda.current_stream(dev)
     ring[0].copy_(host[0], non_blocking=True)

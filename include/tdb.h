@@ -76,6 +76,18 @@ enum tdb_error_mode {
   TDB_ERRMODE_NONE = 3       /* never (fixed rank, no control) */
 };
 
+/* Time integrator of the evolution equations (Eqs. 2.15, 2.16) with the snapshot difference
+   Delta V = V_{k+1} - V_k as the data forcing (first-order forward difference, Sec. 2.3). */
+enum tdb_integrator {
+  TDB_EULER = 0,      /* explicit Euler: one projection pass per snapshot */
+  TDB_HEUN = 1        /* Heun's second-order Runge-Kutta scheme (Sec. 3.1 compares it with
+                         Euler): the Euler increment at the state of step k gives a predicted
+                         state, the increment there a second one, and the step takes their
+                         mean.  Both stages use Delta V (the piecewise-linear interpolant of
+                         the snapshots); the predicted state is not re-orthonormalised.  Two
+                         projection passes and two fused updates per snapshot. */
+};
+
 typedef struct tdb_config {
   int ndim;                         /* p, 2..TDB_MAX_MODES */
   int64_t dims[TDB_MAX_MODES];      /* N_n, mode 1 fastest */
@@ -92,6 +104,7 @@ typedef struct tdb_config {
                                        forced exact checks; 0 = 1 */
   int reorth;                       /* 1 = weighted Cholesky-QR of U_n after each step
                                        (recommended; the paper is silent), 0 = off */
+  int integrator;                   /* enum tdb_integrator; TDB_EULER (0) unless set */
 } tdb_config;
 
 /* Per-step report (host struct filled by tdb_push_snapshot). */

@@ -665,7 +665,8 @@ __device__ void rows_mxp(const UpdArgs& a, int n, int64_t i0, int tile, unsigned
   __syncthreads();
 }
 
-// Phase 2 on one tile of mode n: P_n, E = X - U P_n, U' = U + E, partial C = U'^T W U'.
+// Phase 2 on one tile of mode n: P_n, E = X - U P_n, U' = U + E (Heun's second stage:
+// U' = (U0 + U + E) / 2), partial C = U'^T W U'.
 template <typename Tc>
 __device__ void rows_u1(const UpdArgs& a, int n, int64_t i0, int tile, unsigned char* sm) {
   const ModeDesc& d = a.d;
@@ -695,7 +696,8 @@ __device__ void rows_u1(const UpdArgs& a, int n, int64_t i0, int tile, unsigned 
   if (ca < r && i < N) {
     Tc e = __ldcg(&((const Tc*)a.X[n])[i + N * ca]);
     for (int b = 0; b < r; ++b) e -= Ush[li][b] * Psh[b + LD * ca];
-    const double up = a.U[n][i + N * ca] + (double)e;
+    const int64_t ix = i + N * ca;
+    const double up = a.T0 ? 0.5 * ((a.U[n][ix] + a.U0[n][ix]) + (double)e) : a.U[n][ix] + (double)e;
     a.Up[n][i + N * ca] = up;
     upc = (Tc)up;
   }
@@ -894,7 +896,7 @@ __device__ void rows_u2(const UpdArgs& a, int n, int64_t i0, unsigned char* sm) 
 }
 
 // Core mode product dst = src x_n R_n (R_n upper triangular); the first mode adds dS
-// to T.  Work is split by mode-n fibers (the r_n entries at fixed other indices):
+// to T (Heun's second stage: forms (T0 + T + dS) / 2).  Work is split by mode-n fibers (the r_n entries at fixed other indices):
 // each pass stages F fibers per CTA in shared memory (one coalesced load per
 // thread), F chosen so that every CTA of the grid has some.
 template <typename Tc>
@@ -917,7 +919,12 @@ __device__ void core_mode(const UpdArgs& a, int n, const double* src, double* ds
     if (act) {
       const int64_t l = f % L, q = f / L;
       idx = l + L * (j + (int64_t)r * q);
-      Xs[j * F + fl] = (n == 0) ? src[idx] + (double)dS[idx] : __ldcg(&src[idx]);
+      if (n != 0)
+        Xs[j * F + fl] = __ldcg(&src[idx]);
+      else if (a.T0)
+        Xs[j * F + fl] = 0.5 * ((src[idx] + a.T0[idx]) + (double)dS[idx]);
+      else
+        Xs[j * F + fl] = src[idx] + (double)dS[idx];
     }
     __syncthreads();
     if (act) {

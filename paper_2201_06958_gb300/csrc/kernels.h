@@ -78,6 +78,11 @@ struct UpdArgs {
   int ntile, gsplit;
   int warm, reorth;
   int skip_finish;               // phase 7 (G, G^{-1}, sigma^2) left to launch_gram_finish
+  // Heun's second stage: the right-hand side is evaluated at the predicted state held in
+  // T/U, and the new state is (y_k + y_pred + increment) / 2 with y_k = (T0, U0_n) in
+  // the layout of T/U.  Null for an Euler step (and for Heun's first stage).
+  const double* T0;
+  const double* U0[kMaxModes];
   unsigned* bar;                 // arrival counter of the grid barriers (zeroed per launch)
   unsigned long long* stamps;    // per-phase timer stamps (profiling), or null
   unsigned* flags;

@@ -394,6 +394,7 @@ tdb_status validate(const tdb_config* cfg, std::string& err) {
     err = "bad error_mode";
     return TDB_ERR_INVALID_ARG;
   }
+  if (cfg->integrator < TDB_EULER || cfg->integrator > TDB_HEUN) { err = "bad integrator"; return TDB_ERR_INVALID_ARG; }
   if (cfg->eps_th > 0 && !(cfg->gamma_th > 0 && cfg->gamma_th <= 100)) { err = "gamma_th must be in (0, 100]"; return TDB_ERR_INVALID_ARG; }
   for (int n = 0; n < cfg->ndim; ++n) {
     if (cfg->rank[n] < 0 || cfg->rank[n] > kMaxRank) { err = "rank outside 0..32"; return TDB_ERR_RANK; }
@@ -889,6 +890,62 @@ void prepare_step(tdb_ctx* ctx) {
 // a1..a7 and the step record, on ctx->stream.  `all_paths` (graph capture) enqueues the
 // exact-error kernels on every step, gated by the device word, so that the recorded
 // work does not depend on host decisions.
+// a3..a6 (and phase 7's refresh of G_n, G_n^{-1}, sigma^(n) unless skip_finish): the fused
+// cooperative update on the projections in ctx->dS / ctx->Y.  heun = Heun's second stage,
+// combining with the state of step k kept in Tbak / Ubak.
+template <typename Tc>
+tdb_status fused_update(tdb_ctx* ctx, bool reorth, bool skip_finish, bool heun) {
+  const int p = ctx->p;
+  UpdArgs a;
+  memset(&a, 0, sizeof(a));
+  a.d = mode_desc(ctx);
+  int64_t Rprod = 1, ntiles = 0;
+  for (int n = 0; n < p; ++n) Rprod *= ctx->r[n];
+  for (int n = 0; n < p; ++n) {
+    a.Y[n] = ctx->Y[n];
+    a.U[n] = ctx->U[n];
+    a.Up[n] = ctx->Up[n];
+    a.X[n] = ctx->X[n];
+    a.w[n] = ctx->w[n];
+    a.A[n] = ctx->A[n];
+    a.Uc[n] = ctx->Uc[n];
+    a.U0[n] = heun ? ctx->Ubak[n] : nullptr;
+    ntiles += (ctx->N[n] + 31) / 32;
+  }
+  a.dS = ctx->dS;
+  a.y3 = (ctx->use_tc && tc_defers_ds(p, ctx->N, ctx->r)) ? ctx->Y[2] : nullptr;
+  a.dS_out = ctx->dS;
+  a.T = ctx->T;
+  a.T2 = ctx->T2;
+  a.T0 = heun ? ctx->Tbak : nullptr;
+  a.Tcore = ctx->Tcore;
+  a.G = ctx->G;
+  a.Ginv = ctx->Ginv;
+  a.Ginvf = ctx->Ginvf;
+  a.R = ctx->R;
+  a.Rinv = ctx->Rinv;
+  a.sig2 = ctx->sig2;
+  a.Vprev = ctx->Vprev;
+  a.part = ctx->rowpart;
+  a.ntile = ctx->ntile;
+  a.gpart = ctx->Gpart;
+  a.gsplit = gram_split(ctx->r, p, ctx->gsplit);
+  a.warm = ctx->warm ? 1 : 0;
+  a.reorth = reorth ? 1 : 0;
+  a.skip_finish = skip_finish ? 1 : 0;
+  a.bar = ctx->bar;
+  a.stamps = ctx->prof ? ctx->stamps : nullptr;
+  a.flags = ctx->flags;
+  const int64_t hint = std::max<int64_t>({ntiles, (int64_t)p * a.gsplit, Rprod / 2048});
+  const tdb_status us = launch_update<Tc>(a, (int)std::min<int64_t>(hint, 1 << 20), ctx->stream);
+  if (us != TDB_OK) {
+    ctx->err = us == TDB_ERR_UNSUPPORTED ? "cooperative launch unsupported" : "fused update launch failed";
+    return us;
+  }
+  CHECK_LAUNCH();
+  return TDB_OK;
+}
+
 template <typename Tc>
 tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths) {
   cudaStream_t s = ctx->stream;
@@ -900,68 +957,38 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
   CK(cudaMemcpyAsync(ctx->est_dev, ctx->est_pin, sizeof(EstState), cudaMemcpyHostToDevice, s));
   cudaEvent_t* ev = ctx->prof ? ctx->pev : nullptr;
   if (ev) CK(cudaEventRecord(ev[0], s));
-  // a1 + a2: difference and projection
-  if (ctx->use_tc) {
-    TRY(tc_project(ctx->tc, (const float*)Vn, (const float*)Vp, ctx->p, ctx->N, ctx->r, (const void* const*)ctx->A,
-                   (const double* const*)ctx->w, (float*)ctx->ping, (float*)ctx->pong, (float*)ctx->dV,
-                   (float*)ctx->dS, (float* const*)ctx->Y, &ctx->rb_dev->dv2, ctx->flags, s, ev ? ev + 4 : nullptr,
-                   ctx->err, true));
-  } else {
-    launch_diff<Tc>(Vn, Vp, (Tc*)ctx->dV, ctx->S, s);
-    launch_wnorm2<Tc>((const Tc*)ctx->dV, nullptr, weight_view(ctx), ctx->npart, ctx->nblk, &ctx->rb_dev->dv2,
-                      ctx->flags, s);
-    CHECK_LAUNCH();
-    TRY(project_tree<Tc>(ctx, (const Tc*)ctx->dV, ev ? ev + 4 : nullptr));
+  int64_t Rprod = 1;
+  for (int n = 0; n < p; ++n) Rprod *= ctx->r[n];
+  // a1 + a2: difference and projection onto the current bases
+  auto project = [&](cudaEvent_t* evm) -> tdb_status {
+    if (ctx->use_tc) {
+      TRY(tc_project(ctx->tc, (const float*)Vn, (const float*)Vp, ctx->p, ctx->N, ctx->r, (const void* const*)ctx->A,
+                     (const double* const*)ctx->w, (float*)ctx->ping, (float*)ctx->pong, (float*)ctx->dV,
+                     (float*)ctx->dS, (float* const*)ctx->Y, &ctx->rb_dev->dv2, ctx->flags, s, evm, ctx->err, true));
+    } else {
+      launch_diff<Tc>(Vn, Vp, (Tc*)ctx->dV, ctx->S, s);
+      launch_wnorm2<Tc>((const Tc*)ctx->dV, nullptr, weight_view(ctx), ctx->npart, ctx->nblk, &ctx->rb_dev->dv2,
+                        ctx->flags, s);
+      CHECK_LAUNCH();
+      TRY(project_tree<Tc>(ctx, (const Tc*)ctx->dV, evm));
+    }
+    return TDB_OK;
+  };
+  const bool heun = ctx->cfg.integrator == TDB_HEUN;
+  if (heun) {
+    // Heun's first stage: keep y_k = (T, U_n), then the Euler increment at y_k gives the
+    // predicted state in place (no re-orthonormalisation; G_n, G_n^{-1} refreshed for it)
+    CK(cudaMemcpyAsync(ctx->Tbak, ctx->T, sizeof(double) * Rprod, cudaMemcpyDeviceToDevice, s));
+    for (int n = 0; n < p; ++n)
+      CK(cudaMemcpyAsync(ctx->Ubak[n], ctx->U[n], sizeof(double) * ctx->N[n] * ctx->r[n], cudaMemcpyDeviceToDevice, s));
+    TRY(project(nullptr));
+    TRY(fused_update<Tc>(ctx, false, false, false));
   }
+  TRY(project(ev ? ev + 4 : nullptr));
   if (ev) CK(cudaEventRecord(ev[1], s));
-  // a3..a6 and the refresh of G_n, G_n^{-1}, sigma^(n): one cooperative launch
-  {
-    UpdArgs a;
-    memset(&a, 0, sizeof(a));
-    a.d = mode_desc(ctx);
-    int64_t Rprod = 1, ntiles = 0;
-    for (int n = 0; n < p; ++n) Rprod *= ctx->r[n];
-    for (int n = 0; n < p; ++n) {
-      a.Y[n] = ctx->Y[n];
-      a.U[n] = ctx->U[n];
-      a.Up[n] = ctx->Up[n];
-      a.X[n] = ctx->X[n];
-      a.w[n] = ctx->w[n];
-      a.A[n] = ctx->A[n];
-      a.Uc[n] = ctx->Uc[n];
-      ntiles += (ctx->N[n] + 31) / 32;
-    }
-    a.dS = ctx->dS;
-    a.y3 = (ctx->use_tc && tc_defers_ds(p, ctx->N, ctx->r)) ? ctx->Y[2] : nullptr;
-    a.dS_out = ctx->dS;
-    a.T = ctx->T;
-    a.T2 = ctx->T2;
-    a.Tcore = ctx->Tcore;
-    a.G = ctx->G;
-    a.Ginv = ctx->Ginv;
-    a.Ginvf = ctx->Ginvf;
-    a.R = ctx->R;
-    a.Rinv = ctx->Rinv;
-    a.sig2 = ctx->sig2;
-    a.Vprev = ctx->Vprev;
-    a.part = ctx->rowpart;
-    a.ntile = ctx->ntile;
-    a.gpart = ctx->Gpart;
-    a.gsplit = gram_split(ctx->r, p, ctx->gsplit);
-    a.warm = ctx->warm ? 1 : 0;
-    a.reorth = ctx->cfg.reorth != 0;
-    a.skip_finish = split ? 1 : 0;
-    a.bar = ctx->bar;
-    a.stamps = ctx->prof ? ctx->stamps : nullptr;
-    a.flags = ctx->flags;
-    const int64_t hint = std::max<int64_t>({ntiles, (int64_t)p * a.gsplit, Rprod / 2048});
-    const tdb_status us = launch_update<Tc>(a, (int)std::min<int64_t>(hint, 1 << 20), s);
-    if (us != TDB_OK) {
-      ctx->err = us == TDB_ERR_UNSUPPORTED ? "cooperative launch unsupported" : "fused update launch failed";
-      return us;
-    }
-    CHECK_LAUNCH();
-  }
+  // a3..a6 and the refresh of G_n, G_n^{-1}, sigma^(n): one cooperative launch (Heun's
+  // second stage: the increment at the predicted state, combined with y_k)
+  TRY(fused_update<Tc>(ctx, ctx->cfg.reorth != 0, split, heun));
   if (ev) CK(cudaEventRecord(ev[2], s));
   if (split) {
     // exact error every step: G_n, G_n^{-1}, sigma^(n) and the estimator's features on a

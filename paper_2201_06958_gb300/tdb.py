@@ -25,6 +25,7 @@ MAX_RANK = 32
 
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 ERROR_MODE = {"exact": 0, "every_k": 1, "mlp": 2, "none": 3}
+INTEGRATOR = {"euler": 0, "heun": 1}
 ACTIONS = {0: "none", 1: "reinit", 2: "increase", 3: "decrease", 4: "revert", 5: "cap"}
 
 TDB_OK = 0
@@ -45,6 +46,7 @@ class tdb_config(C.Structure):
         ("error_mode", C.c_int),
         ("error_every", C.c_int),
         ("reorth", C.c_int),
+        ("integrator", C.c_int),
     ]
 
 
@@ -177,7 +179,8 @@ def _dptr(a: np.ndarray):
 def make_config(dims: Sequence[int], rank: Sequence[int], rank_max: Optional[Sequence[int]] = None,
                 weights: Optional[Sequence[Optional[np.ndarray]]] = None, eps_th: float = 0.0,
                 gamma_th: float = 99.999, slope_window: int = 10, precision: str = "fp32",
-                error_mode: str = "exact", error_every: int = 1, reorth: bool = True):
+                error_mode: str = "exact", error_every: int = 1, reorth: bool = True,
+                integrator: str = "euler"):
     """Build a tdb_config; returns (config, keepalive) - keep the second alive while the config is used."""
     p = len(dims)
     cfg = tdb_config()
@@ -198,6 +201,7 @@ def make_config(dims: Sequence[int], rank: Sequence[int], rank_max: Optional[Seq
     cfg.error_mode = ERROR_MODE[error_mode]
     cfg.error_every = int(error_every)
     cfg.reorth = 1 if reorth else 0
+    cfg.integrator = INTEGRATOR[integrator]
     return cfg, keep
 
 
@@ -206,7 +210,8 @@ class TDB:
     current torch stream of that device at construction."""
 
     def __init__(self, dims, rank, rank_max=None, weights=None, eps_th=0.0, gamma_th=99.999, slope_window=10,
-                 precision="fp32", error_mode="exact", error_every=1, reorth=True, device=None, stream=None):
+                 precision="fp32", error_mode="exact", error_every=1, reorth=True, integrator="euler",
+                 device=None, stream=None):
         self.lib = load()
         self.dims = [int(d) for d in dims]
         self.p = len(self.dims)
@@ -214,7 +219,7 @@ class TDB:
         self.dtype = torch.float64 if precision == "fp64" else torch.float32
         self.device = torch.device(device or "cuda:0")
         self.cfg, self._keep = make_config(dims, rank, rank_max, weights, eps_th, gamma_th, slope_window,
-                                           precision, error_mode, error_every, reorth)
+                                           precision, error_mode, error_every, reorth, integrator)
         nbytes = self.lib.tdb_workspace_bytes(C.byref(self.cfg))
         if nbytes == 0:
             raise TDBError(1, "invalid configuration")

@@ -50,6 +50,10 @@ def test_workspace_bytes_and_validation(lib):
     assert lib.tdb_workspace_bytes(C.byref(bad)) == 0            # ndim 5
     bad, _ = tdb.make_config([8, 8], [40, 2])
     assert lib.tdb_workspace_bytes(C.byref(bad)) == 0            # rank > 32
+    heun, _ = tdb.make_config([512, 256, 12], [0, 0, 0], [16, 16, 12], eps_th=1e-4, integrator="heun")
+    assert lib.tdb_workspace_bytes(C.byref(heun)) == n           # Heun reuses the step's buffers
+    heun.integrator = 2
+    assert lib.tdb_workspace_bytes(C.byref(heun)) == 0           # no such integrator
     # init with a null workspace fails cleanly with TDB_ERR_WORKSPACE, before any device work
     ctx = C.c_void_p()
     st = lib.tdb_init(C.byref(ctx), C.byref(cfg), None, 0, C.c_void_p(16), None)
