@@ -294,11 +294,12 @@ __global__ void k_si_inner(const T* __restrict__ X, const T* __restrict__ Y, int
 }
 
 // Cholesky-QR factor of the Gram G = Z^T Z, in the working precision T: with
-// D = diag(G)^{1/2}, D^{-1} G D^{-1} = L L^T (a shift of 1e-5 or 1e-2 on the unit
-// diagonal is added if that fails), and Rinv = D^{-1} L^{-T} so that Q = Z Rinv
+// D = diag(G)^{1/2}, D^{-1} G D^{-1} + shift0 I = L L^T (a shift of 1e-5 or 1e-2 on the
+// unit diagonal instead if that fails), and Rinv = D^{-1} L^{-T} so that Q = Z Rinv
 // has (near) orthonormal columns.
 template <typename T>
-__global__ void k_si_cholinv(const double* __restrict__ G, int m, double* __restrict__ Rinv, unsigned* flags) {
+__global__ void k_si_cholinv(const double* __restrict__ G, int m, double shift0, double* __restrict__ Rinv,
+                             unsigned* flags) {
   extern __shared__ unsigned char smraw_ci[];
   T* S = (T*)smraw_ci;         // m x m (ld 64)
   T* Li = S + 64 * 64;         // m x m (ld 64)
@@ -310,7 +311,7 @@ __global__ void k_si_cholinv(const double* __restrict__ G, int m, double* __rest
   }
   __syncthreads();
   for (int attempt = 0; attempt < 3; ++attempt) {
-    double shift = attempt == 0 ? 0.0 : (attempt == 1 ? 1e-5 : 1e-2);
+    double shift = attempt == 0 ? shift0 : (attempt == 1 ? 1e-5 : 1e-2);
     for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
       int i = e % m, j = e / m;
       S[i + 64 * j] = (T)(G[i + (int64_t)m * j] / (d[i] * d[j]) + (i == j ? shift : 0.0));
@@ -422,12 +423,31 @@ tdb_status eig_subspace(const T* Cc, const double* C64, int n, int k, int iters,
     cudaFuncSetAttribute(k_si_cholinv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, 2 * 64 * 64 * (int)sizeof(T));
     attr = true;
   }
+  // Each iteration re-orthonormalises Z = C Q by shifted Cholesky-QR followed by two plain
+  // passes (shifted CholeskyQR3 of Fukaya, Kannan, Nakatsukasa, Yamamoto and Yanagisawa,
+  // SIAM J. Sci. Comput. 2020).  The shift s = 11 (n m + m (m + 1)) u ||Z||_2^2, with
+  // ||Z||_2^2 <= m for the unit-diagonal scaled Gram, makes the first factor succeed for
+  // kappa(Z) up to about u^{-1}, leaving kappa(Q) near u^{-1/2}; the plain passes then make Q
+  // orthonormal to working precision.  A plain Cholesky-QR alone breaks down when C Q is
+  // (numerically) rank deficient: a mode longer than the product of the others (a grouped
+  // spatial mode), or a fast-decaying spectrum.
+  const double u = sizeof(T) == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+  const double s0 = 11.0 * ((double)n * m + (double)m * (m + 1)) * u * m;
+  const size_t ci_smem = 2 * 64 * 64 * sizeof(T);
+  const int inner_blocks = (m * m * 32 + 255) / 256;
   k_si_start<T><<<blocks_nm, 256, 0, s>>>(ws.Q, n, m); count_launch();
   for (int it = 0; it < iters; ++it) {
     k_si_gemm<T><<<ggrid, 256, 0, s>>>(Cc, ws.Q, ws.Z, n, m); count_launch();
-    k_si_inner<T><<<(m * m * 32 + 255) / 256, 256, 0, s>>>(ws.Z, ws.Z, n, m, ws.G); count_launch();
-    k_si_cholinv<T><<<1, 256, 2 * 64 * 64 * sizeof(T), s>>>(ws.G, m, ws.R, flags); count_launch();
+    k_si_inner<T><<<inner_blocks, 256, 0, s>>>(ws.Z, ws.Z, n, m, ws.G); count_launch();
+    k_si_cholinv<T><<<1, 256, ci_smem, s>>>(ws.G, m, s0, ws.R, flags); count_launch();
     k_si_apply<T><<<blocks_nm, 256, 0, s>>>(ws.Z, ws.R, n, m, m, 1, ws.Q); count_launch();
+    for (int pass = 0; pass < 2; ++pass) {
+      T* src = pass == 0 ? ws.Q : ws.Z;
+      T* dst = pass == 0 ? ws.Z : ws.Q;
+      k_si_inner<T><<<inner_blocks, 256, 0, s>>>(src, src, n, m, ws.G); count_launch();
+      k_si_cholinv<T><<<1, 256, ci_smem, s>>>(ws.G, m, 0.0, ws.R, flags); count_launch();
+      k_si_apply<T><<<blocks_nm, 256, 0, s>>>(src, ws.R, n, m, m, 1, dst); count_launch();
+    }
   }
   // Rayleigh-Ritz
   k_si_gemm<T><<<ggrid, 256, 0, s>>>(Cc, ws.Q, ws.Z, n, m); count_launch();

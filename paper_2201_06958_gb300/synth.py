@@ -381,16 +381,64 @@ def make_batch(seed: int = 1005, count: int = 64):
     return out
 
 
+# ---------------------------------------------------------------------------
+# grouped modes (p < d): contiguous groups of grid dimensions as one mode
+# ---------------------------------------------------------------------------
+
+def group_modes(wl: Workload, groups: Sequence[Sequence[int]], rank_max: Optional[Sequence[int]] = None,
+                name: Optional[str] = None) -> Workload:
+    """The same snapshots with each group of consecutive modes taken as one mode (the
+    disjoint decomposition of the independent variables into p groups of Sec. 2.1; the
+    two-dimensional spatial bases of the TDB-2 scheme of Sec. 3.2).  With mode 1 fastest, a
+    group (m, ..., m + g - 1) has the linear index i_m + N_m i_{m+1} + ..., so the storage
+    tensor is only reshaped, and the group's quadrature weights are the products of its
+    members' weights in that index order (the product rule of the group's grid)."""
+    flat = [m for g in groups for m in g]
+    if flat != list(range(wl.ndim)) or any(list(g) != list(range(g[0], g[0] + len(g))) for g in groups):
+        raise ValueError("groups must be consecutive runs covering the modes in order")
+    dims, weights = [], []
+    for g in groups:
+        n, w = 1, np.ones(1)
+        for m in g:
+            n *= wl.dims[m]
+            w = np.kron(wl.weights[m], w)          # the later mode varies slower
+        dims.append(n)
+        weights.append(w)
+    store = tuple(reversed(dims))
+    if rank_max is None:
+        rank_max = [min(32, n) for n in dims]
+
+    def field(t, device):
+        return wl._field(t, device).reshape(store)
+
+    dfield = None
+    if wl._dfield is not None:
+        def dfield(t, device):
+            return wl._dfield(t, device).reshape(store)
+
+    return Workload(name or wl.name + "_grouped", dims, wl.dtype, wl.dt, wl.steps, [0] * len(dims),
+                    list(rank_max), wl.eps_th, wl.gamma_th, weights, field, dfield)
+
+
+def _reactive_dbo(seed: int, nx: int = 32, ny: int = 16, ns: int = 12, **kw) -> Workload:
+    """The reactive flow as the TDB-2 (DBO) scheme of Sec. 3.2: one two-dimensional spatial
+    mode (nx * ny points, product trapezoid weights) and the species mode."""
+    return group_modes(_reactive(seed, nx=nx, ny=ny, ns=ns, **kw), [[0, 1], [2]], rank_max=[12, 12],
+                       name="reactive_dbo")
+
+
 WORKLOADS = {
     "analytic": lambda seed=1001, **kw: _analytic(seed, **kw),
     "reactive": lambda seed=1002, **kw: _reactive(seed, **kw),
     "stochastic": lambda seed=1003, **kw: _stochastic(seed, **kw),
     "channel": lambda seed=1004, **kw: _channel(seed, **kw),
     "runge": lambda seed=1005, **kw: _runge(seed, **kw),
+    "reactive_dbo": lambda seed=1006, **kw: _reactive_dbo(seed, **kw),
 }
 
 
-DEFAULT_SEEDS = {"analytic": 1001, "reactive": 1002, "stochastic": 1003, "channel": 1004, "runge": 1005}
+DEFAULT_SEEDS = {"analytic": 1001, "reactive": 1002, "stochastic": 1003, "channel": 1004, "runge": 1005,
+                 "reactive_dbo": 1006}
 
 
 def default_seed(name: str) -> int:

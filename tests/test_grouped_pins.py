@@ -1,0 +1,87 @@
+"""Grouped (multi-dimensional) modes: the TDB-2 / DBO scheme of Sec. 3.2 on CPU.
+
+Grouping consecutive modes is a reshape of the storage tensor with product quadrature
+weights; for two modes the truncated HOSVD is the truncated SVD of the weighted matrix
+(Eckart-Young), so the TDB-2 error is the optimal one of its rank and no larger than the
+TDB-1 error of a decomposition whose grouped unfolding has that rank.
+"""
+
+import math
+
+import numpy as np
+import torch
+
+import oracle as O
+from paper_2201_06958_gb300 import synth as S
+
+
+def _pair(seed=1006, nx=24, ny=10, ns=7):
+    t1 = S._reactive(seed, nx=nx, ny=ny, ns=ns)
+    t2 = S.group_modes(t1, [[0, 1], [2]], rank_max=[ns, ns])
+    return t1, t2
+
+
+def test_grouping_is_a_reshape_with_product_weights():
+    """Same data, same weighted norm (nx != ny, so a transposed weight product fails),
+    and the grouped weight of (i_1, i_2) is w_1(i_1) w_2(i_2) at i_1 + N_1 i_2."""
+    t1, t2 = _pair()
+    assert t2.dims == [24 * 10, 7]
+    a = t1.snapshot(3).reshape(-1)
+    b = t2.snapshot(3).reshape(-1)
+    assert torch.equal(a, b)
+    V1, V2 = t1.logical(3), t2.logical(3)
+    n1, n2 = O.weighted_norm2(V1, t1.weights), O.weighted_norm2(V2, t2.weights)
+    assert abs(n1 - n2) <= 1e-14 * n1
+    i1, i2 = 5, 7
+    assert t2.weights[0][i1 + 24 * i2] == t1.weights[0][i1] * t1.weights[1][i2]
+    with np.testing.assert_raises(ValueError):
+        S.group_modes(t1, [[0, 2], [1]])
+
+
+def test_tdb2_hosvd_is_the_weighted_svd():
+    """p = 2: the oracle's HOSVD error at ranks (r, r) equals the discarded singular values
+    of W_1^(1/2) V W_2^(1/2) (a library SVD), and the TDB-1 HOSVD error at (r1, r2, r3) is
+    never below the TDB-2 error at min(r1 r2, r3)."""
+    t1, t2 = _pair()
+    V1, V2 = t1.logical(0), t2.logical(0)
+    s = np.linalg.svd(np.sqrt(t2.weights[0])[:, None] * V2 * np.sqrt(t2.weights[1])[None, :], compute_uv=False)
+    for r in (1, 3, 5):
+        T, U, _ = O.hosvd(V2, t2.weights, [r, r])
+        e = O.error_exact(V2, T, U, t2.weights)
+        ref = math.sqrt(float(np.sum(s[r:] ** 2)))
+        assert abs(e - ref) <= 1e-9 * ref + 1e-15, (r, e, ref)
+    for rr in ((2, 2, 3), (3, 2, 4), (4, 4, 5), (2, 3, 7)):
+        T, U, _ = O.hosvd(V1, t1.weights, list(rr))
+        e1 = O.error_exact(V1, T, U, t1.weights)
+        r = min(rr[0] * rr[1], rr[2])
+        T, U, _ = O.hosvd(V2, t2.weights, [r, r])
+        e2 = O.error_exact(V2, T, U, t2.weights)
+        assert e2 <= e1 * (1 + 1e-12), (rr, e1, e2)
+
+
+def test_tdb2_storage_is_the_two_mode_compression_ratio():
+    """The TDB-2 storage of Sec. 3.2, r N_1 N_2 + r n_s + r^2, is the general
+    sum r_n N_n + prod r_n of Sec. 2.6 for the grouped dimensions."""
+    for r, N1, N2, ns in ((4, 251, 76, 23), (12, 32, 16, 12), (1, 2, 3, 4)):
+        cr = O.compression_ratio([N1 * N2, ns], [r, r])
+        assert math.isclose(cr, N1 * N2 * ns / O.storage_tdb2(r, N1, N2, ns), rel_tol=1e-15)
+
+
+def test_grouped_euler_step_keeps_exact_rank_data_exact():
+    """A grouped mode is an ordinary mode to the method: on data whose grouped unfolding
+    has rank r and fixed column space, the two-mode Euler step reproduces every
+    snapshot (the fixed-subspace case of Sec. 2.2 in the grouped variables)."""
+    rng = np.random.default_rng(5)
+    t1, t2 = _pair()
+    w = t2.weights
+    N1, N2, r = t2.dims[0], t2.dims[1], 3
+    Q1, _ = np.linalg.qr(rng.standard_normal((N1, r)))
+    Q2, _ = np.linalg.qr(rng.standard_normal((N2, r)))
+    U = [Q1 / np.sqrt(w[0])[:, None], Q2 / np.sqrt(w[1])[:, None]]
+    V = [O.reconstruct(np.diag([3.0, 2.0, 1.0]) + 0.1 * k * rng.standard_normal((r, r)), U) for k in range(6)]
+    T = O.multi_mode_product(V[0], [(w[n][:, None] * U[n]).T for n in range(2)])
+    Uc = [u.copy() for u in U]
+    for k in range(1, 6):
+        T, Uc, _, _ = O.step_euler(T, Uc, w, V[k - 1], V[k])
+        e = O.error_exact(V[k], T, Uc, w)
+        assert e <= 1e-12 * math.sqrt(O.weighted_norm2(V[k], w)), (k, e)
