@@ -113,7 +113,8 @@ typedef struct tdb_step_info {
   double eps;                       /* exact error after the step and any control (Eq. 2.20),
                                        or the estimate when eps_exact == 0 */
   int eps_exact;                    /* 1 = exact evaluation this step, 0 = estimate / none */
-  double eps_step;                  /* exact error of the Euler step before control acted */
+  double eps_step;                  /* exact error of the time step (Euler or Heun) before
+                                       control acted */
   double gamma[TDB_MAX_MODES];      /* gamma^(n)(r_n) in percent (Eq. 2.21, second form) */
   double sigma_min[TDB_MAX_MODES];  /* smallest singular value of T_(n) (Eq. 2.18) */
   int ranks[TDB_MAX_MODES];         /* r_n after the step */
