@@ -3,7 +3,7 @@
 // with mean-squared-error loss, back-propagation and Adam, in FP32.  The paper
 // monitors the error by computing it (Eq. 2.20); the estimator predicts log10 of
 // that error from reduced quantities so that most steps can skip the full pass,
-// and the exact error stays the fallback and the judge.
+// and the exact error stays the fallback and the only input to rank decisions.
 //
 // Parameter vector (float, MLP_NPARAM entries): W1 (H x F, row-major), b1 (H),
 // W2 (H x H, row-major), b2 (H), w3 (H), b3 (1).
