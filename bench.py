@@ -214,7 +214,10 @@ while elapsed < budget and steps < {max_steps}:
     k += 1
     V = S.to_logical(wl.snapshot(k))
     t0 = time.perf_counter()
-    T1, U1, _, _ = O.step_euler(st.T, st.U, w, V_prev, V)
+    if {heun}:
+        T1, U1 = O.step_heun(st.T, st.U, w, V_prev, V)
+    else:
+        T1, U1, _, _ = O.step_euler(st.T, st.U, w, V_prev, V)
     st = O.TDBState(T1, U1)
     eps = O.error_exact(V, st.T, st.U, w)
     if controller is not None:
@@ -226,20 +229,21 @@ print(json.dumps({{"steps": steps, "seconds": elapsed}}))
 """
 
 
-def cpu_baseline(workload: str, budget_s: float, max_steps: int):
+def cpu_baseline(workload: str, budget_s: float, max_steps: int, integrator: str = "euler"):
     cores = os.cpu_count() or 1
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(cores)
     env["CUDA_VISIBLE_DEVICES"] = ""
-    code = CPU_SNIPPET.format(root=ROOT, wl=workload, budget=budget_s, max_steps=max_steps)
+    code = CPU_SNIPPET.format(root=ROOT, wl=workload, budget=budget_s, max_steps=max_steps,
+                              heun=integrator == "heun")
     p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
     if p.returncode != 0:
         return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "error": p.stderr[-400:]}
     d = json.loads(p.stdout.strip().splitlines()[-1])
     return {"value": d["steps"] / d["seconds"], "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {d['steps']} steps of the same stream (FP64 numpy oracle, exact error and rank "
-                      f"control every step), {d['seconds']:.1f} s of CPU time"}
+            "sample": f"first {d['steps']} steps of the same stream (FP64 numpy oracle, {integrator} step, exact "
+                      f"error and rank control every step), {d['seconds']:.1f} s of CPU time"}
 
 
 # ---------------------------------------------------------------------------
@@ -251,7 +255,7 @@ def run_reference(args, world, rank):
     cores = os.cpu_count() or 1
     wl_name = args.workload
     total = args.warmup + args.steps
-    code = CPU_SNIPPET.format(root=ROOT, wl=wl_name, budget=1e9, max_steps=total)
+    code = CPU_SNIPPET.format(root=ROOT, wl=wl_name, budget=1e9, max_steps=total, heun=args.integrator == "heun")
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(cores)
@@ -263,13 +267,14 @@ def run_reference(args, world, rank):
     d = json.loads(p.stdout.strip().splitlines()[-1])
     per_step = d["seconds"] / max(d["steps"], 1)
     value = 1.0 / per_step
-    wl = workload_desc(wl_name)
+    wl = dict(workload_desc(wl_name), integrator=args.integrator)
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": wl,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": f"{d['steps']} full steps (warm-up included in the mean) of the FP64 numpy oracle"},
+                         "sample": f"{d['steps']} full steps (warm-up included in the mean) of the FP64 numpy oracle, "
+                                   f"{args.integrator} step"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -477,8 +482,8 @@ def run_tdb(args, world, rank, local):
         line["e2e"] = run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_params, args.api,
                               args.integrator)
 
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.integrator == "euler":
-        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample_seconds, K)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args.workload, args.cpu_sample_seconds, K, args.integrator)
     if rank == 0:
         print(json.dumps(line))
 
