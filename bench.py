@@ -186,6 +186,30 @@ def recorded_traffic(kernel_key: str, sha: str):
     return e.get("dram_bytes_per_launch")
 
 
+def projection_flops(dims, ranks):
+    """Algorithmic flops of one projection pass (Eqs. 2.15, 2.16) at the given ranks.
+    'first_contractions': what the fused kernel does on S-sized data, the mode-1 and mode-2
+    contractions of the difference (2 r_1 + 2 r_2 per element; the rest is rank-sized).
+    'paper_2rd': the paper's O(r d S) count for projecting onto every mode, 2 sum_n r_n per
+    element (Sec. 2.6)."""
+    S = 1
+    for d in dims:
+        S *= int(d)
+    r = [float(x) for x in ranks]
+    return {"first_contractions": 2.0 * (r[0] + r[1]) * S, "paper_2rd": 2.0 * sum(r) * S}
+
+
+def flops_fields(dims, acts, kernel_ms):
+    """projection_flops at the mean ranks of a timed run (acts: (action, ranks) per step),
+    with the rate of the first contractions over the projection kernel's duration.  The
+    path is bound by HBM, not by these flops."""
+    p = len(dims)
+    mean_ranks = [sum(a[1][n] for a in acts) / max(len(acts), 1) for n in range(p)]
+    fl = projection_flops(dims, mean_ranks)
+    return dict(fl, mean_ranks=[round(x, 2) for x in mean_ranks],
+                tflops_first_contractions=fl["first_contractions"] / (kernel_ms * 1e-3) / 1e12)
+
+
 # ---------------------------------------------------------------------------
 # CPU baseline: the oracle as it stands on a bounded sample (spawned process)
 # ---------------------------------------------------------------------------
@@ -442,6 +466,7 @@ def run_tdb(args, world, rank, local):
                                       "control_host": prof.ms_control / max(prof.steps, 1)},
                 "update_phase_us_per_step": [round(prof.us_update_phase[k] / max(prof.steps, 1), 2)
                                              for k in range(prof.update_phases)]}
+    roofline["flops_per_launch"] = flops_fields(wl.dims, res["acts"], kernel_ms)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,

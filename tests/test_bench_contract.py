@@ -28,3 +28,17 @@ def test_reference_arm_json_line(integrator):
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
     assert d["config"]["workload"].startswith("reactive 512x256x12")
     assert d["config"]["integrator"] == integrator
+
+
+def test_projection_flop_counts():
+    """2 (r_1 + r_2) per element for the two first contractions, 2 sum r_n for the paper's
+    O(r d S) count; the rate uses the kernel time in ms."""
+    sys.path.insert(0, ROOT)
+    import bench
+    fl = bench.projection_flops([512, 256, 12], [16, 16, 12])
+    S = 512 * 256 * 12
+    assert fl["first_contractions"] == 64 * S and fl["paper_2rd"] == 88 * S
+    acts = [(0, (16, 16, 12)), (1, (14, 16, 10))]
+    f = bench.flops_fields([512, 256, 12], acts, 0.5)
+    assert f["mean_ranks"] == [15.0, 16.0, 11.0]
+    assert abs(f["tflops_first_contractions"] - 2 * 31 * S / 0.5e-3 / 1e12) < 1e-12
