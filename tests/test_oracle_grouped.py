@@ -85,3 +85,42 @@ def test_grouped_euler_step_keeps_exact_rank_data_exact():
         T, Uc, _, _ = O.step_euler(T, Uc, w, V[k - 1], V[k])
         e = O.error_exact(V[k], T, Uc, w)
         assert e <= 1e-12 * math.sqrt(O.weighted_norm2(V[k], w)), (k, e)
+
+
+def _grouped_analytic_rk4(n, steps, dt):
+    wl = S.group_modes(S.make_workload("analytic", n=n, dt=dt, steps=steps), [[0, 1], [2]], rank_max=[4, 4])
+    w = wl.weights
+    T, U, _ = O.hosvd(wl.logical(0), w, [4, 4])
+    vdot = lambda t: S.to_logical(wl.snapshot_dot(t))
+    for k in range(1, steps + 1):
+        T, U = O.step_rk4(T, U, w, (k - 1) * dt, dt, vdot)
+    V = wl.logical(steps)
+    return O.error_exact(V, T, U, w) / math.sqrt(O.weighted_norm2(V, w))
+
+
+def test_grouped_analytic_field_is_exact_rank_and_recovered_at_order_4():
+    """The analytic field sum_j a_j f_j(x_1) g_j(x_2) h_j(x_3) grouped as ((x_1, x_2), x_3) is
+    sum_j a_j (f_j g_j) h_j: rank 4 in both modes (the fifth weighted Gram eigenvalue is
+    rounding), so the two-mode equations keep e = 0 and RK4 with the exact derivative
+    converges at order 4 in the grouped variables, as in three modes."""
+    wl = S.group_modes(S.make_workload("analytic", n=16), [[0, 1], [2]])
+    spec = O.hosvd_spectrum(wl.logical(3), wl.weights)
+    for n in range(2):
+        lam = spec[n][0] / spec[n][0][0]
+        assert lam[3] > 1e-3 and lam[4] < 1e-13, lam[:6]
+    e1 = _grouped_analytic_rk4(16, 50, 4e-3)
+    e2 = _grouped_analytic_rk4(16, 100, 2e-3)
+    assert 12.0 < e1 / e2 < 20.0, (e1, e2)
+    assert e2 < 1e-9
+
+
+def test_grouped_controller_moves_both_ranks_together():
+    """Two modes: r_1 <= r_2 and r_2 <= r_1 (the product bound of Sec. 2.2), so every
+    rank the controller sets on the grouped reactive stream has r_1 = r_2, through an
+    increase and a revert."""
+    wl = S.make_workload("reactive_dbo")
+    snaps = [S.to_logical(wl.snapshot(k, dtype=torch.float64)) for k in range(41)]
+    ctrl = O.ControllerConfig(5e-5, 99.99, 5, [12, 12])
+    _, recs = O.compress_stream(snaps, wl.weights, [0, 0], ctrl)
+    assert all(r.ranks[0] == r.ranks[1] for r in recs)
+    assert {"increase", "revert"} <= {r.action for r in recs}
