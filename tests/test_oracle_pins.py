@@ -426,6 +426,63 @@ def test_controller_decrease_and_revert():
     assert eps0 < 1e-3
 
 
+def test_rank_from_core_counts_the_error_in_the_denominator():
+    """Eq. 2.21, second form: gamma(r) = sum_{i<=r} sigma_i^2 / (sum_i sigma_i^2 + eps^2).
+    With sigma^2 = (1/2, 1/4, 1/4) and gamma_th = 60 %, eps = 0 needs r = 2 (3/4 >= 0.6);
+    eps^2 = 1 makes the target 1.2, which no r reaches, so the rule keeps every mode."""
+    sig = np.sqrt(np.array([0.5, 0.25, 0.25]))
+    assert O.rank_from_core(sig, 0.0, 60.0) == 2
+    assert O.rank_from_core(sig, 1.0, 60.0) == 3
+    # eps^2 = 1/4: target 0.75, reached at r = 2 exactly
+    assert O.rank_from_core(sig, 0.5, 60.0) == 2
+    assert O.rank_from_core(sig, 0.5, 61.0) == 3
+
+
+def test_controller_raise_ties_go_to_the_lowest_mode():
+    """Equal discarded HOSVD energy in every mode: the increment rule raises mode 1 (the
+    lowest index), and the product bound needs no other mode to follow."""
+    lam = np.array([1.0, 0.5, 0.25, 0.125])
+    w = [np.full(4, 0.25)] * 3
+    ctrl = O.Controller(O.ControllerConfig(eps_th=1.0, gamma_th=99.0, slope_window=3, rank_max=[4, 4, 4]),
+                        (4, 4, 4), w)
+    assert ctrl._raise_one([2, 2, 2], [lam, lam, lam]) == [3, 2, 2]
+    # unequal: the mode that discards most is raised
+    assert ctrl._raise_one([2, 2, 2], [lam, lam, np.array([1.0, 0.5, 0.5, 0.5])]) == [2, 2, 3]
+
+
+def test_controller_slope_window_restarts_after_reinit():
+    """Steps with a HOSVD re-initialisation are excluded from the error slope and the window
+    restarts (Sec. 2.5): after a re-initialising act the history is empty, and it then
+    holds exactly the errors of the following plain steps."""
+    rng = np.random.default_rng(14)
+    V, w = _lowrank_tensor(rng, (8, 7, 6), [1.0, 0.2, 1e-2])
+    T, U, _ = O.hosvd(V, w, [2, 2, 2])
+    ctrl = O.Controller(O.ControllerConfig(eps_th=1e-3, gamma_th=99.0, slope_window=3, rank_max=[3, 3, 3]),
+                        V.shape, w)
+    st = O.TDBState(T, U)
+    for e in (5e-4, 4e-4):
+        ctrl.act(V, st, e)
+    assert ctrl.history == [5e-4, 4e-4]
+    st2, _, n_re, action = ctrl.act(V, st, 0.5)     # above eps_th: re-initialise
+    assert n_re >= 1 and action in ("reinit", "increase")
+    assert ctrl.history == []
+    ctrl.act(V, st2, 3e-4)
+    assert ctrl.history == [3e-4]
+
+
+def test_hosvd_sign_convention():
+    """Each HOSVD vector's entry of largest magnitude is positive (the sign convention that
+    makes the oracle's bases unique up to rotation within equal eigenvalues)."""
+    rng = np.random.default_rng(15)
+    dims = (9, 7, 6)
+    w = [_rand_weights(rng, N) for N in dims]
+    V = rng.standard_normal(dims)
+    for lam, Q in O.hosvd_spectrum(V, w):
+        for j in range(Q.shape[1]):
+            i = int(np.argmax(np.abs(Q[:, j])))
+            assert Q[i, j] > 0
+
+
 def test_runge_field_and_derivative_closed_form():
     """The Runge workload is Eq. 3.1's function itself: values at grid points and the
     analytic time derivative against a central difference."""
