@@ -135,8 +135,14 @@ typedef struct tdb_ctx tdb_ctx;
 size_t tdb_workspace_bytes(const tdb_config* cfg);
 
 /* Initialise by truncated HOSVD of V0 (Sec. 2.3 last paragraph; ranks by gamma_th,
- * Sec. 2.5).  V0: device snapshot.  stream: cudaStream_t (NULL = legacy default).
- * On success *ctx owns nothing on the device but its view of workspace. */
+ * Sec. 2.5).  V0: device snapshot in the layout of tdb_push_snapshot, borrowed the same
+ * way.  workspace: device, 256-byte aligned, >= tdb_workspace_bytes(cfg) bytes, owned by
+ * the caller and outliving the context.  stream: cudaStream_t (NULL = legacy default).
+ * On success *ctx owns nothing on the device but its view of workspace.  Errors:
+ * TDB_ERR_INVALID_ARG / TDB_ERR_SHAPE / TDB_ERR_RANK (cfg), TDB_ERR_WORKSPACE,
+ * TDB_ERR_UNSUPPORTED (a shape the tensor-core projection does not take, in
+ * TDB_BF16_TTM), TDB_ERR_NONFINITE, TDB_ERR_TIMEOUT, TDB_ERR_CUDA; the message is in
+ * tdb_last_error(NULL). */
 tdb_status tdb_init(tdb_ctx** ctx, const tdb_config* cfg, void* workspace, size_t workspace_bytes,
                     const void* V0, void* stream);
 
@@ -148,11 +154,18 @@ tdb_status tdb_init_from_factors(tdb_ctx** ctx, const tdb_config* cfg, void* wor
                                  const double* const* U, const int* ranks, const void* V0,
                                  void* stream);
 
-/* One step of the compressor with the next snapshot (device pointer):
+/* One step of the compressor with the next snapshot (device pointer, prod N_n elements
+ * of the snapshot type, storage order (N_p, ..., N_1) with mode 1 fastest):
  * difference, fused projection (Eqs. 2.15, 2.16), pseudo-inverse and complement
- * projection (Sec. 2.2), Euler update, re-orthonormalisation, error (Eq. 2.20) per
- * error_mode, and rank control (Sec. 2.5).  info (host, nullable) receives the
- * report; the call synchronises the stream. */
+ * projection (Sec. 2.2), the time step of cfg.integrator (Euler, or Heun's two
+ * stages), re-orthonormalisation, error (Eq. 2.20) per error_mode, and rank control
+ * (Sec. 2.5).  V_next is borrowed: it becomes the previous snapshot and must stay
+ * unmodified until the next push returns.  info (host, nullable) receives the report;
+ * the call synchronises the stream.  Errors: TDB_ERR_INVALID_ARG (null ctx or
+ * snapshot), TDB_ERR_STATE (before init), TDB_ERR_NONFINITE (a non-finite difference),
+ * TDB_ERR_RANK_DEFICIENT (a core Gram or basis Gram not positive definite),
+ * TDB_ERR_TIMEOUT (a bounded device wait ran out), TDB_ERR_CUDA; TDB_WARN_RANK_CAP
+ * (the step completed, but the error stays above eps_th at the rank caps). */
 tdb_status tdb_push_snapshot(tdb_ctx* ctx, const void* V_next, tdb_step_info* info);
 
 /* Write V^TDB = T x_1 U_1 ... x_p U_p (Eq. 2.5) into V_out (device, caller-owned,
