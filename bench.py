@@ -253,21 +253,38 @@ print(json.dumps({{"steps": steps, "seconds": elapsed}}))
 """
 
 
-def cpu_baseline(workload: str, budget_s: float, max_steps: int, integrator: str = "euler"):
-    cores = os.cpu_count() or 1
+def _oracle_sample(workload: str, budget_s: float, max_steps: int, integrator: str, threads: int):
+    """Run the oracle on the first steps of the stream in a child process with ``threads``
+    BLAS/OpenMP threads; returns (steps, seconds) or an error string."""
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
-        env[k] = str(cores)
+        env[k] = str(threads)
     env["CUDA_VISIBLE_DEVICES"] = ""
     code = CPU_SNIPPET.format(root=ROOT, wl=workload, budget=budget_s, max_steps=max_steps,
                               heun=integrator == "heun")
     p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
     if p.returncode != 0:
-        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "error": p.stderr[-400:]}
+        return p.stderr[-400:]
     d = json.loads(p.stdout.strip().splitlines()[-1])
-    return {"value": d["steps"] / d["seconds"], "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"first {d['steps']} steps of the same stream (FP64 numpy oracle, {integrator} step, exact "
-                      f"error and rank control every step), {d['seconds']:.1f} s of CPU time"}
+    return d["steps"], d["seconds"]
+
+
+def cpu_baseline(workload: str, budget_s: float, max_steps: int, integrator: str = "euler"):
+    """The oracle as it stands on the host cores (all of them), plus a shorter
+    single-threaded sample of the same stream."""
+    cores = os.cpu_count() or 1
+    r = _oracle_sample(workload, budget_s, max_steps, integrator, cores)
+    if isinstance(r, str):
+        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle", "error": r}
+    steps, secs = r
+    out = {"value": steps / secs, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"first {steps} steps of the same stream (FP64 numpy oracle, {integrator} step, exact "
+                     f"error and rank control every step), {secs:.1f} s of CPU time"}
+    r1 = _oracle_sample(workload, max(budget_s / 3.0, 1.0), max_steps, integrator, 1)
+    if not isinstance(r1, str):
+        out["single_thread"] = {"value": r1[0] / r1[1], "unit": UNIT, "cores": 1,
+                                "sample": f"first {r1[0]} steps, {r1[1]:.1f} s"}
+    return out
 
 
 # ---------------------------------------------------------------------------
