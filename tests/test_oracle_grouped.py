@@ -34,6 +34,8 @@ def test_grouping_is_a_reshape_with_product_weights():
     assert abs(n1 - n2) <= 1e-14 * n1
     i1, i2 = 5, 7
     assert t2.weights[0][i1 + 24 * i2] == t1.weights[0][i1] * t1.weights[1][i2]
+    # the product rule of two unit-sum trapezoid rules is a unit-sum rule on the grouped grid (C6)
+    assert abs(t2.weights[0].sum() - 1.0) <= 1e-14 and np.array_equal(t2.weights[1], t1.weights[2])
     with np.testing.assert_raises(ValueError):
         S.group_modes(t1, [[0, 2], [1]])
 
