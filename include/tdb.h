@@ -172,9 +172,13 @@ tdb_status tdb_push_snapshot(tdb_ctx* ctx, const void* V_next, tdb_step_info* in
  * prod N_n elements of the snapshot type).  Stream-ordered, no sync. */
 tdb_status tdb_reconstruct(tdb_ctx* ctx, void* V_out);
 
-/* Exact error of the current state against V_now (device) and one pass of the
- * Sec. 2.5 rule on it (re-initialising from V_now if it fires).  ranks_out:
- * host int[p] (nullable); eps_out: host (nullable).  Synchronises. */
+/* Exact error (Eq. 2.20) of the current state against V_now (device, same layout and
+ * type as the pushes) and one pass of the Sec. 2.5 rule on it, re-initialising by HOSVD
+ * of V_now if it fires.  Afterwards the state stands for V_now: V_now becomes the
+ * previous snapshot of the next push (borrowed as by tdb_push_snapshot).  ranks_out:
+ * host int[p] (nullable), the ranks after the rule; eps_out: host (nullable), the error
+ * after the rule.  Synchronises.  Errors as tdb_reinit; TDB_WARN_RANK_CAP when the error
+ * stays above eps_th at the rank caps. */
 tdb_status tdb_adapt_rank(tdb_ctx* ctx, const void* V_now, int* ranks_out, double* eps_out);
 
 /* Re-initialise the state from V_now (device snapshot, same layout and type as the
@@ -283,23 +287,59 @@ int64_t tdb_kernel_launches(void);
  * e.g. a simulation code that hands every byte of the GPU to its own pool
  * allocator, or runs where cudaMalloc is not allowed after start-up.  The paper
  * has no counterpart: this is a packaging of the existing computation.
- *   dims, ranks : host, ndim entries (2..4 modes; N_1 a multiple of 4; r_1, r_2 <= 32)
+ *   dims, ranks : host, ndim entries (layout of tdb_push_snapshot, mode 1 fastest)
  *   V_next, V_prev : device float snapshots (layout as above)
  *   A[n] : device float N_n x r_n, the weighted bases W_n U_n; w[n] : device double, N_n
  *   dS (prod r_n), Y[n] (the tensor with mode n of size N_n, other modes r_m) and
  *   dv2 (||V_next - V_prev||_W^2, one double): device outputs owned by the caller.
- * Scratch comes from a static device array of 16 MiB compiled into the library
- * (held by every GPU that loads it until process exit); sizes needing more are
- * refused with TDB_ERR_WORKSPACE before anything is launched.  The call allocates
- * nothing (no cudaMalloc or allocating library routine).  The first call on a
- * device looks up the array's device address once for that device; make that first
- * call before any stream capture.  All calls share the array and it keeps the last
- * call's contents (every value read is written earlier in the same call), so calls
- * that overlap on the GPU - on different streams or host threads - race.  The call
- * synchronises `stream` and returns TDB_ERR_TIMEOUT if a bounded device wait ran out. */
+ * Refusals, all before anything is launched:
+ *   TDB_ERR_INVALID_ARG  ndim outside 2..4, or a NULL pointer argument;
+ *   TDB_ERR_SHAPE        some N_n < 1 or N_n > 1024;
+ *   TDB_ERR_RANK         some r_n < 1, r_n > N_n or r_n > TDB_MAX_RANK (32);
+ *   TDB_ERR_UNSUPPORTED  N_1 not a multiple of 4 (16-byte TMA row stride), r_1 or r_2
+ *                        above 32, the bases' BF16 images too large for shared memory,
+ *                        or a GPU that is not compute capability 10.x (tcgen05);
+ *   TDB_ERR_WORKSPACE    the sizes need more than the 16 MiB of static scratch.
+ * Scratch comes from a static device array of 16 MiB compiled into the library.  A
+ * device holds it from the moment the library's projection module is loaded there
+ * until process exit; CUDA loads modules lazily by default, so that is usually the
+ * first call on the device that runs a tensor-core projection (this entry point, or
+ * a TDB_BF16_TTM context's first step).  A caller whose pool allocator will reserve
+ * the whole GPU should make its first call on each device before the pool does, or
+ * the module load can fail (TDB_ERR_CUDA).  The call allocates nothing (no cudaMalloc
+ * or allocating library routine).  The first call on a device also looks up the
+ * array's device address once for that device; make that first call before any
+ * stream capture.  All calls share the array and it keeps the last call's contents
+ * (every value read is written earlier in the same call), so calls that overlap on
+ * the GPU - on different streams or host threads - race.  Each call ends by
+ * synchronising `stream`, and returns TDB_ERR_TIMEOUT if a bounded device wait ran
+ * out. */
 tdb_status tdb_project_noalloc(int ndim, const int64_t* dims, const int* ranks, const float* V_next,
                                const float* V_prev, const float* const* A, const double* const* w, float* dS,
                                float* const* Y, double* dv2, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Diagnostics.  The paper has no counterpart: these exercise the library's own device
+ * arithmetic and failure handling, for tests.
+ *
+ * tdb_selftest_recip: the double reciprocal and reciprocal square root the small-matrix
+ *   kernels use (Newton-Raphson from a float seed, see k_update.cu) over n doubles:
+ *   rcp[i] = 1/x[i], rsqrt[i] = 1/sqrt(x[i]) for x[i] > 0 (0 otherwise).  x, rcp, rsqrt:
+ *   device arrays of n doubles owned by the caller.  Synchronises `stream`.
+ *   TDB_ERR_INVALID_ARG for a NULL pointer or n < 0.
+ * tdb_selftest_timeout: makes one of the library's bounded device waits run out on
+ *   purpose - which = 0: the fused update's grid barrier, launched on two co-resident
+ *   CTAs and waiting for a third arrival; which = 1: the projection kernel's mbarrier
+ *   wait, on a barrier nothing arrives at - with a limit of limit_cycles SM clock
+ *   cycles (1 .. 4e9) instead of the usual ~2 s.  scratch: device, >= 16 bytes, owned by
+ *   the caller (barrier counter and status word; cleared here).  The kernel returns
+ *   after the limit with the timeout bit set; the call synchronises `stream` and
+ *   returns TDB_ERR_TIMEOUT (the expected result), TDB_OK if the wait ended otherwise,
+ *   TDB_ERR_INVALID_ARG for bad arguments or TDB_ERR_CUDA.  The CUDA context stays
+ *   usable afterwards.
+ * ------------------------------------------------------------------------- */
+tdb_status tdb_selftest_recip(const double* x, double* rcp, double* rsqrt, int64_t n, void* stream);
+tdb_status tdb_selftest_timeout(int which, int64_t limit_cycles, unsigned* scratch, void* stream);
 
 /* Library version and build facts: "tdb <ver> sm_103a". */
 /* ---------------------------------------------------------------------------

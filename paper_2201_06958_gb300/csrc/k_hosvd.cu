@@ -252,6 +252,15 @@ __global__ void k_si_start(T* __restrict__ Q, int n, int m) {
     Q[e] = (T)hash_unit((uint32_t)(e % n), (uint32_t)(e / n));
 }
 
+// Warm start: the first k0 columns from Q0 (n x k0, a previous solve), the rest hash columns.
+template <typename T>
+__global__ void k_si_warm(T* __restrict__ Q, int n, int m, const double* __restrict__ Q0, int k0) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)n * m; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t col = e / n;
+    Q[e] = col < k0 ? (T)Q0[e] : (T)hash_unit((uint32_t)(e % n), (uint32_t)col);
+  }
+}
+
 // Z = C Q   (C: n x n, Q and Z: n x m, all leading dim n).  Block = 32 rows x 8 cols.
 template <typename T>
 __global__ void k_si_gemm(const T* __restrict__ C, const T* __restrict__ Q, T* __restrict__ Z, int n, int m) {
@@ -413,7 +422,8 @@ template tdb_status eig_leading_small<double>(const double*, const double*, int,
 
 template <typename T>
 tdb_status eig_subspace(const T* Cc, const double* C64, int n, int k, int iters, const SubspaceWs<T>& ws,
-                        unsigned* flags, double* ev, double* Q, double* trace, double* scratch, cudaStream_t s) {
+                        unsigned* flags, double* ev, double* Q, double* trace, double* scratch, cudaStream_t s,
+                        const double* Q0) {
   const int m = std::min(n, std::min(64, k + 16));
   const int mm = (m + 1) & ~1;
   int blocks_nm = (int)std::min<int64_t>(((int64_t)n * m + 255) / 256, 1024);
@@ -435,7 +445,11 @@ tdb_status eig_subspace(const T* Cc, const double* C64, int n, int k, int iters,
   const double s0 = 11.0 * ((double)n * m + (double)m * (m + 1)) * u * m;
   const size_t ci_smem = 2 * 64 * 64 * sizeof(T);
   const int inner_blocks = (m * m * 32 + 255) / 256;
-  k_si_start<T><<<blocks_nm, 256, 0, s>>>(ws.Q, n, m); count_launch();
+  if (Q0) {
+    k_si_warm<T><<<blocks_nm, 256, 0, s>>>(ws.Q, n, m, Q0, std::min(k, m)); count_launch();
+  } else {
+    k_si_start<T><<<blocks_nm, 256, 0, s>>>(ws.Q, n, m); count_launch();
+  }
   for (int it = 0; it < iters; ++it) {
     k_si_gemm<T><<<ggrid, 256, 0, s>>>(Cc, ws.Q, ws.Z, n, m); count_launch();
     k_si_inner<T><<<inner_blocks, 256, 0, s>>>(ws.Z, ws.Z, n, m, ws.G); count_launch();
@@ -468,9 +482,9 @@ tdb_status eig_subspace(const T* Cc, const double* C64, int n, int k, int iters,
   return TDB_OK;
 }
 template tdb_status eig_subspace<float>(const float*, const double*, int, int, int, const SubspaceWs<float>&, unsigned*,
-                                        double*, double*, double*, double*, cudaStream_t);
+                                        double*, double*, double*, double*, cudaStream_t, const double*);
 template tdb_status eig_subspace<double>(const double*, const double*, int, int, int, const SubspaceWs<double>&,
-                                         unsigned*, double*, double*, double*, double*, cudaStream_t);
+                                         unsigned*, double*, double*, double*, double*, cudaStream_t, const double*);
 
 // U = W^{-1/2} Q[:, :r] (before the Cholesky-QR that makes U^T W U = I exact)
 __global__ void k_scale_basis(const double* __restrict__ Q, const double* __restrict__ w, int64_t n, int r,

@@ -27,6 +27,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "small_dev.cuh"
+#include "tc_project.h"
 
 namespace tdb {
 
@@ -38,11 +39,18 @@ constexpr size_t kUpdSmem = 48 * 1024;   // largest phase: the Gram finish, 45.6
 constexpr int GJ_THREADS = 256;          // threads 0..255 invert G_n by Gauss-Jordan
 
 // ---------------------------------------------------------------------------
-// Double reciprocal and reciprocal square root.  The float seed is built from the
-// bit pattern with integer operations (no double-pipe conversion) and refined to a
-// residual of the seed's error to the fourth power (two Newton steps; for the
-// reciprocal the second step's square is formed alongside the first, three
-// dependent operations); |x| outside [2^-120, 2^120] takes the plain division.
+// Double reciprocal and reciprocal square root by Newton-Raphson iteration from a
+// float seed (the textbook method; e.g. P. Markstein, IA-64 and Elementary
+// Functions, 2000, ch. 8).  The seed is the hardware float approximation
+// (rcp.approx / rsqrt.approx) of x truncated to float, built from the bit pattern with
+// integer operations (no double-pipe conversion).  Reciprocal: with e0 = 1 - x y0,
+// Newton's step on f(y) = 1/y - x gives y1 = y0 (1 + e0), whose residual is e0^2; a
+// second step y1 (1 + e0^2) leaves e0^4 (the square formed alongside the first step,
+// three dependent operations).  Reciprocal square root: two Newton steps on
+// f(y) = 1/y^2 - x, y <- y + (y/2)(1 - x y^2), each squaring the relative error.  The
+// float seed is good to about 2^-22, so two steps leave far less than one double ulp
+// before the final rounding; tests check both against 1/x and 1/sqrt(x) within 2 ulp.
+// |x| outside [2^-120, 2^120] takes the plain division (and square root).
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool seedable(double x) {
   const unsigned e = ((unsigned)__double2hiint(x) >> 20) & 0x7ffu;
@@ -360,15 +368,16 @@ __device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
 __device__ __forceinline__ void red_release_gpu(unsigned* p, unsigned v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
+constexpr long long kGridWaitCycles = 4000000000ll;   // ~2 s at 2 GHz
 __device__ __forceinline__ bool grid_sync(unsigned* count, unsigned k, unsigned nblocks, unsigned* flags,
-                                          volatile int* abort_sh) {
+                                          volatile int* abort_sh, long long limit = kGridWaitCycles) {
   __syncthreads();
   if (threadIdx.x == 0) {
     red_release_gpu(count, 1u);
     const unsigned target = k * nblocks;
     const long long t0 = clock64();
     while (ld_acquire_gpu(count) < target) {
-      if (clock64() - t0 > 4000000000ll || (ld_acquire_gpu(flags) & kFlagTimeout)) {
+      if (clock64() - t0 > limit || (ld_acquire_gpu(flags) & kFlagTimeout)) {
         atomicOr(flags, kFlagTimeout);
         *abort_sh = 1;
         break;
@@ -963,23 +972,43 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_update(UpdArgs a) {
     *t_out = task - tile_base[n];
   };
 
-  // 1: M, X, partial P; the last CTA also forms dS = Y_3 x_3 A_3^T when the projection
-  // left it (read from phase 4 on)
+  // 1: M, X, partial P; dS = Y_2 x_2 A_2^T when the projection left it
   for (int task = blockIdx.x; task < ntiles_total; task += nb) {
     int n, t;
     tile_of(task, &n, &t);
     rows_mxp<Tc>(a, n, (int64_t)t * 32, t, smraw);
   }
-  if (a.y3 && blockIdx.x == nb - 1) {
-    const Tc* Y3 = (const Tc*)a.y3;
-    const Tc* A3 = (const Tc*)a.A[2];
-    const int r12 = d.r[0] * d.r[1], r3 = d.r[2];
-    const int N3 = (int)d.N[2];
-    for (int e = threadIdx.x; e < r12 * r3; e += blockDim.x) {
-      const int a12 = e % r12, c = e / r12;
-      Tc s = Tc(0);
-      for (int sl = 0; sl < N3; ++sl) s += Y3[a12 + (int64_t)r12 * sl] * A3[sl + (int64_t)N3 * c];
-      ((Tc*)a.dS_out)[e] = s;
+  if (a.ds_y2) {
+    // dS = Y_2 x_2 A_2^T (Eqs. 2.15/2.16: dS = Y_n x_n A_n^T for every n), read from
+    // phase 4 on.  Eight consecutive threads share one element (every CTA takes a share
+    // of the elements): each sums every eighth i2 with all its loads in flight, then the
+    // eight partial sums are added by shuffles in a fixed order.
+    const Tc* Y2 = (const Tc*)a.ds_y2;
+    const Tc* A2 = (const Tc*)a.A[1];
+    const int r1 = d.r[0], r2 = d.r[1];
+    const int N2 = (int)d.N[1];
+    const int64_t tot = prod_r(d);
+    const int grp = threadIdx.x >> 3, part = threadIdx.x & 7;
+    const int ngrp = blockDim.x >> 3;
+    const int64_t stride = (int64_t)nb * ngrp;
+    const int64_t rounds = (tot + stride - 1) / stride;
+    for (int64_t k = 0; k < rounds; ++k) {
+      const int64_t e = blockIdx.x + (int64_t)nb * grp + stride * k;
+      Tc acc = Tc(0);
+      if (e < tot) {
+        const int a1 = (int)(e % r1);
+        const int64_t rest = e / r1;
+        const int b = (int)(rest % r2);
+        const int64_t q = rest / r2;
+        const Tc* y = Y2 + a1 + (int64_t)r1 * N2 * q;      // Y_2[a1 + r1 (i2 + N2 q)]
+        const Tc* A = A2 + (int64_t)N2 * b;
+#pragma unroll 16
+        for (int i2 = part; i2 < N2; i2 += 8) acc += __ldcg(&y[(int64_t)r1 * i2]) * A[i2];
+      }
+      acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      if (e < tot && part == 0) ((Tc*)a.dS_out)[e] = acc;
     }
   }
   if (!grid_sync(a.bar, ++nbar, nb, a.flags, &abort_sh)) return;
@@ -1106,4 +1135,68 @@ tdb_status launch_update(UpdArgs& a, int grid_hint, cudaStream_t s) {
 template tdb_status launch_update<float>(UpdArgs&, int, cudaStream_t);
 template tdb_status launch_update<double>(UpdArgs&, int, cudaStream_t);
 
+// ---------------------------------------------------------------------------
+// Diagnostics (tdb_selftest_recip, tdb_selftest_timeout): the double reciprocal helpers
+// over an array, and the update kernel's grid barrier waiting for one CTA more than the
+// grid holds - an arrival that never comes - so that its bounded wait runs out.
+// ---------------------------------------------------------------------------
+__global__ void k_selftest_recip(const double* __restrict__ x, double* __restrict__ rcp, double* __restrict__ rs,
+                                 int64_t n) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = x[i];
+    rcp[i] = drcp(v);
+    rs[i] = v > 0.0 ? drsqrt(v) : 0.0;
+  }
+}
+
+__global__ void k_selftest_gridwait(unsigned* bar, unsigned* flags, long long limit) {
+  __shared__ int abort_sh;
+  if (threadIdx.x == 0) abort_sh = 0;
+  grid_sync(bar, 1u, gridDim.x + 1u, flags, &abort_sh, limit);
+}
+
 }  // namespace tdb
+
+extern "C" tdb_status tdb_selftest_recip(const double* x, double* rcp, double* rsqrt, int64_t n, void* stream) {
+  using namespace tdb;
+  if (!x || !rcp || !rsqrt || n < 0) return TDB_ERR_INVALID_ARG;
+  if (n == 0) return TDB_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int blocks = (int)std::min<int64_t>((n + 255) / 256, 1024);
+  k_selftest_recip<<<blocks, 256, 0, s>>>(x, rcp, rsqrt, n);
+  count_launch();
+  if (cudaGetLastError() != cudaSuccess) return TDB_ERR_CUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? TDB_OK : TDB_ERR_CUDA;
+}
+
+extern "C" tdb_status tdb_selftest_timeout(int which, int64_t limit_cycles, unsigned* scratch, void* stream) {
+  using namespace tdb;
+  if (!scratch || limit_cycles < 1 || limit_cycles > 4000000000ll || (which != 0 && which != 1))
+    return TDB_ERR_INVALID_ARG;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMemsetAsync(scratch, 0, 4 * sizeof(unsigned), s) != cudaSuccess) return TDB_ERR_CUDA;
+  unsigned* flags = scratch + 2;
+  if (which == 0) {
+    // two co-resident CTAs (cooperative launch): the barrier's target is three arrivals
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2);
+    cfg.blockDim = dim3(32);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (cudaLaunchKernelEx(&cfg, k_selftest_gridwait, scratch, flags, (long long)limit_cycles) != cudaSuccess)
+      return TDB_ERR_CUDA;
+    count_launch();
+  } else {
+    const tdb_status st = tc_selftest_mbar_wait(flags, (long long)limit_cycles, s);
+    if (st != TDB_OK) return st;
+  }
+  unsigned h = 0;
+  if (cudaMemcpyAsync(&h, flags, sizeof(unsigned), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return TDB_ERR_CUDA;
+  return (h & kFlagTimeout) ? TDB_ERR_TIMEOUT : TDB_OK;
+}

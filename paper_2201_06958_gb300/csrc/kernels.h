@@ -55,7 +55,7 @@ struct UpdArgs {
   ModeDesc d;
   const void* Y[kMaxModes];      // projections Y_n (Tc)
   const void* dS;                // core increment (Tc)
-  const void* y3;                // Y_3 (Tc, three modes): when set, phase 1 forms dS = Y_3 x_3 A_3^T
+  const void* ds_y2;             // Y_2 (Tc): when set, phase 1 forms dS = Y_2 x_2 A_2^T
   void* dS_out;                  // ... into this buffer (the one dS points to)
   double* T;                     // core (in: step k, out: step k+1)
   double* T2;                    // scratch core
@@ -174,8 +174,11 @@ struct SubspaceWs {
   T* JV;       // 64 x 64
 };
 template <typename T>
+// Q0 (nullable, n x k doubles, may be Q itself): warm start from a previous solve instead
+// of hash columns.
 tdb_status eig_subspace(const T* Cc, const double* C64, int n, int k, int iters, const SubspaceWs<T>& ws,
-                        unsigned* flags, double* ev, double* Q, double* trace, double* scratch, cudaStream_t s);
+                        unsigned* flags, double* ev, double* Q, double* trace, double* scratch, cudaStream_t s,
+                        const double* Q0 = nullptr);
 void launch_scale_basis(const double* Q, const double* w, int64_t n, int r, double* U, cudaStream_t s);
 
 }  // namespace tdb

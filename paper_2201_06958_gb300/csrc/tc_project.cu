@@ -96,13 +96,14 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 
 // Bounded wait on a phase parity.  Returns false (and raises the abort flag) on
 // timeout or when another role already aborted.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* flags) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* flags,
+                                          long long limit = TIMEOUT_CYCLES) {
   long long t0 = clock64();
   for (int it = 0;; ++it) {
     if (mbar_try_wait(bar, parity)) return true;
     if ((it & 255) == 255) {
       if (*abort_flag) return false;
-      if (clock64() - t0 > TIMEOUT_CYCLES) {
+      if (clock64() - t0 > limit) {
         *abort_flag = 1;
         atomicOr(flags, kFlagTimeout);
         return false;
@@ -471,6 +472,21 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   }
 }
 
+// Diagnostic: the projection kernel's bounded mbarrier wait on a barrier that no thread
+// and no copy ever arrives at, so that the wait runs out and raises the timeout flag.
+__global__ void k_selftest_mbar(unsigned* flags, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ int abort_flag;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    abort_flag = 0;
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) mbar_wait(smem_u32(&bar), 0, &abort_flag, flags, limit);
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // BF16 operand images of the weighted bases (K-major, 128-byte swizzle):
 // 64-row K blocks of rpad rows x 128 B; element (k, a) of block g at
@@ -496,111 +512,160 @@ __global__ void k_pack_bimg(const float* __restrict__ A1, int N1, int r1, int rp
   }
 }
 
-// Z1 (r1 x N2 x S, column-major) and Z2 (N1 x r2 x S) from the tile partials.
-__global__ void k_tc_reduce(const float* __restrict__ Z1p, const float* __restrict__ Z2p, int N1, int N2, int nslice,
-                            int nq1, int nq2, int r1, int r2, float* __restrict__ Z1, float* __restrict__ Z2) {
-  const int64_t n1 = (int64_t)r1 * N2 * nslice, n2 = (int64_t)N1 * r2 * nslice;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n1 + n2; e += (int64_t)gridDim.x * blockDim.x) {
-    if (e < n1) {
-      // e = a + r1 (i2 + N2 s); partial index [q][s][i2][a] is the same offset within each q
-      float s = 0.f;
-      for (int q = 0; q < nq1; ++q) s += Z1p[q * n1 + e];
-      Z1[e] = s;
-    } else {
-      const int64_t f = e - n1;                  // f = i1 + N1 (b + r2 s)
-      const int64_t i1 = f % N1;
-      const int64_t bs = f / N1;
-      const int64_t b = bs % r2, sl = bs / r2;
-      float s = 0.f;
-      for (int q = 0; q < nq2; ++q) s += Z2p[((q * nslice + sl) * (int64_t)N1 + i1) * r2 + b];
-      Z2[f] = s;
-    }
-  }
-}
+// Finish, first launch.  The fused kernel leaves partial first contractions over the
+// tiles q of the contracted mode: Z1p at e + n1 (s + S q), e = a + r1 i2, n1 = r1 N2
+// (mode 1 contracted), and Z2p at f + n2 (s + S q), f = b + r2 i1, n2 = N1 r2 (mode 2
+// contracted), s the slice (i3 + N3 i4).  This launch sums them over q and contracts the
+// slices with B (S x J):
+//   Y_2[e + n1 j] = sum_s Z1[e, s] B[s, j],    Y_1[i1 + N1 (b + r2 j)] = sum_s Z2[f, s] B[s, j],
+// with B = A_3 (three modes), B[i3 + N3 i4, c + r3 d] = A_3[i3, c] A_4[i4, d] (four modes,
+// the Kronecker product that contracts modes 3 and 4 at once) or the 1 x 1 identity (two
+// modes).  It also writes Z1 = sum_q Z1p when there is more than one tile along mode 1
+// (the next launch forms Y_3 from it) and, in its first CTA, ||dV||_W^2 from the fused
+// kernel's per-CTA partials.  A CTA owns 64 elements of one side and one of `nsplit`
+// slice ranges; with nsplit > 1 each CTA writes its partial and the last CTA of the
+// tile to arrive sums the partials in split order (the same order whichever CTA is
+// last, so results do not vary from run to run) and resets the tile's counter.
+constexpr int FS_TE = 64, FS_SC = 64, FS_JMAX = 128, FS_SPLIT_MAX = 32;
+struct FinArgs {
+  const float* Z1p;
+  const float* Z2p;
+  int N1, N2, S, nq1, nq2, r1, r2;
+  const float* A3;       // N3 x r3 (null: two modes, B = [1])
+  const float* A4;       // N4 x r4 (null: three modes)
+  int N3, r3, N4, r4, J;
+  float* Z1;             // r1 x N2 x S (written when nq1 > 1)
+  float* Y2;
+  float* Y1;
+  float* part;           // [tile][split][J][64]
+  unsigned* cnt;         // per tile, zero between launches
+  int nsplit, nt1, nt2;
+  const double* npart;
+  int nnp;
+  double* dv2;
+};
 
-// Three-mode finish, first launch.  A CTA owns a tile of 64 elements: of Z1 (r1 x N2,
-// element e = a + r1 i2) or of Z2 (element f = b + r2 i1).  For slices in chunks of
-// 16 it stages z[s][e] = sum_q of the partials (one coalesced pass, all loads of a
-// chunk in flight), writes Z1, and accumulates Y_2 = Z1 x_3 A_3^T or
-// Y_1 = Z2 x_3 A_3^T from shared memory (thread per (element, c), c < r3 <= 32).
-// Both partial layouts put (element, slice, tile q) at e + n (q S + s).  CTA 0 also
-// adds the per-CTA ||dV||_W^2 partials.
-constexpr int FA_TE = 64, FA_SC = 16;
-__global__ void __launch_bounds__(256) k_tc_finish_a(const float* __restrict__ Z1p, const float* __restrict__ Z2p,
-                                                     int N1, int N2, int S, int nq1, int nq2, int r1, int r2, int r3,
-                                                     const float* __restrict__ A3, float* __restrict__ Z1,
-                                                     float* __restrict__ Y2, float* __restrict__ Y1,
-                                                     const double* __restrict__ npart, int nnp,
-                                                     double* __restrict__ dv2) {
-  __shared__ float zs[FA_SC][FA_TE + 1];
-  __shared__ float as[FA_SC][33];
+template <int JT>   // accumulators per thread: outputs j = jg + 4 t, t < JT (J <= 4 JT)
+__global__ void __launch_bounds__(256) k_tc_finish_sk(FinArgs f) {
+  extern __shared__ float fs_sm[];
+  float (*zs)[FS_TE + 1] = (float(*)[FS_TE + 1])fs_sm;       // [FS_SC][65]
+  float* bs = fs_sm + FS_SC * (FS_TE + 1);                    // [FS_SC][J]
+  __shared__ int last_sh;
+  __shared__ double dsh[32];
   const int tid = threadIdx.x;
+  const int tile = blockIdx.x / f.nsplit, sp = blockIdx.x % f.nsplit;
   if (blockIdx.x == 0) {
-    __shared__ double sh[32];
     double t = 0.0;
-    for (int i = tid; i < nnp; i += blockDim.x) t += npart[i];
-    t = block_sum(t, sh);
-    if (tid == 0) *dv2 = t;
+    for (int i = tid; i < f.nnp; i += blockDim.x) t += f.npart[i];
+    t = block_sum(t, dsh);
+    if (tid == 0) *f.dv2 = t;
   }
-  const int64_t n1 = (int64_t)r1 * N2, n2 = (int64_t)N1 * r2;
-  const int nt1 = (int)((n1 + FA_TE - 1) / FA_TE), nt2 = (int)((n2 + FA_TE - 1) / FA_TE);
-  for (int tile = blockIdx.x; tile < nt1 + nt2; tile += gridDim.x) {
-    const bool first = tile < nt1;
-    const int64_t e0 = (int64_t)(first ? tile : tile - nt1) * FA_TE;
-    const int64_t ne = first ? n1 : n2;
-    const int nq = first ? nq1 : nq2;
-    const float* Pp = first ? Z1p : Z2p;
-    float acc[8];
+  const bool first = tile < f.nt1;
+  const int64_t ne = first ? (int64_t)f.r1 * f.N2 : (int64_t)f.N1 * f.r2;
+  const int64_t e0 = (int64_t)(first ? tile : tile - f.nt1) * FS_TE;
+  const int nq = first ? f.nq1 : f.nq2;
+  const float* Pp = first ? f.Z1p : f.Z2p;
+  const bool write_z = first && f.nq1 > 1;
+  const int J = f.J;
+  const int s_lo = (int)((int64_t)f.S * sp / f.nsplit), s_hi = (int)((int64_t)f.S * (sp + 1) / f.nsplit);
+  const int el = tid % FS_TE, jg = tid / FS_TE;           // outputs (el, j = jg + 4 t)
+  float acc[JT];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j] = 0.f;
-    for (int s0 = 0; s0 < S; s0 += FA_SC) {
-      const int sc = min(FA_SC, S - s0);
+  for (int t = 0; t < JT; ++t) acc[t] = 0.f;
+  for (int s0 = s_lo; s0 < s_hi; s0 += FS_SC) {
+    const int sc = min(FS_SC, s_hi - s0);
+    // partial sums over q: all loads of the chunk in flight together
 #pragma unroll
-      for (int u = 0; u < FA_SC * FA_TE / 256; ++u) {
-        const int idx = tid + 256 * u;
-        const int el = idx % FA_TE, sl = idx / FA_TE;
-        const int64_t e = e0 + el;
-        const bool in = sl < sc && e < ne;
-        const float* pe = Pp + e + ne * (int64_t)(s0 + sl);
-        float v[4];
+    for (int u = 0; u < FS_SC * FS_TE / 256; ++u) {
+      const int idx = tid + 256 * u;
+      const int xl = idx % FS_TE, sl = idx / FS_TE;
+      const int64_t e = e0 + xl;
+      const bool in = sl < sc && e < ne;
+      const float* pe = Pp + e + ne * (int64_t)(s0 + sl);
+      float v[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) v[q] = (in && q < nq) ? __ldcg(&pe[ne * (int64_t)q * S]) : 0.f;
-        float z = ((v[0] + v[1]) + v[2]) + v[3];
-        if (in) {
-          for (int q = 4; q < nq; ++q) z += __ldcg(&pe[ne * (int64_t)q * S]);
-          if (first) Z1[e + n1 * (s0 + sl)] = z;
-        }
-        zs[sl][el] = z;
+      for (int q = 0; q < 4; ++q) v[q] = (in && q < nq) ? __ldcg(&pe[ne * (int64_t)q * f.S]) : 0.f;
+      float z = ((v[0] + v[1]) + v[2]) + v[3];
+      if (in) {
+        for (int q = 4; q < nq; ++q) z += __ldcg(&pe[ne * (int64_t)q * f.S]);
+        if (write_z) f.Z1[e + ne * (int64_t)(s0 + sl)] = z;
       }
-      for (int idx = tid; idx < FA_SC * 32; idx += 256) {
-        const int sl = idx / 32, c = idx % 32;
-        as[sl][c] = (sl < sc && c < r3) ? __ldg(&A3[s0 + sl + (int64_t)S * c]) : 0.f;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int pidx = tid + 256 * j;
-        const int el = pidx % FA_TE, c = pidx / FA_TE;
-        if (c < r3)
-          for (int sl = 0; sl < sc; ++sl) acc[j] = fmaf(as[sl][c], zs[sl][el], acc[j]);
-      }
-      __syncthreads();
+      zs[sl][xl] = z;
     }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int pidx = tid + 256 * j;
-      const int el = pidx % FA_TE, c = pidx / FA_TE;
-      const int64_t e = e0 + el;
-      if (c < r3 && e < ne) {
-        if (first) {
-          Y2[e + n1 * c] = acc[j];
+    for (int idx = tid; idx < FS_SC * J; idx += 256) {
+      const int sl = idx / J, j = idx % J;
+      float bv = 0.f;
+      if (sl < sc) {
+        const int s = s0 + sl;
+        if (!f.A3) {
+          bv = 1.f;
+        } else if (!f.A4) {
+          bv = __ldg(&f.A3[s + (int64_t)f.N3 * j]);
         } else {
-          const int64_t b = e % r2, i1 = e / r2;
-          Y1[i1 + (int64_t)N1 * (b + (int64_t)r2 * c)] = acc[j];
+          const int i3 = s % f.N3, i4 = s / f.N3, c = j % f.r3, dd = j / f.r3;
+          bv = __ldg(&f.A3[i3 + (int64_t)f.N3 * c]) * __ldg(&f.A4[i4 + (int64_t)f.N4 * dd]);
         }
       }
+      bs[sl * J + j] = bv;
     }
+    __syncthreads();
+    for (int sl = 0; sl < sc; ++sl) {
+      const float z = zs[sl][el];
+#pragma unroll
+      for (int t = 0; t < JT; ++t) {
+        const int j = jg + 4 * t;
+        if (j < J) acc[t] = fmaf(bs[sl * J + j], z, acc[t]);
+      }
+    }
+    __syncthreads();
   }
+  auto store = [&](int64_t e, int j, float v) {
+    if (e >= ne) return;
+    if (first) {
+      f.Y2[e + ne * (int64_t)j] = v;
+    } else {
+      const int64_t b = e % f.r2, i1 = e / f.r2;
+      f.Y1[i1 + (int64_t)f.N1 * (b + (int64_t)f.r2 * j)] = v;
+    }
+  };
+  if (f.nsplit == 1) {
+#pragma unroll
+    for (int t = 0; t < JT; ++t) {
+      const int j = jg + 4 * t;
+      if (j < J) store(e0 + el, j, acc[t]);
+    }
+    return;
+  }
+  float* mine = f.part + ((int64_t)tile * f.nsplit + sp) * (int64_t)J * FS_TE;
+#pragma unroll
+  for (int t = 0; t < JT; ++t) {
+    const int j = jg + 4 * t;
+    if (j < J) mine[j * FS_TE + el] = acc[t];
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) {
+    const unsigned prev = atomicAdd(&f.cnt[tile], 1u);
+    last_sh = (prev == (unsigned)f.nsplit - 1u);
+  }
+  __syncthreads();
+  if (!last_sh) return;
+  __threadfence();
+  // the tile's J x 64 outputs, each the sum of nsplit partials in split order; every
+  // load of an output is issued before the additions
+  const float* base = f.part + (int64_t)tile * f.nsplit * J * FS_TE;
+  for (int o = tid; o < J * FS_TE; o += blockDim.x) {
+    const int j = o / FS_TE, x = o % FS_TE;
+    float vals[FS_SPLIT_MAX];
+#pragma unroll
+    for (int q = 0; q < FS_SPLIT_MAX; ++q)
+      vals[q] = q < f.nsplit ? __ldcg(&base[((int64_t)q * J + j) * FS_TE + x]) : 0.f;
+    float v = 0.f;
+#pragma unroll
+    for (int q = 0; q < FS_SPLIT_MAX; ++q) v += vals[q];
+    store(e0 + x, j, v);
+  }
+  if (tid == 0) f.cnt[tile] = 0u;
 }
 
 // Three-mode finish, second launch: Y_3 = Z1 x_2 A_2^T (r1 x r2 x S), a CTA per
@@ -699,6 +764,12 @@ int rpad_of(int r) { return r <= 16 ? 16 : 32; }
 
 }  // namespace
 
+tdb_status tc_selftest_mbar_wait(unsigned* flags, long long limit, cudaStream_t s) {
+  k_selftest_mbar<<<1, 32, 0, s>>>(flags, limit);
+  count_launch();
+  return cudaGetLastError() == cudaSuccess ? TDB_OK : TDB_ERR_CUDA;
+}
+
 bool tc_supported(int p, const int64_t* N, const int* cap, std::string& err) {
   if (p < 2 || p > 4) { err = "needs 2..4 modes"; return false; }
   if (N[0] % 4 != 0) { err = "N_1 must be a multiple of 4 (16-byte TMA row stride)"; return false; }
@@ -728,6 +799,14 @@ void tc_carve(TcPlan& plan, Carver& cv, int p, const int64_t* N, const int* cap)
   plan.wsl = cv.take<double>((size_t)nslice);
   plan.w12f = cv.take<float>((size_t)(nq1 + nq2) * TILE);
   plan.npart = cv.take<double>(1024);
+  // finish: split partials ((3 x 152 + tiles) x 64 x J floats bounds nsplit x tiles x 64 x J
+  // for the split count the launch picks) and one arrival counter per tile
+  const int jmax = p == 2 ? 1 : (p == 3 ? cap[2] : cap[2] * cap[3]);
+  const int64_t ntmax = ((int64_t)cap[0] * N[1] + FS_TE - 1) / FS_TE + ((int64_t)N[0] * cap[1] + FS_TE - 1) / FS_TE;
+  plan.fpart_cap = (size_t)(3 * 152 + ntmax) * FS_TE * jmax;
+  plan.fpart = cv.take<float>(plan.fpart_cap);
+  plan.fcnt_n = (int)ntmax;
+  plan.fcnt = cv.take<unsigned>((size_t)ntmax);
 }
 
 tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, const int64_t* N, const int* r,
@@ -815,73 +894,93 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
     err = std::string("k_tc_project launch: ") + cudaGetErrorString(e);
     return TDB_ERR_CUDA;
   }
-  if (tc_defers_ds(p, N, r)) {
-    // two launches: the partial sums with Y_2, Y_1 and ||dV||^2, then Y_3; dS follows in
-    // the update kernel (defer_ds) or as one mode product here
-    const int64_t ntile = ((int64_t)r[0] * N2 + FA_TE - 1) / FA_TE + ((int64_t)N1 * r[1] + FA_TE - 1) / FA_TE;
-    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>(ntile, 152 * 8));
-    k_tc_finish_a<<<blocks, 256, 0, s>>>(plan.z1p, plan.z2p, N1, N2, nslice, nq1, nq2, r[0], r[1], r[2],
-                                         (const float*)A[2], Z1, Y[1], Y[0], plan.npart, grid, dv2);
-    count_launch();
-    k_tc_finish_b<<<std::min(nslice, 152 * 8), 256, kFinishBSmem, s>>>(Z1, N2, nslice, r[0], r[1],
-                                                                       (const float*)A[1], Y[2]);
-    count_launch();
-    if (!defer_ds) {
-      const int64_t L = (int64_t)r[0] * r[1];
-      launch_modeprod<float, float, float>(Y[2], dS, (const float*)A[2], L, nslice, r[2], 1, nslice, 1, s);
-    }
-    e = cudaGetLastError();
-    if (e != cudaSuccess) {
-      err = std::string("projection finish: ") + cudaGetErrorString(e);
-      return TDB_ERR_CUDA;
-    }
-    return TDB_OK;
+  // finish: Y_1, Y_2 (and Z1) from the tile partials, the slices contracted with
+  // B = A_3 (x A_4); then Y_3 (three modes) or W = Z1 x_2 A_2^T (four modes) per slice
+  const int J = p == 2 ? 1 : (p == 3 ? r[2] : r[2] * r[3]);
+  const int nt1 = (int)(((int64_t)r[0] * N2 + FS_TE - 1) / FS_TE);
+  const int nt2 = (int)(((int64_t)N1 * r[1] + FS_TE - 1) / FS_TE);
+  int nsplit = (int)std::max<int64_t>(1, (3 * 152 + nt1 + nt2 - 1) / (nt1 + nt2));
+  nsplit = std::min({nsplit, std::max(1, nslice / FS_SC), FS_SPLIT_MAX});
+  while (nsplit > 1 && (size_t)nsplit * (nt1 + nt2) * FS_TE * J > plan.fpart_cap) --nsplit;
+  if (J > FS_JMAX) {
+    err = "finish: r_3 r_4 above 128";
+    return TDB_ERR_UNSUPPORTED;
   }
-  launch_sum_partials(plan.npart, grid, dv2, s);
-  // Z1 (r1 x N2 x S) and Z2 (N1 x r2 x S)
-  {
-    int64_t tot = (int64_t)r[0] * N2 * nslice + (int64_t)N1 * r[1] * nslice;
-    int blocks = (int)std::min<int64_t>((tot + 255) / 256, 152 * 8);
-    k_tc_reduce<<<blocks, 256, 0, s>>>(plan.z1p, plan.z2p, N1, N2, nslice, nq1, nq2, r[0], r[1], Z1, Z2);
-    count_launch();
+  if (!plan.fcnt_ready) {
+    cudaMemsetAsync(plan.fcnt, 0, sizeof(unsigned) * plan.fcnt_n, s);
+    plan.fcnt_ready = true;
   }
-  // remaining contractions on rank-sized tensors (mode products, FP32)
-  auto mp = [&](const float* in, float* out, int n, int64_t* cur) {
-    int64_t L = 1, Q = 1;
-    for (int m = 0; m < n; ++m) L *= cur[m];
-    for (int m = n + 1; m < p; ++m) Q *= cur[m];
-    launch_modeprod<float, float, float>(in, out, (const float*)A[n], L, (int)cur[n], r[n], Q, N[n], 1, s);
-    cur[n] = r[n];
-  };
-  if (p == 2) {
-    cudaMemcpyAsync(Y[1], Z1, sizeof(float) * r[0] * N2, cudaMemcpyDeviceToDevice, s);
-    cudaMemcpyAsync(Y[0], Z2, sizeof(float) * N1 * r[1], cudaMemcpyDeviceToDevice, s);
-    int64_t cur[kMaxModes] = {r[0], N2, 1, 1};
-    mp(Y[1], dS, 1, cur);
-  } else if (p == 3) {
-    int64_t c1[kMaxModes] = {r[0], N2, N[2], 1};
-    mp(Z1, Y[1], 2, c1);                               // Y_2 = Z1 x_3 A_3^T
-    int64_t c2[kMaxModes] = {r[0], N2, N[2], 1};
-    mp(Z1, Y[2], 1, c2);                               // Y_3 = Z1 x_2 A_2^T
-    int64_t c3[kMaxModes] = {N1, r[1], N[2], 1};
-    mp(Z2, Y[0], 2, c3);                               // Y_1 = Z2 x_3 A_3^T
-    int64_t c4[kMaxModes] = {r[0], r[1], N[2], 1};
-    mp(Y[2], dS, 2, c4);                               // dS = Y_3 x_3 A_3^T
-  } else {
-    int64_t a[kMaxModes] = {r[0], N2, N[2], N[3]};
-    mp(Z1, scratch, 3, a);                             // Z1 x_4
-    mp(scratch, Y[1], 2, a);                           // Y_2 = (Z1 x_4) x_3
-    int64_t b[kMaxModes] = {r[0], N2, N[2], N[3]};
-    mp(Z1, scratch, 3, b);
-    mp(scratch, Y[2], 1, b);                           // Y_3 = (Z1 x_4) x_2
-    int64_t c[kMaxModes] = {r[0], N2, N[2], N[3]};
-    mp(Z1, scratch, 2, c);
-    mp(scratch, Y[3], 1, c);                           // Y_4 = (Z1 x_3) x_2
-    int64_t d[kMaxModes] = {N1, r[1], N[2], N[3]};
-    mp(Z2, scratch, 3, d);
-    mp(scratch, Y[0], 2, d);                           // Y_1 = (Z2 x_4) x_3
-    int64_t f[kMaxModes] = {r[0], r[1], r[2], N[3]};
-    mp(Y[3], dS, 3, f);                                // dS = Y_4 x_4 A_4^T
+  if (nt1 + nt2 > plan.fcnt_n) {
+    err = "finish: tile counters exceeded";
+    return TDB_ERR_UNSUPPORTED;
+  }
+  FinArgs f;
+  f.Z1p = plan.z1p;
+  f.Z2p = plan.z2p;
+  f.N1 = N1;
+  f.N2 = N2;
+  f.S = nslice;
+  f.nq1 = nq1;
+  f.nq2 = nq2;
+  f.r1 = r[0];
+  f.r2 = r[1];
+  f.A3 = p >= 3 ? (const float*)A[2] : nullptr;
+  f.A4 = p >= 4 ? (const float*)A[3] : nullptr;
+  f.N3 = p >= 3 ? (int)N[2] : 1;
+  f.r3 = p >= 3 ? r[2] : 1;
+  f.N4 = p >= 4 ? (int)N[3] : 1;
+  f.r4 = p >= 4 ? r[3] : 1;
+  f.J = J;
+  f.Z1 = Z1;
+  f.Y2 = Y[1];
+  f.Y1 = Y[0];
+  f.part = plan.fpart;
+  f.cnt = plan.fcnt;
+  f.nsplit = nsplit;
+  f.nt1 = nt1;
+  f.nt2 = nt2;
+  f.npart = plan.npart;
+  f.nnp = grid;
+  f.dv2 = dv2;
+  const size_t fsm = sizeof(float) * (FS_SC * (FS_TE + 1) + FS_SC * J);
+  if (!plan.fin_attr) {
+    const int mx = (int)(sizeof(float) * (FS_SC * (FS_TE + 1) + FS_SC * FS_JMAX));
+    cudaFuncSetAttribute(k_tc_finish_sk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_tc_finish_sk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_tc_finish_sk<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_tc_finish_sk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_tc_finish_sk<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    cudaFuncSetAttribute(k_tc_finish_sk<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+    plan.fin_attr = true;
+  }
+  const dim3 fgrid((nt1 + nt2) * nsplit);
+  if (J <= 4) k_tc_finish_sk<1><<<fgrid, 256, fsm, s>>>(f);
+  else if (J <= 8) k_tc_finish_sk<2><<<fgrid, 256, fsm, s>>>(f);
+  else if (J <= 16) k_tc_finish_sk<4><<<fgrid, 256, fsm, s>>>(f);
+  else if (J <= 32) k_tc_finish_sk<8><<<fgrid, 256, fsm, s>>>(f);
+  else if (J <= 64) k_tc_finish_sk<16><<<fgrid, 256, fsm, s>>>(f);
+  else k_tc_finish_sk<32><<<fgrid, 256, fsm, s>>>(f);
+  count_launch();
+  if (p >= 3) {
+    // Z1 summed over the mode-1 tiles: the partials themselves when there is one tile
+    const float* z1 = nq1 > 1 ? Z1 : plan.z1p;
+    float* out = p == 3 ? Y[2] : scratch;
+    k_tc_finish_b<<<std::min(nslice, 152 * 8), 256, kFinishBSmem, s>>>(z1, N2, nslice, r[0], r[1],
+                                                                       (const float*)A[1], out);
+    count_launch();
+    if (p == 4) {
+      // Y_3 = W x_4 A_4^T and Y_4 = W x_3 A_3^T from W = Z1 x_2 A_2^T (r1 x r2 x N3 x N4)
+      const int64_t L12 = (int64_t)r[0] * r[1];
+      launch_modeprod<float, float, float>(scratch, Y[2], (const float*)A[3], L12 * N[2], (int)N[3], r[3], 1, N[3], 1,
+                                           s);
+      launch_modeprod<float, float, float>(scratch, Y[3], (const float*)A[2], L12, (int)N[2], r[2], N[3], N[2], 1, s);
+    }
+  }
+  if (!defer_ds) {
+    // dS = Y_2 x_2 A_2^T (otherwise the update kernel forms it)
+    int64_t Q = 1;
+    for (int n = 2; n < p; ++n) Q *= r[n];
+    launch_modeprod<float, float, float>(Y[1], dS, (const float*)A[1], r[0], N2, r[1], Q, N2, 1, s);
   }
   e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -914,10 +1013,11 @@ size_t noalloc_layout(Carver& cv, TcPlan& plan, int p, const int64_t* N, const i
   int64_t S = 1;
   for (int n = 0; n < p; ++n) S *= N[n];
   *Z1 = cv.take<float>((size_t)(S / N[0]) * r[0]);
-  *Z2 = cv.take<float>((size_t)(S / N[1]) * r[1]);
-  int64_t sc = 1;
-  for (int n = 0; n < p; ++n) sc = std::max<int64_t>(sc, S / N[n] * r[n]);
-  *scratch = cv.take<float>((size_t)sc);
+  *Z2 = nullptr;                                       // (the finish does not form Z2)
+  // W = Z1 x_2 A_2^T of four modes (r1 r2 N3 N4); at least one element
+  int64_t sc = (int64_t)r[0] * r[1];
+  for (int n = 2; n < p; ++n) sc *= N[n];
+  *scratch = cv.take<float>((size_t)std::max<int64_t>(sc, 1));
   return cv.off;
 }
 }  // namespace

@@ -15,19 +15,25 @@ struct TcPlan {
   double* wsl = nullptr;              // product of the weights of modes >= 3, per slice
   float* w12f = nullptr;              // float w_1, w_2, zero-padded to whole tiles
   double* npart = nullptr;            // per-CTA ||dV||_W^2
+  float* fpart = nullptr;             // split partials of the finishing contraction
+  size_t fpart_cap = 0;               // floats
+  unsigned* fcnt = nullptr;           // per-tile arrival counters of the finish (zero at rest)
+  int fcnt_n = 0;
+  bool fcnt_ready = false;
+  bool fin_attr = false;
   bool wsl_ready = false;
   bool attr_set = false;
 };
 
 bool tc_supported(int p, const int64_t* N, const int* cap, std::string& err);
-// Three modes with few slices (N_3 <= 64, r_3 <= 32): tc_project finishes with the two
-// fused launches (each CTA walks all slices, so many slices would serialise them) and
-// leaves dS = Y_3 x_3 A_3^T to the update kernel.
-inline bool tc_defers_ds(int p, const int64_t* N, const int* r) { return p == 3 && N[2] <= 64 && r[2] <= 32; }
+// One CTA waits on an mbarrier nothing arrives at, with the projection kernel's bounded
+// wait and the given limit (clock cycles); the timeout bit lands in *flags.
+tdb_status tc_selftest_mbar_wait(unsigned* flags, long long limit, cudaStream_t s);
 void tc_carve(TcPlan& plan, Carver& cv, int p, const int64_t* N, const int* cap);
-// dS (unless tc_defers_ds) and Y_n of dV = Vn - Vp (Eqs. 2.15, 2.16) and ||dV||_W^2 into *dv2.  A: FP32
-// weighted bases (N_n x r_n); w: mode weights; Z1 (r1 x N2 x S), Z2 (N1 x r2 x S)
-// and scratch (>= the largest intermediate) are device buffers of the caller.
+// Y_n of dV = Vn - Vp (Eqs. 2.15, 2.16), dS unless defer_ds (the update kernel then forms
+// dS = Y_2 x_2 A_2^T), and ||dV||_W^2 into *dv2.  A: FP32 weighted bases (N_n x r_n);
+// w: mode weights; Z1 (r1 x N2 x S) and scratch (>= r1 r2 prod_{n>2} N_n) are device
+// buffers of the caller; Z2 is not used.
 tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, const int64_t* N, const int* r,
                       const void* const* A, const double* const* w, float* Z1, float* Z2, float* scratch,
                       float* dS, float* const* Y, double* dv2, unsigned* flags, cudaStream_t s, cudaEvent_t* evm,

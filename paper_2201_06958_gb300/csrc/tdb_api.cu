@@ -90,6 +90,8 @@ struct tdb_ctx {
   unsigned long long* stamps;     // phase timer stamps of the fused update (profiling)
   int ntile = 1;
   double* sig2;
+  double* sig2_lag;               // sigma^2 of the state a step starts from (estimator features)
+  int* need_scratch;              // the estimator's gate word when it does not gate
   float* Vprev;
   float* Vprev_bak;
   double* npart;
@@ -330,6 +332,8 @@ void carve(tdb_ctx* c, Carver& cv) {
   c->wcolT = cv.take<char>((size_t)(c->S / c->N[0]) * tsz);
   c->stamps = cv.take<unsigned long long>(32);
   c->sig2 = cv.take<double>(p * kMaxRank);
+  c->sig2_lag = cv.take<double>(p * kMaxRank);
+  c->need_scratch = cv.take<int>(1);
   c->Vprev = cv.take<float>(p * kMaxRank * kMaxRank);
   c->Vprev_bak = cv.take<float>(p * kMaxRank * kMaxRank);
   c->nblk = 608;
@@ -341,17 +345,18 @@ void carve(tdb_ctx* c, Carver& cv) {
   int64_t nn = (Nmax + 1) & ~1;
   c->C64 = cv.take<double>(Nmax * Nmax);
   c->Cc = cv.take<char>(Nmax * Nmax * tsz);
+  // eigensolver blocks: double in every compute type (float contexts refine in double)
   int64_t nsmall = std::min<int64_t>(nn, 96);
-  c->jA = cv.take<char>(nsmall * nsmall * tsz);
-  c->jV = cv.take<char>(nsmall * nsmall * tsz);
-  c->siQ = cv.take<char>(Nmax * 64 * tsz);
-  c->siZ = cv.take<char>(Nmax * 64 * tsz);
-  c->siX = cv.take<char>(Nmax * 64 * tsz);
+  c->jA = cv.take<double>(nsmall * nsmall);
+  c->jV = cv.take<double>(nsmall * nsmall);
+  c->siQ = cv.take<double>(Nmax * 64);
+  c->siZ = cv.take<double>(Nmax * 64);
+  c->siX = cv.take<double>(Nmax * 64);
   c->siG = cv.take<double>(64 * 64);
   c->siR = cv.take<double>(64 * 64);
-  c->siH = cv.take<char>(64 * 64 * tsz);
-  c->siJA = cv.take<char>(64 * 64 * tsz);
-  c->siJV = cv.take<char>(64 * 64 * tsz);
+  c->siH = cv.take<double>(64 * 64);
+  c->siJA = cv.take<double>(64 * 64);
+  c->siJV = cv.take<double>(64 * 64);
   int ntile = (int)((Nmax + 31) / 32);
   c->wpart_cap = std::max<size_t>((size_t)(ntile * (ntile + 1) / 2) * 8 * 1024, (size_t)152 * 64 * 64);
   c->wpart = cv.take<double>(c->wpart_cap);
@@ -619,13 +624,26 @@ tdb_status hosvd_spectrum(tdb_ctx* ctx, const Tc* V) {
       CHECK_LAUNCH();
       const int Nn = (int)ctx->N[n];
       tdb_status st;
-      if (Nn <= 48)   // (the single-CTA Jacobi is slower than the subspace iteration above ~48)
-        st = eig_leading_small<float>((const float*)ctx->Cc, ctx->C64, Nn, ctx->kcap[n], (float*)ctx->jA,
-                                      (float*)ctx->jV, ctx->flags, ctx->ev[n], ctx->Qeig[n], ctx->trace + n,
-                                      ctx->eigscratch, s);
-      else
+      // The Gram is accurate to about 1e-9 of its largest entries (float products,
+      // float-float sums), but a float eigensolver resolves eigenvectors only where the
+      // eigenvalue gaps exceed about 1e-6 of the largest eigenvalue; the eigenvectors the
+      // rank rule keeps at gamma_th = 99.999 % sit below that.  So the solve is double: the
+      // single-CTA Jacobi on the double Gram for short modes, and for long ones the float
+      // subspace iteration as a warm start refined by three double iterations with
+      // Rayleigh-Ritz.
+      if (Nn <= 48) {
+        st = eig_leading_small<double>(ctx->C64, ctx->C64, Nn, ctx->kcap[n], (double*)ctx->jA, (double*)ctx->jV,
+                                       ctx->flags, ctx->ev[n], ctx->Qeig[n], ctx->trace + n, ctx->eigscratch, s);
+      } else {
         st = eig_si_float((const float*)ctx->Cc, ctx->C64, Nn, ctx->kcap[n], 24, ctx->eigf, ctx->bar, ctx->flags,
                           ctx->ev[n], ctx->Qeig[n], ctx->trace + n, s);
+        if (st == TDB_OK) {
+          SubspaceWs<double> ws{(double*)ctx->siQ, (double*)ctx->siZ, (double*)ctx->siX, ctx->siG, ctx->siR,
+                                (double*)ctx->siH, (double*)ctx->siJA, (double*)ctx->siJV};
+          st = eig_subspace<double>(ctx->C64, ctx->C64, Nn, ctx->kcap[n], 3, ws, ctx->flags, ctx->ev[n],
+                                    ctx->Qeig[n], ctx->trace + n, ctx->eigscratch, s, ctx->Qeig[n]);
+        }
+      }
       if (st != TDB_OK) { ctx->err = "eigensolver launch failed"; return st; }
       CHECK_LAUNCH();
     }
@@ -913,7 +931,7 @@ tdb_status fused_update(tdb_ctx* ctx, bool reorth, bool skip_finish, bool heun) 
     ntiles += (ctx->N[n] + 31) / 32;
   }
   a.dS = ctx->dS;
-  a.y3 = (ctx->use_tc && tc_defers_ds(p, ctx->N, ctx->r)) ? ctx->Y[2] : nullptr;
+  a.ds_y2 = ctx->use_tc ? ctx->Y[1] : nullptr;       // the projection leaves dS to phase 1
   a.dS_out = ctx->dS;
   a.T = ctx->T;
   a.T2 = ctx->T2;
@@ -950,11 +968,15 @@ template <typename Tc>
 tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths) {
   cudaStream_t s = ctx->stream;
   const int p = ctx->p;
-  // exact error on every step: the G_n refresh runs beside it on the context's second stream
-  const bool split = ctx->cfg.error_mode == TDB_ERRMODE_EXACT && ctx->aux && ctx->ev_fork && ctx->ev_join;
+  // exact error every step, or gated by the estimator: the G_n refresh (G_n, G_n^{-1},
+  // sigma^(n)) runs beside the error on the context's second stream
+  const bool split = (ctx->cfg.error_mode == TDB_ERRMODE_EXACT || ctx->cfg.error_mode == TDB_ERRMODE_MLP) &&
+                     ctx->aux && ctx->ev_fork && ctx->ev_join;
   CK(cudaMemsetAsync(ctx->rb_dev, 0, sizeof(Readback), s));
   CK(cudaMemcpyAsync(&ctx->rb_dev->need, ctx->need_pin, sizeof(int), cudaMemcpyHostToDevice, s));
   CK(cudaMemcpyAsync(ctx->est_dev, ctx->est_pin, sizeof(EstState), cudaMemcpyHostToDevice, s));
+  // the estimator's sigma features are those of the state the step starts from
+  CK(cudaMemcpyAsync(ctx->sig2_lag, ctx->sig2, sizeof(double) * p * kMaxRank, cudaMemcpyDeviceToDevice, s));
   cudaEvent_t* ev = ctx->prof ? ctx->pev : nullptr;
   if (ev) CK(cudaEventRecord(ev[0], s));
   int64_t Rprod = 1;
@@ -990,38 +1012,38 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
   // second stage: the increment at the predicted state, combined with y_k)
   TRY(fused_update<Tc>(ctx, ctx->cfg.reorth != 0, split, heun));
   if (ev) CK(cudaEventRecord(ev[2], s));
+  // the estimator's gate decides the error evaluation only in TDB_ERRMODE_MLP; otherwise
+  // its decision goes to a scratch word and the host's schedule stands
+  const bool mlp = ctx->cfg.error_mode == TDB_ERRMODE_MLP;
+  auto features = [&](cudaStream_t q) {
+    if (ctx->f64) return;
+    int64_t nds = 1;
+    for (int n = 0; n < p; ++n) nds *= ctx->r[n];
+    est_features(ctx->est_dev, (const float*)ctx->dS, (int)nds, &ctx->rb_dev->dv2, ctx->sig2_lag, ctx->r, p,
+                 ctx->mlpP, ctx->mlpNorm, ctx->rb_dev->feat, &ctx->rb_dev->est,
+                 mlp ? &ctx->rb_dev->need : ctx->need_scratch, &ctx->rb_dev->ds2, q);
+  };
+  // a7: error, exact or estimated (the estimator's features and gate first).  Recorded
+  // steps enqueue the error kernels on every step, gated by the device word.
+  const int* gate = nullptr;
+  if (ctx->cfg.error_mode != TDB_ERRMODE_EXACT && (all_paths || ctx->gated_step)) gate = &ctx->rb_dev->need;
+  const bool run_error = all_paths || ctx->need_host;
   if (split) {
-    // exact error every step: G_n, G_n^{-1}, sigma^(n) and the estimator's features on a
-    // second branch while this one evaluates Eq. 2.20 (neither reads what the other writes)
     CK(cudaEventRecord(ctx->ev_fork, s));
     CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
     launch_gram_finish(mode_desc(ctx), ctx->Gpart, gram_split(ctx->r, p, ctx->gsplit), ctx->G, ctx->Ginv, ctx->Ginvf,
                        ctx->sig2, ctx->Vprev, ctx->warm ? 1 : 0, ctx->flags, ctx->aux);
-    if (!ctx->f64) {
-      int64_t nds = 1;
-      for (int n = 0; n < p; ++n) nds *= ctx->r[n];
-      est_features(ctx->est_dev, (const float*)ctx->dS, (int)nds, &ctx->rb_dev->dv2, ctx->sig2, ctx->r, p, ctx->mlpP,
-                   ctx->mlpNorm, ctx->rb_dev->feat, &ctx->rb_dev->est, &ctx->rb_dev->need, &ctx->rb_dev->ds2, ctx->aux);
-    }
+    features(s);
     CHECK_LAUNCH();
-    TRY(exact_error2<Tc>(ctx, Vn, nullptr));
+    if (run_error) TRY(exact_error2<Tc>(ctx, Vn, gate));
     CK(cudaEventRecord(ctx->ev_join, ctx->aux));
     CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
     if (ev) CK(cudaEventRecord(ev[3], s));
     return readback_enqueue(ctx);
   }
-  // a7: error, exact or estimated
-  if (!ctx->f64) {
-    int64_t nds = 1;
-    for (int n = 0; n < p; ++n) nds *= ctx->r[n];
-    est_features(ctx->est_dev, (const float*)ctx->dS, (int)nds, &ctx->rb_dev->dv2, ctx->sig2, ctx->r, p, ctx->mlpP,
-                 ctx->mlpNorm, ctx->rb_dev->feat, &ctx->rb_dev->est, &ctx->rb_dev->need, &ctx->rb_dev->ds2, s);
-    CHECK_LAUNCH();
-  }
-  if (all_paths)
-    TRY(exact_error2<Tc>(ctx, Vn, &ctx->rb_dev->need));
-  else if (ctx->need_host)
-    TRY(exact_error2<Tc>(ctx, Vn, ctx->gated_step ? &ctx->rb_dev->need : nullptr));
+  features(s);
+  CHECK_LAUNCH();
+  if (run_error) TRY(exact_error2<Tc>(ctx, Vn, gate));
   if (ev) CK(cudaEventRecord(ev[3], s));
   return readback_enqueue(ctx);
 }
@@ -1450,6 +1472,9 @@ tdb_status tdb_adapt_rank(tdb_ctx* ctx, const void* V_now, int* ranks_out, doubl
     return act == ACT_CAP ? TDB_WARN_RANK_CAP : TDB_OK;
   };
   tdb_status st = ctx->f64 ? run(double()) : run(float());
+  // the state now stands for V_now (re-initialised from it, or accepted against it):
+  // the next push differences against V_now
+  if (st == TDB_OK || st == TDB_WARN_RANK_CAP) ctx->V_prev = V_now;
   if (ranks_out)
     for (int n = 0; n < ctx->p; ++n) ranks_out[n] = ctx->r[n];
   return st;

@@ -79,6 +79,7 @@ EXPORTS = [
     "tdb_mlp_param_count", "tdb_mlp_forward", "tdb_mlp_loss_grad", "tdb_mlp_adam_step", "tdb_estimator_fit",
     "tdb_estimator_params", "tdb_estimator_trace", "tdb_set_input_slots", "tdb_push_slot",
     "tdb_batch_create", "tdb_batch_push", "tdb_batch_last_error", "tdb_batch_destroy", "tdb_get_graph_counters",
+    "tdb_selftest_recip", "tdb_selftest_timeout",
 ]
 
 
@@ -148,6 +149,10 @@ def load(path: str = LIB_PATH):
     lib.tdb_project_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int), vp, vp,
                                         C.POINTER(vp), C.POINTER(vp), vp, C.POINTER(vp), vp, vp]
     lib.tdb_project_noalloc.restype = st
+    lib.tdb_selftest_recip.argtypes = [vp, vp, vp, C.c_int64, vp]
+    lib.tdb_selftest_recip.restype = st
+    lib.tdb_selftest_timeout.argtypes = [C.c_int, C.c_int64, vp, vp]
+    lib.tdb_selftest_timeout.restype = st
     lib.tdb_mlp_param_count.argtypes = []
     lib.tdb_mlp_param_count.restype = C.c_int
     lib.tdb_mlp_forward.argtypes = [vp, vp, C.c_int, vp, vp]
@@ -484,6 +489,28 @@ def project_noalloc(dims, ranks, V_next: torch.Tensor, V_prev: torch.Tensor, A, 
     return lib.tdb_project_noalloc(p, cdims, cr, C.c_void_p(V_next.data_ptr()), C.c_void_p(V_prev.data_ptr()),
                                    aptr, wptr, C.c_void_p(dS.data_ptr()), yptr, C.c_void_p(dv2.data_ptr()),
                                    C.c_void_p(s.cuda_stream))
+
+
+def selftest_recip(x: torch.Tensor):
+    """tdb_selftest_recip on a float64 device tensor: (1/x, 1/sqrt(x)) from the library's
+    double reciprocal helpers."""
+    lib = load()
+    x = x.contiguous()
+    rcp, rs = torch.empty_like(x), torch.empty_like(x)
+    st = lib.tdb_selftest_recip(C.c_void_p(x.data_ptr()), C.c_void_p(rcp.data_ptr()), C.c_void_p(rs.data_ptr()),
+                                x.numel(), C.c_void_p(torch.cuda.current_stream(x.device).cuda_stream))
+    if st != 0:
+        raise TDBError(st, "tdb_selftest_recip")
+    return rcp, rs
+
+
+def selftest_timeout(which: int, limit_cycles: int, device="cuda") -> int:
+    """tdb_selftest_timeout: run one bounded device wait until it runs out; returns the
+    status (TDB_ERR_TIMEOUT = 7 expected)."""
+    lib = load()
+    scratch = torch.zeros(4, dtype=torch.int32, device=device)
+    return lib.tdb_selftest_timeout(int(which), int(limit_cycles), C.c_void_p(scratch.data_ptr()),
+                                    C.c_void_p(torch.cuda.current_stream(scratch.device).cuda_stream))
 
 
 def mlp_forward(params: torch.Tensor, X: torch.Tensor) -> torch.Tensor:

@@ -54,6 +54,11 @@ def abs_bound(dV, U, w, keep):
     ((192, 129, 12, 3), (30, 30, 8, 3)), # four modes, ragged mode 2, padded rank 32
     ((256, 100), (20, 20)),              # two modes (DBO)
     ((64, 64, 64), (4, 4, 4)),           # one tile per slice
+    # more tile-slices than SMs: the persistent path (several tiles per CTA, the whole
+    # operand images resident, the TMEM double buffer and the stages reused across tiles)
+    ((256, 128, 512), (20, 20, 20)),     # the stochastic shape at rank 20: 1024 tiles, 8 stages
+    ((256, 128, 320), (16, 16, 12)),     # 640 tiles, 16 stages
+    ((192, 129, 192, 3), (30, 30, 30, 3)),  # the channel shape at its rank caps: 2304 tiles
 ])
 def test_bf16_projection_within_rounding_bound(tdbmod, dims, ranks):
     rng = np.random.default_rng(200)
