@@ -1,23 +1,25 @@
 // tc_project.cu - the projection of Eqs. 2.15/2.16 with the snapshot difference
 // fused in, on the 5th-generation tensor cores (sm_103a).
 //
-// The snapshot is viewed as N1 x N2 x S (S = product of the modes after the
-// second).  One persistent CTA loop walks 128 x 128 (i1 x i2) tiles of one slice s:
-//   * TMA (cp.async.bulk.tensor) streams 64 x 16 FP32 boxes of V_{k+1} and V_k
-//     into eight shared-memory stages, one per converter warp;
-//   * eight converter warps form dV = V_{k+1} - V_k in FP32 (before any rounding),
-//     accumulate ||dV||_W^2, round to BF16 and write one 128-byte-swizzled tile;
-//   * one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32 in TMEM) on
-//     that tile twice: as the K-major A operand of Z1 = dV x_1 A_1^T (M = i2,
-//     K = i1) and as the MN-major A operand of Z2 = dV x_2 A_2^T (M = i1, K = i2);
-//     the weighted bases A_n = W_n U_n are resident in shared memory as BF16;
-//   * four epilogue warps drain the TMEM accumulators (tcgen05.ld) into partial
-//     sums over the i1 tiles (Z1) and i2 tiles (Z2).
-// A small reduction and mode products on the rank-sized remainders then give
-// dS and every Y_n (dimension tree: contract mode 1 first for Y_{n>=2} and dS,
-// mode 2 first for Y_1).
-// Every wait is bounded: on timeout the kernel records a flag, stops issuing,
-// drains its own copies and frees TMEM before returning.
+// The snapshot is viewed as N1 x N2 x S (S = product of the modes after the second)
+// and cut into 128 x 128 (i1 x i2) tile positions.  Every CTA of the persistent grid
+// keeps one tile position and walks a strided set of the slices s:
+//   * TMA (cp.async.bulk.tensor) streams each 128 x 16 FP32 strip of V_{k+1} and V_k
+//     (8 KB boxes) into that strip's 16 KB shared-memory stage, eight strips per tile;
+//   * eight converter warps, one per strip and stage, form dV = V_{k+1} - V_k in FP32
+//     (before any rounding), accumulate ||dV||_W^2, round to BF16 and write the tile
+//     128-byte-swizzled;
+//   * one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32 in TMEM) on that tile
+//     twice: as the K-major A operand of Z1 = dV x_1 A_1^T (M = i2, K = i1) and as the
+//     MN-major A operand of Z2 = dV x_2 A_2^T (M = i1, K = i2); the tile position's rows of
+//     the weighted bases A_n = W_n U_n are packed into shared memory as BF16 by the
+//     epilogue warps at the start;
+//   * four epilogue warps drain the TMEM accumulators (tcgen05.ld) into partial sums
+//     over the i1 tiles (Z1) and i2 tiles (Z2).
+// A finishing launch sums the partials and contracts the remaining modes, giving every
+// Y_n (dS = Y_2 x_2 A_2^T follows in the update kernel or in a mode product).
+// Every wait is bounded: on timeout the kernel records a flag, stops issuing, drains
+// its own copies and frees TMEM before returning.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -31,42 +33,48 @@ namespace tdb {
 namespace {
 
 constexpr int TILE = 128;
-constexpr int SUB_I1 = 64, SUB_I2 = 16;
-constexpr int NSUB = 16;                                 // sub-tiles per tile: 2 i1 halves x 8 i2 strips
-constexpr int BOX_BYTES = SUB_I1 * SUB_I2 * 4;           // 4 KB
-constexpr int STAGE_BYTES = 2 * BOX_BYTES;               // V_{k+1} and V_k boxes
+constexpr int SUB_I1 = 128, SUB_I2 = 16;                 // one TMA box: the tile's i1 width x 16 rows of i2
+constexpr int NSTRIP = TILE / SUB_I2;                    // 8 strips per tile
+constexpr int BOX_BYTES = SUB_I1 * SUB_I2 * 4;           // 8 KB
+constexpr int STAGE_BYTES = 2 * BOX_BYTES;               // V_{k+1} and V_k boxes of one strip: 16 KB
+constexpr int NSTAGE = NSTRIP;                           // one stage per strip (and per converter warp)
 constexpr int BF_TILE_BYTES = TILE * TILE * 2;           // 32 KB
 constexpr int HALF_BYTES = BF_TILE_BYTES / 2;            // one 64-wide i1 half: 128 rows x 128 B
 constexpr int NUM_EPI_WARPS = 4;                         // warps 0..3 (TMEM lane quadrants 0..3)
 constexpr int TMA_WARP = 4;
 constexpr int MMA_WARP = 5;
 constexpr int CONV_WARP0 = 6;
-constexpr int NUM_CONV_WARPS = 8;
+constexpr int NUM_CONV_WARPS = NSTRIP;                   // converter warp c owns strip c
 constexpr int NUM_WARPS = CONV_WARP0 + NUM_CONV_WARPS;   // 14
 constexpr int NUM_THREADS = NUM_WARPS * 32;              // 448
-constexpr int MAX_STAGES = 16;                           // one stage per sub-tile when shared memory allows, else 8
-constexpr int MIN_STAGES = 8;                            // (one per converter warp, used twice per tile)
 constexpr uint32_t TMEM_COLS = 128;                      // 2 buffers x (D1 32 cols + D2 32 cols)
 constexpr long long TIMEOUT_CYCLES = 4000000000ll;       // ~2 s at 2 GHz
 constexpr int kSmemLimit = 227 * 1024 - 512;             // dynamic shared memory (static use 256 B)
 
+// Every CTA keeps one tile position (q1, q2) and walks the slices s0, s0 + cstep, ...,
+// so only that position's two K blocks of each operand image are resident.
 struct Params {
   int N1, N2, nslice;
-  int nq1, nq2;
+  int nq1, nq2, nq12;            // tile positions: nq1 x nq2
+  int cstep;                     // CTAs per tile position
   int r1, r2, r1pad, r2pad;
-  int nunits, nstages;
-  int b1_bytes, b2_bytes;        // resident image bytes in shared memory
-  int bsub;                      // 1: one unit per CTA, only its two K blocks of each image resident
+  int b1_bytes, b2_bytes;        // the position's two K blocks of A_1 and A_2 (BF16 images)
   float* Z1p;                    // [nq1][nslice][N2][r1]
   float* Z2p;                    // [nq2][nslice][N1][r2]
-  const uint4* B1img;            // BF16 operand images (global)
-  const uint4* B2img;
+  const float* A1;               // weighted bases A_1 = W_1 U_1 (N1 x r1) and A_2 (N2 x r2), FP32
+  const float* A2;
   const float* w1f;             // float copies of w_1, w_2, zero-padded to whole tiles
   const float* w2f;
   const double* wsl;             // slice weights (product over modes >= 3)
   double* npart;                 // per-CTA ||dV||_W^2
   unsigned* flags;
 };
+
+// Shared memory of the fused kernel: 1 KB alignment slack, two BF16 tiles, the two image
+// blocks, the epilogue staging, the stages, the barriers.
+__host__ __device__ constexpr int smem_fixed_bytes(int b1, int b2) {
+  return 1024 + 2 * BF_TILE_BYTES + ((b1 + 1023) & ~1023) + ((b2 + 1023) & ~1023) + NUM_EPI_WARPS * 32 * 33 * 4 + 512;
+}
 
 // ---------------------------------------------------------------------------
 // PTX wrappers
@@ -184,31 +192,34 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
 // ---------------------------------------------------------------------------
 // The fused kernel
 // ---------------------------------------------------------------------------
-template <int NS>   // pipeline stages: 16 (one per sub-tile) or 8 (one per converter warp)
 __global__ void __launch_bounds__(NUM_THREADS, 1)
     k_tc_project(const __grid_constant__ CUtensorMap tmVn, const __grid_constant__ CUtensorMap tmVp, Params P) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* bf_tiles = smem;                                          // 2 x 32 KB
-  unsigned char* b1_smem = bf_tiles + 2 * BF_TILE_BYTES;                   // resident A_1 image
-  unsigned char* b2_smem = b1_smem + ((P.b1_bytes + 1023) & ~1023);        // resident A_2 image
+  unsigned char* b1_smem = bf_tiles + 2 * BF_TILE_BYTES;                   // A_1 blocks of this position
+  unsigned char* b2_smem = b1_smem + ((P.b1_bytes + 1023) & ~1023);        // A_2 blocks
   float* epi_stage = (float*)(b2_smem + ((P.b2_bytes + 1023) & ~1023));   // 4 warps x 32 x 33 floats
-  unsigned char* stages = (unsigned char*)(epi_stage + NUM_EPI_WARPS * 32 * 33);   // nstages x 8 KB
-  uint64_t* bars = (uint64_t*)(stages + NS * STAGE_BYTES);
-  uint64_t* full = bars;                    // [MAX_STAGES]
-  uint64_t* empty = bars + MAX_STAGES;      // [MAX_STAGES]
-  uint64_t* bf_full = bars + 2 * MAX_STAGES;
+  unsigned char* stages = (unsigned char*)(epi_stage + NUM_EPI_WARPS * 32 * 33);   // 8 x 16 KB
+  uint64_t* bars = (uint64_t*)(stages + NSTAGE * STAGE_BYTES);
+  uint64_t* full = bars;                    // [NSTAGE]
+  uint64_t* empty = bars + NSTAGE;          // [NSTAGE]
+  uint64_t* bf_full = bars + 2 * NSTAGE;
   uint64_t* mma_done = bf_full + 2;
   uint64_t* epi_done = mma_done + 2;
-  uint64_t* bimg_full = epi_done + 2;       // the operand images have landed
+  uint64_t* bimg_full = epi_done + 2;       // the operand images are in place
   uint32_t* tmem_slot = (uint32_t*)(bimg_full + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
   __shared__ double red[32];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // this CTA's tile position and its first slice
+  const int pos = blockIdx.x % P.nq12;
+  const int q1 = pos % P.nq1, q2 = pos / P.nq1;
+  const int s_first = blockIdx.x / P.nq12;
 
   if (tid == 0) {
-    for (int s = 0; s < MAX_STAGES; ++s) {
+    for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
     }
@@ -217,7 +228,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       mbar_init(smem_u32(&mma_done[b]), 1);
       mbar_init(smem_u32(&epi_done[b]), NUM_EPI_WARPS);
     }
-    mbar_init(smem_u32(bimg_full), 1);
+    mbar_init(smem_u32(bimg_full), NUM_EPI_WARPS);
     *abort_flag = 0;
     fence_mbar_init();
   }
@@ -236,60 +247,32 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
   if (warp == TMA_WARP) {
     if (lane == 0) {
-      // sub-tile j = h*8 + q (i1 half h, i2 strip q) goes to stage j % nstages and is
-      // converted by warp q: with 16 stages every sub-tile of a tile is in flight at
-      // once, with 8 each stage is used twice per tile (h = 0 then h = 1)
-      // sub-tiles wholly outside the tensor (ragged last tiles) are neither loaded nor
-      // waited for; both sides skip the same ones and count the uses of each stage
-      int ucount[NS];
-#pragma unroll
-      for (int j = 0; j < NS; ++j) ucount[j] = 0;
-      // the BF16 images of the weighted bases (A_1, A_2), resident for the CTA's units
-      // (only the unit's two K blocks of each when it has one unit) by one bulk copy
-      // each; with 16 stages they follow the first tile's copies, with 8 they lead
-      bool b_issued = false;
-      auto issue_b = [&]() {
-        const uint32_t bb = smem_u32(bimg_full);
-        mbar_arrive_expect_tx(bb, (uint32_t)(P.b1_bytes + P.b2_bytes));
-        const int u0 = blockIdx.x;
-        const char* s1 = (const char*)P.B1img + (P.bsub ? (size_t)(u0 % P.nq1) * P.b1_bytes : 0);
-        const char* s2 = (const char*)P.B2img + (P.bsub ? (size_t)((u0 / P.nq1) % P.nq2) * P.b2_bytes : 0);
-        bulk_load(smem_u32(b1_smem), s1, (uint32_t)P.b1_bytes, bb);
-        bulk_load(smem_u32(b2_smem), s2, (uint32_t)P.b2_bytes, bb);
-        b_issued = true;
-      };
-      if (NS < NSUB && blockIdx.x < P.nunits) issue_b();
+      // the strips of every slice: strip j goes to stage j (its converter's), once per
+      // slice; strips wholly past N2 are neither loaded nor waited for, on both sides
       bool ok = true;
       int t = 0;
-      for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x, ++t) {
-        const int q1 = u % P.nq1, q2 = (u / P.nq1) % P.nq2, sl = u / (P.nq1 * P.nq2);
+      const int x = q1 * TILE;
+      for (int sl = s_first; sl < P.nslice && ok; sl += P.cstep, ++t) {
 #pragma unroll
-        for (int j = 0; j < NSUB; ++j) {
-          const int x = q1 * TILE + (j >> 3) * SUB_I1;
-          const int y = q2 * TILE + (j & 7) * SUB_I2;
-          if (!ok || x >= P.N1 || y >= P.N2) continue;
-          const int st = j % NS, use = ucount[st];
-          if (!mbar_wait(smem_u32(&empty[st]), (use & 1) ^ 1, abort_flag, P.flags)) { ok = false; continue; }
-          ucount[st] = use + 1;
-          const uint32_t fb = smem_u32(&full[st]);
+        for (int j = 0; j < NSTRIP; ++j) {
+          const int y = q2 * TILE + j * SUB_I2;
+          if (!ok || y >= P.N2) continue;
+          if (!mbar_wait(smem_u32(&empty[j]), (t & 1) ^ 1, abort_flag, P.flags)) { ok = false; continue; }
+          const uint32_t fb = smem_u32(&full[j]);
           mbar_arrive_expect_tx(fb, STAGE_BYTES);
-          const uint32_t dst = smem_u32(stages + st * STAGE_BYTES);
+          const uint32_t dst = smem_u32(stages + j * STAGE_BYTES);
           tma_load_3d(dst, &tmVn, x, y, sl, fb);
           tma_load_3d(dst + BOX_BYTES, &tmVp, x, y, sl, fb);
         }
-        if (!b_issued && ok) issue_b();
       }
       // drain: every armed copy has landed before the CTA may leave
-      if (b_issued) {
-        long long t0 = clock64();
-        while (!mbar_try_wait(smem_u32(bimg_full), 0) && clock64() - t0 < TIMEOUT_CYCLES) {
-        }
-      }
+      if (t > 0) {
 #pragma unroll
-      for (int j = 0; j < NS; ++j) {
-        if (ucount[j] == 0) continue;
-        long long t0 = clock64();
-        while (!mbar_try_wait(smem_u32(&full[j]), (ucount[j] - 1) & 1) && clock64() - t0 < TIMEOUT_CYCLES) {
+        for (int j = 0; j < NSTRIP; ++j) {
+          if (q2 * TILE + j * SUB_I2 >= P.N2) continue;
+          long long t0 = clock64();
+          while (!mbar_try_wait(smem_u32(&full[j]), (t - 1) & 1) && clock64() - t0 < TIMEOUT_CYCLES) {
+          }
         }
       }
     }
@@ -300,17 +283,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       const uint32_t b1 = smem_u32(b1_smem), b2 = smem_u32(b2_smem);
       const uint32_t blk1 = (uint32_t)P.r1pad * 128u, blk2 = (uint32_t)P.r2pad * 128u;
       int t = 0;
-      bool ok = true;
-      for (int u = blockIdx.x; u < P.nunits; u += gridDim.x, ++t) {
-        const int q1 = u % P.nq1, q2 = (u / P.nq1) % P.nq2;
-        const int kb1 = P.bsub ? 0 : q1 * 2, kb2 = P.bsub ? 0 : q2 * 2;   // first K block of the unit
+      for (int sl = s_first; sl < P.nslice; sl += P.cstep, ++t) {
         const int buf = t & 1;
-        if (t == 0 && !mbar_wait(smem_u32(bimg_full), 0, abort_flag, P.flags)) { ok = false; break; }
-        if (!mbar_wait(smem_u32(&bf_full[buf]), (t >> 1) & 1, abort_flag, P.flags)) { ok = false; break; }
-        if (t >= 2 && !mbar_wait(smem_u32(&epi_done[buf]), ((t >> 1) - 1) & 1, abort_flag, P.flags)) {
-          ok = false;
-          break;
-        }
+        if (t == 0 && !mbar_wait(smem_u32(bimg_full), 0, abort_flag, P.flags)) break;
+        if (!mbar_wait(smem_u32(&bf_full[buf]), (t >> 1) & 1, abort_flag, P.flags)) break;
+        if (t >= 2 && !mbar_wait(smem_u32(&epi_done[buf]), ((t >> 1) - 1) & 1, abort_flag, P.flags)) break;
         tc_fence_after();
         const uint32_t tile = bf_base + buf * BF_TILE_BYTES;
         const uint32_t d1 = tmem_base + buf * 64;
@@ -319,14 +296,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
           uint64_t ad = smem_desc(tile + (kk >> 2) * HALF_BYTES + (kk & 3) * 32, 16, 1024);
-          uint64_t bd = smem_desc(b1 + (kb1 + (kk >> 2)) * blk1 + (kk & 3) * 32, 16, 1024);
+          uint64_t bd = smem_desc(b1 + (kk >> 2) * blk1 + (kk & 3) * 32, 16, 1024);
           mma_bf16(d1, ad, bd, idesc1, kk > 0 ? 1u : 0u);
         }
         // Z2 tile: D2[i1, b] = sum_{i2} dV[i1, i2] A2[i2, b]  (A: MN-major view, M = i1, K = i2)
 #pragma unroll
         for (int kk = 0; kk < 8; ++kk) {
           uint64_t ad = smem_desc(tile + kk * 2048, HALF_BYTES, 1024);
-          uint64_t bd = smem_desc(b2 + (kb2 + (kk >> 2)) * blk2 + (kk & 3) * 32, 16, 1024);
+          uint64_t bd = smem_desc(b2 + (kk >> 2) * blk2 + (kk & 3) * 32, 16, 1024);
           mma_bf16(d2, ad, bd, idesc2, kk > 0 ? 1u : 0u);
         }
         mma_commit(smem_u32(&mma_done[buf]));
@@ -338,13 +315,54 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         while (!mbar_try_wait(smem_u32(&mma_done[tl & 1]), (tl >> 1) & 1) && clock64() - t0 < TIMEOUT_CYCLES) {
         }
       }
-      (void)ok;
     }
   } else if (warp < NUM_EPI_WARPS) {
+    // First the BF16 operand images of this tile position: rows q1*128 .. q1*128+127 of
+    // A_1 and q2*128 .. of A_2 as two 64-row K blocks each, in the 128-byte-swizzled
+    // K-major layout the MMA reads (element (k, a) of block g at g rpad 128 + a 128 +
+    // ((k / 8) ^ (a % 8)) 16 + (k % 8) 2 bytes; zero past N_n and r_n).  A thread packs
+    // eight consecutive k of one column a per item: one 16-byte shared store.
+    {
+      const int et = tid;                              // 0 .. 127
+      for (int img = 0; img < 2; ++img) {
+        const float* A = img == 0 ? P.A1 : P.A2;
+        const int N = img == 0 ? P.N1 : P.N2, r = img == 0 ? P.r1 : P.r2, rpad = img == 0 ? P.r1pad : P.r2pad;
+        const int i0 = (img == 0 ? q1 : q2) * TILE;
+        unsigned char* dst = img == 0 ? b1_smem : b2_smem;
+        const bool vec = img == 0;                     // N_1 is a multiple of 4: whole float4 in or out
+        for (int item = et; item < 2 * rpad * 8; item += NUM_EPI_WARPS * 32) {
+          const int kc = item & 7, a = (item >> 3) % rpad, g = (item >> 3) / rpad;
+          const int i = i0 + g * 64 + kc * 8;
+          float v[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) v[u] = 0.f;
+          if (a < r) {
+            const float* col = A + (int64_t)N * a;
+            if (vec) {
+#pragma unroll
+              for (int h = 0; h < 2; ++h)
+                if (i + 4 * h < N) {
+                  const float4 x = __ldg((const float4*)(col + i + 4 * h));
+                  v[4 * h] = x.x; v[4 * h + 1] = x.y; v[4 * h + 2] = x.z; v[4 * h + 3] = x.w;
+                }
+            } else {
+#pragma unroll
+              for (int u = 0; u < 8; ++u)
+                if (i + u < N) v[u] = __ldg(col + i + u);
+            }
+          }
+          const uint4 pk = make_uint4(pack_bf16x2(v[0], v[1]), pack_bf16x2(v[2], v[3]), pack_bf16x2(v[4], v[5]),
+                                      pack_bf16x2(v[6], v[7]));
+          *(uint4*)(dst + g * rpad * 128 + a * 128 + ((kc ^ (a & 7)) << 4)) = pk;
+        }
+      }
+      fence_proxy_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(bimg_full));
+    }
     // epilogue: TMEM lanes 32*warp .. 32*warp+31
     int t = 0;
-    for (int u = blockIdx.x; u < P.nunits; u += gridDim.x, ++t) {
-      const int q1 = u % P.nq1, q2 = (u / P.nq1) % P.nq2, sl = u / (P.nq1 * P.nq2);
+    for (int sl = s_first; sl < P.nslice; sl += P.cstep, ++t) {
       const int buf = t & 1;
       if (!mbar_wait(smem_u32(&mma_done[buf]), (t >> 1) & 1, abort_flag, P.flags)) break;
       tc_fence_after();
@@ -393,29 +411,40 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       if (lane == 0) mbar_arrive(smem_u32(&epi_done[buf]));
     }
   } else if (warp >= CONV_WARP0) {
-    // converter warp c takes sub-tiles (h = 0, strip c) and (h = 1, strip c) of every tile
+    // converter warp c owns strip c (rows c*16 .. c*16+15 of the tile's i2) and stage c:
+    // it forms dV in FP32, adds its weighted square to ||dV||_W^2, rounds to BF16 and
+    // writes both 64-wide i1 halves of the strip into the 128-byte-swizzled tile
     const int c = warp - CONV_WARP0;
     const int cx = lane & 15, ry = lane >> 4;
     const int chunk = cx >> 1, hoff = (cx & 1) * 8;
-    int ucnt0 = 0, ucnt1 = 0;                        // uses of this warp's stage(s)
+    const bool strip_in = q2 * TILE + c * SUB_I2 < P.N2;
+    bool half_in[2];
+    float w1v[2][4], w2v[8];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      half_in[h] = q1 * TILE + h * 64 < P.N1;
+      const float4 w = __ldg((const float4*)(P.w1f + q1 * TILE + h * 64 + 4 * cx));
+      w1v[h][0] = w.x; w1v[h][1] = w.y; w1v[h][2] = w.z; w1v[h][3] = w.w;
+    }
+    // weights of the rows this lane converts (zero past N_2)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) w2v[k] = __ldg(&P.w2f[q2 * TILE + c * SUB_I2 + ry + 2 * k]);
     int t = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < P.nunits && ok; u += gridDim.x, ++t) {
-      const int q1 = u % P.nq1, q2 = (u / P.nq1) % P.nq2, sl = u / (P.nq1 * P.nq2);
+    for (int sl = s_first; sl < P.nslice && ok; sl += P.cstep, ++t) {
       const int buf = t & 1;
       if (t >= 2 && !mbar_wait(smem_u32(&mma_done[buf]), ((t >> 1) - 1) & 1, abort_flag, P.flags)) break;
+      const double wsl = __ldg(&P.wsl[sl]);
       float acc = 0.f;
-      // weights of the rows this lane converts (zero past N_2): fetched once per tile
-      float w2v[8];
-#pragma unroll
-      for (int k = 0; k < 8; ++k) w2v[k] = __ldg(&P.w2f[q2 * TILE + c * SUB_I2 + ry + 2 * k]);
+      const bool have = strip_in && mbar_wait(smem_u32(&full[c]), t & 1, abort_flag, P.flags);
+      if (strip_in && !have) { ok = false; break; }
+      const float4* vn = (const float4*)(stages + c * STAGE_BYTES);
+      const float4* vp = (const float4*)(stages + c * STAGE_BYTES + BOX_BYTES);
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
-        if (!ok) continue;
-        const int j = h * 8 + c, st = j % NS;
         unsigned char* half = bf_tiles + buf * BF_TILE_BYTES + h * HALF_BYTES;
-        if (q1 * TILE + h * SUB_I1 >= P.N1 || q2 * TILE + c * SUB_I2 >= P.N2) {
-          // wholly outside the tensor: zeros in the BF16 tile, no copy to wait for
+        if (!have || !half_in[h]) {
+          // outside the tensor: zeros in the BF16 tile
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
             const int r = c * SUB_I2 + ry + 2 * k;
@@ -423,29 +452,23 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           }
           continue;
         }
-        const int use = (NS == MAX_STAGES && h == 1) ? ucnt1++ : ucnt0++;
-        if (!mbar_wait(smem_u32(&full[st]), use & 1, abort_flag, P.flags)) { ok = false; continue; }
-        const float4* vn = (const float4*)(stages + st * STAGE_BYTES);
-        const float4* vp = (const float4*)(stages + st * STAGE_BYTES + BOX_BYTES);
-        const int i1b = q1 * TILE + h * SUB_I1 + 4 * cx;
-        const float4 w1q = __ldg((const float4*)(P.w1f + i1b));
-        const float w1v[4] = {w1q.x, w1q.y, w1q.z, w1q.w};
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
-          const int row = ry + 2 * k;                 // 0..15 within the box
-          const float4 a = vn[row * 16 + cx];
-          const float4 b = vp[row * 16 + cx];
+          const int row = ry + 2 * k;                 // 0..15 within the strip
+          const float4 a = vn[row * 32 + h * 16 + cx];
+          const float4 b = vp[row * 32 + h * 16 + cx];
           const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
           const int r = c * SUB_I2 + row;             // tile row (i2 within the tile)
-          acc += w2v[k] * (w1v[0] * d0 * d0 + w1v[1] * d1 * d1 + w1v[2] * d2 * d2 + w1v[3] * d3 * d3);
+          acc += w2v[k] * (w1v[h][0] * d0 * d0 + w1v[h][1] * d1 * d1 + w1v[h][2] * d2 * d2 + w1v[h][3] * d3 * d3);
           uint2 pk = make_uint2(pack_bf16x2(d0, d1), pack_bf16x2(d2, d3));
           *(uint2*)(half + r * 128 + ((chunk ^ (r & 7)) << 4) + hoff) = pk;
         }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&empty[st]));
       }
-      if (!ok) break;
-      acc_norm += (double)acc * P.wsl[sl];
+      if (have) {
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&empty[c]));
+      }
+      acc_norm += (double)acc * wsl;
       fence_proxy_async();
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bf_full[buf]));
@@ -487,31 +510,6 @@ __global__ void k_selftest_mbar(unsigned* flags, long long limit) {
   __syncthreads();
 }
 
-// ---------------------------------------------------------------------------
-// BF16 operand images of the weighted bases (K-major, 128-byte swizzle):
-// 64-row K blocks of rpad rows x 128 B; element (k, a) of block g at
-//   g*rpad*128 + a*128 + (((k/8) ^ (a%8)) * 16) + (k%8)*2.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void pack_bimg_elem(const float* __restrict__ A, int N, int r, int rpad, int e,
-                                               __nv_bfloat16* __restrict__ img) {
-  const int k = e % 64, a = (e / 64) % rpad, g = e / (64 * rpad);
-  const int i = g * 64 + k;
-  float v = (a < r && i < N) ? A[i + (int64_t)N * a] : 0.f;
-  const int off = g * rpad * 64 + a * 64 + (((k >> 3) ^ (a & 7)) << 3) + (k & 7);
-  img[off] = __float2bfloat16_rn(v);
-}
-
-// Both images in one launch: elements [0, nblk1 rpad1 64) of A_1, then those of A_2.
-__global__ void k_pack_bimg(const float* __restrict__ A1, int N1, int r1, int rpad1, int nblk1,
-                            __nv_bfloat16* __restrict__ img1, const float* __restrict__ A2, int N2, int r2, int rpad2,
-                            int nblk2, __nv_bfloat16* __restrict__ img2) {
-  const int tot1 = nblk1 * rpad1 * 64, total = tot1 + nblk2 * rpad2 * 64;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < total; e += gridDim.x * blockDim.x) {
-    if (e < tot1) pack_bimg_elem(A1, N1, r1, rpad1, e, img1);
-    else pack_bimg_elem(A2, N2, r2, rpad2, e - tot1, img2);
-  }
-}
-
 // Finish, first launch.  The fused kernel leaves partial first contractions over the
 // tiles q of the contracted mode: Z1p at e + n1 (s + S q), e = a + r1 i2, n1 = r1 N2
 // (mode 1 contracted), and Z2p at f + n2 (s + S q), f = b + r2 i1, n2 = N1 r2 (mode 2
@@ -522,11 +520,13 @@ __global__ void k_pack_bimg(const float* __restrict__ A1, int N1, int r1, int rp
 // the Kronecker product that contracts modes 3 and 4 at once) or the 1 x 1 identity (two
 // modes).  It also writes Z1 = sum_q Z1p when there is more than one tile along mode 1
 // (the next launch forms Y_3 from it) and, in its first CTA, ||dV||_W^2 from the fused
-// kernel's per-CTA partials.  A CTA owns 64 elements of one side and one of `nsplit`
-// slice ranges; with nsplit > 1 each CTA writes its partial and the last CTA of the
-// tile to arrive sums the partials in split order (the same order whichever CTA is
-// last, so results do not vary from run to run) and resets the tile's counter.
-constexpr int FS_TE = 64, FS_SC = 64, FS_JMAX = 128, FS_SPLIT_MAX = 32;
+// kernel's per-CTA partials.  A CTA owns 256 elements of one side (a thread per element,
+// its slice values in registers) and one of `nsplit` slice ranges; the slices' rows of B
+// are staged in shared memory and read as float4 broadcasts, 32 outputs j at a time.
+// With nsplit > 1 each CTA writes its partial and k_tc_finish_red adds the partials of
+// every output in split order (so results do not vary from run to run).
+constexpr int FS_TE = 256, FS_SC = 16, FS_JB = 32, FS_JMAX = 128, FS_SPLIT_MAX = 32;
+constexpr int FS_CTAS = 2 * 152;   // split target: about two CTAs per SM
 struct FinArgs {
   const float* Z1p;
   const float* Z2p;
@@ -537,20 +537,15 @@ struct FinArgs {
   float* Z1;             // r1 x N2 x S (written when nq1 > 1)
   float* Y2;
   float* Y1;
-  float* part;           // [tile][split][J][64]
-  unsigned* cnt;         // per tile, zero between launches
+  float* part;           // [tile][split][J][256]
   int nsplit, nt1, nt2;
   const double* npart;
   int nnp;
   double* dv2;
 };
 
-template <int JT>   // accumulators per thread: outputs j = jg + 4 t, t < JT (J <= 4 JT)
-__global__ void __launch_bounds__(256) k_tc_finish_sk(FinArgs f) {
-  extern __shared__ float fs_sm[];
-  float (*zs)[FS_TE + 1] = (float(*)[FS_TE + 1])fs_sm;       // [FS_SC][65]
-  float* bs = fs_sm + FS_SC * (FS_TE + 1);                    // [FS_SC][J]
-  __shared__ int last_sh;
+__global__ void __launch_bounds__(FS_TE) k_tc_finish_sk(FinArgs f) {
+  extern __shared__ __align__(16) float fs_sm[];    // B rows of a slice chunk: [FS_SC][Jp]
   __shared__ double dsh[32];
   const int tid = threadIdx.x;
   const int tile = blockIdx.x / f.nsplit, sp = blockIdx.x % f.nsplit;
@@ -562,111 +557,124 @@ __global__ void __launch_bounds__(256) k_tc_finish_sk(FinArgs f) {
   }
   const bool first = tile < f.nt1;
   const int64_t ne = first ? (int64_t)f.r1 * f.N2 : (int64_t)f.N1 * f.r2;
-  const int64_t e0 = (int64_t)(first ? tile : tile - f.nt1) * FS_TE;
+  const int64_t e = (int64_t)(first ? tile : tile - f.nt1) * FS_TE + tid;
+  const bool in = e < ne;
   const int nq = first ? f.nq1 : f.nq2;
-  const float* Pp = first ? f.Z1p : f.Z2p;
+  const float* Pp = (first ? f.Z1p : f.Z2p) + (in ? e : 0);
   const bool write_z = first && f.nq1 > 1;
-  const int J = f.J;
+  const int J = f.J, Jp = (J + 3) & ~3;
   const int s_lo = (int)((int64_t)f.S * sp / f.nsplit), s_hi = (int)((int64_t)f.S * (sp + 1) / f.nsplit);
-  const int el = tid % FS_TE, jg = tid / FS_TE;           // outputs (el, j = jg + 4 t)
-  float acc[JT];
-#pragma unroll
-  for (int t = 0; t < JT; ++t) acc[t] = 0.f;
-  for (int s0 = s_lo; s0 < s_hi; s0 += FS_SC) {
-    const int sc = min(FS_SC, s_hi - s0);
-    // partial sums over q: all loads of the chunk in flight together
-#pragma unroll
-    for (int u = 0; u < FS_SC * FS_TE / 256; ++u) {
-      const int idx = tid + 256 * u;
-      const int xl = idx % FS_TE, sl = idx / FS_TE;
-      const int64_t e = e0 + xl;
-      const bool in = sl < sc && e < ne;
-      const float* pe = Pp + e + ne * (int64_t)(s0 + sl);
-      float v[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) v[q] = (in && q < nq) ? __ldcg(&pe[ne * (int64_t)q * f.S]) : 0.f;
-      float z = ((v[0] + v[1]) + v[2]) + v[3];
-      if (in) {
-        for (int q = 4; q < nq; ++q) z += __ldcg(&pe[ne * (int64_t)q * f.S]);
-        if (write_z) f.Z1[e + ne * (int64_t)(s0 + sl)] = z;
-      }
-      zs[sl][xl] = z;
+  const int64_t qstride = ne * (int64_t)f.S;
+  float* mine = f.part + ((int64_t)tile * f.nsplit + sp) * (int64_t)J * FS_TE;
+  auto store = [&](int64_t ee, int j, float v) {
+    if (first) {
+      f.Y2[ee + ne * (int64_t)j] = v;
+    } else {
+      const int64_t b = ee % f.r2, i1 = ee / f.r2;
+      f.Y1[i1 + (int64_t)f.N1 * (b + (int64_t)f.r2 * j)] = v;
     }
-    for (int idx = tid; idx < FS_SC * J; idx += 256) {
-      const int sl = idx / J, j = idx % J;
-      float bv = 0.f;
-      if (sl < sc) {
-        const int s = s0 + sl;
-        if (!f.A3) {
-          bv = 1.f;
-        } else if (!f.A4) {
-          bv = __ldg(&f.A3[s + (int64_t)f.N3 * j]);
-        } else {
-          const int i3 = s % f.N3, i4 = s / f.N3, c = j % f.r3, dd = j / f.r3;
-          bv = __ldg(&f.A3[i3 + (int64_t)f.N3 * c]) * __ldg(&f.A4[i4 + (int64_t)f.N4 * dd]);
+  };
+  for (int j0 = 0; j0 < J; j0 += FS_JB) {
+    const int jn = min(FS_JB, J - j0);
+    float acc[FS_JB];
+#pragma unroll
+    for (int t = 0; t < FS_JB; ++t) acc[t] = 0.f;
+    for (int s0 = s_lo; s0 < s_hi; s0 += FS_SC) {
+      const int sc = min(FS_SC, s_hi - s0);
+      // this element's slice values summed over q: every load of the chunk issued first
+      float z[FS_SC];
+#pragma unroll
+      for (int u = 0; u < FS_SC; ++u) {
+        float v = 0.f;
+        if (in && u < sc) {
+          const float* pe = Pp + ne * (int64_t)(s0 + u);
+          v = __ldcg(pe);
+          for (int q = 1; q < nq; ++q) v += __ldcg(pe + qstride * q);
+        }
+        z[u] = v;
+      }
+      if (write_z && j0 == 0 && in) {
+#pragma unroll
+        for (int u = 0; u < FS_SC; ++u)
+          if (u < sc) f.Z1[e + ne * (int64_t)(s0 + u)] = z[u];
+      }
+      __syncthreads();
+      for (int idx = tid; idx < FS_SC * Jp; idx += blockDim.x) {
+        const int sl = idx / Jp, j = idx % Jp;
+        float bv = 0.f;
+        if (sl < sc && j < J) {
+          const int s = s0 + sl;
+          if (!f.A3) {
+            bv = 1.f;
+          } else if (!f.A4) {
+            bv = __ldg(&f.A3[s + (int64_t)f.N3 * j]);
+          } else {
+            const int i3 = s % f.N3, i4 = s / f.N3, c = j % f.r3, dd = j / f.r3;
+            bv = __ldg(&f.A3[i3 + (int64_t)f.N3 * c]) * __ldg(&f.A4[i4 + (int64_t)f.N4 * dd]);
+          }
+        }
+        fs_sm[sl * Jp + j] = bv;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int u = 0; u < FS_SC; ++u) {
+        const float* brow = fs_sm + u * Jp + j0;
+#pragma unroll
+        for (int t4 = 0; t4 < FS_JB / 4; ++t4) {
+          if (4 * t4 < jn) {
+            const float4 bb = *reinterpret_cast<const float4*>(brow + 4 * t4);
+            acc[4 * t4] = fmaf(bb.x, z[u], acc[4 * t4]);
+            acc[4 * t4 + 1] = fmaf(bb.y, z[u], acc[4 * t4 + 1]);
+            acc[4 * t4 + 2] = fmaf(bb.z, z[u], acc[4 * t4 + 2]);
+            acc[4 * t4 + 3] = fmaf(bb.w, z[u], acc[4 * t4 + 3]);
+          }
         }
       }
-      bs[sl * J + j] = bv;
     }
-    __syncthreads();
-    for (int sl = 0; sl < sc; ++sl) {
-      const float z = zs[sl][el];
+    if (f.nsplit == 1) {
+      if (in) {
 #pragma unroll
-      for (int t = 0; t < JT; ++t) {
-        const int j = jg + 4 * t;
-        if (j < J) acc[t] = fmaf(bs[sl * J + j], z, acc[t]);
+        for (int t = 0; t < FS_JB; ++t)
+          if (t < jn) store(e, j0 + t, acc[t]);
       }
+    } else {
+#pragma unroll
+      for (int t = 0; t < FS_JB; ++t)
+        if (t < jn) mine[(int64_t)(j0 + t) * FS_TE + tid] = acc[t];
     }
-    __syncthreads();
   }
-  auto store = [&](int64_t e, int j, float v) {
-    if (e >= ne) return;
+}
+
+// Finish, split partials: output (e, j) of a tile is the sum of its nsplit partials in
+// split order (one thread per output, every load issued before the additions).
+__global__ void __launch_bounds__(256) k_tc_finish_red(FinArgs f) {
+  const int J = f.J;
+  const int64_t per_tile = (int64_t)J * FS_TE;
+  const int64_t total = (int64_t)(f.nt1 + f.nt2) * per_tile;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < total; o += (int64_t)gridDim.x * blockDim.x) {
+    const int tile = (int)(o / per_tile);
+    const int rem = (int)(o % per_tile);
+    const int j = rem / FS_TE, x = rem % FS_TE;
+    const bool first = tile < f.nt1;
+    const int64_t ne = first ? (int64_t)f.r1 * f.N2 : (int64_t)f.N1 * f.r2;
+    const int64_t e = (int64_t)(first ? tile : tile - f.nt1) * FS_TE + x;
+    if (e >= ne) continue;
+    const float* base = f.part + (int64_t)tile * f.nsplit * per_tile + (int64_t)j * FS_TE + x;
+    float vals[FS_SPLIT_MAX];
+#pragma unroll
+    for (int q = 0; q < FS_SPLIT_MAX; ++q) vals[q] = q < f.nsplit ? __ldcg(&base[(int64_t)q * per_tile]) : 0.f;
+    float v = 0.f;
+#pragma unroll
+    for (int q = 0; q < FS_SPLIT_MAX; ++q) v += vals[q];
     if (first) {
       f.Y2[e + ne * (int64_t)j] = v;
     } else {
       const int64_t b = e % f.r2, i1 = e / f.r2;
       f.Y1[i1 + (int64_t)f.N1 * (b + (int64_t)f.r2 * j)] = v;
     }
-  };
-  if (f.nsplit == 1) {
-#pragma unroll
-    for (int t = 0; t < JT; ++t) {
-      const int j = jg + 4 * t;
-      if (j < J) store(e0 + el, j, acc[t]);
-    }
-    return;
   }
-  float* mine = f.part + ((int64_t)tile * f.nsplit + sp) * (int64_t)J * FS_TE;
-#pragma unroll
-  for (int t = 0; t < JT; ++t) {
-    const int j = jg + 4 * t;
-    if (j < J) mine[j * FS_TE + el] = acc[t];
-  }
-  __threadfence();
-  __syncthreads();
-  if (tid == 0) {
-    const unsigned prev = atomicAdd(&f.cnt[tile], 1u);
-    last_sh = (prev == (unsigned)f.nsplit - 1u);
-  }
-  __syncthreads();
-  if (!last_sh) return;
-  __threadfence();
-  // the tile's J x 64 outputs, each the sum of nsplit partials in split order; every
-  // load of an output is issued before the additions
-  const float* base = f.part + (int64_t)tile * f.nsplit * J * FS_TE;
-  for (int o = tid; o < J * FS_TE; o += blockDim.x) {
-    const int j = o / FS_TE, x = o % FS_TE;
-    float vals[FS_SPLIT_MAX];
-#pragma unroll
-    for (int q = 0; q < FS_SPLIT_MAX; ++q)
-      vals[q] = q < f.nsplit ? __ldcg(&base[((int64_t)q * J + j) * FS_TE + x]) : 0.f;
-    float v = 0.f;
-#pragma unroll
-    for (int q = 0; q < FS_SPLIT_MAX; ++q) v += vals[q];
-    store(e0 + x, j, v);
-  }
-  if (tid == 0) f.cnt[tile] = 0u;
 }
+
 
 // Three-mode finish, second launch: Y_3 = Z1 x_2 A_2^T (r1 x r2 x S), a CTA per
 // slice, i2 in chunks of FB_CH staged in shared memory (thread per output (a1, a2)).
@@ -779,11 +787,12 @@ bool tc_supported(int p, const int64_t* N, const int* cap, std::string& err) {
   cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
   cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
   if (major != 10) { err = "needs a compute capability 10.x GPU (tcgen05)"; return false; }
-  int nq1 = (int)((N[0] + TILE - 1) / TILE), nq2 = (int)((N[1] + TILE - 1) / TILE);
-  int b1 = nq1 * 2 * rpad_of(cap[0]) * 128, b2 = nq2 * 2 * rpad_of(cap[1]) * 128;
-  int fixed = 1024 + 2 * BF_TILE_BYTES + ((b1 + 1023) & ~1023) + ((b2 + 1023) & ~1023) + NUM_EPI_WARPS * 32 * 33 * 4 +
-              512;
-  if (fixed + MIN_STAGES * STAGE_BYTES > kSmemLimit) { err = "basis images too large for shared memory"; return false; }
+  // each CTA holds its tile position's two K blocks of each image
+  const int b1 = 2 * rpad_of(cap[0]) * 128, b2 = 2 * rpad_of(cap[1]) * 128;
+  if (smem_fixed_bytes(b1, b2) + NSTAGE * STAGE_BYTES > kSmemLimit) {
+    err = "shared memory budget exceeded";
+    return false;
+  }
   return get_encoder(err);
 }
 
@@ -792,21 +801,17 @@ void tc_carve(TcPlan& plan, Carver& cv, int p, const int64_t* N, const int* cap)
   int64_t nslice = 1;
   for (int n = 2; n < p; ++n) nslice *= N[n];
   int nq1 = (int)((N[0] + TILE - 1) / TILE), nq2 = (int)((N[1] + TILE - 1) / TILE);
-  plan.Abf[0] = cv.take<char>((size_t)nq1 * 2 * rpad_of(cap[0]) * 128);
-  plan.Abf[1] = cv.take<char>((size_t)nq2 * 2 * rpad_of(cap[1]) * 128);
   plan.z1p = cv.take<float>((size_t)nq1 * nslice * N[1] * cap[0]);
   plan.z2p = cv.take<float>((size_t)nq2 * nslice * N[0] * cap[1]);
   plan.wsl = cv.take<double>((size_t)nslice);
   plan.w12f = cv.take<float>((size_t)(nq1 + nq2) * TILE);
   plan.npart = cv.take<double>(1024);
-  // finish: split partials ((3 x 152 + tiles) x 64 x J floats bounds nsplit x tiles x 64 x J
-  // for the split count the launch picks) and one arrival counter per tile
+  // finish: split partials ((FS_CTAS + tiles) x 256 x J floats bound nsplit x tiles x 256 x J
+  // for the split count the launch picks)
   const int jmax = p == 2 ? 1 : (p == 3 ? cap[2] : cap[2] * cap[3]);
   const int64_t ntmax = ((int64_t)cap[0] * N[1] + FS_TE - 1) / FS_TE + ((int64_t)N[0] * cap[1] + FS_TE - 1) / FS_TE;
-  plan.fpart_cap = (size_t)(3 * 152 + ntmax) * FS_TE * jmax;
+  plan.fpart_cap = (size_t)(FS_CTAS + ntmax) * FS_TE * jmax;
   plan.fpart = cv.take<float>(plan.fpart_cap);
-  plan.fcnt_n = (int)ntmax;
-  plan.fcnt = cv.take<unsigned>((size_t)ntmax);
 }
 
 tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, const int64_t* N, const int* r,
@@ -819,14 +824,6 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   for (int n = 2; n < p; ++n) nslice *= (int)N[n];
   const int nq1 = (N1 + TILE - 1) / TILE, nq2 = (N2 + TILE - 1) / TILE;
   const int r1pad = rpad_of(r[0]), r2pad = rpad_of(r[1]);
-  // operand images of A_1 = W_1 U_1 and A_2 = W_2 U_2 (refreshed every step)
-  {
-    const int tot = nq1 * 2 * r1pad * 64 + nq2 * 2 * r2pad * 64;
-    k_pack_bimg<<<(tot + 255) / 256, 256, 0, s>>>((const float*)A[0], N1, r[0], r1pad, nq1 * 2,
-                                                  (__nv_bfloat16*)plan.Abf[0], (const float*)A[1], N2, r[1], r2pad,
-                                                  nq2 * 2, (__nv_bfloat16*)plan.Abf[1]);
-    count_launch();
-  }
   if (!plan.wsl_ready) {
     k_slice_weights<<<(nslice + 255) / 256, 256, 0, s>>>(p, p >= 3 ? w[2] : nullptr, p >= 3 ? (int)N[2] : 1,
                                                          p >= 4 ? w[3] : nullptr, p >= 4 ? (int)N[3] : 1, plan.wsl);
@@ -850,43 +847,37 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   P.r2 = r[1];
   P.r1pad = r1pad;
   P.r2pad = r2pad;
-  P.nunits = nq1 * nq2 * nslice;
+  P.nq12 = nq1 * nq2;
   int dev = 0, nsm = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = std::min(P.nunits, std::min(nsm, 1024));
-  // one unit per CTA: only that unit's two K blocks of each image are resident
-  P.bsub = grid >= P.nunits ? 1 : 0;
-  P.b1_bytes = (P.bsub ? 2 : nq1 * 2) * r1pad * 128;
-  P.b2_bytes = (P.bsub ? 2 : nq2 * 2) * r2pad * 128;
-  // 1 KB alignment slack for the 1024-byte swizzle atoms, then one stage per converter warp
-  int fixed = 1024 + 2 * BF_TILE_BYTES + ((P.b1_bytes + 1023) & ~1023) + ((P.b2_bytes + 1023) & ~1023) +
-              NUM_EPI_WARPS * 32 * 33 * 4 + 512;
-  P.nstages = ((size_t)fixed + (size_t)MAX_STAGES * STAGE_BYTES <= (size_t)kSmemLimit) ? MAX_STAGES : MIN_STAGES;
-  if ((size_t)fixed + (size_t)P.nstages * STAGE_BYTES > (size_t)kSmemLimit) {
+  // persistent grid: for every tile position the same number of CTAs (at most one per SM
+  // in all), each walking a strided set of the slices
+  P.cstep = std::max(1, std::min(nslice, std::min(nsm, 1024) / P.nq12));
+  const int grid = P.nq12 * P.cstep;
+  P.b1_bytes = 2 * r1pad * 128;
+  P.b2_bytes = 2 * r2pad * 128;
+  const int fixed = smem_fixed_bytes(P.b1_bytes, P.b2_bytes);
+  if (fixed + NSTAGE * STAGE_BYTES > kSmemLimit) {
     err = "shared memory budget exceeded";
     return TDB_ERR_UNSUPPORTED;
   }
-  size_t smem = (size_t)fixed + (size_t)P.nstages * STAGE_BYTES;
+  const size_t smem = (size_t)fixed + (size_t)NSTAGE * STAGE_BYTES;
   P.Z1p = plan.z1p;
   P.Z2p = plan.z2p;
-  P.B1img = (const uint4*)plan.Abf[0];
-  P.B2img = (const uint4*)plan.Abf[1];
+  P.A1 = (const float*)A[0];
+  P.A2 = (const float*)A[1];
   P.w1f = plan.w12f;
   P.w2f = plan.w12f + nq1 * TILE;
   P.wsl = plan.wsl;
   P.npart = plan.npart;
   P.flags = flags;
   if (!plan.attr_set) {
-    cudaFuncSetAttribute(k_tc_project<MAX_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
-    cudaFuncSetAttribute(k_tc_project<MIN_STAGES>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
+    cudaFuncSetAttribute(k_tc_project, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     plan.attr_set = true;
   }
   if (evm) cudaEventRecord(evm[0], s);
-  if (P.nstages == MAX_STAGES)
-    k_tc_project<MAX_STAGES><<<grid, NUM_THREADS, smem, s>>>(tmn, tmp, P);
-  else
-    k_tc_project<MIN_STAGES><<<grid, NUM_THREADS, smem, s>>>(tmn, tmp, P);
+  k_tc_project<<<grid, NUM_THREADS, smem, s>>>(tmn, tmp, P);
   count_launch();
   if (evm) cudaEventRecord(evm[1], s);
   cudaError_t e = cudaGetLastError();
@@ -899,19 +890,11 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   const int J = p == 2 ? 1 : (p == 3 ? r[2] : r[2] * r[3]);
   const int nt1 = (int)(((int64_t)r[0] * N2 + FS_TE - 1) / FS_TE);
   const int nt2 = (int)(((int64_t)N1 * r[1] + FS_TE - 1) / FS_TE);
-  int nsplit = (int)std::max<int64_t>(1, (3 * 152 + nt1 + nt2 - 1) / (nt1 + nt2));
+  int nsplit = (int)std::max<int64_t>(1, (FS_CTAS + nt1 + nt2 - 1) / (nt1 + nt2));
   nsplit = std::min({nsplit, std::max(1, nslice / FS_SC), FS_SPLIT_MAX});
   while (nsplit > 1 && (size_t)nsplit * (nt1 + nt2) * FS_TE * J > plan.fpart_cap) --nsplit;
   if (J > FS_JMAX) {
     err = "finish: r_3 r_4 above 128";
-    return TDB_ERR_UNSUPPORTED;
-  }
-  if (!plan.fcnt_ready) {
-    cudaMemsetAsync(plan.fcnt, 0, sizeof(unsigned) * plan.fcnt_n, s);
-    plan.fcnt_ready = true;
-  }
-  if (nt1 + nt2 > plan.fcnt_n) {
-    err = "finish: tile counters exceeded";
     return TDB_ERR_UNSUPPORTED;
   }
   FinArgs f;
@@ -935,32 +918,20 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   f.Y2 = Y[1];
   f.Y1 = Y[0];
   f.part = plan.fpart;
-  f.cnt = plan.fcnt;
   f.nsplit = nsplit;
   f.nt1 = nt1;
   f.nt2 = nt2;
   f.npart = plan.npart;
   f.nnp = grid;
   f.dv2 = dv2;
-  const size_t fsm = sizeof(float) * (FS_SC * (FS_TE + 1) + FS_SC * J);
-  if (!plan.fin_attr) {
-    const int mx = (int)(sizeof(float) * (FS_SC * (FS_TE + 1) + FS_SC * FS_JMAX));
-    cudaFuncSetAttribute(k_tc_finish_sk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_tc_finish_sk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_tc_finish_sk<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_tc_finish_sk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_tc_finish_sk<16>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    cudaFuncSetAttribute(k_tc_finish_sk<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
-    plan.fin_attr = true;
-  }
-  const dim3 fgrid((nt1 + nt2) * nsplit);
-  if (J <= 4) k_tc_finish_sk<1><<<fgrid, 256, fsm, s>>>(f);
-  else if (J <= 8) k_tc_finish_sk<2><<<fgrid, 256, fsm, s>>>(f);
-  else if (J <= 16) k_tc_finish_sk<4><<<fgrid, 256, fsm, s>>>(f);
-  else if (J <= 32) k_tc_finish_sk<8><<<fgrid, 256, fsm, s>>>(f);
-  else if (J <= 64) k_tc_finish_sk<16><<<fgrid, 256, fsm, s>>>(f);
-  else k_tc_finish_sk<32><<<fgrid, 256, fsm, s>>>(f);
+  const size_t fsm = sizeof(float) * FS_SC * ((J + 3) & ~3);
+  k_tc_finish_sk<<<(nt1 + nt2) * nsplit, FS_TE, fsm, s>>>(f);
   count_launch();
+  if (nsplit > 1) {
+    const int64_t outs = (int64_t)(nt1 + nt2) * J * FS_TE;
+    k_tc_finish_red<<<(int)std::min<int64_t>((outs + 255) / 256, 152 * 16), 256, 0, s>>>(f);
+    count_launch();
+  }
   if (p >= 3) {
     // Z1 summed over the mode-1 tiles: the partials themselves when there is one tile
     const float* z1 = nq1 > 1 ? Z1 : plan.z1p;

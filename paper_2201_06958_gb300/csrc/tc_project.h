@@ -9,7 +9,6 @@ namespace tdb {
 
 struct TcPlan {
   int p = 0;
-  void* Abf[2] = {nullptr, nullptr};  // BF16 operand images of A_1, A_2 (128-byte swizzled, K-major)
   float* z1p = nullptr;               // [tiles along i1][slices][N2][r1] partial dV x_1 A_1^T
   float* z2p = nullptr;               // [tiles along i2][slices][N1][r2] partial dV x_2 A_2^T
   double* wsl = nullptr;              // product of the weights of modes >= 3, per slice
@@ -17,10 +16,7 @@ struct TcPlan {
   double* npart = nullptr;            // per-CTA ||dV||_W^2
   float* fpart = nullptr;             // split partials of the finishing contraction
   size_t fpart_cap = 0;               // floats
-  unsigned* fcnt = nullptr;           // per-tile arrival counters of the finish (zero at rest)
-  int fcnt_n = 0;
-  bool fcnt_ready = false;
-  bool fin_attr = false;
+
   bool wsl_ready = false;
   bool attr_set = false;
 };

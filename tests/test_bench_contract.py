@@ -26,7 +26,7 @@ def test_reference_arm_json_line(integrator):
     assert d["impl"] == "reference" and d["value"] > 0 and d["steps"] == 2 and d["warmup"] == 1
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
-    assert d["config"]["workload"].startswith("reactive 512x256x12")
+    assert d["config"]["workload"].startswith("stochastic 256x128x512")
     assert d["config"]["integrator"] == integrator
 
 
