@@ -33,7 +33,7 @@ import numpy as np
 
 __all__ = [
     "unfold", "fold", "mode_product", "multi_mode_product", "weighted_bases",
-    "project", "core_gram", "basis_rhs", "tdb_rhs", "step_euler", "step_heun", "step_rk4",
+    "project", "core_gram", "basis_rhs", "tdb_rhs", "step_euler", "step_heun", "step_rk2_central", "step_rk4",
     "cholqr", "reconstruct", "weighted_norm2", "error_exact",
     "hosvd_spectrum", "hosvd", "rank_from_spectrum", "rank_from_core",
     "core_singular_values", "gamma_percent", "rotate_coherent",
@@ -177,6 +177,30 @@ def step_heun(T, U, w, V_k, V_k1, reorth: bool = True):
     k2T, k2U = tdb_rhs(Tp, Up, w, dV)
     T1 = T + 0.5 * (k1T + k2T)
     U1 = [U[n] + 0.5 * (k1U[n] + k2U[n]) for n in range(T.ndim)]
+    if reorth:
+        T1, U1 = cholqr(T1, U1, w)
+    return T1, U1
+
+
+def step_rk2_central(T, U, w, V_km1, V_k, V_k1, reorth: bool = True):
+    """One step of the midpoint second-order Runge-Kutta scheme with second-order central
+    differences of the data (Sec. 3.1 compares the central second-order approximation of
+    the data derivative with the first-order one and with the exact derivative, and
+    advances with a second-order RK scheme; Sec. 2.3 notes that higher-order differences
+    keep several snapshots in memory).  Stage 1 takes the derivative at t_k,
+    dt V'(t_k) ~ (V_{k+1} - V_{k-1}) / 2, over half a step to the midpoint state; stage 2
+    takes the derivative at t_k + dt/2, dt V'(t_k + dt/2) ~ V_{k+1} - V_k (the central
+    difference about the midpoint), at the midpoint state, over the whole step from the
+    state of step k.  Without V_{k-1} (the first step) stage 1 uses (V_{k+1} - V_k) / 2.
+    Re-orthonormalisation after the step (reading C4; the midpoint state is an
+    intermediate of the scheme and is not).  Returns (T', U')."""
+    dV1 = 0.25 * (V_k1 - V_km1) if V_km1 is not None else 0.5 * (V_k1 - V_k)
+    k1T, k1U = tdb_rhs(T, U, w, dV1)
+    Tm = T + k1T
+    Um = [U[n] + k1U[n] for n in range(T.ndim)]
+    k2T, k2U = tdb_rhs(Tm, Um, w, V_k1 - V_k)
+    T1 = T + k2T
+    U1 = [U[n] + k2U[n] for n in range(T.ndim)]
     if reorth:
         T1, U1 = cholqr(T1, U1, w)
     return T1, U1
