@@ -276,12 +276,23 @@ def hosvd_spectrum(V: np.ndarray, w: Sequence[np.ndarray]):
     squared mode-n singular values of the weighted data (Sec. 2.4; Sec. 2.6 gives
     the same correlation matrix for the HOSVD cost).  Returns a list of
     (lambda descending, Q) with Q orthonormal columns, sign fixed.
+
+    A mode longer than the product M of the others (a grouped spatial mode, Sec. 3.2)
+    has C_n = B B^T of rank at most M, with B the weighted unfolding (N_n x M): its
+    nonzero eigenvalues are the squared singular values of B and their eigenvectors B's
+    left singular vectors.  For such a mode the thin SVD of B gives them (a library
+    routine as a step, the same definition without forming the N_n x N_n matrix), and
+    the list holds M eigenvalues and M vectors; the rest of the spectrum is zero.
     """
     sw = [np.sqrt(wn) for wn in w]
     Vw = multi_mode_product(V, [np.diag(s) for s in sw])
     out = []
     for n in range(V.ndim):
         Vn = unfold(Vw, n)
+        if Vn.shape[0] > Vn.shape[1]:
+            Q, sv, _ = np.linalg.svd(Vn, full_matrices=False)
+            out.append((sv * sv, _sign_fix(Q)))
+            continue
         C = Vn @ Vn.T
         lam, Q = np.linalg.eigh(C)
         order = np.argsort(lam)[::-1]

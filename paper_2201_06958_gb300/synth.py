@@ -427,6 +427,13 @@ def _reactive_dbo(seed: int, nx: int = 32, ny: int = 16, ns: int = 12, **kw) -> 
                        name="reactive_dbo")
 
 
+def _reactive_tdb2(seed: int, nx: int = 251, ny: int = 76, ns: int = 23, **kw) -> Workload:
+    """TDB-2 at the size of Sec. 3.2: the reactive recipe on a 251 x 76 grid with 23 species,
+    the grid taken as one 19,076-point spatial mode beside the species mode."""
+    return group_modes(_reactive(seed, nx=nx, ny=ny, ns=ns, **kw), [[0, 1], [2]], rank_max=[23, 23],
+                       name="reactive_tdb2")
+
+
 WORKLOADS = {
     "analytic": lambda seed=1001, **kw: _analytic(seed, **kw),
     "reactive": lambda seed=1002, **kw: _reactive(seed, **kw),
@@ -434,11 +441,12 @@ WORKLOADS = {
     "channel": lambda seed=1004, **kw: _channel(seed, **kw),
     "runge": lambda seed=1005, **kw: _runge(seed, **kw),
     "reactive_dbo": lambda seed=1006, **kw: _reactive_dbo(seed, **kw),
+    "reactive_tdb2": lambda seed=1007, **kw: _reactive_tdb2(seed, **kw),
 }
 
 
 DEFAULT_SEEDS = {"analytic": 1001, "reactive": 1002, "stochastic": 1003, "channel": 1004, "runge": 1005,
-                 "reactive_dbo": 1006}
+                 "reactive_dbo": 1006, "reactive_tdb2": 1007}
 
 
 def default_seed(name: str) -> int:

@@ -126,3 +126,25 @@ def test_grouped_controller_moves_both_ranks_together():
     _, recs = O.compress_stream(snaps, wl.weights, [0, 0], ctrl)
     assert all(r.ranks[0] == r.ranks[1] for r in recs)
     assert {"increase", "revert"} <= {r.action for r in recs}
+
+
+def test_long_mode_spectrum_by_thin_svd_equals_gram_eigendecomposition():
+    """A mode longer than the product of the others (60 > 4 x 3) takes its HOSVD spectrum
+    from the thin SVD of the weighted unfolding: the same leading eigenvalues and
+    eigenvectors (as projectors) as the eigen-decomposition of its N_n x N_n Gram, and a
+    zero tail beyond the 12 returned values."""
+    rng = np.random.default_rng(61)
+    dims = (60, 4, 3)
+    w = [rng.uniform(0.5, 1.5, N) for N in dims]
+    w = [x / x.sum() for x in w]
+    V = rng.standard_normal(dims)
+    lam, Q = O.hosvd_spectrum(V, w)[0]
+    assert lam.shape == (12,) and Q.shape == (60, 12)
+    B = np.sqrt(w[0])[:, None] * O.unfold(V * np.sqrt(w[1])[None, :, None] * np.sqrt(w[2])[None, None, :], 0)
+    ev, EV = np.linalg.eigh(B @ B.T)
+    order = np.argsort(ev)[::-1]
+    ev, EV = ev[order], EV[:, order]
+    assert np.allclose(lam, ev[:12], rtol=1e-12, atol=1e-14 * ev[0])
+    assert np.abs(ev[12:]).max() <= 1e-12 * ev[0]
+    for k in (3, 7, 12):
+        assert np.abs(Q[:, :k] @ Q[:, :k].T - EV[:, :k] @ EV[:, :k].T).max() <= 1e-10
