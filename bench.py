@@ -45,8 +45,9 @@ def parse_args():
                     choices=["reactive", "stochastic", "channel", "analytic", "runge", "reactive_dbo", "batch"])
     ap.add_argument("--precision", default="auto", choices=["auto", "bf16", "fp32", "fp64"])
     ap.add_argument("--error-mode", default="auto", choices=["auto", "exact", "mlp", "every_k"])
-    ap.add_argument("--integrator", default="euler", choices=["euler", "heun"],
-                    help="heun: two projection passes per snapshot (second-order scheme)")
+    ap.add_argument("--integrator", default="euler", choices=["euler", "heun", "rk2_central"],
+                    help="heun / rk2_central: two projection passes per snapshot (second-order schemes; "
+                         "rk2_central uses central differences of the data and tdb_push_snapshot)")
     ap.add_argument("--train-steps", type=int, default=300,
                     help="steps of the separate training stream for the error estimator")
     ap.add_argument("--api", default="slots", choices=["slots", "pointer"],
@@ -227,6 +228,7 @@ budget = {budget}
 ctrl = O.ControllerConfig(wl.eps_th, wl.gamma_th, 10, wl.rank_max) if wl.eps_th > 0 else None
 # only the compressor is timed; snapshot generation is outside the clock
 V_prev = S.to_logical(wl.snapshot(0))
+V_pp = None
 spec = O.hosvd_spectrum(V_prev, w)
 caps = O.rank_caps(wl.dims, wl.rank_max)
 r = [min(caps[n], O.rank_from_spectrum(spec[n][0], wl.gamma_th)) if wl.rank[n] == 0 else wl.rank[n] for n in range(wl.ndim)]
@@ -242,6 +244,8 @@ while elapsed < budget and steps < {max_steps}:
     t0 = time.perf_counter()
     if {heun}:
         T1, U1 = O.step_heun(st.T, st.U, w, V_prev, V)
+    elif {rk2c}:
+        T1, U1 = O.step_rk2_central(st.T, st.U, w, V_pp, V_prev, V)
     else:
         T1, U1, _, _ = O.step_euler(st.T, st.U, w, V_prev, V)
     st = O.TDBState(T1, U1)
@@ -250,7 +254,7 @@ while elapsed < budget and steps < {max_steps}:
         st, eps, _, _ = controller.act(V, st, eps)
     elapsed += time.perf_counter() - t0
     steps += 1
-    V_prev = V
+    V_pp, V_prev = V_prev, V
 print(json.dumps({{"steps": steps, "seconds": elapsed}}))
 """
 
@@ -263,7 +267,7 @@ def _oracle_sample(workload: str, budget_s: float, max_steps: int, integrator: s
         env[k] = str(threads)
     env["CUDA_VISIBLE_DEVICES"] = ""
     code = CPU_SNIPPET.format(root=ROOT, wl=workload, budget=budget_s, max_steps=max_steps,
-                              heun=integrator == "heun")
+                              heun=integrator == "heun", rk2c=integrator == "rk2_central")
     p = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
     if p.returncode != 0:
         return p.stderr[-400:]
@@ -298,7 +302,8 @@ def run_reference(args, world, rank):
     cores = os.cpu_count() or 1
     wl_name = args.workload
     total = args.warmup + args.steps
-    code = CPU_SNIPPET.format(root=ROOT, wl=wl_name, budget=1e9, max_steps=total, heun=args.integrator == "heun")
+    code = CPU_SNIPPET.format(root=ROOT, wl=wl_name, budget=1e9, max_steps=total, heun=args.integrator == "heun",
+                              rk2c=args.integrator == "rk2_central")
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(cores)
@@ -566,7 +571,9 @@ def run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_para
     c = tdb.TDB(wl.dims, wl.rank, rank_max=wl.rank_max, weights=wl.weights, eps_th=wl.eps_th,
                 gamma_th=wl.gamma_th, precision=precision, error_mode=err_mode, error_every=20,
                 integrator=integrator, device=dev)
-    ring = [torch.empty_like(snaps[0]) for _ in range(2)]
+    # the library borrows the last pushed snapshot (the last two under central differences)
+    nring = 3 if integrator == "rk2_central" else 2
+    ring = [torch.empty_like(snaps[0]) for _ in range(nring)]
     stream = torch.cuda.current_stream(dev)
     ring[0].copy_(host[0], non_blocking=True)
     c.init(ring[0])
@@ -578,7 +585,7 @@ def run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_para
     info = tdb.tdb_step_info()
 
     def step(k):
-        buf = ring[k % 2]
+        buf = ring[k % nring]
         buf.copy_(host[k], non_blocking=True)          # H2D of this step's snapshot (pinned)
         if slots:                                      # the step; it reads the result back to the host
             return lib.tdb_push_slot(c.ctx, 1 - k % 2, C.byref(info))
@@ -604,12 +611,51 @@ def run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_para
             "exact_evals": cnt["exact_evals"]}
 
 
+def train_estimator_on_configs(dev, tdb, S, steps=120):
+    """Fit the error estimator on traces of the analytic, reactive and stochastic streams
+    (the single-tensor workloads), each run in BF16 with the exact error every step; returns
+    (parameters, report).  Not timed."""
+    import torch
+    Xs, ts, used = [], [], []
+    for name, kw in (("analytic", {"n": 64}), ("reactive", {}), ("stochastic", {})):
+        wl = S.make_workload(name, seed=7000 + S.default_seed(name), **kw)
+        c = tdb.TDB(wl.dims, wl.rank or [4] * wl.ndim, rank_max=wl.rank_max, weights=wl.weights,
+                    eps_th=wl.eps_th, gamma_th=wl.gamma_th, precision="bf16", error_mode="exact", device=dev)
+        bufs = [wl.snapshot(0, device=dev, dtype=torch.float32), None]
+        c.init(bufs[0])
+        for k in range(1, steps + 1):
+            bufs[k % 2] = wl.snapshot(k, device=dev, dtype=torch.float32)
+            c.push(bufs[k % 2])
+        X, t = c.estimator_trace()
+        Xs.append(X)
+        ts.append(t)
+        used.append(f"{name} ({len(t)} rows)")
+        c.close()
+    import numpy as np
+    X, t = np.concatenate(Xs), np.concatenate(ts)
+    wl = S.make_workload("reactive", nx=64, ny=48, ns=6)
+    c = tdb.TDB(wl.dims, [4, 4, 3], weights=wl.weights, precision="bf16", error_mode="exact", device=dev)
+    c.init(wl.snapshot(0, device=dev))
+    c.estimator_load_trace(X, t)
+    t0 = time.perf_counter()
+    loss = c.estimator_fit(iters=2000, lr=3e-3, seed=11, gate=0.9)
+    torch.cuda.synchronize()
+    params = c.estimator_params()
+    c.close()
+    return params, {"train_streams": ", ".join(used), "rows": int(len(t)), "fit_loss": loss,
+                    "fit_seconds": time.perf_counter() - t0, "gate": 0.9, "max_skip": 20}
+
+
 def run_batch(args, world, rank, local):
     """The batched configuration: 64 independent 3-mode tensors (N_n ~ U{32..128}, ranks
-    U{4..24}), one context each (BF16 tensor cores where N_1 is a multiple of 4, FP32
-    otherwise), every member's step recorded into one graph over 8 streams.  value =
-    member snapshots per second.  Each batch step first moves the 64 resident snapshots
-    into the members' input slots (torch._foreach_copy_, inside the timed region)."""
+    U{4..24}), one BF16 tensor-core context each (members whose N_1 is not a multiple of 4
+    stream zero-padded copies), launch shapes picked by the projection's tuner on each
+    member's first step, the learned error estimator trained on traces of the
+    single-tensor streams (configs 1-3) gating each member's exact error (eps_th = 5e-3,
+    above the members' 1e-3 noise floor; ranks fixed at their initial values), every
+    member's step recorded into one graph over 8 streams.  value = member snapshots per
+    second.  Each batch step first moves the 64 resident snapshots into the members'
+    input slots (torch._foreach_copy_, inside the timed region)."""
     import ctypes as C
     import torch
     from paper_2201_06958_gb300 import build_lib, tdb, synth as S
@@ -617,6 +663,7 @@ def run_batch(args, world, rank, local):
     lib = tdb.load()
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
+    est_params, est_info = train_estimator_on_configs(dev, tdb, S)
     members = S.make_batch(seed=1005 + 10 * rank, count=64)
     K, W = min(args.steps, 200), args.warmup
     nsnap = W + K + 1
@@ -631,12 +678,12 @@ def run_batch(args, world, rank, local):
         for k in range(nsnap):
             st[k] = wl.snapshot(k, device=dev)
         streams.append(st)
-        prec = "bf16" if wl.dims[0] % 4 == 0 else "fp32"
-        c = tdb.TDB(wl.dims, wl.rank, rank_max=wl.rank_max, weights=wl.weights, precision=prec,
-                    error_mode="every_k", error_every=20, device=dev)
+        c = tdb.TDB(wl.dims, wl.rank, rank_max=wl.rank_max, weights=wl.weights, eps_th=5e-3, gamma_th=wl.gamma_th,
+                    precision="bf16", error_mode="mlp", error_every=20, device=dev)
         sl = [torch.empty_like(st[0]), torch.empty_like(st[0])]
         sl[1].copy_(st[0])
         c.init(sl[1]).set_input_slots(sl[0], sl[1])
+        c.estimator_params(est_params, gate=0.9)
         ctxs.append(c)
         slots.append(sl)
     batch = tdb.Batch(ctxs, nstreams=8)
@@ -672,18 +719,29 @@ def run_batch(args, world, rank, local):
     value, ms_total = replica_value(world, K * len(ctxs), ms, host_s)
     counters = batch.counters()
     nbf16 = sum(1 for c in ctxs if c.precision == "bf16")
+    tun = [c.tuning() for c in ctxs]
+    exact = sum(c.counters()["exact_evals"] for c in ctxs)
     alg = 2 * 4 * total
     gbs = alg / (ms_total / K * 1e-3) / 1e9
     peak, peak_kind = measured_peaks()
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_total / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "bf16+f32", "data": "synthetic",
+        "dtype": "bf16", "data": "synthetic",
         "config": {"workload": f"batch of {len(ctxs)} 3-mode tensors, N_n ~ U{{32..128}}, r ~ U{{4..24}}, "
-                               f"{total / 1e6:.1f}M elements per batch step, fixed ranks, exact error every 20 steps",
-                   "members": len(ctxs), "members_bf16": nbf16, "elements_per_step": total, "api": "batch graph",
+                               f"{total / 1e6:.1f}M elements per batch step, ranks fixed at their initial values, "
+                               "exact error gated by the learned estimator (eps_th = 5e-3)",
+                   "members": len(ctxs), "members_bf16": nbf16,
+                   "members_padded": sum(1 for wl in members if wl.dims[0] % 4 != 0),
+                   "elements_per_step": total, "api": "batch graph",
                    "ingest": "torch._foreach_copy_ of the resident snapshots into the slots, timed",
                    "parallelism": f"replicas x{world}"},
+        "estimator": dict(est_info, exact_eval_fraction=exact / max(len(ctxs) * (K + W), 1)),
+        "tuner": {"members_below_full_grid": sum(1 for t in tun
+                                                 if t["candidates"] and t["ctas_per_position"] < max(t["candidates"])),
+                  "members_timed": sum(1 for t in tun if t["timed"]),
+                  "choices": [t["ctas_per_position"] for t in tun],
+                  "finish_split_targets": [t["finish_split_target"] for t in tun]},
         "roofline": {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
                      "traffic": None, "kernel": "whole batch step (graph)", "algorithmic_bytes_per_launch": alg,
                      "peak_source": peak_kind},
@@ -747,6 +805,8 @@ def run_scaling_sweep(args):
 
 def main():
     args = parse_args()
+    if args.integrator == "rk2_central":
+        args.api = "pointer"          # its central differences need three snapshots; slots hold two
     if args.scaling_sweep:
         run_scaling_sweep(args)
         return

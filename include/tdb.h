@@ -65,7 +65,11 @@ enum tdb_precision {
   TDB_FP64 = 0,       /* double snapshots; every step in double (parity mode) */
   TDB_FP32 = 1,       /* float snapshots; unfused CUDA-core kernels, float products */
   TDB_BF16_TTM = 2    /* float snapshots; fused difference + projection on the tensor
-                         cores (bf16 operands, fp32 accumulation), fp64 small algebra */
+                         cores (bf16 operands, fp32 accumulation), fp64 small algebra.
+                         Where N_1 is not a multiple of 4 (TMA needs 16-byte row strides) the
+                         step first copies V_{k+1} and V_k into zero-padded rows of the
+                         workspace (two extra snapshot-sized buffers, an extra read and write
+                         of both snapshots per projection pass). */
 };
 
 /* When the exact error of Eq. 2.20 is evaluated. */
@@ -80,12 +84,23 @@ enum tdb_error_mode {
    Delta V = V_{k+1} - V_k as the data forcing (first-order forward difference, Sec. 2.3). */
 enum tdb_integrator {
   TDB_EULER = 0,      /* explicit Euler: one projection pass per snapshot */
-  TDB_HEUN = 1        /* Heun's second-order Runge-Kutta scheme (Sec. 3.1 compares it with
+  TDB_HEUN = 1,       /* Heun's second-order Runge-Kutta scheme (Sec. 3.1 compares it with
                          Euler): the Euler increment at the state of step k gives a predicted
                          state, the increment there a second one, and the step takes their
                          mean.  Both stages use Delta V (the piecewise-linear interpolant of
                          the snapshots); the predicted state is not re-orthonormalised.  Two
                          projection passes and two fused updates per snapshot. */
+  TDB_RK2_CENTRAL = 2 /* the midpoint second-order Runge-Kutta scheme with second-order
+                         central differences of the data (Sec. 3.1): stage 1 takes
+                         dt V'(t_k) ~ (V_{k+1} - V_{k-1}) / 2 over half a step to the midpoint
+                         state, stage 2 takes dt V'(t_k + dt/2) ~ V_{k+1} - V_k at the midpoint
+                         state over the whole step from the state of step k.  The first step
+                         after an (re)initialisation, a state load or tdb_adapt_rank uses
+                         (V_{k+1} - V_k) / 2 in stage 1.  Keeps the last TWO pushed snapshots
+                         borrowed (V_{k-1} and V_k must stay unmodified until the next push
+                         returns); tdb_push_snapshot only (input slots and batches refuse it
+                         with TDB_ERR_UNSUPPORTED).  Two projection passes and two fused
+                         updates per snapshot. */
 };
 
 typedef struct tdb_config {
@@ -253,6 +268,11 @@ tdb_status tdb_estimator_params(tdb_ctx* ctx, float* get_out, const float* set_i
 /* Recorded training rows: on input *n is the capacity of X (n x 8) and t (n); on
  * output the number recorded (X, t may be NULL to query). */
 tdb_status tdb_estimator_trace(tdb_ctx* ctx, float* X, float* t, int* n);
+/* Install training rows recorded elsewhere (e.g. tdb_estimator_trace of contexts run on
+ * other streams) before tdb_estimator_fit: X (host, n x 8) and t (host, n) replace the
+ * context's own rows (append = 0) or are added after them (append = 1); the trace keeps
+ * its most recent 8192 rows.  TDB_ERR_INVALID_ARG for null data or n < 1. */
+tdb_status tdb_estimator_load_trace(tdb_ctx* ctx, const float* X, const float* t, int n, int append);
 
 /* Accumulated device times of the phases of tdb_push_snapshot, measured with CUDA
  * events on the context's stream while profiling is enabled (tdb_set_profiling).
@@ -341,6 +361,19 @@ tdb_status tdb_project_noalloc(int ndim, const int64_t* dims, const int* ranks, 
 tdb_status tdb_selftest_recip(const double* x, double* rcp, double* rsqrt, int64_t n, void* stream);
 tdb_status tdb_selftest_timeout(int which, int64_t limit_cycles, unsigned* scratch, void* stream);
 
+/* The launch shape the tensor-core projection's tuner chose for this context (TDB_BF16_TTM
+ * only; the paper has no counterpart).  The tile is fixed (128 x 128, eight strips); the
+ * tuner times, on the context's first step outside stream capture, each candidate number
+ * of CTAs per tile position in the persistent grid and each split target of the finishing
+ * contraction, and keeps the fastest (cached per shape for the process).  Host outputs,
+ * each nullable: ctas = CTAs per tile position, fin_target = the finish's split target
+ * (CTAs), ncand = candidates timed (0 when the choice came from the cache), cand /
+ * cand_us = up to 4 candidates and their microseconds per launch, fin_cand / fin_us = the
+ * 3 split targets and theirs.  TDB_ERR_STATE before the first step or without the
+ * tensor-core path. */
+tdb_status tdb_tc_tuning(const tdb_ctx* ctx, int* ctas, int* fin_target, int* ncand, int* cand, float* cand_us,
+                         int* fin_cand, float* fin_us);
+
 /* Library version and build facts: "tdb <ver> sm_103a". */
 /* ---------------------------------------------------------------------------
  * Input slots and recorded steps.  The paper streams one snapshot per step (Sec. 2.3);
@@ -351,7 +384,8 @@ tdb_status tdb_selftest_timeout(int which, int64_t limit_cycles, unsigned* scrat
  *   into them, e.g. straight from a simulation or a host copy).  NULL, NULL removes them.
  * tdb_push_slot: one step with V_{k+1} in slot[parity] and V_k in slot[1 - parity];
  *   the previous step (or the init) must have consumed slot[1 - parity], otherwise
- *   TDB_ERR_STATE.  The device work of the step is recorded once per slot parity and
+ *   TDB_ERR_STATE; TDB_ERR_UNSUPPORTED under TDB_RK2_CENTRAL (its central differences
+ *   need three snapshots).  The device work of the step is recorded once per slot parity and
  *   rank configuration as a CUDA graph and replayed afterwards, so a step costs one
  *   launch; the results are those of tdb_push_snapshot on the same snapshots.  Steps
  *   run as tdb_push_snapshot does (not recorded) while profiling is enabled, on the

@@ -21,19 +21,20 @@ long long launches_so_far() { return g_launches.load(std::memory_order_relaxed);
 // Elementwise
 // ---------------------------------------------------------------------------
 
+// out = scale (a - b): the snapshot difference (scale 1), or a scaled central difference
 template <typename T>
-__global__ void k_diff(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out, int64_t n) {
+__global__ void k_diff(const T* __restrict__ a, const T* __restrict__ b, T* __restrict__ out, int64_t n, T scale) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    out[i] = a[i] - b[i];
+    out[i] = (a[i] - b[i]) * scale;
 }
 
 template <typename T>
-void launch_diff(const T* a, const T* b, T* out, int64_t n, cudaStream_t s) {
+void launch_diff(const T* a, const T* b, T* out, int64_t n, cudaStream_t s, T scale) {
   int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
-  k_diff<T><<<blocks, 256, 0, s>>>(a, b, out, n); count_launch();
+  k_diff<T><<<blocks, 256, 0, s>>>(a, b, out, n, scale); count_launch();
 }
-template void launch_diff<float>(const float*, const float*, float*, int64_t, cudaStream_t);
-template void launch_diff<double>(const double*, const double*, double*, int64_t, cudaStream_t);
+template void launch_diff<float>(const float*, const float*, float*, int64_t, cudaStream_t, float);
+template void launch_diff<double>(const double*, const double*, double*, int64_t, cudaStream_t, double);
 
 // A = W U in the compute type: A[i + N a] = w[i] U[i + N a]  (Eq. 2.17).
 template <typename T>

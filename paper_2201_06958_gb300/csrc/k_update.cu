@@ -675,7 +675,8 @@ __device__ void rows_mxp(const UpdArgs& a, int n, int64_t i0, int tile, unsigned
 }
 
 // Phase 2 on one tile of mode n: P_n, E = X - U P_n, U' = U + E (Heun's second stage:
-// U' = (U0 + U + E) / 2), partial C = U'^T W U'.
+// U' = (U0 + U + E) / 2; the midpoint scheme's second stage: U' = U0 + E), partial
+// C = U'^T W U'.
 template <typename Tc>
 __device__ void rows_u1(const UpdArgs& a, int n, int64_t i0, int tile, unsigned char* sm) {
   const ModeDesc& d = a.d;
@@ -706,7 +707,9 @@ __device__ void rows_u1(const UpdArgs& a, int n, int64_t i0, int tile, unsigned 
     Tc e = __ldcg(&((const Tc*)a.X[n])[i + N * ca]);
     for (int b = 0; b < r; ++b) e -= Ush[li][b] * Psh[b + LD * ca];
     const int64_t ix = i + N * ca;
-    const double up = a.T0 ? 0.5 * ((a.U[n][ix] + a.U0[n][ix]) + (double)e) : a.U[n][ix] + (double)e;
+    const double up = !a.T0             ? a.U[n][ix] + (double)e
+                      : a.combine == 2 ? a.U0[n][ix] + (double)e
+                                       : 0.5 * ((a.U[n][ix] + a.U0[n][ix]) + (double)e);
     a.Up[n][i + N * ca] = up;
     upc = (Tc)up;
   }
@@ -905,7 +908,7 @@ __device__ void rows_u2(const UpdArgs& a, int n, int64_t i0, unsigned char* sm) 
 }
 
 // Core mode product dst = src x_n R_n (R_n upper triangular); the first mode adds dS
-// to T (Heun's second stage: forms (T0 + T + dS) / 2).  Work is split by mode-n fibers (the r_n entries at fixed other indices):
+// to T (Heun's second stage: forms (T0 + T + dS) / 2; the midpoint scheme's: T0 + dS).  Work is split by mode-n fibers (the r_n entries at fixed other indices):
 // each pass stages F fibers per CTA in shared memory (one coalesced load per
 // thread), F chosen so that every CTA of the grid has some.
 template <typename Tc>
@@ -930,6 +933,8 @@ __device__ void core_mode(const UpdArgs& a, int n, const double* src, double* ds
       idx = l + L * (j + (int64_t)r * q);
       if (n != 0)
         Xs[j * F + fl] = __ldcg(&src[idx]);
+      else if (a.T0 && a.combine == 2)
+        Xs[j * F + fl] = a.T0[idx] + (double)dS[idx];
       else if (a.T0)
         Xs[j * F + fl] = 0.5 * ((src[idx] + a.T0[idx]) + (double)dS[idx]);
       else

@@ -83,6 +83,7 @@ struct UpdArgs {
   // the layout of T/U.  Null for an Euler step (and for Heun's first stage).
   const double* T0;
   const double* U0[kMaxModes];
+  int combine;                   // with T0: 1 = Heun's mean (T0 + T + dT) / 2, 2 = T0 + dT (midpoint)
   unsigned* bar;                 // arrival counter of the grid barriers (zeroed per launch)
   unsigned long long* stamps;    // per-phase timer stamps (profiling), or null
   unsigned* flags;
@@ -100,7 +101,7 @@ void count_launch(int n = 1);
 long long launches_so_far();
 
 // k_basic.cu
-template <typename T> void launch_diff(const T* a, const T* b, T* out, int64_t n, cudaStream_t s);
+template <typename T> void launch_diff(const T* a, const T* b, T* out, int64_t n, cudaStream_t s, T scale = T(1));
 template <typename T> void launch_weighted_bases(const double* U, const double* w, T* A, int64_t N, int r, cudaStream_t s);
 template <typename Ts, typename Td> void launch_cast(const Ts* a, Td* b, int64_t n, cudaStream_t s);
 template <typename Tb> void launch_add(const double* a, const Tb* b, double* out, int64_t n, cudaStream_t s);

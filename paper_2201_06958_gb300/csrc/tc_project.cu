@@ -25,7 +25,9 @@
 #include <cudaTypedefs.h>
 
 #include <cstring>
+#include <map>
 #include <mutex>
+#include <tuple>
 
 #include "tc_project.h"
 
@@ -68,6 +70,7 @@ struct Params {
   const double* wsl;             // slice weights (product over modes >= 3)
   double* npart;                 // per-CTA ||dV||_W^2
   unsigned* flags;
+  float dscale;                  // dV = dscale (V_{k+1} - V_k) (1; 1/4 or 1/2 for a central difference)
 };
 
 // Shared memory of the fused kernel: 1 KB alignment slack, two BF16 tiles, the two image
@@ -329,7 +332,9 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         const int N = img == 0 ? P.N1 : P.N2, r = img == 0 ? P.r1 : P.r2, rpad = img == 0 ? P.r1pad : P.r2pad;
         const int i0 = (img == 0 ? q1 : q2) * TILE;
         unsigned char* dst = img == 0 ? b1_smem : b2_smem;
-        const bool vec = img == 0;                     // N_1 is a multiple of 4: whole float4 in or out
+        // float4 reads only where every column of A starts on a 16-byte boundary (N a
+        // multiple of 4; a whole float4 is then in or out); otherwise element by element
+        const bool vec = (N & 3) == 0;
         for (int item = et; item < 2 * rpad * 8; item += NUM_EPI_WARPS * 32) {
           const int kc = item & 7, a = (item >> 3) % rpad, g = (item >> 3) / rpad;
           const int i = i0 + g * 64 + kc * 8;
@@ -457,7 +462,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const int row = ry + 2 * k;                 // 0..15 within the strip
           const float4 a = vn[row * 32 + h * 16 + cx];
           const float4 b = vp[row * 32 + h * 16 + cx];
-          const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z, d3 = a.w - b.w;
+          const float d0 = (a.x - b.x) * P.dscale, d1 = (a.y - b.y) * P.dscale;
+          const float d2 = (a.z - b.z) * P.dscale, d3 = (a.w - b.w) * P.dscale;
           const int r = c * SUB_I2 + row;             // tile row (i2 within the tile)
           acc += w2v[k] * (w1v[h][0] * d0 * d0 + w1v[h][1] * d1 * d1 + w1v[h][2] * d2 * d2 + w1v[h][3] * d3 * d3);
           uint2 pk = make_uint2(pack_bf16x2(d0, d1), pack_bf16x2(d2, d3));
@@ -527,6 +533,7 @@ __global__ void k_selftest_mbar(unsigned* flags, long long limit) {
 // every output in split order (so results do not vary from run to run).
 constexpr int FS_TE = 256, FS_SC = 16, FS_JB = 32, FS_JMAX = 128, FS_SPLIT_MAX = 32;
 constexpr int FS_CTAS = 2 * 152;   // split target: about two CTAs per SM
+constexpr int FS_NQ_MAX = 1024 / 128;   // tiles along mode 1 or 2 (modes of at most 1024 points)
 struct FinArgs {
   const float* Z1p;
   const float* Z2p;
@@ -544,7 +551,9 @@ struct FinArgs {
   double* dv2;
 };
 
+template <int NQ>   // tiles along the contracted mode, rounded up to a power of two (<= 8)
 __global__ void __launch_bounds__(FS_TE) k_tc_finish_sk(FinArgs f) {
+  constexpr int SC = NQ <= 2 ? FS_SC : (NQ == 4 ? FS_SC / 2 : FS_SC / 4);   // slices per chunk
   extern __shared__ __align__(16) float fs_sm[];    // B rows of a slice chunk: [FS_SC][Jp]
   __shared__ double dsh[32];
   const int tid = threadIdx.x;
@@ -579,27 +588,32 @@ __global__ void __launch_bounds__(FS_TE) k_tc_finish_sk(FinArgs f) {
     float acc[FS_JB];
 #pragma unroll
     for (int t = 0; t < FS_JB; ++t) acc[t] = 0.f;
-    for (int s0 = s_lo; s0 < s_hi; s0 += FS_SC) {
-      const int sc = min(FS_SC, s_hi - s0);
-      // this element's slice values summed over q: every load of the chunk issued first
-      float z[FS_SC];
+    for (int s0 = s_lo; s0 < s_hi; s0 += SC) {
+      const int sc = min(SC, s_hi - s0);
+      // this element's slice values summed over q: every load of the chunk is issued
+      // into registers before the first addition
+      float raw[SC * NQ];
 #pragma unroll
-      for (int u = 0; u < FS_SC; ++u) {
-        float v = 0.f;
-        if (in && u < sc) {
-          const float* pe = Pp + ne * (int64_t)(s0 + u);
-          v = __ldcg(pe);
-          for (int q = 1; q < nq; ++q) v += __ldcg(pe + qstride * q);
-        }
+      for (int u = 0; u < SC; ++u) {
+        const float* pe = Pp + ne * (int64_t)(s0 + u);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) raw[u * NQ + q] = (in && u < sc && q < nq) ? __ldcg(pe + qstride * q) : 0.f;
+      }
+      float z[SC];
+#pragma unroll
+      for (int u = 0; u < SC; ++u) {
+        float v = raw[u * NQ];
+#pragma unroll
+        for (int q = 1; q < NQ; ++q) v += raw[u * NQ + q];
         z[u] = v;
       }
       if (write_z && j0 == 0 && in) {
 #pragma unroll
-        for (int u = 0; u < FS_SC; ++u)
+        for (int u = 0; u < SC; ++u)
           if (u < sc) f.Z1[e + ne * (int64_t)(s0 + u)] = z[u];
       }
       __syncthreads();
-      for (int idx = tid; idx < FS_SC * Jp; idx += blockDim.x) {
+      for (int idx = tid; idx < SC * Jp; idx += blockDim.x) {
         const int sl = idx / Jp, j = idx % Jp;
         float bv = 0.f;
         if (sl < sc && j < J) {
@@ -617,7 +631,7 @@ __global__ void __launch_bounds__(FS_TE) k_tc_finish_sk(FinArgs f) {
       }
       __syncthreads();
 #pragma unroll
-      for (int u = 0; u < FS_SC; ++u) {
+      for (int u = 0; u < SC; ++u) {
         const float* brow = fs_sm + u * Jp + j0;
 #pragma unroll
         for (int t4 = 0; t4 < FS_JB / 4; ++t4) {
@@ -719,6 +733,20 @@ __global__ void __launch_bounds__(256) k_tc_finish_b(const float* __restrict__ Z
   }
 }
 
+// Copies of V_{k+1} and V_k with the rows of mode 1 padded to N1p (a multiple of 4, the
+// 16-byte row stride TMA needs) by zeros: a[i + N1p c] = (i < N1 ? V[i + N1 c] : 0).
+__global__ void k_pad_rows(const float* __restrict__ Vn, const float* __restrict__ Vp, int N1, int N1p, int64_t ncol,
+                           float* __restrict__ an, float* __restrict__ ap) {
+  const int64_t tot = (int64_t)N1p * ncol;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t c = e / N1p;
+    const int i = (int)(e - c * N1p);
+    const bool in = i < N1;
+    an[e] = in ? __ldcs(&Vn[i + (int64_t)N1 * c]) : 0.f;
+    ap[e] = in ? __ldcs(&Vp[i + (int64_t)N1 * c]) : 0.f;
+  }
+}
+
 // Float copies of w_1 and w_2, zero-padded to whole 128-wide tiles (read by the converters).
 __global__ void k_weights_f(const double* w1, int N1, int L1, const double* w2, int N2, int L2, float* out) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < L1 + L2; i += gridDim.x * blockDim.x)
@@ -753,9 +781,10 @@ bool get_encoder(std::string& err) {
   return true;
 }
 
-bool encode_map(CUtensorMap* tm, const float* base, int N1, int N2, int nslice, std::string& err) {
-  cuuint64_t dims[3] = {(cuuint64_t)N1, (cuuint64_t)N2, (cuuint64_t)nslice};
-  cuuint64_t strides[2] = {(cuuint64_t)N1 * 4, (cuuint64_t)N1 * N2 * 4};
+// ld1: row pitch of mode 1 in elements (N1, or N1 rounded up to 4 for a padded copy)
+bool encode_map(CUtensorMap* tm, const float* base, int N1, int ld1, int N2, int nslice, std::string& err) {
+  cuuint64_t dims[3] = {(cuuint64_t)ld1, (cuuint64_t)N2, (cuuint64_t)nslice};
+  cuuint64_t strides[2] = {(cuuint64_t)ld1 * 4, (cuuint64_t)ld1 * N2 * 4};
   cuuint32_t box[3] = {SUB_I1, SUB_I2, 1};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = g_encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)base, dims, strides, box, estr,
@@ -772,6 +801,94 @@ int rpad_of(int r) { return r <= 16 ? 16 : 32; }
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// Launch-shape tuner.  The tile (128 x 128, eight 16-row strips) is fixed by the MMA
+// shape and the TMEM layout; what varies with the tensor's shape is the work split: how
+// many CTAs share a tile position in the persistent grid (all SMs for a large tensor;
+// fewer can win for a small one, whose per-CTA start-up then dominates), and how many
+// slice ranges the finishing contraction splits into.  On a plan's first call outside
+// stream capture every candidate is timed with CUDA events on the call's own inputs (one
+// warm-up and three timed launches) and the fastest kept; choices are cached per shape
+// and device for the process.
+// ---------------------------------------------------------------------------
+struct TuneKey {
+  int dev, N1, ld1, N2, nslice, r1pad, r2pad, J, p;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(dev, N1, ld1, N2, nslice, r1pad, r2pad, J, p) <
+           std::tie(o.dev, o.N1, o.ld1, o.N2, o.nslice, o.r1pad, o.r2pad, o.J, o.p);
+  }
+};
+struct TuneChoice {
+  int cstep, fin_target;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune_cache;
+
+bool tune_lookup(const TuneKey& k, TcPlan& plan) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune_cache.find(k);
+  if (it == g_tune_cache.end()) return false;
+  plan.cstep = it->second.cstep;
+  plan.fin_target = it->second.fin_target;
+  plan.ncand = 0;
+  plan.from_cache = true;
+  return true;
+}
+
+void tune_store(const TuneKey& k, const TcPlan& plan) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[k] = TuneChoice{plan.cstep, plan.fin_target};
+}
+
+template <typename FP, typename FF>
+void tune_shape(TcPlan& plan, int cmax, FP&& project, FF&& finish, cudaStream_t s) {
+  cudaEvent_t ea = nullptr, eb = nullptr;
+  cudaEventCreate(&ea);
+  cudaEventCreate(&eb);
+  auto time_us = [&](auto&& fn) {
+    fn();
+    cudaEventRecord(ea, s);
+    for (int i = 0; i < 3; ++i) fn();
+    cudaEventRecord(eb, s);
+    cudaEventSynchronize(eb);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ea, eb);
+    return ms * 1000.f / 3.f;
+  };
+  int cands[TcPlan::kMaxCand];
+  int nc = 0;
+  for (int c : {cmax, (3 * cmax + 3) / 4, (cmax + 1) / 2, (cmax + 3) / 4}) {
+    c = std::max(1, c);
+    bool dup = false;
+    for (int i = 0; i < nc; ++i) dup |= cands[i] == c;
+    if (!dup && nc < TcPlan::kMaxCand) cands[nc++] = c;
+  }
+  plan.ncand = nc;
+  int best = cmax;
+  float best_us = 1e30f;
+  for (int i = 0; i < nc; ++i) {
+    const float us = time_us([&] { project(cands[i]); });
+    plan.cand[i] = cands[i];
+    plan.cand_us[i] = us;
+    if (us < best_us) { best_us = us; best = cands[i]; }
+  }
+  plan.cstep = best;
+  project(best);                      // partials of the chosen shape for the finish candidates
+  int fbest = FS_CTAS;
+  float fbest_us = 1e30f;
+  const int targets[3] = {152, 2 * 152, 4 * 152};
+  for (int i = 0; i < 3; ++i) {
+    const float us = time_us([&] { finish(targets[i]); });
+    plan.fin_cand[i] = targets[i];
+    plan.fin_us[i] = us;
+    if (us < fbest_us) { fbest_us = us; fbest = targets[i]; }
+  }
+  plan.fin_target = fbest;
+  plan.from_cache = false;
+  cudaEventDestroy(ea);
+  cudaEventDestroy(eb);
+}
+
 tdb_status tc_selftest_mbar_wait(unsigned* flags, long long limit, cudaStream_t s) {
   k_selftest_mbar<<<1, 32, 0, s>>>(flags, limit);
   count_launch();
@@ -780,7 +897,6 @@ tdb_status tc_selftest_mbar_wait(unsigned* flags, long long limit, cudaStream_t 
 
 bool tc_supported(int p, const int64_t* N, const int* cap, std::string& err) {
   if (p < 2 || p > 4) { err = "needs 2..4 modes"; return false; }
-  if (N[0] % 4 != 0) { err = "N_1 must be a multiple of 4 (16-byte TMA row stride)"; return false; }
   if (cap[0] > 32 || cap[1] > 32) { err = "ranks of modes 1, 2 must be <= 32"; return false; }
   int dev = 0, major = 0, minor = 0;
   cudaGetDevice(&dev);
@@ -804,6 +920,11 @@ void tc_carve(TcPlan& plan, Carver& cv, int p, const int64_t* N, const int* cap)
   plan.z1p = cv.take<float>((size_t)nq1 * nslice * N[1] * cap[0]);
   plan.z2p = cv.take<float>((size_t)nq2 * nslice * N[0] * cap[1]);
   plan.wsl = cv.take<double>((size_t)nslice);
+  if (N[0] % 4 != 0) {
+    const size_t padn = (size_t)((N[0] + 3) & ~3) * N[1] * nslice;
+    plan.pad[0] = cv.take<float>(padn);
+    plan.pad[1] = cv.take<float>(padn);
+  }
   plan.w12f = cv.take<float>((size_t)(nq1 + nq2) * TILE);
   plan.npart = cv.take<double>(1024);
   // finish: split partials ((FS_CTAS + tiles) x 256 x J floats bound nsplit x tiles x 256 x J
@@ -817,7 +938,7 @@ void tc_carve(TcPlan& plan, Carver& cv, int p, const int64_t* N, const int* cap)
 tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, const int64_t* N, const int* r,
                       const void* const* A, const double* const* w, float* Z1, float* Z2, float* scratch,
                       float* dS, float* const* Y, double* dv2, unsigned* flags, cudaStream_t s, cudaEvent_t* evm,
-                      std::string& err, bool defer_ds) {
+                      std::string& err, bool defer_ds, float dscale) {
   if (!get_encoder(err)) return TDB_ERR_UNSUPPORTED;
   const int N1 = (int)N[0], N2 = (int)N[1];
   int nslice = 1;
@@ -833,8 +954,24 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
     count_launch();
     plan.wsl_ready = true;
   }
+  // rows of mode 1 whose byte length is not a multiple of 16: the kernel streams zero-padded
+  // copies of both snapshots instead (TMA's row stride rule)
+  const int ld1 = (N1 + 3) & ~3;
+  if (ld1 != N1) {
+    if (!plan.pad[0] || !plan.pad[1]) {
+      err = "no padded snapshot buffers (N_1 not a multiple of 4)";
+      return TDB_ERR_UNSUPPORTED;
+    }
+    const int64_t tot = (int64_t)ld1 * N2 * nslice;
+    k_pad_rows<<<(int)std::min<int64_t>((tot + 255) / 256, 152 * 16), 256, 0, s>>>(Vn, Vp, N1, ld1,
+                                                                                   (int64_t)N2 * nslice, plan.pad[0],
+                                                                                   plan.pad[1]);
+    count_launch();
+    Vn = plan.pad[0];
+    Vp = plan.pad[1];
+  }
   CUtensorMap tmn, tmp;
-  if (!encode_map(&tmn, Vn, N1, N2, nslice, err) || !encode_map(&tmp, Vp, N1, N2, nslice, err))
+  if (!encode_map(&tmn, Vn, N1, ld1, N2, nslice, err) || !encode_map(&tmp, Vp, N1, ld1, N2, nslice, err))
     return TDB_ERR_UNSUPPORTED;
   Params P;
   memset(&P, 0, sizeof(P));
@@ -852,9 +989,8 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   // persistent grid: for every tile position the same number of CTAs (at most one per SM
-  // in all), each walking a strided set of the slices
-  P.cstep = std::max(1, std::min(nslice, std::min(nsm, 1024) / P.nq12));
-  const int grid = P.nq12 * P.cstep;
+  // in all), each walking a strided set of the slices; how many is the tuner's choice
+  const int cmax = std::max(1, std::min(nslice, std::min(nsm, 1024) / P.nq12));
   P.b1_bytes = 2 * r1pad * 128;
   P.b2_bytes = 2 * r2pad * 128;
   const int fixed = smem_fixed_bytes(P.b1_bytes, P.b2_bytes);
@@ -872,31 +1008,31 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   P.wsl = plan.wsl;
   P.npart = plan.npart;
   P.flags = flags;
+  P.dscale = dscale;
   if (!plan.attr_set) {
     cudaFuncSetAttribute(k_tc_project, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     plan.attr_set = true;
   }
-  if (evm) cudaEventRecord(evm[0], s);
-  k_tc_project<<<grid, NUM_THREADS, smem, s>>>(tmn, tmp, P);
-  count_launch();
-  if (evm) cudaEventRecord(evm[1], s);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    err = std::string("k_tc_project launch: ") + cudaGetErrorString(e);
-    return TDB_ERR_CUDA;
-  }
+  auto launch_project = [&](int cstep) {
+    P.cstep = cstep;
+    k_tc_project<<<P.nq12 * cstep, NUM_THREADS, smem, s>>>(tmn, tmp, P);
+    count_launch();
+  };
   // finish: Y_1, Y_2 (and Z1) from the tile partials, the slices contracted with
   // B = A_3 (x A_4); then Y_3 (three modes) or W = Z1 x_2 A_2^T (four modes) per slice
   const int J = p == 2 ? 1 : (p == 3 ? r[2] : r[2] * r[3]);
   const int nt1 = (int)(((int64_t)r[0] * N2 + FS_TE - 1) / FS_TE);
   const int nt2 = (int)(((int64_t)N1 * r[1] + FS_TE - 1) / FS_TE);
-  int nsplit = (int)std::max<int64_t>(1, (FS_CTAS + nt1 + nt2 - 1) / (nt1 + nt2));
-  nsplit = std::min({nsplit, std::max(1, nslice / FS_SC), FS_SPLIT_MAX});
-  while (nsplit > 1 && (size_t)nsplit * (nt1 + nt2) * FS_TE * J > plan.fpart_cap) --nsplit;
   if (J > FS_JMAX) {
     err = "finish: r_3 r_4 above 128";
     return TDB_ERR_UNSUPPORTED;
   }
+  auto nsplit_for = [&](int target) {
+    int ns = (int)std::max<int64_t>(1, (target + nt1 + nt2 - 1) / (nt1 + nt2));
+    ns = std::min({ns, std::max(1, nslice / FS_SC), FS_SPLIT_MAX});
+    while (ns > 1 && (size_t)ns * (nt1 + nt2) * FS_TE * J > plan.fpart_cap) --ns;
+    return ns;
+  };
   FinArgs f;
   f.Z1p = plan.z1p;
   f.Z2p = plan.z2p;
@@ -918,20 +1054,56 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   f.Y2 = Y[1];
   f.Y1 = Y[0];
   f.part = plan.fpart;
-  f.nsplit = nsplit;
   f.nt1 = nt1;
   f.nt2 = nt2;
   f.npart = plan.npart;
-  f.nnp = grid;
   f.dv2 = dv2;
   const size_t fsm = sizeof(float) * FS_SC * ((J + 3) & ~3);
-  k_tc_finish_sk<<<(nt1 + nt2) * nsplit, FS_TE, fsm, s>>>(f);
-  count_launch();
-  if (nsplit > 1) {
-    const int64_t outs = (int64_t)(nt1 + nt2) * J * FS_TE;
-    k_tc_finish_red<<<(int)std::min<int64_t>((outs + 255) / 256, 152 * 16), 256, 0, s>>>(f);
+  const int nqm = std::max(nq1, nq2);
+  auto launch_finish = [&](int nsplit) {
+    f.nsplit = nsplit;
+    const dim3 fgrid((nt1 + nt2) * nsplit);
+    if (nqm <= 1) k_tc_finish_sk<1><<<fgrid, FS_TE, fsm, s>>>(f);
+    else if (nqm <= 2) k_tc_finish_sk<2><<<fgrid, FS_TE, fsm, s>>>(f);
+    else if (nqm <= 4) k_tc_finish_sk<4><<<fgrid, FS_TE, fsm, s>>>(f);
+    else k_tc_finish_sk<8><<<fgrid, FS_TE, fsm, s>>>(f);
     count_launch();
+    if (nsplit > 1) {
+      const int64_t outs = (int64_t)(nt1 + nt2) * J * FS_TE;
+      k_tc_finish_red<<<(int)std::min<int64_t>((outs + 255) / 256, 152 * 16), 256, 0, s>>>(f);
+      count_launch();
+    }
+  };
+  // launch shape: tuned once per plan on its first call outside stream capture (cached
+  // process-wide per shape); under capture before that, the full grid
+  if (!plan.tuned) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+      const TuneKey key{dev, N1, ld1, N2, nslice, r1pad, r2pad, J, p};
+      if (!tune_lookup(key, plan)) {
+        tune_shape(plan, cmax, launch_project, [&](int target) {
+          f.nnp = P.nq12 * plan.cstep;
+          launch_finish(nsplit_for(target));
+        }, s);
+        tune_store(key, plan);
+      }
+      plan.tuned = true;
+    } else {
+      cudaGetLastError();
+    }
   }
+  const int cstep = plan.tuned ? std::min(plan.cstep, cmax) : cmax;
+  const int grid = P.nq12 * cstep;
+  if (evm) cudaEventRecord(evm[0], s);
+  launch_project(cstep);
+  if (evm) cudaEventRecord(evm[1], s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    err = std::string("k_tc_project launch: ") + cudaGetErrorString(e);
+    return TDB_ERR_CUDA;
+  }
+  f.nnp = grid;
+  launch_finish(nsplit_for(plan.tuned ? plan.fin_target : FS_CTAS));
   if (p >= 3) {
     // Z1 summed over the mode-1 tiles: the partials themselves when there is one tile
     const float* z1 = nq1 > 1 ? Z1 : plan.z1p;
@@ -1010,6 +1182,7 @@ extern "C" tdb_status tdb_project_noalloc(int ndim, const int64_t* dims, const i
     if (N[n] < 1 || N[n] > 1024) return TDB_ERR_SHAPE;
     if (r[n] < 1 || r[n] > kMaxRank || r[n] > N[n] || !A[n] || !w[n] || !Y[n]) return TDB_ERR_RANK;
   }
+  if (N[0] % 4 != 0) return TDB_ERR_UNSUPPORTED;       // (no room for padded copies in the static scratch)
   if (!tc_supported(ndim, N, r, err)) return TDB_ERR_UNSUPPORTED;
   // sizes beyond the static scratch are refused before anything is launched
   TcPlan plan;

@@ -163,6 +163,7 @@ struct tdb_ctx {
 
   // host state
   const void* V_prev = nullptr;
+  const void* V_prev2 = nullptr;   // the snapshot before V_prev (central differences), or null
   bool ready = false;
   bool warm = false;
   int64_t step = 0, reinits = 0, exact_evals = 0;
@@ -399,7 +400,7 @@ tdb_status validate(const tdb_config* cfg, std::string& err) {
     err = "bad error_mode";
     return TDB_ERR_INVALID_ARG;
   }
-  if (cfg->integrator < TDB_EULER || cfg->integrator > TDB_HEUN) { err = "bad integrator"; return TDB_ERR_INVALID_ARG; }
+  if (cfg->integrator < TDB_EULER || cfg->integrator > TDB_RK2_CENTRAL) { err = "bad integrator"; return TDB_ERR_INVALID_ARG; }
   if (cfg->eps_th > 0 && !(cfg->gamma_th > 0 && cfg->gamma_th <= 100)) { err = "gamma_th must be in (0, 100]"; return TDB_ERR_INVALID_ARG; }
   for (int n = 0; n < cfg->ndim; ++n) {
     if (cfg->rank[n] < 0 || cfg->rank[n] > kMaxRank) { err = "rank outside 0..32"; return TDB_ERR_RANK; }
@@ -909,10 +910,12 @@ void prepare_step(tdb_ctx* ctx) {
 // exact-error kernels on every step, gated by the device word, so that the recorded
 // work does not depend on host decisions.
 // a3..a6 (and phase 7's refresh of G_n, G_n^{-1}, sigma^(n) unless skip_finish): the fused
-// cooperative update on the projections in ctx->dS / ctx->Y.  heun = Heun's second stage,
-// combining with the state of step k kept in Tbak / Ubak.
+// cooperative update on the projections in ctx->dS / ctx->Y.  combine: 0 = the increment on
+// the current state; with the state of step k kept in Tbak / Ubak, 1 = Heun's second stage
+// (the mean of y_k and the predicted state plus the increment), 2 = the midpoint scheme's
+// second stage (y_k plus the increment taken at the midpoint state).
 template <typename Tc>
-tdb_status fused_update(tdb_ctx* ctx, bool reorth, bool skip_finish, bool heun) {
+tdb_status fused_update(tdb_ctx* ctx, bool reorth, bool skip_finish, int combine) {
   const int p = ctx->p;
   UpdArgs a;
   memset(&a, 0, sizeof(a));
@@ -927,7 +930,7 @@ tdb_status fused_update(tdb_ctx* ctx, bool reorth, bool skip_finish, bool heun) 
     a.w[n] = ctx->w[n];
     a.A[n] = ctx->A[n];
     a.Uc[n] = ctx->Uc[n];
-    a.U0[n] = heun ? ctx->Ubak[n] : nullptr;
+    a.U0[n] = combine ? ctx->Ubak[n] : nullptr;
     ntiles += (ctx->N[n] + 31) / 32;
   }
   a.dS = ctx->dS;
@@ -935,7 +938,8 @@ tdb_status fused_update(tdb_ctx* ctx, bool reorth, bool skip_finish, bool heun) 
   a.dS_out = ctx->dS;
   a.T = ctx->T;
   a.T2 = ctx->T2;
-  a.T0 = heun ? ctx->Tbak : nullptr;
+  a.T0 = combine ? ctx->Tbak : nullptr;
+  a.combine = combine;
   a.Tcore = ctx->Tcore;
   a.G = ctx->G;
   a.Ginv = ctx->Ginv;
@@ -964,8 +968,9 @@ tdb_status fused_update(tdb_ctx* ctx, bool reorth, bool skip_finish, bool heun) 
   return TDB_OK;
 }
 
+// Vpp: the snapshot before Vp (central differences of TDB_RK2_CENTRAL), or null.
 template <typename Tc>
-tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths) {
+tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths, const Tc* Vpp = nullptr) {
   cudaStream_t s = ctx->stream;
   const int p = ctx->p;
   // exact error every step, or gated by the estimator: the G_n refresh (G_n, G_n^{-1},
@@ -981,14 +986,15 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
   if (ev) CK(cudaEventRecord(ev[0], s));
   int64_t Rprod = 1;
   for (int n = 0; n < p; ++n) Rprod *= ctx->r[n];
-  // a1 + a2: difference and projection onto the current bases
-  auto project = [&](cudaEvent_t* evm) -> tdb_status {
+  // a1 + a2: difference scale (Vn - Vfrom) and its projection onto the current bases
+  auto project = [&](cudaEvent_t* evm, const Tc* Vfrom, double scale) -> tdb_status {
     if (ctx->use_tc) {
-      TRY(tc_project(ctx->tc, (const float*)Vn, (const float*)Vp, ctx->p, ctx->N, ctx->r, (const void* const*)ctx->A,
-                     (const double* const*)ctx->w, (float*)ctx->ping, (float*)ctx->pong, (float*)ctx->dV,
-                     (float*)ctx->dS, (float* const*)ctx->Y, &ctx->rb_dev->dv2, ctx->flags, s, evm, ctx->err, true));
+      TRY(tc_project(ctx->tc, (const float*)Vn, (const float*)Vfrom, ctx->p, ctx->N, ctx->r,
+                     (const void* const*)ctx->A, (const double* const*)ctx->w, (float*)ctx->ping, (float*)ctx->pong,
+                     (float*)ctx->dV, (float*)ctx->dS, (float* const*)ctx->Y, &ctx->rb_dev->dv2, ctx->flags, s, evm,
+                     ctx->err, true, (float)scale));
     } else {
-      launch_diff<Tc>(Vn, Vp, (Tc*)ctx->dV, ctx->S, s);
+      launch_diff<Tc>(Vn, Vfrom, (Tc*)ctx->dV, ctx->S, s, (Tc)scale);
       launch_wnorm2<Tc>((const Tc*)ctx->dV, nullptr, weight_view(ctx), ctx->npart, ctx->nblk, &ctx->rb_dev->dv2,
                         ctx->flags, s);
       CHECK_LAUNCH();
@@ -996,21 +1002,27 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
     }
     return TDB_OK;
   };
-  const bool heun = ctx->cfg.integrator == TDB_HEUN;
-  if (heun) {
-    // Heun's first stage: keep y_k = (T, U_n), then the Euler increment at y_k gives the
-    // predicted state in place (no re-orthonormalisation; G_n, G_n^{-1} refreshed for it)
+  const int scheme = ctx->cfg.integrator;
+  if (scheme == TDB_HEUN || scheme == TDB_RK2_CENTRAL) {
+    // first stage: keep y_k = (T, U_n), then an Euler increment at y_k gives the
+    // intermediate state in place (no re-orthonormalisation; G_n, G_n^{-1} refreshed for
+    // it).  Heun: the whole step with Delta V (the predicted state).  Midpoint scheme:
+    // half a step with the central difference at t_k, (V_{k+1} - V_{k-1}) / 4, or
+    // (V_{k+1} - V_k) / 2 without V_{k-1}.
     CK(cudaMemcpyAsync(ctx->Tbak, ctx->T, sizeof(double) * Rprod, cudaMemcpyDeviceToDevice, s));
     for (int n = 0; n < p; ++n)
       CK(cudaMemcpyAsync(ctx->Ubak[n], ctx->U[n], sizeof(double) * ctx->N[n] * ctx->r[n], cudaMemcpyDeviceToDevice, s));
-    TRY(project(nullptr));
-    TRY(fused_update<Tc>(ctx, false, false, false));
+    if (scheme == TDB_HEUN) TRY(project(nullptr, Vp, 1.0));
+    else if (Vpp) TRY(project(nullptr, Vpp, 0.25));
+    else TRY(project(nullptr, Vp, 0.5));
+    TRY(fused_update<Tc>(ctx, false, false, 0));
   }
-  TRY(project(ev ? ev + 4 : nullptr));
+  TRY(project(ev ? ev + 4 : nullptr, Vp, 1.0));
   if (ev) CK(cudaEventRecord(ev[1], s));
-  // a3..a6 and the refresh of G_n, G_n^{-1}, sigma^(n): one cooperative launch (Heun's
-  // second stage: the increment at the predicted state, combined with y_k)
-  TRY(fused_update<Tc>(ctx, ctx->cfg.reorth != 0, split, heun));
+  // a3..a6 and the refresh of G_n, G_n^{-1}, sigma^(n): one cooperative launch (second
+  // stages: the increment at the intermediate state, combined with y_k)
+  TRY(fused_update<Tc>(ctx, ctx->cfg.reorth != 0, split,
+                       scheme == TDB_HEUN ? 1 : (scheme == TDB_RK2_CENTRAL ? 2 : 0)));
   if (ev) CK(cudaEventRecord(ev[2], s));
   // the estimator's gate decides the error evaluation only in TDB_ERRMODE_MLP; otherwise
   // its decision goes to a scratch word and the host's schedule stands
@@ -1108,6 +1120,7 @@ tdb_status finish_step(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
     if (exact) ctx->est.steps_since_exact = 0;
     if (n_re > 0) ctx->est.steps_since_reinit = 0;
   }
+  ctx->V_prev2 = ctx->cfg.integrator == TDB_RK2_CENTRAL ? ctx->V_prev : nullptr;
   ctx->V_prev = Vn;
   if (info) {
     memset(info, 0, sizeof(*info));
@@ -1141,7 +1154,7 @@ tdb_status finish_step(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
 template <typename Tc>
 tdb_status step_impl(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
   prepare_step(ctx);
-  TRY(enqueue_step<Tc>(ctx, Vn, (const Tc*)ctx->V_prev, false));
+  TRY(enqueue_step<Tc>(ctx, Vn, (const Tc*)ctx->V_prev, false, (const Tc*)ctx->V_prev2));
   CK(cudaStreamSynchronize(ctx->stream));
   TRY(readback_done(ctx));
   return finish_step<Tc>(ctx, Vn, info);
@@ -1255,6 +1268,10 @@ tdb_status slot_check(tdb_ctx* ctx, int parity) {
   if (!ctx->ready) { ctx->err = "push before init"; return TDB_ERR_STATE; }
   if (parity != 0 && parity != 1) { ctx->err = "slot parity must be 0 or 1"; return TDB_ERR_INVALID_ARG; }
   if (!ctx->slot[0] || !ctx->slot[1]) { ctx->err = "input slots not set (tdb_set_input_slots)"; return TDB_ERR_STATE; }
+  if (ctx->cfg.integrator == TDB_RK2_CENTRAL) {
+    ctx->err = "central differences need three snapshots; use tdb_push_snapshot";
+    return TDB_ERR_UNSUPPORTED;
+  }
   if (ctx->V_prev != ctx->slot[1 - parity]) {
     ctx->err = "the previous snapshot is not in the other slot";
     return TDB_ERR_STATE;
@@ -1397,6 +1414,7 @@ tdb_status tdb_init(tdb_ctx** out, const tdb_config* cfg, void* ws, size_t ws_by
     return st;
   }
   ctx->V_prev = V0;
+  ctx->V_prev2 = nullptr;
   ctx->ready = true;
   *out = ctx;
   return TDB_OK;
@@ -1438,6 +1456,7 @@ tdb_status tdb_init_from_factors(tdb_ctx** out, const tdb_config* cfg, void* ws,
     return st;
   }
   ctx->V_prev = V0;
+  ctx->V_prev2 = nullptr;
   ctx->ready = true;
   *out = ctx;
   return TDB_OK;
@@ -1474,7 +1493,10 @@ tdb_status tdb_adapt_rank(tdb_ctx* ctx, const void* V_now, int* ranks_out, doubl
   tdb_status st = ctx->f64 ? run(double()) : run(float());
   // the state now stands for V_now (re-initialised from it, or accepted against it):
   // the next push differences against V_now
-  if (st == TDB_OK || st == TDB_WARN_RANK_CAP) ctx->V_prev = V_now;
+  if (st == TDB_OK || st == TDB_WARN_RANK_CAP) {
+    ctx->V_prev = V_now;
+    ctx->V_prev2 = nullptr;
+  }
   if (ranks_out)
     for (int n = 0; n < ctx->p; ++n) ranks_out[n] = ctx->r[n];
   return st;
@@ -1497,6 +1519,7 @@ tdb_status tdb_reinit(tdb_ctx* ctx, const void* V_now) {
     ctx->history.clear();
     ctx->reinits += 1;
     ctx->V_prev = V_now;
+    ctx->V_prev2 = nullptr;
   }
   return st;
 }
@@ -1611,6 +1634,7 @@ tdb_status tdb_load_state(tdb_ctx* ctx, const void* buf, size_t bytes, const voi
   if (st != TDB_OK) return st;
   TRY(readback(ctx));
   ctx->V_prev = V_prev;
+  ctx->V_prev2 = nullptr;
   ctx->ready = true;
   return TDB_OK;
 }
@@ -1696,6 +1720,23 @@ tdb_status tdb_estimator_trace(tdb_ctx* ctx, float* X, float* t, int* n) {
   return TDB_OK;
 }
 
+tdb_status tdb_estimator_load_trace(tdb_ctx* ctx, const float* X, const float* t, int n, int append) {
+  if (!ctx || !X || !t || n < 1) return TDB_ERR_INVALID_ARG;
+  if (!append) {
+    ctx->hX.clear();
+    ctx->hT.clear();
+  }
+  ctx->hX.insert(ctx->hX.end(), X, X + (size_t)n * MLP_F);
+  ctx->hT.insert(ctx->hT.end(), t, t + n);
+  const int have = (int)ctx->hT.size();
+  if (have > ctx->tr_cap) {
+    const int drop = have - ctx->tr_cap;
+    ctx->hX.erase(ctx->hX.begin(), ctx->hX.begin() + (size_t)drop * MLP_F);
+    ctx->hT.erase(ctx->hT.begin(), ctx->hT.begin() + drop);
+  }
+  return TDB_OK;
+}
+
 tdb_status tdb_set_profiling(tdb_ctx* ctx, int enable) {
   if (!ctx) return TDB_ERR_INVALID_ARG;
   if (enable) {
@@ -1749,8 +1790,10 @@ tdb_status tdb_push_slot(tdb_ctx* ctx, int parity, tdb_step_info* info) {
 tdb_status tdb_batch_create(tdb_batch** out, tdb_ctx* const* members, int n, int nstreams, void* stream) {
   if (!out || !members || n < 1 || nstreams < 1) return TDB_ERR_INVALID_ARG;
   *out = nullptr;
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
     if (!members[i] || !members[i]->ready) return TDB_ERR_STATE;
+    if (members[i]->cfg.integrator == TDB_RK2_CENTRAL) return TDB_ERR_UNSUPPORTED;   // slots hold two snapshots
+  }
   tdb_batch* b = new (std::nothrow) tdb_batch();
   if (!b) return TDB_ERR_INVALID_ARG;
   b->m.assign(members, members + n);
@@ -1888,6 +1931,25 @@ tdb_status tdb_get_graph_counters(const tdb_ctx* ctx, const tdb_batch* b, int64_
 
 void tdb_batch_destroy(tdb_batch* b) { delete b; }
 
-const char* tdb_version(void) { return "tdb 0.2 sm_103a"; }
+tdb_status tdb_tc_tuning(const tdb_ctx* ctx, int* ctas, int* fin_target, int* ncand, int* cand, float* cand_us,
+                         int* fin_cand, float* fin_us) {
+  if (!ctx) return TDB_ERR_INVALID_ARG;
+  if (!ctx->use_tc || !ctx->tc.tuned) return TDB_ERR_STATE;
+  const TcPlan& t = ctx->tc;
+  if (ctas) *ctas = t.cstep;
+  if (fin_target) *fin_target = t.fin_target;
+  if (ncand) *ncand = t.ncand;
+  for (int i = 0; i < t.ncand; ++i) {
+    if (cand) cand[i] = t.cand[i];
+    if (cand_us) cand_us[i] = t.cand_us[i];
+  }
+  for (int i = 0; i < 3; ++i) {
+    if (fin_cand) fin_cand[i] = t.ncand ? t.fin_cand[i] : 0;
+    if (fin_us) fin_us[i] = t.ncand ? t.fin_us[i] : 0.f;
+  }
+  return TDB_OK;
+}
+
+const char* tdb_version(void) { return "tdb 0.3 sm_103a"; }
 
 }  // extern "C"

@@ -25,7 +25,7 @@ MAX_RANK = 32
 
 PRECISION = {"fp64": 0, "fp32": 1, "bf16": 2}
 ERROR_MODE = {"exact": 0, "every_k": 1, "mlp": 2, "none": 3}
-INTEGRATOR = {"euler": 0, "heun": 1}
+INTEGRATOR = {"euler": 0, "heun": 1, "rk2_central": 2}
 ACTIONS = {0: "none", 1: "reinit", 2: "increase", 3: "decrease", 4: "revert", 5: "cap"}
 
 TDB_OK = 0
@@ -79,7 +79,7 @@ EXPORTS = [
     "tdb_mlp_param_count", "tdb_mlp_forward", "tdb_mlp_loss_grad", "tdb_mlp_adam_step", "tdb_estimator_fit",
     "tdb_estimator_params", "tdb_estimator_trace", "tdb_set_input_slots", "tdb_push_slot",
     "tdb_batch_create", "tdb_batch_push", "tdb_batch_last_error", "tdb_batch_destroy", "tdb_get_graph_counters",
-    "tdb_selftest_recip", "tdb_selftest_timeout",
+    "tdb_selftest_recip", "tdb_selftest_timeout", "tdb_tc_tuning", "tdb_estimator_load_trace",
 ]
 
 
@@ -149,6 +149,11 @@ def load(path: str = LIB_PATH):
     lib.tdb_project_noalloc.argtypes = [C.c_int, C.POINTER(C.c_int64), C.POINTER(C.c_int), vp, vp,
                                         C.POINTER(vp), C.POINTER(vp), vp, C.POINTER(vp), vp, vp]
     lib.tdb_project_noalloc.restype = st
+    lib.tdb_estimator_load_trace.argtypes = [vp, vp, vp, C.c_int, C.c_int]
+    lib.tdb_estimator_load_trace.restype = st
+    lib.tdb_tc_tuning.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                  C.POINTER(C.c_int), C.POINTER(C.c_float), C.POINTER(C.c_int), C.POINTER(C.c_float)]
+    lib.tdb_tc_tuning.restype = st
     lib.tdb_selftest_recip.argtypes = [vp, vp, vp, C.c_int64, vp]
     lib.tdb_selftest_recip.restype = st
     lib.tdb_selftest_timeout.argtypes = [C.c_int, C.c_int64, vp, vp]
@@ -277,7 +282,7 @@ class TDB:
         info = tdb_step_info()
         st = self.lib.tdb_push_snapshot(self.ctx, C.c_void_p(V.data_ptr()), C.byref(info))
         self._check(st)
-        self._prev = V
+        self._prev2, self._prev = self._prev, V      # borrowed by the library until the next pushes
         return {
             "step": info.step, "eps": info.eps, "eps_exact": bool(info.eps_exact), "eps_step": info.eps_step,
             "gamma": list(info.gamma)[: self.p], "sigma_min": list(info.sigma_min)[: self.p],
@@ -378,6 +383,17 @@ class TDB:
         return {"steps": s.value, "reinits": r.value, "exact_evals": e.value, "graph_replays": g.value,
                 "graph_records": gr.value}
 
+    def tuning(self) -> dict:
+        """The tensor-core projection's launch shape (tdb_tc_tuning): CTAs per tile position,
+        the finish's split target, and the candidates the tuner timed (us per launch)."""
+        ctas, fin, nc = C.c_int(), C.c_int(), C.c_int()
+        cand, cus = (C.c_int * 4)(), (C.c_float * 4)()
+        fc, fus = (C.c_int * 3)(), (C.c_float * 3)()
+        self._check(self.lib.tdb_tc_tuning(self.ctx, C.byref(ctas), C.byref(fin), C.byref(nc), cand, cus, fc, fus))
+        return {"ctas_per_position": ctas.value, "finish_split_target": fin.value, "timed": nc.value > 0,
+                "candidates": {int(cand[i]): float(cus[i]) for i in range(nc.value)},
+                "finish_candidates": {int(fc[i]): float(fus[i]) for i in range(3) if nc.value > 0}}
+
     def save_state(self) -> bytes:
         n = C.c_size_t(0)
         self._check(self.lib.tdb_save_state(self.ctx, None, C.byref(n)))
@@ -412,6 +428,14 @@ class TDB:
         self._check(self.lib.tdb_estimator_trace(self.ctx, X.ctypes.data_as(C.c_void_p), t.ctypes.data_as(C.c_void_p),
                                                  C.byref(n)))
         return X, t
+
+    def estimator_load_trace(self, X: np.ndarray, t: np.ndarray, append: bool = False):
+        """Install training rows (n x 8 features, n targets) recorded elsewhere."""
+        X = np.ascontiguousarray(X, dtype=np.float32)
+        t = np.ascontiguousarray(t, dtype=np.float32)
+        self._check(self.lib.tdb_estimator_load_trace(self.ctx, X.ctypes.data_as(C.c_void_p),
+                                                      t.ctypes.data_as(C.c_void_p), int(t.size), int(append)))
+        return self
 
     def close(self):
         if self.ctx:

@@ -53,6 +53,8 @@ def test_workspace_bytes_and_validation(lib):
     heun, _ = tdb.make_config([512, 256, 12], [0, 0, 0], [16, 16, 12], eps_th=1e-4, integrator="heun")
     assert lib.tdb_workspace_bytes(C.byref(heun)) == n           # Heun reuses the step's buffers
     heun.integrator = 2
+    assert lib.tdb_workspace_bytes(C.byref(heun)) == n           # the midpoint scheme reuses them too
+    heun.integrator = 3
     assert lib.tdb_workspace_bytes(C.byref(heun)) == 0           # no such integrator
     # init with a null workspace fails cleanly with TDB_ERR_WORKSPACE, before any device work
     ctx = C.c_void_p()

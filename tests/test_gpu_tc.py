@@ -59,6 +59,7 @@ def abs_bound(dV, U, w, keep):
     ((256, 128, 512), (20, 20, 20)),     # the stochastic shape at rank 20: 1024 tiles, 8 stages
     ((256, 128, 320), (16, 16, 12)),     # 640 tiles, 16 stages
     ((192, 129, 192, 3), (30, 30, 30, 3)),  # the channel shape at its rank caps: 2304 tiles
+    ((101, 67, 9), (7, 6, 4)),           # N_1 not a multiple of 4: zero-padded copies of both snapshots
 ])
 def test_bf16_projection_within_rounding_bound(tdbmod, dims, ranks):
     rng = np.random.default_rng(200)
@@ -128,3 +129,36 @@ def test_bf16_dv_norm_matches(tdbmod):
     info = c.push(S.from_logical(V1, dtype=torch.float32, device="cuda"))
     ref = np.sqrt(O.weighted_norm2(V1 - V0, w))
     assert abs(info["dv_norm"] - ref) <= 1e-5 * ref
+
+
+@cuda
+def test_launch_shape_tuner(tdbmod):
+    """The projection's tuner times its candidate grids on the first step and keeps the
+    fastest; a second context of the same shape takes the choice from the process-wide
+    cache without timing; both produce the same projection (the shape changes only the
+    work split, not the arithmetic of an element beyond the order of the slice sums)."""
+    rng = np.random.default_rng(202)
+    dims, ranks = (128, 96, 300), (8, 6, 5)
+    w, U, T = case(rng, dims, ranks)
+    V0 = rng.standard_normal(dims).astype(np.float32).astype(np.float64)
+    V1 = (V0 + 1e-2 * rng.standard_normal(dims)).astype(np.float32).astype(np.float64)
+    g0 = S.from_logical(V0, dtype=torch.float32, device="cuda")
+    g1 = S.from_logical(V1, dtype=torch.float32, device="cuda")
+    out = []
+    for i in range(2):
+        c = tdbmod.TDB(dims, ranks, weights=w, precision="bf16", error_mode="none")
+        c.init_from_factors(T, U, g0)
+        c.push(g1)
+        t = c.tuning()
+        out.append((t, c.projection()))
+        c.close()
+    t0, t1 = out[0][0], out[1][0]
+    assert t0["timed"] and len(t0["candidates"]) >= 2
+    assert t0["ctas_per_position"] in t0["candidates"]
+    assert t0["ctas_per_position"] == min(t0["candidates"], key=t0["candidates"].get)
+    assert t0["finish_split_target"] in t0["finish_candidates"]
+    assert not t1["timed"] and t1["ctas_per_position"] == t0["ctas_per_position"]
+    dSo, Yo = O.project(V1 - V0, U, w)
+    B = abs_bound(V1 - V0, U, w, keep=-1)
+    for _, (dS, Y) in out:
+        assert np.all(np.abs(dS - dSo) <= 2.0 ** -7 * B + 1e-30)
