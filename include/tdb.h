@@ -48,7 +48,9 @@ extern "C" {
 typedef enum tdb_status {
   TDB_OK = 0,
   TDB_ERR_INVALID_ARG = 1,     /* null pointer, bad enum, bad threshold */
-  TDB_ERR_SHAPE = 2,           /* ndim outside 2..4, a mode size outside 1..1024, >= 2^31 elements */
+  TDB_ERR_SHAPE = 2,           /* ndim outside 2..4, >= 2^31 elements, or a mode of more than 1024
+                                  points that is neither the first nor the last, or whose other
+                                  modes hold more than 1024 points together */
   TDB_ERR_RANK = 3,            /* a rank outside 1..min(N_n, prod_{m!=n} r_m, TDB_MAX_RANK) */
   TDB_ERR_RANK_DEFICIENT = 4,  /* T_(n) T_(n)^T or U^T W U not positive definite */
   TDB_ERR_NONFINITE = 5,       /* NaN or Inf in a snapshot or in the state */
@@ -105,7 +107,13 @@ enum tdb_integrator {
 
 typedef struct tdb_config {
   int ndim;                         /* p, 2..TDB_MAX_MODES */
-  int64_t dims[TDB_MAX_MODES];      /* N_n, mode 1 fastest */
+  int64_t dims[TDB_MAX_MODES];      /* N_n, mode 1 fastest.  Modes of up to 1024 points; the
+                                       first or the last mode may be longer when the product
+                                       of the others is at most 1024 (a grouped spatial mode,
+                                       Sec. 3.2): its HOSVD then comes from the short side,
+                                       the Gram of the other modes' merged index, whose
+                                       eigenvalues are C_n's nonzero ones and whose
+                                       eigenvectors z map to C_n's as B z / sqrt(lambda). */
   int rank[TDB_MAX_MODES];          /* initial r_n; 0 = from gamma_th on the HOSVD spectrum */
   int rank_max[TDB_MAX_MODES];      /* cap on r_n (<= TDB_MAX_RANK); 0 = TDB_MAX_RANK */
   const double* weights[TDB_MAX_MODES]; /* host, length N_n: diagonal of W^(n) (Eq. 2.17);

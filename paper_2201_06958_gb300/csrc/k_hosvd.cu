@@ -500,4 +500,100 @@ void launch_scale_basis(const double* Q, const double* w, int64_t n, int r, doub
   k_scale_basis<<<blocks, 256, 0, s>>>(Q, w, n, r, U); count_launch();
 }
 
+// ---------------------------------------------------------------------------
+// A long first or last mode n (more points than the product M of the other modes) from
+// the short side: with B = W_n^{1/2} V_(n) W_{-n}^{1/2} (N_n x M), C_n = B B^T has the
+// nonzero eigenvalues of K = B^T B (M x M) and, for K z = lambda z, the unit eigenvector
+// B z / sqrt(lambda) - the left singular vectors of B.  So the HOSVD of such a mode needs
+// K, its leading eigenpairs and one product with B, never the N_n x N_n matrix.
+// Column q of B^T is the merged index of the other modes, whose weight is
+// w_q = prod_{m != n} w_m (i_m) with q = i_a + N_a (i_b + ...) over those modes in order.
+// ---------------------------------------------------------------------------
+__global__ void k_merge_weights(WeightView wv, int skip, int64_t M, double* __restrict__ wq) {
+  for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < M; c += (int64_t)gridDim.x * blockDim.x) {
+    int64_t idx = c;
+    double w = 1.0;
+    for (int m = 0; m < wv.p; ++m) {
+      if (m == skip) continue;
+      w *= wv.w[m][idx % wv.N[m]];
+      idx /= wv.N[m];
+    }
+    wq[c] = w;
+    wq[M + c] = sqrt(w);
+  }
+}
+void launch_merge_weights(const WeightView& wv, int skip, int64_t M, double* wq, cudaStream_t s) {
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((M + 255) / 256, 1024));
+  k_merge_weights<<<blocks, 256, 0, s>>>(wv, skip, M, wq); count_launch();
+}
+
+// Q[:, j] = B Z[:, j] / sqrt(lambda_j) in double.  Element (i, q) of B is
+// V[i + N_n q] (first mode) or V[q + M i] (last mode), times sqrt(w_n(i) w_q) when the
+// weights are given (sqw_q = sqrt(w_q)), else V is already weighted.
+template <typename Tv>
+__global__ void k_short_map(const Tv* __restrict__ V, int first, int64_t Nn, int64_t M, const double* __restrict__ wn,
+                            const double* __restrict__ sqw, const double* __restrict__ Z, const double* __restrict__ ev,
+                            int k, double* __restrict__ Q) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Nn; i += (int64_t)gridDim.x * blockDim.x) {
+    const double si = wn ? sqrt(wn[i]) : 1.0;
+    for (int j = 0; j < k; ++j) {
+      const double* z = Z + M * j;
+      double acc = 0.0;
+      for (int64_t q = 0; q < M; ++q) {
+        const double v = (double)V[first ? i + Nn * q : q + M * i];
+        acc = fma(sqw ? v * sqw[q] : v, z[q], acc);
+      }
+      const double lam = ev[j];
+      Q[i + Nn * j] = lam > 0.0 ? si * acc / sqrt(lam) : 0.0;
+    }
+  }
+}
+
+// Each column scaled to unit length, its entry of largest magnitude made positive (the
+// first such entry on ties), as for the eigenvectors of the direct route.
+__global__ void k_col_unit_sign(double* __restrict__ Q, int64_t n) {
+  __shared__ double red[32];
+  __shared__ double bv[32];
+  __shared__ long long bi[32];
+  __shared__ long long imax;
+  double* q = Q + n * blockIdx.x;
+  double nrm = 0.0, best = -1.0;
+  long long ib = 0x7fffffffffffffffll;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const double a = q[i];
+    nrm += a * a;
+    if (fabs(a) > best) { best = fabs(a); ib = i; }
+  }
+  nrm = block_sum(nrm, red);
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const long long oi = __shfl_xor_sync(0xffffffffu, ib, o);
+    if (ob > best || (ob == best && oi < ib)) { best = ob; ib = oi; }
+  }
+  if ((threadIdx.x & 31) == 0) { bv[threadIdx.x >> 5] = best; bi[threadIdx.x >> 5] = ib; }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b0 = bv[0];
+    long long i0 = bi[0];
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+      if (bv[w] > b0 || (bv[w] == b0 && bi[w] < i0)) { b0 = bv[w]; i0 = bi[w]; }
+    imax = i0;
+  }
+  __syncthreads();
+  const double sc = (q[imax] < 0.0 ? -1.0 : 1.0) / sqrt(nrm > 0.0 ? nrm : 1.0);
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) q[i] *= sc;
+}
+
+template <typename Tv>
+void launch_short_map(const Tv* V, int first, int64_t Nn, int64_t M, const double* wn, const double* sqw,
+                      const double* Z, const double* ev, int k, double* Q, cudaStream_t s) {
+  const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((Nn + 127) / 128, 1024));
+  k_short_map<Tv><<<blocks, 128, 0, s>>>(V, first, Nn, M, wn, sqw, Z, ev, k, Q); count_launch();
+  k_col_unit_sign<<<k, 256, 0, s>>>(Q, Nn); count_launch();
+}
+template void launch_short_map<float>(const float*, int, int64_t, int64_t, const double*, const double*,
+                                      const double*, const double*, int, double*, cudaStream_t);
+template void launch_short_map<double>(const double*, int, int64_t, int64_t, const double*, const double*,
+                                       const double*, const double*, int, double*, cudaStream_t);
+
 }  // namespace tdb

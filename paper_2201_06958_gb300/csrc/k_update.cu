@@ -37,6 +37,10 @@ constexpr int LD = kMaxRank;
 constexpr int UPD_THREADS = 1024;
 constexpr size_t kUpdSmem = 48 * 1024;   // largest phase: the Gram finish, 45.6 KB
 constexpr int GJ_THREADS = 256;          // threads 0..255 invert G_n by Gauss-Jordan
+// Modes with more row tiles than this (more than 1024 points) have their per-tile partial
+// sums of P_n and C_n reduced once by the whole grid (reduce_long) instead of by every
+// tile's CTA (P_n) or the mode's one CTA (C_n).
+constexpr int kTreeTiles = 32;
 
 // ---------------------------------------------------------------------------
 // Double reciprocal and reciprocal square root by Newton-Raphson iteration from a
@@ -693,9 +697,13 @@ __device__ void rows_u1(const UpdArgs& a, int n, int64_t i0, int tile, unsigned 
     const int e = threadIdx.x, ra = e % LD, rb = e / LD;
     Tc s = Tc(0);
     if (ra < r && rb < r) {
-      const Tc* src = part + (int64_t)n * a.ntile * LD * LD + e;
+      if (nt > kTreeTiles) {
+        s = __ldcg(&((const Tc*)a.red)[(int64_t)n * LD * LD + e]);
+      } else {
+        const Tc* src = part + (int64_t)n * a.ntile * LD * LD + e;
 #pragma unroll 8
-      for (int t = 0; t < nt; ++t) s += __ldcg(&src[(int64_t)t * LD * LD]);
+        for (int t = 0; t < nt; ++t) s += __ldcg(&src[(int64_t)t * LD * LD]);
+      }
     }
     Psh[e] = s;
   }
@@ -726,6 +734,33 @@ __device__ void rows_u1(const UpdArgs& a, int n, int64_t i0, int tile, unsigned 
   __syncthreads();
 }
 
+// Phases 1b / 2b, only for modes with more than kTreeTiles row tiles: the per-tile
+// partials of P_n (which = 0) or C_n (which = 1) summed by the whole grid, a warp per
+// entry, its lanes over every 32nd tile, then a butterfly of shuffles (the same order on
+// every run).  Results go to red[which][n], read by every tile of phase 2 (P_n) or by
+// the Cholesky-QR of phase 3 (C_n).
+template <typename Tc>
+__device__ void reduce_long(const UpdArgs& a, int which) {
+  const ModeDesc& d = a.d;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const Tc* part = (const Tc*)a.part + (int64_t)which * d.p * a.ntile * LD * LD;
+  Tc* red = (Tc*)a.red + (int64_t)which * kMaxModes * LD * LD;
+  for (int64_t task = gw; task < (int64_t)d.p * LD * LD; task += nw) {
+    const int n = (int)(task / (LD * LD)), e = (int)(task % (LD * LD));
+    const int nt = (int)((d.N[n] + 31) / 32);
+    const int r = d.r[n], ra = e % LD, rb = e / LD;
+    if (nt <= kTreeTiles || ra >= r || rb >= r) continue;     // the same for the whole warp
+    const Tc* src = part + (int64_t)n * a.ntile * LD * LD + e;
+    Tc s = Tc(0);
+    for (int t = lane; t < nt; t += 32) s += __ldcg(&src[(int64_t)t * LD * LD]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) red[(int64_t)n * LD * LD + e] = s;
+  }
+}
+
 // Phase 3 for mode n (one CTA): C_n from the partials, R (upper, C = R^T R) and R^{-1}.
 template <typename Tc>
 __device__ void mode_cholqr(const UpdArgs& a, int n, unsigned char* sm) {
@@ -748,9 +783,13 @@ __device__ void mode_cholqr(const UpdArgs& a, int n, unsigned char* sm) {
     for (int e = threadIdx.x; e < LD * LD; e += blockDim.x) {
       const int ra = e % LD, rb = e / LD;
       double s = 0.0;
-      if (ra < r && rb < r)
+      if (ra < r && rb < r) {
+        if (nt > kTreeTiles)
+          s = (double)__ldcg(&((const Tc*)a.red)[(int64_t)(kMaxModes + n) * LD * LD + e]);
+        else
 #pragma unroll 8
-        for (int t = 0; t < nt; ++t) s += (double)__ldcg(&part[(int64_t)t * LD * LD + e]);
+          for (int t = 0; t < nt; ++t) s += (double)__ldcg(&part[(int64_t)t * LD * LD + e]);
+      }
       C[e] = s;
     }
     __syncthreads();
@@ -771,9 +810,13 @@ __device__ void mode_cholqr(const UpdArgs& a, int n, unsigned char* sm) {
     for (int e = threadIdx.x; e < LD * LD; e += blockDim.x) {
       const int ra = e % LD, rb = e / LD;
       float s = 0.f;
-      if (ra < r && rb < r)
+      if (ra < r && rb < r) {
+        if (nt > kTreeTiles)
+          s = (float)__ldcg(&((const Tc*)a.red)[(int64_t)(kMaxModes + n) * LD * LD + e]);
+        else
 #pragma unroll 8
-        for (int t = 0; t < nt; ++t) s += (float)__ldcg(&part[(int64_t)t * LD * LD + e]);
+          for (int t = 0; t < nt; ++t) s += (float)__ldcg(&part[(int64_t)t * LD * LD + e]);
+      }
       Cf[e] = s;
     }
     __syncthreads();
@@ -970,6 +1013,8 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_update(UpdArgs a) {
     ntiles_total += (int)((d.N[n] + 31) / 32);
   }
   tile_base[p] = ntiles_total;
+  bool tree = false;
+  for (int n = 0; n < p; ++n) tree |= (d.N[n] + 31) / 32 > kTreeTiles;
   auto tile_of = [&](int task, int* n_out, int* t_out) {
     int n = 0;
     while (task >= tile_base[n + 1]) ++n;
@@ -1018,6 +1063,10 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_update(UpdArgs a) {
   }
   if (!grid_sync(a.bar, ++nbar, nb, a.flags, &abort_sh)) return;
   stamp(st_sh, a.stamps, ++nst);
+  if (tree) {
+    reduce_long<Tc>(a, 0);
+    if (!grid_sync(a.bar, ++nbar, nb, a.flags, &abort_sh)) return;
+  }
 
   // 2: P, U', partial C
   for (int task = blockIdx.x; task < ntiles_total; task += nb) {
@@ -1027,6 +1076,10 @@ __global__ void __launch_bounds__(UPD_THREADS, 1) k_update(UpdArgs a) {
   }
   if (!grid_sync(a.bar, ++nbar, nb, a.flags, &abort_sh)) return;
   stamp(st_sh, a.stamps, ++nst);
+  if (tree && a.reorth) {
+    reduce_long<Tc>(a, 1);
+    if (!grid_sync(a.bar, ++nbar, nb, a.flags, &abort_sh)) return;
+  }
 
   // 3: Cholesky-QR factors, one CTA per mode
   for (int n = blockIdx.x; n < p; n += nb) mode_cholqr<Tc>(a, n, smraw);

@@ -74,6 +74,7 @@ struct UpdArgs {
   double* sig2;                  // p x LD, descending (out)
   float* Vprev;                  // p x LD x LD, eigenvectors of G_n (Jacobi warm start; in and out)
   void* part;                    // 2 x p x ntile x LD x LD partial sums (Tc scratch)
+  void* red;                     // 2 x kMaxModes x LD x LD sums of the partials of modes over 1024 points (Tc)
   double* gpart;                 // p x gsplit x LD x LD Gram partials (scratch)
   int ntile, gsplit;
   int warm, reorth;
@@ -181,5 +182,9 @@ tdb_status eig_subspace(const T* Cc, const double* C64, int n, int k, int iters,
                         unsigned* flags, double* ev, double* Q, double* trace, double* scratch, cudaStream_t s,
                         const double* Q0 = nullptr);
 void launch_scale_basis(const double* Q, const double* w, int64_t n, int r, double* U, cudaStream_t s);
+void launch_merge_weights(const WeightView& wv, int skip, int64_t M, double* wq, cudaStream_t s);
+template <typename Tv>
+void launch_short_map(const Tv* V, int first, int64_t Nn, int64_t M, const double* wn, const double* sqw,
+                      const double* Z, const double* ev, int k, double* Q, cudaStream_t s);
 
 }  // namespace tdb

@@ -533,7 +533,7 @@ __global__ void k_selftest_mbar(unsigned* flags, long long limit) {
 // every output in split order (so results do not vary from run to run).
 constexpr int FS_TE = 256, FS_SC = 16, FS_JB = 32, FS_JMAX = 128, FS_SPLIT_MAX = 32;
 constexpr int FS_CTAS = 2 * 152;   // split target: about two CTAs per SM
-constexpr int FS_NQ_MAX = 1024 / 128;   // tiles along mode 1 or 2 (modes of at most 1024 points)
+constexpr int FS_NQ_MAX = 8;   // tiles along mode 1 or 2 loaded at once; more are added in order after them
 struct FinArgs {
   const float* Z1p;
   const float* Z2p;
@@ -551,7 +551,7 @@ struct FinArgs {
   double* dv2;
 };
 
-template <int NQ>   // tiles along the contracted mode, rounded up to a power of two (<= 8)
+template <int NQ>   // tiles along the contracted mode, rounded up to a power of two (<= FS_NQ_MAX)
 __global__ void __launch_bounds__(FS_TE) k_tc_finish_sk(FinArgs f) {
   constexpr int SC = NQ <= 2 ? FS_SC : (NQ == 4 ? FS_SC / 2 : FS_SC / 4);   // slices per chunk
   extern __shared__ __align__(16) float fs_sm[];    // B rows of a slice chunk: [FS_SC][Jp]
@@ -605,6 +605,11 @@ __global__ void __launch_bounds__(FS_TE) k_tc_finish_sk(FinArgs f) {
         float v = raw[u * NQ];
 #pragma unroll
         for (int q = 1; q < NQ; ++q) v += raw[u * NQ + q];
+        if (NQ == FS_NQ_MAX && nq > NQ && in && u < sc) {
+          // a long mode (more than FS_NQ_MAX tiles): the rest in tile order
+          const float* pe = Pp + ne * (int64_t)(s0 + u);
+          for (int q = NQ; q < nq; ++q) v += __ldcg(pe + qstride * q);
+        }
         z[u] = v;
       }
       if (write_z && j0 == 0 && in) {

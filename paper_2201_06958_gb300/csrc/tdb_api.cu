@@ -83,6 +83,7 @@ struct tdb_ctx {
   double* Gpart;
   int gsplit = 1;
   double* rowpart;
+  double* rowred;                 // grid-wide sums of the row partials of modes over 1024 points
   unsigned* bar;                  // grid-barrier words of the fused update
   unsigned* redcnt;               // last-CTA reduction counters (zero between launches)
   void* w1T;                      // w_1 in the compute type
@@ -119,6 +120,8 @@ struct tdb_ctx {
   double* Qeig[kMaxModes];
   double* trace;
   double* eigscratch;
+  double* Zs;                     // eigenvectors of the short-side Gram of a long mode (M x kcap)
+  double* wq;                     // merged weights of the other modes and their square roots (2 M)
   // BF16 tensor-core projection
   TcPlan tc;
   bool use_tc = false;
@@ -233,6 +236,12 @@ namespace {
     if (s_ != TDB_OK) return s_;          \
   } while (0)
 
+// A mode of more points than this (the first or the last, the others' product at most this)
+// takes its HOSVD from the short side: the Gram of the other modes' merged index.
+constexpr int64_t kDirectGramMax = 1024;
+bool short_side(const tdb_ctx* c, int n) { return c->N[n] > kDirectGramMax; }
+int64_t gram_dim(const tdb_ctx* c, int n) { return short_side(c, n) ? c->S / c->N[n] : c->N[n]; }
+
 int64_t prod_except(const int64_t* a, int p, int n) {
   int64_t v = 1;
   for (int m = 0; m < p; ++m)
@@ -289,8 +298,9 @@ void carve(tdb_ctx* c, Carver& cv) {
   const size_t tsz = c->f64 ? 8 : 4;
   int64_t Rprod = 1;
   for (int n = 0; n < p; ++n) Rprod *= c->cap[n];
-  int64_t Nmax = 0;
+  int64_t Nmax = 0, Ng = 0;   // longest mode; largest Gram the HOSVD forms
   for (int n = 0; n < p; ++n) Nmax = std::max<int64_t>(Nmax, c->N[n]);
+  for (int n = 0; n < p; ++n) Ng = std::max<int64_t>(Ng, gram_dim(c, n));
   for (int n = 0; n < p; ++n) {
     int64_t nr = c->N[n] * c->cap[n];
     c->w[n] = cv.take<double>(c->N[n]);
@@ -327,6 +337,7 @@ void carve(tdb_ctx* c, Carver& cv) {
   c->Gpart = cv.take<double>((size_t)p * c->gsplit * kMaxRank * kMaxRank);
   c->ntile = (int)((Nmax + 31) / 32);
   c->rowpart = cv.take<double>((size_t)2 * p * c->ntile * kMaxRank * kMaxRank);
+  c->rowred = cv.take<double>((size_t)2 * kMaxModes * kMaxRank * kMaxRank);
   c->bar = cv.take<unsigned>(2);
   c->redcnt = cv.take<unsigned>(8);
   c->w1T = cv.take<char>((size_t)c->N[0] * tsz);
@@ -342,36 +353,38 @@ void carve(tdb_ctx* c, Carver& cv) {
   c->rb_dev = cv.take<Readback>(1);
   c->est_dev = cv.take<EstState>(1);
   c->flags = &c->rb_dev->flags;
-  // HOSVD scratch
-  int64_t nn = (Nmax + 1) & ~1;
-  c->C64 = cv.take<double>(Nmax * Nmax);
-  c->Cc = cv.take<char>(Nmax * Nmax * tsz);
+  // HOSVD scratch (sized by the Gram dimension: N_n, or the short side of a long mode)
+  int64_t nn = (Ng + 1) & ~1;
+  c->C64 = cv.take<double>(Ng * Ng);
+  c->Cc = cv.take<char>(Ng * Ng * tsz);
   // eigensolver blocks: double in every compute type (float contexts refine in double)
   int64_t nsmall = std::min<int64_t>(nn, 96);
   c->jA = cv.take<double>(nsmall * nsmall);
   c->jV = cv.take<double>(nsmall * nsmall);
-  c->siQ = cv.take<double>(Nmax * 64);
-  c->siZ = cv.take<double>(Nmax * 64);
-  c->siX = cv.take<double>(Nmax * 64);
+  c->siQ = cv.take<double>(Ng * 64);
+  c->siZ = cv.take<double>(Ng * 64);
+  c->siX = cv.take<double>(Ng * 64);
   c->siG = cv.take<double>(64 * 64);
   c->siR = cv.take<double>(64 * 64);
   c->siH = cv.take<double>(64 * 64);
   c->siJA = cv.take<double>(64 * 64);
   c->siJV = cv.take<double>(64 * 64);
-  int ntile = (int)((Nmax + 31) / 32);
+  int ntile = (int)((Ng + 31) / 32);
   c->wpart_cap = std::max<size_t>((size_t)(ntile * (ntile + 1) / 2) * 8 * 1024, (size_t)152 * 64 * 64);
   c->wpart = cv.take<double>(c->wpart_cap);
-  c->eigf = c->f64 ? nullptr : cv.take<float>(eig_si_scratch_floats((int)Nmax));
+  c->eigf = c->f64 ? nullptr : cv.take<float>(eig_si_scratch_floats((int)Ng));
   for (int n = 0; n < p; ++n) c->wsf[n] = c->f64 ? nullptr : cv.take<float>(c->N[n]);
   for (int n = 0; n < p; ++n) {
-    c->kcap[n] = (int)std::min<int64_t>(c->N[n], c->cap[n] + 2);
+    c->kcap[n] = (int)std::min<int64_t>(gram_dim(c, n), c->cap[n] + 2);
     c->ev[n] = cv.take<double>(c->kcap[n]);
     c->Qeig[n] = cv.take<double>(c->N[n] * c->kcap[n]);
   }
   c->trace = cv.take<double>(p);
   int kmax = 0;
   for (int n = 0; n < p; ++n) kmax = std::max(kmax, c->kcap[n]);
-  c->eigscratch = cv.take<double>(64 + Nmax * (kmax + 2));
+  c->eigscratch = cv.take<double>(64 + Ng * (kmax + 2));
+  c->Zs = cv.take<double>(Ng * kmax);
+  c->wq = cv.take<double>(2 * Ng);
   c->mlpP = cv.take<float>(MLP_NPARAM);
   c->mlpNorm = cv.take<float>(2 * MLP_F + 2);
   c->mlpM = cv.take<float>(MLP_NPARAM);
@@ -388,12 +401,19 @@ void carve(tdb_ctx* c, Carver& cv) {
 tdb_status validate(const tdb_config* cfg, std::string& err) {
   if (!cfg) { err = "null config"; return TDB_ERR_INVALID_ARG; }
   if (cfg->ndim < 2 || cfg->ndim > kMaxModes) { err = "ndim must be 2..4"; return TDB_ERR_SHAPE; }
-  for (int n = 0; n < cfg->ndim; ++n)
-    if (cfg->dims[n] < 1 || cfg->dims[n] > 1024) { err = "mode sizes must be 1..1024"; return TDB_ERR_SHAPE; }
   {
     int64_t S = 1;
-    for (int n = 0; n < cfg->ndim; ++n) S *= cfg->dims[n];
-    if (S >= ((int64_t)1 << 31)) { err = "a snapshot must have fewer than 2^31 elements"; return TDB_ERR_SHAPE; }
+    for (int n = 0; n < cfg->ndim; ++n) {
+      if (cfg->dims[n] < 1 || cfg->dims[n] >= ((int64_t)1 << 31)) { err = "mode sizes must be positive"; return TDB_ERR_SHAPE; }
+      S *= cfg->dims[n];
+      if (S >= ((int64_t)1 << 31)) { err = "a snapshot must have fewer than 2^31 elements"; return TDB_ERR_SHAPE; }
+    }
+    for (int n = 0; n < cfg->ndim; ++n)
+      if (cfg->dims[n] > kDirectGramMax && ((n != 0 && n != cfg->ndim - 1) || S / cfg->dims[n] > kDirectGramMax)) {
+        err = "a mode of more than 1024 points must be the first or the last, and the other modes at most 1024 "
+              "points together";
+        return TDB_ERR_SHAPE;
+      }
   }
   if (cfg->precision < TDB_FP64 || cfg->precision > TDB_BF16_TTM) { err = "bad precision"; return TDB_ERR_INVALID_ARG; }
   if (cfg->error_mode < TDB_ERRMODE_EXACT || cfg->error_mode > TDB_ERRMODE_NONE) {
@@ -608,6 +628,70 @@ tdb_status readback(tdb_ctx* ctx) {
 // ---------------------------------------------------------------------------
 // HOSVD: per-mode spectrum (leading eigenpairs and trace), then the truncated state
 // ---------------------------------------------------------------------------
+// Spectrum and leading eigenvectors of C_n for a long first or last mode n from the short
+// side: K, the weighted Gram of the other modes' merged index (M x M, M = S / N_n), has the
+// nonzero eigenvalues of C_n, and its unit eigenvector z maps to C_n's as B z / sqrt(lambda)
+// (B the weighted unfolding; the thin SVD of B).  Float compute types read the weighted
+// data in ctx->rec and solve in double as for the direct route.
+template <typename Tc>
+tdb_status hosvd_short(tdb_ctx* ctx, const Tc* V, int n) {
+  cudaStream_t s = ctx->stream;
+  const int64_t Nn = ctx->N[n], M = ctx->S / Nn;
+  const int first = (n == 0) ? 1 : 0;
+  const int k = ctx->kcap[n], Mi = (int)M;
+  tdb_status st;
+  if (!ctx->f64) {
+    launch_gram_weighted((const float*)ctx->rec, first ? Nn : 1, M, first ? 1 : Nn, ctx->wpart, ctx->wpart_cap,
+                         ctx->C64, (float*)ctx->Cc, s);
+    CHECK_LAUNCH();
+    if (Mi <= 48) {
+      st = eig_leading_small<double>(ctx->C64, ctx->C64, Mi, k, (double*)ctx->jA, (double*)ctx->jV, ctx->flags,
+                                     ctx->ev[n], ctx->Zs, ctx->trace + n, ctx->eigscratch, s);
+    } else {
+      st = eig_si_float((const float*)ctx->Cc, ctx->C64, Mi, k, 24, ctx->eigf, ctx->bar, ctx->flags, ctx->ev[n],
+                        ctx->Zs, ctx->trace + n, s);
+      if (st == TDB_OK) {
+        SubspaceWs<double> ws{(double*)ctx->siQ, (double*)ctx->siZ, (double*)ctx->siX, ctx->siG, ctx->siR,
+                              (double*)ctx->siH, (double*)ctx->siJA, (double*)ctx->siJV};
+        st = eig_subspace<double>(ctx->C64, ctx->C64, Mi, k, 3, ws, ctx->flags, ctx->ev[n], ctx->Zs, ctx->trace + n,
+                                  ctx->eigscratch, s, ctx->Zs);
+      }
+    }
+    if (st != TDB_OK) { ctx->err = "eigensolver launch failed"; return st; }
+    launch_short_map<float>((const float*)ctx->rec, first, Nn, M, nullptr, nullptr, ctx->Zs, ctx->ev[n], k,
+                            ctx->Qeig[n], s);
+  } else {
+    launch_merge_weights(weight_view(ctx), n, M, ctx->wq, s);
+    // K as the mode Gram of a two-mode view: (N_n, M) for the first mode, (M, N_n) for the last
+    GramView g;
+    g.p = 2;
+    g.n = first;
+    for (int m = 0; m < kMaxModes; ++m) { g.N[m] = 1; g.w[m] = nullptr; }
+    g.N[first ? 0 : 1] = Nn;
+    g.w[first ? 0 : 1] = ctx->w[n];
+    g.N[first ? 1 : 0] = M;
+    g.w[first ? 1 : 0] = ctx->wq;
+    g.Nn = M;
+    g.L = first ? Nn : 1;
+    g.Q = first ? 1 : Nn;
+    launch_wgram<Tc>(V, g, ctx->wpart, ctx->wpart_cap, ctx->C64, ctx->Cc, 0, s);
+    CHECK_LAUNCH();
+    if (Mi <= 96) {
+      st = eig_leading_small<Tc>((const Tc*)ctx->Cc, ctx->C64, Mi, k, (Tc*)ctx->jA, (Tc*)ctx->jV, ctx->flags,
+                                 ctx->ev[n], ctx->Zs, ctx->trace + n, ctx->eigscratch, s);
+    } else {
+      SubspaceWs<Tc> ws{(Tc*)ctx->siQ, (Tc*)ctx->siZ, (Tc*)ctx->siX, ctx->siG, ctx->siR,
+                        (Tc*)ctx->siH, (Tc*)ctx->siJA, (Tc*)ctx->siJV};
+      st = eig_subspace<Tc>((const Tc*)ctx->Cc, ctx->C64, Mi, k, 24, ws, ctx->flags, ctx->ev[n], ctx->Zs,
+                            ctx->trace + n, ctx->eigscratch, s);
+    }
+    if (st != TDB_OK) { ctx->err = "eigensolver launch failed"; return st; }
+    launch_short_map<Tc>(V, first, Nn, M, ctx->w[n], ctx->wq + M, ctx->Zs, ctx->ev[n], k, ctx->Qeig[n], s);
+  }
+  CHECK_LAUNCH();
+  return TDB_OK;
+}
+
 template <typename Tc>
 tdb_status hosvd_spectrum(tdb_ctx* ctx, const Tc* V) {
   cudaStream_t s = ctx->stream;
@@ -617,6 +701,10 @@ tdb_status hosvd_spectrum(tdb_ctx* ctx, const Tc* V) {
     launch_weight_data((const float*)V, ctx->p, ctx->N, ctx->wsf, ctx->S, (float*)ctx->rec, s);
     CHECK_LAUNCH();
     for (int n = 0; n < ctx->p; ++n) {
+      if (short_side(ctx, n)) {
+        TRY(hosvd_short<Tc>(ctx, V, n));
+        continue;
+      }
       int64_t L = 1, Q = 1;
       for (int m = 0; m < n; ++m) L *= ctx->N[m];
       for (int m = n + 1; m < ctx->p; ++m) Q *= ctx->N[m];
@@ -650,6 +738,10 @@ tdb_status hosvd_spectrum(tdb_ctx* ctx, const Tc* V) {
     }
   } else
   for (int n = 0; n < ctx->p; ++n) {
+    if (short_side(ctx, n)) {
+      TRY(hosvd_short<Tc>(ctx, V, n));
+      continue;
+    }
     GramView g;
     g.p = ctx->p;
     g.n = n;
@@ -949,6 +1041,7 @@ tdb_status fused_update(tdb_ctx* ctx, bool reorth, bool skip_finish, int combine
   a.sig2 = ctx->sig2;
   a.Vprev = ctx->Vprev;
   a.part = ctx->rowpart;
+  a.red = ctx->rowred;
   a.ntile = ctx->ntile;
   a.gpart = ctx->Gpart;
   a.gsplit = gram_split(ctx->r, p, ctx->gsplit);

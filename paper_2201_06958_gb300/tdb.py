@@ -50,6 +50,13 @@ class tdb_config(C.Structure):
     ]
 
 
+class tdb_profile(C.Structure):
+    _fields_ = [("steps", C.c_int64), ("ms_project", C.c_double), ("ms_project_main", C.c_double),
+                ("ms_update", C.c_double), ("ms_error", C.c_double), ("ms_control", C.c_double),
+                ("launches_main", C.c_int64), ("update_phases", C.c_int64),
+                ("us_update_phase", C.c_double * 12)]
+
+
 class tdb_step_info(C.Structure):
     _fields_ = [
         ("step", C.c_int64),
@@ -374,6 +381,18 @@ class TDB:
         yptr = (C.POINTER(C.c_double) * self.p)(*[_dptr(y) for y in Ys])
         self._check(self.lib.tdb_get_projection(self.ctx, _dptr(dS), yptr))
         return dS.reshape(r, order="F"), [y.reshape(sh, order="F") for y, sh in zip(Ys, shapes)]
+
+    def set_profiling(self, enable: bool):
+        """Start (and zero) or stop the per-phase device timers (tdb_set_profiling)."""
+        self._check(self.lib.tdb_set_profiling(self.ctx, 1 if enable else 0))
+
+    def profile(self) -> dict:
+        """Accumulated device milliseconds per phase of tdb_push_snapshot (tdb_get_profile)."""
+        pr = tdb_profile()
+        self._check(self.lib.tdb_get_profile(self.ctx, C.byref(pr)))
+        return {"steps": pr.steps, "ms_project": pr.ms_project, "ms_project_main": pr.ms_project_main,
+                "ms_update": pr.ms_update, "ms_error": pr.ms_error, "ms_control": pr.ms_control,
+                "us_update_phase": [pr.us_update_phase[i] for i in range(pr.update_phases)]}
 
     def counters(self):
         s, r, e = C.c_int64(), C.c_int64(), C.c_int64()

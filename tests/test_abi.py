@@ -65,6 +65,21 @@ def test_workspace_bytes_and_validation(lib):
     assert st == 1
 
 
+def test_long_mode_shape_rules(lib):
+    """A mode of more than 1024 points is accepted as the first or the last mode when the
+    other modes hold at most 1024 points together (its HOSVD comes from the short side);
+    otherwise tdb_workspace_bytes refuses the shape (0).  The long mode's Gram is never
+    sized: the paper-size TDB-2 shape (19,076 x 23) needs far less than a 19,076^2 matrix."""
+    for dims in ([4, 2000, 4], [2000, 40, 40], [2000, 2000], [1025, 1025]):
+        cfg, _ = tdb.make_config(dims, [2] * len(dims), precision="fp64")
+        assert lib.tdb_workspace_bytes(C.byref(cfg)) == 0, dims
+    for dims in ([2000, 8, 4], [8, 4, 2000], [19076, 23], [1024, 1024]):
+        cfg, _ = tdb.make_config(dims, [2] * len(dims), precision="fp64")
+        assert lib.tdb_workspace_bytes(C.byref(cfg)) > 0, dims
+    cfg, _ = tdb.make_config([19076, 23], [0, 0], [23, 23], precision="fp64")
+    assert lib.tdb_workspace_bytes(C.byref(cfg)) < 19076 * 19076 * 8 // 10
+
+
 def test_struct_layout_matches_header():
     # offsets computed by the C compiler for include/tdb.h (x86-64 and aarch64 agree)
     assert C.sizeof(tdb.tdb_config) == 144
