@@ -454,8 +454,9 @@ def run_tdb(args, world, rank, local):
         return {"ms": ms, "host_s": t_host, "eps": eps, "prof": prof, "clocks": clocks, "launches": launches,
                 "counters": counters, "acts": acts}
 
-    # timed run: recorded steps, no instrumentation; then a shorter profiled run of the same
-    # stream (steps not recorded, CUDA events around each phase and the projection kernel)
+    # timed run: recorded steps, no instrumentation; then a profiled run of the same stream
+    # (CUDA events around each phase and the projection kernel, recorded into the step's graph
+    # as external event nodes)
     res = run(precision, timed_profile=False)
     resp = run(precision, timed_profile=True) if res is not None else None
     if res is None:
@@ -491,6 +492,10 @@ def run_tdb(args, world, rank, local):
                 "update_phase_us_per_step": [round(prof.us_update_phase[k] / max(prof.steps, 1), 2)
                                              for k in range(prof.update_phases)]}
     roofline["flops_per_launch"] = flops_fields(wl.dims, res["acts"], kernel_ms)
+    # where the kernel's CUDA events ran: inside the recorded step (external event-record
+    # nodes of the replayed graph, as in the timed run) or in eager steps
+    roofline["kernel_events_in"] = ("recorded step (graph replay)" if resp["counters"]["graph_replays"] > 0
+                                    else "eager steps")
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,

@@ -61,22 +61,23 @@ struct Params {
   int cstep;                     // CTAs per tile position
   int r1, r2, r1pad, r2pad;
   int b1_bytes, b2_bytes;        // the position's two K blocks of A_1 and A_2 (BF16 images)
-  float* Z1p;                    // [nq1][nslice][N2][r1]
-  float* Z2p;                    // [nq2][nslice][N1][r2]
+  float* Z1p;                    // [nq1][nslice][r1][N2]  (i2 fastest)
+  float* Z2p;                    // [nq2][nslice][r2][N1]  (i1 fastest)
   const float* A1;               // weighted bases A_1 = W_1 U_1 (N1 x r1) and A_2 (N2 x r2), FP32
   const float* A2;
   const float* w1f;             // float copies of w_1, w_2, zero-padded to whole tiles
   const float* w2f;
   const double* wsl;             // slice weights (product over modes >= 3)
-  double* npart;                 // per-CTA ||dV||_W^2
+  double* npart;                 // ||dV||_W^2 per converter warp: [CTA][NUM_CONV_WARPS]
   unsigned* flags;
-  float dscale;                  // dV = dscale (V_{k+1} - V_k) (1; 1/4 or 1/2 for a central difference)
+  float dscale;                  // dV = dscale (V_{k+1} - V_k) (1; 1/4 or 1/2 for a central difference): a
+                                 // power of two, applied to the accumulators and the norm (exact)
 };
 
 // Shared memory of the fused kernel: 1 KB alignment slack, two BF16 tiles, the two image
-// blocks, the epilogue staging, the stages, the barriers.
+// blocks, the stages, the barriers.
 __host__ __device__ constexpr int smem_fixed_bytes(int b1, int b2) {
-  return 1024 + 2 * BF_TILE_BYTES + ((b1 + 1023) & ~1023) + ((b2 + 1023) & ~1023) + NUM_EPI_WARPS * 32 * 33 * 4 + 512;
+  return 1024 + 2 * BF_TILE_BYTES + ((b1 + 1023) & ~1023) + ((b2 + 1023) & ~1023) + 512;
 }
 
 // ---------------------------------------------------------------------------
@@ -105,6 +106,20 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
   return ok != 0;
 }
 
+__device__ __forceinline__ bool mbar_test_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ void prefetch_tmap(const CUtensorMap* tm) {
+  asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)tm) : "memory");
+}
+
 // Bounded wait on a phase parity.  Returns false (and raises the abort flag) on
 // timeout or when another role already aborted.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* flags,
@@ -121,6 +136,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
       }
     }
   }
+}
+
+// The same wait for a whole warp: lane 0 polls, the outcome is broadcast (so the lanes
+// leave together even when the wait runs out), then every lane takes the completed phase
+// itself (it cannot move on before this warp's own next arrival).
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, volatile int* abort_flag,
+                                               unsigned* flags) {
+  int ok = 0;
+  if ((threadIdx.x & 31) == 0) ok = mbar_wait(bar, parity, abort_flag, flags) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (ok) mbar_try_wait(bar, parity);
+  return ok != 0;
 }
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int x, int y, int z, uint32_t bar) {
@@ -202,8 +229,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   unsigned char* bf_tiles = smem;                                          // 2 x 32 KB
   unsigned char* b1_smem = bf_tiles + 2 * BF_TILE_BYTES;                   // A_1 blocks of this position
   unsigned char* b2_smem = b1_smem + ((P.b1_bytes + 1023) & ~1023);        // A_2 blocks
-  float* epi_stage = (float*)(b2_smem + ((P.b2_bytes + 1023) & ~1023));   // 4 warps x 32 x 33 floats
-  unsigned char* stages = (unsigned char*)(epi_stage + NUM_EPI_WARPS * 32 * 33);   // 8 x 16 KB
+  unsigned char* stages = b2_smem + ((P.b2_bytes + 1023) & ~1023);        // 8 x 16 KB
   uint64_t* bars = (uint64_t*)(stages + NSTAGE * STAGE_BYTES);
   uint64_t* full = bars;                    // [NSTAGE]
   uint64_t* empty = bars + NSTAGE;          // [NSTAGE]
@@ -213,7 +239,6 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   uint64_t* bimg_full = epi_done + 2;       // the operand images are in place
   uint32_t* tmem_slot = (uint32_t*)(bimg_full + 1);
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
-  __shared__ double red[32];
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // this CTA's tile position and its first slice
@@ -221,7 +246,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   const int q1 = pos % P.nq1, q2 = pos / P.nq1;
   const int s_first = blockIdx.x / P.nq12;
 
-  if (tid == 0) {
+  // the TMA lane initialises the barriers and issues the first slice's strips at once (every
+  // stage is free); no other thread touches a barrier before the block-wide sync below
+  const bool tma_lane = (warp == TMA_WARP && lane == 0);
+  const int x_tile = q1 * TILE;
+  if (tma_lane) {
+    prefetch_tmap(&tmVn);
+    prefetch_tmap(&tmVp);
     for (int s = 0; s < NSTAGE; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
@@ -234,6 +265,19 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     mbar_init(smem_u32(bimg_full), NUM_EPI_WARPS);
     *abort_flag = 0;
     fence_mbar_init();
+    fence_proxy_async();
+    if (s_first < P.nslice) {
+#pragma unroll
+      for (int j = 0; j < NSTRIP; ++j) {
+        const int y = q2 * TILE + j * SUB_I2;
+        if (y >= P.N2) continue;
+        const uint32_t fb = smem_u32(&full[j]);
+        mbar_arrive_expect_tx(fb, STAGE_BYTES);
+        const uint32_t dst = smem_u32(stages + j * STAGE_BYTES);
+        tma_load_3d(dst, &tmVn, x_tile, y, s_first, fb);
+        tma_load_3d(dst + BOX_BYTES, &tmVp, x_tile, y, s_first, fb);
+      }
+    }
   }
   if (warp == MMA_WARP) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
@@ -251,31 +295,55 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   if (warp == TMA_WARP) {
     if (lane == 0) {
       // the strips of every slice: strip j goes to stage j (its converter's), once per
-      // slice; strips wholly past N2 are neither loaded nor waited for, on both sides
-      bool ok = true;
-      int t = 0;
-      const int x = q1 * TILE;
-      for (int sl = s_first; sl < P.nslice && ok; sl += P.cstep, ++t) {
+      // slice; strips wholly past N2 are neither loaded nor waited for, on both sides.
+      // Each stage is refilled as soon as its converter releases it, whatever the other
+      // stages do: the lane polls the empty barriers without blocking on any one of them.
+      const int nt = s_first < P.nslice ? (P.nslice - 1 - s_first) / P.cstep + 1 : 0;
+      int tj[NSTRIP];            // per stage: slices loaded so far (the first at the start)
+      int left = 0;
+#pragma unroll
+      for (int j = 0; j < NSTRIP; ++j) {
+        const bool in = q2 * TILE + j * SUB_I2 < P.N2;
+        tj[j] = in ? (nt > 0 ? 1 : 0) : nt;
+        left += nt - tj[j];
+      }
+      long long t0 = clock64();
+      int it = 0;
+      while (left > 0) {
+        bool moved = false;
 #pragma unroll
         for (int j = 0; j < NSTRIP; ++j) {
-          const int y = q2 * TILE + j * SUB_I2;
-          if (!ok || y >= P.N2) continue;
-          if (!mbar_wait(smem_u32(&empty[j]), (t & 1) ^ 1, abort_flag, P.flags)) { ok = false; continue; }
-          const uint32_t fb = smem_u32(&full[j]);
-          mbar_arrive_expect_tx(fb, STAGE_BYTES);
-          const uint32_t dst = smem_u32(stages + j * STAGE_BYTES);
-          tma_load_3d(dst, &tmVn, x, y, sl, fb);
-          tma_load_3d(dst + BOX_BYTES, &tmVp, x, y, sl, fb);
+          if (tj[j] < nt && mbar_test_wait(smem_u32(&empty[j]), (tj[j] & 1) ^ 1)) {
+            const uint32_t fb = smem_u32(&full[j]);
+            mbar_arrive_expect_tx(fb, STAGE_BYTES);
+            const uint32_t dst = smem_u32(stages + j * STAGE_BYTES);
+            const int y = q2 * TILE + j * SUB_I2, sl = s_first + tj[j] * P.cstep;
+            tma_load_3d(dst, &tmVn, x_tile, y, sl, fb);
+            tma_load_3d(dst + BOX_BYTES, &tmVp, x_tile, y, sl, fb);
+            ++tj[j];
+            --left;
+            moved = true;
+          }
+        }
+        if (moved) {
+          t0 = clock64();
+          continue;
+        }
+        if ((++it & 63) == 63) {
+          if (*abort_flag) break;
+          if (clock64() - t0 > TIMEOUT_CYCLES) {
+            *abort_flag = 1;
+            atomicOr(P.flags, kFlagTimeout);
+            break;
+          }
         }
       }
       // drain: every armed copy has landed before the CTA may leave
-      if (t > 0) {
 #pragma unroll
-        for (int j = 0; j < NSTRIP; ++j) {
-          if (q2 * TILE + j * SUB_I2 >= P.N2) continue;
-          long long t0 = clock64();
-          while (!mbar_try_wait(smem_u32(&full[j]), (t - 1) & 1) && clock64() - t0 < TIMEOUT_CYCLES) {
-          }
+      for (int j = 0; j < NSTRIP; ++j) {
+        if (q2 * TILE + j * SUB_I2 >= P.N2 || tj[j] == 0) continue;
+        long long t1 = clock64();
+        while (!mbar_try_wait(smem_u32(&full[j]), (tj[j] - 1) & 1) && clock64() - t1 < TIMEOUT_CYCLES) {
         }
       }
     }
@@ -369,46 +437,33 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     int t = 0;
     for (int sl = s_first; sl < P.nslice; sl += P.cstep, ++t) {
       const int buf = t & 1;
-      if (!mbar_wait(smem_u32(&mma_done[buf]), (t >> 1) & 1, abort_flag, P.flags)) break;
+      if (!mbar_wait_warp(smem_u32(&mma_done[buf]), (t >> 1) & 1, abort_flag, P.flags)) break;
       tc_fence_after();
       const uint32_t lane_base = (uint32_t)(32 * warp) << 16;
-      float* es = epi_stage + warp * 32 * 33;       // this warp's 32 rows, padded to 33
       float v[32];
-      // Z1 partial, rows i2 = q2*128 + 32*warp + lane: the warp's 32 rows x r1 values are one
-      // contiguous block of Z1p, written through shared memory with consecutive lanes on
-      // consecutive addresses
+      // Z1 partial, row i2 = q2*128 + 32*warp + lane: column a of the slice's block is
+      // contiguous in i2, so each store of the warp covers 32 consecutive floats
       tmem_ld16(tmem_base + lane_base + buf * 64, v);
       if (P.r1pad > 16) tmem_ld16(tmem_base + lane_base + buf * 64 + 16, v + 16);
-#pragma unroll
-      for (int a = 0; a < 32; ++a) es[lane * 33 + a] = v[a];
-      __syncwarp();
       {
-        const int row0 = q2 * TILE + 32 * warp;
-        const int nrow = min(32, P.N2 - row0);
-        float* dst = P.Z1p + (((size_t)q1 * P.nslice + sl) * P.N2 + row0) * P.r1;
-        int rw = lane / P.r1, col = lane % P.r1;
-        for (int e = lane; e < nrow * P.r1; e += 32) {
-          dst[e] = es[rw * 33 + col];
-          col += 32;
-          while (col >= P.r1) { col -= P.r1; ++rw; }
+        const int i2 = q2 * TILE + 32 * warp + lane;
+        if (i2 < P.N2) {
+          float* dst = P.Z1p + ((size_t)q1 * P.nslice + sl) * (size_t)P.r1 * P.N2 + i2;
+#pragma unroll
+          for (int a = 0; a < 32; ++a)
+            if (a < P.r1) dst[(size_t)a * P.N2] = v[a] * P.dscale;
         }
       }
-      __syncwarp();
-      // Z2 partial, rows i1 = q1*128 + 32*warp + lane
+      // Z2 partial, row i1 = q1*128 + 32*warp + lane
       tmem_ld16(tmem_base + lane_base + buf * 64 + 32, v);
       if (P.r2pad > 16) tmem_ld16(tmem_base + lane_base + buf * 64 + 48, v + 16);
-#pragma unroll
-      for (int a = 0; a < 32; ++a) es[lane * 33 + a] = v[a];
-      __syncwarp();
       {
-        const int row0 = q1 * TILE + 32 * warp;
-        const int nrow = min(32, P.N1 - row0);
-        float* dst = P.Z2p + (((size_t)q2 * P.nslice + sl) * P.N1 + row0) * P.r2;
-        int rw = lane / P.r2, col = lane % P.r2;
-        for (int e = lane; e < nrow * P.r2; e += 32) {
-          dst[e] = es[rw * 33 + col];
-          col += 32;
-          while (col >= P.r2) { col -= P.r2; ++rw; }
+        const int i1 = q1 * TILE + 32 * warp + lane;
+        if (i1 < P.N1) {
+          float* dst = P.Z2p + ((size_t)q2 * P.nslice + sl) * (size_t)P.r2 * P.N1 + i1;
+#pragma unroll
+          for (int b = 0; b < 32; ++b)
+            if (b < P.r2) dst[(size_t)b * P.N1] = v[b] * P.dscale;
         }
       }
       tc_fence_before();
@@ -438,10 +493,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     bool ok = true;
     for (int sl = s_first; sl < P.nslice && ok; sl += P.cstep, ++t) {
       const int buf = t & 1;
-      if (t >= 2 && !mbar_wait(smem_u32(&mma_done[buf]), ((t >> 1) - 1) & 1, abort_flag, P.flags)) break;
+      if (t >= 2 && !mbar_wait_warp(smem_u32(&mma_done[buf]), ((t >> 1) - 1) & 1, abort_flag, P.flags)) break;
       const double wsl = __ldg(&P.wsl[sl]);
       float acc = 0.f;
-      const bool have = strip_in && mbar_wait(smem_u32(&full[c]), t & 1, abort_flag, P.flags);
+      const bool have = strip_in && mbar_wait_warp(smem_u32(&full[c]), t & 1, abort_flag, P.flags);
       if (strip_in && !have) { ok = false; break; }
       const float4* vn = (const float4*)(stages + c * STAGE_BYTES);
       const float4* vp = (const float4*)(stages + c * STAGE_BYTES + BOX_BYTES);
@@ -462,8 +517,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const int row = ry + 2 * k;                 // 0..15 within the strip
           const float4 a = vn[row * 32 + h * 16 + cx];
           const float4 b = vp[row * 32 + h * 16 + cx];
-          const float d0 = (a.x - b.x) * P.dscale, d1 = (a.y - b.y) * P.dscale;
-          const float d2 = (a.z - b.z) * P.dscale, d3 = (a.w - b.w) * P.dscale;
+          const float d0 = a.x - b.x, d1 = a.y - b.y;
+          const float d2 = a.z - b.z, d3 = a.w - b.w;
           const int r = c * SUB_I2 + row;             // tile row (i2 within the tile)
           acc += w2v[k] * (w1v[h][0] * d0 * d0 + w1v[h][1] * d1 * d1 + w1v[h][2] * d2 * d2 + w1v[h][3] * d3 * d3);
           uint2 pk = make_uint2(pack_bf16x2(d0, d1), pack_bf16x2(d2, d3));
@@ -479,22 +534,15 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&bf_full[buf]));
     }
+    // this warp's share of ||dV||_W^2, written as soon as its strips are done (the finishing
+    // launch adds the partials); dV carries the factor dscale, a power of two (exact)
+    const double s = warp_sum(acc_norm);
+    if (lane == 0) P.npart[(size_t)blockIdx.x * NUM_CONV_WARPS + c] = s * ((double)P.dscale * (double)P.dscale);
   }
 
-  // ||dV||_W^2 partial of this CTA (converter threads contribute, others add 0)
+  // TMEM is released once every role is done with it
   tc_fence_before();
   __syncthreads();
-  {
-    double s = acc_norm;
-    s = warp_sum(s);
-    if (lane == 0) red[warp] = s;
-    __syncthreads();
-    if (tid == 0) {
-      double tot = 0.0;
-      for (int w = 0; w < NUM_WARPS; ++w) tot += red[w];
-      P.npart[blockIdx.x] = tot;
-    }
-  }
   if (warp == MMA_WARP) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
@@ -517,11 +565,11 @@ __global__ void k_selftest_mbar(unsigned* flags, long long limit) {
 }
 
 // Finish, first launch.  The fused kernel leaves partial first contractions over the
-// tiles q of the contracted mode: Z1p at e + n1 (s + S q), e = a + r1 i2, n1 = r1 N2
-// (mode 1 contracted), and Z2p at f + n2 (s + S q), f = b + r2 i1, n2 = N1 r2 (mode 2
+// tiles q of the contracted mode: Z1p at e + n1 (s + S q), e = i2 + N2 a, n1 = r1 N2
+// (mode 1 contracted), and Z2p at f + n2 (s + S q), f = i1 + N1 b, n2 = N1 r2 (mode 2
 // contracted), s the slice (i3 + N3 i4).  This launch sums them over q and contracts the
 // slices with B (S x J):
-//   Y_2[e + n1 j] = sum_s Z1[e, s] B[s, j],    Y_1[i1 + N1 (b + r2 j)] = sum_s Z2[f, s] B[s, j],
+//   Y_2[a + r1 (i2 + N2 j)] = sum_s Z1[e, s] B[s, j],    Y_1[f + n2 j] = sum_s Z2[f, s] B[s, j],
 // with B = A_3 (three modes), B[i3 + N3 i4, c + r3 d] = A_3[i3, c] A_4[i4, d] (four modes,
 // the Kronecker product that contracts modes 3 and 4 at once) or the 1 x 1 identity (two
 // modes).  It also writes Z1 = sum_q Z1p when there is more than one tile along mode 1
@@ -541,7 +589,7 @@ struct FinArgs {
   const float* A3;       // N3 x r3 (null: two modes, B = [1])
   const float* A4;       // N4 x r4 (null: three modes)
   int N3, r3, N4, r4, J;
-  float* Z1;             // r1 x N2 x S (written when nq1 > 1)
+  float* Z1;             // N2 x r1 x S, i2 fastest (written when nq1 > 1)
   float* Y2;
   float* Y1;
   float* part;           // [tile][split][J][256]
@@ -577,10 +625,10 @@ __global__ void __launch_bounds__(FS_TE) k_tc_finish_sk(FinArgs f) {
   float* mine = f.part + ((int64_t)tile * f.nsplit + sp) * (int64_t)J * FS_TE;
   auto store = [&](int64_t ee, int j, float v) {
     if (first) {
-      f.Y2[ee + ne * (int64_t)j] = v;
+      const int64_t a = ee / f.N2, i2 = ee - a * f.N2;
+      f.Y2[a + (int64_t)f.r1 * i2 + ne * (int64_t)j] = v;
     } else {
-      const int64_t b = ee % f.r2, i1 = ee / f.r2;
-      f.Y1[i1 + (int64_t)f.N1 * (b + (int64_t)f.r2 * j)] = v;
+      f.Y1[ee + ne * (int64_t)j] = v;
     }
   };
   for (int j0 = 0; j0 < J; j0 += FS_JB) {
@@ -686,10 +734,10 @@ __global__ void __launch_bounds__(256) k_tc_finish_red(FinArgs f) {
 #pragma unroll
     for (int q = 0; q < FS_SPLIT_MAX; ++q) v += vals[q];
     if (first) {
-      f.Y2[e + ne * (int64_t)j] = v;
+      const int64_t a = e / f.N2, i2 = e - a * f.N2;
+      f.Y2[a + (int64_t)f.r1 * i2 + ne * (int64_t)j] = v;
     } else {
-      const int64_t b = e % f.r2, i1 = e / f.r2;
-      f.Y1[i1 + (int64_t)f.N1 * (b + (int64_t)f.r2 * j)] = v;
+      f.Y1[e + ne * (int64_t)j] = v;
     }
   }
 }
@@ -703,7 +751,7 @@ constexpr size_t kFinishBSmem = (size_t)(32 * FB_CH + 32 * (FB_CH + 1)) * sizeof
 __global__ void __launch_bounds__(256) k_tc_finish_b(const float* __restrict__ Z1, int N2, int S, int r1, int r2,
                                                      const float* __restrict__ A2, float* __restrict__ Y3) {
   extern __shared__ float fb_sm[];
-  float* zs = fb_sm;                   // r1 x FB_CH (element a + r1 il)
+  float* zs = fb_sm;                   // r1 x FB_CH (element a + r1 il), from Z1 at i2 + N2 a + r1 N2 s
   float* as = zs + 32 * FB_CH;         // FB_CH x r2 (ld FB_CH + 1)
   const int tid = threadIdx.x;
   const int64_t n1 = (int64_t)r1 * N2;
@@ -711,9 +759,12 @@ __global__ void __launch_bounds__(256) k_tc_finish_b(const float* __restrict__ Z
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
     for (int i0 = 0; i0 < N2; i0 += FB_CH) {
       const int ch = min(FB_CH, N2 - i0);
-      const float* src = Z1 + (int64_t)r1 * i0 + n1 * sl;
+      const float* src = Z1 + i0 + n1 * sl;
 #pragma unroll 4
-      for (int e = tid; e < r1 * ch; e += 256) zs[e] = __ldcg(&src[e]);
+      for (int e = tid; e < r1 * ch; e += 256) {
+        const int il = e % ch, a = e / ch;
+        zs[a + r1 * il] = __ldcg(&src[il + (int64_t)N2 * a]);
+      }
 #pragma unroll 4
       for (int e = tid; e < ch * r2; e += 256) {
         const int il = e % ch, b = e / ch;
@@ -931,7 +982,7 @@ void tc_carve(TcPlan& plan, Carver& cv, int p, const int64_t* N, const int* cap)
     plan.pad[1] = cv.take<float>(padn);
   }
   plan.w12f = cv.take<float>((size_t)(nq1 + nq2) * TILE);
-  plan.npart = cv.take<double>(1024);
+  plan.npart = cv.take<double>((size_t)1024 * NUM_CONV_WARPS);
   // finish: split partials ((FS_CTAS + tiles) x 256 x J floats bound nsplit x tiles x 256 x J
   // for the split count the launch picks)
   const int jmax = p == 2 ? 1 : (p == 3 ? cap[2] : cap[2] * cap[3]);
@@ -1087,7 +1138,7 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
       const TuneKey key{dev, N1, ld1, N2, nslice, r1pad, r2pad, J, p};
       if (!tune_lookup(key, plan)) {
         tune_shape(plan, cmax, launch_project, [&](int target) {
-          f.nnp = P.nq12 * plan.cstep;
+          f.nnp = P.nq12 * plan.cstep * NUM_CONV_WARPS;
           launch_finish(nsplit_for(target));
         }, s);
         tune_store(key, plan);
@@ -1099,15 +1150,15 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   }
   const int cstep = plan.tuned ? std::min(plan.cstep, cmax) : cmax;
   const int grid = P.nq12 * cstep;
-  if (evm) cudaEventRecord(evm[0], s);
+  if (evm) cudaEventRecordWithFlags(evm[0], s, cudaEventRecordExternal);
   launch_project(cstep);
-  if (evm) cudaEventRecord(evm[1], s);
+  if (evm) cudaEventRecordWithFlags(evm[1], s, cudaEventRecordExternal);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     err = std::string("k_tc_project launch: ") + cudaGetErrorString(e);
     return TDB_ERR_CUDA;
   }
-  f.nnp = grid;
+  f.nnp = grid * NUM_CONV_WARPS;
   launch_finish(nsplit_for(plan.tuned ? plan.fin_target : FS_CTAS));
   if (p >= 3) {
     // Z1 summed over the mode-1 tiles: the partials themselves when there is one tile

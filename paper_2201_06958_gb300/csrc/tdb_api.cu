@@ -162,6 +162,8 @@ struct tdb_ctx {
   cudaStream_t aux = nullptr;        // second branch of a step (G_n refresh beside the exact error)
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool graph_broken = false;
+  bool prof_graph_ok = true;      // profiled steps may be recorded (their events time in a graph)
+  bool last_graphed = false;      // the step being finished ran as a graph replay
   int64_t graph_replays = 0, graph_records = 0;
 
   // host state
@@ -489,9 +491,9 @@ tdb_status project_tree(tdb_ctx* ctx, const Tc* dV, cudaEvent_t* evm) {
   Tc* pong = (Tc*)ctx->pong;
   // Z1 = dV x_1 A_1^T, then each Y_n (n >= 2) contracts the remaining modes but n
   for (int m = 0; m < p; ++m) dims[m] = ctx->N[m];
-  if (evm) cudaEventRecord(evm[0], s);
+  if (evm) cudaEventRecordWithFlags(evm[0], s, cudaEventRecordExternal);
   mp(dV, ping, 0, dims);
-  if (evm) cudaEventRecord(evm[1], s);
+  if (evm) cudaEventRecordWithFlags(evm[1], s, cudaEventRecordExternal);
   int64_t z1dims[kMaxModes];
   for (int m = 0; m < p; ++m) z1dims[m] = dims[m];
   for (int n = 1; n < p; ++n) {
@@ -1076,7 +1078,7 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
   // the estimator's sigma features are those of the state the step starts from
   CK(cudaMemcpyAsync(ctx->sig2_lag, ctx->sig2, sizeof(double) * p * kMaxRank, cudaMemcpyDeviceToDevice, s));
   cudaEvent_t* ev = ctx->prof ? ctx->pev : nullptr;
-  if (ev) CK(cudaEventRecord(ev[0], s));
+  if (ev) CK(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
   int64_t Rprod = 1;
   for (int n = 0; n < p; ++n) Rprod *= ctx->r[n];
   // a1 + a2: difference scale (Vn - Vfrom) and its projection onto the current bases
@@ -1111,12 +1113,12 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
     TRY(fused_update<Tc>(ctx, false, false, 0));
   }
   TRY(project(ev ? ev + 4 : nullptr, Vp, 1.0));
-  if (ev) CK(cudaEventRecord(ev[1], s));
+  if (ev) CK(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
   // a3..a6 and the refresh of G_n, G_n^{-1}, sigma^(n): one cooperative launch (second
   // stages: the increment at the intermediate state, combined with y_k)
   TRY(fused_update<Tc>(ctx, ctx->cfg.reorth != 0, split,
                        scheme == TDB_HEUN ? 1 : (scheme == TDB_RK2_CENTRAL ? 2 : 0)));
-  if (ev) CK(cudaEventRecord(ev[2], s));
+  if (ev) CK(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
   // the estimator's gate decides the error evaluation only in TDB_ERRMODE_MLP; otherwise
   // its decision goes to a scratch word and the host's schedule stands
   const bool mlp = ctx->cfg.error_mode == TDB_ERRMODE_MLP;
@@ -1143,13 +1145,13 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
     if (run_error) TRY(exact_error2<Tc>(ctx, Vn, gate));
     CK(cudaEventRecord(ctx->ev_join, ctx->aux));
     CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
-    if (ev) CK(cudaEventRecord(ev[3], s));
+    if (ev) CK(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
     return readback_enqueue(ctx);
   }
   features(s);
   CHECK_LAUNCH();
   if (run_error) TRY(exact_error2<Tc>(ctx, Vn, gate));
-  if (ev) CK(cudaEventRecord(ev[3], s));
+  if (ev) CK(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
   return readback_enqueue(ctx);
 }
 
@@ -1160,12 +1162,22 @@ tdb_status finish_step(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
   const int p = ctx->p;
   ctx->warm = true;
   cudaEvent_t* ev = ctx->prof ? ctx->pev : nullptr;
+  float m01 = 0, m12 = 0, m23 = 0, m45 = 0;
   if (ev) {
-    float m01 = 0, m12 = 0, m23 = 0, m45 = 0;
-    CK(cudaEventElapsedTime(&m01, ev[0], ev[1]));
-    CK(cudaEventElapsedTime(&m12, ev[1], ev[2]));
-    CK(cudaEventElapsedTime(&m23, ev[2], ev[3]));
-    CK(cudaEventElapsedTime(&m45, ev[4], ev[5]));
+    cudaError_t e = cudaEventElapsedTime(&m01, ev[0], ev[1]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&m12, ev[1], ev[2]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&m23, ev[2], ev[3]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&m45, ev[4], ev[5]);
+    if (e != cudaSuccess && ctx->last_graphed) {
+      // the events of a recorded step could not be timed: later profiled steps run eagerly
+      cudaGetLastError();
+      ctx->prof_graph_ok = false;
+      ev = nullptr;
+    } else {
+      CK(e);
+    }
+  }
+  if (ev) {
     ctx->pacc.steps++;
     ctx->pacc.ms_project += m01;
     ctx->pacc.ms_update += m12;
@@ -1246,6 +1258,7 @@ tdb_status finish_step(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
 
 template <typename Tc>
 tdb_status step_impl(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
+  ctx->last_graphed = false;
   prepare_step(ctx);
   TRY(enqueue_step<Tc>(ctx, Vn, (const Tc*)ctx->V_prev, false, (const Tc*)ctx->V_prev2));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1313,9 +1326,12 @@ tdb_status capture_step(tdb_ctx* ctx, int parity, cudaGraphExec_t* out) {
 template <typename Tc>
 tdb_status step_slot(tdb_ctx* ctx, int parity, tdb_step_info* info) {
   const Tc* Vn = (const Tc*)ctx->slot[parity];
-  // the tensor-core plan prepares its constant weights on its first (eager) call;
-  // profiled steps run eagerly (events inside a graph cannot be timed)
-  const bool can_graph = !ctx->graph_broken && !ctx->prof && (!ctx->use_tc || ctx->tc.wsl_ready);
+  // the tensor-core plan prepares its constant weights on its first (eager) call.
+  // Profiled steps are recorded too: their timing events are external event-record nodes,
+  // so the phases are timed as the recorded step runs them (eagerly if the runtime cannot
+  // time such events)
+  const bool can_graph = !ctx->graph_broken && (!ctx->prof || ctx->prof_graph_ok) && (!ctx->use_tc || ctx->tc.wsl_ready);
+  ctx->last_graphed = can_graph;
   if (!can_graph) return step_impl<Tc>(ctx, Vn, info);
   prepare_step(ctx);
   const uint64_t key = graph_key(ctx);
@@ -1559,6 +1575,7 @@ tdb_status tdb_push_snapshot(tdb_ctx* ctx, const void* V_next, tdb_step_info* in
   if (!ctx) return TDB_ERR_INVALID_ARG;
   if (!ctx->ready) { ctx->err = "push before init"; return TDB_ERR_STATE; }
   if (!V_next) { ctx->err = "null snapshot"; return TDB_ERR_INVALID_ARG; }
+  ctx->last_graphed = false;
   return ctx->f64 ? step_impl<double>(ctx, (const double*)V_next, info)
                   : step_impl<float>(ctx, (const float*)V_next, info);
 }
@@ -1986,6 +2003,7 @@ tdb_status tdb_batch_push(tdb_batch* b, int parity, tdb_step_info* infos) {
       b->gexec[parity] = nullptr;
       for (size_t i = 0; i < n; ++i) {
         tdb_ctx* c = b->m[i];
+        c->last_graphed = false;
         tdb_status st = enqueue_any(c, parity);
         if (st == TDB_OK && cudaStreamSynchronize(c->stream) != cudaSuccess) st = TDB_ERR_CUDA;
         if (st == TDB_OK) st = readback_done(c);
@@ -2006,6 +2024,7 @@ tdb_status tdb_batch_push(tdb_batch* b, int parity, tdb_step_info* infos) {
   count_launch((int)b->gcount[parity]);
   for (size_t i = 0; i < n; ++i) {
     tdb_ctx* c = b->m[i];
+    c->last_graphed = true;
     tdb_status st = readback_done(c);
     if (st == TDB_OK) st = finish_any(c, parity, infos ? infos + i : nullptr);
     note(st, i);
