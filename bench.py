@@ -55,6 +55,9 @@ def parse_args():
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--profile-region", action="store_true",
+                    help="bracket the timed steps of the main run with cudaProfilerStart/Stop (for "
+                         "ncu --profile-from-start off)")
     ap.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     ap.add_argument("--scaling-sweep", action="store_true",
                     help="TDB step vs on-GPU HOSVD over N^3 grids of the Runge function (one JSON line)")
@@ -354,11 +357,7 @@ def run_tdb(args, world, rank, local):
     lib.tdb_get_profile.argtypes = [C.c_void_p, C.c_void_p]
     lib.tdb_kernel_launches.restype = C.c_int64
 
-    class tdb_profile(C.Structure):
-        _fields_ = [("steps", C.c_int64), ("ms_project", C.c_double), ("ms_project_main", C.c_double),
-                    ("ms_update", C.c_double), ("ms_error", C.c_double), ("ms_control", C.c_double),
-                    ("launches_main", C.c_int64), ("update_phases", C.c_int64),
-                    ("us_update_phase", C.c_double * 12)]
+    tdb_profile = tdb.tdb_profile
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
@@ -431,6 +430,9 @@ def run_tdb(args, world, rank, local):
         time.sleep(0.3)
         stream = torch.cuda.current_stream(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        region = args.profile_region and not timed_profile and mode == err_mode and prec == precision
+        if region:
+            torch.cuda.cudart().cudaProfilerStart()
         t_host0 = time.perf_counter()
         e0.record(stream)
         for k in range(W + 1, W + K + 1):
@@ -442,6 +444,8 @@ def run_tdb(args, world, rank, local):
         e1.record(stream)
         torch.cuda.synchronize()
         t_host = time.perf_counter() - t_host0
+        if region:
+            torch.cuda.cudart().cudaProfilerStop()
         clocks = sampler.stop()
         launches = lib.tdb_kernel_launches() - l0
         barrier(world)
@@ -496,6 +500,12 @@ def run_tdb(args, world, rank, local):
     # nodes of the replayed graph, as in the timed run) or in eager steps
     roofline["kernel_events_in"] = ("recorded step (graph replay)" if resp["counters"]["graph_replays"] > 0
                                     else "eager steps")
+    if prof.spans > 0:
+        # the kernel's own duration (first CTA start to last CTA end, device global timer), for
+        # comparison with the event time above, which adds the launch and the event nodes
+        span_ms = prof.us_project_span / prof.spans * 1e-3
+        roofline["kernel_span_ms"] = span_ms
+        roofline["span_frac"] = alg_bytes / (span_ms * 1e-3) / 1e9 / peak
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
@@ -531,6 +541,16 @@ def run_tdb(args, world, rank, local):
             line["plain_fp32"]["first_divergence"] = {
                 "step": W + 1 + div, "this": list(res["acts"][div]), "plain": list(ref["acts"][div]),
                 "this_exact": res["eps"][div] == res["eps"][div]}
+
+    # what the learned estimator gains: the same path with the exact error on every step
+    if not args.no_compare and err_mode == "mlp":
+        ex = run(precision, timed_profile=False, mode="exact")
+        if ex is not None:
+            _, ms_ex = replica_value(world, K, ex["ms"], ex["host_s"])
+            v_ex = world * K / (ms_ex * 1e-3)
+            line["estimator_gain"] = {"exact_every_step": v_ex, "unit": UNIT, "ratio": value / v_ex,
+                                      "same_decisions": res["acts"] == ex["acts"],
+                                      "exact_evals": [res["counters"]["exact_evals"], ex["counters"]["exact_evals"]]}
 
     # end to end through the C ABI from pinned host buffers
     if not args.no_e2e:

@@ -301,6 +301,11 @@ typedef struct tdb_profile {
                                  rows M/X/P, P reduce, rows U'/C, Cholesky-QR factors,
                                  rows U'' with the core product of mode 1, core products of
                                  modes 2..p, Gram partials, Gram finish */
+  double us_project_span;     /* TDB_BF16_TTM: microseconds summed over the timed steps from the
+                                 first CTA's start to the last CTA's end of the main projection
+                                 kernel (device global timer); the CUDA-event time of
+                                 ms_project_main adds the launch and the event nodes to it */
+  int64_t spans;              /* launches measured in us_project_span */
 } tdb_profile;
 
 /* enable != 0 starts (and zeroes) the accumulation; 0 stops it. */

@@ -296,10 +296,183 @@ __global__ void __launch_bounds__(256) k_recon_err(const T* __restrict__ V, cons
   }
 }
 
+// Float exact error, row-major variant: lane l of a warp owns rows i0 + R l .. i0 + R l + R - 1
+// of a block of 32 R rows, with U_1 of those rows (R x r_1) and w_1 in registers, and walks a
+// contiguous range of columns c.  Each column's R rows per lane, H[:, c] (lanes < r_1) and
+// w_c (lane 0) arrive by cp.async into a ring of D column slots per warp (D columns in
+// flight per warp, no registers held); H[:, c] is broadcast by shuffles.  Per column the
+// lane forms U_1 H[:, c] for its rows, the weighted squared difference, and adds w_c times
+// it to a float sum that goes into the double accumulator every D columns.
+constexpr int RE_D = 8;           // columns in flight per warp
+template <int R>
+__device__ __forceinline__ void cp_async_rows(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = valid ? 4 * R : 0;
+  if (R == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+  else if (R == 2)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(valid ? 4 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+template <int R, int RM>
+__global__ void __launch_bounds__(256, 2) k_recon_err_rows(const float* __restrict__ V, const float* __restrict__ U1,
+                                                         const float* __restrict__ H, int r1, int N1, unsigned ncol,
+                                                         const float* __restrict__ w1, const float* __restrict__ wcol,
+                                                         int vec, double* __restrict__ partial,
+                                                         unsigned* __restrict__ counter, double* __restrict__ out,
+                                                         unsigned* flags, const int* __restrict__ gate) {
+  if (gate && *gate == 0) return;          // the estimator ruled this evaluation out
+  constexpr int SLOT = 32 * R + RM + 4;    // floats per column slot: rows, H[:, c] (zero past r_1), w_c
+  __shared__ __align__(16) float ring[8][RE_D][SLOT];
+  __shared__ double sh[32];
+  __shared__ bool last;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  float (*slot)[SLOT] = ring[wib];
+  // H entries past r_1 are never copied: zero them once (they meet zero rows of U_1)
+  for (int e = lane; e < RE_D * RM; e += 32) slot[e / RM][32 * R + e % RM] = 0.f;
+  __syncwarp();
+  const int nrb = (N1 + 32 * R - 1) / (32 * R);
+  const unsigned gw = blockIdx.x * (blockDim.x >> 5) + wib, tw = gridDim.x * (blockDim.x >> 5);
+  const unsigned wpr = tw >= (unsigned)nrb ? tw / nrb : 1u;   // warps per row block
+  double acc = 0.0;
+  bool bad = false;
+  const unsigned kk = gw % wpr;
+  const unsigned c_lo = (unsigned)((uint64_t)ncol * kk / wpr), c_hi = (unsigned)((uint64_t)ncol * (kk + 1) / wpr);
+  if (gw < wpr * (unsigned)nrb && c_lo < c_hi) {
+    const int rb = (int)(gw / wpr);
+    const int i0 = rb * 32 * R + R * lane;
+    float u[R][RM], wr[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      const int i = i0 + q;
+      wr[q] = i < N1 ? w1[i] : 0.f;
+#pragma unroll
+      for (int a = 0; a < RM; ++a) u[q][a] = (i < N1 && a < r1) ? U1[i + (size_t)N1 * a] : 0.f;
+    }
+    // source pointers of the next column to issue, advanced by one column per issue; past
+    // c_hi the copies read nothing (zero bytes) from the last valid column
+    const bool rows_in = i0 < N1;
+    const float* vsrc = V + (size_t)N1 * c_lo + (rows_in ? i0 : 0);
+    const float* hsrc = H + (size_t)r1 * c_lo + (lane < r1 ? lane : 0);
+    const float* wsrc = wcol + c_lo;
+    unsigned cnext = c_lo;
+    auto issue = [&](int sl) {
+      const bool in = cnext < c_hi;
+      if (vec) {
+        cp_async_rows<R>(&slot[sl][R * lane], vsrc, in && rows_in);
+      } else {
+#pragma unroll
+        for (int q = 0; q < R; ++q) cp_async4(&slot[sl][R * lane + q], vsrc + (i0 + q < N1 ? q : 0), in && i0 + q < N1);
+      }
+      if (lane < r1) cp_async4(&slot[sl][32 * R + lane], hsrc, in);
+      if (lane == 0) cp_async4(&slot[sl][32 * R + RM], wsrc, in);
+      cp_async_commit();
+      if (in && cnext + 1 < c_hi) {
+        vsrc += N1;
+        hsrc += r1;
+        wsrc += 1;
+      }
+      ++cnext;
+    };
+#pragma unroll
+    for (int t = 0; t < RE_D; ++t) issue(t);
+    float csum = 0.f;
+    int sl = 0;
+    for (unsigned c = c_lo; c < c_hi; ++c) {
+      cp_async_wait<RE_D - 1>();           // this column's copies (the oldest group) have landed
+      __syncwarp();
+      float v[R], h[RM];
+      if (R == 4) {
+        const float4 t4 = *reinterpret_cast<const float4*>(&slot[sl][4 * lane]);
+        v[0] = t4.x; v[1 % R] = t4.y; v[2 % R] = t4.z; v[3 % R] = t4.w;
+      } else if (R == 2) {
+        const float2 t2 = *reinterpret_cast<const float2*>(&slot[sl][2 * lane]);
+        v[0] = t2.x; v[1 % R] = t2.y;
+      } else {
+        v[0] = slot[sl][lane];
+      }
+#pragma unroll
+      for (int j = 0; j < RM / 4; ++j) {
+        const float4 t4 = *reinterpret_cast<const float4*>(&slot[sl][32 * R + 4 * j]);
+        h[4 * j] = t4.x; h[4 * j + 1] = t4.y; h[4 * j + 2] = t4.z; h[4 * j + 3] = t4.w;
+      }
+      const float wc = slot[sl][32 * R + RM];
+      __syncwarp();
+      issue(sl);                           // the slot refills with the column D ahead
+      float rec[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) rec[q] = 0.f;
+#pragma unroll
+      for (int a = 0; a < RM; ++a)
+#pragma unroll
+        for (int q = 0; q < R; ++q) rec[q] = fmaf(u[q][a], h[a], rec[q]);
+      float s = 0.f;
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        const float d = v[q] - rec[q];
+        s = fmaf(wr[q] * d, d, s);
+      }
+      csum = fmaf(wc, s, csum);
+      if (++sl == RE_D) {
+        sl = 0;
+        bad |= !isfinite(csum);
+        acc += (double)csum;
+        csum = 0.f;
+      }
+    }
+    cp_async_wait<0>();
+    bad |= !isfinite(csum);
+    acc += (double)csum;
+  }
+  acc = block_sum(acc, sh);
+  if (bad && flags) atomicOr(flags, kFlagNonFinite);
+  if (threadIdx.x == 0) {
+    partial[blockIdx.x] = acc;
+    __threadfence();
+    last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  double t = 0.0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) t += __ldcg(&partial[b]);
+  t = block_sum(t, sh);
+  if (threadIdx.x == 0) {
+    *out = t;
+    atomicExch(counter, 0u);
+  }
+}
+
 template <typename T>
 void launch_recon_err(const T* V, const T* U1, const T* H, int r1, int N1, int64_t ncol, const T* w1, const T* wcol,
                       double* partial, unsigned* counter, int nblocks, double* out, unsigned* flags, cudaStream_t s,
                       const int* gate) {
+  if constexpr (sizeof(T) == 4) {
+    // the row-major variant: U_1 in registers, cp.async column ring
+    const uintptr_t va = (uintptr_t)V;
+    const int vec4 = (N1 % 4) == 0 && va % 16 == 0, vec2 = (N1 % 2) == 0 && va % 8 == 0;
+    const int blocks = std::max(1, std::min(nblocks, 2 * 152));
+    if (r1 <= 8)
+      k_recon_err_rows<4, 8><<<blocks, 256, 0, s>>>(V, U1, H, r1, N1, (unsigned)ncol, w1, wcol, vec4, partial,
+                                                    counter, out, flags, gate);
+    else if (r1 <= 16)
+      k_recon_err_rows<4, 16><<<blocks, 256, 0, s>>>(V, U1, H, r1, N1, (unsigned)ncol, w1, wcol, vec4, partial,
+                                                     counter, out, flags, gate);
+    else
+      k_recon_err_rows<2, 32><<<blocks, 256, 0, s>>>(V, U1, H, r1, N1, (unsigned)ncol, w1, wcol, vec2, partial,
+                                                     counter, out, flags, gate);
+    count_launch();
+    return;
+  }
   const size_t st_bytes = (size_t)N1 * (r1 + 1) * sizeof(T);
   const int stage = st_bytes <= 96 * 1024 ? 1 : 0;
   static bool attr[2] = {false, false};

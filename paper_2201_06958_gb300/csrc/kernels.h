@@ -97,6 +97,15 @@ struct GramView {
   int64_t L, Q, Nn;
 };
 
+// A timing event on stream s: an external event-record node while s is being captured
+// (so that the replayed graph records it), an ordinary record otherwise.
+inline cudaError_t record_timing_event(cudaEvent_t ev, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+    return cudaEventRecordWithFlags(ev, s, cudaEventRecordExternal);
+  return cudaEventRecord(ev, s);
+}
+
 // Process-wide count of libtdb kernel launches (tdb_kernel_launches).
 void count_launch(int n = 1);
 long long launches_so_far();

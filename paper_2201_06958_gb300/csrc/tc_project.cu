@@ -70,6 +70,7 @@ struct Params {
   const double* wsl;             // slice weights (product over modes >= 3)
   double* npart;                 // ||dV||_W^2 per converter warp: [CTA][NUM_CONV_WARPS]
   unsigned* flags;
+  unsigned long long* span;      // profiling: {first CTA start, last CTA end, ...} (global timer), or null
   float dscale;                  // dV = dscale (V_{k+1} - V_k) (1; 1/4 or 1/2 for a central difference): a
                                  // power of two, applied to the accumulators and the norm (exact)
 };
@@ -84,6 +85,11 @@ __host__ __device__ constexpr int smem_fixed_bytes(int b1, int b2) {
 // PTX wrappers
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
 
 __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
@@ -120,6 +126,10 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* tm) {
   asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)tm) : "memory");
 }
 
+// Programmatic launch: wait until the stream's previous kernel has completed and its
+// writes are visible (a no-op when the kernel was launched the ordinary way).
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // Bounded wait on a phase parity.  Returns false (and raises the abort flag) on
 // timeout or when another role already aborted.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int* abort_flag, unsigned* flags,
@@ -131,6 +141,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
       if (*abort_flag) return false;
       if (clock64() - t0 > limit) {
         *abort_flag = 1;
+        grid_dep_wait();                 // the previous kernel clears the step's flags
         atomicOr(flags, kFlagTimeout);
         return false;
       }
@@ -241,6 +252,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   volatile int* abort_flag = (volatile int*)(tmem_slot + 1);
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (P.span && tid == 0) atomicMin(&P.span[0], global_ns());
   // this CTA's tile position and its first slice
   const int pos = blockIdx.x % P.nq12;
   const int q1 = pos % P.nq1, q2 = pos / P.nq1;
@@ -333,6 +345,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           if (*abort_flag) break;
           if (clock64() - t0 > TIMEOUT_CYCLES) {
             *abort_flag = 1;
+            grid_dep_wait();
             atomicOr(P.flags, kFlagTimeout);
             break;
           }
@@ -540,9 +553,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     if (lane == 0) P.npart[(size_t)blockIdx.x * NUM_CONV_WARPS + c] = s * ((double)P.dscale * (double)P.dscale);
   }
 
-  // TMEM is released once every role is done with it
+  // TMEM is released once every role is done with it; the kernel completes only after the
+  // stream's previous kernel (programmatic launch)
   tc_fence_before();
   __syncthreads();
+  if (tid == 0) {
+    grid_dep_wait();
+    if (P.span) atomicMax(&P.span[1], global_ns());
+  }
   if (warp == MMA_WARP) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
@@ -596,6 +614,7 @@ struct FinArgs {
   int nsplit, nt1, nt2;
   const double* npart;
   int nnp;
+  unsigned long long* span;     // profiling words of the main kernel (see Params), or null
   double* dv2;
 };
 
@@ -611,6 +630,16 @@ __global__ void __launch_bounds__(FS_TE) k_tc_finish_sk(FinArgs f) {
     for (int i = tid; i < f.nnp; i += blockDim.x) t += f.npart[i];
     t = block_sum(t, dsh);
     if (tid == 0) *f.dv2 = t;
+    if (tid == 0 && f.span) {
+      // the main kernel has completed: its span into the sums, the words reset for the next
+      const unsigned long long a = f.span[0], b = f.span[1];
+      if (b > a) {
+        f.span[2] += b - a;
+        f.span[3] += 1;
+      }
+      f.span[0] = ~0ull;
+      f.span[1] = 0ull;
+    }
   }
   const bool first = tile < f.nt1;
   const int64_t ne = first ? (int64_t)f.r1 * f.N2 : (int64_t)f.N1 * f.r2;
@@ -994,7 +1023,7 @@ void tc_carve(TcPlan& plan, Carver& cv, int p, const int64_t* N, const int* cap)
 tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, const int64_t* N, const int* r,
                       const void* const* A, const double* const* w, float* Z1, float* Z2, float* scratch,
                       float* dS, float* const* Y, double* dv2, unsigned* flags, cudaStream_t s, cudaEvent_t* evm,
-                      std::string& err, bool defer_ds, float dscale) {
+                      std::string& err, bool defer_ds, float dscale, bool pdl) {
   if (!get_encoder(err)) return TDB_ERR_UNSUPPORTED;
   const int N1 = (int)N[0], N2 = (int)N[1];
   int nslice = 1;
@@ -1065,13 +1094,28 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   P.npart = plan.npart;
   P.flags = flags;
   P.dscale = dscale;
+  P.span = plan.tuned ? plan.span : nullptr;
   if (!plan.attr_set) {
     cudaFuncSetAttribute(k_tc_project, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     plan.attr_set = true;
   }
   auto launch_project = [&](int cstep) {
     P.cstep = cstep;
-    k_tc_project<<<P.nq12 * cstep, NUM_THREADS, smem, s>>>(tmn, tmp, P);
+    if (pdl) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(P.nq12 * cstep);
+      cfg.blockDim = dim3(NUM_THREADS);
+      cfg.dynamicSmemBytes = smem;
+      cfg.stream = s;
+      cudaLaunchAttribute at[1];
+      at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+      at[0].val.programmaticStreamSerializationAllowed = 1;
+      cfg.attrs = at;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, k_tc_project, tmn, tmp, P);
+    } else {
+      k_tc_project<<<P.nq12 * cstep, NUM_THREADS, smem, s>>>(tmn, tmp, P);
+    }
     count_launch();
   };
   // finish: Y_1, Y_2 (and Z1) from the tile partials, the slices contracted with
@@ -1113,6 +1157,7 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   f.nt1 = nt1;
   f.nt2 = nt2;
   f.npart = plan.npart;
+  f.span = nullptr;
   f.dv2 = dv2;
   const size_t fsm = sizeof(float) * FS_SC * ((J + 3) & ~3);
   const int nqm = std::max(nq1, nq2);
@@ -1150,15 +1195,16 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   }
   const int cstep = plan.tuned ? std::min(plan.cstep, cmax) : cmax;
   const int grid = P.nq12 * cstep;
-  if (evm) cudaEventRecordWithFlags(evm[0], s, cudaEventRecordExternal);
+  if (evm && !pdl) record_timing_event(evm[0], s);
   launch_project(cstep);
-  if (evm) cudaEventRecordWithFlags(evm[1], s, cudaEventRecordExternal);
+  if (evm) record_timing_event(evm[1], s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     err = std::string("k_tc_project launch: ") + cudaGetErrorString(e);
     return TDB_ERR_CUDA;
   }
   f.nnp = grid * NUM_CONV_WARPS;
+  f.span = P.span;
   launch_finish(nsplit_for(plan.tuned ? plan.fin_target : FS_CTAS));
   if (p >= 3) {
     // Z1 summed over the mode-1 tiles: the partials themselves when there is one tile

@@ -37,6 +37,23 @@ struct Readback {
   unsigned flags;
 };
 
+// The step's first kernel: clears the step record, fetches the host's gate word and the
+// estimator state from pinned host memory (read through its device mapping), keeps the
+// sigma^2 the step starts from (the estimator's features), and lets the projection that
+// follows start its set-up early (programmatic launch).  One CTA.
+__global__ void k_step_begin(Readback* rb, const int* need_h, const EstState* est_h, EstState* est_d,
+                             const double* sig2, double* sig2_lag, int nsig) {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  unsigned* w = (unsigned*)rb;
+  for (int i = threadIdx.x; i < (int)(sizeof(Readback) / 4); i += blockDim.x) w[i] = 0u;
+  const unsigned* es = (const unsigned*)est_h;
+  unsigned* ed = (unsigned*)est_d;
+  for (int i = threadIdx.x; i < (int)(sizeof(EstState) / 4); i += blockDim.x) ed[i] = es[i];
+  for (int i = threadIdx.x; i < nsig; i += blockDim.x) sig2_lag[i] = sig2[i];
+  __syncthreads();
+  if (threadIdx.x == 0) rb->need = *(volatile const int*)need_h;
+}
+
 }  // namespace tdb
 
 using namespace tdb;
@@ -89,6 +106,7 @@ struct tdb_ctx {
   void* w1T;                      // w_1 in the compute type
   void* wcolT;                    // mode-1 column weights prod_{m>1} w_m in the compute type
   unsigned long long* stamps;     // phase timer stamps of the fused update (profiling)
+  unsigned long long* span_dev;   // the projection kernel's span words (profiling, TcPlan::span)
   int ntile = 1;
   double* sig2;
   double* sig2_lag;               // sigma^2 of the state a step starts from (estimator features)
@@ -150,6 +168,8 @@ struct tdb_ctx {
   Readback* rb_pin = nullptr;
   EstState* est_pin = nullptr;
   int* need_pin = nullptr;
+  const EstState* est_pin_d = nullptr;   // device views of the pinned words (null: copies instead)
+  const int* need_pin_d = nullptr;
   EstState* est_dev = nullptr;
   bool need_host = false;          // this step's host gate (evaluate the exact error)
   bool gated_step = false;         // the estimator decides on the device this step
@@ -164,6 +184,7 @@ struct tdb_ctx {
   bool graph_broken = false;
   bool prof_graph_ok = true;      // profiled steps may be recorded (their events time in a graph)
   bool last_graphed = false;      // the step being finished ran as a graph replay
+  bool main_from_start = false;   // its projection kernel is timed from the step's first event
   int64_t graph_replays = 0, graph_records = 0;
 
   // host state
@@ -345,6 +366,7 @@ void carve(tdb_ctx* c, Carver& cv) {
   c->w1T = cv.take<char>((size_t)c->N[0] * tsz);
   c->wcolT = cv.take<char>((size_t)(c->S / c->N[0]) * tsz);
   c->stamps = cv.take<unsigned long long>(32);
+  c->span_dev = cv.take<unsigned long long>(4);
   c->sig2 = cv.take<double>(p * kMaxRank);
   c->sig2_lag = cv.take<double>(p * kMaxRank);
   c->need_scratch = cv.take<int>(1);
@@ -491,9 +513,9 @@ tdb_status project_tree(tdb_ctx* ctx, const Tc* dV, cudaEvent_t* evm) {
   Tc* pong = (Tc*)ctx->pong;
   // Z1 = dV x_1 A_1^T, then each Y_n (n >= 2) contracts the remaining modes but n
   for (int m = 0; m < p; ++m) dims[m] = ctx->N[m];
-  if (evm) cudaEventRecordWithFlags(evm[0], s, cudaEventRecordExternal);
+  if (evm) record_timing_event(evm[0], s);
   mp(dV, ping, 0, dims);
-  if (evm) cudaEventRecordWithFlags(evm[1], s, cudaEventRecordExternal);
+  if (evm) record_timing_event(evm[1], s);
   int64_t z1dims[kMaxModes];
   for (int m = 0; m < p; ++m) z1dims[m] = dims[m];
   for (int n = 1; n < p; ++n) {
@@ -1072,22 +1094,36 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
   // sigma^(n)) runs beside the error on the context's second stream
   const bool split = (ctx->cfg.error_mode == TDB_ERRMODE_EXACT || ctx->cfg.error_mode == TDB_ERRMODE_MLP) &&
                      ctx->aux && ctx->ev_fork && ctx->ev_join;
-  CK(cudaMemsetAsync(ctx->rb_dev, 0, sizeof(Readback), s));
-  CK(cudaMemcpyAsync(&ctx->rb_dev->need, ctx->need_pin, sizeof(int), cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(ctx->est_dev, ctx->est_pin, sizeof(EstState), cudaMemcpyHostToDevice, s));
-  // the estimator's sigma features are those of the state the step starts from
-  CK(cudaMemcpyAsync(ctx->sig2_lag, ctx->sig2, sizeof(double) * p * kMaxRank, cudaMemcpyDeviceToDevice, s));
   cudaEvent_t* ev = ctx->prof ? ctx->pev : nullptr;
-  if (ev) CK(cudaEventRecordWithFlags(ev[0], s, cudaEventRecordExternal));
+  const int scheme = ctx->cfg.integrator;
+  // the step opens with one small kernel (step record cleared, host words fetched, the
+  // estimator's sigma features - those of the state the step starts from - kept); an Euler
+  // step's projection follows it by programmatic launch, so the projection's set-up
+  // (barriers, TMEM, the first loads) overlaps it.  Its events then bracket both.
+  const bool begin_kernel = ctx->need_pin_d && ctx->est_pin_d;
+  const bool pdl = begin_kernel && ctx->use_tc && scheme == TDB_EULER;
+  if (ctx->use_tc) ctx->tc.span = ev ? ctx->span_dev : nullptr;
+  if (ev) CK(record_timing_event(ev[0], s));
+  ctx->main_from_start = pdl;        // the projection's start event is the step's (ev[0])
+  if (begin_kernel) {
+    k_step_begin<<<1, 256, 0, s>>>(ctx->rb_dev, ctx->need_pin_d, ctx->est_pin_d, ctx->est_dev, ctx->sig2,
+                                   ctx->sig2_lag, p * kMaxRank);
+    count_launch();
+  } else {
+    CK(cudaMemsetAsync(ctx->rb_dev, 0, sizeof(Readback), s));
+    CK(cudaMemcpyAsync(&ctx->rb_dev->need, ctx->need_pin, sizeof(int), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->est_dev, ctx->est_pin, sizeof(EstState), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(ctx->sig2_lag, ctx->sig2, sizeof(double) * p * kMaxRank, cudaMemcpyDeviceToDevice, s));
+  }
   int64_t Rprod = 1;
   for (int n = 0; n < p; ++n) Rprod *= ctx->r[n];
   // a1 + a2: difference scale (Vn - Vfrom) and its projection onto the current bases
-  auto project = [&](cudaEvent_t* evm, const Tc* Vfrom, double scale) -> tdb_status {
+  auto project = [&](cudaEvent_t* evm, const Tc* Vfrom, double scale, bool after_begin) -> tdb_status {
     if (ctx->use_tc) {
       TRY(tc_project(ctx->tc, (const float*)Vn, (const float*)Vfrom, ctx->p, ctx->N, ctx->r,
                      (const void* const*)ctx->A, (const double* const*)ctx->w, (float*)ctx->ping, (float*)ctx->pong,
                      (float*)ctx->dV, (float*)ctx->dS, (float* const*)ctx->Y, &ctx->rb_dev->dv2, ctx->flags, s, evm,
-                     ctx->err, true, (float)scale));
+                     ctx->err, true, (float)scale, after_begin));
     } else {
       launch_diff<Tc>(Vn, Vfrom, (Tc*)ctx->dV, ctx->S, s, (Tc)scale);
       launch_wnorm2<Tc>((const Tc*)ctx->dV, nullptr, weight_view(ctx), ctx->npart, ctx->nblk, &ctx->rb_dev->dv2,
@@ -1097,7 +1133,6 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
     }
     return TDB_OK;
   };
-  const int scheme = ctx->cfg.integrator;
   if (scheme == TDB_HEUN || scheme == TDB_RK2_CENTRAL) {
     // first stage: keep y_k = (T, U_n), then an Euler increment at y_k gives the
     // intermediate state in place (no re-orthonormalisation; G_n, G_n^{-1} refreshed for
@@ -1107,18 +1142,18 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
     CK(cudaMemcpyAsync(ctx->Tbak, ctx->T, sizeof(double) * Rprod, cudaMemcpyDeviceToDevice, s));
     for (int n = 0; n < p; ++n)
       CK(cudaMemcpyAsync(ctx->Ubak[n], ctx->U[n], sizeof(double) * ctx->N[n] * ctx->r[n], cudaMemcpyDeviceToDevice, s));
-    if (scheme == TDB_HEUN) TRY(project(nullptr, Vp, 1.0));
-    else if (Vpp) TRY(project(nullptr, Vpp, 0.25));
-    else TRY(project(nullptr, Vp, 0.5));
+    if (scheme == TDB_HEUN) TRY(project(nullptr, Vp, 1.0, false));
+    else if (Vpp) TRY(project(nullptr, Vpp, 0.25, false));
+    else TRY(project(nullptr, Vp, 0.5, false));
     TRY(fused_update<Tc>(ctx, false, false, 0));
   }
-  TRY(project(ev ? ev + 4 : nullptr, Vp, 1.0));
-  if (ev) CK(cudaEventRecordWithFlags(ev[1], s, cudaEventRecordExternal));
+  TRY(project(ev ? ev + 4 : nullptr, Vp, 1.0, pdl));
+  if (ev) CK(record_timing_event(ev[1], s));
   // a3..a6 and the refresh of G_n, G_n^{-1}, sigma^(n): one cooperative launch (second
   // stages: the increment at the intermediate state, combined with y_k)
   TRY(fused_update<Tc>(ctx, ctx->cfg.reorth != 0, split,
                        scheme == TDB_HEUN ? 1 : (scheme == TDB_RK2_CENTRAL ? 2 : 0)));
-  if (ev) CK(cudaEventRecordWithFlags(ev[2], s, cudaEventRecordExternal));
+  if (ev) CK(record_timing_event(ev[2], s));
   // the estimator's gate decides the error evaluation only in TDB_ERRMODE_MLP; otherwise
   // its decision goes to a scratch word and the host's schedule stands
   const bool mlp = ctx->cfg.error_mode == TDB_ERRMODE_MLP;
@@ -1145,13 +1180,13 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
     if (run_error) TRY(exact_error2<Tc>(ctx, Vn, gate));
     CK(cudaEventRecord(ctx->ev_join, ctx->aux));
     CK(cudaStreamWaitEvent(s, ctx->ev_join, 0));
-    if (ev) CK(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
+    if (ev) CK(record_timing_event(ev[3], s));
     return readback_enqueue(ctx);
   }
   features(s);
   CHECK_LAUNCH();
   if (run_error) TRY(exact_error2<Tc>(ctx, Vn, gate));
-  if (ev) CK(cudaEventRecordWithFlags(ev[3], s, cudaEventRecordExternal));
+  if (ev) CK(record_timing_event(ev[3], s));
   return readback_enqueue(ctx);
 }
 
@@ -1167,7 +1202,7 @@ tdb_status finish_step(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
     cudaError_t e = cudaEventElapsedTime(&m01, ev[0], ev[1]);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&m12, ev[1], ev[2]);
     if (e == cudaSuccess) e = cudaEventElapsedTime(&m23, ev[2], ev[3]);
-    if (e == cudaSuccess) e = cudaEventElapsedTime(&m45, ev[4], ev[5]);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&m45, ctx->main_from_start ? ev[0] : ev[4], ev[5]);
     if (e != cudaSuccess && ctx->last_graphed) {
       // the events of a recorded step could not be timed: later profiled steps run eagerly
       cudaGetLastError();
@@ -1455,6 +1490,16 @@ tdb_status common_init(tdb_ctx** out, const tdb_config* cfg, void* ws, size_t ws
   }
   ctx->est_pin = (EstState*)((char*)ctx->rb_pin + ((sizeof(Readback) + 15) & ~(size_t)15));
   ctx->need_pin = (int*)((char*)ctx->est_pin + ((sizeof(EstState) + 15) & ~(size_t)15));
+  {
+    void* dp = nullptr;
+    if (cudaHostGetDevicePointer(&dp, ctx->rb_pin, 0) == cudaSuccess && dp) {
+      char* base = (char*)dp;
+      ctx->est_pin_d = (const EstState*)(base + ((char*)ctx->est_pin - (char*)ctx->rb_pin));
+      ctx->need_pin_d = (const int*)(base + ((char*)ctx->need_pin - (char*)ctx->rb_pin));
+    } else {
+      cudaGetLastError();
+    }
+  }
   cudaMemsetAsync(ctx->rb_dev, 0, sizeof(Readback), ctx->stream);
   cudaMemsetAsync(ctx->redcnt, 0, 8 * sizeof(unsigned), ctx->stream);
   if (ctx->f64)
@@ -1854,6 +1899,9 @@ tdb_status tdb_set_profiling(tdb_ctx* ctx, int enable) {
       if (!ctx->pev[i]) CK(cudaEventCreate(&ctx->pev[i]));
     memset(&ctx->pacc, 0, sizeof(ctx->pacc));
     CK(cudaMemsetAsync(ctx->stamps, 0, 32 * sizeof(unsigned long long), ctx->stream));
+    static const unsigned long long span0[4] = {~0ull, 0ull, 0ull, 0ull};
+    CK(cudaMemcpyAsync(ctx->span_dev, span0, sizeof(span0), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
   }
   ctx->prof = enable != 0;
   return TDB_OK;
@@ -1864,6 +1912,11 @@ tdb_status tdb_get_profile(tdb_ctx* ctx, tdb_profile* out) {
   unsigned long long st[32];
   CK(cudaMemcpyAsync(st, ctx->stamps, sizeof(st), cudaMemcpyDeviceToHost, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
+  unsigned long long sp[4] = {0, 0, 0, 0};
+  CK(cudaMemcpyAsync(sp, ctx->span_dev, sizeof(sp), cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  ctx->pacc.us_project_span = 1e-3 * (double)sp[2];
+  ctx->pacc.spans = (int64_t)sp[3];
   ctx->pacc.update_phases = std::min(6 + ctx->p, 12);
   for (int k = 0; k < 12; ++k) ctx->pacc.us_update_phase[k] = k < ctx->pacc.update_phases ? 1e-3 * (double)st[16 + k] : 0.0;
   *out = ctx->pacc;

@@ -54,7 +54,7 @@ class tdb_profile(C.Structure):
     _fields_ = [("steps", C.c_int64), ("ms_project", C.c_double), ("ms_project_main", C.c_double),
                 ("ms_update", C.c_double), ("ms_error", C.c_double), ("ms_control", C.c_double),
                 ("launches_main", C.c_int64), ("update_phases", C.c_int64),
-                ("us_update_phase", C.c_double * 12)]
+                ("us_update_phase", C.c_double * 12), ("us_project_span", C.c_double), ("spans", C.c_int64)]
 
 
 class tdb_step_info(C.Structure):
@@ -392,7 +392,8 @@ class TDB:
         self._check(self.lib.tdb_get_profile(self.ctx, C.byref(pr)))
         return {"steps": pr.steps, "ms_project": pr.ms_project, "ms_project_main": pr.ms_project_main,
                 "ms_update": pr.ms_update, "ms_error": pr.ms_error, "ms_control": pr.ms_control,
-                "us_update_phase": [pr.us_update_phase[i] for i in range(pr.update_phases)]}
+                "us_update_phase": [pr.us_update_phase[i] for i in range(pr.update_phases)],
+                "us_project_span": pr.us_project_span, "spans": pr.spans}
 
     def counters(self):
         s, r, e = C.c_int64(), C.c_int64(), C.c_int64()

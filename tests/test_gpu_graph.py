@@ -97,3 +97,39 @@ def test_batch_equals_members_stepped_alone(tdbmod):
     c = batch.counters()
     assert c["graph_replays"] >= steps - 1 and c["graph_records"] <= 3, c
     batch.close()
+
+
+@cuda
+def test_profiling_eager_and_recorded(tdbmod):
+    """The per-phase timers work on plain pushes (eager events) and on recorded steps
+    (external event-record nodes in the step graph), change no result, and the projection
+    kernel's span (device global timer) is positive and below its event time."""
+    wl = S.make_workload("reactive", nx=128, ny=64, ns=8)
+    snaps = [wl.snapshot(k, device="cuda") for k in range(13)]
+    kw = dict(rank_max=[6, 6, 4], weights=wl.weights, eps_th=0.0, precision="bf16", error_mode="exact")
+    A = tdbmod.TDB(wl.dims, [6, 6, 4], **kw).init(snaps[0])
+    B = tdbmod.TDB(wl.dims, [6, 6, 4], **kw)
+    slots = [torch.empty_like(snaps[0]), torch.empty_like(snaps[0])]
+    slots[1].copy_(snaps[0])
+    B.init(slots[1])
+    B.set_input_slots(slots[0], slots[1])
+    for k in range(1, 4):
+        A.push(snaps[k])
+        slots[(k - 1) % 2].copy_(snaps[k])
+        B.push_slot((k - 1) % 2)
+    A.set_profiling(True)
+    B.set_profiling(True)
+    for k in range(4, 13):
+        ia = A.push(snaps[k])
+        slots[(k - 1) % 2].copy_(snaps[k])
+        ib = B.push_slot((k - 1) % 2)
+        same_info(ia, ib)
+    for c, recorded in ((A, False), (B, True)):
+        pr = c.profile()
+        assert pr["steps"] == 9, pr
+        for key in ("ms_project", "ms_project_main", "ms_update", "ms_error"):
+            assert pr[key] > 0.0, (recorded, key, pr)
+        assert pr["spans"] == 9, pr
+        assert 0.0 < pr["us_project_span"] < pr["ms_project_main"] * 1e3, pr
+    assert B.counters()["graph_replays"] >= 9
+    same_factors(A, B)
