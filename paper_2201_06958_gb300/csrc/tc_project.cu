@@ -225,6 +225,32 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Packed FP32 pairs (the .f32x2 forms of sm_100+): two lanes of arithmetic per instruction,
+// each element rounded as the scalar instruction would round it.
+__device__ __forceinline__ uint64_t f2(float x, float y) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ void f2_split(uint64_t v, float& x, float& y) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(x), "=f"(y) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2_sub(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_mul(uint64_t a, uint64_t b) {
+  uint64_t r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ uint64_t f2_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
   __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
   return *reinterpret_cast<uint32_t*>(&h);
@@ -492,12 +518,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
     const int chunk = cx >> 1, hoff = (cx & 1) * 8;
     const bool strip_in = q2 * TILE + c * SUB_I2 < P.N2;
     bool half_in[2];
-    float w1v[2][4], w2v[8];
+    uint64_t w1p[2][2];                 // w_1 of this lane's four columns in each half, as pairs
+    float w2v[8];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       half_in[h] = q1 * TILE + h * 64 < P.N1;
       const float4 w = __ldg((const float4*)(P.w1f + q1 * TILE + h * 64 + 4 * cx));
-      w1v[h][0] = w.x; w1v[h][1] = w.y; w1v[h][2] = w.z; w1v[h][3] = w.w;
+      w1p[h][0] = f2(w.x, w.y);
+      w1p[h][1] = f2(w.z, w.w);
     }
     // weights of the rows this lane converts (zero past N_2)
 #pragma unroll
@@ -530,10 +558,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           const int row = ry + 2 * k;                 // 0..15 within the strip
           const float4 a = vn[row * 32 + h * 16 + cx];
           const float4 b = vp[row * 32 + h * 16 + cx];
-          const float d0 = a.x - b.x, d1 = a.y - b.y;
-          const float d2 = a.z - b.z, d3 = a.w - b.w;
+          // dV in FP32 pairs; sum_j w_1(j) dV_j^2 of the row's four columns, then times w_2
+          const uint64_t d01 = f2_sub(f2(a.x, a.y), f2(b.x, b.y));
+          const uint64_t d23 = f2_sub(f2(a.z, a.w), f2(b.z, b.w));
+          const uint64_t q = f2_fma(f2_mul(w1p[h][1], d23), d23, f2_mul(f2_mul(w1p[h][0], d01), d01));
+          float q0, q1v, d0, d1, d2, d3;
+          f2_split(q, q0, q1v);
+          acc = fmaf(w2v[k], q0 + q1v, acc);
+          f2_split(d01, d0, d1);
+          f2_split(d23, d2, d3);
           const int r = c * SUB_I2 + row;             // tile row (i2 within the tile)
-          acc += w2v[k] * (w1v[h][0] * d0 * d0 + w1v[h][1] * d1 * d1 + w1v[h][2] * d2 * d2 + w1v[h][3] * d3 * d3);
           uint2 pk = make_uint2(pack_bf16x2(d0, d1), pack_bf16x2(d2, d3));
           *(uint2*)(half + r * 128 + ((chunk ^ (r & 7)) << 4) + hoff) = pk;
         }

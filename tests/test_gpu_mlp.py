@@ -107,3 +107,39 @@ def test_estimator_gain_on_reactive_stream(tdbmod):
     ratio = est_at_skips / true_at_skips
     assert np.all((ratio > 0.8) & (ratio < 1.25)), (ratio.min(), ratio.max())
     assert any(a != "none" for a, _ in acts_b[150:]), "the gated phase should include a control action"
+
+
+@cuda
+def test_estimator_gain_in_device_time_stochastic(tdbmod):
+    """What the learned estimator buys, in device time (CUDA events per phase), on the
+    stochastic stream (256 x 128 x 512, BF16 projection), where the exact error is a full
+    pass over a 67 MB snapshot.  A records exact errors for 150 steps and fits the
+    estimator; then A gates the exact error while B evaluates it every step, for 100 more
+    steps.  A takes B's decisions at every step, evaluates the error exactly on at most a
+    third of the gated steps, and spends less device time than B on the error phase and on
+    the whole step."""
+    wl = S.make_workload("stochastic")
+    w = wl.weights
+    steps, fit_at = 250, 150
+    snaps = [wl.snapshot(k, device="cuda") for k in range(steps + 1)]
+    kw = dict(rank_max=wl.rank_max, weights=w, eps_th=wl.eps_th, gamma_th=wl.gamma_th, precision="bf16",
+              error_every=20)
+    A = tdbmod.TDB(wl.dims, wl.rank, error_mode="mlp", **kw).init(snaps[0])
+    B = tdbmod.TDB(wl.dims, wl.rank, error_mode="exact", **kw).init(snaps[0])
+    for k in range(1, steps + 1):
+        ia = A.push(snaps[k])
+        ib = B.push(snaps[k])
+        assert (ia["action"], ia["ranks"]) == (ib["action"], ib["ranks"]), k
+        if k == fit_at:
+            loss = A.estimator_fit(iters=2000, lr=3e-3, seed=7, gate=0.9)
+            assert loss < 0.1, loss
+            A.set_profiling(True)
+            B.set_profiling(True)
+    gated = steps - fit_at
+    exact_after = A.counters()["exact_evals"] - fit_at
+    assert exact_after <= gated / 3, exact_after
+    pa, pb = A.profile(), B.profile()
+    assert pa["steps"] == pb["steps"] == gated, (pa["steps"], pb["steps"])
+    tot = lambda pr: pr["ms_project"] + pr["ms_update"] + pr["ms_error"]
+    assert pa["ms_error"] < pb["ms_error"], (pa, pb)
+    assert tot(pa) < tot(pb), (pa, pb)
