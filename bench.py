@@ -42,7 +42,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="tdb", choices=["tdb", "reference"])
     ap.add_argument("--workload", default="stochastic",
-                    choices=["reactive", "stochastic", "channel", "analytic", "runge", "reactive_dbo", "batch"])
+                    choices=["reactive", "stochastic", "channel", "analytic", "runge", "reactive_dbo", "reactive_tdb2", "batch"])
     ap.add_argument("--precision", default="auto", choices=["auto", "bf16", "fp32", "fp64"])
     ap.add_argument("--error-mode", default="auto", choices=["auto", "exact", "mlp", "every_k"])
     ap.add_argument("--integrator", default="euler", choices=["euler", "heun", "rk2_central"],

@@ -896,7 +896,8 @@ tdb_status seed_estimator(tdb_ctx* ctx, const Tc* V) {
   return TDB_OK;
 }
 
-// Largest discarded HOSVD energy among modes below their caps (lowest mode on ties),
+// Largest discarded HOSVD energy among modes below their caps (lowest mode on ties, energies
+// equal to 1e-9 relative counting as tied),
 // then other modes follow until r_n <= prod_{m != n} r_m holds.
 bool raise_one(tdb_ctx* ctx, const std::vector<int>& r, std::vector<int>& out) {
   auto disc = [&](int n, int rn) {
@@ -912,7 +913,8 @@ bool raise_one(tdb_ctx* ctx, const std::vector<int>& r, std::vector<int>& out) {
     for (int n = 0; n < ctx->p; ++n) {
       if (n == exclude || out[n] >= ctx->cap[n]) continue;
       double d = disc(n, out[n]);
-      if (d > bv) { bv = d; best = n; }
+      // a later mode wins only by more than rounding (equal spectra of a symmetric field)
+      if (best < 0 || d > bv * (1.0 + 1e-9)) { bv = d; best = n; }
     }
     return best;
   };

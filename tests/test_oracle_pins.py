@@ -444,7 +444,8 @@ def test_rank_from_core_counts_the_error_in_the_denominator():
 
 def test_controller_raise_ties_go_to_the_lowest_mode():
     """Equal discarded HOSVD energy in every mode: the increment rule raises mode 1 (the
-    lowest index), and the product bound needs no other mode to follow."""
+    lowest index), and the product bound needs no other mode to follow.  Energies equal to
+    1e-9 relative count as equal (rounding of equal spectra)."""
     lam = np.array([1.0, 0.5, 0.25, 0.125])
     w = [np.full(4, 0.25)] * 3
     ctrl = O.Controller(O.ControllerConfig(eps_th=1.0, gamma_th=99.0, slope_window=3, rank_max=[4, 4, 4]),
@@ -452,6 +453,12 @@ def test_controller_raise_ties_go_to_the_lowest_mode():
     assert ctrl._raise_one([2, 2, 2], [lam, lam, lam]) == [3, 2, 2]
     # unequal: the mode that discards most is raised
     assert ctrl._raise_one([2, 2, 2], [lam, lam, np.array([1.0, 0.5, 0.5, 0.5])]) == [2, 2, 3]
+    # equal up to rounding (a symmetric field's modes): still a tie, the lowest mode is raised;
+    # a difference well above rounding decides
+    lam_up = lam * np.array([1.0, 1.0, 1.0 + 1e-13, 1.0 + 1e-13])
+    assert ctrl._raise_one([2, 2, 2], [lam, lam_up, lam]) == [3, 2, 2]
+    lam_more = lam * np.array([1.0, 1.0, 1.0 + 1e-4, 1.0 + 1e-4])
+    assert ctrl._raise_one([2, 2, 2], [lam, lam_more, lam]) == [2, 3, 2]
 
 
 def test_controller_slope_window_restarts_after_reinit():
