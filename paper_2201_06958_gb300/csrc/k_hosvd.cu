@@ -330,11 +330,33 @@ __global__ void k_si_cholinv(const double* __restrict__ G, int m, double shift0,
     if (good) break;
     if (attempt == 2 && threadIdx.x == 0) atomicOr(flags, kFlagEigNoConv);
   }
-  trinv_lower_smem_t<T>(S, Li, 64, m);
+  // Li = L^{-1} by forward substitution on all columns at once: after step k row k of Li is
+  // final (scaled by 1/L_kk) and is taken out of the rows below it (one FMA per entry,
+  // spread over the block, instead of one thread per column)
+  __shared__ T dinv[64];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) dinv[i] = T(1) / S[i + 64 * i];
+  for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
+    const int i = e % m, j = e / m;
+    Li[i + 64 * j] = (i == j) ? T(1) : T(0);
+  }
+  __syncthreads();
+  for (int k = 0; k < m; ++k) {
+    for (int j = threadIdx.x; j <= k; j += blockDim.x) Li[k + 64 * j] *= dinv[k];
+    __syncthreads();
+    const int rows = m - k - 1, cols = k + 1;
+    for (int e = threadIdx.x; e < rows * cols; e += blockDim.x) {
+      const int i = k + 1 + e / cols, j = e % cols;
+      Li[i + 64 * j] -= S[i + 64 * k] * Li[k + 64 * j];
+    }
+    __syncthreads();
+  }
+  __shared__ double dinvd[64];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) dinvd[i] = 1.0 / d[i];
+  __syncthreads();
   for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
     int i = e % m, j = e / m;
     // Rinv = D^{-1} L^{-T}:  Rinv[i][j] = Li[j][i] / d[i]
-    Rinv[i + (int64_t)m * j] = (j >= i) ? (double)Li[j + 64 * i] / d[i] : 0.0;
+    Rinv[i + (int64_t)m * j] = (j >= i) ? (double)Li[j + 64 * i] * dinvd[i] : 0.0;
   }
 }
 
@@ -474,7 +496,10 @@ tdb_status eig_subspace(const T* Cc, const double* C64, int n, int k, int iters,
     cudaFuncSetAttribute(k_jacobi_small_full<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     attr2 = true;
   }
-  T tol = sizeof(T) == 8 ? T(1e-15) : T(1e-6);
+  // Rayleigh-Ritz Jacobi: to the rounding floor from a cold start; from a warm start (the
+  // refinement of a float solve) off-diagonal mass 1e-26 of the diagonal's suffices (the
+  // Ritz values are then refined as Rayleigh quotients against the double Gram)
+  T tol = sizeof(T) == 8 ? (Q0 ? T(1e-13) : T(1e-15)) : T(1e-6);
   k_jacobi_small_full<T><<<1, 512, sm, s>>>(ws.H, m, ws.JA, ws.JV, 30, tol, flags); count_launch();
   // Ritz vectors X = Q S  (S = JV, mm x mm with ld mm; use its first m rows)
   k_si_ritz<T><<<(int)std::min<int64_t>(((int64_t)n * mm + 255) / 256, 1024), 256, 0, s>>>(ws.Q, ws.JV, n, m, mm, ws.X); count_launch();
