@@ -463,9 +463,12 @@ class StepRecord:
     cr: float
 
 
-# Relative difference below which two modes' discarded HOSVD energies count as equal in the
-# raise-one rule (rounding of equal spectra, e.g. the three modes of a symmetric field).
+# Difference below which two modes' discarded HOSVD energy fractions (1 - kept/total) count
+# as equal in the raise-one rule: rounding of equal spectra (the three modes of a symmetric
+# field) reaches the fractions as an absolute error near the double unit, so the band is
+# 1e-9 relative plus 1e-12 absolute.
 TIE_REL = 1e-9
+TIE_ABS = 1e-12
 
 
 class Controller:
@@ -476,7 +479,7 @@ class Controller:
     (ii)  If the re-initialised error is still above epsilon_th, raise the ranks to
           those the HOSVD spectrum asks for at gamma_th (never lower), and if that
           changes nothing raise by one the mode with the largest discarded HOSVD
-          energy (lowest mode on ties, equal to 1e-9 relative; other modes follow where the product bound
+          energy (lowest mode on ties, within 1e-9 relative + 1e-12; other modes follow where the product bound
           r_n <= prod_{m != n} r_m requires it); re-initialise; repeat until epsilon <=
           epsilon_th or every rank is at its cap.
     (iii) Otherwise record epsilon in the slope window.  If some mode captures more
@@ -512,9 +515,9 @@ class Controller:
                 if n in exclude or new[n] >= self.caps[n]:
                     continue
                 d = self._discarded(lam[n], new[n])
-                # a later mode wins only by more than rounding: energies equal to 1e-9
-                # relative are a tie (modes of a symmetric field), and ties go to the lowest
-                if best < 0 or d > best_val * (1.0 + TIE_REL):
+                # a later mode wins only by more than rounding: fractions within the tie band
+                # are equal (modes of a symmetric field), and ties go to the lowest mode
+                if best < 0 or d > best_val * (1.0 + TIE_REL) + TIE_ABS:
                     best, best_val = n, d
             return best
         new = list(r)

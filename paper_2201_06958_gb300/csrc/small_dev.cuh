@@ -2,6 +2,7 @@
 // cyclic Jacobi, Cholesky and triangular inverse.
 #pragma once
 #include "common.cuh"
+#include "fastrcp.cuh"
 
 namespace tdb {
 
@@ -45,10 +46,22 @@ __device__ __noinline__ int jacobi_smem(T* A, T* V, int lda, int n, int max_swee
         T c = 1, s = 0;
         const T thr = tol * T(1e-3);   // skip rotations of negligible pairs (no square root, compute type)
         if (apq != T(0) && apq * apq > thr * thr * fabs(app * aqq)) {
-          T theta = (aqq - app) / (T(2) * apq);
-          T t = (theta >= 0 ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
-          c = T(1) / sqrt(t * t + T(1));
-          s = t * c;
+          if constexpr (sizeof(T) == 8) {
+            // the same formulas with the Newton-refined reciprocal and reciprocal square root
+            // (FP64 division and square root are long sequences here; this runs per pair per round)
+            const double theta = (aqq - app) * drcp(2.0 * apq);
+            const double at = fabs(theta);
+            const double x = fma(at, at, 1.0);
+            const double root = at < 1e150 ? x * drsqrt(x) : at;      // sqrt(theta^2 + 1)
+            const double t = (theta >= 0 ? 1.0 : -1.0) * drcp(at + root);
+            c = drsqrt(fma(t, t, 1.0));
+            s = t * c;
+          } else {
+            T theta = (aqq - app) / (T(2) * apq);
+            T t = (theta >= 0 ? T(1) : T(-1)) / (fabs(theta) + sqrt(theta * theta + T(1)));
+            c = T(1) / sqrt(t * t + T(1));
+            s = t * c;
+          }
         }
         cs[2 * k] = c; cs[2 * k + 1] = s;
         pq[2 * k] = p; pq[2 * k + 1] = q;
@@ -88,15 +101,24 @@ template <typename T>
 __device__ __forceinline__ bool chol_smem_t(T* S, int lda, int r, bool* ok_sh) {
   if (threadIdx.x == 0) *ok_sh = true;
   __syncthreads();
+  __shared__ T inv_dk;
   for (int k = 0; k < r; ++k) {
     if (threadIdx.x == 0) {
       T d = S[k + lda * k];
       if (!(d > T(0))) { *ok_sh = false; d = T(1); }
-      S[k + lda * k] = sqrt(d);
+      if constexpr (sizeof(T) == 8) {
+        const double y = drsqrt(d);     // one reciprocal square root per pivot (Newton-refined)
+        S[k + lda * k] = d * y;
+        inv_dk = y;
+      } else {
+        const T sd = sqrt(d);
+        S[k + lda * k] = sd;
+        inv_dk = T(1) / sd;
+      }
     }
     __syncthreads();
-    T dk = S[k + lda * k];
-    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) S[i + lda * k] /= dk;
+    const T ik = inv_dk;
+    for (int i = k + 1 + threadIdx.x; i < r; i += blockDim.x) S[i + lda * k] *= ik;
     __syncthreads();
     for (int e = threadIdx.x; e < (r - k - 1) * (r - k - 1); e += blockDim.x) {
       int i = k + 1 + e % (r - k - 1), j = k + 1 + e / (r - k - 1);

@@ -896,8 +896,8 @@ tdb_status seed_estimator(tdb_ctx* ctx, const Tc* V) {
   return TDB_OK;
 }
 
-// Largest discarded HOSVD energy among modes below their caps (lowest mode on ties, energies
-// equal to 1e-9 relative counting as tied),
+// Largest discarded HOSVD energy among modes below their caps (lowest mode on ties, fractions
+// within 1e-9 relative + 1e-12 counting as tied),
 // then other modes follow until r_n <= prod_{m != n} r_m holds.
 bool raise_one(tdb_ctx* ctx, const std::vector<int>& r, std::vector<int>& out) {
   auto disc = [&](int n, int rn) {
@@ -913,8 +913,9 @@ bool raise_one(tdb_ctx* ctx, const std::vector<int>& r, std::vector<int>& out) {
     for (int n = 0; n < ctx->p; ++n) {
       if (n == exclude || out[n] >= ctx->cap[n]) continue;
       double d = disc(n, out[n]);
-      // a later mode wins only by more than rounding (equal spectra of a symmetric field)
-      if (best < 0 || d > bv * (1.0 + 1e-9)) { bv = d; best = n; }
+      // a later mode wins only by more than rounding: discarded fractions within 1e-9
+      // relative + 1e-12 are tied (equal spectra of a symmetric field)
+      if (best < 0 || d > bv * (1.0 + 1e-9) + 1e-12) { bv = d; best = n; }
     }
     return best;
   };

@@ -444,8 +444,8 @@ def test_rank_from_core_counts_the_error_in_the_denominator():
 
 def test_controller_raise_ties_go_to_the_lowest_mode():
     """Equal discarded HOSVD energy in every mode: the increment rule raises mode 1 (the
-    lowest index), and the product bound needs no other mode to follow.  Energies equal to
-    1e-9 relative count as equal (rounding of equal spectra)."""
+    lowest index), and the product bound needs no other mode to follow.  Fractions within
+    1e-9 relative + 1e-12 count as equal (rounding of equal spectra)."""
     lam = np.array([1.0, 0.5, 0.25, 0.125])
     w = [np.full(4, 0.25)] * 3
     ctrl = O.Controller(O.ControllerConfig(eps_th=1.0, gamma_th=99.0, slope_window=3, rank_max=[4, 4, 4]),
@@ -459,6 +459,11 @@ def test_controller_raise_ties_go_to_the_lowest_mode():
     assert ctrl._raise_one([2, 2, 2], [lam, lam_up, lam]) == [3, 2, 2]
     lam_more = lam * np.array([1.0, 1.0, 1.0 + 1e-4, 1.0 + 1e-4])
     assert ctrl._raise_one([2, 2, 2], [lam, lam_more, lam]) == [2, 3, 2]
+    # small discarded fractions (1.3e-7) whose rounding-level absolute difference (7e-16) is
+    # 5e-9 of them: still a tie; a difference of 1e-10 absolute decides
+    tail = np.array([1.0, 0.5, 1e-7, 1e-7])
+    assert ctrl._raise_one([2, 2, 2], [tail, tail + np.array([0, 0, 1e-15, 0]), tail]) == [3, 2, 2]
+    assert ctrl._raise_one([2, 2, 2], [tail, tail + np.array([0, 0, 1.5e-10, 0]), tail]) == [2, 3, 2]
 
 
 def test_controller_slope_window_restarts_after_reinit():
