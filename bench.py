@@ -729,6 +729,8 @@ def run_batch(args, world, rank, local):
     time.sleep(0.3)
     stream = torch.cuda.current_stream(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.profile_region:
+        torch.cuda.cudart().cudaProfilerStart()
     t0 = time.perf_counter()
     e0.record(stream)
     for k in range(W + 1, W + K + 1):
@@ -738,6 +740,8 @@ def run_batch(args, world, rank, local):
     e1.record(stream)
     torch.cuda.synchronize()
     host_s = time.perf_counter() - t0
+    if args.profile_region:
+        torch.cuda.cudart().cudaProfilerStop()
     clocks = sampler.stop()
     launches = lib.tdb_kernel_launches() - l0
     ms = e0.elapsed_time(e1)
@@ -759,6 +763,7 @@ def run_batch(args, world, rank, local):
                    "members": len(ctxs), "members_bf16": nbf16,
                    "members_padded": sum(1 for wl in members if wl.dims[0] % 4 != 0),
                    "elements_per_step": total, "api": "batch graph",
+                   "grid_cap_per_member": max(8, torch.cuda.get_device_properties(dev).multi_processor_count // 8),
                    "ingest": "torch._foreach_copy_ of the resident snapshots into the slots, timed",
                    "parallelism": f"replicas x{world}"},
         "estimator": dict(est_info, exact_eval_fraction=exact / max(len(ctxs) * (K + W), 1)),

@@ -1109,7 +1109,8 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   // persistent grid: for every tile position the same number of CTAs (at most one per SM
   // in all), each walking a strided set of the slices; how many is the tuner's choice
-  const int cmax = std::max(1, std::min(nslice, std::min(nsm, 1024) / P.nq12));
+  int cmax = std::max(1, std::min(nslice, std::min(nsm, 1024) / P.nq12));
+  if (plan.grid_cap > 0) cmax = std::max(1, std::min(cmax, plan.grid_cap / P.nq12));
   P.b1_bytes = 2 * r1pad * 128;
   P.b2_bytes = 2 * r2pad * 128;
   const int fixed = smem_fixed_bytes(P.b1_bytes, P.b2_bytes);
