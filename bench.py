@@ -763,7 +763,6 @@ def run_batch(args, world, rank, local):
                    "members": len(ctxs), "members_bf16": nbf16,
                    "members_padded": sum(1 for wl in members if wl.dims[0] % 4 != 0),
                    "elements_per_step": total, "api": "batch graph",
-                   "grid_cap_per_member": max(8, torch.cuda.get_device_properties(dev).multi_processor_count // 8),
                    "ingest": "torch._foreach_copy_ of the resident snapshots into the slots, timed",
                    "parallelism": f"replicas x{world}"},
         "estimator": dict(est_info, exact_eval_fraction=exact / max(len(ctxs) * (K + W), 1)),

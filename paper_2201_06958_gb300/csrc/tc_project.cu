@@ -641,7 +641,12 @@ struct FinArgs {
   const float* A3;       // N3 x r3 (null: two modes, B = [1])
   const float* A4;       // N4 x r4 (null: three modes)
   int N3, r3, N4, r4, J;
-  float* Z1;             // N2 x r1 x S, i2 fastest (written when nq1 > 1)
+  float* Z1;             // N2 x r1 x S, i2 fastest (written when nq1 > 1 and W is not fused)
+  // W = Z1 x_2 A_2^T (r1 x r2 x S: Y_3 for three modes) formed here when a first-side CTA
+  // holds whole i2 columns (te1 = N2 floor(256 / N2) elements, N2 <= 256)
+  float* W;
+  const float* A2;
+  int fuse_w, te1;
   float* Y2;
   float* Y1;
   float* part;           // [tile][split][J][256]
@@ -677,11 +682,24 @@ __global__ void __launch_bounds__(FS_TE) k_tc_finish_sk(FinArgs f) {
   }
   const bool first = tile < f.nt1;
   const int64_t ne = first ? (int64_t)f.r1 * f.N2 : (int64_t)f.N1 * f.r2;
-  const int64_t e = (int64_t)(first ? tile : tile - f.nt1) * FS_TE + tid;
-  const bool in = e < ne;
+  const int te = first ? f.te1 : FS_TE;                // elements per CTA on this side
+  const int64_t e = (int64_t)(first ? tile : tile - f.nt1) * te + tid;
+  const bool in = tid < te && e < ne;
+  const bool fw = first && f.fuse_w;
+  const int Jp0 = (f.J + 3) & ~3;
+  float* zs = fs_sm + FS_SC * Jp0;                     // fw: the chunk's z values [FS_SC][FS_TE]
+  float* a2s = zs + FS_SC * FS_TE;                     // fw: A_2 (N2 x r2, ld N2 + 1)
+  const int na = fw ? te / f.N2 : 0;                   // a1 values this CTA holds whole
+  const int a1_lo = fw ? tile * na : 0;
+  if (fw) {
+    for (int idx = tid; idx < f.N2 * f.r2; idx += blockDim.x) {
+      const int i2 = idx % f.N2, b = idx / f.N2;
+      a2s[i2 + (f.N2 + 1) * b] = __ldg(&f.A2[i2 + (int64_t)f.N2 * b]);
+    }
+  }
   const int nq = first ? f.nq1 : f.nq2;
   const float* Pp = (first ? f.Z1p : f.Z2p) + (in ? e : 0);
-  const bool write_z = first && f.nq1 > 1;
+  const bool write_z = first && f.nq1 > 1 && !f.fuse_w;
   const int J = f.J, Jp = (J + 3) & ~3;
   const int s_lo = (int)((int64_t)f.S * sp / f.nsplit), s_hi = (int)((int64_t)f.S * (sp + 1) / f.nsplit);
   const int64_t qstride = ne * (int64_t)f.S;
@@ -728,6 +746,11 @@ __global__ void __launch_bounds__(FS_TE) k_tc_finish_sk(FinArgs f) {
         for (int u = 0; u < SC; ++u)
           if (u < sc) f.Z1[e + ne * (int64_t)(s0 + u)] = z[u];
       }
+      if (fw && j0 == 0) {
+        __syncthreads();                                 // the previous chunk's W is done with zs
+#pragma unroll
+        for (int u = 0; u < SC; ++u) zs[u * FS_TE + tid] = (in && u < sc) ? z[u] : 0.f;
+      }
       __syncthreads();
       for (int idx = tid; idx < SC * Jp; idx += blockDim.x) {
         const int sl = idx / Jp, j = idx % Jp;
@@ -746,6 +769,19 @@ __global__ void __launch_bounds__(FS_TE) k_tc_finish_sk(FinArgs f) {
         fs_sm[sl * Jp + j] = bv;
       }
       __syncthreads();
+      if (fw && j0 == 0) {
+        // W[a1, a2, s] = sum_i2 Z1[i2, a1, s] A2[i2, a2] for this CTA's whole columns a1
+        const int nout = na * f.r2 * sc;
+        for (int o = tid; o < nout; o += blockDim.x) {
+          const int b = o % f.r2, rest = o / f.r2, al = rest % na, u = rest / na;
+          const float* zc = zs + u * FS_TE + al * f.N2;
+          const float* ac = a2s + (f.N2 + 1) * b;
+          float w = 0.f;
+          for (int i2 = 0; i2 < f.N2; ++i2) w = fmaf(zc[i2], ac[i2], w);
+          const int a1 = a1_lo + al;
+          if (a1 < f.r1) f.W[a1 + (int64_t)f.r1 * (b + (int64_t)f.r2 * (s0 + u))] = w;
+        }
+      }
 #pragma unroll
       for (int u = 0; u < SC; ++u) {
         const float* brow = fs_sm + u * Jp + j0;
@@ -787,8 +823,9 @@ __global__ void __launch_bounds__(256) k_tc_finish_red(FinArgs f) {
     const int j = rem / FS_TE, x = rem % FS_TE;
     const bool first = tile < f.nt1;
     const int64_t ne = first ? (int64_t)f.r1 * f.N2 : (int64_t)f.N1 * f.r2;
-    const int64_t e = (int64_t)(first ? tile : tile - f.nt1) * FS_TE + x;
-    if (e >= ne) continue;
+    const int te = first ? f.te1 : FS_TE;
+    const int64_t e = (int64_t)(first ? tile : tile - f.nt1) * te + x;
+    if (x >= te || e >= ne) continue;
     const float* base = f.part + (int64_t)tile * f.nsplit * per_tile + (int64_t)j * FS_TE + x;
     float vals[FS_SPLIT_MAX];
 #pragma unroll
@@ -1109,8 +1146,7 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
   // persistent grid: for every tile position the same number of CTAs (at most one per SM
   // in all), each walking a strided set of the slices; how many is the tuner's choice
-  int cmax = std::max(1, std::min(nslice, std::min(nsm, 1024) / P.nq12));
-  if (plan.grid_cap > 0) cmax = std::max(1, std::min(cmax, plan.grid_cap / P.nq12));
+  const int cmax = std::max(1, std::min(nslice, std::min(nsm, 1024) / P.nq12));
   P.b1_bytes = 2 * r1pad * 128;
   P.b2_bytes = 2 * r2pad * 128;
   const int fixed = smem_fixed_bytes(P.b1_bytes, P.b2_bytes);
@@ -1156,7 +1192,10 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   // finish: Y_1, Y_2 (and Z1) from the tile partials, the slices contracted with
   // B = A_3 (x A_4); then Y_3 (three modes) or W = Z1 x_2 A_2^T (four modes) per slice
   const int J = p == 2 ? 1 : (p == 3 ? r[2] : r[2] * r[3]);
-  const int nt1 = (int)(((int64_t)r[0] * N2 + FS_TE - 1) / FS_TE);
+  // W = Z1 x_2 A_2^T inside the finish when its first-side CTAs can hold whole i2 columns
+  const bool fuse_w = p >= 3 && N2 <= FS_TE;
+  const int te1 = fuse_w ? N2 * (FS_TE / N2) : FS_TE;
+  const int nt1 = (int)(((int64_t)r[0] * N2 + te1 - 1) / te1);
   const int nt2 = (int)(((int64_t)N1 * r[1] + FS_TE - 1) / FS_TE);
   if (J > FS_JMAX) {
     err = "finish: r_3 r_4 above 128";
@@ -1186,6 +1225,10 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   f.r4 = p >= 4 ? r[3] : 1;
   f.J = J;
   f.Z1 = Z1;
+  f.W = p == 3 ? Y[2] : scratch;
+  f.A2 = (const float*)A[1];
+  f.fuse_w = fuse_w ? 1 : 0;
+  f.te1 = te1;
   f.Y2 = Y[1];
   f.Y1 = Y[0];
   f.part = plan.fpart;
@@ -1194,7 +1237,19 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   f.npart = plan.npart;
   f.span = nullptr;
   f.dv2 = dv2;
-  const size_t fsm = sizeof(float) * FS_SC * ((J + 3) & ~3);
+  const size_t fsm = sizeof(float) * (FS_SC * ((J + 3) & ~3) +
+                                      (fuse_w ? FS_SC * FS_TE + (size_t)(N2 + 1) * r[1] : 0));
+  if (fsm > 48 * 1024) {
+    static bool fs_attr = false;
+    if (!fs_attr) {
+      const int lim = 100 * 1024;
+      cudaFuncSetAttribute(k_tc_finish_sk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      cudaFuncSetAttribute(k_tc_finish_sk<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      cudaFuncSetAttribute(k_tc_finish_sk<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      cudaFuncSetAttribute(k_tc_finish_sk<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+      fs_attr = true;
+    }
+  }
   const int nqm = std::max(nq1, nq2);
   auto launch_finish = [&](int nsplit) {
     f.nsplit = nsplit;
@@ -1242,12 +1297,14 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   f.span = P.span;
   launch_finish(nsplit_for(plan.tuned ? plan.fin_target : FS_CTAS));
   if (p >= 3) {
-    // Z1 summed over the mode-1 tiles: the partials themselves when there is one tile
-    const float* z1 = nq1 > 1 ? Z1 : plan.z1p;
-    float* out = p == 3 ? Y[2] : scratch;
-    k_tc_finish_b<<<std::min(nslice, 152 * 8), 256, kFinishBSmem, s>>>(z1, N2, nslice, r[0], r[1],
-                                                                       (const float*)A[1], out);
-    count_launch();
+    if (!fuse_w) {
+      // Z1 summed over the mode-1 tiles: the partials themselves when there is one tile
+      const float* z1 = nq1 > 1 ? Z1 : plan.z1p;
+      float* out = p == 3 ? Y[2] : scratch;
+      k_tc_finish_b<<<std::min(nslice, 152 * 8), 256, kFinishBSmem, s>>>(z1, N2, nslice, r[0], r[1],
+                                                                         (const float*)A[1], out);
+      count_launch();
+    }
     if (p == 4) {
       // Y_3 = W x_4 A_4^T and Y_4 = W x_3 A_3^T from W = Z1 x_2 A_2^T (r1 x r2 x N3 x N4)
       const int64_t L12 = (int64_t)r[0] * r[1];

@@ -34,8 +34,6 @@ struct TcPlan {
   // profiling: device words {first CTA start, last CTA end, summed spans (ns), launches} of
   // the main kernel, accumulated by the finishing launch; null when not profiling
   unsigned long long* span = nullptr;
-  // CTAs the projection may take in all (a batch member's share of the SMs), 0: the GPU
-  int grid_cap = 0;
 };
 
 bool tc_supported(int p, const int64_t* N, const int* cap, std::string& err);

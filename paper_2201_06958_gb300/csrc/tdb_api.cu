@@ -183,7 +183,6 @@ struct tdb_ctx {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool graph_broken = false;
   bool prof_graph_ok = true;      // profiled steps may be recorded (their events time in a graph)
-  int grid_cap = 0;               // batch member: CTAs its grid-wide kernels may take (0: the GPU)
   bool last_graphed = false;      // the step being finished ran as a graph replay
   bool main_from_start = false;   // its projection kernel is timed from the step's first event
   int64_t graph_replays = 0, graph_records = 0;
@@ -600,9 +599,8 @@ tdb_status exact_error2(tdb_ctx* ctx, const Tc* V, const int* gate = nullptr) {
     src = dst;
   }
   launch_recon_err<Tc>(V, (const Tc*)ctx->Uc[0], src, ctx->r[0], (int)ctx->N[0], ctx->S / ctx->N[0],
-                       (const Tc*)ctx->w1T, (const Tc*)ctx->wcolT, ctx->npart, ctx->redcnt,
-                       ctx->grid_cap > 0 ? std::min(ctx->nblk, ctx->grid_cap) : ctx->nblk, &ctx->rb_dev->err2,
-                       ctx->flags, s, gate);
+                       (const Tc*)ctx->w1T, (const Tc*)ctx->wcolT, ctx->npart, ctx->redcnt, ctx->nblk,
+                       &ctx->rb_dev->err2, ctx->flags, s, gate);
   CHECK_LAUNCH();
   return TDB_OK;
 }
@@ -1080,8 +1078,7 @@ tdb_status fused_update(tdb_ctx* ctx, bool reorth, bool skip_finish, int combine
   a.bar = ctx->bar;
   a.stamps = ctx->prof ? ctx->stamps : nullptr;
   a.flags = ctx->flags;
-  int64_t hint = std::max<int64_t>({ntiles, (int64_t)p * a.gsplit, Rprod / 2048});
-  if (ctx->grid_cap > 0) hint = std::min<int64_t>(hint, ctx->grid_cap);   // a batch member's share
+  const int64_t hint = std::max<int64_t>({ntiles, (int64_t)p * a.gsplit, Rprod / 2048});
   const tdb_status us = launch_update<Tc>(a, (int)std::min<int64_t>(hint, 1 << 20), ctx->stream);
   if (us != TDB_OK) {
     ctx->err = us == TDB_ERR_UNSUPPORTED ? "cooperative launch unsupported" : "fused update launch failed";
@@ -1313,7 +1310,6 @@ uint64_t graph_key(const tdb_ctx* ctx) {
   auto mix = [&](uint64_t v) { k = (k ^ v) * 1099511628211ull; };
   for (int n = 0; n < ctx->p; ++n) mix((uint64_t)ctx->r[n]);
   mix(ctx->prof ? 1 : 0);
-  mix((uint64_t)ctx->grid_cap);
   mix(ctx->warm ? 1 : 0);
   mix((uint64_t)ctx->cfg.error_mode);
   mix(ctx->use_tc ? 1 : 0);
@@ -1986,16 +1982,6 @@ tdb_status tdb_batch_create(tdb_batch** out, tdb_ctx* const* members, int n, int
     delete b;
     return TDB_ERR_CUDA;
   }
-  // every member's grid-wide kernels take at most its stream's share of the SMs, so that
-  // members on different streams run side by side instead of one after another
-  int dev = 0, nsm = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-  const int cap = std::max(8, nsm / ns);
-  for (tdb_ctx* c : b->m) {
-    c->grid_cap = cap;
-    c->tc.grid_cap = cap;
-  }
   *out = b;
   return TDB_OK;
 }
@@ -2111,14 +2097,7 @@ tdb_status tdb_get_graph_counters(const tdb_ctx* ctx, const tdb_batch* b, int64_
   return TDB_OK;
 }
 
-void tdb_batch_destroy(tdb_batch* b) {
-  if (!b) return;
-  for (tdb_ctx* c : b->m) {
-    c->grid_cap = 0;
-    c->tc.grid_cap = 0;
-  }
-  delete b;
-}
+void tdb_batch_destroy(tdb_batch* b) { delete b; }
 
 tdb_status tdb_tc_tuning(const tdb_ctx* ctx, int* ctas, int* fin_target, int* ncand, int* cand, float* cand_us,
                          int* fin_cand, float* fin_us) {
