@@ -184,7 +184,10 @@ tdb_status tdb_init_from_factors(tdb_ctx** ctx, const tdb_config* cfg, void* wor
  * stages), re-orthonormalisation, error (Eq. 2.20) per error_mode, and rank control
  * (Sec. 2.5).  V_next is borrowed: it becomes the previous snapshot and must stay
  * unmodified until the next push returns.  info (host, nullable) receives the report;
- * the call synchronises the stream.  Errors: TDB_ERR_INVALID_ARG (null ctx or
+ * the call synchronises the stream.  A (V_next, V_k, V_{k-1}) pointer tuple pushed for
+ * the second time (a ring of input buffers) has its device work recorded as a CUDA graph
+ * and replayed while it recurs (six such graphs kept, least recently used dropped); the
+ * results are those of the unrecorded step.  Errors: TDB_ERR_INVALID_ARG (null ctx or
  * snapshot), TDB_ERR_STATE (before init), TDB_ERR_NONFINITE (a non-finite difference),
  * TDB_ERR_RANK_DEFICIENT (a core Gram or basis Gram not positive definite),
  * TDB_ERR_TIMEOUT (a bounded device wait ran out), TDB_ERR_CUDA; TDB_WARN_RANK_CAP
@@ -401,8 +404,9 @@ tdb_status tdb_tc_tuning(const tdb_ctx* ctx, int* ctas, int* fin_target, int* nc
  *   need three snapshots).  The device work of the step is recorded once per slot parity and
  *   rank configuration as a CUDA graph and replayed afterwards, so a step costs one
  *   launch; the results are those of tdb_push_snapshot on the same snapshots.  Steps
- *   run as tdb_push_snapshot does (not recorded) while profiling is enabled, on the
- *   first step of a tensor-core context, or if the configuration cannot be recorded.
+ *   run unrecorded on the first step of a tensor-core context, while profiling is
+ *   enabled if the runtime cannot time events inside a graph, or if the configuration
+ *   cannot be recorded.
  * ------------------------------------------------------------------------- */
 tdb_status tdb_set_input_slots(tdb_ctx* ctx, const void* slot0, const void* slot1);
 tdb_status tdb_push_slot(tdb_ctx* ctx, int parity, tdb_step_info* info /* nullable, host */);

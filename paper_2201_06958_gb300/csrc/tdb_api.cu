@@ -186,6 +186,20 @@ struct tdb_ctx {
   bool last_graphed = false;      // the step being finished ran as a graph replay
   bool main_from_start = false;   // its projection kernel is timed from the step's first event
   int64_t graph_replays = 0, graph_records = 0;
+  // steps of tdb_push_snapshot, recorded per (V_{k+1}, V_k, V_{k-1}) pointer tuple once
+  // the tuple recurs (a ring of input buffers); tuples seen once run eagerly
+  struct PtrGraph {
+    const void* v[3];
+    uint64_t key;
+    cudaGraphExec_t exec;
+    long long count;
+    uint64_t used;
+  };
+  static constexpr int kPtrGraphs = 6, kPtrSeen = 8;
+  PtrGraph pgraph[kPtrGraphs] = {};
+  const void* pseen[kPtrSeen][3] = {};
+  int pseen_next = 0;
+  uint64_t ptick = 0;
 
   // host state
   const void* V_prev = nullptr;
@@ -201,6 +215,8 @@ struct tdb_ctx {
   ~tdb_ctx() {
     for (int i = 0; i < 2; ++i)
       if (gexec[i]) cudaGraphExecDestroy(gexec[i]);
+    for (auto& g : pgraph)
+      if (g.exec) cudaGraphExecDestroy(g.exec);
     if (cap_stream) cudaStreamDestroy(cap_stream);
     if (aux) cudaStreamDestroy(aux);
     if (ev_fork) cudaEventDestroy(ev_fork);
@@ -1324,11 +1340,14 @@ void drop_graphs(tdb_ctx* ctx) {
   }
 }
 
-// Record the step on the context's stream into an executable graph (parity = slot of V_{k+1}).
+
+// Record the step with V_{k+1} = Vn, V_k = Vp (and V_{k-1} = Vpp, central differences)
+// into an executable graph; count receives the library kernels it holds.
 // (The caller's stream may be the legacy default stream, which cannot be captured: the
 // work is recorded on a private stream and the graph launched on the caller's.)
 template <typename Tc>
-tdb_status capture_step(tdb_ctx* ctx, int parity, cudaGraphExec_t* out) {
+tdb_status capture_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, const Tc* Vpp, cudaGraphExec_t* out,
+                        long long* count) {
   if (!ctx->cap_stream && cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
     cudaGetLastError();
     ctx->err = "capture stream unavailable";
@@ -1344,9 +1363,9 @@ tdb_status capture_step(tdb_ctx* ctx, int parity, cudaGraphExec_t* out) {
   cudaStream_t own = ctx->stream;
   ctx->stream = s;
   const long long l0 = launches_so_far();
-  tdb_status st = enqueue_step<Tc>(ctx, (const Tc*)ctx->slot[parity], (const Tc*)ctx->slot[1 - parity], true);
-  ctx->gcount[parity] = launches_so_far() - l0;
-  count_launch(-(int)ctx->gcount[parity]);     // recorded, not launched; counted per replay
+  tdb_status st = enqueue_step<Tc>(ctx, Vn, Vp, true, Vpp);
+  *count = launches_so_far() - l0;
+  count_launch(-(int)*count);     // recorded, not launched; counted per replay
   ctx->stream = own;
   cudaError_t e = cudaStreamEndCapture(s, &g);
   if (st != TDB_OK || e != cudaSuccess || !g) {
@@ -1376,7 +1395,8 @@ tdb_status step_slot(tdb_ctx* ctx, int parity, tdb_step_info* info) {
   if (!ctx->gexec[parity] || ctx->gkey[parity] != key) {
     if (ctx->gexec[parity]) cudaGraphExecDestroy(ctx->gexec[parity]);
     ctx->gexec[parity] = nullptr;
-    if (capture_step<Tc>(ctx, parity, &ctx->gexec[parity]) != TDB_OK) {
+    if (capture_step<Tc>(ctx, Vn, (const Tc*)ctx->slot[1 - parity], (const Tc*)nullptr, &ctx->gexec[parity],
+                         &ctx->gcount[parity]) != TDB_OK) {
       // stream capture unavailable for this configuration: run this and later steps eagerly
       ctx->graph_broken = true;
       ctx->gexec[parity] = nullptr;
@@ -1391,6 +1411,67 @@ tdb_status step_slot(tdb_ctx* ctx, int parity, tdb_step_info* info) {
   CK(cudaGraphLaunch(ctx->gexec[parity], ctx->stream));
   ctx->graph_replays++;
   count_launch((int)ctx->gcount[parity]);
+  CK(cudaStreamSynchronize(ctx->stream));
+  TRY(readback_done(ctx));
+  return finish_step<Tc>(ctx, Vn, info);
+}
+
+// tdb_push_snapshot: a (V_{k+1}, V_k, V_{k-1}) tuple met for the second time is recorded
+// (the step's key as for slots, the pointers besides) and replayed while it recurs; the
+// least recently used of the kept graphs gives way to a new one.
+template <typename Tc>
+tdb_status step_pointer(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
+  const void* tup[3] = {Vn, ctx->V_prev, ctx->V_prev2};
+  const bool can_graph = !ctx->graph_broken && (!ctx->prof || ctx->prof_graph_ok) && (!ctx->use_tc || ctx->tc.wsl_ready);
+  auto same = [&](const void* const* v) { return v[0] == tup[0] && v[1] == tup[1] && v[2] == tup[2]; };
+  tdb_ctx::PtrGraph* hit = nullptr;
+  if (can_graph)
+    for (auto& g : ctx->pgraph)
+      if (g.exec && same(g.v)) hit = &g;
+  bool seen = false;
+  if (can_graph && !hit)
+    for (auto& v : ctx->pseen) seen = seen || same(v);
+  if (!hit && !seen) {
+    if (can_graph) {
+      memcpy(ctx->pseen[ctx->pseen_next], tup, sizeof(tup));
+      ctx->pseen_next = (ctx->pseen_next + 1) % tdb_ctx::kPtrSeen;
+    }
+    return step_impl<Tc>(ctx, Vn, info);
+  }
+  ctx->last_graphed = true;
+  prepare_step(ctx);
+  const uint64_t key = graph_key(ctx);
+  if (!hit) {
+    for (auto& g : ctx->pgraph)
+      if (!hit && !g.exec) hit = &g;
+    if (!hit) {
+      hit = &ctx->pgraph[0];
+      for (auto& g : ctx->pgraph)
+        if (g.used < hit->used) hit = &g;
+      cudaGraphExecDestroy(hit->exec);
+    }
+    *hit = {};
+    memcpy(hit->v, tup, sizeof(tup));
+  }
+  if (!hit->exec || hit->key != key) {
+    if (hit->exec) cudaGraphExecDestroy(hit->exec);
+    hit->exec = nullptr;
+    if (capture_step<Tc>(ctx, Vn, (const Tc*)tup[1], (const Tc*)tup[2], &hit->exec, &hit->count) != TDB_OK) {
+      ctx->graph_broken = true;
+      *hit = {};
+      ctx->last_graphed = false;
+      TRY(enqueue_step<Tc>(ctx, Vn, (const Tc*)tup[1], false, (const Tc*)tup[2]));
+      CK(cudaStreamSynchronize(ctx->stream));
+      TRY(readback_done(ctx));
+      return finish_step<Tc>(ctx, Vn, info);
+    }
+    hit->key = key;
+    ctx->graph_records++;
+  }
+  hit->used = ++ctx->ptick;
+  CK(cudaGraphLaunch(hit->exec, ctx->stream));
+  ctx->graph_replays++;
+  count_launch((int)hit->count);
   CK(cudaStreamSynchronize(ctx->stream));
   TRY(readback_done(ctx));
   return finish_step<Tc>(ctx, Vn, info);
@@ -1624,8 +1705,8 @@ tdb_status tdb_push_snapshot(tdb_ctx* ctx, const void* V_next, tdb_step_info* in
   if (!ctx->ready) { ctx->err = "push before init"; return TDB_ERR_STATE; }
   if (!V_next) { ctx->err = "null snapshot"; return TDB_ERR_INVALID_ARG; }
   ctx->last_graphed = false;
-  return ctx->f64 ? step_impl<double>(ctx, (const double*)V_next, info)
-                  : step_impl<float>(ctx, (const float*)V_next, info);
+  return ctx->f64 ? step_pointer<double>(ctx, (const double*)V_next, info)
+                  : step_pointer<float>(ctx, (const float*)V_next, info);
 }
 
 tdb_status tdb_reconstruct(tdb_ctx* ctx, void* V_out) {

@@ -4,7 +4,9 @@ tdb_push_slot records a step's device work as a CUDA graph (once per slot parity
 rank configuration) and replays it; a batch records every member's step into one
 graph over several streams.  Neither changes what a step computes, so the step records
 and the final factors must equal those of tdb_push_snapshot on the same snapshots,
-including across control actions (re-initialisations and rank changes re-record)."""
+including across control actions (re-initialisations and rank changes re-record).
+tdb_push_snapshot records a step once its (V_{k+1}, V_k, V_{k-1}) pointer tuple recurs, as a
+ring of input buffers makes it do; its results equal those of pushes that never recur."""
 
 import numpy as np
 import pytest
@@ -133,3 +135,30 @@ def test_profiling_eager_and_recorded(tdbmod):
         assert 0.0 < pr["us_project_span"] < pr["ms_project_main"] * 1e3, pr
     assert B.counters()["graph_replays"] >= 9
     same_factors(A, B)
+
+
+@cuda
+@pytest.mark.parametrize("precision,integrator,ring", [("bf16", "euler", 3), ("fp32", "euler", 3),
+                                                       ("fp32", "rk2_central", 4)])
+def test_pointer_ring_graph_steps_equal_unrecorded_pushes(tdbmod, precision, integrator, ring):
+    wl = S.make_workload("reactive")
+    steps = 60
+    snaps = [wl.snapshot(k, device="cuda") for k in range(steps + 1)]
+    kw = dict(rank_max=wl.rank_max, weights=wl.weights, eps_th=8e-5, gamma_th=99.9, slope_window=5,
+              precision=precision, error_mode="exact", integrator=integrator)
+    A = tdbmod.TDB(wl.dims, wl.rank, **kw).init(snaps[0])
+    bufs = [torch.empty_like(snaps[0]) for _ in range(ring)]
+    bufs[0].copy_(snaps[0])
+    B = tdbmod.TDB(wl.dims, wl.rank, **kw).init(bufs[0])
+    actions = set()
+    for k in range(1, steps + 1):
+        bufs[k % ring].copy_(snaps[k])
+        ib = B.push(bufs[k % ring])
+        ia = A.push(snaps[k])
+        same_info(ia, ib)
+        actions.add(ia["action"])
+    same_factors(A, B)
+    assert actions - {"none"}, "the run should include a control action (re-recording the step)"
+    assert A.counters()["graph_replays"] == 0, A.counters()
+    c = B.counters()
+    assert c["graph_replays"] >= steps - 3 * ring and ring <= c["graph_records"] < steps // 2, c
