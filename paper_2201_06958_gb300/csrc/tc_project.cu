@@ -129,6 +129,7 @@ __device__ __forceinline__ void prefetch_tmap(const CUtensorMap* tm) {
 // Programmatic launch: wait until the stream's previous kernel has completed and its
 // writes are visible (a no-op when the kernel was launched the ordinary way).
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 // Bounded wait on a phase parity.  Returns false (and raises the abort flag) on
 // timeout or when another role already aborted.
@@ -159,6 +160,17 @@ __device__ __forceinline__ bool mbar_wait_warp(uint32_t bar, uint32_t parity, vo
   ok = __shfl_sync(0xffffffffu, ok, 0);
   if (ok) mbar_try_wait(bar, parity);
   return ok != 0;
+}
+
+// L2 policy for the Z partials: kept in L2 against the streamed snapshots (the finishing
+// launch reads them right after this kernel)
+__device__ __forceinline__ uint64_t l2_evict_last_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ void st_l2_keep(float* p, float v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.f32 [%0], %1, %2;" ::"l"(p), "f"(v), "l"(pol) : "memory");
 }
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, int x, int y, int z, uint32_t bar) {
@@ -279,42 +291,44 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (P.span && tid == 0) atomicMin(&P.span[0], global_ns());
+  // the finishing launch may be scheduled now: it waits for this grid before it reads
+  // anything this grid writes
+  if (tid == 0) grid_dep_launch();
   // this CTA's tile position and its first slice
   const int pos = blockIdx.x % P.nq12;
   const int q1 = pos % P.nq1, q2 = pos / P.nq1;
   const int s_first = blockIdx.x / P.nq12;
 
-  // the TMA lane initialises the barriers and issues the first slice's strips at once (every
-  // stage is free); no other thread touches a barrier before the block-wide sync below
-  const bool tma_lane = (warp == TMA_WARP && lane == 0);
+  // lane 0 of the TMA warp initialises the barriers; then lane j (< 8) of that warp, the
+  // owner of stage j, issues the first slice's strip j at once (every stage is free).  No
+  // other warp touches a barrier before the block-wide sync below.
   const int x_tile = q1 * TILE;
-  if (tma_lane) {
-    prefetch_tmap(&tmVn);
-    prefetch_tmap(&tmVp);
-    for (int s = 0; s < NSTAGE; ++s) {
-      mbar_init(smem_u32(&full[s]), 1);
-      mbar_init(smem_u32(&empty[s]), 1);
-    }
-    for (int b = 0; b < 2; ++b) {
-      mbar_init(smem_u32(&bf_full[b]), NUM_CONV_WARPS);
-      mbar_init(smem_u32(&mma_done[b]), 1);
-      mbar_init(smem_u32(&epi_done[b]), NUM_EPI_WARPS);
-    }
-    mbar_init(smem_u32(bimg_full), NUM_EPI_WARPS);
-    *abort_flag = 0;
-    fence_mbar_init();
-    fence_proxy_async();
-    if (s_first < P.nslice) {
-#pragma unroll
-      for (int j = 0; j < NSTRIP; ++j) {
-        const int y = q2 * TILE + j * SUB_I2;
-        if (y >= P.N2) continue;
-        const uint32_t fb = smem_u32(&full[j]);
-        mbar_arrive_expect_tx(fb, STAGE_BYTES);
-        const uint32_t dst = smem_u32(stages + j * STAGE_BYTES);
-        tma_load_3d(dst, &tmVn, x_tile, y, s_first, fb);
-        tma_load_3d(dst + BOX_BYTES, &tmVp, x_tile, y, s_first, fb);
+  if (warp == TMA_WARP) {
+    if (lane == 0) {
+      prefetch_tmap(&tmVn);
+      prefetch_tmap(&tmVp);
+      for (int s = 0; s < NSTAGE; ++s) {
+        mbar_init(smem_u32(&full[s]), 1);
+        mbar_init(smem_u32(&empty[s]), 1);
       }
+      for (int b = 0; b < 2; ++b) {
+        mbar_init(smem_u32(&bf_full[b]), NUM_CONV_WARPS);
+        mbar_init(smem_u32(&mma_done[b]), 1);
+        mbar_init(smem_u32(&epi_done[b]), NUM_EPI_WARPS);
+      }
+      mbar_init(smem_u32(bimg_full), NUM_EPI_WARPS);
+      *abort_flag = 0;
+      fence_mbar_init();
+      fence_proxy_async();
+    }
+    __syncwarp();
+    const int y = q2 * TILE + lane * SUB_I2;
+    if (lane < NSTRIP && s_first < P.nslice && y < P.N2) {
+      const uint32_t fb = smem_u32(&full[lane]);
+      mbar_arrive_expect_tx(fb, STAGE_BYTES);
+      const uint32_t dst = smem_u32(stages + lane * STAGE_BYTES);
+      tma_load_3d(dst, &tmVn, x_tile, y, s_first, fb);
+      tma_load_3d(dst + BOX_BYTES, &tmVp, x_tile, y, s_first, fb);
     }
   }
   if (warp == MMA_WARP) {
@@ -331,39 +345,27 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   double acc_norm = 0.0;
 
   if (warp == TMA_WARP) {
-    if (lane == 0) {
-      // the strips of every slice: strip j goes to stage j (its converter's), once per
-      // slice; strips wholly past N2 are neither loaded nor waited for, on both sides.
-      // Each stage is refilled as soon as its converter releases it, whatever the other
-      // stages do: the lane polls the empty barriers without blocking on any one of them.
+    if (lane < NSTRIP) {
+      // lane j refills stage j with strip j of each of this CTA's slices, as soon as its
+      // converter releases it; the eight lanes poll and issue side by side, so a burst of
+      // releases is refilled at once.  Strips wholly past N2 are neither loaded nor
+      // waited for, on both sides.
+      const int j = lane;
       const int nt = s_first < P.nslice ? (P.nslice - 1 - s_first) / P.cstep + 1 : 0;
-      int tj[NSTRIP];            // per stage: slices loaded so far (the first at the start)
-      int left = 0;
-#pragma unroll
-      for (int j = 0; j < NSTRIP; ++j) {
-        const bool in = q2 * TILE + j * SUB_I2 < P.N2;
-        tj[j] = in ? (nt > 0 ? 1 : 0) : nt;
-        left += nt - tj[j];
-      }
+      const int y = q2 * TILE + j * SUB_I2;
+      const bool in = y < P.N2;
+      int tj = in ? (nt > 0 ? 1 : 0) : nt;      // slices loaded so far (the first at the start)
+      const uint32_t fb = smem_u32(&full[j]), eb = smem_u32(&empty[j]);
+      const uint32_t dst = smem_u32(stages + j * STAGE_BYTES);
       long long t0 = clock64();
       int it = 0;
-      while (left > 0) {
-        bool moved = false;
-#pragma unroll
-        for (int j = 0; j < NSTRIP; ++j) {
-          if (tj[j] < nt && mbar_test_wait(smem_u32(&empty[j]), (tj[j] & 1) ^ 1)) {
-            const uint32_t fb = smem_u32(&full[j]);
-            mbar_arrive_expect_tx(fb, STAGE_BYTES);
-            const uint32_t dst = smem_u32(stages + j * STAGE_BYTES);
-            const int y = q2 * TILE + j * SUB_I2, sl = s_first + tj[j] * P.cstep;
-            tma_load_3d(dst, &tmVn, x_tile, y, sl, fb);
-            tma_load_3d(dst + BOX_BYTES, &tmVp, x_tile, y, sl, fb);
-            ++tj[j];
-            --left;
-            moved = true;
-          }
-        }
-        if (moved) {
+      while (tj < nt) {
+        if (mbar_test_wait(eb, (tj & 1) ^ 1)) {
+          mbar_arrive_expect_tx(fb, STAGE_BYTES);
+          const int sl = s_first + tj * P.cstep;
+          tma_load_3d(dst, &tmVn, x_tile, y, sl, fb);
+          tma_load_3d(dst + BOX_BYTES, &tmVp, x_tile, y, sl, fb);
+          ++tj;
           t0 = clock64();
           continue;
         }
@@ -377,12 +379,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           }
         }
       }
-      // drain: every armed copy has landed before the CTA may leave
-#pragma unroll
-      for (int j = 0; j < NSTRIP; ++j) {
-        if (q2 * TILE + j * SUB_I2 >= P.N2 || tj[j] == 0) continue;
+      // drain: every armed copy of this stage has landed before the CTA may leave
+      if (in && tj > 0) {
         long long t1 = clock64();
-        while (!mbar_try_wait(smem_u32(&full[j]), (tj[j] - 1) & 1) && clock64() - t1 < TIMEOUT_CYCLES) {
+        while (!mbar_try_wait(fb, (tj - 1) & 1) && clock64() - t1 < TIMEOUT_CYCLES) {
         }
       }
     }
@@ -473,6 +473,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       if (lane == 0) mbar_arrive(smem_u32(bimg_full));
     }
     // epilogue: TMEM lanes 32*warp .. 32*warp+31
+    const uint64_t keep = l2_evict_last_policy();
     int t = 0;
     for (int sl = s_first; sl < P.nslice; sl += P.cstep, ++t) {
       const int buf = t & 1;
@@ -490,7 +491,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           float* dst = P.Z1p + ((size_t)q1 * P.nslice + sl) * (size_t)P.r1 * P.N2 + i2;
 #pragma unroll
           for (int a = 0; a < 32; ++a)
-            if (a < P.r1) dst[(size_t)a * P.N2] = v[a] * P.dscale;
+            if (a < P.r1) st_l2_keep(dst + (size_t)a * P.N2, v[a] * P.dscale, keep);
         }
       }
       // Z2 partial, row i1 = q1*128 + 32*warp + lane
@@ -502,7 +503,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           float* dst = P.Z2p + ((size_t)q2 * P.nslice + sl) * (size_t)P.r2 * P.N1 + i1;
 #pragma unroll
           for (int b = 0; b < 32; ++b)
-            if (b < P.r2) dst[(size_t)b * P.N1] = v[b] * P.dscale;
+            if (b < P.r2) st_l2_keep(dst + (size_t)b * P.N1, v[b] * P.dscale, keep);
         }
       }
       tc_fence_before();
@@ -657,16 +658,52 @@ struct FinArgs {
   double* dv2;
 };
 
+// Row stride of A_2 in the fused finish's shared memory: = 4 (mod 32), so that the lanes
+// of a warp (eight columns b x four i2 phases) read 32 different banks.
+__host__ __device__ constexpr int a2_stride(int N2) { return N2 + ((36 - N2 % 32) % 32); }
+
 template <int NQ>   // tiles along the contracted mode, rounded up to a power of two (<= FS_NQ_MAX)
-__global__ void __launch_bounds__(FS_TE) k_tc_finish_sk(FinArgs f) {
+__global__ void __launch_bounds__(FS_TE, 2) k_tc_finish_sk(FinArgs f) {
   constexpr int SC = NQ <= 2 ? FS_SC : (NQ == 4 ? FS_SC / 2 : FS_SC / 4);   // slices per chunk
+  constexpr int BPT = FS_SC * FS_JMAX / FS_TE;      // B values a thread stages per chunk
   extern __shared__ __align__(16) float fs_sm[];    // B rows of a slice chunk: [FS_SC][Jp]
   __shared__ double dsh[32];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) grid_dep_launch();
   const int tile = blockIdx.x / f.nsplit, sp = blockIdx.x % f.nsplit;
-  if (blockIdx.x == 0) {
+  const bool first = tile < f.nt1;
+  const bool fw = first && f.fuse_w;
+  const int Jp0 = (f.J + 3) & ~3;
+  float* zs = fs_sm + FS_SC * Jp0;                     // fw: the chunk's z values [FS_SC][FS_TE]
+  float* a2s = zs + FS_SC * FS_TE;                     // fw: A_2 (N2 x r2, ld a2_stride(N2))
+  const int a2st = a2_stride(f.N2);
+  if (fw) {
+    // A_2 is an input of the step (not written by the main kernel): staged before the wait
+    for (int i0 = tid; i0 < f.N2 * f.r2; i0 += 4 * FS_TE) {
+      float v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[k] = i0 + k * FS_TE < f.N2 * f.r2 ? __ldg(&f.A2[i0 + k * FS_TE]) : 0.f;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int idx = i0 + k * FS_TE;
+        if (idx < f.N2 * f.r2) a2s[idx % f.N2 + a2st * (idx / f.N2)] = v[k];
+      }
+    }
+  }
+  // programmatic launch: the main kernel's results (partials, norms, span words) are
+  // complete and visible after this
+  grid_dep_wait();
+  if (blockIdx.x == gridDim.x - 1) {
+    // ||dV||_W^2: the main kernel's partials, eight loads in flight per thread (in the last
+    // CTA, a second-side one whenever there is one: those form no W)
     double t = 0.0;
-    for (int i = tid; i < f.nnp; i += blockDim.x) t += f.npart[i];
+    for (int i0 = tid; i0 < f.nnp; i0 += 8 * FS_TE) {
+      double v[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) v[k] = i0 + k * FS_TE < f.nnp ? __ldcg(&f.npart[i0 + k * FS_TE]) : 0.0;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) t += v[k];
+    }
     t = block_sum(t, dsh);
     if (tid == 0) *f.dv2 = t;
     if (tid == 0 && f.span) {
@@ -680,23 +717,12 @@ __global__ void __launch_bounds__(FS_TE) k_tc_finish_sk(FinArgs f) {
       f.span[1] = 0ull;
     }
   }
-  const bool first = tile < f.nt1;
   const int64_t ne = first ? (int64_t)f.r1 * f.N2 : (int64_t)f.N1 * f.r2;
   const int te = first ? f.te1 : FS_TE;                // elements per CTA on this side
   const int64_t e = (int64_t)(first ? tile : tile - f.nt1) * te + tid;
   const bool in = tid < te && e < ne;
-  const bool fw = first && f.fuse_w;
-  const int Jp0 = (f.J + 3) & ~3;
-  float* zs = fs_sm + FS_SC * Jp0;                     // fw: the chunk's z values [FS_SC][FS_TE]
-  float* a2s = zs + FS_SC * FS_TE;                     // fw: A_2 (N2 x r2, ld N2 + 1)
   const int na = fw ? te / f.N2 : 0;                   // a1 values this CTA holds whole
   const int a1_lo = fw ? tile * na : 0;
-  if (fw) {
-    for (int idx = tid; idx < f.N2 * f.r2; idx += blockDim.x) {
-      const int i2 = idx % f.N2, b = idx / f.N2;
-      a2s[i2 + (f.N2 + 1) * b] = __ldg(&f.A2[i2 + (int64_t)f.N2 * b]);
-    }
-  }
   const int nq = first ? f.nq1 : f.nq2;
   const float* Pp = (first ? f.Z1p : f.Z2p) + (in ? e : 0);
   const bool write_z = first && f.nq1 > 1 && !f.fuse_w;
@@ -728,6 +754,28 @@ __global__ void __launch_bounds__(FS_TE) k_tc_finish_sk(FinArgs f) {
 #pragma unroll
         for (int q = 0; q < NQ; ++q) raw[u * NQ + q] = (in && u < sc && q < nq) ? __ldcg(pe + qstride * q) : 0.f;
       }
+      // this chunk's B rows, loaded beside the partials (staged in shared memory below)
+      float bpre[BPT];
+#pragma unroll
+      for (int k = 0; k < BPT; ++k) {
+        const int idx = tid + k * FS_TE;
+        float bv = 0.f;
+        if (idx < SC * Jp) {
+          const int sl = idx % SC, j = idx / SC;       // consecutive threads: consecutive slices
+          if (sl < sc && j < J) {
+            const int s = s0 + sl;
+            if (!f.A3) {
+              bv = 1.f;
+            } else if (!f.A4) {
+              bv = __ldg(&f.A3[s + (int64_t)f.N3 * j]);
+            } else {
+              const int i3 = s % f.N3, i4 = s / f.N3, c = j % f.r3, dd = j / f.r3;
+              bv = __ldg(&f.A3[i3 + (int64_t)f.N3 * c]) * __ldg(&f.A4[i4 + (int64_t)f.N4 * dd]);
+            }
+          }
+        }
+        bpre[k] = bv;
+      }
       float z[SC];
 #pragma unroll
       for (int u = 0; u < SC; ++u) {
@@ -746,40 +794,71 @@ __global__ void __launch_bounds__(FS_TE) k_tc_finish_sk(FinArgs f) {
         for (int u = 0; u < SC; ++u)
           if (u < sc) f.Z1[e + ne * (int64_t)(s0 + u)] = z[u];
       }
+      __syncthreads();                                   // the previous chunk is done with zs, fs_sm
       if (fw && j0 == 0) {
-        __syncthreads();                                 // the previous chunk's W is done with zs
 #pragma unroll
         for (int u = 0; u < SC; ++u) zs[u * FS_TE + tid] = (in && u < sc) ? z[u] : 0.f;
       }
-      __syncthreads();
-      for (int idx = tid; idx < SC * Jp; idx += blockDim.x) {
-        const int sl = idx / Jp, j = idx % Jp;
-        float bv = 0.f;
-        if (sl < sc && j < J) {
-          const int s = s0 + sl;
-          if (!f.A3) {
-            bv = 1.f;
-          } else if (!f.A4) {
-            bv = __ldg(&f.A3[s + (int64_t)f.N3 * j]);
-          } else {
-            const int i3 = s % f.N3, i4 = s / f.N3, c = j % f.r3, dd = j / f.r3;
-            bv = __ldg(&f.A3[i3 + (int64_t)f.N3 * c]) * __ldg(&f.A4[i4 + (int64_t)f.N4 * dd]);
-          }
-        }
-        fs_sm[sl * Jp + j] = bv;
+#pragma unroll
+      for (int k = 0; k < BPT; ++k) {
+        const int idx = tid + k * FS_TE;
+        if (idx < SC * Jp) fs_sm[(idx % SC) * Jp + idx / SC] = bpre[k];
       }
       __syncthreads();
       if (fw && j0 == 0) {
-        // W[a1, a2, s] = sum_i2 Z1[i2, a1, s] A2[i2, a2] for this CTA's whole columns a1
-        const int nout = na * f.r2 * sc;
-        for (int o = tid; o < nout; o += blockDim.x) {
-          const int b = o % f.r2, rest = o / f.r2, al = rest % na, u = rest / na;
-          const float* zc = zs + u * FS_TE + al * f.N2;
-          const float* ac = a2s + (f.N2 + 1) * b;
-          float w = 0.f;
-          for (int i2 = 0; i2 < f.N2; ++i2) w = fmaf(zc[i2], ac[i2], w);
-          const int a1 = a1_lo + al;
-          if (a1 < f.r1) f.W[a1 + (int64_t)f.r1 * (b + (int64_t)f.r2 * (s0 + u))] = w;
+        // W[a1, a2, s] = sum_i2 Z1[i2, a1, s] A2[i2, a2] for this CTA's whole columns a1: a
+        // warp per (a1, eight a2, four slices); lane (b, phase) sums i2 = phase (mod 4) for
+        // the four slices side by side, then the four phases are added by shuffles
+        if ((f.N2 & 3) == 0) {
+          // whole float4 runs of i2: a thread per output (a1, slice, a2), a2 fastest, two
+          // chains (even and odd runs) added at the end
+          const int nout = na * sc * f.r2;
+          for (int o = tid; o < nout; o += FS_TE) {
+            const int b = o % f.r2, rest = o / f.r2, u = rest % sc, al = rest / sc;
+            const float4* zc = reinterpret_cast<const float4*>(zs + u * FS_TE + al * f.N2);
+            const float4* ac = reinterpret_cast<const float4*>(a2s + a2st * b);
+            float w0 = 0.f, w1 = 0.f;
+            const int nq4 = f.N2 >> 2;
+            int q = 0;
+#pragma unroll 2
+            for (; q + 1 < nq4; q += 2) {
+              const float4 z0 = zc[q], a0 = ac[q], z1 = zc[q + 1], a1v = ac[q + 1];
+              w0 = fmaf(z0.x, a0.x, w0); w0 = fmaf(z0.y, a0.y, w0); w0 = fmaf(z0.z, a0.z, w0); w0 = fmaf(z0.w, a0.w, w0);
+              w1 = fmaf(z1.x, a1v.x, w1); w1 = fmaf(z1.y, a1v.y, w1); w1 = fmaf(z1.z, a1v.z, w1); w1 = fmaf(z1.w, a1v.w, w1);
+            }
+            if (q < nq4) {
+              const float4 z0 = zc[q], a0 = ac[q];
+              w0 = fmaf(z0.x, a0.x, w0); w0 = fmaf(z0.y, a0.y, w0); w0 = fmaf(z0.z, a0.z, w0); w0 = fmaf(z0.w, a0.w, w0);
+            }
+            const int a1 = a1_lo + al;
+            if (a1 < f.r1) f.W[a1 + (int64_t)f.r1 * (b + (int64_t)f.r2 * (s0 + u))] = w0 + w1;
+          }
+        } else {
+          const int nbg = (f.r2 + 7) >> 3, nug = (sc + 3) >> 2;
+          const int nitem = na * nbg * nug;
+          const int bl = lane & 7, ph = lane >> 3;
+          for (int item = warp; item < nitem; item += FS_TE / 32) {
+            const int bg = item % nbg, rest = item / nbg, al = rest % na, u0 = 4 * (rest / na);
+            const int b = bg * 8 + bl;
+            const float* zc = zs + u0 * FS_TE + al * f.N2;
+            const float* ac = a2s + a2st * (b < f.r2 ? b : f.r2 - 1);
+            float w[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll 4
+            for (int i2 = ph; i2 < f.N2; i2 += 4) {
+              const float av = ac[i2];
+#pragma unroll
+              for (int u = 0; u < 4; ++u) w[u] = fmaf(zc[u * FS_TE + i2], av, w[u]);
+            }
+            const int a1 = a1_lo + al;
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+              float x = w[u];
+              x += __shfl_xor_sync(0xffffffffu, x, 8);
+              x += __shfl_xor_sync(0xffffffffu, x, 16);
+              if (ph == 0 && b < f.r2 && a1 < f.r1 && u0 + u < sc)
+                f.W[a1 + (int64_t)f.r1 * (b + (int64_t)f.r2 * (s0 + u0 + u))] = x;
+            }
+          }
         }
       }
 #pragma unroll
@@ -814,6 +893,7 @@ __global__ void __launch_bounds__(FS_TE) k_tc_finish_sk(FinArgs f) {
 // Finish, split partials: output (e, j) of a tile is the sum of its nsplit partials in
 // split order (one thread per output, every load issued before the additions).
 __global__ void __launch_bounds__(256) k_tc_finish_red(FinArgs f) {
+  grid_dep_wait();                  // programmatic launch: the split partials are complete
   const int J = f.J;
   const int64_t per_tile = (int64_t)J * FS_TE;
   const int64_t total = (int64_t)(f.nt1 + f.nt2) * per_tile;
@@ -1170,9 +1250,10 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
     cudaFuncSetAttribute(k_tc_project, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemLimit);
     plan.attr_set = true;
   }
-  auto launch_project = [&](int cstep) {
+  // (the tuner launches it plainly: a programmatic launch would overlap the launch before)
+  auto launch_project = [&](int cstep, bool prog) {
     P.cstep = cstep;
-    if (pdl) {
+    if (prog) {
       cudaLaunchConfig_t cfg = {};
       cfg.gridDim = dim3(P.nq12 * cstep);
       cfg.blockDim = dim3(NUM_THREADS);
@@ -1201,8 +1282,10 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
     err = "finish: r_3 r_4 above 128";
     return TDB_ERR_UNSUPPORTED;
   }
+  // splits per tile: the grid stays within the target (whole waves of resident CTAs: two
+  // per SM), at least one split
   auto nsplit_for = [&](int target) {
-    int ns = (int)std::max<int64_t>(1, (target + nt1 + nt2 - 1) / (nt1 + nt2));
+    int ns = (int)std::max<int64_t>(1, target / (nt1 + nt2));
     ns = std::min({ns, std::max(1, nslice / FS_SC), FS_SPLIT_MAX});
     while (ns > 1 && (size_t)ns * (nt1 + nt2) * FS_TE * J > plan.fpart_cap) --ns;
     return ns;
@@ -1238,7 +1321,7 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   f.span = nullptr;
   f.dv2 = dv2;
   const size_t fsm = sizeof(float) * (FS_SC * ((J + 3) & ~3) +
-                                      (fuse_w ? FS_SC * FS_TE + (size_t)(N2 + 1) * r[1] : 0));
+                                      (fuse_w ? FS_SC * FS_TE + (size_t)a2_stride(N2) * r[1] : 0));
   if (fsm > 48 * 1024) {
     static bool fs_attr = false;
     if (!fs_attr) {
@@ -1251,18 +1334,32 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
     }
   }
   const int nqm = std::max(nq1, nq2);
+  // both finishing kernels start by programmatic launch behind the kernel before them (their
+  // set-up overlaps its tail; they wait for it before reading its results)
+  auto launch_pdl = [&](auto kern, int grid, int block, size_t sm) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = sm;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, f);
+    count_launch();
+  };
   auto launch_finish = [&](int nsplit) {
     f.nsplit = nsplit;
-    const dim3 fgrid((nt1 + nt2) * nsplit);
-    if (nqm <= 1) k_tc_finish_sk<1><<<fgrid, FS_TE, fsm, s>>>(f);
-    else if (nqm <= 2) k_tc_finish_sk<2><<<fgrid, FS_TE, fsm, s>>>(f);
-    else if (nqm <= 4) k_tc_finish_sk<4><<<fgrid, FS_TE, fsm, s>>>(f);
-    else k_tc_finish_sk<8><<<fgrid, FS_TE, fsm, s>>>(f);
-    count_launch();
+    const int fgrid = (nt1 + nt2) * nsplit;
+    if (nqm <= 1) launch_pdl(k_tc_finish_sk<1>, fgrid, FS_TE, fsm);
+    else if (nqm <= 2) launch_pdl(k_tc_finish_sk<2>, fgrid, FS_TE, fsm);
+    else if (nqm <= 4) launch_pdl(k_tc_finish_sk<4>, fgrid, FS_TE, fsm);
+    else launch_pdl(k_tc_finish_sk<8>, fgrid, FS_TE, fsm);
     if (nsplit > 1) {
       const int64_t outs = (int64_t)(nt1 + nt2) * J * FS_TE;
-      k_tc_finish_red<<<(int)std::min<int64_t>((outs + 255) / 256, 152 * 16), 256, 0, s>>>(f);
-      count_launch();
+      launch_pdl(k_tc_finish_red, (int)std::min<int64_t>((outs + 255) / 256, 152 * 16), 256, 0);
     }
   };
   // launch shape: tuned once per plan on its first call outside stream capture (cached
@@ -1272,7 +1369,7 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
     if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
       const TuneKey key{dev, N1, ld1, N2, nslice, r1pad, r2pad, J, p};
       if (!tune_lookup(key, plan)) {
-        tune_shape(plan, cmax, launch_project, [&](int target) {
+        tune_shape(plan, cmax, [&](int c) { launch_project(c, false); }, [&](int target) {
           f.nnp = P.nq12 * plan.cstep * NUM_CONV_WARPS;
           launch_finish(nsplit_for(target));
         }, s);
@@ -1286,7 +1383,7 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
   const int cstep = plan.tuned ? std::min(plan.cstep, cmax) : cmax;
   const int grid = P.nq12 * cstep;
   if (evm && !pdl) record_timing_event(evm[0], s);
-  launch_project(cstep);
+  launch_project(cstep, pdl);
   if (evm) record_timing_event(evm[1], s);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
