@@ -50,8 +50,9 @@ def parse_args():
                          "rk2_central uses central differences of the data and tdb_push_snapshot)")
     ap.add_argument("--train-steps", type=int, default=300,
                     help="steps of the separate training stream for the error estimator")
-    ap.add_argument("--api", default="slots", choices=["slots", "pointer"],
-                    help="slots: input slots + recorded step graphs (default); pointer: tdb_push_snapshot")
+    ap.add_argument("--api", default="pointer", choices=["slots", "pointer"],
+                    help="pointer: tdb_push_snapshot on the resident snapshots (default); slots: each "
+                         "snapshot copied into an input slot, recorded step graphs")
     ap.add_argument("--no-compare", action="store_true", help="skip the plain FP32 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -454,9 +455,13 @@ def run_tdb(args, world, rank, local):
         lib.tdb_get_profile(c.ctx, C.byref(prof))
         lib.tdb_set_profiling(c.ctx, 0)
         counters = c.counters()
+        try:
+            tuning = c.tuning() if prec == "bf16" else None
+        except tdb.TDBError:
+            tuning = None
         c.close()
         return {"ms": ms, "host_s": t_host, "eps": eps, "prof": prof, "clocks": clocks, "launches": launches,
-                "counters": counters, "acts": acts}
+                "counters": counters, "acts": acts, "tuning": tuning}
 
     # timed run: recorded steps, no instrumentation; then a profiled run of the same stream
     # (CUDA events around each phase and the projection kernel, recorded into the step's graph
@@ -520,6 +525,7 @@ def run_tdb(args, world, rank, local):
         "roofline": roofline, "clocks": res["clocks"], "gpu_launches": int(res["launches"]),
         "reinits": res["counters"]["reinits"], "exact_evals": res["counters"]["exact_evals"],
         "graph": {"replays": res["counters"]["graph_replays"], "records": res["counters"]["graph_records"]},
+        "tc_shape": res.get("tuning"),
     }
     if est_info is not None:
         line["estimator"] = dict(est_info, exact_eval_fraction=res["counters"]["exact_evals"] / max(K + W, 1))
@@ -558,8 +564,8 @@ def run_tdb(args, world, rank, local):
     # The line carries the faster (a large snapshot's copy hides the step; a small one's
     # does not pay for the second stream), the other beside it.
     if not args.no_e2e:
-        e2e_serial = run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_params, args.api,
-                             args.integrator)
+        e2e_serial = run_e2e(wl, precision, err_mode, dev, snaps, W, K, world, lib, tdb, est_params,
+                             "pointer" if args.integrator == "rk2_central" else "slots", args.integrator)
         e2e_serial["how"] = "each step's copy, then the step"
         e2e_pipe = run_e2e_pipelined(wl, precision, err_mode, dev, snaps, W, K, world, tdb, est_params,
                                      args.integrator)

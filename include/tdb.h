@@ -386,7 +386,9 @@ tdb_status tdb_selftest_timeout(int which, int64_t limit_cycles, unsigned* scrat
  * (CTAs), ncand = candidates timed (0 when the choice came from the cache), cand /
  * cand_us = up to 4 candidates and their microseconds per launch, fin_cand / fin_us = the
  * 3 split targets and theirs.  TDB_ERR_STATE before the first step or without the
- * tensor-core path. */
+ * tensor-core path.  The environment variable TDB_TC_SHAPE="ctas,target" (two positive
+ * integers) replaces the tuning by that shape (ctas clamped to the tile positions' slice
+ * count), e.g. to profile the shape a timed run chose. */
 tdb_status tdb_tc_tuning(const tdb_ctx* ctx, int* ctas, int* fin_target, int* ncand, int* cand, float* cand_us,
                          int* fin_cand, float* fin_us);
 

@@ -278,10 +278,17 @@ __global__ void __launch_bounds__(256) k_est_features(const EstState* __restrict
   } else if (wid == 3 && lane < 2 * F + 2) {
     nrm_s[lane] = norm[lane];
   }
-  float sf = 0.f;
-  for (int i = tid; i < nds; i += blockDim.x) sf = fmaf(dS[i], dS[i], sf);
-  const double s = block_sum((double)sf, sh);     // (its barriers also publish the values above)
   const EstState st = *stp;     // the host's estimator state of this step (device copy)
+  // ||dS||^2: eight loads in flight per thread
+  float sf = 0.f;
+  for (int i0 = tid; i0 < nds; i0 += 8 * 256) {
+    float v[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) v[k] = i0 + k * 256 < nds ? dS[i0 + k * 256] : 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) sf = fmaf(v[k], v[k], sf);
+  }
+  const double s = block_sum((double)sf, sh);     // (its barriers also publish the values above)
   if (tid == 0) {
     const double d2 = *dv2;
     const float res2 = (float)fmax(d2 - s, 0.0);

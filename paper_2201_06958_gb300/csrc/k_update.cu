@@ -321,13 +321,14 @@ __device__ __forceinline__ bool grid_sync(unsigned* count, unsigned k, unsigned 
     red_release_gpu(count, 1u);
     const unsigned target = k * nblocks;
     const long long t0 = clock64();
+    unsigned it = 0;
+    // one load per poll; the clock and another CTA's timeout flag every 32nd
     while (ld_acquire_gpu(count) < target) {
-      if (clock64() - t0 > limit || (ld_acquire_gpu(flags) & kFlagTimeout)) {
+      if ((++it & 31) == 0 && (clock64() - t0 > limit || (ld_acquire_gpu(flags) & kFlagTimeout))) {
         atomicOr(flags, kFlagTimeout);
         *abort_sh = 1;
         break;
       }
-      __nanosleep(20);
     }
   }
   __syncthreads();

@@ -20,6 +20,8 @@
 // Y_n (dS = Y_2 x_2 A_2^T follows in the update kernel or in a mode product).
 // Every wait is bounded: on timeout the kernel records a flag, stops issuing, drains
 // its own copies and frees TMEM before returning.
+#include <cstdio>
+#include <cstdlib>
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cudaTypedefs.h>
@@ -1368,7 +1370,15 @@ tdb_status tc_project(TcPlan& plan, const float* Vn, const float* Vp, int p, con
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
       const TuneKey key{dev, N1, ld1, N2, nslice, r1pad, r2pad, J, p};
-      if (!tune_lookup(key, plan)) {
+      // a fixed shape from the environment (reproducible profiles): TDB_TC_SHAPE="ctas,target"
+      const char* fixed = getenv("TDB_TC_SHAPE");
+      int fc = 0, ft = 0;
+      if (fixed && sscanf(fixed, "%d,%d", &fc, &ft) == 2 && fc > 0 && ft > 0) {
+        plan.cstep = std::min(fc, cmax);
+        plan.fin_target = ft;
+        plan.ncand = 0;
+        plan.from_cache = false;
+      } else if (!tune_lookup(key, plan)) {
         tune_shape(plan, cmax, [&](int c) { launch_project(c, false); }, [&](int target) {
           f.nnp = P.nq12 * plan.cstep * NUM_CONV_WARPS;
           launch_finish(nsplit_for(target));

@@ -1118,9 +1118,10 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
   // the step opens with one small kernel (step record cleared, host words fetched, the
   // estimator's sigma features - those of the state the step starts from - kept); an Euler
   // step's projection follows it by programmatic launch, so the projection's set-up
-  // (barriers, TMEM, the first loads) overlaps it.  Its events then bracket both.
+  // (barriers, TMEM, the first loads) overlaps it.  A profiled step launches the projection
+  // plainly, so that its events bracket that kernel alone.
   const bool begin_kernel = ctx->need_pin_d && ctx->est_pin_d;
-  const bool pdl = begin_kernel && ctx->use_tc && scheme == TDB_EULER;
+  const bool pdl = begin_kernel && ctx->use_tc && scheme == TDB_EULER && !ev;
   if (ctx->use_tc) ctx->tc.span = ev ? ctx->span_dev : nullptr;
   if (ev) CK(record_timing_event(ev[0], s));
   ctx->main_from_start = pdl;        // the projection's start event is the step's (ev[0])
