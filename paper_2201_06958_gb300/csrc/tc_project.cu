@@ -37,11 +37,12 @@ namespace tdb {
 namespace {
 
 constexpr int TILE = 128;
-constexpr int SUB_I1 = 128, SUB_I2 = 16;                 // one TMA box: the tile's i1 width x 16 rows of i2
+constexpr int SUB_I1 = 64, SUB_I2 = 16;                  // one TMA box: half the tile's i1 width x 16 rows of i2
 constexpr int NSTRIP = TILE / SUB_I2;                    // 8 strips per tile
-constexpr int BOX_BYTES = SUB_I1 * SUB_I2 * 4;           // 8 KB
-constexpr int STAGE_BYTES = 2 * BOX_BYTES;               // V_{k+1} and V_k boxes of one strip: 16 KB
-constexpr int NSTAGE = NSTRIP;                           // one stage per strip (and per converter warp)
+constexpr int NHALF = TILE / SUB_I1;                     // 2 halves (along i1) per strip
+constexpr int BOX_BYTES = SUB_I1 * SUB_I2 * 4;           // 4 KB
+constexpr int STAGE_BYTES = 2 * BOX_BYTES;               // V_{k+1} and V_k boxes of one half strip: 8 KB
+constexpr int NSTAGE = NSTRIP * NHALF;                   // stage 2c + h: half h of strip c (converter warp c)
 constexpr int BF_TILE_BYTES = TILE * TILE * 2;           // 32 KB
 constexpr int HALF_BYTES = BF_TILE_BYTES / 2;            // one 64-wide i1 half: 128 rows x 128 B
 constexpr int NUM_EPI_WARPS = 4;                         // warps 0..3 (TMEM lane quadrants 0..3)
@@ -280,7 +281,7 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   unsigned char* bf_tiles = smem;                                          // 2 x 32 KB
   unsigned char* b1_smem = bf_tiles + 2 * BF_TILE_BYTES;                   // A_1 blocks of this position
   unsigned char* b2_smem = b1_smem + ((P.b1_bytes + 1023) & ~1023);        // A_2 blocks
-  unsigned char* stages = b2_smem + ((P.b2_bytes + 1023) & ~1023);        // 8 x 16 KB
+  unsigned char* stages = b2_smem + ((P.b2_bytes + 1023) & ~1023);        // 16 x 8 KB
   uint64_t* bars = (uint64_t*)(stages + NSTAGE * STAGE_BYTES);
   uint64_t* full = bars;                    // [NSTAGE]
   uint64_t* empty = bars + NSTAGE;          // [NSTAGE]
@@ -301,9 +302,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   const int q1 = pos % P.nq1, q2 = pos / P.nq1;
   const int s_first = blockIdx.x / P.nq12;
 
-  // lane 0 of the TMA warp initialises the barriers; then lane j (< 8) of that warp, the
-  // owner of stage j, issues the first slice's strip j at once (every stage is free).  No
-  // other warp touches a barrier before the block-wide sync below.
+  // lane 0 of the TMA warp initialises the barriers; then lane j (< 16) of that warp, the
+  // owner of stage j (half j % 2 of strip j / 2), issues the first slice's half strip at once
+  // (every stage is free).  A stage whose rows lie past N2 or whose columns lie past N1 is
+  // neither loaded nor waited for, on both sides.  No other warp touches a barrier before
+  // the block-wide sync below.
   const int x_tile = q1 * TILE;
   if (warp == TMA_WARP) {
     if (lane == 0) {
@@ -324,13 +327,13 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       fence_proxy_async();
     }
     __syncwarp();
-    const int y = q2 * TILE + lane * SUB_I2;
-    if (lane < NSTRIP && s_first < P.nslice && y < P.N2) {
+    const int y = q2 * TILE + (lane >> 1) * SUB_I2, x = x_tile + (lane & 1) * SUB_I1;
+    if (lane < NSTAGE && s_first < P.nslice && y < P.N2 && x < P.N1) {
       const uint32_t fb = smem_u32(&full[lane]);
       mbar_arrive_expect_tx(fb, STAGE_BYTES);
       const uint32_t dst = smem_u32(stages + lane * STAGE_BYTES);
-      tma_load_3d(dst, &tmVn, x_tile, y, s_first, fb);
-      tma_load_3d(dst + BOX_BYTES, &tmVp, x_tile, y, s_first, fb);
+      tma_load_3d(dst, &tmVn, x, y, s_first, fb);
+      tma_load_3d(dst + BOX_BYTES, &tmVp, x, y, s_first, fb);
     }
   }
   if (warp == MMA_WARP) {
@@ -347,15 +350,14 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
   double acc_norm = 0.0;
 
   if (warp == TMA_WARP) {
-    if (lane < NSTRIP) {
-      // lane j refills stage j with strip j of each of this CTA's slices, as soon as its
-      // converter releases it; the eight lanes poll and issue side by side, so a burst of
-      // releases is refilled at once.  Strips wholly past N2 are neither loaded nor
-      // waited for, on both sides.
+    if (lane < NSTAGE) {
+      // lane j refills stage j with its half strip of each of this CTA's slices, as soon as
+      // its converter releases it; the sixteen lanes poll and issue side by side, so a burst
+      // of releases is refilled at once.
       const int j = lane;
       const int nt = s_first < P.nslice ? (P.nslice - 1 - s_first) / P.cstep + 1 : 0;
-      const int y = q2 * TILE + j * SUB_I2;
-      const bool in = y < P.N2;
+      const int y = q2 * TILE + (j >> 1) * SUB_I2, x = x_tile + (j & 1) * SUB_I1;
+      const bool in = y < P.N2 && x < P.N1;
       int tj = in ? (nt > 0 ? 1 : 0) : nt;      // slices loaded so far (the first at the start)
       const uint32_t fb = smem_u32(&full[j]), eb = smem_u32(&empty[j]);
       const uint32_t dst = smem_u32(stages + j * STAGE_BYTES);
@@ -365,8 +367,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
         if (mbar_test_wait(eb, (tj & 1) ^ 1)) {
           mbar_arrive_expect_tx(fb, STAGE_BYTES);
           const int sl = s_first + tj * P.cstep;
-          tma_load_3d(dst, &tmVn, x_tile, y, sl, fb);
-          tma_load_3d(dst + BOX_BYTES, &tmVp, x_tile, y, sl, fb);
+          tma_load_3d(dst, &tmVn, x, y, sl, fb);
+          tma_load_3d(dst + BOX_BYTES, &tmVp, x, y, sl, fb);
           ++tj;
           t0 = clock64();
           continue;
@@ -513,9 +515,11 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       if (lane == 0) mbar_arrive(smem_u32(&epi_done[buf]));
     }
   } else if (warp >= CONV_WARP0) {
-    // converter warp c owns strip c (rows c*16 .. c*16+15 of the tile's i2) and stage c:
-    // it forms dV in FP32, adds its weighted square to ||dV||_W^2, rounds to BF16 and
-    // writes both 64-wide i1 halves of the strip into the 128-byte-swizzled tile
+    // converter warp c owns strip c (rows c*16 .. c*16+15 of the tile's i2) and its two
+    // half-strip stages 2c, 2c + 1 (i1 halves): it forms dV in FP32, adds its weighted
+    // square to ||dV||_W^2, rounds to BF16 and writes the half into the 128-byte-swizzled
+    // tile, releasing each stage as soon as that half is converted (its refill then
+    // overlaps the other half's conversion)
     const int c = warp - CONV_WARP0;
     const int cx = lane & 15, ry = lane >> 4;
     const int chunk = cx >> 1, hoff = (cx & 1) * 8;
@@ -540,14 +544,16 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
       if (t >= 2 && !mbar_wait_warp(smem_u32(&mma_done[buf]), ((t >> 1) - 1) & 1, abort_flag, P.flags)) break;
       const double wsl = __ldg(&P.wsl[sl]);
       float acc = 0.f;
-      const bool have = strip_in && mbar_wait_warp(smem_u32(&full[c]), t & 1, abort_flag, P.flags);
-      if (strip_in && !have) { ok = false; break; }
-      const float4* vn = (const float4*)(stages + c * STAGE_BYTES);
-      const float4* vp = (const float4*)(stages + c * STAGE_BYTES + BOX_BYTES);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
+      for (int h = 0; h < NHALF; ++h) {
+        const int j = 2 * c + h;                      // this half's stage
+        const bool loaded = strip_in && half_in[h];
+        const bool have = loaded && mbar_wait_warp(smem_u32(&full[j]), t & 1, abort_flag, P.flags);
+        if (loaded && !have) { ok = false; break; }
+        const float4* vn = (const float4*)(stages + j * STAGE_BYTES);
+        const float4* vp = (const float4*)(stages + j * STAGE_BYTES + BOX_BYTES);
         unsigned char* half = bf_tiles + buf * BF_TILE_BYTES + h * HALF_BYTES;
-        if (!have || !half_in[h]) {
+        if (!have) {
           // outside the tensor: zeros in the BF16 tile
 #pragma unroll
           for (int k = 0; k < 8; ++k) {
@@ -559,8 +565,8 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
 #pragma unroll
         for (int k = 0; k < 8; ++k) {
           const int row = ry + 2 * k;                 // 0..15 within the strip
-          const float4 a = vn[row * 32 + h * 16 + cx];
-          const float4 b = vp[row * 32 + h * 16 + cx];
+          const float4 a = vn[row * 16 + cx];
+          const float4 b = vp[row * 16 + cx];
           // dV in FP32 pairs; sum_j w_1(j) dV_j^2 of the row's four columns, then times w_2
           const uint64_t d01 = f2_sub(f2(a.x, a.y), f2(b.x, b.y));
           const uint64_t d23 = f2_sub(f2(a.z, a.w), f2(b.z, b.w));
@@ -574,11 +580,10 @@ __global__ void __launch_bounds__(NUM_THREADS, 1)
           uint2 pk = make_uint2(pack_bf16x2(d0, d1), pack_bf16x2(d2, d3));
           *(uint2*)(half + r * 128 + ((chunk ^ (r & 7)) << 4) + hoff) = pk;
         }
-      }
-      if (have) {
         __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&empty[c]));
+        if (lane == 0) mbar_arrive(smem_u32(&empty[j]));
       }
+      if (!ok) break;
       acc_norm += (double)acc * wsl;
       fence_proxy_async();
       __syncwarp();
