@@ -157,7 +157,10 @@ struct tdb_ctx {
   float* trT = nullptr;
   int mlp_parts = 128;
   int tr_cap = 8192;
+  // recorded (features, target) rows: the last tr_cap rows from tr_off on (the rows before
+  // tr_off are dropped in one move once they number tr_cap, so each row costs O(1))
   std::vector<float> hX, hT;
+  size_t tr_off = 0;
   // profiling (CUDA events on the stream)
   bool prof = false;
   cudaEvent_t pev[6] = {nullptr};
@@ -1210,6 +1213,19 @@ tdb_status enqueue_step(tdb_ctx* ctx, const Tc* Vn, const Tc* Vp, bool all_paths
   return readback_enqueue(ctx);
 }
 
+// The recorded estimator rows: keep the last tr_cap; compact once the dropped rows number
+// tr_cap (amortised O(1) per row).
+void trace_trim(tdb_ctx* ctx) {
+  const size_t rows = ctx->hT.size();
+  if (rows - ctx->tr_off > (size_t)ctx->tr_cap) ctx->tr_off = rows - (size_t)ctx->tr_cap;
+  if (ctx->tr_off >= (size_t)ctx->tr_cap) {
+    ctx->hX.erase(ctx->hX.begin(), ctx->hX.begin() + ctx->tr_off * MLP_F);
+    ctx->hT.erase(ctx->hT.begin(), ctx->hT.begin() + ctx->tr_off);
+    ctx->tr_off = 0;
+  }
+}
+int trace_rows(const tdb_ctx* ctx) { return (int)(ctx->hT.size() - ctx->tr_off); }
+
 // After the step record is back: errors, rank control (Sec. 2.5), estimator bookkeeping,
 // the step info.
 template <typename Tc>
@@ -1267,12 +1283,9 @@ tdb_status finish_step(tdb_ctx* ctx, const Tc* Vn, tdb_step_info* info) {
   if (feats) {
     // training row: features and the change of log10 error over this step (target of the network)
     if (exact && eps > 0 && std::isfinite(eps)) {
-      if ((int)ctx->hT.size() >= ctx->tr_cap) {
-        ctx->hX.erase(ctx->hX.begin(), ctx->hX.begin() + MLP_F);
-        ctx->hT.erase(ctx->hT.begin());
-      }
       ctx->hX.insert(ctx->hX.end(), ctx->rb.feat, ctx->rb.feat + MLP_F);
       ctx->hT.push_back((float)(std::log10(eps) - ctx->est.last_log_eps));
+      trace_trim(ctx);
     }
     const double e_now = exact ? eps_after : eps;
     if (e_now > 0 && std::isfinite(e_now)) ctx->est.last_log_eps = std::log10(e_now);
@@ -1905,11 +1918,12 @@ const char* tdb_status_string(tdb_status s) {
 tdb_status tdb_estimator_fit(tdb_ctx* ctx, int iters, float lr, uint64_t seed, double gate, double* loss_out) {
   if (!ctx || iters < 1 || !(lr > 0) || !(gate > 0)) return TDB_ERR_INVALID_ARG;
   if (!ctx->ready || ctx->f64) { ctx->err = "estimator needs an initialised FP32/BF16 context"; return TDB_ERR_STATE; }
-  const int n = (int)ctx->hT.size();
+  const int n = trace_rows(ctx);
   if (n < 16) { ctx->err = "fewer than 16 exact evaluations recorded"; return TDB_ERR_STATE; }
   cudaStream_t s = ctx->stream;
-  CK(cudaMemcpyAsync(ctx->trX, ctx->hX.data(), sizeof(float) * n * MLP_F, cudaMemcpyHostToDevice, s));
-  CK(cudaMemcpyAsync(ctx->trT, ctx->hT.data(), sizeof(float) * n, cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ctx->trX, ctx->hX.data() + ctx->tr_off * MLP_F, sizeof(float) * n * MLP_F,
+                     cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(ctx->trT, ctx->hT.data() + ctx->tr_off, sizeof(float) * n, cudaMemcpyHostToDevice, s));
   est_normalize(ctx->trX, ctx->trT, n, ctx->mlpNorm, s);
   est_init_params(ctx->mlpP, (unsigned long long)seed, s);
   CK(cudaMemsetAsync(ctx->mlpM, 0, sizeof(float) * MLP_NPARAM, s));
@@ -1950,11 +1964,11 @@ tdb_status tdb_estimator_params(tdb_ctx* ctx, float* get_out, const float* set_i
 
 tdb_status tdb_estimator_trace(tdb_ctx* ctx, float* X, float* t, int* n) {
   if (!ctx || !n) return TDB_ERR_INVALID_ARG;
-  const int have = (int)ctx->hT.size();
+  const int have = trace_rows(ctx);
   if (X && t) {
     const int m = std::min(*n, have);
-    memcpy(X, ctx->hX.data(), sizeof(float) * m * MLP_F);
-    memcpy(t, ctx->hT.data(), sizeof(float) * m);
+    memcpy(X, ctx->hX.data() + ctx->tr_off * MLP_F, sizeof(float) * m * MLP_F);
+    memcpy(t, ctx->hT.data() + ctx->tr_off, sizeof(float) * m);
   }
   *n = have;
   return TDB_OK;
@@ -1965,15 +1979,11 @@ tdb_status tdb_estimator_load_trace(tdb_ctx* ctx, const float* X, const float* t
   if (!append) {
     ctx->hX.clear();
     ctx->hT.clear();
+    ctx->tr_off = 0;
   }
   ctx->hX.insert(ctx->hX.end(), X, X + (size_t)n * MLP_F);
   ctx->hT.insert(ctx->hT.end(), t, t + n);
-  const int have = (int)ctx->hT.size();
-  if (have > ctx->tr_cap) {
-    const int drop = have - ctx->tr_cap;
-    ctx->hX.erase(ctx->hX.begin(), ctx->hX.begin() + (size_t)drop * MLP_F);
-    ctx->hT.erase(ctx->hT.begin(), ctx->hT.begin() + drop);
-  }
+  trace_trim(ctx);
   return TDB_OK;
 }
 

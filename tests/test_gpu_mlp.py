@@ -143,3 +143,33 @@ def test_estimator_gain_in_device_time_stochastic(tdbmod):
     tot = lambda pr: pr["ms_project"] + pr["ms_update"] + pr["ms_error"]
     assert pa["ms_error"] < pb["ms_error"], (pa, pb)
     assert tot(pa) < tot(pb), (pa, pb)
+
+
+@cuda
+def test_trace_keeps_the_last_rows_in_order(tdbmod):
+    """The recorded (features, target) rows form a window of the last 8192, oldest first,
+    through loads, appends and a reset; dropping old rows keeps the order of the rest."""
+    wl = S.make_workload("reactive", nx=64, ny=32, ns=4)
+    c = tdbmod.TDB(wl.dims, [4, 4, 2], weights=wl.weights, precision="fp32", error_mode="exact")
+    c.init(wl.snapshot(0, device="cuda"))
+    F, cap = 8, 8192
+
+    def rows(lo, hi):
+        k = np.arange(lo, hi, dtype=np.float32)
+        return np.repeat(k[:, None], F, axis=1) + np.arange(F, dtype=np.float32) / 16, k * 0.5
+
+    X, t = rows(0, 20000)
+    c.estimator_load_trace(X, t)
+    gx, gt = c.estimator_trace()
+    assert gx.shape == (cap, F) and np.array_equal(gt, t[-cap:]) and np.array_equal(gx, X[-cap:])
+    for lo in range(20000, 20000 + 3 * cap, 977):           # appends past several compactions
+        X2, t2 = rows(lo, lo + 977)
+        c.estimator_load_trace(X2, t2, append=True)
+        X, t = np.concatenate([X, X2]), np.concatenate([t, t2])
+        gx, gt = c.estimator_trace()
+        assert np.array_equal(gt, t[-cap:]) and np.array_equal(gx, X[-cap:])
+    X3, t3 = rows(5, 105)
+    c.estimator_load_trace(X3, t3)                          # a reset
+    gx, gt = c.estimator_trace()
+    assert np.array_equal(gt, t3) and np.array_equal(gx, X3)
+    c.close()
