@@ -4,11 +4,13 @@
 // The snapshot is viewed as N1 x N2 x S (S = product of the modes after the second)
 // and cut into 128 x 128 (i1 x i2) tile positions.  Every CTA of the persistent grid
 // keeps one tile position and walks a strided set of the slices s:
-//   * TMA (cp.async.bulk.tensor) streams each 128 x 16 FP32 strip of V_{k+1} and V_k
-//     (8 KB boxes) into that strip's 16 KB shared-memory stage, eight strips per tile;
-//   * eight converter warps, one per strip and stage, form dV = V_{k+1} - V_k in FP32
-//     (before any rounding), accumulate ||dV||_W^2, round to BF16 and write the tile
-//     128-byte-swizzled;
+//   * TMA (cp.async.bulk.tensor) streams each 128 x 16 FP32 strip of V_{k+1} and V_k as
+//     two 64 x 16 halves (4 KB boxes) into two 8 KB shared-memory stages, eight strips per
+//     tile, sixteen stages, each refilled by its own lane of the TMA warp as soon as it
+//     frees;
+//   * eight converter warps, one per strip (two stages each), form dV = V_{k+1} - V_k in
+//     FP32 (before any rounding), accumulate ||dV||_W^2, round to BF16 and write the tile
+//     128-byte-swizzled, releasing each half's stage once it is converted;
 //   * one thread issues tcgen05.mma (kind::f16, BF16 x BF16 -> FP32 in TMEM) on that tile
 //     twice: as the K-major A operand of Z1 = dV x_1 A_1^T (M = i2, K = i1) and as the
 //     MN-major A operand of Z2 = dV x_2 A_2^T (M = i1, K = i2); the tile position's rows of
