@@ -38,7 +38,9 @@ UNIT = "snapshots/s"
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps; default: the workload's stream length (stochastic 500, reactive "
+                         "1000, channel 300, analytic 200, runge 400, batch 200)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="tdb", choices=["tdb", "reference"])
     ap.add_argument("--workload", default="stochastic",
@@ -907,8 +909,15 @@ def run_scaling_sweep(args):
                       "data": "synthetic", "config": {"workload": "runge N^3, t = 1, ranks (6, 6, 6) fixed"}}))
 
 
+# the configured stream length of each workload (its synthetic stream's step count)
+DEFAULT_STEPS = {"stochastic": 500, "reactive": 1000, "channel": 300, "analytic": 200, "runge": 400,
+                 "reactive_dbo": 1000, "reactive_tdb2": 1000, "batch": 200}
+
+
 def main():
     args = parse_args()
+    if args.steps is None:
+        args.steps = DEFAULT_STEPS.get(args.workload, 100)
     if args.integrator == "rk2_central":
         args.api = "pointer"          # its central differences need three snapshots; slots hold two
     if args.scaling_sweep:
