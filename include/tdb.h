@@ -276,8 +276,9 @@ tdb_status tdb_estimator_fit(tdb_ctx* ctx, int iters, float lr, uint64_t seed, d
  * feature means, feature scales, target mean, target scale) and / or install one
  * (set_in, same layout; gate > 0 replaces the gate factor).  Either may be NULL. */
 tdb_status tdb_estimator_params(tdb_ctx* ctx, float* get_out, const float* set_in, double gate);
-/* Recorded training rows: on input *n is the capacity of X (n x 8) and t (n); on
- * output the number recorded (X, t may be NULL to query). */
+/* Recorded training rows, oldest first (the most recent 8192; each exact evaluation of a
+ * float context adds one): on input *n is the capacity of X (n x 8) and t (n); on output
+ * the number recorded (X, t may be NULL to query). */
 tdb_status tdb_estimator_trace(tdb_ctx* ctx, float* X, float* t, int* n);
 /* Install training rows recorded elsewhere (e.g. tdb_estimator_trace of contexts run on
  * other streams) before tdb_estimator_fit: X (host, n x 8) and t (host, n) replace the
